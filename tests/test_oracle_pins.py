@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each check is a published value,
+a library routine that implements a textbook algorithm independently, a
+brute-force loop, an exactness theorem of the paper, or its error bound.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+import ttinputs as ti
+from oracle import linalg, philox, pstt2 as P, tt
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers(golden):
+    for row in golden("philox4x32_10_kat.txt"):
+        v = [int(t, 16) for t in row]
+        out = philox.philox4x32_10(*[np.uint64(c) for c in v[:4]], v[4], v[5])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_gaussian_moments_and_independence():
+    z = philox.test_matrix(seed=11, stream=3, nrows=50_000, ncols=8)
+    f = z.ravel()
+    n = f.size
+    assert abs(f.mean()) < 5.0 / math.sqrt(n)
+    assert abs(f.var() - 1.0) < 6.0 * math.sqrt(2.0 / n)
+    assert abs(np.mean(f ** 4) - 3.0) < 6.0 * math.sqrt(96.0 / n)
+    c = np.corrcoef(z.T)
+    assert np.max(np.abs(c - np.eye(8))) < 5.0 / math.sqrt(z.shape[0])
+    # different streams and seeds are different matrices
+    z2 = philox.test_matrix(seed=11, stream=4, nrows=1000, ncols=8)
+    z3 = philox.test_matrix(seed=12, stream=3, nrows=1000, ncols=8)
+    assert abs(np.corrcoef(z[:1000].ravel(), z2.ravel())[0, 1]) < 0.1
+    assert abs(np.corrcoef(z[:1000].ravel(), z3.ravel())[0, 1]) < 0.1
+
+
+def test_gaussian_rows_are_counter_addressed():
+    full = philox.test_matrix(5, 7, 300, 11)
+    rows = np.array([299, 0, 17, 17, 128], dtype=np.uint64)
+    np.testing.assert_array_equal(philox.gaussian(5, 7, rows, 11), full[rows.astype(int)])
+    # column j does not depend on how many columns are requested
+    np.testing.assert_array_equal(philox.test_matrix(5, 7, 300, 3), full[:, :3])
+    # 64-bit row indices use the high counter word
+    big = np.array([2 ** 32 + 5], dtype=np.uint64)
+    assert not np.allclose(philox.gaussian(5, 7, big, 4), full[5, :4])
+
+
+def test_round_to_matches_torch_bf16():
+    x = np.random.default_rng(0).standard_normal(10_000) * 10.0 ** np.random.default_rng(1).uniform(-5, 5, 10_000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(philox.round_to(x, "bf16"), ref)
+
+
+def test_round_to_tf32_cases():
+    # 1 + 2^-11 is a tie between 1 and 1 + 2^-10 -> even (1); 1 + 3*2^-11 -> 1 + 2^-9
+    cases = {1.0 + 2.0 ** -11: 1.0, 1.0 + 3 * 2.0 ** -11: 1.0 + 2.0 ** -9,
+             1.0 + 2.0 ** -10: 1.0 + 2.0 ** -10, -(1.0 + 2.0 ** -12): -1.0}
+    for a, b in cases.items():
+        assert philox.round_to(np.array([a]), "tf32")[0] == b
+    x = np.random.default_rng(2).standard_normal(1000)
+    r = philox.round_to(x, "tf32")
+    assert np.all(np.abs(r - x) <= 2.0 ** -11 * np.abs(x) * 1.0000001)
+
+
+# ---------------------------------------------------------------- QR / LS
+@pytest.mark.parametrize("m,n", [(40, 9), (9, 9), (6, 13), (300, 16)])
+def test_cpqr_matches_lapack_geqp3(m, n):
+    rng = np.random.default_rng(m * 100 + n)
+    A = rng.standard_normal((m, n)) * np.geomspace(1, 1e-3, n)[None, :]
+    Q, R, piv = linalg.householder_cpqr(A)
+    k = min(m, n)
+    Qs, Rs, ps = scipy.linalg.qr(A, pivoting=True, mode="economic")
+    np.testing.assert_array_equal(piv, ps)
+    np.testing.assert_allclose(np.abs(R), np.abs(Rs[:k]), atol=1e-12 * np.abs(Rs).max())
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(Q @ R, A[:, piv], atol=1e-13 * np.abs(A).max())
+    assert np.all(np.diag(R) >= 0)
+    assert np.all(np.diff(np.abs(np.diag(R))) <= 1e-12)  # rank-revealing order
+
+
+def test_cpqr_rank_deficient_and_ties():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((30, 3)) @ rng.standard_normal((3, 7))
+    Q, R, piv = linalg.householder_cpqr(A)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(7), atol=1e-12)
+    assert np.abs(R[3:, 3:]).max() < 1e-12 * np.abs(R).max()
+    # exact ties: identical columns -> lowest index first
+    B = np.tile(rng.standard_normal((10, 1)), (1, 4))
+    _, _, pb = linalg.householder_cpqr(B)
+    assert pb[0] == 0
+
+
+def test_lstsq_right_matches_numpy():
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((5, 12))
+    S = rng.standard_normal((50, 12))
+    H, rdiag = linalg.lstsq_right(S, B)
+    ref = np.linalg.lstsq(B.T, S.T, rcond=None)[0].T
+    np.testing.assert_allclose(H, ref, rtol=1e-11, atol=1e-12)
+    assert np.all(rdiag > 0)
+
+
+# ---------------------------------------------------------------- TT basics
+def test_unfold_is_column_major_reshape():
+    dims = [3, 4, 2, 5]
+    x = np.arange(120, dtype=np.float64)
+    for k in range(1, 4):
+        Xk = tt.unfold(x, dims, k)
+        for idx in [(0, 0, 0, 0), (2, 3, 1, 4), (1, 2, 0, 3)]:
+            L = idx[0] + 3 * idx[1] + 12 * idx[2] + 24 * idx[3]
+            Nk = int(np.prod(dims[:k]))
+            assert Xk[L % Nk, L // Nk] == x[L]
+
+
+def test_tt_full_matches_brute_force():
+    dims, r = [3, 4, 2, 3], [1, 2, 3, 2, 1]
+    cores = ti.random_tt_cores(dims, r, seed=9)
+    full = tt.tt_full(cores)
+    for L in range(full.size):
+        rem, idx = L, []
+        for n in dims:
+            idx.append(rem % n)
+            rem //= n
+        v = np.ones((1, 1))
+        for G, i in zip(cores, idx):
+            v = v @ G[:, i, :]
+        assert abs(full[L] - v[0, 0]) < 1e-12
+    assert tt.tt_storage([g.shape for g in cores]) == 6 + 24 + 12 + 6
+
+
+def test_table1_storage(golden):
+    for d, n, ranks, gb, mb in golden("table1_sizes.txt"):
+        d, n = int(d), int(n)
+        r = [int(v) for v in ranks.split(",")]
+        shapes = [(r[k], n, r[k + 1]) for k in range(d)]
+        entries = tt.tt_storage(shapes)
+        assert f"{entries * 8 / 2 ** 20:.3g}" == f"{float(mb):.3g}"
+        assert f"{8 * n ** d / 2 ** 30:.3g}" == gb
+
+
+def test_tt_svd_against_dense_svd():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((12, 9)) * np.geomspace(1, 1e-6, 9)[None, :] @ np.linalg.qr(rng.standard_normal((9, 9)))[0]
+    x = A.ravel(order="F")
+    cores = tt.tt_svd(x, [12, 9], eps=1e-3)
+    s = np.linalg.svd(A, compute_uv=False)
+    r = cores[0].shape[2]
+    err = np.linalg.norm(tt.tt_full(cores) - x)
+    assert abs(err - np.sqrt(np.sum(s[r:] ** 2))) < 1e-12 * s[0]
+    assert err <= 1e-3 * np.linalg.norm(x)
+    assert np.sqrt(np.sum(s[r - 1:] ** 2)) > 1e-3 * np.linalg.norm(x)  # minimal rank
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-8])
+def test_tt_svd_error_bound(eps):
+    dims = [6, 5, 4, 5]
+    x = ti.random_tt(dims, [1, 3, 4, 3, 1], seed=1, noise=1e-5)
+    cores = tt.tt_svd(x, dims, eps)
+    assert np.linalg.norm(tt.tt_full(cores) - x) <= eps * np.linalg.norm(x) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- PSTT2
+@pytest.mark.parametrize("passes", [1, 2])
+def test_exact_recovery_config1(passes):
+    dims = [16] * 4
+    x = ti.random_tt(dims, [1, 3, 4, 3, 1], seed=0)
+    o = P.pstt2(x, dims, ranks=[1, 4, 4, 4, 1], p=5, seed=1, passes=passes)
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+    assert [g.shape for g in o["cores"]] == [(1, 16, 4), (4, 16, 4), (4, 16, 4), (4, 16, 1)]
+
+
+@pytest.mark.parametrize("d", [2, 3, 5, 6, 7])
+@pytest.mark.parametrize("passes", [1, 2])
+def test_exact_recovery_any_order(d, passes):
+    dims = [4 + (k % 3) for k in range(d)]
+    r = [1] + [2 + (k % 2) for k in range(d - 1)] + [1]
+    x = ti.random_tt(dims, r, seed=d)
+    o = P.pstt2(x, dims, ranks=[1] + [4] * (d - 1) + [1], p=3, seed=d + 10, passes=passes)
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+
+
+def _proj_terms(x, dims, o):
+    d = len(dims)
+    ds = P.split_index(d)
+    terms = []
+    for k in range(1, d):
+        Xk = tt.unfold(x, dims, k)
+        if k < ds:
+            Q = o["Q"][k]
+            terms.append(np.linalg.norm(Xk - Q @ (Q.T @ Xk)) ** 2)
+        else:
+            Pk = o["P"][k]
+            terms.append(np.linalg.norm(Xk - (Xk @ Pk) @ Pk.T) ** 2)
+    return terms
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_twopass_deterministic_bound_eq_proj_acc(seed):
+    """Theorem 3.2 (eq. proj_acc) with its row-space mirror, per run."""
+    dims = [5, 6, 4, 5, 3]
+    x = ti.random_tt(dims, [1, 4, 5, 5, 3, 1], seed=seed, noise=1e-2)
+    o = P.pstt2(x, dims, ranks=[1, 2, 3, 3, 2, 1], p=2, seed=100 + seed, passes=2)
+    err2 = np.linalg.norm(x - tt.tt_full(o["cores"])) ** 2
+    assert err2 <= sum(_proj_terms(x, dims, o)) * (1 + 1e-10)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_onepass_deterministic_bound(seed):
+    """The one-pass bound of Theorem 3.3's proof: the middle term is replaced by
+    ||Z_{d*} - X_{d*}||^2 with Z_{d*} = H P_{d*}^T."""
+    dims = [5, 6, 4, 5]
+    x = ti.random_tt(dims, [1, 4, 5, 3, 1], seed=seed, noise=1e-2)
+    o = P.pstt2(x, dims, ranks=[1, 2, 3, 2, 1], p=3, seed=200 + seed, passes=1)
+    d, ds = 4, 2
+    terms = _proj_terms(x, dims, o)
+    Xm = tt.unfold(x, dims, ds)
+    terms[ds - 1] = np.linalg.norm(Xm - o["H"] @ o["P"][ds].T) ** 2
+    err2 = np.linalg.norm(x - tt.tt_full(o["cores"])) ** 2
+    assert err2 <= sum(terms) * (1 + 1e-10)
+
+
+def test_d2_reduces_to_range_finder():
+    """d = 2: two-pass PSTT2 is the randomized range finder on X^T; one-pass is
+    S B^+ P^T (the pseudo-inverse form of eq. onepass_final_core)."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((30, 6)) @ rng.standard_normal((6, 25)) + 1e-3 * rng.standard_normal((30, 25))
+    x = A.ravel(order="F")
+    r, p = 4, 3
+    o2 = P.pstt2(x, [30, 25], ranks=[1, r, 1], p=p, seed=3, passes=2)
+    Psi = philox.test_matrix(3, 64 + 1, 30, r + p)
+    Qs, _, _ = scipy.linalg.qr(A.T @ Psi, pivoting=True, mode="economic")
+    Pr = Qs[:, :r]
+    np.testing.assert_allclose(tt.tt_full(o2["cores"]), (A @ Pr @ Pr.T).ravel(order="F"), atol=1e-12)
+    o1 = P.pstt2(x, [30, 25], ranks=[1, r, 1], p=p, seed=3, passes=1)
+    Om = philox.test_matrix(3, 1, 25, r + p)
+    H = (A @ Om) @ np.linalg.pinv(Pr.T @ Om)
+    np.testing.assert_allclose(tt.tt_full(o1["cores"]), (H @ Pr.T).ravel(order="F"), atol=1e-11)
+
+
+def test_expected_error_bound_eq_sketch_bound():
+    """eq. (3.2): E||X - X~||^2 <= sum_j (1 + r_j/(p-1)) sum_{k>r_j} sigma_k^2(X_j),
+    checked on a seed average (two-pass, where Theorem 3.2's bound applies)."""
+    dims = [6, 5, 6]
+    x = ti.random_tt(dims, [1, 5, 5, 1], seed=3, noise=5e-2)
+    ranks = [1, 2, 2, 1]
+    p = 3
+    rhs = 0.0
+    for k in (1, 2):
+        s = np.linalg.svd(tt.unfold(x, dims, k), compute_uv=False)
+        rhs += (1 + ranks[k] / (p - 1)) * np.sum(s[ranks[k]:] ** 2)
+    errs = [np.linalg.norm(x - tt.tt_full(P.pstt2(x, dims, ranks=ranks, p=p, seed=s, passes=2)["cores"])) ** 2
+            for s in range(40)]
+    assert np.mean(errs) <= rhs
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_eps_mode_meets_tolerance(eps):
+    dims = [8, 7, 6, 7, 8]
+    x = ti.random_tt(dims, [1, 3, 4, 4, 3, 1], seed=4, noise=1e-7)
+    for passes in (1, 2):
+        o = P.pstt2(x, dims, eps=eps, rmax=8, p=6, seed=5, passes=passes)
+        assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= eps * np.linalg.norm(x)
+        assert o["r"][1:-1] == [3, 4, 4, 3]
+
+
+def test_sketches_match_brute_force_sums():
+    """Step 2 against the definition written as explicit sums over entries."""
+    dims = [3, 2, 4, 2]
+    x = ti.random_tt(dims, [1, 2, 2, 2, 1], seed=7)
+    l = 3
+    sk = P.sketches(x, dims, [None, l, l, l, l], seed=9, passes=1)
+    N = tt.prods(dims)
+    for k, S in sk["S"].items():
+        Om = philox.test_matrix(9, k, N[4] // N[k], l)
+        ref = np.zeros((N[k], l))
+        for L in range(N[4]):
+            ref[L % N[k]] += x[L] * Om[L // N[k]]
+        np.testing.assert_allclose(S, ref, atol=1e-12)
+    for k, R in sk["R"].items():
+        Ps = philox.test_matrix(9, 64 + k, N[k], l)
+        ref = np.zeros((N[4] // N[k], l))
+        for L in range(N[4]):
+            ref[L // N[k]] += x[L] * Ps[L % N[k]]
+        np.testing.assert_allclose(R, ref, atol=1e-12)
+
+
+def test_streaming_equals_one_shot():
+    dims = [6, 5, 4, 7]
+    x = ti.random_tt(dims, [1, 3, 3, 3, 1], seed=8, noise=1e-3)
+    full = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=4, seed=2, passes=1)
+    Nd1 = 6 * 5 * 4
+    slabs = [(a, c, x[a * Nd1:(a + c) * Nd1]) for a, c in [(4, 3), (0, 2), (2, 2)]]
+    st = P.pstt2_stream(slabs, dims, ranks=[1, 3, 3, 3, 1], p=4, seed=2)
+    np.testing.assert_allclose(tt.tt_full(st["cores"]), tt.tt_full(full["cores"]), atol=1e-12)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def test_planted_mistakes_are_caught(monkeypatch):
+    """A plausible slip in core assembly (a transposed operand) or in the
+    middle-core solve (a dropped pseudo-inverse) must break exact recovery."""
+    dims = [5, 4, 6, 5]
+    x = ti.random_tt(dims, [1, 2, 3, 2, 1], seed=1)
+    good = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=3, seed=4)
+    assert np.linalg.norm(x - tt.tt_full(good["cores"])) < 1e-12 * np.linalg.norm(x)
+
+    orig = P.outer_cores
+
+    def swapped(dims_, r, Q, Pb):
+        cores = orig(dims_, r, Q, Pb)
+        d = len(dims_)
+        cores[d - 1] = np.transpose(cores[d - 1], (2, 1, 0)).copy() if cores[d - 1].shape[0] == cores[d - 1].shape[2] else cores[d - 1][::-1].copy()
+        return cores
+
+    monkeypatch.setattr(P, "outer_cores", swapped)
+    bad = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=3, seed=4)
+    assert np.linalg.norm(x - tt.tt_full(bad["cores"])) > 1e-3 * np.linalg.norm(x)
+    monkeypatch.setattr(P, "outer_cores", orig)
+
+    monkeypatch.setattr(P, "lstsq_right", lambda S, B: (S[:, :B.shape[0]], np.ones(B.shape[0])))
+    bad2 = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=3, seed=4)
+    assert np.linalg.norm(x - tt.tt_full(bad2["cores"])) > 1e-3 * np.linalg.norm(x)
