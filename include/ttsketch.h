@@ -1,0 +1,234 @@
+/*
+ * ttsketch.h - C ABI of the GB300 (sm_103a) streaming two-sided TT sketch.
+ *
+ * The operation is PSTT2 / PSTT2-onepass of Shi, Ruth & Townsend, "Parallel
+ * algorithms for computing the tensor-train decomposition", Sec. 3.2:
+ * given a d-way tensor X (n_1 x ... x n_d), target TT ranks r or a tolerance
+ * eps, and an oversampling p, return TT cores G_1..G_d whose contraction X~
+ * approximates X with ||X - X~||_F <= eps ||X||_F (eq. (1.1), the problem
+ * statement of the paper; with ranks known, Sec. 4.1).
+ *
+ * Conventions used throughout:
+ *  - X is column-major with i_1 fastest (Sec. 2.1); the k-th unfolding X_k is
+ *    the same buffer seen as N_k x M_k, N_k = n_1..n_k, M_k = n_{k+1}..n_d.
+ *  - d* = ceil(d/2).  Column sketches S_k = X_k Omega_k (k < d*, plus k = d*
+ *    in one-pass mode), row sketches R_k = X_k^T Psi_k (k = d*..d-1).
+ *  - Omega_k / Psi_k are i.i.d. N(0,1) test matrices regenerated on the fly
+ *    from a Philox4x32-10 counter stream keyed by `seed` (never stored).
+ *  - Cores are FP64, written into ONE caller buffer: core k (1-based) lives
+ *    at element offset core_off[k] with the padded shape
+ *    rpad[k-1] x n_k x rpad[k], entry (a, i, c) at a + rpad[k-1] (i + n_k c);
+ *    entries outside the actual ranks are zero, so the padded cores
+ *    represent exactly the same tensor.  Actual ranks go to a device int
+ *    array of d+1 entries.  Nothing has to come back to the host, which keeps
+ *    every call asynchronous.
+ *
+ * Pointer kinds: "device" pointers are CUDA device (or managed) memory of the
+ * current device; "host" pointers are ordinary host memory.  All calls are
+ * asynchronous on `stream` unless stated otherwise; argument errors are
+ * returned synchronously; conditions found on the device (a singular
+ * least-squares matrix, a rank cap reached) are written to a status word in
+ * the workspace and reported by tt_query_status.  The library never traps or
+ * aborts the process.
+ *
+ * Ownership: the caller owns X, the workspace, the core buffer, the rank
+ * array and any gradient buffer.  A plan is a host object; it owns no device
+ * memory.  No call allocates device memory.  The workspace holds all state
+ * between the calls of one decomposition (sketches, bases, factorisations)
+ * and stays valid until the next tt_pstt2* call on the same workspace.
+ */
+#ifndef TTSKETCH_H
+#define TTSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_MAXD 16   /* largest supported order d                        */
+#define TT_MAXL 64   /* largest supported sketch width l = r + p          */
+
+typedef struct tt_plan_s* tt_plan_t;
+typedef void* tt_stream_t; /* a cudaStream_t; NULL means the legacy default stream */
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_INVALID_ARG = 1,     /* bad shape, rank, width, pointer or state      */
+  TT_ERR_UNSUPPORTED = 2,     /* valid request this build cannot serve          */
+  TT_ERR_CUDA = 3,            /* a CUDA runtime call failed                     */
+  TT_ERR_STATE = 4,           /* calls out of order (e.g. slab twice)           */
+  TT_ERR_RANK_DEFICIENT = 5,  /* device: B = P^T Omega (one-pass) is singular   */
+  TT_ERR_TIMEOUT = 6,         /* device: a bounded wait gave up                 */
+  TT_WARN_RANK_CAP = 7,       /* device: eps not met at rmax; cores still valid */
+  TT_ERR_NO_DEVICE = 8        /* no usable CUDA device                          */
+} tt_status;
+
+typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
+
+/* Arithmetic of the sketch (the hot loop).  The small solves (QR, least
+ * squares, core products) are always FP64.
+ *  FP64: FP64 FMA everywhere (the correctness path).
+ *  TF32 / BF16: tensor cores with FP32 accumulation, flushed into FP64 sketch
+ *    accumulators.  The test-matrix entries are rounded once to the MMA type;
+ *    X is split into a high and a low part of the MMA type (two products),
+ *    which keeps the error of the sketch near 2^-22 (TF32) / 2^-17 (BF16)
+ *    relative instead of 2^-11 / 2^-9. */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_TF32 = 1, TT_PREC_BF16 = 2 } tt_prec;
+
+typedef struct {
+  int d;                     /* order, 2 <= d <= TT_MAXD                         */
+  int64_t n[TT_MAXD];        /* mode sizes n_1..n_d (n[0..d-1]), each >= 1       */
+  double eps;                /* > 0: tolerance mode; == 0: fixed-rank mode       */
+  int ranks[TT_MAXD + 1];    /* fixed-rank mode: r_0..r_d, r_0 = r_d = 1         */
+  int rmax;                  /* tolerance mode: rank cap (sketch width rmax + p) */
+  int p;                     /* oversampling, >= 2 (Theorem 3.3 needs p >= 2)    */
+  uint64_t seed;             /* Philox key of the test matrices                  */
+  int passes;                /* 1 = PSTT2-onepass (hot path); 2 = PSTT2          */
+  tt_dtype x_dtype;          /* storage type of X                                */
+  tt_prec prec;              /* arithmetic of the sketch                         */
+} tt_problem;
+
+/* ---------------------------------------------------------------- plans */
+
+/* Build a host plan for one problem (Sec. 3.2: split d*, widths l_k = r_k + p
+ * or rmax + p, the sketch list, the workspace layout).  Host only; touches no
+ * device.  Fixed ranks are clamped to min(N_k, M_k).  On error *out = NULL. */
+tt_status tt_sketch_plan(const tt_problem* prob, tt_plan_t* out);
+
+/* Plan for `count` independent problems processed together by the batched
+ * calls (one persistent sketch launch over all of them).  Each problem gets
+ * its own slice of the workspace, core buffer and rank array. */
+tt_status tt_sketch_plan_batched(const tt_problem* probs, int count, tt_plan_t* out);
+
+void tt_plan_destroy(tt_plan_t plan);
+
+/* Sizes the caller must allocate: workspace bytes (device, 256-byte aligned
+ * base) and the number of FP64 entries of the core buffer (all items of a
+ * batched plan together).  Any pointer may be NULL. */
+tt_status tt_plan_sizes(tt_plan_t plan, size_t* workspace_bytes, int64_t* core_entries,
+                        int* rank_entries);
+
+/* Core layout of item `item` (0 for a single plan): core_off[k] for
+ * k = 1..d (index 0 unused; offsets are into the whole core buffer) and the
+ * padded ranks rpad[0..d].  Host arrays of TT_MAXD + 1 entries. */
+tt_status tt_plan_core_layout(tt_plan_t plan, int item, int64_t* core_off, int* rpad);
+
+/* Where sketch number `index` (0-based, in plan order: column sketches
+ * k = 1..d*-1, the one-pass middle sketch S_{d*}, then row sketches
+ * k = d*..d-1) of item `item` lives in the workspace: FP64, column-major,
+ * rows x width at byte offset *byte_off.  type: 0 = column sketch S_k = X_k
+ * Omega_k, 1 = row sketch R_k = X_k^T Psi_k.  For tests and inspection; the
+ * contents are valid after an accumulate and before the next finalize (the
+ * finalize factorises basis sketches in place).  TT_ERR_INVALID_ARG past
+ * the last sketch. */
+tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, int* k, int64_t* rows,
+                              int* width, int64_t* byte_off);
+
+/* Problem of item `item` as stored by the plan (ranks clamped). */
+tt_status tt_plan_problem(tt_plan_t plan, int item, tt_problem* out);
+
+/* ------------------------------------------------------------ forward */
+
+/* One-shot PSTT2 of X (device, x_dtype, prod(n) entries): zero the sketches,
+ * sketch every unfolding in one pass over X (a second pass in two-pass mode),
+ * then form the cores (= tt_pstt2_begin + one accumulate of the whole tensor
+ * + tt_pstt2_finalize). */
+tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* ranks,
+                   tt_stream_t stream);
+
+/* Streaming form (one-pass plans only).  begin zeroes the sketches; each
+ * accumulate adds the contribution of one slab, a contiguous range
+ * [first_last, first_last + count_last) of the LAST mode (device pointer to
+ * count_last * N_{d-1} entries), in any order, each index exactly once;
+ * finalize forms the cores.  The host checks the slab bookkeeping (a repeated
+ * or out-of-range index is TT_ERR_STATE / TT_ERR_INVALID_ARG). */
+tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream);
+tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_last,
+                              int64_t count_last, void* ws, tt_stream_t stream);
+tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
+                            tt_stream_t stream);
+
+/* Batched one-pass PSTT2: X_ptrs is a HOST array of `count` device pointers
+ * (one tensor per item).  All items are sketched by one persistent launch and
+ * finalized by batched launches; nothing synchronises, so the whole call can
+ * be captured in a CUDA graph. */
+tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores,
+                           int* ranks, tt_stream_t stream);
+
+/* ----------------------------------------------------------- backward */
+
+/* Adjoint of the one-pass map X -> cores with the pivots and ranks of the
+ * last forward call frozen (the map is then smooth): given dL/dcores (device,
+ * same padded layout as the cores), write dL/dX (device, x_dtype, prod(n)
+ * entries; overwritten).  X enters only through the sketches, so
+ * dX = sum_k Sbar_k Omega_k^T + sum_k Psi_k Rbar_k^T, with the test matrices
+ * regenerated from Philox.  Uses the state saved in ws by the forward call. */
+tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void* dX,
+                            tt_stream_t stream);
+
+/* ------------------------------------------------------ reconstruction */
+
+/* Dense X~ = G_1(:, i_1, :) ... G_d(:, i_d, :) (Sec. 2.2) from padded cores
+ * (device) into Xt (device, dtype, prod(n) entries).  Uses ws for the left
+ * and right interfaces. */
+tt_status tt_reconstruct(tt_plan_t plan, const double* cores, void* Xt, tt_dtype dtype, void* ws,
+                         tt_stream_t stream);
+
+/* Fused error: out2 (device, 2 doubles, overwritten) = [||X - X~||_F^2,
+ * ||X||_F^2] without materialising X~ (eq. (1.1)). */
+tt_status tt_reconstruct_error(tt_plan_t plan, const double* cores, const void* X, double* out2,
+                               void* ws, tt_stream_t stream);
+
+/* Adjoint of tt_reconstruct: dcores (device, padded layout, overwritten) from
+ * dL/dX~ (device, dtype). */
+tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const void* dXt,
+                                  tt_dtype dtype, double* dcores, void* ws, tt_stream_t stream);
+
+/* -------------------------------------------------------------- status */
+
+/* SYNCHRONOUS: waits for `stream`, then reads the workspace status word and
+ * the rank array.  status_host (may be NULL) receives TT_OK,
+ * TT_WARN_RANK_CAP, TT_ERR_RANK_DEFICIENT or TT_ERR_TIMEOUT (the worst seen
+ * over all items); ranks_host (may be NULL) receives rank_entries ints. */
+tt_status tt_query_status(tt_plan_t plan, const void* ws, const int* ranks, int* status_host,
+                          int* ranks_host, tt_stream_t stream);
+
+const char* tt_status_string(tt_status s);
+
+/* -------------------------------------------------------- test helpers */
+
+/* Test matrix entries (the Gaussian stream of the library) for rows
+ * [row0, row0 + nrows) and columns [0, ncols) of stream `stream_id`, written
+ * column-major to out (device, FP64, nrows x ncols) exactly as the sketch of
+ * precision `prec` uses them (FP64 values, or the FP32 generator rounded to
+ * TF32 / BF16). */
+tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nrows, int ncols,
+                         tt_prec prec, double* out, tt_stream_t stream);
+
+/* Raw Philox4x32-10 on `count` counters (device uint32 arrays of 4*count,
+ * key = (key0, key1)); out gets 4*count words. */
+tt_status tt_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
+                           int64_t count, tt_stream_t stream);
+
+/* Synthetic input: the Hilbert-type tensor 1/(x_{i_1} + ... + x_{i_d}),
+ * x_i = 1 + i/(n-1), for the slab [first_last, first_last + count_last) of
+ * the last mode, written to out (device, dtype).  The sum is formed in FP64
+ * from i_1 upwards, then rounded to dtype. */
+tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last,
+                                   int64_t count_last, void* out, tt_dtype dtype,
+                                   tt_stream_t stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter, incremented at every launch; for benchmarks that
+ * report how many of the library's kernels ran inside a timed region). */
+int64_t tt_kernel_launches(void);
+
+/* Library version string (build id). */
+const char* tt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTSKETCH_H */

@@ -18,7 +18,9 @@ Readings of the paper taken here (every one is listed in the design doc):
   consistent reading of eq. (3.5)).
 * A2  the one-pass extra sketch is on the column side: S_{d*} = X_{d*} Omega_{d*},
   H = S_{d*} (P_{d*}^T Omega_{d*})^+  (least squares through QR of B^T).
-* A3  sketch widths l_k = r_k + p (fixed-rank mode) or rmax + p (eps mode).
+* A3  sketch widths l_k = r_k + p (fixed-rank mode) or rmax + p (eps mode),
+  where a requested r_k is first clamped to min(N_k, M_k), the largest rank
+  X_k can have (eq. (2.1), r_k <= rank(X_k)).
 * A4  CPQR: largest recomputed column norm, lowest index on ties, diag(R)>=0.
 * A5  eps-mode rank: smallest r >= 1 with ||R_22^(r)||_F <= eps/sqrt(d-1) ||S||_F,
   capped at rmax (flagged) and at min(N_k, M_k).
@@ -48,6 +50,13 @@ def pick_rank_eps(R, eps, d, rmax, rcap):
         if tail <= thr:
             return r, False
     return max(limit, 1), True
+
+
+def clamp_ranks(dims, ranks):
+    """r_k <= min(N_k, M_k) (eq. (2.1): r_k <= rank(X_k))."""
+    N = prods(dims)
+    d = len(dims)
+    return [1] + [min(int(ranks[k]), N[k], N[d] // N[k]) for k in range(1, d)] + [1]
 
 
 def sketch_widths(d, ranks, p, eps_mode, rmax):
@@ -169,6 +178,7 @@ def pstt2(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, passes=1,
         ranks = [int(v) for v in ranks]
         if len(ranks) != d + 1:
             raise ValueError("ranks needs d+1 entries")
+        ranks = clamp_ranks(dims, ranks)
     ds = split_index(d)
     widths = sketch_widths(d, ranks, p, eps_mode, rmax)
     sk = sketches(x, dims, widths, seed, passes, test_fmt)
@@ -196,6 +206,8 @@ def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1):
     ds = split_index(d)
     N = prods(dims)
     eps_mode = eps is not None and eps > 0
+    if not eps_mode:
+        ranks = clamp_ranks(dims, ranks)
     widths = sketch_widths(d, ranks, p, eps_mode, rmax)
     S = {k: np.zeros((N[k], widths[k] if k < ds else widths[ds])) for k in range(1, ds + 1)}
     R = {k: np.zeros((N[d] // N[k], widths[k])) for k in range(ds, d)}

@@ -1,0 +1,191 @@
+"""Python wrapper of one plan: device buffers as torch tensors, calls through
+the C ABI (argument marshalling only)."""
+import ctypes as C
+
+import torch
+
+from . import _native as N
+
+_DT = {torch.float32: N.TT_F32, torch.float64: N.TT_F64}
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class TTSketch:
+    """One decomposition problem (or a batch of them) with its device state.
+
+    dims: mode sizes; ranks (fixed-rank mode, [1, r_1, .., r_{d-1}, 1]) or eps
+    (> 0, tolerance mode, with rmax); p: oversampling; seed: Philox key;
+    passes: 1 (one-pass, the hot path) or 2; x_dtype: torch.float32/float64;
+    prec: 'fp64' | 'tf32' | 'bf16'.
+    """
+
+    PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
+
+    def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
+                 x_dtype=torch.float32, prec="fp64", device="cuda", batch=None):
+        L = N.lib()
+        self.device = torch.device(device)
+        if batch is None:
+            probs = [dict(dims=dims, ranks=ranks, eps=eps, rmax=rmax, p=p, seed=seed)]
+        else:
+            probs = batch
+        arr = (N.tt_problem * len(probs))()
+        for i, pr in enumerate(probs):
+            arr[i] = N.make_problem(pr["dims"], ranks=pr.get("ranks"), eps=pr.get("eps", eps),
+                                    rmax=pr.get("rmax", rmax), p=pr.get("p", p),
+                                    seed=pr.get("seed", seed), passes=passes,
+                                    x_dtype=_DT[x_dtype], prec=self.PRECS[prec])
+        h = C.c_void_p()
+        if batch is None:
+            N.check(L.tt_sketch_plan(C.byref(arr[0]), C.byref(h)), "tt_sketch_plan")
+        else:
+            N.check(L.tt_sketch_plan_batched(arr, len(probs), C.byref(h)), "tt_sketch_plan_batched")
+        self.plan = h
+        self.count = len(probs)
+        self.x_dtype = x_dtype
+        ws, ce, re_ = C.c_size_t(), C.c_int64(), C.c_int()
+        N.check(L.tt_plan_sizes(h, C.byref(ws), C.byref(ce), C.byref(re_)), "tt_plan_sizes")
+        self.ws_bytes, self.core_entries, self.rank_entries = ws.value, ce.value, re_.value
+        self.items = []
+        for i in range(self.count):
+            off = (C.c_int64 * (N.TT_MAXD + 1))()
+            rp = (C.c_int * (N.TT_MAXD + 1))()
+            N.check(L.tt_plan_core_layout(h, i, off, rp), "tt_plan_core_layout")
+            q = N.tt_problem()
+            N.check(L.tt_plan_problem(h, i, C.byref(q)), "tt_plan_problem")
+            d = q.d
+            self.items.append(dict(d=d, dims=[q.n[k] for k in range(d)],
+                                   core_off=[off[k] for k in range(d + 1)],
+                                   rpad=[rp[k] for k in range(d + 1)]))
+        self.dims = self.items[0]["dims"]
+        self.d = self.items[0]["d"]
+        self.ws = torch.empty(max(self.ws_bytes, 8) // 8 + 32, dtype=torch.float64, device=self.device)
+        self.cores = torch.zeros(max(self.core_entries, 1), dtype=torch.float64, device=self.device)
+        self.ranks = torch.zeros(max(self.rank_entries, 1), dtype=torch.int32, device=self.device)
+
+    def __del__(self):
+        try:
+            if getattr(self, "plan", None):
+                N.lib().tt_plan_destroy(self.plan)
+                self.plan = None
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- forward
+    def pstt2(self, X, stream=None):
+        N.check(N.lib().tt_pstt2(self.plan, _ptr(X), _ptr(self.ws), _ptr(self.cores), _ptr(self.ranks),
+                                 _stream(stream)), "tt_pstt2")
+        return self
+
+    def begin(self, stream=None):
+        N.check(N.lib().tt_pstt2_begin(self.plan, _ptr(self.ws), _stream(stream)), "tt_pstt2_begin")
+
+    def accumulate(self, slab, first, count, stream=None):
+        N.check(N.lib().tt_pstt2_accumulate(self.plan, _ptr(slab), int(first), int(count), _ptr(self.ws),
+                                            _stream(stream)), "tt_pstt2_accumulate")
+
+    def finalize(self, stream=None):
+        N.check(N.lib().tt_pstt2_finalize(self.plan, _ptr(self.ws), _ptr(self.cores), _ptr(self.ranks),
+                                          _stream(stream)), "tt_pstt2_finalize")
+        return self
+
+    def batched(self, Xs, stream=None):
+        arr = (C.c_void_p * len(Xs))(*[x.data_ptr() for x in Xs])
+        N.check(N.lib().tt_pstt2_batched(self.plan, arr, _ptr(self.ws), _ptr(self.cores), _ptr(self.ranks),
+                                         _stream(stream)), "tt_pstt2_batched")
+        return self
+
+    def backward(self, dcores, dX, stream=None):
+        N.check(N.lib().tt_pstt2_backward(self.plan, _ptr(self.ws), _ptr(dcores), _ptr(dX), _stream(stream)),
+                "tt_pstt2_backward")
+
+    # -------------------------------------------------------- reconstruction
+    def reconstruct(self, dtype=torch.float64, cores=None, stream=None):
+        n = 1
+        for v in self.dims:
+            n *= v
+        out = torch.empty(n, dtype=dtype, device=self.device)
+        N.check(N.lib().tt_reconstruct(self.plan, _ptr(self.cores if cores is None else cores), _ptr(out),
+                                       _DT[dtype], _ptr(self.ws), _stream(stream)), "tt_reconstruct")
+        return out
+
+    def error(self, X, stream=None, cores=None):
+        out2 = torch.empty(2, dtype=torch.float64, device=self.device)
+        N.check(N.lib().tt_reconstruct_error(self.plan, _ptr(self.cores if cores is None else cores), _ptr(X),
+                                             _ptr(out2), _ptr(self.ws), _stream(stream)),
+                "tt_reconstruct_error")
+        return out2
+
+    def reconstruct_backward(self, dXt, stream=None):
+        dc = torch.empty_like(self.cores)
+        N.check(N.lib().tt_reconstruct_backward(self.plan, _ptr(self.cores), _ptr(dXt), _DT[dXt.dtype],
+                                                _ptr(dc), _ptr(self.ws), _stream(stream)),
+                "tt_reconstruct_backward")
+        return dc
+
+    def sketches(self, item=0):
+        """Every sketch of one item, read from the workspace: list of
+        (type, k, tensor rows x width) -- valid between accumulate and finalize."""
+        out = []
+        i = 0
+        while True:
+            ty, k, w = C.c_int(), C.c_int(), C.c_int()
+            rows, off = C.c_int64(), C.c_int64()
+            st = N.lib().tt_plan_sketch_info(self.plan, item, i, C.byref(ty), C.byref(k), C.byref(rows),
+                                             C.byref(w), C.byref(off))
+            if st != N.TT_OK:
+                break
+            flat = self.ws[off.value // 8: off.value // 8 + rows.value * w.value]
+            out.append((ty.value, k.value, flat.reshape(w.value, rows.value).T))
+            i += 1
+        return out
+
+    # ---------------------------------------------------------------- status
+    def status(self, stream=None):
+        st = C.c_int()
+        rk = (C.c_int * max(self.rank_entries, 1))()
+        N.check(N.lib().tt_query_status(self.plan, _ptr(self.ws), _ptr(self.ranks), C.byref(st), rk,
+                                        _stream(stream)), "tt_query_status")
+        return st.value, list(rk)[:self.rank_entries]
+
+    def core_list(self, item=0):
+        """Cores of one item as host float64 arrays of shape (r_{k-1}, n_k, r_k)
+        (actual ranks, padding removed)."""
+        import numpy as np
+        it = self.items[item]
+        _, ranks = self.status()
+        base = sum(self.items[i]["d"] + 1 for i in range(item))
+        r = ranks[base:base + it["d"] + 1]
+        host = self.cores.cpu().numpy()
+        out = []
+        for k in range(1, it["d"] + 1):
+            rp0, rp1, n = it["rpad"][k - 1], it["rpad"][k], it["dims"][k - 1]
+            G = host[it["core_off"][k]:it["core_off"][k] + rp0 * n * rp1].reshape((rp0, n, rp1), order="F")
+            out.append(np.ascontiguousarray(G[:r[k - 1], :, :r[k]]))
+        return out
+
+
+def pstt2(X, dims, **kw):
+    """One-shot convenience: returns the TTSketch holding the cores."""
+    t = TTSketch(dims, x_dtype=X.dtype, **kw)
+    return t.pstt2(X)
+
+
+def tt_entries_from_cores(cores, idx):
+    """Evaluate a TT at given multi-indices on the host (float64), for checks."""
+    import numpy as np
+    out = np.empty(len(idx))
+    for m, ii in enumerate(idx):
+        v = np.ones((1,))
+        for G, i in zip(cores, ii):
+            v = v @ G[:, int(i), :]
+        out[m] = v[0]
+    return out

@@ -1,0 +1,748 @@
+// FP64 finalize: orthonormal bases, ranks, the one-pass middle core and the
+// core products (Sec. 3.2; Algorithm 2 steps 4-8; eq. (3.1) and its row-space
+// mirror; eq. (3.3) for the middle core).
+//
+// Bases.  The paper takes a CPQR of each sketch and keeps Q(:, 1:r_k); it
+// forms the ON bases of the distributed sketches with a skinny (TSQR) QR
+// (Sec. 4.2, Benson et al.).  Here every basis sketch Y (m x l, m up to
+// n^{ceil(d/2)}) is reduced by a TSQR tree of Householder QRs of row blocks;
+// the CPQR is taken on the l x l root factor R, which has the same column
+// norms and inner products as Y (Y = Q_1 R), so it selects the same pivots:
+// R Pi = Q_2 Rt.  Then Q_k = Q_1 Q_2(:, 1:r_k), formed top-down through the
+// tree.  Signs are normalised so that diag(Rt) >= 0.
+//
+// Ranks.  Fixed-rank mode keeps the (clamped) target.  Tolerance mode takes
+// the smallest r with ||Rt(r:, r:)||_F <= eps/sqrt(d-1) ||Y||_F (the per-
+// unfolding split of Theorem 3.2), capped at rmax; the cap is flagged.  Ranks
+// stay on the device; later kernels read them from there.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace tts {
+
+const DevSketch* plan_sketches_host(const Plan* p);
+int plan_num_items(const Plan* p);
+int plan_max_lev(const Plan* p);
+int plan_ntasks(const Plan* p, int lev);
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int64_t kTableOffB = 256;
+
+__device__ __forceinline__ const DevTables& tables(const char* wsb) {
+  return *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
+}
+__device__ __forceinline__ const DevSketch* dsk(const char* wsb) {
+  return reinterpret_cast<const DevSketch*>(wsb + tables(wsb).off_sketches);
+}
+__device__ __forceinline__ const DevItem* ditems(const char* wsb) {
+  return reinterpret_cast<const DevItem*>(wsb + tables(wsb).off_items);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (all threads get the result).  Uses red[32].
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// In-shared-memory Householder QR of an nr x w block A (ld = lda), nr >= 1.
+// On exit column i holds v_i in rows i..nr-1 (v_i(0) at the diagonal), beta[i]
+// = 2 / (v_i^T v_i) (0 for a zero column), rdiag[i] = R(i, i); the strict
+// upper triangle holds R.
+__device__ void house_qr(double* A, int lda, int nr, int w, double* beta, double* rdiag,
+                         double* red) {
+  const int kmax = min(nr, w);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = 0; i < kmax; ++i) {
+    double part = 0.0;
+    for (int r = i + threadIdx.x; r < nr; r += blockDim.x) part += A[r + lda * i] * A[r + lda * i];
+    const double nsq = block_sum(part, red);
+    const double x0 = A[i + lda * i];
+    const double nx = sqrt(nsq);
+    double alpha = 0.0, b = 0.0;
+    if (nx > 0.0) {
+      alpha = -copysign(nx, x0);
+      const double v0 = x0 - alpha;
+      const double vn2 = nsq - x0 * x0 + v0 * v0;
+      b = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      A[i + lda * i] = (nx > 0.0) ? x0 - alpha : 0.0;
+      beta[i] = b;
+      rdiag[i] = alpha;
+    }
+    __syncthreads();
+    if (b != 0.0) {
+      for (int c = i + 1 + wid; c < w; c += nw) {
+        double dot = 0.0;
+        for (int r = i + lane; r < nr; r += 32) dot += A[r + lda * i] * A[r + lda * c];
+        dot = warp_sum(dot) * b;
+        for (int r = i + lane; r < nr; r += 32) A[r + lda * c] -= dot * A[r + lda * i];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = kmax + threadIdx.x; i < w; i += blockDim.x) {
+    beta[i] = 0.0;
+    rdiag[i] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Apply the reflectors of a block (V: nr x w in global or shared, ld = ldv,
+// beta) to Z (nr x ncol, ld = ldz):  Z <- H_0 ... H_{k-1} Z.
+__device__ void apply_q(const double* V, int64_t ldv, const double* beta, int nr, int w, double* Z,
+                        int64_t ldz, int ncol) {
+  const int kmax = min(nr, w);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = kmax - 1; i >= 0; --i) {
+    const double b = beta[i];
+    if (b != 0.0) {
+      for (int c = wid; c < ncol; c += nw) {
+        double dot = 0.0;
+        for (int r = i + lane; r < nr; r += 32) dot += V[r + ldv * i] * Z[r + ldz * c];
+        dot = warp_sum(dot) * b;
+        for (int r = i + lane; r < nr; r += 32) Z[r + ldz * c] -= dot * V[r + ldv * i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void flag_status(char* wsb, int bits) {
+  atomicOr(reinterpret_cast<int*>(wsb + kStatusOff), bits);
+}
+
+// ------------------------------------------------------------------ TSQR up
+// One task = one row block of level L of one basis sketch.  Non-root blocks
+// write their R into the next level's matrix; the root block also does the
+// CPQR of R, the rank decision and the first expansion step.
+__global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, int* ranks) {
+  extern __shared__ double sm[];
+  const DevTables& T = tables(wsb);
+  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[L])[blockIdx.x];
+  const DevSketch s = dsk(wsb)[task.sk];
+  const DevItem& it = ditems(wsb)[s.item];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int w = s.width;
+  const int64_t m = s.lev_rows[L];
+  const int64_t r0 = (int64_t)task.blk * s.bl;
+  const int nr = (int)imin64(s.bl, m - r0);
+  const int lda = nr + 1;
+  double* A = sm;                         // lda x w
+  double* red = A + (size_t)lda * w;      // 32
+  double* beta = red + 32;                // w
+  double* rdiag = beta + TT_MAXL;         // w
+  double* Rs = rdiag + TT_MAXL;           // w x w (root only)
+  double* Q2 = Rs + TT_MAXL * TT_MAXL;    // w x w (root only)
+  __shared__ int piv[TT_MAXL];
+  __shared__ int s_rank;
+  double* Y = ws + s.lev_mat[L];
+  for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
+    const int r = o % nr, c = o / nr;
+    A[r + lda * c] = Y[r0 + r + m * c];
+  }
+  __syncthreads();
+  house_qr(A, lda, nr, w, beta, rdiag, red);
+  const int kmax = min(nr, w);
+  // Householder vectors back in place, scalars to the level's beta array
+  for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
+    const int r = o % nr, c = o / nr;
+    Y[r0 + r + m * c] = A[r + lda * c];
+  }
+  for (int i = threadIdx.x; i < w; i += blockDim.x) ws[s.lev_beta[L] + (int64_t)task.blk * w + i] = beta[i];
+  auto rval = [&](int i, int c) -> double {
+    if (i >= kmax || c < i) return 0.0;
+    return c == i ? rdiag[i] : A[i + lda * c];
+  };
+  const bool root = (s.lev_nblk[L] == 1);
+  if (!root) {
+    const int64_t m1 = s.lev_rows[L + 1];
+    double* Yn = ws + s.lev_mat[L + 1];
+    for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
+      const int i = o % w, c = o / w;
+      Yn[(int64_t)task.blk * w + i + m1 * c] = rval(i, c);
+    }
+    return;
+  }
+  // ---- root: CPQR of R (w x w) in shared memory
+  for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
+    const int i = o % w, c = o / w;
+    Rs[i + w * c] = rval(i, c);
+  }
+  for (int c = threadIdx.x; c < w; c += blockDim.x) piv[c] = c;
+  __syncthreads();
+  __shared__ double nrm[TT_MAXL];
+  __shared__ double qb[TT_MAXL], qd[TT_MAXL];
+  double total2 = 0.0;
+  for (int o = threadIdx.x; o < w * w; o += blockDim.x) total2 += Rs[o] * Rs[o];
+  total2 = block_sum(total2, red);
+  for (int i = 0; i < w; ++i) {
+    for (int c = i + threadIdx.x; c < w; c += blockDim.x) {
+      double t = 0.0;
+      for (int r = i; r < w; ++r) t += Rs[r + w * c] * Rs[r + w * c];
+      nrm[c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int j = i;
+      for (int c = i + 1; c < w; ++c)
+        if (nrm[c] > nrm[j]) j = c;
+      if (j != i) {
+        for (int r = 0; r < w; ++r) {
+          const double t = Rs[r + w * i];
+          Rs[r + w * i] = Rs[r + w * j];
+          Rs[r + w * j] = t;
+        }
+        const int t = piv[i];
+        piv[i] = piv[j];
+        piv[j] = t;
+      }
+    }
+    __syncthreads();
+    // Householder on column i, rows i..w-1 (w <= 64: one warp is enough)
+    if (threadIdx.x < 32) {
+      double part = 0.0;
+      for (int r = i + threadIdx.x; r < w; r += 32) part += Rs[r + w * i] * Rs[r + w * i];
+      const double nsq = warp_sum(part);
+      const double x0 = Rs[i + w * i];
+      const double nx = sqrt(nsq);
+      double alpha = 0.0, b = 0.0;
+      if (nx > 0.0) {
+        alpha = -copysign(nx, x0);
+        const double v0 = x0 - alpha;
+        const double vn2 = nsq - x0 * x0 + v0 * v0;
+        b = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+      }
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        Rs[i + w * i] = nx > 0.0 ? x0 - alpha : 0.0;
+        qb[i] = b;
+        qd[i] = alpha;
+      }
+    }
+    __syncthreads();
+    const double b = qb[i];
+    if (b != 0.0) {
+      for (int c = i + 1 + threadIdx.x; c < w; c += blockDim.x) {
+        double dot = 0.0;
+        for (int r = i; r < w; ++r) dot += Rs[r + w * i] * Rs[r + w * c];
+        dot *= b;
+        for (int r = i; r < w; ++r) Rs[r + w * c] -= dot * Rs[r + w * i];
+      }
+    }
+    __syncthreads();
+  }
+  // Q2 = H_0 ... H_{w-1} I
+  for (int o = threadIdx.x; o < w * w; o += blockDim.x) Q2[o] = (o % w == o / w) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int i = w - 1; i >= 0; --i) {
+    const double b = qb[i];
+    if (b != 0.0) {
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        double dot = 0.0;
+        for (int r = i; r < w; ++r) dot += Rs[r + w * i] * Q2[r + w * c];
+        dot *= b;
+        for (int r = i; r < w; ++r) Q2[r + w * c] -= dot * Rs[r + w * i];
+      }
+    }
+    __syncthreads();
+  }
+  // Rt with signs normalised (diag >= 0), Q2 columns likewise
+  double* Rt = ws + s.off_rt;
+  for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
+    const int i = o % w, c = o / w;
+    const double sg = qd[i] < 0.0 ? -1.0 : 1.0;
+    double v = 0.0;
+    if (c > i) v = Rs[i + w * c];
+    else if (c == i) v = qd[i];
+    Rt[o] = sg * v;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
+    const int c = o / w;
+    const double sg = qd[c] < 0.0 ? -1.0 : 1.0;
+    Q2[o] *= sg;
+    ws[s.off_q2 + o] = Q2[o];
+  }
+  for (int c = threadIdx.x; c < w; c += blockDim.x) reinterpret_cast<int*>(ws + s.off_piv)[c] = piv[c];
+  __syncthreads();
+  // rank decision
+  if (threadIdx.x == 0) {
+    const int limit = min(s.rpad, w);
+    int r = s.target_rank;
+    if (it.eps_mode) {
+      const double thr = it.eps / sqrt((double)max(it.d - 1, 1)) * sqrt(total2);
+      r = limit;
+      bool met = false;
+      for (int cand = 1; cand <= limit; ++cand) {
+        double tail = 0.0;
+        for (int c = cand; c < w; ++c)
+          for (int i2 = cand; i2 <= c; ++i2) tail += Rt[i2 + w * c] * Rt[i2 + w * c];
+        if (sqrt(tail) <= thr) {
+          r = cand;
+          met = true;
+          break;
+        }
+      }
+      if (!met) flag_status(wsb, ST_RANK_CAP);
+    }
+    r = max(1, min(r, limit));
+    s_rank = r;
+    int* rk = ranks + it.rank_off;
+    rk[s.k] = r;
+    if (s.k == 1) rk[0] = 1;
+    if (s.k == it.d - 1) rk[it.d] = 1;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  // leading r x r block of Rt for the backward pass (rpad x rpad, zero padded)
+  for (int o = threadIdx.x; o < s.rpad * s.rpad; o += blockDim.x) {
+    const int i = o % s.rpad, c = o / s.rpad;
+    ws[it.off_rr[s.k] + o] = (i < r && c < r) ? Rt[i + w * c] : 0.0;
+  }
+  // Z_root = Q_root [Q2(:, 1:r); 0]  (m x rpad, columns >= r are zero)
+  double* Z = ws + s.lev_z[L];
+  for (int o = threadIdx.x; o < nr * s.rpad; o += blockDim.x) {
+    const int rr = o % nr, c = o / nr;
+    Z[rr + m * c] = (c < r && rr < w) ? Q2[rr + w * c] : 0.0;
+  }
+  __syncthreads();
+  apply_q(A, lda, beta, nr, w, Z, m, r);
+}
+
+// ---------------------------------------------------------------- TSQR down
+// Z_L(block) = Q_block [Z_{L+1}(rows of this block's R); 0].
+__global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int L, const int* ranks) {
+  extern __shared__ double sm[];
+  const DevTables& T = tables(wsb);
+  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[L])[blockIdx.x];
+  const DevSketch s = dsk(wsb)[task.sk];
+  if (s.nlev - 1 <= L) return;  // root of this tree, already expanded
+  const DevItem& it = ditems(wsb)[s.item];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int w = s.width;
+  const int r = ranks[it.rank_off + s.k];
+  const int64_t m = s.lev_rows[L];
+  const int64_t r0 = (int64_t)task.blk * s.bl;
+  const int nr = (int)imin64(s.bl, m - r0);
+  const int lda = nr + 1;
+  double* V = sm;
+  double* beta = V + (size_t)lda * w;
+  const double* Y = ws + s.lev_mat[L];
+  for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
+    const int rr = o % nr, c = o / nr;
+    V[rr + lda * c] = Y[r0 + rr + m * c];
+  }
+  for (int i = threadIdx.x; i < w; i += blockDim.x) beta[i] = ws[s.lev_beta[L] + (int64_t)task.blk * w + i];
+  const int64_t m1 = s.lev_rows[L + 1];
+  const double* Zin = ws + s.lev_z[L + 1];
+  double* Z = ws + s.lev_z[L];
+  const int kmax = min(nr, w);
+  for (int o = threadIdx.x; o < nr * s.rpad; o += blockDim.x) {
+    const int rr = o % nr, c = o / nr;
+    Z[r0 + rr + m * c] = (c < r && rr < kmax) ? Zin[(int64_t)task.blk * w + rr + m1 * c] : 0.0;
+  }
+  __syncthreads();
+  apply_q(V, lda, beta, nr, w, Z + r0, m, r);
+}
+
+// --------------------------------------------------------- one-pass middle
+// B = P_{d*}^T Omega_{d*}  (r x l), summed over row chunks with atomics.
+__global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item, const int* ranks) {
+  constexpr int CH = 32;
+  __shared__ double Ps[CH * TT_MAXL];
+  __shared__ double Gs[CH * (TT_MAXL + 1)];
+  const DevItem& it = ditems(wsb)[item];
+  const DevSketch sp = dsk(wsb)[it.basis_of_k[it.ds]];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int r = ranks[it.rank_off + it.ds];
+  const int l = it.lmid;
+  const int64_t M = sp.rows;
+  const double* Pm = ws + sp.lev_z[0];
+  for (int64_t v0 = (int64_t)blockIdx.x * CH; v0 < M; v0 += (int64_t)gridDim.x * CH) {
+    const int nv = (int)imin64(CH, M - v0);
+    __syncthreads();
+    for (int o = threadIdx.x; o < CH * r; o += blockDim.x) {
+      const int v = o % CH, c = o / CH;
+      Ps[v + CH * c] = v < nv ? Pm[v0 + v + M * c] : 0.0;
+    }
+    const int nq = (l + 3) / 4;
+    for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
+      const int v = o % nv, q = o / nv;
+      double z[4];
+      normals4_f64(it.seed, (uint32_t)it.ds, (uint64_t)(v0 + v), (uint32_t)q, z);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = z[t];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < r * l; o += blockDim.x) {
+      const int c = o % r, j = o / r;
+      double acc = 0.0;
+      for (int v = 0; v < nv; ++v) acc += Ps[v + CH * c] * Gs[v + CH * j];
+      atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
+    }
+  }
+}
+
+// QR of B^T (l x r) -> QB (l x r), RB (r x r); singular B is flagged.
+__global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item, const int* ranks) {
+  __shared__ double A[TT_MAXL * (TT_MAXL + 1)];
+  __shared__ double beta[TT_MAXL], rdiag[TT_MAXL], red[32];
+  const DevItem& it = ditems(wsb)[item];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int r = ranks[it.rank_off + it.ds];
+  const int l = it.lmid;
+  const int rp = it.rpad[it.ds];
+  const int lda = l + 1;
+  for (int o = threadIdx.x; o < l * r; o += blockDim.x) {
+    const int j = o % l, c = o / l;
+    A[j + lda * c] = ws[it.off_B + c + (int64_t)rp * j];  // B^T(j, c) = B(c, j)
+  }
+  __syncthreads();
+  house_qr(A, lda, l, r, beta, rdiag, red);
+  // RB (rp x rp) with diag >= 0; QB = H_0..H_{r-1} [I_r; 0] with matching signs
+  double* RB = ws + it.off_RB;
+  double* QB = ws + it.off_QB;
+  __shared__ double sgn[TT_MAXL];
+  __shared__ double rmax_abs;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < r; ++i) mx = fmax(mx, fabs(rdiag[i]));
+    rmax_abs = mx;
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) sgn[i] = rdiag[i] < 0.0 ? -1.0 : 1.0;
+  __syncthreads();
+  for (int o = threadIdx.x; o < rp * rp; o += blockDim.x) {
+    const int i = o % rp, c = o / rp;
+    double v = 0.0;
+    if (i < r && c < r && c >= i) v = sgn[i] * (c == i ? rdiag[i] : A[i + lda * c]);
+    RB[o] = v;
+  }
+  if (threadIdx.x == 0) {
+    bool sing = !(rmax_abs > 0.0);
+    for (int i = 0; i < r; ++i)
+      if (!(fabs(rdiag[i]) > 1e-13 * rmax_abs)) sing = true;
+    if (sing) flag_status(wsb, ST_RANK_DEFICIENT);
+  }
+  for (int o = threadIdx.x; o < l * rp; o += blockDim.x) {
+    const int j = o % l, c = o / l;
+    QB[j + (int64_t)l * c] = (c < r && j == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  apply_q(A, lda, beta, l, r, QB, l, r);
+  for (int o = threadIdx.x; o < l * r; o += blockDim.x) {
+    const int c = o / l;
+    QB[o] *= sgn[c];
+  }
+}
+
+// H = S_{d*} QB RB^{-T}  (N_{d*} x rpad), one thread per row.
+__global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item, const int* ranks) {
+  __shared__ double QBs[TT_MAXL * TT_MAXL];
+  __shared__ double RBs[TT_MAXL * TT_MAXL];
+  const DevItem& it = ditems(wsb)[item];
+  const DevSketch sm_ = dsk(wsb)[it.mid_sk];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int r = ranks[it.rank_off + it.ds];
+  const int rp = it.rpad[it.ds];
+  const int l = it.lmid;
+  for (int o = threadIdx.x; o < l * r; o += blockDim.x) QBs[o] = ws[it.off_QB + o];
+  for (int o = threadIdx.x; o < rp * rp; o += blockDim.x) RBs[o] = ws[it.off_RB + o];
+  __syncthreads();
+  const int64_t Nm = sm_.rows;
+  const double* S = ws + sm_.off;
+  double* H = ws + it.off_H;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < Nm; u += (int64_t)gridDim.x * blockDim.x) {
+    double h[TT_MAXL];
+    double srow[TT_MAXL];
+    for (int j = 0; j < l; ++j) srow[j] = S[u + Nm * j];
+    for (int c = 0; c < r; ++c) {
+      double t = 0.0;
+      for (int j = 0; j < l; ++j) t += srow[j] * QBs[j + l * c];
+      h[c] = t;
+    }
+    // H RB^T = T with RB upper triangular: back substitution from the last column
+    for (int c = r - 1; c >= 0; --c) {
+      double t = h[c];
+      for (int c2 = c + 1; c2 < r; ++c2) t -= h[c2] * RBs[c + rp * c2];
+      const double dgn = RBs[c + rp * c];
+      h[c] = dgn != 0.0 ? t / dgn : 0.0;
+    }
+    for (int c = 0; c < rp; ++c) H[u + Nm * c] = c < r ? h[c] : 0.0;
+  }
+}
+
+// --------------------------------------------------------------- the cores
+// Left type  (k <= d*): G(a,i,c) = sum_u A(u,a) B(u + N_{k-1} i, c),  A = Q_{k-1}
+//            (identity 1x1 for k = 1), B = Q_k or H (middle core, one-pass).
+// Right type (k > d*):  G(a,i,c) = sum_v A(i + n_k v, a) B(v, c),   A = P_{k-1},
+//            B = P_k (identity 1x1 for k = d).
+__global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* cores, const int* ranks,
+                                                         int item0, int nitems, int only_k) {
+  const int pair = blockIdx.x;
+  const int item = item0 + pair / TT_MAXD;
+  const int k = pair % TT_MAXD + 1;
+  if (item >= item0 + nitems) return;
+  const DevItem& it = ditems(wsb)[item];
+  if (k > it.d) return;
+  if (only_k > 0 && k != only_k) return;
+  if (only_k == 0 && k == it.ds && it.passes == 2) return;  // second pass computes it
+  const DevSketch* S = dsk(wsb);
+  const double* ws = reinterpret_cast<const double*>(wsb);
+  const int* rk = ranks + it.rank_off;
+  const int ra = rk[k - 1], rc = rk[k];
+  const int rpa = it.rpad[k - 1], rpc = it.rpad[k];
+  const int64_t nk = it.n[k - 1];
+  const int64_t total = (int64_t)rpa * nk * rpc;
+  double* G = cores + it.core_off[k];
+  const bool left = k <= it.ds;
+  const double* A = nullptr;
+  const double* B = nullptr;
+  int64_t lda = 0, ldb = 0, inner = 0;
+  if (left) {
+    inner = it.N[k - 1];
+    if (k >= 2) {
+      const DevSketch& sa = S[it.basis_of_k[k - 1]];
+      A = ws + sa.lev_z[0];
+      lda = sa.rows;
+    }
+    if (k == it.ds) {
+      B = ws + it.off_H;
+      ldb = it.N[k];
+    } else {
+      const DevSketch& sb = S[it.basis_of_k[k]];
+      B = ws + sb.lev_z[0];
+      ldb = sb.rows;
+    }
+  } else {
+    inner = it.N[it.d] / it.N[k];
+    const DevSketch& sa = S[it.basis_of_k[k - 1]];
+    A = ws + sa.lev_z[0];
+    lda = sa.rows;
+    if (k < it.d) {
+      const DevSketch& sb = S[it.basis_of_k[k]];
+      B = ws + sb.lev_z[0];
+      ldb = sb.rows;
+    }
+  }
+  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.y * blockDim.x) {
+    const int a = (int)(e % rpa);
+    const int64_t i = (e / rpa) % nk;
+    const int c = (int)(e / (rpa * nk));
+    double acc = 0.0;
+    if (a < ra && c < rc) {
+      if (left) {
+        if (A == nullptr) {
+          acc = B[i + ldb * c];
+        } else {
+          for (int64_t u = 0; u < inner; ++u) acc += A[u + lda * a] * B[u + inner * i + ldb * c];
+        }
+      } else {
+        if (B == nullptr) {
+          acc = A[i + lda * a];
+        } else {
+          for (int64_t v = 0; v < inner; ++v) acc += A[i + nk * v + lda * a] * B[v + ldb * c];
+        }
+      }
+    }
+    G[e] = acc;
+  }
+}
+
+// Two-pass middle core, eq. (3.5): G_{d*}(a, i, c) =
+//   sum_{u, v} Q_{d*-1}(u, a) X(u + N_{d*-1} i + N_{d*} v) P_{d*}(v, c).
+// One block per (i, chunk of v): y(v, a) = sum_u Q(u, a) X(...), then the
+// block adds sum_v y(v, a) P(v, c) into the (zeroed) core with atomics.
+__global__ void __launch_bounds__(kThreads) twopass_mid_kernel(char* wsb, const void* X, double* cores,
+                                                               const int* ranks) {
+  constexpr int CH = 64;
+  __shared__ double Ys[CH * TT_MAXL];
+  const DevItem& it = ditems(wsb)[0];
+  const DevSketch* S = dsk(wsb);
+  const double* ws = reinterpret_cast<const double*>(wsb);
+  const int ds = it.ds;
+  const int* rk = ranks + it.rank_off;
+  const int ra = rk[ds - 1], rc = rk[ds];
+  const int rpa = it.rpad[ds - 1];
+  const int64_t Np = it.N[ds - 1], nk = it.n[ds - 1], Nm = it.N[ds];
+  const int64_t Mm = it.N[it.d] / Nm;
+  const double* Q = nullptr;
+  int64_t ldq = 1;
+  if (ds >= 2) {
+    Q = ws + S[it.basis_of_k[ds - 1]].lev_z[0];
+    ldq = S[it.basis_of_k[ds - 1]].rows;
+  }
+  const DevSketch& sp = S[it.basis_of_k[ds]];
+  const double* Pm = ws + sp.lev_z[0];
+  double* G = cores + it.core_off[ds];
+  const int64_t nchunks = (Mm + CH - 1) / CH;
+  for (int64_t job = blockIdx.x; job < nk * nchunks; job += gridDim.x) {
+    const int64_t i = job % nk, v0 = (job / nk) * CH;
+    const int nv = (int)imin64(CH, Mm - v0);
+    __syncthreads();
+    for (int o = threadIdx.x; o < CH * ra; o += blockDim.x) {
+      const int v = o % CH, a = o / CH;
+      double acc = 0.0;
+      if (v < nv) {
+        const int64_t base = Np * i + Nm * (v0 + v);
+        for (int64_t u = 0; u < Np; ++u) {
+          const double x = it.x_f64 ? ((const double*)X)[base + u] : (double)((const float*)X)[base + u];
+          acc += (Q ? Q[u + ldq * a] : 1.0) * x;
+        }
+      }
+      Ys[v + CH * a] = acc;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < ra * rc; o += blockDim.x) {
+      const int a = o % ra, c = o / ra;
+      double acc = 0.0;
+      for (int v = 0; v < nv; ++v) acc += Ys[v + CH * a] * Pm[v0 + v + sp.rows * c];
+      atomicAdd(G + a + rpa * (i + nk * c), acc);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mid_b_mixed(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st);
+
+cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st) {
+  char* wsb = (char*)ws;
+  const int max_lev = plan_max_lev(&P);
+  const DevSketch* sks = plan_sketches_host(&P);
+  const int nitems = plan_num_items(&P);
+  cudaError_t e;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(tsqr_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tsqr_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  // smem: block (bl+1) x w + scalars + two w x w matrices (root)
+  int maxw = 1, maxbl = 1;
+  for (int i = 0, n = 0; i < nitems; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    for (int s = 0; s < it.nsk; ++s) {
+      const DevSketch& d = sks[it.sk0 + s];
+      if (!d.basis) continue;
+      maxw = std::max(maxw, d.width);
+      maxbl = std::max(maxbl, d.bl);
+      ++n;
+    }
+  }
+  size_t smem_up = 0;
+  for (int i = 0; i < nitems; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    for (int s = 0; s < it.nsk; ++s) {
+      const DevSketch& d = sks[it.sk0 + s];
+      if (!d.basis) continue;
+      const size_t need = sizeof(double) * ((size_t)(d.bl + 1) * d.width + 32 + 2 * TT_MAXL +
+                                            2 * TT_MAXL * TT_MAXL);
+      smem_up = std::max(smem_up, need);
+    }
+  }
+  e = cudaMemsetAsync(wsb + kStatusOff, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  for (int L = 0; L < max_lev; ++L) {
+    const int nt = plan_ntasks(&P, L);
+    if (nt == 0) continue;
+    count_launch();
+    tsqr_level_kernel<<<nt, kThreads, smem_up, st>>>(wsb, L, ranks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  for (int L = max_lev - 2; L >= 0; --L) {
+    const int nt = plan_ntasks(&P, L);
+    if (nt == 0) continue;
+    const size_t smem = sizeof(double) * ((size_t)(maxbl + 1) * maxw + TT_MAXL);
+    count_launch();
+    tsqr_expand_kernel<<<nt, kThreads, smem, st>>>(wsb, L, ranks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // one-pass middle cores
+  for (int i = 0; i < nitems; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    if (it.passes != 1) continue;
+    const int rp = it.rpad[it.ds];
+    e = cudaMemsetAsync((double*)ws + it.off_B, 0, sizeof(double) * rp * it.lmid, st);
+    if (e != cudaSuccess) return e;
+    if (it.prec == TT_PREC_FP64) {
+      const int64_t M = sks[it.basis_of_k[it.ds]].rows;
+      const int grid = (int)std::min<int64_t>((M + 31) / 32, 4LL * device_sm_count());
+      count_launch();
+      mid_b_kernel_f64<<<grid, kThreads, 0, st>>>(wsb, i, ranks);
+      e = cudaGetLastError();
+    } else {
+      e = launch_mid_b_mixed(P, i, ws, ranks, st);
+    }
+    if (e != cudaSuccess) return e;
+    count_launch();
+    mid_ls_kernel<<<1, kThreads, 0, st>>>(wsb, i, ranks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t Nm = it.N[it.ds];
+    const int grid = (int)std::min<int64_t>((Nm + 127) / 128, 8LL * device_sm_count());
+    count_launch();
+    mid_h_kernel<<<grid, 128, 0, st>>>(wsb, i, ranks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)(nitems * TT_MAXD), 16);
+  count_launch();
+  cores_kernel<<<grid, kThreads, 0, st>>>(wsb, cores, ranks, 0, nitems, 0);
+  return cudaGetLastError();
+}
+
+// Cores of one item only (k = only_k), used by the two-pass middle core.
+cudaError_t launch_cores_one(const Plan& P, int item, int only_k, void* ws, double* cores,
+                             const int* ranks, cudaStream_t st) {
+  dim3 grid((unsigned)TT_MAXD, 16);
+  count_launch();
+  cores_kernel<<<grid, kThreads, 0, st>>>((char*)ws, cores, ranks, item, 1, only_k);
+  return cudaGetLastError();
+}
+
+}  // namespace tts
+
+namespace tts {
+cudaError_t launch_twopass_mid(const Plan& P, const void* X, void* ws, double* cores, const int* ranks,
+                               cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[0];
+  const int ds = it.ds;
+  cudaError_t e = cudaMemsetAsync(cores + it.core_off[ds], 0,
+                                  sizeof(double) * it.rpad[ds - 1] * it.n[ds - 1] * it.rpad[ds], st);
+  if (e != cudaSuccess) return e;
+  const int64_t Mm = it.N[it.d] / it.N[ds];
+  const int64_t jobs = it.n[ds - 1] * ((Mm + 63) / 64);
+  const int grid = (int)std::min<int64_t>(jobs, 8LL * device_sm_count());
+  count_launch();
+  twopass_mid_kernel<<<grid, kThreads, 0, st>>>((char*)ws, X, cores, ranks);
+  return cudaGetLastError();
+}
+}  // namespace tts

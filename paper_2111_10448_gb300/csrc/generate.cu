@@ -1,0 +1,132 @@
+// Synthetic inputs and raw access to the Gaussian stream (test and benchmark
+// helpers of the C ABI).
+#include <algorithm>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace tts {
+namespace {
+
+struct Dims {
+  int d;
+  int64_t n[TT_MAXD];
+};
+
+// Hilbert-type tensor 1 / (x_{i_1} + ... + x_{i_d}), x_i = 1 + i/(n-1)
+// (the large streaming workload); slab [first, first + count) of the last mode.
+__global__ void hilbert_type_kernel(Dims D, int64_t first, int64_t count, void* out, int f64) {
+  int64_t inner = 1;
+  for (int k = 0; k < D.d - 1; ++k) inner *= D.n[k];
+  const int64_t total = inner * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e;
+    double s = 0.0;
+    for (int k = 0; k < D.d; ++k) {
+      int64_t i;
+      if (k < D.d - 1) {
+        i = rem % D.n[k];
+        rem /= D.n[k];
+      } else {
+        i = rem + first;
+      }
+      const double x = 1.0 + (double)i / (double)(D.n[k] > 1 ? D.n[k] - 1 : 1);
+      s = (k == 0) ? x : s + x;
+    }
+    const double v = 1.0 / s;
+    if (f64) ((double*)out)[e] = v;
+    else ((float*)out)[e] = (float)v;
+  }
+}
+
+__global__ void test_matrix_f64_kernel(uint64_t seed, int sid, int64_t row0, int64_t nrows, int ncols,
+                                       double* out) {
+  const int nq = (ncols + 3) / 4;
+  const int64_t total = nrows * nq;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % nrows;
+    const int q = (int)(e / nrows);
+    double z[4];
+    normals4_f64(seed, (uint32_t)sid, (uint64_t)(row0 + r), (uint32_t)q, z);
+    for (int t = 0; t < 4; ++t)
+      if (4 * q + t < ncols) out[r + nrows * (4 * q + t)] = z[t];
+  }
+}
+
+__global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                              int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c0 = ctr[4 * e], c1 = ctr[4 * e + 1], c2 = ctr[4 * e + 2], c3 = ctr[4 * e + 3];
+    philox4x32_10(c0, c1, c2, c3, k0, k1);
+    out[4 * e] = c0;
+    out[4 * e + 1] = c1;
+    out[4 * e + 2] = c2;
+    out[4 * e + 3] = c3;
+  }
+}
+
+int grid_for(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * device_sm_count()));
+}
+
+}  // namespace
+
+cudaError_t launch_test_matrix_mixed(uint64_t seed, int sid, int64_t row0, int64_t nrows, int ncols,
+                                     int prec, double* out, cudaStream_t st);
+
+}  // namespace tts
+
+using namespace tts;
+
+extern "C" {
+
+tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last, int64_t count_last,
+                                   void* out, tt_dtype dtype, tt_stream_t stream) {
+  if (d < 1 || d > TT_MAXD || !n || !out || first_last < 0 || count_last < 0) return TT_ERR_INVALID_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  Dims D;
+  D.d = d;
+  int64_t inner = 1;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1) return TT_ERR_INVALID_ARG;
+    D.n[k] = n[k];
+    if (k < d - 1) inner *= n[k];
+  }
+  if (first_last + count_last > n[d - 1]) return TT_ERR_INVALID_ARG;
+  if (count_last == 0) return TT_OK;
+  count_launch();
+  hilbert_type_kernel<<<grid_for(inner * count_last), 256, 0, (cudaStream_t)stream>>>(
+      D, first_last, count_last, out, dtype == TT_F64);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nrows, int ncols,
+                         tt_prec prec, double* out, tt_stream_t stream) {
+  if (!out || nrows < 0 || row0 < 0 || ncols < 0 || ncols > TT_MAXL) return TT_ERR_INVALID_ARG;
+  if (nrows == 0 || ncols == 0) return TT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == TT_PREC_FP64) {
+    count_launch();
+    test_matrix_f64_kernel<<<grid_for(nrows * ((ncols + 3) / 4)), 256, 0, st>>>(seed, stream_id, row0, nrows,
+                                                                                ncols, out);
+    return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
+  if (prec != TT_PREC_TF32 && prec != TT_PREC_BF16) return TT_ERR_INVALID_ARG;
+  return launch_test_matrix_mixed(seed, stream_id, row0, nrows, ncols, prec, out, st) == cudaSuccess
+             ? TT_OK
+             : TT_ERR_CUDA;
+}
+
+tt_status tt_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
+                           int64_t count, tt_stream_t stream) {
+  if (!ctr || !out || count < 0) return TT_ERR_INVALID_ARG;
+  if (count == 0) return TT_OK;
+  count_launch();
+  philox_kernel<<<grid_for(count), 256, 0, (cudaStream_t)stream>>>(ctr, key0, key1, out, count);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the translation units of libttsketch.
+//
+// Notation follows the paper (Sec. 2.1, 3.2): X is column-major, N_k =
+// n_1..n_k, M_k = n_{k+1}..n_d, d* = ceil(d/2).  Column sketches S_k = X_k
+// Omega_k (k < d*, and k = d* in one-pass mode) and row sketches
+// R_k = X_k^T Psi_k (k = d*..d-1).
+//
+// The sketch kernels see X as a stack of "planes" X(:, w, :) of size
+// n_1 x n_d, w = (i_2..i_{d-1}) in [0, W), W = N_{d-1}/n_1.  For every
+// sketch, the contribution of one plane is a plain product:
+//   column sketch k: S_k[a + n_1 wlo, j] += sum_b X(a, w, b) Omega_k[whi + hs b, j]
+//   row sketch k:    R_k[whi + hs b, j]  += sum_a X(a, w, b) Psi_k[a + n_1 wlo, j]
+// with wlo = w mod (N_k/n_1), whi = w div (N_k/n_1), hs = N_{d-1}/N_k and b the
+// global index of the last mode.  (For k = 1 the column sketch has wlo = 0;
+// for k = d-1 the row sketch has whi = 0: these two collect every plane.)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/ttsketch.h"
+
+namespace tts {
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr int kMaxLev = 8;        // TSQR tree depth limit
+constexpr int kMaxSk = TT_MAXD;   // sketches per item (d of them at most)
+
+enum SkType : int { SK_COL = 0, SK_ROW = 1 };
+
+// Status bits written on the device (workspace word 0).
+enum : int { ST_RANK_CAP = 1, ST_RANK_DEFICIENT = 2, ST_TIMEOUT = 4 };
+
+struct DevSketch {
+  int64_t rows;        // N_k (column) or M_k (row)
+  int64_t off;         // FP64 sketch, column-major rows x width, element offset in ws
+  int64_t wdiv;        // N_k / n_1
+  int64_t hstride;     // N_{d-1} / N_k
+  int type;            // SK_COL / SK_ROW
+  int k;               // unfolding index, 1-based
+  int width;           // l of this sketch
+  int stream_id;       // Philox stream (k or 64 + k)
+  int basis;           // 1: QR'd into an orthonormal basis; 0: one-pass middle sketch
+  int item;            // owning item
+  // ---- basis sketches: TSQR tree (level 0 is the sketch itself)
+  int nlev;            // number of levels; level nlev-1 is the root (one block)
+  int bl;              // rows per block at every level
+  int rpad;            // padded rank (columns of the basis)
+  int rank_slot;       // index into the rank array of this sketch's rank r_k
+  int target_rank;     // fixed-rank mode target (already clamped)
+  int rcap;            // min(N_k, M_k)
+  int64_t lev_rows[kMaxLev];
+  int64_t lev_nblk[kMaxLev];
+  int64_t lev_mat[kMaxLev];   // level matrix (rows x width) offset; lev_mat[0] = off
+  int64_t lev_beta[kMaxLev];  // nblk * width Householder scalars
+  int64_t lev_z[kMaxLev];     // rows x rpad expansion buffer; lev_z[0] = the basis Q_k / P_k
+  int64_t off_rt;      // CPQR R factor of the root R (width x width)
+  int64_t off_q2;      // CPQR Q factor (width x width)
+  int64_t off_piv;     // pivots (width ints, stored as int in a double slot area)
+};
+
+struct DevItem {
+  int d, ds, passes, prec, x_f64, nsk, eps_mode;
+  int sk0;                 // first sketch index in the sketch table
+  int mid_sk;              // index of the one-pass middle sketch (-1 in two-pass)
+  int basis_of_k[TT_MAXD + 1];  // sketch index of the basis of unfolding k (1..d-1)
+  int64_t n[TT_MAXD];
+  int64_t N[TT_MAXD + 1];
+  int64_t W;               // planes: N_{d-1} / n_1
+  double eps;
+  int rmax, p;
+  uint64_t seed;
+  int rpad[TT_MAXD + 1];
+  int64_t core_off[TT_MAXD + 1];
+  int64_t rank_off;        // first entry of this item's d+1 ranks in the rank array
+  // one-pass middle core
+  int64_t off_B, off_QB, off_RB, off_H;
+  int lmid;
+  // reconstruction interfaces
+  int64_t off_L[TT_MAXD + 1];   // L_k, N_k x rpad_k (k = 1..ds)
+  int64_t off_Rt[TT_MAXD + 2];  // Rt_k, rpad_{k-1} x M_{k-1} (k = ds+1..d)
+  // backward
+  int64_t off_bar;          // start of the backward scratch of this item
+  int64_t off_sbar[TT_MAXD + 1];  // adjoint of each sketch (same layout as the sketch)
+  int64_t off_qbar[TT_MAXD + 1];  // adjoint of each basis Q_k / P_k
+  int64_t off_hbar;         // adjoint of H
+  int64_t off_bbar;         // adjoint of B
+  int64_t off_rr[TT_MAXD + 1];    // leading r x r block of the basis R factor (rpad x rpad)
+  const void* X;            // batched: device pointer of this item's tensor (set per call)
+};
+
+struct Task {               // one block of one TSQR level (finalize)
+  int sk;                   // sketch index
+  int blk;                  // block index
+};
+
+// Device-resident tables, stored at the start of the workspace.
+struct DevTables {
+  int nitems, nsk;
+  int64_t off_items, off_sketches;   // byte offsets from ws base
+  int64_t off_tasks[kMaxLev];        // byte offsets of per-level task arrays
+  int ntasks[kMaxLev];
+};
+
+// Byte offset of the status word inside the workspace.
+constexpr int64_t kStatusOff = 0;
+
+// ---------------------------------------------------------------- host side
+struct Plan;
+const DevItem* plan_items_host(const Plan* p);
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t first, int64_t count,
+                              void* ws, cudaStream_t st);
+cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t first,
+                                int64_t count, void* ws, cudaStream_t st);
+bool mixed_tc_supported(const Plan& P, int item, int64_t count);
+cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st);
+cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, void* Xt, int x_f64,
+                               const void* Xcmp, int cmp_f64, double* out2, void* ws,
+                               cudaStream_t st);
+cudaError_t launch_reconstruct_backward(const Plan& P, int item, const double* cores,
+                                        const void* dXt, int dx_f64, double* dcores, void* ws,
+                                        cudaStream_t st);
+cudaError_t launch_backward(const Plan& P, int item, const double* dcores, void* dX, void* ws,
+                            cudaStream_t st);
+cudaError_t launch_sketch_batched(const Plan& P, void* ws, cudaStream_t st);
+
+int device_sm_count();
+void count_launch(int n = 1);
+
+}  // namespace tts

@@ -1,0 +1,84 @@
+// Device side of the library's Gaussian stream.
+//
+// The paper draws the test matrices of Algorithm 2 (and of the one-pass
+// variant, eq. (3.3)) with i.i.d. standard Gaussian entries; this library
+// regenerates them on the fly from a counter-based generator instead of
+// storing them.  Definition (independent of, and identical in meaning to, the
+// host-side definition used by the tests):
+//   Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of
+//     (hi0, lo0) = c0 * 0xD2511F53, (hi1, lo1) = c2 * 0xCD9E8D57,
+//     c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),
+//   key bumped by (0x9E3779B9, 0xBB67AE85) after each round.
+//   key = (seed lo, seed hi); entry (row, j) of stream s uses the counter
+//   (row lo, row hi, j / 4, s) and Box-Muller on the four output words:
+//   rho = sqrt(-2 ln u(x0)), theta = 2 pi u(x1) -> (rho cos, rho sin) for
+//   j % 4 = 0, 1 and likewise (x2, x3) for j % 4 = 2, 3.
+//   FP64 uniforms: u = (x + 1/2) 2^-32.
+//   FP32 uniforms (mixed precision): u = (2 (x >> 9) + 1) 2^-24, exact in FP32.
+#pragma once
+#include <cstdint>
+
+namespace tts {
+
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                              uint32_t& c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// Four consecutive FP64 normals z[4q..4q+3] of row `row` of stream `sid`.
+__device__ __forceinline__ void normals4_f64(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q,
+                                             double z[4]) {
+  uint32_t c0 = (uint32_t)row, c1 = (uint32_t)(row >> 32), c2 = q, c3 = sid;
+  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u0 = ((double)c0 + 0.5) * 0x1p-32;
+  const double u1 = ((double)c1 + 0.5) * 0x1p-32;
+  const double u2 = ((double)c2 + 0.5) * 0x1p-32;
+  const double u3 = ((double)c3 + 0.5) * 0x1p-32;
+  const double ra = sqrt(-2.0 * log(u0));
+  const double rb = sqrt(-2.0 * log(u2));
+  double sa, ca, sb, cb;
+  sincospi(2.0 * u1, &sa, &ca);
+  sincospi(2.0 * u3, &sb, &cb);
+  z[0] = ra * ca;
+  z[1] = ra * sa;
+  z[2] = rb * cb;
+  z[3] = rb * sb;
+}
+
+// FP32 generator of the mixed-precision sketches.  Kept out of line so that
+// every kernel that needs the same entry (the sketch, and the middle-core
+// solve that regenerates Omega_{d*}) runs one compiled body and gets
+// bit-identical values.
+__device__ __noinline__ void normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q,
+                                          float z[4]);
+
+// Round an FP32 value to the MMA input type, nearest-even, returned as FP32.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  const uint32_t lsb = (u >> 13) & 1u;
+  u = (u + 0xFFFu + lsb) & ~0x1FFFu;
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ float round_bf16(float x) {
+  uint32_t u = __float_as_uint(x);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7FFFu + lsb) & ~0xFFFFu;
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ float round_prec(float x, int prec) {
+  return prec == TT_PREC_TF32 ? round_tf32(x) : round_bf16(x);
+}
+
+}  // namespace tts

@@ -1,0 +1,591 @@
+// Host plan, workspace layout and the C ABI entry points of libttsketch.
+//
+// The plan follows the paper's PSTT2 (Sec. 3.2): split d* = ceil(d/2);
+// column bases Q_k of X_k for k < d*, row bases P_k of X_k for k = d*..d-1
+// (reading A1 of the design notes); in one-pass mode one extra column sketch
+// S_{d*} = X_{d*} Omega_{d*} whose pseudo-inverse solve gives the middle core
+// (eq. (3.3) applied to the middle unfolding; readings A2, A3).  Sketch
+// widths are l_k = r_k + p (fixed ranks) or rmax + p (tolerance mode).
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace tts {
+
+struct Plan {
+  std::vector<tt_problem> probs;
+  std::vector<DevItem> items;
+  std::vector<DevSketch> sketches;
+  std::vector<Task> tasks[kMaxLev];
+  int max_lev = 0;
+  int64_t ws_doubles = 0;      // total workspace in doubles
+  int64_t core_entries = 0;
+  int rank_entries = 0;
+  std::vector<unsigned char> blob;  // device tables (uploaded to ws + kTableOff)
+  const void* uploaded_ws = nullptr;
+  // streaming bookkeeping (single-item plans)
+  std::vector<char> slab_seen;
+  bool begun = false;
+  bool forward_done = false;
+};
+
+static constexpr int64_t kTableOff = 256;  // bytes
+
+const DevItem* plan_items_host(const Plan* p) { return p->items.data(); }
+const DevSketch* plan_sketches_host(const Plan* p) { return p->sketches.data(); }
+int plan_num_items(const Plan* p) { return (int)p->items.size(); }
+int plan_max_lev(const Plan* p) { return p->max_lev; }
+int plan_ntasks(const Plan* p, int lev) { return lev < kMaxLev ? (int)p->tasks[lev].size() : 0; }
+cudaError_t launch_twopass_mid(const Plan& P, const void* X, void* ws, double* cores, const int* ranks,
+                               cudaStream_t st);
+
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Allocate `count` doubles in the workspace (256-byte aligned).
+struct WsAlloc {
+  int64_t top;  // in doubles
+  int64_t take(int64_t count) {
+    top = align_up(top, 32);
+    const int64_t o = top;
+    top += std::max<int64_t>(count, 1);
+    return o;
+  }
+};
+
+static tt_status validate(const tt_problem& q) {
+  if (q.d < 2 || q.d > TT_MAXD) return TT_ERR_INVALID_ARG;
+  for (int k = 0; k < q.d; ++k)
+    if (q.n[k] < 1) return TT_ERR_INVALID_ARG;
+  if (q.p < 1) return TT_ERR_INVALID_ARG;
+  if (q.passes != 1 && q.passes != 2) return TT_ERR_INVALID_ARG;
+  if (!(q.eps >= 0.0)) return TT_ERR_INVALID_ARG;
+  if (q.x_dtype != TT_F32 && q.x_dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  if (q.prec != TT_PREC_FP64 && q.prec != TT_PREC_TF32 && q.prec != TT_PREC_BF16)
+    return TT_ERR_INVALID_ARG;
+  if (q.prec != TT_PREC_FP64 && q.x_dtype != TT_F32) return TT_ERR_UNSUPPORTED;
+  if (q.eps > 0.0) {
+    if (q.rmax < 1 || q.rmax + q.p > TT_MAXL) return TT_ERR_INVALID_ARG;
+  } else {
+    if (q.ranks[0] != 1 || q.ranks[q.d] != 1) return TT_ERR_INVALID_ARG;
+    for (int k = 1; k < q.d; ++k)
+      if (q.ranks[k] < 1) return TT_ERR_INVALID_ARG;
+  }
+  // total size must fit int64 comfortably
+  double tot = 1.0;
+  for (int k = 0; k < q.d; ++k) tot *= (double)q.n[k];
+  if (tot > 9.0e15) return TT_ERR_INVALID_ARG;
+  return TT_OK;
+}
+
+// Build the item (tables + workspace layout) of one problem.
+static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t& core_top,
+                            int& rank_top) {
+  tt_problem q = q0;
+  DevItem it;
+  std::memset(&it, 0, sizeof(it));
+  const int d = q.d;
+  it.d = d;
+  it.ds = (d + 1) / 2;
+  it.passes = q.passes;
+  it.prec = q.prec;
+  it.x_f64 = q.x_dtype == TT_F64;
+  it.eps_mode = q.eps > 0.0;
+  it.eps = q.eps;
+  it.rmax = q.rmax;
+  it.p = q.p;
+  it.seed = q.seed;
+  it.N[0] = 1;
+  for (int k = 0; k < d; ++k) {
+    it.n[k] = q.n[k];
+    it.N[k + 1] = it.N[k] * q.n[k];
+  }
+  it.W = it.N[d - 1] / it.n[0];
+  const int ds = it.ds;
+  // ranks, padded ranks and widths
+  int width[TT_MAXD + 1] = {0};
+  it.rpad[0] = it.rpad[d] = 1;
+  for (int k = 1; k < d; ++k) {
+    const int64_t rcap = std::min(it.N[k], it.N[d] / it.N[k]);
+    if (it.eps_mode) {
+      it.rpad[k] = (int)std::min<int64_t>(q.rmax, rcap);
+      width[k] = q.rmax + q.p;
+    } else {
+      const int r = (int)std::min<int64_t>(q.ranks[k], rcap);
+      q.ranks[k] = r;
+      it.rpad[k] = r;
+      width[k] = r + q.p;
+    }
+    if (width[k] > TT_MAXL) return TT_ERR_INVALID_ARG;
+  }
+  it.lmid = width[ds];
+  P.probs.push_back(q);
+
+  // sketches
+  it.sk0 = (int)P.sketches.size();
+  it.mid_sk = -1;
+  auto add = [&](int type, int k, int basis) {
+    DevSketch s;
+    std::memset(&s, 0, sizeof(s));
+    s.type = type;
+    s.k = k;
+    s.basis = basis;
+    s.item = (int)P.items.size();
+    s.width = width[k];
+    s.rows = type == SK_COL ? it.N[k] : it.N[d] / it.N[k];
+    s.wdiv = it.N[k] / it.n[0];
+    s.hstride = it.N[d - 1] / it.N[k];
+    s.stream_id = type == SK_COL ? k : 64 + k;
+    s.off = ws.take(s.rows * s.width);
+    s.rpad = basis ? it.rpad[k] : 0;
+    s.target_rank = it.eps_mode ? it.rpad[k] : q.ranks[k];
+    s.rcap = (int)std::min(it.N[k], it.N[d] / it.N[k]);
+    s.rank_slot = k;
+    P.sketches.push_back(s);
+    return (int)P.sketches.size() - 1;
+  };
+  for (int k = 1; k < ds; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
+  if (q.passes == 1) it.mid_sk = add(SK_COL, ds, 0);
+  for (int k = ds; k < d; ++k) it.basis_of_k[k] = add(SK_ROW, k, 1);
+  it.nsk = (int)P.sketches.size() - it.sk0;
+
+  // TSQR trees of the basis sketches
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+    DevSketch& s = P.sketches[si];
+    if (!s.basis) continue;
+    const int w = s.width;
+    int bl = (int)((98304 / (8 * w)) / 32 * 32);
+    bl = std::max(bl, 2 * w);
+    s.bl = bl;
+    int64_t m = s.rows;
+    int L = 0;
+    while (true) {
+      if (L >= kMaxLev) return TT_ERR_UNSUPPORTED;
+      s.lev_rows[L] = m;
+      s.lev_nblk[L] = (m + bl - 1) / bl;
+      s.lev_mat[L] = (L == 0) ? s.off : ws.take(m * w);
+      s.lev_beta[L] = ws.take(s.lev_nblk[L] * w);
+      s.lev_z[L] = ws.take(m * s.rpad);
+      if (s.lev_nblk[L] == 1) break;
+      m = s.lev_nblk[L] * w;
+      ++L;
+    }
+    s.nlev = L + 1;
+    s.off_rt = ws.take((int64_t)w * w);
+    s.off_q2 = ws.take((int64_t)w * w);
+    s.off_piv = ws.take(w);
+    P.max_lev = std::max(P.max_lev, s.nlev);
+  }
+  // cores and ranks
+  for (int k = 1; k <= d; ++k) {
+    it.core_off[k] = core_top;
+    core_top += (int64_t)it.rpad[k - 1] * it.n[k - 1] * it.rpad[k];
+  }
+  it.rank_off = rank_top;
+  rank_top += d + 1;
+  // one-pass middle core
+  if (q.passes == 1) {
+    const int r = it.rpad[ds];
+    it.off_B = ws.take((int64_t)r * it.lmid);
+    it.off_QB = ws.take((int64_t)it.lmid * r);
+    it.off_RB = ws.take((int64_t)r * r);
+    it.off_H = ws.take(it.N[ds] * r);
+  }
+  // reconstruction interfaces
+  for (int k = 1; k <= ds; ++k) it.off_L[k] = ws.take(it.N[k] * it.rpad[k]);
+  for (int k = ds + 1; k <= d; ++k) it.off_Rt[k] = ws.take((int64_t)it.rpad[k - 1] * (it.N[d] / it.N[k - 1]));
+  // backward scratch
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+    const DevSketch& s = P.sketches[si];
+    it.off_sbar[si - it.sk0] = ws.take(s.rows * s.width);
+  }
+  for (int k = 1; k < d; ++k) {
+    const DevSketch& s = P.sketches[it.basis_of_k[k]];
+    it.off_qbar[k] = ws.take(s.rows * s.rpad);
+    it.off_rr[k] = ws.take((int64_t)s.rpad * s.rpad);
+  }
+  if (q.passes == 1) {
+    it.off_hbar = ws.take(it.N[ds] * it.rpad[ds]);
+    it.off_bbar = ws.take((int64_t)it.rpad[ds] * it.lmid);
+  }
+  P.items.push_back(it);
+  return TT_OK;
+}
+
+static void build_blob(Plan& P) {
+  for (int L = 0; L < kMaxLev; ++L) P.tasks[L].clear();
+  for (int si = 0; si < (int)P.sketches.size(); ++si) {
+    const DevSketch& s = P.sketches[si];
+    if (!s.basis) continue;
+    for (int L = 0; L < s.nlev; ++L)
+      for (int64_t b = 0; b < s.lev_nblk[L]; ++b) P.tasks[L].push_back(Task{si, (int)b});
+  }
+  DevTables t;
+  std::memset(&t, 0, sizeof(t));
+  t.nitems = (int)P.items.size();
+  t.nsk = (int)P.sketches.size();
+  int64_t off = kTableOff + (int64_t)align_up(sizeof(DevTables), 64);
+  t.off_items = off;
+  off += align_up((int64_t)(sizeof(DevItem) * P.items.size()), 64);
+  t.off_sketches = off;
+  off += align_up((int64_t)(sizeof(DevSketch) * P.sketches.size()), 64);
+  for (int L = 0; L < kMaxLev; ++L) {
+    t.off_tasks[L] = off;
+    t.ntasks[L] = (int)P.tasks[L].size();
+    off += align_up((int64_t)(sizeof(Task) * P.tasks[L].size()), 64);
+  }
+  P.blob.assign((size_t)(off - kTableOff), 0);
+  auto put = [&](int64_t at, const void* src, size_t n) {
+    if (n) std::memcpy(P.blob.data() + (at - kTableOff), src, n);
+  };
+  put(kTableOff, &t, sizeof(t));
+  put(t.off_items, P.items.data(), sizeof(DevItem) * P.items.size());
+  put(t.off_sketches, P.sketches.data(), sizeof(DevSketch) * P.sketches.size());
+  for (int L = 0; L < kMaxLev; ++L) put(t.off_tasks[L], P.tasks[L].data(), sizeof(Task) * P.tasks[L].size());
+}
+
+static tt_status build_all(Plan& P, const tt_problem* probs, int count, int64_t base_doubles) {
+  WsAlloc ws{base_doubles};
+  int64_t core_top = 0;
+  int rank_top = 0;
+  for (int i = 0; i < count; ++i) {
+    tt_status st = validate(probs[i]);
+    if (st == TT_OK) st = build_item(P, probs[i], ws, core_top, rank_top);
+    if (st != TT_OK) return st;
+  }
+  build_blob(P);
+  P.ws_doubles = align_up(ws.top, 32);
+  P.core_entries = core_top;
+  P.rank_entries = rank_top;
+  return TT_OK;
+}
+
+static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
+  if (!out) return TT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!probs || count < 1) return TT_ERR_INVALID_ARG;
+  // Pass 1 sizes the device tables (they depend on the TSQR trees); pass 2
+  // lays the data out after them.
+  int64_t table_end = 0;
+  {
+    Plan tmp;
+    tt_status st = build_all(tmp, probs, count, 0);
+    if (st != TT_OK) return st;
+    table_end = kTableOff + (int64_t)tmp.blob.size();
+  }
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) return TT_ERR_INVALID_ARG;
+  tt_status st = build_all(*P, probs, count, align_up(table_end, 256) / 8);
+  if (st != TT_OK || kTableOff + (int64_t)P->blob.size() > table_end) {
+    delete P;
+    return st != TT_OK ? st : TT_ERR_INVALID_ARG;
+  }
+  if (count == 1) P->slab_seen.assign((size_t)P->items[0].n[P->items[0].d - 1], 0);
+  *out = reinterpret_cast<tt_plan_t>(P);
+  return TT_OK;
+}
+
+static Plan* as_plan(tt_plan_t p) { return reinterpret_cast<Plan*>(p); }
+
+static tt_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TT_OK;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return TT_ERR_NO_DEVICE;
+  return TT_ERR_CUDA;
+}
+
+static tt_status ensure_uploaded(Plan& P, void* ws, cudaStream_t st) {
+  if (P.uploaded_ws == ws) return TT_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return TT_ERR_STATE;  // first use of a workspace must happen outside capture
+  cudaError_t e = cudaMemcpyAsync((char*)ws + kTableOff, P.blob.data(), P.blob.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(st);  // the host blob must stay unchanged until copied
+  if (e != cudaSuccess) return cuda_status(e);
+  P.uploaded_ws = ws;
+  return TT_OK;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int device_sm_count() {
+  static int cached = -1;
+  if (cached > 0) return cached;
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  cached = n;
+  return n;
+}
+
+static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
+  const DevItem& it = P.items[item];
+  double* base = (double*)ws;
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+    const DevSketch& s = P.sketches[si];
+    cudaError_t e = cudaMemsetAsync(base + s.off, 0, sizeof(double) * s.rows * s.width, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return TT_OK;
+}
+
+static tt_status accumulate(Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                            cudaStream_t st) {
+  const DevItem& it = P.items[item];
+  cudaError_t e;
+  if (it.prec != TT_PREC_FP64 && !mixed_tc_supported(P, item, count)) return TT_ERR_UNSUPPORTED;
+  if (it.prec == TT_PREC_FP64) {
+    e = launch_sketch_f64(P, item, X, first, count, ws, st);
+  } else {
+    e = launch_sketch_mixed(P, item, X, first, count, ws, st);
+  }
+  return cuda_status(e);
+}
+
+}  // namespace tts
+
+using namespace tts;
+
+extern "C" {
+
+tt_status tt_sketch_plan(const tt_problem* prob, tt_plan_t* out) { return make_plan(prob, 1, out); }
+
+tt_status tt_sketch_plan_batched(const tt_problem* probs, int count, tt_plan_t* out) {
+  return make_plan(probs, count, out);
+}
+
+void tt_plan_destroy(tt_plan_t plan) { delete as_plan(plan); }
+
+tt_status tt_plan_sizes(tt_plan_t plan, size_t* workspace_bytes, int64_t* core_entries,
+                        int* rank_entries) {
+  Plan* P = as_plan(plan);
+  if (!P) return TT_ERR_INVALID_ARG;
+  if (workspace_bytes) *workspace_bytes = (size_t)P->ws_doubles * 8;
+  if (core_entries) *core_entries = P->core_entries;
+  if (rank_entries) *rank_entries = P->rank_entries;
+  return TT_OK;
+}
+
+tt_status tt_plan_core_layout(tt_plan_t plan, int item, int64_t* core_off, int* rpad) {
+  Plan* P = as_plan(plan);
+  if (!P || item < 0 || item >= (int)P->items.size()) return TT_ERR_INVALID_ARG;
+  const DevItem& it = P->items[item];
+  for (int k = 0; k <= TT_MAXD; ++k) {
+    if (core_off) core_off[k] = (k >= 1 && k <= it.d) ? it.core_off[k] : 0;
+    if (rpad) rpad[k] = k <= it.d ? it.rpad[k] : 0;
+  }
+  return TT_OK;
+}
+
+tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, int* k, int64_t* rows,
+                              int* width, int64_t* byte_off) {
+  Plan* P = as_plan(plan);
+  if (!P || item < 0 || item >= (int)P->items.size()) return TT_ERR_INVALID_ARG;
+  const DevItem& it = P->items[item];
+  if (index < 0 || index >= it.nsk) return TT_ERR_INVALID_ARG;
+  const DevSketch& s = P->sketches[it.sk0 + index];
+  if (type) *type = s.type;
+  if (k) *k = s.k;
+  if (rows) *rows = s.rows;
+  if (width) *width = s.width;
+  if (byte_off) *byte_off = s.off * 8;
+  return TT_OK;
+}
+
+tt_status tt_plan_problem(tt_plan_t plan, int item, tt_problem* out) {
+  Plan* P = as_plan(plan);
+  if (!P || !out || item < 0 || item >= (int)P->probs.size()) return TT_ERR_INVALID_ARG;
+  *out = P->probs[item];
+  return TT_OK;
+}
+
+tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  if (P->items[0].passes != 1) return TT_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  s = zero_sketches(*P, 0, ws, st);
+  if (s != TT_OK) return s;
+  std::fill(P->slab_seen.begin(), P->slab_seen.end(), 0);
+  P->begun = true;
+  P->forward_done = false;
+  return TT_OK;
+}
+
+tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_last,
+                              int64_t count_last, void* ws, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws || !slab || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  const DevItem& it = P->items[0];
+  if (!P->begun) return TT_ERR_STATE;
+  if (first_last < 0 || count_last < 1 || first_last + count_last > it.n[it.d - 1])
+    return TT_ERR_INVALID_ARG;
+  for (int64_t i = first_last; i < first_last + count_last; ++i)
+    if (P->slab_seen[(size_t)i]) return TT_ERR_STATE;
+  tt_status s = accumulate(*P, 0, slab, first_last, count_last, ws, (cudaStream_t)stream);
+  if (s != TT_OK) return s;
+  for (int64_t i = first_last; i < first_last + count_last; ++i) P->slab_seen[(size_t)i] = 1;
+  return TT_OK;
+}
+
+tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
+                            tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws || !cores || !ranks || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  if (!P->begun) return TT_ERR_STATE;
+  for (char c : P->slab_seen)
+    if (!c) return TT_ERR_STATE;
+  tt_status s = cuda_status(launch_finalize(*P, ws, cores, ranks, (cudaStream_t)stream));
+  if (s != TT_OK) return s;
+  P->begun = false;
+  P->forward_done = true;
+  return TT_OK;
+}
+
+tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* ranks,
+                   tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !X || !ws || !cores || !ranks || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DevItem& it = P->items[0];
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  s = zero_sketches(*P, 0, ws, st);
+  if (s != TT_OK) return s;
+  s = accumulate(*P, 0, X, 0, it.n[it.d - 1], ws, st);
+  if (s != TT_OK) return s;
+  if (it.passes == 2) {
+    s = cuda_status(launch_finalize(*P, ws, cores, ranks, st));  // bases + outer cores
+    if (s != TT_OK) return s;
+    s = cuda_status(launch_twopass_mid(*P, X, ws, cores, ranks, st));  // second pass over X
+  } else {
+    s = cuda_status(launch_finalize(*P, ws, cores, ranks, st));
+  }
+  if (s != TT_OK) return s;
+  P->begun = false;
+  P->forward_done = true;
+  return TT_OK;
+}
+
+tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores,
+                           int* ranks, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !X_ptrs || !ws || !cores || !ranks) return TT_ERR_INVALID_ARG;
+  for (const DevItem& it : P->items)
+    if (it.passes != 1) return TT_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    if (!X_ptrs[i]) return TT_ERR_INVALID_ARG;
+    P->items[i].X = X_ptrs[i];
+  }
+  // item pointers live in the device tables: rebuild and (re)upload
+  build_blob(*P);
+  P->uploaded_ws = nullptr;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    s = zero_sketches(*P, (int)i, ws, st);
+    if (s != TT_OK) return s;
+  }
+  s = cuda_status(launch_sketch_batched(*P, ws, st));
+  if (s != TT_OK) return s;
+  s = cuda_status(launch_finalize(*P, ws, cores, ranks, st));
+  if (s != TT_OK) return s;
+  P->forward_done = true;
+  return TT_OK;
+}
+
+tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void* dX,
+                            tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws || !dcores || !dX || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  if (!P->forward_done) return TT_ERR_STATE;
+  if (P->items[0].passes != 1) return TT_ERR_UNSUPPORTED;
+  return cuda_status(launch_backward(*P, 0, dcores, dX, ws, (cudaStream_t)stream));
+}
+
+tt_status tt_reconstruct(tt_plan_t plan, const double* cores, void* Xt, tt_dtype dtype, void* ws,
+                         tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !cores || !Xt || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  return cuda_status(launch_reconstruct(*P, 0, cores, Xt, dtype == TT_F64, nullptr, 0, nullptr, ws, st));
+}
+
+tt_status tt_reconstruct_error(tt_plan_t plan, const double* cores, const void* X, double* out2,
+                               void* ws, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !cores || !X || !out2 || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  return cuda_status(launch_reconstruct(*P, 0, cores, nullptr, 0, X, P->items[0].x_f64, out2, ws, st));
+}
+
+tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const void* dXt,
+                                  tt_dtype dtype, double* dcores, void* ws, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !cores || !dXt || !dcores || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  return cuda_status(launch_reconstruct_backward(*P, 0, cores, dXt, dtype == TT_F64, dcores, ws, st));
+}
+
+tt_status tt_query_status(tt_plan_t plan, const void* ws, const int* ranks, int* status_host,
+                          int* ranks_host, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  int word = 0;
+  e = cudaMemcpy(&word, (const char*)ws + kStatusOff, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (status_host) {
+    int s = TT_OK;
+    if (word & ST_RANK_CAP) s = TT_WARN_RANK_CAP;
+    if (word & ST_TIMEOUT) s = TT_ERR_TIMEOUT;
+    if (word & ST_RANK_DEFICIENT) s = TT_ERR_RANK_DEFICIENT;
+    *status_host = s;
+  }
+  if (ranks_host) {
+    if (!ranks) return TT_ERR_INVALID_ARG;
+    e = cudaMemcpy(ranks_host, ranks, sizeof(int) * P->rank_entries, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return TT_OK;
+}
+
+const char* tt_status_string(tt_status s) {
+  switch (s) {
+    case TT_OK: return "ok";
+    case TT_ERR_INVALID_ARG: return "invalid argument";
+    case TT_ERR_UNSUPPORTED: return "unsupported";
+    case TT_ERR_CUDA: return "CUDA runtime error";
+    case TT_ERR_STATE: return "calls out of order";
+    case TT_ERR_RANK_DEFICIENT: return "rank-deficient least-squares matrix";
+    case TT_ERR_TIMEOUT: return "device wait timed out";
+    case TT_WARN_RANK_CAP: return "tolerance not met at rmax";
+    case TT_ERR_NO_DEVICE: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+int64_t tt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* tt_version(void) { return "ttsketch-gb300 sm_103a " __DATE__; }
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Reconstruction X~(i_1..i_d) = G_1(:, i_1, :) ... G_d(:, i_d, :) (Sec. 2.2)
+// and its fused relative-error form (eq. (1.1)).
+//
+// The cores are contracted into a left interface L_{d*} (N_{d*} x r_{d*}) and a
+// right interface Rt_{d*+1} (r_{d*} x M_{d*}); then X~ = L_{d*} Rt_{d*+1} seen as
+// the middle unfolding, one thread per entry (FP64).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace tts {
+namespace {
+
+constexpr int kThreads = 256;
+
+// L_k(u + N_{k-1} i, c) = sum_a L_{k-1}(u, a) G_k(a, i, c);  L_0 = [1].
+__global__ void iface_left_kernel(const double* Lp, int64_t Np, int rpp, const double* G, int64_t nk,
+                                  int rpk, double* Lo) {
+  const int64_t Nk = Np * nk;
+  const int64_t total = Nk * rpk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e % Nk;
+    const int c = (int)(e / Nk);
+    const int64_t u = row % Np, i = row / Np;
+    double acc = 0.0;
+    if (Lp == nullptr) {
+      acc = G[0 + rpp * (i + nk * c)];
+    } else {
+      for (int a = 0; a < rpp; ++a) acc += Lp[u + Np * a] * G[a + rpp * (i + nk * c)];
+    }
+    Lo[row + Nk * c] = acc;
+  }
+}
+
+// Rt_k(a, i + n_k v) = sum_c G_k(a, i, c) Rt_{k+1}(c, v);  Rt_{d+1} = [1].
+__global__ void iface_right_kernel(const double* Rn, int64_t Mn, int rpn, const double* G, int64_t nk,
+                                   int rpa, double* Ro) {
+  const int64_t Mk = nk * Mn;
+  const int64_t total = (int64_t)rpa * Mk;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % rpa);
+    const int64_t col = e / rpa;
+    const int64_t i = col % nk, v = col / nk;
+    double acc = 0.0;
+    if (Rn == nullptr) {
+      acc = G[a + rpa * (i + nk * 0)];
+    } else {
+      for (int c = 0; c < rpn; ++c) acc += G[a + rpa * (i + nk * c)] * Rn[c + rpn * v];
+    }
+    Ro[a + (int64_t)rpa * col] = acc;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// X~(u + Nm v) = sum_c L(u, c) Rt(c, v); optionally store it and/or accumulate
+// [sum (X - X~)^2, sum X^2].
+__global__ void __launch_bounds__(kThreads) dense_kernel(const double* L, const double* Rt, int64_t Nm,
+                                                         int64_t Mm, int rp, void* out, int out_f64,
+                                                         const void* Xc, int xc_f64, double* out2) {
+  double e2 = 0.0, x2 = 0.0;
+  const int64_t total = Nm * Mm;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = e % Nm, v = e / Nm;
+    double acc = 0.0;
+    for (int c = 0; c < rp; ++c) acc += L[u + Nm * c] * Rt[c + (int64_t)rp * v];
+    if (out) {
+      if (out_f64) ((double*)out)[e] = acc;
+      else ((float*)out)[e] = (float)acc;
+    }
+    if (Xc) {
+      const double x = xc_f64 ? ((const double*)Xc)[e] : (double)((const float*)Xc)[e];
+      e2 += (x - acc) * (x - acc);
+      x2 += x * x;
+    }
+  }
+  if (out2) {
+    __shared__ double red[2][32];
+    e2 = warp_sum(e2);
+    x2 = warp_sum(x2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][wid] = e2;
+      red[1][wid] = x2;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      double a = lane < (int)(blockDim.x >> 5) ? red[0][lane] : 0.0;
+      double b = lane < (int)(blockDim.x >> 5) ? red[1][lane] : 0.0;
+      a = warp_sum(a);
+      b = warp_sum(b);
+      if (lane == 0) {
+        atomicAdd(out2, a);
+        atomicAdd(out2 + 1, b);
+      }
+    }
+  }
+}
+
+int grid_for(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 16LL * device_sm_count()));
+}
+
+}  // namespace
+
+cudaError_t build_interfaces(const Plan& P, int item, const double* cores, void* ws, cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[item];
+  double* W = (double*)ws;
+  const int d = it.d, ds = it.ds;
+  for (int k = 1; k <= ds; ++k) {
+    const double* Lp = k == 1 ? nullptr : W + it.off_L[k - 1];
+    const int64_t n = it.N[k] * it.rpad[k];
+    count_launch();
+    iface_left_kernel<<<grid_for(n), kThreads, 0, st>>>(Lp, it.N[k - 1], it.rpad[k - 1],
+                                                        cores + it.core_off[k], it.n[k - 1],
+                                                        it.rpad[k], W + it.off_L[k]);
+  }
+  for (int k = d; k >= ds + 1; --k) {
+    const double* Rn = k == d ? nullptr : W + it.off_Rt[k + 1];
+    const int64_t Mn = it.N[d] / it.N[k];
+    const int64_t n = (int64_t)it.rpad[k - 1] * it.n[k - 1] * Mn;
+    count_launch();
+    iface_right_kernel<<<grid_for(n), kThreads, 0, st>>>(Rn, Mn, it.rpad[k], cores + it.core_off[k],
+                                                         it.n[k - 1], it.rpad[k - 1], W + it.off_Rt[k]);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, void* Xt, int x_f64,
+                               const void* Xcmp, int cmp_f64, double* out2, void* ws,
+                               cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[item];
+  cudaError_t e = build_interfaces(P, item, cores, ws, st);
+  if (e != cudaSuccess) return e;
+  if (out2) {
+    e = cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+  }
+  double* W = (double*)ws;
+  const int ds = it.ds;
+  const int64_t Nm = it.N[ds], Mm = it.N[it.d] / it.N[ds];
+  count_launch();
+  dense_kernel<<<grid_for(Nm * Mm), kThreads, 0, st>>>(W + it.off_L[ds], W + it.off_Rt[ds + 1], Nm, Mm,
+                                                       it.rpad[ds], Xt, x_f64, Xcmp, cmp_f64, out2);
+  return cudaGetLastError();
+}
+
+}  // namespace tts

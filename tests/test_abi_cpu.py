@@ -1,0 +1,165 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads and
+exports every declared symbol, and the host plan computes the paper's sizes."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2111_10448_gb300 import _native as N
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ttsketch.h")
+
+
+def declared_symbols():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tt_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = N.lib()
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(N.EXPORTED) == decl
+
+
+def plan(dims, **kw):
+    q = N.make_problem(dims, **kw)
+    h = C.c_void_p()
+    st = N.lib().tt_sketch_plan(C.byref(q), C.byref(h))
+    return st, h
+
+
+def sizes(h):
+    ws, ce, re_ = C.c_size_t(), C.c_int64(), C.c_int()
+    N.check(N.lib().tt_plan_sizes(h, C.byref(ws), C.byref(ce), C.byref(re_)), "sizes")
+    return ws.value, ce.value, re_.value
+
+
+def layout(h, item=0):
+    off = (C.c_int64 * (N.TT_MAXD + 1))()
+    rp = (C.c_int * (N.TT_MAXD + 1))()
+    N.check(N.lib().tt_plan_core_layout(h, item, off, rp), "layout")
+    return list(off), list(rp)
+
+
+def sketch_list(h, item=0):
+    out = []
+    i = 0
+    while True:
+        ty, k, w, rows, off = C.c_int(), C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        if N.lib().tt_plan_sketch_info(h, item, i, C.byref(ty), C.byref(k), C.byref(rows), C.byref(w),
+                                       C.byref(off)) != N.TT_OK:
+            return out
+        out.append((ty.value, k.value, rows.value, w.value, off.value))
+        i += 1
+
+
+def test_table1_core_storage_through_plan(golden):
+    """Table 1 TT sizes, computed by the plan's core layout (fixed ranks)."""
+    for d, n, ranks, gb, mb in golden("table1_sizes.txt"):
+        d, n = int(d), int(n)
+        r = [int(v) for v in ranks.split(",")]
+        st, h = plan([n] * d, ranks=r, p=2)
+        assert st == N.TT_OK
+        _, ce, re_ = sizes(h)
+        assert f"{ce * 8 / 2 ** 20:.3g}" == f"{float(mb):.3g}"
+        assert re_ == d + 1
+        N.lib().tt_plan_destroy(h)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6, 9])
+def test_split_and_sketch_list(d):
+    """d* = ceil(d/2); column sketches k < d* (+ the middle one in one-pass),
+    row sketches k = d*..d-1 (the dimensionally consistent reading of the
+    middle-core formula); widths l = r + p."""
+    dims = [3 + (k % 3) for k in range(d)]
+    r = [1] + [2] * (d - 1) + [1]
+    ds = (d + 1) // 2
+    Nk = [1]
+    for n in dims:
+        Nk.append(Nk[-1] * n)
+    for passes in (1, 2):
+        st, h = plan(dims, ranks=r, p=3, passes=passes)
+        assert st == N.TT_OK
+        sk = sketch_list(h)
+        want = [(0, k, Nk[k]) for k in range(1, ds)]
+        if passes == 1:
+            want.append((0, ds, Nk[ds]))
+        want += [(1, k, Nk[d] // Nk[k]) for k in range(ds, d)]
+        assert [(t, k, rows) for t, k, rows, _, _ in sk] == want
+        assert all(w == 2 + 3 for _, _, _, w, _ in sk)
+        offs = sorted(o for *_, o in sk)
+        assert all(o % 256 == 0 for o in offs)
+        N.lib().tt_plan_destroy(h)
+
+
+def test_memory_footprint_follows_the_paper():
+    """Sketch storage of PSTT2 is O(r n^floor(d/2)) and of PSTT2-onepass
+    O(r n^ceil(d/2)) (Sec. 4.3, eqs. M_PSTT2 and M_PSTT2-onepass)."""
+    n, r, p = 10, 3, 2
+    for d in (5, 6, 7):
+        for passes, expo in ((2, d // 2), (1, (d + 1) // 2)):
+            st, h = plan([n] * d, ranks=[1] + [r] * (d - 1) + [1], p=p, passes=passes)
+            biggest = max(rows for _, _, rows, _, _ in sketch_list(h))
+            assert biggest == n ** expo
+            N.lib().tt_plan_destroy(h)
+
+
+def test_rank_clamping_and_padding():
+    st, h = plan([4, 50, 3], ranks=[1, 9, 9, 1], p=2)
+    assert st == N.TT_OK
+    off, rp = layout(h)
+    assert rp[:4] == [1, 4, 3, 1]  # min(N_k, M_k)
+    assert off[1] == 0 and off[2] == 1 * 4 * 4 and off[3] == 16 + 4 * 50 * 3
+    N.lib().tt_plan_destroy(h)
+    st, h = plan([8, 8, 8, 8], eps=1e-6, rmax=6, p=10)
+    off, rp = layout(h)
+    assert rp[:5] == [1, 6, 6, 6, 1]
+    N.lib().tt_plan_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dims=[5], ranks=[1, 1]),
+    dict(dims=[5, 5], ranks=[2, 2, 1]),
+    dict(dims=[5, 5], ranks=[1, 0, 1]),
+    dict(dims=[5, 0, 5], ranks=[1, 1, 1, 1]),
+    dict(dims=[5, 5], ranks=[1, 2, 1], p=0),
+    dict(dims=[5, 5], ranks=[1, 2, 1], passes=3),
+    dict(dims=[5, 5], eps=1e-3, rmax=0),
+    dict(dims=[5, 5], eps=1e-3, rmax=60, p=10),
+    dict(dims=[100, 100], ranks=[1, 70, 1]),
+])
+def test_invalid_problems_rejected(bad):
+    dims = bad.pop("dims")
+    st, h = plan(dims, **bad)
+    assert st == N.TT_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_mixed_needs_fp32_storage():
+    st, _ = plan([8, 8, 8], ranks=[1, 2, 2, 1], x_dtype=N.TT_F64, prec=N.TT_PREC_BF16)
+    assert st == N.TT_ERR_UNSUPPORTED
+
+
+def test_status_strings():
+    for s in range(9):
+        assert N.lib().tt_status_string(s)
+    assert b"ttsketch" in N.lib().tt_version()
+
+
+def test_batched_plan_slices():
+    probs = (N.tt_problem * 3)()
+    for i, dims in enumerate([[4, 5, 6], [6, 6, 6, 6], [3, 9]]):
+        probs[i] = N.make_problem(dims, ranks=[1] + [2] * (len(dims) - 1) + [1], p=2)
+    h = C.c_void_p()
+    N.check(N.lib().tt_sketch_plan_batched(probs, 3, C.byref(h)), "batched")
+    _, ce, re_ = sizes(h)
+    assert re_ == 4 + 5 + 3
+    offs = [layout(h, i)[0] for i in range(3)]
+    assert offs[1][1] == offs[0][3] + 2 * 6 * 1
+    assert ce == offs[2][2] + 2 * 9 * 1
+    N.lib().tt_plan_destroy(h)

@@ -1,0 +1,108 @@
+"""GPU parity of the mixed-precision (TF32 / BF16 tensor-core) sketch path.
+
+Bars (derived from the arithmetic):
+* test-matrix entries: the FP32 generator rounded to the MMA type equals the
+  oracle's FP64 normal rounded to that type, except for rare one-ulp flips at
+  rounding boundaries (<0.1% of entries, never more than one ulp);
+* sketches: equal to the oracle's FP64 product of the split X (hi + lo in the
+  MMA type) with the rounded test matrix, up to FP32 accumulation within a tile
+  (max-norm relative 2e-5);
+* reconstruction: within 10 eps of the FP64 oracle (relative Frobenius), the
+  precision form's stated target.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import ttinputs as ti
+from oracle import philox, pstt2 as OP, tt as OT
+from paper_2111_10448_gb300 import TTSketch, _native as N
+from tests.gpu_util import rel, sketch_dict, to_dev
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
+ULP = {"tf32": 2.0 ** -10, "bf16": 2.0 ** -7}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_test_matrix_mixed_matches_rounded_oracle(prec):
+    nrows, ncols, sid = 20000, 26, 5
+    out = torch.empty(nrows * ncols, dtype=torch.float64, device="cuda")
+    N.check(N.lib().tt_test_matrix(3, sid, 17, nrows, ncols, PREC[prec], C.c_void_p(out.data_ptr()),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream)), "tm")
+    got = out.cpu().numpy().reshape(ncols, nrows).T
+    ref = philox.round_to(philox.gaussian(3, sid, np.arange(17, 17 + nrows, dtype=np.uint64), ncols), prec)
+    diff = np.abs(got - ref)
+    assert np.all(diff <= ULP[prec] * np.abs(ref) * 1.0001 + 1e-30)
+    assert np.mean(diff > 0) < 1e-3
+    assert np.array_equal(philox.round_to(got, prec), got)  # values are exact in the MMA type
+
+
+def _split(x, prec):
+    hi = philox.round_to(x, prec)
+    lo = philox.round_to(x - hi, prec)
+    return hi + lo
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("dims,r", [([40, 7, 6, 70], [1, 4, 5, 4, 1]), ([9, 8, 7, 6, 5, 9], [1, 5, 6, 6, 5, 5, 1]),
+                                    ([130, 100], [1, 6, 1])])
+def test_mixed_sketches_match_oracle(prec, dims, r):
+    x = ti.random_tt(dims, r, seed=2, noise=1e-6).astype(np.float32)
+    target = [1] + [v for v in r[1:-1]] + [1]
+    t = TTSketch(dims, ranks=target, p=6, seed=4, x_dtype=torch.float32, prec=prec)
+    t.begin()
+    t.accumulate(to_dev(x), 0, dims[-1])
+    sk = sketch_dict(t)
+    t.finalize()
+    xs = _split(x.astype(np.float64), prec)
+    o = OP.pstt2(xs, dims, ranks=target, p=6, seed=4, passes=1, test_fmt=prec)
+    for k, S in o["sketch"]["S"].items():
+        G = sk[(0, k)]
+        assert np.max(np.abs(G - S)) <= 2e-5 * np.max(np.abs(S)), (k, np.max(np.abs(G - S)) / np.max(np.abs(S)))
+    for k, R in o["sketch"]["R"].items():
+        G = sk[(1, k)]
+        assert np.max(np.abs(G - R)) <= 2e-5 * np.max(np.abs(R)), (k,)
+    st, _ = t.status()
+    assert st == 0
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("case", ["config2_small", "config3_small"])
+def test_mixed_within_10eps_of_oracle(prec, case):
+    if case == "config2_small":
+        dims, eps, p, rmax = [9] * 6, 1e-5, 10, 16
+        x = ti.random_tt(dims, [1, 9, 10, 10, 10, 9, 1], seed=0, noise=1e-6).astype(np.float32)
+    else:
+        dims, eps, p, rmax = [32] * 4, 1e-6, 10, 6
+        x = ti.hilbert_type(dims, np.float32)
+    x64 = x.astype(np.float64)
+    t = TTSketch(dims, eps=eps, rmax=rmax, p=p, seed=1, x_dtype=torch.float32, prec=prec).pstt2(to_dev(x))
+    f = TTSketch(dims, eps=eps, rmax=rmax, p=p, seed=1, x_dtype=torch.float32, prec="fp64").pstt2(to_dev(x))
+    o = OP.pstt2(x64, dims, eps=eps, rmax=rmax, p=p, seed=1)
+    xt = t.reconstruct().cpu().numpy()
+    ref = OT.tt_full(o["cores"])
+    e_or = rel(xt, ref, x64)
+    e_x = rel(xt, x64, x64)
+    e_f = rel(xt, f.reconstruct().cpu().numpy(), x64)
+    print(f"{case} {prec}: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} |X~-X~fp64gpu|={e_f:.2e} ranks={t.status()[1]}")
+    assert e_or <= 10 * eps
+    assert e_x <= 10 * eps
+    assert e_f <= 10 * eps
+
+
+def test_mixed_streaming_equals_one_shot():
+    dims = [24, 10, 12, 20]
+    x = ti.random_tt(dims, [1, 3, 4, 3, 1], seed=6, noise=1e-5).astype(np.float32)
+    X = to_dev(x)
+    one = TTSketch(dims, ranks=[1, 3, 4, 3, 1], p=5, seed=3, prec="bf16").pstt2(X)
+    t = TTSketch(dims, ranks=[1, 3, 4, 3, 1], p=5, seed=3, prec="bf16")
+    Nd1 = 24 * 10 * 12
+    t.begin()
+    for first, cnt in [(12, 8), (0, 5), (5, 7)]:
+        t.accumulate(X[first * Nd1:(first + cnt) * Nd1].clone(), first, cnt)
+    t.finalize()
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-9
