@@ -58,6 +58,7 @@ _SIGS = {
     "tt_plan_problem": (C.c_int, [_P, C.c_int, C.POINTER(tt_problem)]),
     "tt_plan_sketch_info": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "tt_sketch_kernel_kind": (C.c_int, [_P, C.c_int64]),
     "tt_pstt2": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "tt_pstt2_begin": (C.c_int, [_P, _P, _P]),
     "tt_pstt2_accumulate": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),

@@ -114,6 +114,7 @@ cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t fi
 cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t first,
                                 int64_t count, void* ws, cudaStream_t st);
 bool mixed_tc_supported(const Plan& P, int item, int64_t count);
+bool use_tc_kernel(const Plan& P, int item, int64_t count);
 cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st);
 cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, void* Xt, int x_f64,
                                const void* Xcmp, int cmp_f64, double* out2, void* ws,

@@ -61,8 +61,7 @@ __device__ __forceinline__ void normals4_f64(uint64_t seed, uint32_t sid, uint64
 // every kernel that needs the same entry (the sketch, and the middle-core
 // solve that regenerates Omega_{d*}) runs one compiled body and gets
 // bit-identical values.
-__device__ __noinline__ void normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q,
-                                          float z[4]);
+__device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q);
 
 // Round an FP32 value to the MMA input type, nearest-even, returned as FP32.
 __device__ __forceinline__ float round_tf32(float x) {

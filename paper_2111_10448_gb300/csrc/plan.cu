@@ -398,6 +398,13 @@ tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, in
   return TT_OK;
 }
 
+int tt_sketch_kernel_kind(tt_plan_t plan, int64_t count_last) {
+  Plan* P = as_plan(plan);
+  if (!P || P->items.empty()) return -1;
+  if (P->items[0].prec == TT_PREC_FP64) return 0;
+  return use_tc_kernel(*P, 0, count_last) ? 2 : 1;
+}
+
 tt_status tt_plan_problem(tt_plan_t plan, int item, tt_problem* out) {
   Plan* P = as_plan(plan);
   if (!P || !out || item < 0 || item >= (int)P->probs.size()) return TT_ERR_INVALID_ARG;

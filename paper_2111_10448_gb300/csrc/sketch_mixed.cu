@@ -4,14 +4,17 @@
 // All of them live in this translation unit and call the one out-of-line FP32
 // generator below.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include <cuda_bf16.h>
 
 #include "internal.cuh"
 #include "philox.cuh"
 
 namespace tts {
 
-__device__ __noinline__ void normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q,
-                                          float z[4]) {
+__device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q) {
   uint32_t c0 = (uint32_t)row, c1 = (uint32_t)(row >> 32), c2 = q, c3 = sid;
   philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
   const float u0 = __fmul_rn((float)((c0 >> 9) * 2u + 1u), 0x1p-24f);
@@ -23,10 +26,7 @@ __device__ __noinline__ void normals4_f32(uint64_t seed, uint32_t sid, uint64_t 
   float sa, ca, sb, cb;
   sincospif(__fmul_rn(2.0f, u1), &sa, &ca);
   sincospif(__fmul_rn(2.0f, u3), &sb, &cb);
-  z[0] = __fmul_rn(ra, ca);
-  z[1] = __fmul_rn(ra, sa);
-  z[2] = __fmul_rn(rb, cb);
-  z[3] = __fmul_rn(rb, sb);
+  return make_float4(__fmul_rn(ra, ca), __fmul_rn(ra, sa), __fmul_rn(rb, cb), __fmul_rn(rb, sb));
 }
 
 namespace {
@@ -39,8 +39,8 @@ __global__ void test_matrix_mixed_kernel(uint64_t seed, int sid, int64_t row0, i
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e % nrows;
     const int q = (int)(e / nrows);
-    float z[4];
-    normals4_f32(seed, (uint32_t)sid, (uint64_t)(row0 + r), (uint32_t)q, z);
+    const float4 z4 = normals4_f32(seed, (uint32_t)sid, (uint64_t)(row0 + r), (uint32_t)q);
+    const float z[4] = {z4.x, z4.y, z4.z, z4.w};
     for (int t = 0; t < 4; ++t)
       if (4 * q + t < ncols) out[r + nrows * (4 * q + t)] = (double)round_prec(z[t], prec);
   }
@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item, c
     const int nq = (l + 3) / 4;
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
-      float z[4];
-      normals4_f32(it.seed, (uint32_t)it.ds, (uint64_t)(v0 + v), (uint32_t)q, z);
+      const float4 z4 = normals4_f32(it.seed, (uint32_t)it.ds, (uint64_t)(v0 + v), (uint32_t)q);
+      const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = (double)round_prec(z[t], it.prec);
@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
         const int r = o % nr, q = o / nr;
         const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
                                   : (uint64_t)((a0 + r) + a.n1 * wlo);
-        float z[4];
-        normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q, z);
+        const float4 z4 = normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
+        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
       }
@@ -274,6 +274,515 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
 }
 
 }  // namespace
+
+// ----------------------------------------------------------------------------
+// tcgen05 plane kernel: the fused multi-sketch for large planes (n_1 and the
+// slab's last-mode extent both 128 or 256, d = 3 or 4), BF16 with X split into
+// hi + lo, FP32 accumulators in tensor memory, FP64 flush.
+//
+// Per plane w the column sketches form ONE product D_L = X(:, w, :) [B_1 | B_2]
+// (M = i_1, K = i_d, N = l * #column sketches) and the row sketches ONE product
+// D_R = X(:, w, :)^T [C_1 | C_2] (M = i_d, K = i_1), where the B / C blocks are
+// the test-matrix rows the plane needs (regenerated here).  The plane is
+// processed in 128 x 128 quarters.  A quarter is stored once in shared memory,
+// as BF16 hi and lo tiles in the no-swizzle core-matrix layout (8 x 8 blocks,
+// i_1 contiguous inside a 16-byte row, i_d the row index); that single layout
+// is the MN-major A operand of D_L and the K-major A operand of D_R, so every
+// X element is written to shared memory once and read by the tensor core
+// twice per part.  Core matrices are 144 bytes apart along i_1 (16 bytes of
+// padding), which makes the producers' 16-byte stores conflict-free.
+//
+// Accumulator slots: w = kL + WL kR with WL = N_{d*}/n_1.  All column-sketch
+// output rows depend on w only through kL, all row-sketch rows only through
+// kR.  A CTA tile is a block of T2 kL values x T3 kR values (16 planes); its
+// D_L slots (one per kL) and D_R slots (one per kR) live in tensor memory for
+// the whole tile and are flushed once, with FP64 atomics, by the epilogue
+// warps.
+//
+// Warp roles (672 threads, one CTA per SM): warps 0-3 epilogue (TMEM lanes
+// 0-127), warp 4 TMEM allocation + MMA issue (one thread), warps 5-12
+// producers (X -> BF16 hi/lo), warps 13-20 test-matrix generation.  Stages
+// are handed over with mbarriers; every wait is bounded (about 2 s), after
+// which the CTA raises the timeout status bit, stops, drains its MMAs and
+// frees its tensor memory.
+namespace tc {
+
+constexpr int kS1 = 144;                 // bytes between core matrices along i_1 (k of B)
+constexpr int kS4 = 16 * kS1;            // 2304: bytes between core matrices along i_d (n of B)
+constexpr int kTileB = 16 * kS4;         // one 128 x 128 BF16 tile
+constexpr int kStageB = 2 * kTileB;      // hi + lo
+constexpr int kStages = 2;
+constexpr int kBBlkB = 4 * kS4;          // one test-matrix block, N <= 32
+constexpr int kBBlks = 4;                // L[h4=0,1], R[h1=0,1] per plane
+constexpr int kBBufs = 2;
+constexpr int kWarps = 21;
+constexpr int kThreads = kWarps * 32;
+constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 8;
+constexpr int kOffB = kStages * kStageB;
+constexpr int kOffBar = kOffB + kBBufs * kBBlks * kBBlkB;
+constexpr int kSmemBytes = kOffBar + 256 + 1024;  // barriers + alignment slack
+constexpr long long kWaitCycles = 4000000000LL;  // bounded waits (~2 s)
+
+struct SkTc {
+  int64_t rows, off, wdiv, hstride;
+  int sid, pad_;
+};
+
+struct TcArgs {
+  const float* X;
+  double* ws;
+  int* status;
+  int64_t n1, first, W, WL, WR, Nd1, tilesL, tilesR;
+  uint64_t seed;
+  int H1, H4, T2, T3, ell, nL, nR, NL, NR, tmem_cols;
+  SkTc col[4], row[4];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; on give-up raises the abort flag and the timeout status bit.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor, no swizzle: start, leading (K-direction)
+// and stride (M/N-direction) byte offsets of the core matrices, version 1.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// Instruction descriptor, kind::f16: BF16 x BF16 -> F32, M = 128.
+__host__ __device__ constexpr uint32_t make_idesc(int n, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_ss(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&b);
+}
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+// Iteration helper shared by all roles: plane (a, b) of tile t is valid when
+// both keys are in range.
+struct TileInfo {
+  int64_t kL0, kR0;
+  int nA, nB;
+};
+__device__ __forceinline__ TileInfo tile_info(const TcArgs& g, int64_t t) {
+  TileInfo ti;
+  const int64_t tl = t % g.tilesL, tr = t / g.tilesL;
+  ti.kL0 = tl * g.T2;
+  ti.kR0 = tr * g.T3;
+  ti.nA = (int)imin64(g.T2, g.WL - ti.kL0);
+  ti.nB = (int)imin64(g.T3, g.WR - ti.kR0);
+  return ti;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
+  // barrier indices
+  const int FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TM_FULL = 8, TM_EMPTY = 9, DRAIN = 10;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 128);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 136);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(bar(FULL_A + s), kProdWarps);
+      mbar_init(bar(EMPTY_A + s), 1);
+      mbar_init(bar(FULL_B + s), kRngWarps);
+      mbar_init(bar(EMPTY_B + s), 1);
+    }
+    mbar_init(bar(TM_FULL), 1);
+    mbar_init(bar(TM_EMPTY), kEpiWarps);
+    mbar_init(bar(DRAIN), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)g.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t ntiles = g.tilesL * g.tilesR;
+  const uint32_t sA = smem_u32(sm);
+  const uint32_t sB = smem_u32(sm + kOffB);
+  const int ell = g.ell;
+
+  if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
+    // ------------------------------------------------------------ producers
+    const int pt = threadIdx.x - kProdWarp0 * 32;   // 0..255
+    const int cb1 = pt & 15, rsub = pt >> 4;         // i_1 core block, row group
+    uint32_t qi = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      const TileInfo ti = tile_info(g, t);
+      for (int b = 0; b < ti.nB && !*abort_flag; ++b)
+        for (int a = 0; a < ti.nA && !*abort_flag; ++a) {
+          const int64_t w = (ti.kL0 + a) + g.WL * (ti.kR0 + b);
+          for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
+            const int h1 = q % g.H1, h4 = q / g.H1;
+            const int st = qi & 1;
+            if (!mbar_wait(bar(EMPTY_A + st), ((qi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
+            const float* src = g.X + (h1 * 128 + cb1 * 8) + g.n1 * w + g.Nd1 * (int64_t)(h4 * 128 + rsub);
+            float4 v[16];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const float4* p4 = reinterpret_cast<const float4*>(src + g.Nd1 * (int64_t)(16 * m));
+              v[2 * m] = __ldcs(p4);
+              v[2 * m + 1] = __ldcs(p4 + 1);
+            }
+            const uint32_t tileA = sA + st * kStageB;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const int i4 = rsub + 16 * m;
+              const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
+                                  v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
+              uint32_t hb[4], lb[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
+                const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
+                lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
+              }
+              const uint32_t off = cb1 * kS1 + (i4 >> 3) * kS4 + (i4 & 7) * 16;
+              st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
+              st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(FULL_A + st));
+          }
+        }
+    }
+  } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
+    // ------------------------------------------------- test-matrix blocks
+    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..255
+    uint32_t pi = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+      const TileInfo ti = tile_info(g, t);
+      for (int b = 0; b < ti.nB && !*abort_flag; ++b)
+        for (int a = 0; a < ti.nA && !*abort_flag; ++a, ++pi) {
+          const int64_t w = (ti.kL0 + a) + g.WL * (ti.kR0 + b);
+          const int buf = pi & 1;
+          if (!mbar_wait(bar(EMPTY_B + buf), ((pi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
+          // blocks: 0..H4-1 = column side (k = i_d), 2..2+H1-1 = row side (k = i_1)
+          const int jobsL = 16 * (g.NL / 4), jobsR = 16 * (g.NR / 4);
+          const int total = g.H4 * jobsL + g.H1 * jobsR;
+          for (int job = rt; job < total; job += kRngWarps * 32) {
+            int blk, jj, nq;
+            bool colside;
+            if (job < g.H4 * jobsL) {
+              colside = true;
+              blk = job / jobsL;
+              jj = job % jobsL;
+            } else {
+              colside = false;
+              blk = (job - g.H4 * jobsL) / jobsR;
+              jj = (job - g.H4 * jobsL) % jobsR;
+            }
+            const int kg = jj & 15, qg = jj >> 4;
+            const int n0 = 4 * qg;
+            const int s = n0 / ell;
+            nq = (n0 % ell) >> 2;
+            float z[8][4];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              uint64_t row;
+              uint32_t sid;
+              if (colside) {
+                const SkTc sk = g.col[s];
+                const int64_t bglob = g.first + blk * 128 + 8 * kg + kk;
+                row = (uint64_t)(w / sk.wdiv + sk.hstride * bglob);
+                sid = (uint32_t)sk.sid;
+              } else {
+                const SkTc sk = g.row[s];
+                const int64_t i1 = blk * 128 + 8 * kg + kk;
+                row = (uint64_t)(i1 + g.n1 * (w % sk.wdiv));
+                sid = (uint32_t)sk.sid;
+              }
+              const float4 r4 = normals4_f32(g.seed, sid, row, (uint32_t)nq);
+              z[kk][0] = r4.x;
+              z[kk][1] = r4.y;
+              z[kk][2] = r4.z;
+              z[kk][3] = r4.w;
+            }
+            const uint32_t base = sB + (buf * kBBlks + (colside ? blk : 2 + blk)) * kBBlkB;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int n = n0 + u;
+              const uint32_t off = kg * kS1 + (n >> 3) * kS4 + (n & 7) * 16;
+              st_shared_v4(base + off, bf16x2_bits(z[0][u], z[1][u]), bf16x2_bits(z[2][u], z[3][u]),
+                           bf16x2_bits(z[4][u], z[5][u]), bf16x2_bits(z[6][u], z[7][u]));
+            }
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(FULL_B + buf));
+        }
+    }
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idL = make_idesc(g.NL, true), idR = make_idesc(g.NR, false);
+      const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
+      uint32_t qi = 0, pi = 0, tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const TileInfo ti = tile_info(g, t);
+        ok = mbar_wait(bar(TM_EMPTY), (tl & 1) ^ 1, abort_flag, g.status);
+        if (!ok) break;
+        tc_fence_after();
+        uint32_t initL = 0, initR = 0;  // slot has been written in this tile
+        for (int b = 0; b < ti.nB && ok; ++b)
+          for (int a = 0; a < ti.nA && ok; ++a, ++pi) {
+            const int buf = pi & 1;
+            ok = mbar_wait(bar(FULL_B + buf), (pi >> 1) & 1, abort_flag, g.status);
+            if (!ok) break;
+            tc_fence_after();
+            for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
+              const int h1 = q % g.H1, h4 = q / g.H1;
+              const int st = qi & 1;
+              ok = mbar_wait(bar(FULL_A + st), (qi >> 1) & 1, abort_flag, g.status);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t tileA = sA + st * kStageB;
+              const uint32_t bL = sB + (buf * kBBlks + h4) * kBBlkB;
+              const uint32_t bR = sB + (buf * kBBlks + 2 + h1) * kBBlkB;
+              const int slotL = a * g.H1 + h1, slotR = b * g.H4 + h4;
+              const uint32_t dL = tmem + (uint32_t)(slotL * g.NL);
+              const uint32_t dR = tmem + colR0 + (uint32_t)(slotR * g.NR);
+              for (int ks = 0; ks < 8; ++ks)
+                for (int part = 0; part < 2; ++part) {
+                  const uint32_t A = tileA + part * kTileB;
+                  const uint32_t accL = ((initL >> slotL) & 1u) | (uint32_t)(ks | part);
+                  mma_bf16_ss(dL, make_desc(A + ks * 2 * kS4, kS4, kS1), make_desc(bL + ks * 2 * kS1, kS1, kS4),
+                              idL, accL);
+                  const uint32_t accR = ((initR >> slotR) & 1u) | (uint32_t)(ks | part);
+                  mma_bf16_ss(dR, make_desc(A + ks * 2 * kS1, kS1, kS4), make_desc(bR + ks * 2 * kS1, kS1, kS4),
+                              idR, accR);
+                }
+              initL |= 1u << slotL;
+              initR |= 1u << slotR;
+              mma_commit(bar(EMPTY_A + st));
+            }
+            if (ok) mma_commit(bar(EMPTY_B + buf));
+          }
+        if (ok) mma_commit(bar(TM_FULL));
+      }
+      // drain this thread's MMAs before the tensor memory is freed
+      mma_commit(bar(DRAIN));
+      const long long t0 = clock64();
+      while (!mbar_try(bar(DRAIN), 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    const int lrow = warp * 32 + lane;  // TMEM lane = row within a 128 half
+    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+    const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
+    uint32_t tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
+      const TileInfo ti = tile_info(g, t);
+      if (!mbar_wait(bar(TM_FULL), tl & 1, abort_flag, g.status)) break;
+      tc_fence_after();
+      // column sketches: slot (a, h1), row i1 = h1*128 + lrow
+      for (int h1 = 0; h1 < g.H1; ++h1) {
+        const int64_t i1 = h1 * 128 + lrow;
+        double acc1[32];
+        for (int j = 0; j < g.NL; ++j) acc1[j] = 0.0;
+        for (int a = 0; a < ti.nA; ++a) {
+          const int64_t kL = ti.kL0 + a;
+          float v[32];
+          const uint32_t c0 = tmem + lane_addr + (uint32_t)((a * g.H1 + h1) * g.NL);
+          for (int c = 0; c < g.NL; c += 16) tmem_ld16(c0 + c, v + c);
+          for (int s = 0; s < g.nL; ++s) {
+            const SkTc sk = g.col[s];
+            if (sk.wdiv == 1) {
+              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += (double)v[s * ell + j];
+            } else {
+              const int64_t row = i1 + g.n1 * (kL % sk.wdiv);
+              for (int j = 0; j < ell; ++j) atomicAdd(g.ws + sk.off + row + sk.rows * j, (double)v[s * ell + j]);
+            }
+          }
+        }
+        for (int s = 0; s < g.nL; ++s)
+          if (g.col[s].wdiv == 1)
+            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.col[s].off + i1 + g.col[s].rows * j, acc1[s * ell + j]);
+      }
+      // row sketches: slot (b, h4), last-mode index bglob = first + h4*128 + lrow
+      for (int h4 = 0; h4 < g.H4; ++h4) {
+        const int64_t bg = g.first + h4 * 128 + lrow;
+        double acc1[32];
+        for (int j = 0; j < g.NR; ++j) acc1[j] = 0.0;
+        for (int b = 0; b < ti.nB; ++b) {
+          const int64_t kR = ti.kR0 + b;
+          float v[32];
+          const uint32_t c0 = tmem + lane_addr + colR0 + (uint32_t)((b * g.H4 + h4) * g.NR);
+          for (int c = 0; c < g.NR; c += 16) tmem_ld16(c0 + c, v + c);
+          for (int s = 0; s < g.nR; ++s) {
+            const SkTc sk = g.row[s];
+            if (sk.wdiv == g.W) {
+              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += (double)v[s * ell + j];
+            } else {
+              const int64_t whi = kR / (sk.wdiv / g.WL);
+              const int64_t row = whi + sk.hstride * bg;
+              for (int j = 0; j < ell; ++j) atomicAdd(g.ws + sk.off + row + sk.rows * j, (double)v[s * ell + j]);
+            }
+          }
+        }
+        for (int s = 0; s < g.nR; ++s)
+          if (g.row[s].wdiv == g.W)
+            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.row[s].off + bg * g.row[s].hstride + g.row[s].rows * j,
+                                                    acc1[s * ell + j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(TM_EMPTY));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)g.tmem_cols));
+  }
+}
+
+// Shape rules of the plane kernel; fills the launch arguments when it applies.
+bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
+  const DevItem& it = plan_items_host(&P)[item];
+  if (it.prec != TT_PREC_BF16 || it.x_f64) return false;
+  if (it.d != 3 && it.d != 4) return false;
+  if (it.n[0] != 128 && it.n[0] != 256) return false;
+  if (count != 128 && count != 256) return false;
+  const DevSketch* sks = plan_sketches_host(&P);
+  TcArgs g;
+  memset(&g, 0, sizeof(g));
+  const int ell = sks[it.sk0].width;
+  int nL = 0, nR = 0;
+  for (int s = 0; s < it.nsk; ++s) {
+    const DevSketch& d = sks[it.sk0 + s];
+    if (d.width != ell) return false;
+    SkTc t{d.rows, d.off, d.wdiv, d.hstride, d.stream_id, 0};
+    if (d.type == SK_COL) {
+      if (nL >= 4) return false;
+      g.col[nL++] = t;
+    } else {
+      if (nR >= 4) return false;
+      g.row[nR++] = t;
+    }
+  }
+  if (ell % 4 != 0) return false;
+  const int NL = nL * ell, NR = nR * ell;
+  if (NL < 16 || NR < 16 || NL > 32 || NR > 32 || NL % 16 || NR % 16) return false;
+  g.n1 = it.n[0];
+  g.W = it.W;
+  g.WL = it.N[it.ds] / it.n[0];
+  g.WR = g.W / g.WL;
+  g.Nd1 = it.N[it.d - 1];
+  g.H1 = (int)(it.n[0] / 128);
+  g.H4 = (int)(count / 128);
+  // tile: T2 x T3 planes, all slots resident in 512 TMEM columns
+  int T2 = (int)std::min<int64_t>(g.WL, 4), T3 = (int)std::min<int64_t>(g.WR, 4);
+  auto cols = [&](int a, int b) { return a * g.H1 * NL + b * g.H4 * NR; };
+  while (cols(T2, T3) > 512 && (T2 > 1 || T3 > 1)) {
+    if (T2 >= T3 && T2 > 1) --T2;
+    else --T3;
+  }
+  while (T2 < g.WL && T2 < 16 && cols(T2 + 1, T3) <= 512) ++T2;
+  while (T3 < g.WR && T3 < 16 && cols(T2, T3 + 1) <= 512) ++T3;
+  if (cols(T2, T3) > 512) return false;
+  g.T2 = T2;
+  g.T3 = T3;
+  int tc = 32;
+  while (tc < cols(T2, T3)) tc <<= 1;
+  g.tmem_cols = tc;
+  g.tilesL = (g.WL + T2 - 1) / T2;
+  g.tilesR = (g.WR + T3 - 1) / T3;
+  g.ell = ell;
+  g.nL = nL;
+  g.nR = nR;
+  g.NL = NL;
+  g.NR = NR;
+  g.seed = it.seed;
+  *out = g;
+  return true;
+}
+
+}  // namespace tc
 
 bool mixed_tc_supported(const Plan& P, int item, int64_t) {
   const DevItem& it = plan_items_host(&P)[item];
@@ -315,8 +824,43 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   return cudaGetLastError();
 }
 
+cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                             cudaStream_t st) {
+  tc::TcArgs g;
+  if (!tc::plan_tc(P, item, count, &g)) return cudaErrorNotSupported;
+  g.X = (const float*)X;
+  g.ws = (double*)ws;
+  g.status = reinterpret_cast<int*>((char*)ws + kStatusOff);
+  g.first = first;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc::sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t ntiles = g.tilesL * g.tilesR;
+  const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
+  count_launch();
+  tc::sketch_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
+  return cudaGetLastError();
+}
+
+// Which mixed kernel a launch uses: the tcgen05 plane kernel when its shape
+// rules hold (TT_SKETCH_KERNEL=mma forces the generic one, for comparisons).
+bool use_tc_kernel(const Plan& P, int item, int64_t count) {
+  static int force = -1;
+  if (force < 0) {
+    const char* e = getenv("TT_SKETCH_KERNEL");
+    force = (e && strcmp(e, "mma") == 0) ? 1 : 0;
+  }
+  tc::TcArgs g;
+  return force == 0 && tc::plan_tc(P, item, count, &g);
+}
+
 cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t first, int64_t count,
                                 void* ws, cudaStream_t st) {
+  if (use_tc_kernel(P, item, count)) return launch_sketch_tc(P, item, X, first, count, ws, st);
   return launch_sketch_mma(P, item, X, first, count, ws, st);
 }
 

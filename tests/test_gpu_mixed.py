@@ -106,3 +106,61 @@ def test_mixed_streaming_equals_one_shot():
         t.accumulate(X[first * Nd1:(first + cnt) * Nd1].clone(), first, cnt)
     t.finalize()
     assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-9
+
+
+# ----------------------------------------------------------- tcgen05 kernel
+@pytest.mark.parametrize("dims,kw", [
+    ([128, 5, 6, 128], dict(ranks=[1, 4, 4, 4, 1], p=4)),            # ragged tiles (5 x 6 planes), l = 8
+    ([256, 3, 4, 256], dict(eps=1e-6, rmax=6, p=10)),               # two halves per side, l = 16
+    ([256, 7, 128], dict(ranks=[1, 4, 4, 1], p=12)),                # d = 3
+])
+def test_tcgen05_sketches_match_oracle(dims, kw):
+    x = ti.random_tt(dims, [1] + [3] * (len(dims) - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", **kw)
+    assert t.kernel_kind() == 2
+    t.begin()
+    t.accumulate(to_dev(x), 0, dims[-1])
+    sk = sketch_dict(t)
+    t.finalize()
+    st, ranks = t.status()
+    assert st in (0, N.TT_WARN_RANK_CAP)
+    xs = _split(x.astype(np.float64), "bf16")
+    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt="bf16", **kw)
+    for k, S in o["sketch"]["S"].items():
+        G = sk[(0, k)]
+        err = np.max(np.abs(G - S)) / np.max(np.abs(S))
+        assert err <= 2e-5, ("S", k, err)
+    for k, R in o["sketch"]["R"].items():
+        G = sk[(1, k)]
+        err = np.max(np.abs(G - R)) / np.max(np.abs(R))
+        assert err <= 2e-5, ("R", k, err)
+
+
+def test_tcgen05_slab_groups_equal_one_shot():
+    dims = [128, 3, 2, 256]
+    x = ti.random_tt(dims, [1, 3, 3, 2, 1], seed=8, noise=1e-5).astype(np.float32)
+    X = to_dev(x)
+    one = TTSketch(dims, ranks=[1, 3, 3, 2, 1], p=5, seed=3, prec="bf16")
+    assert one.kernel_kind(256) == 2 and one.kernel_kind(128) == 2 and one.kernel_kind(16) == 1
+    one.pstt2(X)
+    t = TTSketch(dims, ranks=[1, 3, 3, 2, 1], p=5, seed=3, prec="bf16")
+    Nd1 = 128 * 3 * 2
+    t.begin()
+    t.accumulate(X[128 * Nd1:].clone(), 128, 128)
+    t.accumulate(X[:128 * Nd1].clone(), 0, 128)
+    t.finalize()
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-9
+
+
+def test_tcgen05_hilbert_within_10eps():
+    dims = [256, 8, 8, 256]
+    x = ti.hilbert_type(dims, np.float32)
+    t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="bf16")
+    assert t.kernel_kind() == 2
+    t.pstt2(to_dev(x))
+    f = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="fp64").pstt2(to_dev(x))
+    x64 = x.astype(np.float64)
+    e_x = rel(t.reconstruct().cpu().numpy(), x64, x64)
+    e_f = rel(t.reconstruct().cpu().numpy(), f.reconstruct().cpu().numpy(), x64)
+    print(f"tcgen05 hilbert: |X~-X|={e_x:.2e} |X~-X~fp64|={e_f:.2e} ranks={t.status()[1]}")
+    assert e_x <= 1e-5 and e_f <= 1e-5
