@@ -88,7 +88,12 @@ typedef struct {
   int passes;                /* 1 = PSTT2-onepass (hot path); 2 = PSTT2          */
   tt_dtype x_dtype;          /* storage type of X                                */
   tt_prec prec;              /* arithmetic of the sketch                         */
+  int flags;                 /* TT_FLAG_* bits                                   */
 } tt_problem;
+
+/* Reserve the workspace that tt_reconstruct_backward needs (all left and
+ * right interfaces of the train, about 2 r prod(n) / n bytes x 8). */
+#define TT_FLAG_DIFF 1
 
 /* ---------------------------------------------------------------- plans */
 
@@ -189,7 +194,9 @@ tt_status tt_reconstruct_error(tt_plan_t plan, const double* cores, const void* 
                                void* ws, tt_stream_t stream);
 
 /* Adjoint of tt_reconstruct: dcores (device, padded layout, overwritten) from
- * dL/dX~ (device, dtype). */
+ * dL/dX~ (device, dtype), for the cores `cores` (device).  Every padded entry
+ * gets its gradient too (the padded cores are a valid TT).  Needs a plan made
+ * with TT_FLAG_DIFF (else TT_ERR_STATE). */
 tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const void* dXt,
                                   tt_dtype dtype, double* dcores, void* ws, tt_stream_t stream);
 

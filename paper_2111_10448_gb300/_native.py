@@ -17,6 +17,7 @@ TT_OK, TT_ERR_INVALID_ARG, TT_ERR_UNSUPPORTED, TT_ERR_CUDA, TT_ERR_STATE, \
     TT_ERR_RANK_DEFICIENT, TT_ERR_TIMEOUT, TT_WARN_RANK_CAP, TT_ERR_NO_DEVICE = range(9)
 TT_F32, TT_F64 = 0, 1
 TT_PREC_FP64, TT_PREC_TF32, TT_PREC_BF16 = 0, 1, 2
+TT_FLAG_DIFF = 1
 
 STATUS_NAMES = {
     0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_UNSUPPORTED", 3: "TT_ERR_CUDA",
@@ -37,6 +38,7 @@ class tt_problem(C.Structure):
         ("passes", C.c_int),
         ("x_dtype", C.c_int),
         ("prec", C.c_int),
+        ("flags", C.c_int),
     ]
 
 
@@ -106,7 +108,7 @@ def check(status, where):
 
 
 def make_problem(dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
-                 x_dtype=TT_F32, prec=TT_PREC_FP64):
+                 x_dtype=TT_F32, prec=TT_PREC_FP64, flags=0):
     q = tt_problem()
     q.d = len(dims)
     if q.d > TT_MAXD:
@@ -123,4 +125,5 @@ def make_problem(dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
     q.passes = int(passes)
     q.x_dtype = int(x_dtype)
     q.prec = int(prec)
+    q.flags = int(flags)
     return q

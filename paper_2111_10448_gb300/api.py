@@ -30,7 +30,7 @@ class TTSketch:
     PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
 
     def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
-                 x_dtype=torch.float32, prec="fp64", device="cuda", batch=None):
+                 x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False):
         L = N.lib()
         self.device = torch.device(device)
         if batch is None:
@@ -42,7 +42,8 @@ class TTSketch:
             arr[i] = N.make_problem(pr["dims"], ranks=pr.get("ranks"), eps=pr.get("eps", eps),
                                     rmax=pr.get("rmax", rmax), p=pr.get("p", p),
                                     seed=pr.get("seed", seed), passes=passes,
-                                    x_dtype=_DT[x_dtype], prec=self.PRECS[prec])
+                                    x_dtype=_DT[x_dtype], prec=self.PRECS[prec],
+                                    flags=N.TT_FLAG_DIFF if diff else 0)
         h = C.c_void_p()
         if batch is None:
             N.check(L.tt_sketch_plan(C.byref(arr[0]), C.byref(h)), "tt_sketch_plan")
@@ -124,10 +125,10 @@ class TTSketch:
                 "tt_reconstruct_error")
         return out2
 
-    def reconstruct_backward(self, dXt, stream=None):
+    def reconstruct_backward(self, dXt, cores=None, stream=None):
         dc = torch.empty_like(self.cores)
-        N.check(N.lib().tt_reconstruct_backward(self.plan, _ptr(self.cores), _ptr(dXt), _DT[dXt.dtype],
-                                                _ptr(dc), _ptr(self.ws), _stream(stream)),
+        N.check(N.lib().tt_reconstruct_backward(self.plan, _ptr(self.cores if cores is None else cores), _ptr(dXt),
+                                                _DT[dXt.dtype], _ptr(dc), _ptr(self.ws), _stream(stream)),
                 "tt_reconstruct_backward")
         return dc
 
@@ -176,6 +177,40 @@ class TTSketch:
             G = host[it["core_off"][k]:it["core_off"][k] + rp0 * n * rp1].reshape((rp0, n, rp1), order="F")
             out.append(np.ascontiguousarray(G[:r[k - 1], :, :r[k]]))
         return out
+
+
+class PSTT2Fn(torch.autograd.Function):
+    """X -> padded TT cores (one-pass PSTT2) with the hand-written adjoint
+    (tt_pstt2_backward): pivots and ranks are frozen at this forward call."""
+
+    @staticmethod
+    def forward(ctx, X, sk):
+        sk.pstt2(X.detach().contiguous())
+        ctx.sk = sk
+        ctx.xshape = X.shape
+        return sk.cores.clone()
+
+    @staticmethod
+    def backward(ctx, dcores):
+        sk = ctx.sk
+        dX = torch.empty(ctx.xshape, dtype=sk.x_dtype, device=sk.device)
+        sk.backward(dcores.contiguous(), dX)
+        return dX, None
+
+
+class TTReconstructFn(torch.autograd.Function):
+    """padded TT cores -> dense X~ with its adjoint (tt_reconstruct_backward)."""
+
+    @staticmethod
+    def forward(ctx, cores, sk, dtype):
+        ctx.sk = sk
+        ctx.save_for_backward(cores)
+        return sk.reconstruct(dtype, cores=cores.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, dXt):
+        (cores,) = ctx.saved_tensors
+        return ctx.sk.reconstruct_backward(dXt.contiguous(), cores=cores.contiguous()), None, None
 
 
 def pstt2(X, dims, **kw):

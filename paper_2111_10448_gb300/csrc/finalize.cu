@@ -313,6 +313,12 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, 
     rk[s.k] = r;
     if (s.k == 1) rk[0] = 1;
     if (s.k == it.d - 1) rk[it.d] = 1;
+    if (it.rank_off == 0) {  // copy for the backward of a single-item plan
+      int* cp = reinterpret_cast<int*>(wsb + kRankCopyOff);
+      cp[s.k] = r;
+      if (s.k == 1) cp[0] = 1;
+      if (s.k == it.d - 1) cp[it.d] = 1;
+    }
   }
   __syncthreads();
   const int r = s_rank;

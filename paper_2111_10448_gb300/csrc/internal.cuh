@@ -85,6 +85,11 @@ struct DevItem {
   int64_t off_hbar;         // adjoint of H
   int64_t off_bbar;         // adjoint of B
   int64_t off_rr[TT_MAXD + 1];    // leading r x r block of the basis R factor (rpad x rpad)
+  int64_t off_small;        // 4 x TT_MAXL^2 doubles of backward scratch (single-item plans)
+  int diff;                 // TT_FLAG_DIFF: full interface chain reserved
+  int64_t off_Lall[TT_MAXD + 1];  // left interfaces L_k, k = 1..d-1 (N_k x rpad_k)
+  int64_t off_Rall[TT_MAXD + 2];  // right interfaces Rt_k, k = 2..d (rpad_{k-1} x M_{k-1})
+  int64_t off_Y;            // max_k N_k x rpad_k
   const void* X;            // batched: device pointer of this item's tensor (set per call)
 };
 
@@ -101,8 +106,10 @@ struct DevTables {
   int ntasks[kMaxLev];
 };
 
-// Byte offset of the status word inside the workspace.
+// Byte offset of the status word inside the workspace, and of a copy of the
+// ranks of item 0 (d+1 ints) that the backward reads.
 constexpr int64_t kStatusOff = 0;
+constexpr int64_t kRankCopyOff = 64;
 
 // ---------------------------------------------------------------- host side
 struct Plan;

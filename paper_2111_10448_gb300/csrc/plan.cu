@@ -84,7 +84,7 @@ static tt_status validate(const tt_problem& q) {
 
 // Build the item (tables + workspace layout) of one problem.
 static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t& core_top,
-                            int& rank_top) {
+                            int& rank_top, bool single) {
   tt_problem q = q0;
   DevItem it;
   std::memset(&it, 0, sizeof(it));
@@ -212,6 +212,15 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.off_hbar = ws.take(it.N[ds] * it.rpad[ds]);
     it.off_bbar = ws.take((int64_t)it.rpad[ds] * it.lmid);
   }
+  if (single) it.off_small = ws.take(4LL * TT_MAXL * TT_MAXL);
+  it.diff = (q.flags & TT_FLAG_DIFF) ? 1 : 0;
+  if (it.diff) {
+    int64_t ymax = 1;
+    for (int k = 1; k < d; ++k) it.off_Lall[k] = ws.take(it.N[k] * it.rpad[k]);
+    for (int k = 2; k <= d; ++k) it.off_Rall[k] = ws.take((int64_t)it.rpad[k - 1] * (it.N[d] / it.N[k - 1]));
+    for (int k = 1; k <= d; ++k) ymax = std::max<int64_t>(ymax, it.N[k] * it.rpad[k]);
+    it.off_Y = ws.take(ymax);
+  }
   P.items.push_back(it);
   return TT_OK;
 }
@@ -254,7 +263,7 @@ static tt_status build_all(Plan& P, const tt_problem* probs, int count, int64_t 
   int rank_top = 0;
   for (int i = 0; i < count; ++i) {
     tt_status st = validate(probs[i]);
-    if (st == TT_OK) st = build_item(P, probs[i], ws, core_top, rank_top);
+    if (st == TT_OK) st = build_item(P, probs[i], ws, core_top, rank_top, count == 1);
     if (st != TT_OK) return st;
   }
   build_blob(P);
@@ -545,6 +554,7 @@ tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const voi
   Plan* P = as_plan(plan);
   if (!P || !cores || !dXt || !dcores || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  if (!P->items[0].diff) return TT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
   tt_status s = ensure_uploaded(*P, ws, st);
   if (s != TT_OK) return s;

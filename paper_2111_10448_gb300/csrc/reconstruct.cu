@@ -104,6 +104,57 @@ __global__ void __launch_bounds__(kThreads) dense_kernel(const double* L, const 
   }
 }
 
+// Y(row, c) += sum_{v in chunk} dX(row + Nk v) Rt(c, v)   (Rt: rp x Mk, ld rp)
+__global__ void __launch_bounds__(kThreads) ygram_kernel(const void* dX, int dx_f64, int64_t Nk, int64_t Mk,
+                                                         const double* Rt, int rp, double* Y) {
+  constexpr int VC = 64;
+  __shared__ double Rs[VC * TT_MAXL];
+  const int64_t nrb = (Nk + kThreads - 1) / kThreads;
+  const int64_t nvc = (Mk + VC - 1) / VC;
+  for (int64_t job = blockIdx.x; job < nrb * nvc; job += gridDim.x) {
+    const int64_t rb = job % nrb, vc = job / nrb;
+    const int64_t v0 = vc * VC;
+    const int nv = (int)imin64(VC, Mk - v0);
+    __syncthreads();
+    for (int o = threadIdx.x; o < nv * rp; o += blockDim.x) {
+      const int v = o / rp, c = o % rp;
+      Rs[v * TT_MAXL + c] = Rt ? Rt[c + (int64_t)rp * (v0 + v)] : 1.0;
+    }
+    __syncthreads();
+    const int64_t row = rb * kThreads + threadIdx.x;
+    if (row < Nk) {
+      double acc[TT_MAXL];
+      for (int c = 0; c < rp; ++c) acc[c] = 0.0;
+      for (int v = 0; v < nv; ++v) {
+        const int64_t idx = row + Nk * (v0 + v);
+        const double x = dx_f64 ? ((const double*)dX)[idx] : (double)((const float*)dX)[idx];
+        for (int c = 0; c < rp; ++c) acc[c] += x * Rs[v * TT_MAXL + c];
+      }
+      for (int c = 0; c < rp; ++c) atomicAdd(Y + row + Nk * c, acc[c]);
+    }
+  }
+}
+
+// dG_k(a, i, c) = sum_u L_{k-1}(u, a) Y_k(u + N_{k-1} i, c);  L_0 = [1].
+__global__ void dcore_kernel(const double* Lp, int64_t Np, int rpa, const double* Y, int64_t nk, int rpc,
+                             double* dG) {
+  const int64_t total = (int64_t)rpa * nk * rpc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % rpa);
+    const int64_t i = (e / rpa) % nk;
+    const int c = (int)(e / (rpa * nk));
+    const int64_t Nk = Np * nk;
+    double acc = 0.0;
+    if (Lp == nullptr) {
+      acc = Y[i + Nk * c];
+    } else {
+      for (int64_t u = 0; u < Np; ++u) acc += Lp[u + Np * a] * Y[u + Np * i + Nk * c];
+    }
+    dG[e] = acc;
+  }
+}
+
 int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, 16LL * device_sm_count()));
 }
@@ -149,6 +200,45 @@ cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, voi
   count_launch();
   dense_kernel<<<grid_for(Nm * Mm), kThreads, 0, st>>>(W + it.off_L[ds], W + it.off_Rt[ds + 1], Nm, Mm,
                                                        it.rpad[ds], Xt, x_f64, Xcmp, cmp_f64, out2);
+  return cudaGetLastError();
+}
+
+// Adjoint of the reconstruction: for every core k,
+//   dG_k(a, i, c) = sum_{u, v} L_{k-1}(u, a) dX(u + N_{k-1} i + N_k v) Rt_{k+1}(c, v)
+// with the left / right interfaces of the train (all of them: TT_FLAG_DIFF).
+cudaError_t launch_reconstruct_backward(const Plan& P, int item, const double* cores, const void* dXt,
+                                        int dx_f64, double* dcores, void* ws, cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[item];
+  double* W = (double*)ws;
+  const int d = it.d;
+  for (int k = 1; k < d; ++k) {
+    const double* Lp = k == 1 ? nullptr : W + it.off_Lall[k - 1];
+    count_launch();
+    iface_left_kernel<<<grid_for(it.N[k] * it.rpad[k]), kThreads, 0, st>>>(
+        Lp, it.N[k - 1], it.rpad[k - 1], cores + it.core_off[k], it.n[k - 1], it.rpad[k], W + it.off_Lall[k]);
+  }
+  for (int k = d; k >= 2; --k) {
+    const double* Rn = k == d ? nullptr : W + it.off_Rall[k + 1];
+    const int64_t Mn = it.N[d] / it.N[k];
+    count_launch();
+    iface_right_kernel<<<grid_for((int64_t)it.rpad[k - 1] * it.n[k - 1] * Mn), kThreads, 0, st>>>(
+        Rn, Mn, it.rpad[k], cores + it.core_off[k], it.n[k - 1], it.rpad[k - 1], W + it.off_Rall[k]);
+  }
+  for (int k = 1; k <= d; ++k) {
+    const int64_t Nk = it.N[k], Mk = it.N[d] / it.N[k];
+    const int rpk = it.rpad[k];
+    cudaError_t e = cudaMemsetAsync(W + it.off_Y, 0, sizeof(double) * Nk * rpk, st);
+    if (e != cudaSuccess) return e;
+    const int64_t jobs = ((Nk + kThreads - 1) / kThreads) * ((Mk + 63) / 64);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(jobs, 16LL * device_sm_count()));
+    count_launch();
+    ygram_kernel<<<g, kThreads, 0, st>>>(dXt, dx_f64, Nk, Mk, k == d ? nullptr : W + it.off_Rall[k + 1], rpk,
+                                         W + it.off_Y);
+    count_launch();
+    dcore_kernel<<<grid_for((int64_t)it.rpad[k - 1] * it.n[k - 1] * rpk), kThreads, 0, st>>>(
+        k == 1 ? nullptr : W + it.off_Lall[k - 1], it.N[k - 1], it.rpad[k - 1], W + it.off_Y, it.n[k - 1], rpk,
+        dcores + it.core_off[k]);
+  }
   return cudaGetLastError();
 }
 

@@ -784,6 +784,144 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
 
 }  // namespace tc
 
+// ----------------------------------------------------------------------------
+// Backward kernels that regenerate test matrices (same generator and rounding
+// as the forward sketch of the item's precision).
+namespace {
+
+__device__ __forceinline__ void test_row(int prec, uint64_t seed, int sid, uint64_t row, int l, double* out) {
+  for (int q = 0; q < (l + 3) / 4; ++q) {
+    double z[4];
+    if (prec == TT_PREC_FP64) {
+      normals4_f64(seed, (uint32_t)sid, row, (uint32_t)q, z);
+    } else {
+      const float4 f = normals4_f32(seed, (uint32_t)sid, row, (uint32_t)q);
+      z[0] = round_prec(f.x, prec);
+      z[1] = round_prec(f.y, prec);
+      z[2] = round_prec(f.z, prec);
+      z[3] = round_prec(f.w, prec);
+    }
+    for (int t = 0; t < 4; ++t)
+      if (4 * q + t < l) out[4 * q + t] = z[t];
+  }
+}
+
+// Pbar_{d*}(v, c) += sum_j Omega_{d*}(v, j) Bbar(c, j)
+__global__ void pbar_ls_kernel(char* wsb, int item, const int* ranks) {
+  __shared__ double Bb[TT_MAXL * TT_MAXL];
+  const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + 256);
+  const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
+  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.ds]];
+  double* ws = reinterpret_cast<double*>(wsb);
+  const int r = ranks[it.rank_off + it.ds];
+  const int rp = it.rpad[it.ds];
+  const int l = it.lmid;
+  for (int o = threadIdx.x; o < rp * l; o += blockDim.x) Bb[o] = ws[it.off_bbar + o];
+  __syncthreads();
+  double* Pb = ws + it.off_qbar[it.ds];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < sp.rows; v += (int64_t)gridDim.x * blockDim.x) {
+    double om[TT_MAXL];
+    test_row(it.prec, it.seed, it.ds, (uint64_t)v, l, om);
+    for (int c = 0; c < r; ++c) {
+      double acc = 0.0;
+      for (int j = 0; j < l; ++j) acc += om[j] * Bb[c + rp * j];
+      Pb[v + sp.rows * c] += acc;
+    }
+  }
+}
+
+// dX(a, w, b) = sum_col sum_j Sbar_k[a + n1 wlo, j] Omega_k[whi + hs b, j]
+//             + sum_row sum_j Psi_k[a + n1 wlo, j] Rbar_k[whi + hs b, j]
+// (one tile of 64 x 32 entries of one plane per iteration; written once).
+__global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item, void* dX) {
+  constexpr int TA = 64, TB = 32, LD = TT_MAXL + 1;
+  __shared__ double Lf[TA * LD];
+  __shared__ double Rf[TB * LD];
+  const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + 256);
+  const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
+  const DevSketch* S = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
+  const double* ws = reinterpret_cast<const double*>(wsb);
+  const int64_t n1 = it.n[0], nd = it.n[it.d - 1], W = it.W, Nd1 = it.N[it.d - 1];
+  const int64_t nA = (n1 + TA - 1) / TA, nB = (nd + TB - 1) / TB;
+  const int64_t total = W * nA * nB;
+  const int tid = threadIdx.x;
+  const int ia = tid % TA, ib0 = tid / TA;  // rows ia, columns ib0 + 4 m
+  for (int64_t job = blockIdx.x; job < total; job += gridDim.x) {
+    const int64_t w = job / (nA * nB);
+    const int64_t rem = job - w * nA * nB;
+    const int64_t bb = rem / nA, ab = rem - bb * nA;
+    const int64_t a0 = ab * TA, b0 = bb * TB;
+    const int ta = (int)imin64(TA, n1 - a0), tb = (int)imin64(TB, nd - b0);
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < it.nsk; ++s) {
+      const DevSketch& sk = S[it.sk0 + s];
+      const int l = sk.width;
+      const int64_t wlo = w % sk.wdiv, whi = w / sk.wdiv;
+      const double* bar = ws + it.off_sbar[s];
+      __syncthreads();
+      if (sk.type == SK_COL) {
+        for (int o = tid; o < ta * l; o += blockDim.x) {
+          const int a = o % ta, j = o / ta;
+          Lf[a * LD + j] = bar[(a0 + a + n1 * wlo) + sk.rows * j];
+        }
+        for (int b = tid; b < tb; b += blockDim.x)
+          test_row(it.prec, it.seed, sk.stream_id, (uint64_t)(whi + sk.hstride * (b0 + b)), l, Rf + b * LD);
+      } else {
+        for (int a = tid; a < ta; a += blockDim.x)
+          test_row(it.prec, it.seed, sk.stream_id, (uint64_t)((a0 + a) + n1 * wlo), l, Lf + a * LD);
+        for (int o = tid; o < tb * l; o += blockDim.x) {
+          const int b = o % tb, j = o / tb;
+          Rf[b * LD + j] = bar[(whi + sk.hstride * (b0 + b)) + sk.rows * j];
+        }
+      }
+      __syncthreads();
+      if (ia < ta) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int b = ib0 + 4 * m;
+          if (b < tb) {
+            double v = 0.0;
+            for (int j = 0; j < l; ++j) v += Lf[ia * LD + j] * Rf[b * LD + j];
+            acc[m] += v;
+          }
+        }
+      }
+    }
+    if (ia < ta) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int b = ib0 + 4 * m;
+        if (b < tb) {
+          const int64_t idx = (a0 + ia) + n1 * w + Nd1 * (b0 + b);
+          if (it.x_f64) ((double*)dX)[idx] = acc[m];
+          else ((float*)dX)[idx] = (float)acc[m];
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pbar_ls(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[item];
+  const int64_t M = plan_sketches_host(&P)[it.basis_of_k[it.ds]].rows;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((M + 127) / 128, 8LL * device_sm_count()));
+  count_launch();
+  pbar_ls_kernel<<<grid, 128, 0, st>>>((char*)ws, item, ranks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_adjoint(const Plan& P, int item, void* dX, void* ws, cudaStream_t st) {
+  const DevItem& it = plan_items_host(&P)[item];
+  const int64_t nA = (it.n[0] + 63) / 64, nB = (it.n[it.d - 1] + 31) / 32;
+  const int64_t total = it.W * nA * nB;
+  const int grid = (int)std::min<int64_t>(total, 8LL * device_sm_count());
+  count_launch();
+  sketch_adjoint_kernel<<<grid, 256, 0, st>>>((char*)ws, item, dX);
+  return cudaGetLastError();
+}
+
 bool mixed_tc_supported(const Plan& P, int item, int64_t) {
   const DevItem& it = plan_items_host(&P)[item];
   return it.prec == TT_PREC_TF32 || it.prec == TT_PREC_BF16;
