@@ -17,10 +17,12 @@ namespace tts {
 __device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q) {
   uint32_t c0 = (uint32_t)row, c1 = (uint32_t)(row >> 32), c2 = q, c3 = sid;
   philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-  const float u0 = __fmul_rn((float)((c0 >> 9) * 2u + 1u), 0x1p-24f);
-  const float u1 = __fmul_rn((float)((c1 >> 9) * 2u + 1u), 0x1p-24f);
-  const float u2 = __fmul_rn((float)((c2 >> 9) * 2u + 1u), 0x1p-24f);
-  const float u3 = __fmul_rn((float)((c3 >> 9) * 2u + 1u), 0x1p-24f);
+  // u = (x + 1/2) 2^-32 in FP32: x is rounded to 24 bits (relative error
+  // 2^-24 at any magnitude), then scaled exactly and offset by 2^-33.
+  const float u0 = __fmaf_rn(__uint2float_rn(c0), 0x1p-32f, 0x1p-33f);
+  const float u1 = __fmaf_rn(__uint2float_rn(c1), 0x1p-32f, 0x1p-33f);
+  const float u2 = __fmaf_rn(__uint2float_rn(c2), 0x1p-32f, 0x1p-33f);
+  const float u3 = __fmaf_rn(__uint2float_rn(c3), 0x1p-32f, 0x1p-33f);
   const float ra = __fsqrt_rn(__fmul_rn(-2.0f, logf(u0)));
   const float rb = __fsqrt_rn(__fmul_rn(-2.0f, logf(u2)));
   float sa, ca, sb, cb;

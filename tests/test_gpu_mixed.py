@@ -2,10 +2,10 @@
 
 Bars (derived from the arithmetic):
 * test-matrix entries: the FP32 generator differs from the FP64 definition by
-  about 1e-7 relative (and 1e-6 absolute near zero crossings of cos/sin), so
-  after rounding to the MMA type an entry equals the oracle's rounded FP64
-  normal except for rare flips to the neighbouring value (< 0.5% of entries,
-  at most one ulp or 4e-6 absolute);
+  about 1e-7 relative (at most ~1e-5 absolute, only where u is within 1e-5 of
+  1 so that |z| is tiny), so after rounding to the MMA type an entry equals
+  the oracle's rounded FP64 normal except for rare flips to the neighbouring
+  value (< 0.5% of entries, at most one ulp plus 2e-5 absolute);
 * sketches: equal to the oracle's FP64 product of the split X (hi + lo in the
   MMA type) with its rounded test matrix; the flips above change a sketch
   entry by about 2^-8 |x w| (BF16), which bounds the relative Frobenius
@@ -40,7 +40,7 @@ def test_test_matrix_mixed_matches_rounded_oracle(prec):
     got = out.cpu().numpy().reshape(ncols, nrows).T
     ref = philox.round_to(philox.gaussian(3, sid, np.arange(17, 17 + nrows, dtype=np.uint64), ncols), prec)
     diff = np.abs(got - ref)
-    assert np.all(diff <= ULP[prec] * np.abs(ref) * 1.0001 + 4e-6)
+    assert np.all(diff <= ULP[prec] * np.abs(ref) * 1.0001 + 2e-5)
     assert np.mean(diff > 0) < 5e-3
     assert np.array_equal(philox.round_to(got, prec), got)  # values are exact in the MMA type
 
