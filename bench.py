@@ -35,11 +35,14 @@ SLAB = 16  # last-mode slices per 1 GiB slab (256^3 * 4 B * 16 = 1 GiB)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32"])
     ap.add_argument("--n", type=int, default=256, help="mode size (default: the 17 GB workload)")
+    ap.add_argument("--mid", type=int, default=0,
+                    help="size of the two middle modes (default n); a smaller value keeps the kernel's "
+                         "tile shape on a smaller tensor (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -61,7 +64,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -194,17 +197,17 @@ def run_gpu(a):
         dist.init_process_group("nccl", device_id=dev)
     L = P.lib()
     n = a.n
-    dims = [n] * 4
-    ntot = n ** 4
-    Nd1 = n ** 3
+    m = a.mid or n
+    dims = [n, m, m, n]
+    ntot = n * m * m * n
+    Nd1 = n * m * m
     stream = torch.cuda.Stream(device=dev)
     sp = C.c_void_p(stream.cuda_stream)
 
     # X resident in HBM (generated on the device, not timed)
     X = torch.empty(ntot, dtype=torch.float32, device=dev)
     nn = (C.c_int64 * 4)(*dims)
-    with torch.cuda.stream(stream):
-        N.check(L.tt_generate_hilbert_type(4, nn, 0, n, C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
+    N.check(L.tt_generate_hilbert_type(4, nn, 0, n, C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
     stream.synchronize()
 
     kw = dict(eps=WORKLOAD["eps"], rmax=WORKLOAD["rmax"], p=WORKLOAD["p"], seed=WORKLOAD["seed"] + rank,
@@ -249,7 +252,9 @@ def run_gpu(a):
     st, ranks = t.status(stream)
 
     # accuracy of this run: ||X - X~|| / ||X|| on the device
-    err2 = t.error(X, stream).cpu().numpy()
+    err2 = t.error(X, stream)
+    stream.synchronize()
+    err2 = err2.cpu().numpy()
     rel_err = float((err2[0] / err2[1]) ** 0.5)
 
     out = {}
@@ -264,10 +269,12 @@ def run_gpu(a):
         g1.record(stream)
         torch.cuda.synchronize(dev)
         f_ms = g0.elapsed_time(g1)
-        fe = f.error(X, stream).cpu().numpy()
+        fe = f.error(X, stream)
         # mixed vs FP64: ||X~_mixed - X~_fp64|| / ||X||
         Xf = f.reconstruct(torch.float32, stream=stream)
-        d2 = t.error(Xf, stream).cpu().numpy()
+        d2 = t.error(Xf, stream)
+        stream.synchronize()
+        fe, d2 = fe.cpu().numpy(), d2.cpu().numpy()
         del Xf
         out["fp64_gpu"] = {"value": ntot / (f_ms * 1e-3), "unit": "entries/s", "ms_per_step": f_ms,
                            "rel_err_vs_X": float((fe[0] / fe[1]) ** 0.5),
@@ -319,7 +326,7 @@ def run_gpu(a):
     peak, peak_kind = measured_peaks()
     achieved = ntot * 4 / (sketch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_record(f"sketch_{a.prec}_n{n}"), "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": traffic_record(f"sketch_{a.prec}_{n}x{m}x{m}x{n}"), "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel_ms": sketch_ms, "algorithmic_bytes": ntot * 4}
 
     cpu = None
@@ -331,7 +338,7 @@ def run_gpu(a):
         line = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": a.prec, "data": "synthetic",
-                "config": {"workload": f"Hilbert-type d=4 n={n} FP32 ({ntot * 4 / 1e9:.2f} GB) one-pass PSTT2, "
+                "config": {"workload": f"Hilbert-type d=4 dims={dims} FP32 ({ntot * 4 / 1e9:.2f} GB) one-pass PSTT2, "
                                        f"eps=1e-6 p=10 rmax=6, {a.prec} tensor-core sketch with X split hi+lo, "
                                        "FP64 solves",
                            "l2": "inputs larger than L2 (no flush needed)",
