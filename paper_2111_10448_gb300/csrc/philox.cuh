@@ -15,9 +15,11 @@
 //   j % 4 = 0, 1 and likewise (x2, x3) for j % 4 = 2, 3.
 //   FP64 uniforms: u = (x + 1/2) 2^-32.
 //   FP32 (mixed precision): the same u evaluated in FP32 as
-//   fma(float(x), 2^-32, 2^-33) (relative error <= 2^-24), then logf,
-//   sqrtf and sincospif; the normal differs from the FP64 one by ~1e-7
-//   relative (at most ~1e-5 absolute, where u is within 1e-5 of 1).
+//   fma(float(x), 2^-32, 2^-33) (relative error <= 2^-24), rho from logf and
+//   sqrt, and the angle taken centred, theta - pi = 2 pi u - pi in (-pi, pi],
+//   through the fast sine/cosine (cos theta = -cos(theta - pi), likewise
+//   sin); the normal differs from the FP64 one by about 1e-7 relative and at
+//   most a few 1e-6 absolute.
 #pragma once
 #include <cstdint>
 
@@ -27,14 +29,12 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
                                               uint32_t& c3, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-    c0 = hi1 ^ c1 ^ k0;
-    c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
-    c3 = lo0;
+    const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;  // one 32x32 -> 64-bit multiply each
+    const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
+    c0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    c1 = (uint32_t)p1;
+    c2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c3 = (uint32_t)p0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -60,10 +60,11 @@ __device__ __forceinline__ void normals4_f64(uint64_t seed, uint32_t sid, uint64
   z[3] = rb * sb;
 }
 
-// FP32 generator of the mixed-precision sketches.  Kept out of line so that
-// every kernel that needs the same entry (the sketch, and the middle-core
-// solve that regenerates Omega_{d*}) runs one compiled body and gets
-// bit-identical values.
+// FP32 generator of the mixed-precision sketches: defined out of line in the
+// one translation unit that holds every kernel needing the same entries (the
+// sketch, the middle-core solve that regenerates Omega_{d*}, the backward),
+// so that all of them run one compiled body and get bit-identical values
+// (inlined copies may be contracted or scheduled differently).
 __device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q);
 
 // Round an FP32 value to the MMA input type, nearest-even, returned as FP32.

@@ -25,10 +25,13 @@ __device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_
   const float u3 = __fmaf_rn(__uint2float_rn(c3), 0x1p-32f, 0x1p-33f);
   const float ra = __fsqrt_rn(__fmul_rn(-2.0f, logf(u0)));
   const float rb = __fsqrt_rn(__fmul_rn(-2.0f, logf(u2)));
+  // centred angles 2 pi u - pi in (-pi, pi]: cos(2 pi u) = -cos(.), sin likewise
+  const float ta = __fmaf_rn(u1, 6.28318530717958647692f, -3.14159265358979323846f);
+  const float tb = __fmaf_rn(u3, 6.28318530717958647692f, -3.14159265358979323846f);
   float sa, ca, sb, cb;
-  sincospif(__fmul_rn(2.0f, u1), &sa, &ca);
-  sincospif(__fmul_rn(2.0f, u3), &sb, &cb);
-  return make_float4(__fmul_rn(ra, ca), __fmul_rn(ra, sa), __fmul_rn(rb, cb), __fmul_rn(rb, sb));
+  __sincosf(ta, &sa, &ca);
+  __sincosf(tb, &sb, &cb);
+  return make_float4(-__fmul_rn(ra, ca), -__fmul_rn(ra, sa), -__fmul_rn(rb, cb), -__fmul_rn(rb, sb));
 }
 
 namespace {
@@ -296,14 +299,17 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
 //
 // Accumulator slots: w = kL + WL kR with WL = N_{d*}/n_1.  All column-sketch
 // output rows depend on w only through kL, all row-sketch rows only through
-// kR.  A CTA tile is a block of T2 kL values x T3 kR values (16 planes); its
-// D_L slots (one per kL) and D_R slots (one per kR) live in tensor memory for
-// the whole tile and are flushed once, with FP64 atomics, by the epilogue
-// warps.
+// kR.  A tile is a block of T2 kL values x T3 kR values; tiles are numbered
+// kL-block-major and every CTA takes one contiguous run of them, so its tiles
+// share the kL block except at most once.  The D_L slots (one per kL) stay in
+// tensor memory for the whole run of a kL block and are flushed when the block
+// changes; the D_R slots (one per kR) are double-buffered and flushed after
+// every tile while the next tile is being computed.  Flushes add FP32 tensor-
+// memory values into the FP64 sketches with atomics.
 //
-// Warp roles (672 threads, one CTA per SM): warps 0-3 epilogue (TMEM lanes
+// Warp roles (640 threads, one CTA per SM): warps 0-3 epilogue (TMEM lanes
 // 0-127), warp 4 TMEM allocation + MMA issue (one thread), warps 5-12
-// producers (X -> BF16 hi/lo), warps 13-20 test-matrix generation.  Stages
+// producers (X -> BF16 hi/lo), warps 13-19 test-matrix generation.  Stages
 // are handed over with mbarriers; every wait is bounded (about 2 s), after
 // which the CTA raises the timeout status bit, stops, drains its MMAs and
 // frees its tensor memory.
@@ -317,9 +323,9 @@ constexpr int kStages = 2;
 constexpr int kBBlkB = 4 * kS4;          // one test-matrix block, N <= 32
 constexpr int kBBlks = 4;                // L[h4=0,1], R[h1=0,1] per plane
 constexpr int kBBufs = 2;
-constexpr int kWarps = 21;
+constexpr int kWarps = 20;
 constexpr int kThreads = kWarps * 32;
-constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 8;
+constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 7;
 constexpr int kOffB = kStages * kStageB;
 constexpr int kOffBar = kOffB + kBBufs * kBBlks * kBBlkB;
 constexpr int kSmemBytes = kOffBar + 256 + 1024;  // barriers + alignment slack
@@ -437,7 +443,7 @@ struct TileInfo {
 };
 __device__ __forceinline__ TileInfo tile_info(const TcArgs& g, int64_t t) {
   TileInfo ti;
-  const int64_t tl = t % g.tilesL, tr = t / g.tilesL;
+  const int64_t tl = t / g.tilesR, tr = t % g.tilesR;  // kL-block-major
   ti.kL0 = tl * g.T2;
   ti.kR0 = tr * g.T3;
   ti.nA = (int)imin64(g.T2, g.WL - ti.kL0);
@@ -450,9 +456,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
   // barrier indices
-  const int FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TM_FULL = 8, TM_EMPTY = 9, DRAIN = 10;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 128);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 136);
+  const int FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TML_FULL = 8, TML_EMPTY = 9, DRAIN = 10,
+            TMR_FULL = 11, TMR_EMPTY = 13;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
@@ -463,9 +470,13 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       mbar_init(bar(FULL_B + s), kRngWarps);
       mbar_init(bar(EMPTY_B + s), 1);
     }
-    mbar_init(bar(TM_FULL), 1);
-    mbar_init(bar(TM_EMPTY), kEpiWarps);
+    mbar_init(bar(TML_FULL), 1);
+    mbar_init(bar(TML_EMPTY), kEpiWarps);
     mbar_init(bar(DRAIN), 1);
+    for (int s2 = 0; s2 < 2; ++s2) {
+      mbar_init(bar(TMR_FULL + s2), 1);
+      mbar_init(bar(TMR_EMPTY + s2), kEpiWarps);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -478,7 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int64_t ntiles = g.tilesL * g.tilesR;
+  const int64_t ntiles_all = g.tilesL * g.tilesR;
+  // this CTA's contiguous run of tiles [t_beg, ntiles)
+  const int64_t t_beg = ntiles_all * blockIdx.x / gridDim.x;
+  const int64_t ntiles = ntiles_all * (blockIdx.x + 1) / gridDim.x;
   const uint32_t sA = smem_u32(sm);
   const uint32_t sB = smem_u32(sm + kOffB);
   const int ell = g.ell;
@@ -487,52 +501,71 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     // ------------------------------------------------------------ producers
     const int pt = threadIdx.x - kProdWarp0 * 32;   // 0..255
     const int cb1 = pt & 15, rsub = pt >> 4;         // i_1 core block, row group
+    // The loads of the next quarter are issued before waiting for its stage,
+    // so their latency overlaps the tensor-core work on the stage.
+    const int nq = g.H1 * g.H4;
+    int64_t t = t_beg;
+    int a = 0, b = 0, q = 0;
+    TileInfo ti = tile_info(g, t);
+    auto quarter_src = [&](int64_t tt, const TileInfo& tinf, int aa, int bb, int qq) {
+      const int64_t w = (tinf.kL0 + aa) + g.WL * (tinf.kR0 + bb);
+      const int h1 = qq % g.H1, h4 = qq / g.H1;
+      return g.X + (h1 * 128 + cb1 * 8) + g.n1 * w + g.Nd1 * (int64_t)(h4 * 128 + rsub);
+    };
+    float4 v[16];
+    auto issue = [&](const float* src) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float4* p4 = reinterpret_cast<const float4*>(src + g.Nd1 * (int64_t)(16 * m));
+        v[2 * m] = __ldcs(p4);
+        v[2 * m + 1] = __ldcs(p4 + 1);
+      }
+    };
+    if (t < ntiles) issue(quarter_src(t, ti, 0, 0, 0));
     uint32_t qi = 0;
-    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-      const TileInfo ti = tile_info(g, t);
-      for (int b = 0; b < ti.nB && !*abort_flag; ++b)
-        for (int a = 0; a < ti.nA && !*abort_flag; ++a) {
-          const int64_t w = (ti.kL0 + a) + g.WL * (ti.kR0 + b);
-          for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
-            const int h1 = q % g.H1, h4 = q / g.H1;
-            const int st = qi & 1;
-            if (!mbar_wait(bar(EMPTY_A + st), ((qi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
-            const float* src = g.X + (h1 * 128 + cb1 * 8) + g.n1 * w + g.Nd1 * (int64_t)(h4 * 128 + rsub);
-            float4 v[16];
+    while (t < ntiles && !*abort_flag) {
+      const int st = qi & 1;
+      if (!mbar_wait(bar(EMPTY_A + st), ((qi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
+      const uint32_t tileA = sA + st * kStageB;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-              const float4* p4 = reinterpret_cast<const float4*>(src + g.Nd1 * (int64_t)(16 * m));
-              v[2 * m] = __ldcs(p4);
-              v[2 * m + 1] = __ldcs(p4 + 1);
-            }
-            const uint32_t tileA = sA + st * kStageB;
+      for (int m = 0; m < 8; ++m) {
+        const int i4 = rsub + 16 * m;
+        const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
+                            v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
+        uint32_t hb[4], lb[4];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-              const int i4 = rsub + 16 * m;
-              const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
-                                  v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
-              uint32_t hb[4], lb[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
-                const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
-                lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
-              }
-              const uint32_t off = cb1 * kS1 + (i4 >> 3) * kS4 + (i4 & 7) * 16;
-              st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
-              st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
-            }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar(FULL_A + st));
+        for (int e = 0; e < 4; ++e) {
+          hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
+          const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
+          lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
+        }
+        const uint32_t off = cb1 * kS1 + (i4 >> 3) * kS4 + (i4 & 7) * 16;
+        st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
+        st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(FULL_A + st));
+      ++qi;
+      // advance (quarter, plane, tile) in the order every role uses
+      if (++q == nq) {
+        q = 0;
+        if (++a == ti.nA) {
+          a = 0;
+          if (++b == ti.nB) {
+            b = 0;
+            t += 1;
+            if (t < ntiles) ti = tile_info(g, t);
           }
         }
+      }
+      if (t < ntiles) issue(quarter_src(t, ti, a, b, q));
     }
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
     const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..255
     uint32_t pi = 0;
-    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+    for (int64_t t = t_beg; t < ntiles && !*abort_flag; ++t) {
       const TileInfo ti = tile_info(g, t);
       for (int b = 0; b < ti.nB && !*abort_flag; ++b)
         for (int a = 0; a < ti.nA && !*abort_flag; ++a, ++pi) {
@@ -558,35 +591,43 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
             const int n0 = 4 * qg;
             const int s = n0 / ell;
             nq = (n0 % ell) >> 2;
-            float z[8][4];
+            // four rows are generated together (independent chains) and packed
+            // to BF16 pairs
+            uint32_t pk[4][4];
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              uint64_t row;
-              uint32_t sid;
-              if (colside) {
-                const SkTc sk = g.col[s];
-                const int64_t bglob = g.first + blk * 128 + 8 * kg + kk;
-                row = (uint64_t)(w / sk.wdiv + sk.hstride * bglob);
-                sid = (uint32_t)sk.sid;
-              } else {
-                const SkTc sk = g.row[s];
-                const int64_t i1 = blk * 128 + 8 * kg + kk;
-                row = (uint64_t)(i1 + g.n1 * (w % sk.wdiv));
-                sid = (uint32_t)sk.sid;
+            for (int kk = 0; kk < 8; kk += 4) {
+              float4 r4[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                uint64_t row;
+                uint32_t sid;
+                if (colside) {
+                  const SkTc sk = g.col[s];
+                  const int64_t bglob = g.first + blk * 128 + 8 * kg + kk + h;
+                  row = (uint64_t)(w / sk.wdiv + sk.hstride * bglob);
+                  sid = (uint32_t)sk.sid;
+                } else {
+                  const SkTc sk = g.row[s];
+                  const int64_t i1 = blk * 128 + 8 * kg + kk + h;
+                  row = (uint64_t)(i1 + g.n1 * (w % sk.wdiv));
+                  sid = (uint32_t)sk.sid;
+                }
+                r4[h] = normals4_f32(g.seed, sid, row, (uint32_t)nq);
               }
-              const float4 r4 = normals4_f32(g.seed, sid, row, (uint32_t)nq);
-              z[kk][0] = r4.x;
-              z[kk][1] = r4.y;
-              z[kk][2] = r4.z;
-              z[kk][3] = r4.w;
+#pragma unroll
+              for (int h = 0; h < 4; h += 2) {
+                pk[0][(kk + h) >> 1] = bf16x2_bits(r4[h].x, r4[h + 1].x);
+                pk[1][(kk + h) >> 1] = bf16x2_bits(r4[h].y, r4[h + 1].y);
+                pk[2][(kk + h) >> 1] = bf16x2_bits(r4[h].z, r4[h + 1].z);
+                pk[3][(kk + h) >> 1] = bf16x2_bits(r4[h].w, r4[h + 1].w);
+              }
             }
             const uint32_t base = sB + (buf * kBBlks + (colside ? blk : 2 + blk)) * kBBlkB;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               const int n = n0 + u;
               const uint32_t off = kg * kS1 + (n >> 3) * kS4 + (n & 7) * 16;
-              st_shared_v4(base + off, bf16x2_bits(z[0][u], z[1][u]), bf16x2_bits(z[2][u], z[3][u]),
-                           bf16x2_bits(z[4][u], z[5][u]), bf16x2_bits(z[6][u], z[7][u]));
+              st_shared_v4(base + off, pk[u][0], pk[u][1], pk[u][2], pk[u][3]);
             }
           }
           fence_async_smem();
@@ -599,16 +640,33 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     if (lane == 0) {
       const uint32_t idL = make_idesc(g.NL, true), idR = make_idesc(g.NR, false);
       const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
-      uint32_t qi = 0, pi = 0, tl = 0;
+      const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);  // one R buffer
+      uint32_t qi = 0, pi = 0, lf = 0, ti = 0;
+      int64_t cur_tl = -1;
+      uint32_t initL = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
-        const TileInfo ti = tile_info(g, t);
-        ok = mbar_wait(bar(TM_EMPTY), (tl & 1) ^ 1, abort_flag, g.status);
+      for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti) {
+        const TileInfo tinf = tile_info(g, t);
+        const int64_t tl = t / g.tilesR;
+        if (tl != cur_tl) {
+          // a new kL block: the previous block's L slots go to the epilogue
+          if (cur_tl >= 0) {
+            mma_commit(bar(TML_FULL));
+            ++lf;
+          }
+          ok = mbar_wait(bar(TML_EMPTY), (lf & 1) ^ 1, abort_flag, g.status);
+          if (!ok) break;
+          tc_fence_after();
+          initL = 0;
+          cur_tl = tl;
+        }
+        const uint32_t rb = ti & 1;
+        ok = mbar_wait(bar(TMR_EMPTY + rb), ((ti >> 1) & 1) ^ 1, abort_flag, g.status);
         if (!ok) break;
         tc_fence_after();
-        uint32_t initL = 0, initR = 0;  // slot has been written in this tile
-        for (int b = 0; b < ti.nB && ok; ++b)
-          for (int a = 0; a < ti.nA && ok; ++a, ++pi) {
+        uint32_t initR = 0;
+        for (int b = 0; b < tinf.nB && ok; ++b)
+          for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
             const int buf = pi & 1;
             ok = mbar_wait(bar(FULL_B + buf), (pi >> 1) & 1, abort_flag, g.status);
             if (!ok) break;
@@ -624,25 +682,32 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
               const uint32_t bR = sB + (buf * kBBlks + 2 + h1) * kBBlkB;
               const int slotL = a * g.H1 + h1, slotR = b * g.H4 + h4;
               const uint32_t dL = tmem + (uint32_t)(slotL * g.NL);
-              const uint32_t dR = tmem + colR0 + (uint32_t)(slotR * g.NR);
-              for (int ks = 0; ks < 8; ++ks)
+              const uint32_t dR = tmem + colR0 + rb * colRB + (uint32_t)(slotR * g.NR);
+              // descriptors of k-step 0; a k-step advances the start address
+              // field (16-byte units) by a constant
+              const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
+              const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4);
+              const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> slotR) & 1u;
+#pragma unroll
+              for (int ks = 0; ks < 8; ++ks) {
+#pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                  const uint32_t A = tileA + part * kTileB;
-                  const uint32_t accL = ((initL >> slotL) & 1u) | (uint32_t)(ks | part);
-                  mma_bf16_ss(dL, make_desc(A + ks * 2 * kS4, kS4, kS1), make_desc(bL + ks * 2 * kS1, kS1, kS4),
-                              idL, accL);
-                  const uint32_t accR = ((initR >> slotR) & 1u) | (uint32_t)(ks | part);
-                  mma_bf16_ss(dR, make_desc(A + ks * 2 * kS1, kS1, kS4), make_desc(bR + ks * 2 * kS1, kS1, kS4),
-                              idR, accR);
+                  const uint64_t po = (uint64_t)((part * kTileB) >> 4);
+                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                              idL, accL0 | (uint32_t)(ks | part));
+                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                              idR, accR0 | (uint32_t)(ks | part));
                 }
+              }
               initL |= 1u << slotL;
               initR |= 1u << slotR;
               mma_commit(bar(EMPTY_A + st));
             }
             if (ok) mma_commit(bar(EMPTY_B + buf));
           }
-        if (ok) mma_commit(bar(TM_FULL));
+        if (ok) mma_commit(bar(TMR_FULL + rb));
       }
+      if (ok && cur_tl >= 0) mma_commit(bar(TML_FULL));
       // drain this thread's MMAs before the tensor memory is freed
       mma_commit(bar(DRAIN));
       const long long t0 = clock64();
@@ -655,18 +720,17 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     const int lrow = warp * 32 + lane;  // TMEM lane = row within a 128 half
     const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
     const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
-    uint32_t tl = 0;
-    for (int64_t t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tl) {
-      const TileInfo ti = tile_info(g, t);
-      if (!mbar_wait(bar(TM_FULL), tl & 1, abort_flag, g.status)) break;
+    const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);
+    // L slots of kL block [kL0, kL0 + nA) -> column sketches
+    auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
+      if (!mbar_wait(bar(TML_FULL), lf & 1, abort_flag, g.status)) return false;
       tc_fence_after();
-      // column sketches: slot (a, h1), row i1 = h1*128 + lrow
       for (int h1 = 0; h1 < g.H1; ++h1) {
         const int64_t i1 = h1 * 128 + lrow;
         double acc1[32];
         for (int j = 0; j < g.NL; ++j) acc1[j] = 0.0;
-        for (int a = 0; a < ti.nA; ++a) {
-          const int64_t kL = ti.kL0 + a;
+        for (int a = 0; a < nA; ++a) {
+          const int64_t kL = kL0 + a;
           float v[32];
           const uint32_t c0 = tmem + lane_addr + (uint32_t)((a * g.H1 + h1) * g.NL);
           for (int c = 0; c < g.NL; c += 16) tmem_ld16(c0 + c, v + c);
@@ -684,15 +748,40 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           if (g.col[s].wdiv == 1)
             for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.col[s].off + i1 + g.col[s].rows * j, acc1[s * ell + j]);
       }
-      // row sketches: slot (b, h4), last-mode index bglob = first + h4*128 + lrow
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(TML_EMPTY));
+      return true;
+    };
+    uint32_t lf = 0, ti = 0;
+    int64_t cur_tl = -1, cur_kL0 = 0;
+    int cur_nA = 0;
+    bool ok = true;
+    for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t, ++ti) {
+      const TileInfo tinf = tile_info(g, t);
+      const int64_t tl = t / g.tilesR;
+      if (tl != cur_tl) {
+        if (cur_tl >= 0) {
+          ok = flush_L(cur_kL0, cur_nA, lf);
+          ++lf;
+          if (!ok) break;
+        }
+        cur_tl = tl;
+        cur_kL0 = tinf.kL0;
+        cur_nA = tinf.nA;
+      }
+      // R slots of this tile (buffer ti & 1) -> row sketches
+      const uint32_t rb = ti & 1;
+      if (!mbar_wait(bar(TMR_FULL + rb), (ti >> 1) & 1, abort_flag, g.status)) break;
+      tc_fence_after();
       for (int h4 = 0; h4 < g.H4; ++h4) {
         const int64_t bg = g.first + h4 * 128 + lrow;
         double acc1[32];
         for (int j = 0; j < g.NR; ++j) acc1[j] = 0.0;
-        for (int b = 0; b < ti.nB; ++b) {
-          const int64_t kR = ti.kR0 + b;
+        for (int b = 0; b < tinf.nB; ++b) {
+          const int64_t kR = tinf.kR0 + b;
           float v[32];
-          const uint32_t c0 = tmem + lane_addr + colR0 + (uint32_t)((b * g.H4 + h4) * g.NR);
+          const uint32_t c0 = tmem + lane_addr + colR0 + rb * colRB + (uint32_t)((b * g.H4 + h4) * g.NR);
           for (int c = 0; c < g.NR; c += 16) tmem_ld16(c0 + c, v + c);
           for (int s = 0; s < g.nR; ++s) {
             const SkTc sk = g.row[s];
@@ -712,8 +801,9 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar(TM_EMPTY));
+      if (lane == 0) mbar_arrive(bar(TMR_EMPTY + rb));
     }
+    if (ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
   }
   tc_fence_before();
   __syncthreads();
@@ -758,11 +848,13 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   g.H1 = (int)(it.n[0] / 128);
   g.H4 = (int)(count / 128);
   // tile: T2 x T3 planes, all slots resident in 512 TMEM columns
-  int T2 = (int)std::min<int64_t>(g.WL, 4), T3 = (int)std::min<int64_t>(g.WR, 4);
-  auto cols = [&](int a, int b) { return a * g.H1 * NL + b * g.H4 * NR; };
+  // tile: T2 kL x T3 kR planes; TMEM holds the L slots and two R buffers
+  int T2 = (int)std::min<int64_t>(g.WL, 4), T3 = (int)std::min<int64_t>(g.WR, 2);
+  auto cols = [&](int a, int b) { return a * g.H1 * NL + 2 * b * g.H4 * NR; };
   while (cols(T2, T3) > 512 && (T2 > 1 || T3 > 1)) {
-    if (T2 >= T3 && T2 > 1) --T2;
-    else --T3;
+    if (T2 >= 2 * T3 && T2 > 1) --T2;
+    else if (T3 > 1) --T3;
+    else --T2;
   }
   while (T2 < g.WL && T2 < 16 && cols(T2 + 1, T3) <= 512) ++T2;
   while (T3 < g.WR && T3 < 16 && cols(T2, T3 + 1) <= 512) ++T3;
@@ -964,6 +1056,20 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   return cudaGetLastError();
 }
 
+// The plane kernel needs one CTA of 640 threads with 217 KB of shared memory
+// per SM; checked once against the compiled function and the device.
+static bool tc_kernel_launchable() {
+  static int ok = -1;
+  if (ok < 0) {
+    cudaFuncAttributes fa;
+    int dev = 0, smem_optin = 0;
+    ok = cudaFuncGetAttributes(&fa, tc::sketch_tc_kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+         fa.maxThreadsPerBlock >= tc::kThreads && smem_optin >= tc::kSmemBytes;
+  }
+  return ok == 1;
+}
+
 cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st) {
   tc::TcArgs g;
@@ -979,6 +1085,7 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (!tc_kernel_launchable()) return launch_sketch_mma(P, item, X, first, count, ws, st);
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();

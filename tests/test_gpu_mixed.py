@@ -169,3 +169,74 @@ def test_tcgen05_hilbert_within_10eps():
     e_f = rel(t.reconstruct().cpu().numpy(), f.reconstruct().cpu().numpy(), x64)
     print(f"tcgen05 hilbert: |X~-X|={e_x:.2e} |X~-X~fp64|={e_f:.2e} ranks={t.status()[1]}")
     assert e_x <= 1e-5 and e_f <= 1e-5
+
+
+def _sampled_sketch_check(dims, kw, nsamp=6, seed=7):
+    """Sketch entries of a multi-tile launch, each computed one by one by the
+    oracle (FP64 sums over the whole tensor with the rounded test-matrix rows
+    and the split X), at the shapes where CTAs process several tiles."""
+    n1, n2, n3, n4 = dims
+    Xd = torch.empty(n1 * n2 * n3 * n4, dtype=torch.float32, device="cuda")
+    nn = (C.c_int64 * 4)(*dims)
+    N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, n4, C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
+    t = TTSketch(dims, seed=seed, prec="bf16", **kw)
+    assert t.kernel_kind() == 2
+    t.begin()
+    t.accumulate(Xd, 0, n4)
+    sk = sketch_dict(t)
+    x = ti.hilbert_type(dims, np.float32).astype(np.float64)
+    xs = _split(x, "bf16").reshape((n1, n2, n3, n4), order="F")
+    rng = np.random.default_rng(0)
+    l = sk[(0, 1)].shape[1]
+    bf = lambda A: philox.round_to(A, "bf16")
+    errs = {}
+    for _ in range(nsamp):
+        i1, i2, i3, i4 = [int(rng.integers(v)) for v in dims]
+        # S_1(i1, :) = sum_{i2,i3,i4} X Omega_1[(i2,i3,i4)]
+        Om1 = bf(philox.test_matrix(seed, 1, n2 * n3 * n4, l))
+        ref = xs[i1].reshape(-1, order="F") @ Om1
+        errs.setdefault("S1", []).append(np.abs(sk[(0, 1)][i1] - ref).max() / np.abs(ref).max())
+        # S_2(i1 + n1 i2, :) = sum_{i3,i4} X Omega_2[(i3,i4)]
+        Om2 = bf(philox.test_matrix(seed, 2, n3 * n4, l))
+        ref = xs[i1, i2].reshape(-1, order="F") @ Om2
+        errs.setdefault("S2", []).append(np.abs(sk[(0, 2)][i1 + n1 * i2] - ref).max() / np.abs(ref).max())
+        # R_2(i3 + n3 i4, :) = sum_{i1,i2} X Psi_2[(i1,i2)]
+        Ps2 = bf(philox.test_matrix(seed, 66, n1 * n2, l))
+        ref = xs[:, :, i3, i4].reshape(-1, order="F") @ Ps2
+        errs.setdefault("R2", []).append(np.abs(sk[(1, 2)][i3 + n3 * i4] - ref).max() / np.abs(ref).max())
+        # R_3(i4, :) = sum_{i1,i2,i3} X Psi_3[(i1,i2,i3)]
+        Ps3 = bf(philox.test_matrix(seed, 67, n1 * n2 * n3, l))
+        ref = xs[:, :, :, i4].reshape(-1, order="F") @ Ps3
+        errs.setdefault("R3", []).append(np.abs(sk[(1, 3)][i4] - ref).max() / np.abs(ref).max())
+    return {k: max(v) for k, v in errs.items()}
+
+
+@pytest.mark.parametrize("dims", [[256, 64, 48, 256], [128, 64, 96, 128]])
+def test_tcgen05_multitile_sampled_entries(dims):
+    """Several tiles per CTA (the run-change flush and the double-buffered row
+    accumulators are exercised); entries within the flip bound of the oracle."""
+    e = _sampled_sketch_check(dims, dict(eps=1e-6, rmax=6, p=10))
+    print("multi-tile sampled max rel err:", e)
+    assert all(v <= 2e-3 for v in e.values()), e
+
+
+@pytest.mark.parametrize("dims", [[256, 64, 48, 256], [128, 64, 96, 128]])
+def test_tcgen05_multitile_pipeline_within_10eps(dims):
+    """The whole one-pass pipeline at multi-tile shapes: X~ within 10 eps of X
+    and of the FP64 path; this also checks that the middle-core solve
+    regenerates exactly the test matrix the sketch used (an inconsistent
+    B = P^T Omega costs ~1e-5 here)."""
+    n1, n2, n3, n4 = dims
+    Xd = torch.empty(n1 * n2 * n3 * n4, dtype=torch.float32, device="cuda")
+    nn = (C.c_int64 * 4)(*dims)
+    N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, n4, C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
+    t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="bf16")
+    assert t.kernel_kind() == 2
+    t.pstt2(Xd)
+    f = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="fp64").pstt2(Xd)
+    e_x = t.error(Xd).cpu().numpy()
+    Xf = f.reconstruct(torch.float32)
+    e_f = t.error(Xf).cpu().numpy()
+    rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
+    print(f"multi-tile pipeline {dims}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
+    assert rx <= 1e-5 and rf <= 1e-5
