@@ -330,6 +330,7 @@ constexpr int kOffB = kStages * kStageB;
 constexpr int kOffBar = kOffB + kBBufs * kBBlks * kBBlkB;
 constexpr int kSmemBytes = kOffBar + 256 + 1024;  // barriers + alignment slack
 constexpr long long kWaitCycles = 4000000000LL;  // bounded waits (~2 s)
+constexpr int kMaxChainL = 256;                   // accumulating MMAs per L slot between flushes
 
 struct SkTc {
   int64_t rows, off, wdiv, hstride;
@@ -343,6 +344,7 @@ struct TcArgs {
   int64_t n1, first, W, WL, WR, Nd1, tilesL, tilesR;
   uint64_t seed;
   int H1, H4, T2, T3, ell, nL, nR, NL, NR, tmem_cols;
+  int64_t runL;  // tiles of one kL block accumulated in the L slots before a flush
   SkTc col[4], row[4];
 };
 
@@ -449,6 +451,17 @@ __device__ __forceinline__ TileInfo tile_info(const TcArgs& g, int64_t t) {
   ti.nA = (int)imin64(g.T2, g.WL - ti.kL0);
   ti.nB = (int)imin64(g.T3, g.WR - ti.kR0);
   return ti;
+}
+
+// The L slots of one kL block are flushed after at most runL tiles.  The error
+// of the tensor core's FP32 accumulation in tensor memory grows about linearly
+// with the number of MMAs accumulated into one slot (measured on the 256^4
+// Hilbert-type tensor: 8192 accumulating MMAs per slot gave 4.7e-5 relative
+// reconstruction error, 64 gave 2.3e-6), so a chain is kept to a few hundred
+// MMAs and the sum continues in FP64.
+__device__ __forceinline__ int64_t l_group(const TcArgs& g, int64_t t) {
+  const int64_t tl = t / g.tilesR, tr = t % g.tilesR;
+  return tl * ((g.tilesR + g.runL - 1) / g.runL) + tr / g.runL;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) {
@@ -647,9 +660,9 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       bool ok = true;
       for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti) {
         const TileInfo tinf = tile_info(g, t);
-        const int64_t tl = t / g.tilesR;
+        const int64_t tl = l_group(g, t);
         if (tl != cur_tl) {
-          // a new kL block: the previous block's L slots go to the epilogue
+          // a new L group: the previous group's L slots go to the epilogue
           if (cur_tl >= 0) {
             mma_commit(bar(TML_FULL));
             ++lf;
@@ -759,7 +772,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     bool ok = true;
     for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t, ++ti) {
       const TileInfo tinf = tile_info(g, t);
-      const int64_t tl = t / g.tilesR;
+      const int64_t tl = l_group(g, t);
       if (tl != cur_tl) {
         if (cur_tl >= 0) {
           ok = flush_L(cur_kL0, cur_nA, lf);
@@ -866,6 +879,8 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   g.tmem_cols = tc;
   g.tilesL = (g.WL + T2 - 1) / T2;
   g.tilesR = (g.WR + T3 - 1) / T3;
+  // accumulating MMAs per L slot and tile: T3 planes x H4 quarters x 8 k-steps x (hi, lo)
+  g.runL = std::max<int64_t>(1, kMaxChainL / (T3 * g.H4 * 16));
   g.ell = ell;
   g.nL = nL;
   g.nR = nR;
