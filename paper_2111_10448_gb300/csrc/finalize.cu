@@ -672,8 +672,6 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
       smem_up = std::max(smem_up, need);
     }
   }
-  e = cudaMemsetAsync(wsb + kStatusOff, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
   for (int L = 0; L < max_lev; ++L) {
     const int nt = plan_ntasks(&P, L);
     if (nt == 0) continue;

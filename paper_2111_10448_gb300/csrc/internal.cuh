@@ -23,6 +23,7 @@ namespace tts {
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 constexpr int kMaxLev = 8;        // TSQR tree depth limit
+constexpr int kTcGroupBytes = 2304;  // plane kernel: one 8-column group of a 128-row BF16 block image
 constexpr int kMaxSk = TT_MAXD;   // sketches per item (d of them at most)
 
 enum SkType : int { SK_COL = 0, SK_ROW = 1 };
@@ -91,6 +92,8 @@ struct DevItem {
   int64_t off_Rall[TT_MAXD + 2];  // right interfaces Rt_k, k = 2..d (rpad_{k-1} x M_{k-1})
   int64_t off_Y;            // max_k N_k x rpad_k
   const void* X;            // batched: device pointer of this item's tensor (set per call)
+  int64_t off_tctab;        // plane kernel: staged test-matrix blocks shared by many planes
+  int64_t tctab_doubles;    // its size (0 when the plane kernel cannot serve the item)
 };
 
 struct Task {               // one block of one TSQR level (finalize)

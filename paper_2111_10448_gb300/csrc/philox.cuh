@@ -60,12 +60,31 @@ __device__ __forceinline__ void normals4_f64(uint64_t seed, uint32_t sid, uint64
   z[3] = rb * sb;
 }
 
-// FP32 generator of the mixed-precision sketches: defined out of line in the
-// one translation unit that holds every kernel needing the same entries (the
-// sketch, the middle-core solve that regenerates Omega_{d*}, the backward),
-// so that all of them run one compiled body and get bit-identical values
-// (inlined copies may be contracted or scheduled differently).
-__device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q);
+// Four consecutive FP32 normals of the mixed-precision sketches.  Every
+// operation below is an explicitly rounded intrinsic (or logf), so the
+// compiler has no contraction or reassociation freedom: every inlined copy,
+// in every kernel that regenerates these entries (the sketch, the staged
+// test-matrix tables, the middle-core matrix B, the backward), computes the
+// same bits.
+__device__ __forceinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q) {
+  uint32_t c0 = (uint32_t)row, c1 = (uint32_t)(row >> 32), c2 = q, c3 = sid;
+  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+  // u = (x + 1/2) 2^-32 in FP32: x is rounded to 24 bits (relative error
+  // 2^-24 at any magnitude), then scaled exactly and offset by 2^-33.
+  const float u0 = __fmaf_rn(__uint2float_rn(c0), 0x1p-32f, 0x1p-33f);
+  const float u1 = __fmaf_rn(__uint2float_rn(c1), 0x1p-32f, 0x1p-33f);
+  const float u2 = __fmaf_rn(__uint2float_rn(c2), 0x1p-32f, 0x1p-33f);
+  const float u3 = __fmaf_rn(__uint2float_rn(c3), 0x1p-32f, 0x1p-33f);
+  const float ra = __fsqrt_rn(__fmul_rn(-2.0f, logf(u0)));
+  const float rb = __fsqrt_rn(__fmul_rn(-2.0f, logf(u2)));
+  // centred angles 2 pi u - pi in (-pi, pi]: cos(2 pi u) = -cos(.), sin likewise
+  const float ta = __fmaf_rn(u1, 6.28318530717958647692f, -3.14159265358979323846f);
+  const float tb = __fmaf_rn(u3, 6.28318530717958647692f, -3.14159265358979323846f);
+  float sa, ca, sb, cb;
+  __sincosf(ta, &sa, &ca);
+  __sincosf(tb, &sb, &cb);
+  return make_float4(-__fmul_rn(ra, ca), -__fmul_rn(ra, sa), -__fmul_rn(rb, cb), -__fmul_rn(rb, sb));
+}
 
 // Round an FP32 value to the MMA input type, nearest-even, returned as FP32.
 __device__ __forceinline__ float round_tf32(float x) {

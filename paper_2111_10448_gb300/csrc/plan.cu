@@ -195,6 +195,23 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.off_RB = ws.take((int64_t)r * r);
     it.off_H = ws.take(it.N[ds] * r);
   }
+  // Staging area of the BF16 plane kernel: test-matrix blocks whose rows do
+  // not depend on the plane (column sketches with wdiv > 1, row sketches with
+  // wdiv < W), one 128-row block image per distinct value and half.
+  it.tctab_doubles = 0;
+  if (q.prec == TT_PREC_BF16 && q.x_dtype == TT_F32 && (d == 3 || d == 4) &&
+      (q.n[0] == 128 || q.n[0] == 256)) {
+    int64_t bytes = 0;
+    const int64_t hd = (std::min<int64_t>(q.n[d - 1], 256) + 127) / 128, h1 = q.n[0] / 128;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+      const DevSketch& s = P.sketches[si];
+      const int64_t blk = (int64_t)((s.width + 7) / 8) * kTcGroupBytes;
+      if (s.type == SK_COL && s.wdiv > 1) bytes += (it.W / s.wdiv) * hd * blk;
+      if (s.type == SK_ROW && s.wdiv < it.W) bytes += s.wdiv * h1 * blk;
+    }
+    it.tctab_doubles = (bytes + 7) / 8;
+  }
+  it.off_tctab = it.tctab_doubles ? ws.take(it.tctab_doubles) : 0;
   // reconstruction interfaces
   for (int k = 1; k <= ds; ++k) it.off_L[k] = ws.take(it.N[k] * it.rpad[k]);
   for (int k = ds + 1; k <= d; ++k) it.off_Rt[k] = ws.take((int64_t)it.rpad[k - 1] * (it.N[d] / it.N[k - 1]));
@@ -333,9 +350,15 @@ int device_sm_count() {
   return n;
 }
 
+// Start of a decomposition: clear the status word (so that a bit raised by
+// the sketch kernels survives until tt_query_status) and the sketches.
 static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
   const DevItem& it = P.items[item];
   double* base = (double*)ws;
+  if (item == 0) {
+    cudaError_t e = cudaMemsetAsync((char*)ws + kStatusOff, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
     const DevSketch& s = P.sketches[si];
     cudaError_t e = cudaMemsetAsync(base + s.off, 0, sizeof(double) * s.rows * s.width, st);

@@ -1,8 +1,7 @@
 // Mixed-precision (TF32 / BF16 tensor-core) sketch path and everything that
 // must regenerate its test matrices bit-identically (the middle-core matrix
 // B = P^T Omega_{d*} of the one-pass solve, and the test-matrix export).
-// All of them live in this translation unit and call the one out-of-line FP32
-// generator below.
+// All of them use the FP32 generator of philox.cuh.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -13,26 +12,6 @@
 #include "philox.cuh"
 
 namespace tts {
-
-__device__ __noinline__ float4 normals4_f32(uint64_t seed, uint32_t sid, uint64_t row, uint32_t q) {
-  uint32_t c0 = (uint32_t)row, c1 = (uint32_t)(row >> 32), c2 = q, c3 = sid;
-  philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-  // u = (x + 1/2) 2^-32 in FP32: x is rounded to 24 bits (relative error
-  // 2^-24 at any magnitude), then scaled exactly and offset by 2^-33.
-  const float u0 = __fmaf_rn(__uint2float_rn(c0), 0x1p-32f, 0x1p-33f);
-  const float u1 = __fmaf_rn(__uint2float_rn(c1), 0x1p-32f, 0x1p-33f);
-  const float u2 = __fmaf_rn(__uint2float_rn(c2), 0x1p-32f, 0x1p-33f);
-  const float u3 = __fmaf_rn(__uint2float_rn(c3), 0x1p-32f, 0x1p-33f);
-  const float ra = __fsqrt_rn(__fmul_rn(-2.0f, logf(u0)));
-  const float rb = __fsqrt_rn(__fmul_rn(-2.0f, logf(u2)));
-  // centred angles 2 pi u - pi in (-pi, pi]: cos(2 pi u) = -cos(.), sin likewise
-  const float ta = __fmaf_rn(u1, 6.28318530717958647692f, -3.14159265358979323846f);
-  const float tb = __fmaf_rn(u3, 6.28318530717958647692f, -3.14159265358979323846f);
-  float sa, ca, sb, cb;
-  __sincosf(ta, &sa, &ca);
-  __sincosf(tb, &sb, &cb);
-  return make_float4(-__fmul_rn(ra, ca), -__fmul_rn(ra, sa), -__fmul_rn(rb, cb), -__fmul_rn(rb, sb));
-}
 
 namespace {
 
@@ -317,6 +296,7 @@ namespace tc {
 
 constexpr int kS1 = 144;                 // bytes between core matrices along i_1 (k of B)
 constexpr int kS4 = 16 * kS1;            // 2304: bytes between core matrices along i_d (n of B)
+static_assert(kS4 == kTcGroupBytes, "block image layout");
 constexpr int kTileB = 16 * kS4;         // one 128 x 128 BF16 tile
 constexpr int kStageB = 2 * kTileB;      // hi + lo
 constexpr int kStages = 2;
@@ -334,6 +314,7 @@ constexpr int kMaxChainL = 256;                   // accumulating MMAs per L slo
 
 struct SkTc {
   int64_t rows, off, wdiv, hstride;
+  int64_t tab;  // byte offset of the staged blocks in the workspace, -1: generated per plane
   int sid, pad_;
 };
 
@@ -345,6 +326,8 @@ struct TcArgs {
   uint64_t seed;
   int H1, H4, T2, T3, ell, nL, nR, NL, NR, tmem_cols;
   int64_t runL;  // tiles of one kL block accumulated in the L slots before a flush
+  int genL[4], genR[4], ngenL, ngenR;  // sketches whose blocks the RNG warps generate
+  uint32_t tab_tx;                     // bytes of staged blocks copied per plane
   SkTc col[4], row[4];
 };
 
@@ -356,6 +339,15 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of
+// 16), completing `bytes` of transaction count on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   uint32_t ok;
@@ -464,13 +456,29 @@ __device__ __forceinline__ int64_t l_group(const TcArgs& g, int64_t t) {
   return tl * ((g.tilesR + g.runL - 1) / g.runL) + tr / g.runL;
 }
 
+// The test-matrix row of a plane w = kL + WL kR depends on w / wdiv (column
+// sketches) or w % wdiv (row sketches), with wdiv one of 1, WL, W for d <= 4;
+// these keys avoid a 64-bit division per generated row.
+__device__ __forceinline__ int64_t col_key(const TcArgs& g, const SkTc& sk, int64_t w, int64_t kR) {
+  if (sk.wdiv == 1) return w;
+  if (sk.wdiv == g.WL) return kR;
+  if (sk.wdiv == g.W) return 0;
+  return w / sk.wdiv;
+}
+__device__ __forceinline__ int64_t row_key(const TcArgs& g, const SkTc& sk, int64_t w, int64_t kL) {
+  if (sk.wdiv == 1) return 0;
+  if (sk.wdiv == g.WL) return kL;
+  if (sk.wdiv == g.W) return w;
+  return w % sk.wdiv;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
   // barrier indices
   const int FULL_A = 0, EMPTY_A = 2, FULL_B = 4, EMPTY_B = 6, TML_FULL = 8, TML_EMPTY = 9, DRAIN = 10,
-            TMR_FULL = 11, TMR_EMPTY = 13;
+            TMR_FULL = 11, TMR_EMPTY = 13, TAB_FULL = 15;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -481,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       mbar_init(bar(FULL_A + s), kProdWarps);
       mbar_init(bar(EMPTY_A + s), 1);
       mbar_init(bar(FULL_B + s), kRngWarps);
+      mbar_init(bar(TAB_FULL + s), 1);  // staged-block copies of a plane
       mbar_init(bar(EMPTY_B + s), 1);
     }
     mbar_init(bar(TML_FULL), 1);
@@ -577,20 +586,49 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
     const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..255
+    const int qps = ell / 4;                      // column quads per sketch
+    const int jobsL = 16 * qps * g.ngenL, jobsR = 16 * qps * g.ngenR;  // per 128-row block
+    const int total = g.H4 * jobsL + g.H1 * jobsR;
     uint32_t pi = 0;
+    int64_t tab_last[2] = {-1, -1};  // last plane whose staged copies used each buffer
     for (int64_t t = t_beg; t < ntiles && !*abort_flag; ++t) {
       const TileInfo ti = tile_info(g, t);
       for (int b = 0; b < ti.nB && !*abort_flag; ++b)
         for (int a = 0; a < ti.nA && !*abort_flag; ++a, ++pi) {
-          const int64_t w = (ti.kL0 + a) + g.WL * (ti.kR0 + b);
+          const int64_t kLp = ti.kL0 + a, kRp = ti.kR0 + b;
+          const int64_t w = kLp + g.WL * kRp;
           const int buf = pi & 1;
           if (!mbar_wait(bar(EMPTY_B + buf), ((pi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
           // blocks: 0..H4-1 = column side (k = i_d), 2..2+H1-1 = row side (k = i_1)
-          const int jobsL = 16 * (g.NL / 4), jobsR = 16 * (g.NR / 4);
-          const int total = g.H4 * jobsL + g.H1 * jobsR;
+          if (rt == 0 && g.tab_tx) {
+            // blocks shared by many planes come from the staged tables
+            {
+              mbar_arrive_expect_tx(bar(TAB_FULL + buf), g.tab_tx);
+              tab_last[buf] = pi;
+              const char* wsb = reinterpret_cast<const char*>(g.ws);
+              for (int s = 0; s < g.nL; ++s) {
+                const SkTc sk = g.col[s];
+                if (sk.tab < 0) continue;
+                const uint32_t bytes = (uint32_t)(ell / 8) * kS4;
+                for (int h4 = 0; h4 < g.H4; ++h4)
+                  bulk_g2s(sB + (buf * kBBlks + h4) * kBBlkB + (s * ell / 8) * kS4,
+                           wsb + sk.tab + (col_key(g, sk, w, kRp) * g.H4 + h4) * (int64_t)bytes, bytes,
+                           bar(TAB_FULL + buf));
+              }
+              for (int s = 0; s < g.nR; ++s) {
+                const SkTc sk = g.row[s];
+                if (sk.tab < 0) continue;
+                const uint32_t bytes = (uint32_t)(ell / 8) * kS4;
+                for (int h1 = 0; h1 < g.H1; ++h1)
+                  bulk_g2s(sB + (buf * kBBlks + 2 + h1) * kBBlkB + (s * ell / 8) * kS4,
+                           wsb + sk.tab + (row_key(g, sk, w, kLp) * g.H1 + h1) * (int64_t)bytes, bytes,
+                           bar(TAB_FULL + buf));
+              }
+            }
+          }
           for (int job = rt; job < total; job += kRngWarps * 32) {
-            int blk, jj, nq;
             bool colside;
+            int blk, jj;
             if (job < g.H4 * jobsL) {
               colside = true;
               blk = job / jobsL;
@@ -600,10 +638,16 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
               blk = (job - g.H4 * jobsL) / jobsR;
               jj = (job - g.H4 * jobsL) % jobsR;
             }
-            const int kg = jj & 15, qg = jj >> 4;
-            const int n0 = 4 * qg;
-            const int s = n0 / ell;
-            nq = (n0 % ell) >> 2;
+            const int kg = jj & 15, rest = jj >> 4;
+            const int gi = rest / qps, nq = rest % qps;
+            const int s = colside ? g.genL[gi] : g.genR[gi];
+            const int n0 = s * ell + 4 * nq;
+            const SkTc sk = colside ? g.col[s] : g.row[s];
+            const uint32_t sid = (uint32_t)sk.sid;
+            // column side: row = key + hstride * i_d; row side: row = i_1 + n1 * key
+            const int64_t rbase = colside ? col_key(g, sk, w, kRp) + sk.hstride * (g.first + blk * 128 + 8 * kg)
+                                          : blk * 128 + 8 * kg + g.n1 * row_key(g, sk, w, kLp);
+            const int64_t rstep = colside ? sk.hstride : 1;
             // four rows are generated together (independent chains) and packed
             // to BF16 pairs
             uint32_t pk[4][4];
@@ -611,22 +655,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
             for (int kk = 0; kk < 8; kk += 4) {
               float4 r4[4];
 #pragma unroll
-              for (int h = 0; h < 4; ++h) {
-                uint64_t row;
-                uint32_t sid;
-                if (colside) {
-                  const SkTc sk = g.col[s];
-                  const int64_t bglob = g.first + blk * 128 + 8 * kg + kk + h;
-                  row = (uint64_t)(w / sk.wdiv + sk.hstride * bglob);
-                  sid = (uint32_t)sk.sid;
-                } else {
-                  const SkTc sk = g.row[s];
-                  const int64_t i1 = blk * 128 + 8 * kg + kk + h;
-                  row = (uint64_t)(i1 + g.n1 * (w % sk.wdiv));
-                  sid = (uint32_t)sk.sid;
-                }
-                r4[h] = normals4_f32(g.seed, sid, row, (uint32_t)nq);
-              }
+              for (int h = 0; h < 4; ++h)
+                r4[h] = normals4_f32(g.seed, sid, (uint64_t)(rbase + rstep * (kk + h)), (uint32_t)nq);
 #pragma unroll
               for (int h = 0; h < 4; h += 2) {
                 pk[0][(kk + h) >> 1] = bf16x2_bits(r4[h].x, r4[h + 1].x);
@@ -648,6 +678,15 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           if (lane == 0) mbar_arrive(bar(FULL_B + buf));
         }
     }
+    // Copies still in flight when the CTA gave up must land before it exits.
+    if (rt == 0)
+      for (int b2 = 0; b2 < 2; ++b2)
+        if (tab_last[b2] >= 0) {
+          const long long t0 = clock64();
+          while (!mbar_try(bar(TAB_FULL + b2), (uint32_t)((tab_last[b2] >> 1) & 1)) &&
+                 clock64() - t0 < kWaitCycles) {
+          }
+        }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -682,6 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
             const int buf = pi & 1;
             ok = mbar_wait(bar(FULL_B + buf), (pi >> 1) & 1, abort_flag, g.status);
+            if (ok && g.tab_tx) ok = mbar_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
             if (!ok) break;
             tc_fence_after();
             for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
@@ -740,8 +780,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       tc_fence_after();
       for (int h1 = 0; h1 < g.H1; ++h1) {
         const int64_t i1 = h1 * 128 + lrow;
-        double acc1[32];
-        for (int j = 0; j < g.NL; ++j) acc1[j] = 0.0;
+        float acc1[32];  // FP32 pre-sum over the few slots of one flush
+        for (int j = 0; j < g.NL; ++j) acc1[j] = 0.0f;
         for (int a = 0; a < nA; ++a) {
           const int64_t kL = kL0 + a;
           float v[32];
@@ -750,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           for (int s = 0; s < g.nL; ++s) {
             const SkTc sk = g.col[s];
             if (sk.wdiv == 1) {
-              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += (double)v[s * ell + j];
+              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += v[s * ell + j];
             } else {
               const int64_t row = i1 + g.n1 * (kL % sk.wdiv);
               for (int j = 0; j < ell; ++j) atomicAdd(g.ws + sk.off + row + sk.rows * j, (double)v[s * ell + j]);
@@ -759,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
         }
         for (int s = 0; s < g.nL; ++s)
           if (g.col[s].wdiv == 1)
-            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.col[s].off + i1 + g.col[s].rows * j, acc1[s * ell + j]);
+            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.col[s].off + i1 + g.col[s].rows * j, (double)acc1[s * ell + j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -789,8 +829,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       tc_fence_after();
       for (int h4 = 0; h4 < g.H4; ++h4) {
         const int64_t bg = g.first + h4 * 128 + lrow;
-        double acc1[32];
-        for (int j = 0; j < g.NR; ++j) acc1[j] = 0.0;
+        float acc1[32];  // FP32 pre-sum over the few slots of one flush
+        for (int j = 0; j < g.NR; ++j) acc1[j] = 0.0f;
         for (int b = 0; b < tinf.nB; ++b) {
           const int64_t kR = tinf.kR0 + b;
           float v[32];
@@ -799,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           for (int s = 0; s < g.nR; ++s) {
             const SkTc sk = g.row[s];
             if (sk.wdiv == g.W) {
-              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += (double)v[s * ell + j];
+              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += v[s * ell + j];
             } else {
               const int64_t whi = kR / (sk.wdiv / g.WL);
               const int64_t row = whi + sk.hstride * bg;
@@ -810,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
         for (int s = 0; s < g.nR; ++s)
           if (g.row[s].wdiv == g.W)
             for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.row[s].off + bg * g.row[s].hstride + g.row[s].rows * j,
-                                                    acc1[s * ell + j]);
+                                                    (double)acc1[s * ell + j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -823,6 +863,40 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   tc_fence_after();
   if (warp == kMmaWarp) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)g.tmem_cols));
+  }
+}
+
+// Staged test-matrix blocks of sketch (side, s): block (v, h), h < H, holds the
+// 128 rows v + hstride (first + 128 h + k) (column side) or 128 h + k + n1 v
+// (row side), k = 0..127, as the BF16 K-major core-matrix image the MMA reads
+// (the same layout and rounding the RNG warps produce).
+__global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, int H) {
+  const SkTc sk = colside ? g.col[s] : g.row[s];
+  const int qps = g.ell / 4;
+  const int64_t blkB = (int64_t)(g.ell / 8) * kS4;
+  const int64_t total = nv * H * 16 * qps * 8;
+  char* tab = reinterpret_cast<char*>(g.ws) + sk.tab;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r8 = (int)(e & 7);
+    int64_t rest = e >> 3;
+    const int q = (int)(rest % qps);
+    rest /= qps;
+    const int kg = (int)(rest & 15);
+    rest >>= 4;
+    const int h = (int)(rest % H);
+    const int64_t v = rest / H;
+    const int64_t k = 128 * h + 8 * kg + r8;
+    const uint64_t row = colside ? (uint64_t)(v + sk.hstride * (g.first + k)) : (uint64_t)(k + g.n1 * v);
+    const float4 z = normals4_f32(g.seed, (uint32_t)sk.sid, row, (uint32_t)q);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    char* blk = tab + (v * H + h) * blkB;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * q + u;
+      *reinterpret_cast<__nv_bfloat16*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          __float2bfloat16_rn(zz[u]);
+    }
   }
 }
 
@@ -841,7 +915,7 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
     if (d.width != ell) return false;
-    SkTc t{d.rows, d.off, d.wdiv, d.hstride, d.stream_id, 0};
+    SkTc t{d.rows, d.off, d.wdiv, d.hstride, -1, d.stream_id, 0};
     if (d.type == SK_COL) {
       if (nL >= 4) return false;
       g.col[nL++] = t;
@@ -884,6 +958,36 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   g.ell = ell;
   g.nL = nL;
   g.nR = nR;
+  // Test-matrix blocks whose rows do not depend on the plane (column sketches
+  // with wdiv > 1: rows depend on w / wdiv only; row sketches with wdiv < W:
+  // on w % wdiv only) are generated once per launch into the staging area and
+  // copied per plane; the others are generated per plane.
+  {
+    const int64_t hd = (std::min<int64_t>(it.n[it.d - 1], 256) + 127) / 128;
+    const int64_t blk = (int64_t)((ell + 7) / 8) * kS4;
+    int64_t cur = it.off_tctab * 8;
+    const bool staged = it.tctab_doubles > 0 && ell % 8 == 0;
+    g.tab_tx = 0;
+    for (int s = 0; s < nL; ++s) {
+      if (staged && g.col[s].wdiv > 1) {
+        g.col[s].tab = cur;
+        cur += (g.W / g.col[s].wdiv) * hd * blk;
+        g.tab_tx += (uint32_t)(g.H4 * blk);
+      } else {
+        g.genL[g.ngenL++] = s;
+      }
+    }
+    for (int s = 0; s < nR; ++s) {
+      if (staged && g.row[s].wdiv < g.W) {
+        g.row[s].tab = cur;
+        cur += g.row[s].wdiv * g.H1 * blk;
+        g.tab_tx += (uint32_t)(g.H1 * blk);
+      } else {
+        g.genR[g.ngenR++] = s;
+      }
+    }
+    if (cur > (it.off_tctab + it.tctab_doubles) * 8 && g.tab_tx) return false;
+  }
   g.NL = NL;
   g.NR = NR;
   g.seed = it.seed;
@@ -1101,6 +1205,17 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
     attr_set = true;
   }
   if (!tc_kernel_launchable()) return launch_sketch_mma(P, item, X, first, count, ws, st);
+  for (int side = 0; side < 2; ++side)
+    for (int s = 0; s < (side ? g.nR : g.nL); ++s) {
+      const tc::SkTc& sk = side ? g.row[s] : g.col[s];
+      if (sk.tab < 0) continue;
+      const int64_t nv = side ? sk.wdiv : g.W / sk.wdiv;
+      const int H = side ? g.H1 : g.H4;
+      const int64_t total = nv * H * 16 * (g.ell / 4) * 8;
+      const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8 * device_sm_count());
+      count_launch();
+      tc::tc_table_kernel<<<blocks, 256, 0, st>>>(g, side ? 0 : 1, s, nv, H);
+    }
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
