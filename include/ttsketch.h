@@ -162,6 +162,27 @@ tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_la
 tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
                             tt_stream_t stream);
 
+/* tt_pstt2 without a caller workspace (the paper has no counterpart; this is
+ * a library convenience).  For callers that cannot allocate device memory
+ * where they call: the workspace is a fixed 32 MiB array inside this library,
+ * one per device, so the call allocates nothing.  A plan whose workspace
+ * (tt_plan_sizes) exceeds 32 MiB is refused with TT_ERR_UNSUPPORTED before
+ * anything runs.  X, cores and ranks are as for tt_pstt2; status_dev, if not
+ * NULL, is a device int that receives the device status bits of the call:
+ * 1 = rank cap reached (TT_WARN_RANK_CAP), 2 = singular least-squares matrix
+ * (TT_ERR_RANK_DEFICIENT), 4 = a bounded wait gave up (TT_ERR_TIMEOUT);
+ * 0 = no condition.  Nothing has to be zeroed by the
+ * caller: the call clears the sketches and the status word itself.
+ * The first call on a device sets the array up (it looks up its address) and
+ * the first call with a plan sends that plan's tables into it with a
+ * host-synchronous copy; make those first calls before any stream capture.
+ * The array is shared by every call on the device: calls that can overlap
+ * (on different streams or host threads without ordering) race on it and give
+ * wrong results; order them.  The saved state stays in the array only until
+ * the next call, so tt_pstt2_backward is not available after this call. */
+tt_status tt_pstt2_noalloc(tt_plan_t plan, const void* X, double* cores, int* ranks, int* status_dev,
+                           tt_stream_t stream);
+
 /* Batched one-pass PSTT2: X_ptrs is a HOST array of `count` device pointers
  * (one tensor per item).  All items are sketched by one persistent launch and
  * finalized by batched launches; nothing synchronises, so the whole call can

@@ -62,6 +62,7 @@ _SIGS = {
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "tt_sketch_kernel_kind": (C.c_int, [_P, C.c_int64]),
     "tt_pstt2": (C.c_int, [_P, _P, _P, _P, _P, _P]),
+    "tt_pstt2_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "tt_pstt2_begin": (C.c_int, [_P, _P, _P]),
     "tt_pstt2_accumulate": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),
     "tt_pstt2_finalize": (C.c_int, [_P, _P, _P, _P, _P]),

@@ -116,6 +116,7 @@ constexpr int64_t kRankCopyOff = 64;
 
 // ---------------------------------------------------------------- host side
 struct Plan;
+void plan_forget_upload(Plan* p);
 const DevItem* plan_items_host(const Plan* p);
 
 // Kernel launchers (defined in the .cu files).

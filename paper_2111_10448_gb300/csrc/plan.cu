@@ -317,6 +317,10 @@ static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
 
 static Plan* as_plan(tt_plan_t p) { return reinterpret_cast<Plan*>(p); }
 
+// The next call re-sends the plan tables to its workspace (used when the same
+// workspace address may have held another plan's tables in between).
+void plan_forget_upload(Plan* p) { p->uploaded_ws = nullptr; }
+
 static tt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return TT_OK;
   if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return TT_ERR_NO_DEVICE;
