@@ -183,12 +183,36 @@ tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
 tt_status tt_pstt2_noalloc(tt_plan_t plan, const void* X, double* cores, int* ranks, int* status_dev,
                            tt_stream_t stream);
 
-/* Batched one-pass PSTT2: X_ptrs is a HOST array of `count` device pointers
- * (one tensor per item).  All items are sketched by one persistent launch and
- * finalized by batched launches; nothing synchronises, so the whole call can
- * be captured in a CUDA graph. */
+/* Batched one-pass PSTT2 of many independent tensors (one plan from
+ * tt_sketch_plan_batched; not in the paper).  X_ptrs is a HOST array of
+ * `count` device pointers, one tensor per item (at most 2048 items, all of one
+ * precision; TF32 / BF16 items need FP32 tensors).  The sketches of all items
+ * come from ONE persistent launch: CTAs take tiles of every tensor from a work
+ * counter in the workspace, the largest tensors first, with the launch shape
+ * of the plan (tt_plan_batch_config / tt_plan_autotune).  The bases and cores
+ * of all items are formed by launches that each cover every item.  The first
+ * call on a workspace sends the plan tables (host-synchronous); after that
+ * nothing synchronises with the host, so the call can be captured in a CUDA
+ * graph and replayed (the pointers in X_ptrs are fixed at capture). */
 tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores,
                            int* ranks, tt_stream_t stream);
+
+/* Launch shape of the batched sketch: ta = tile rows along i_1 (32 or 64;
+ * used by FP64 plans, TF32 / BF16 tiles are 64 rows), chunk = tiles a CTA
+ * takes from the work counter at a time (>= 1), ctas_per_sm = persistent CTAs
+ * per SM (1..32).  Host only. */
+tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_sm);
+
+/* Autotuner of the batched sketch (not in the paper): runs the batched
+ * decomposition of X_ptrs once, times the batched sketch launch for every
+ * candidate shape (ta in {32, 64} for FP64 plans, chunk in {1, 4, 16},
+ * ctas_per_sm in {2, 4, 8}; CUDA events on `stream`, the second of two runs
+ * each) and keeps the fastest in the plan, then runs the decomposition once
+ * more with it so that cores and ranks hold a valid result.  Synchronises;
+ * refused during stream capture (TT_ERR_STATE).  best_out (host, 3 ints, may
+ * be NULL) receives the chosen ta, chunk and ctas_per_sm. */
+tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores, int* ranks,
+                           tt_stream_t stream, int* best_out);
 
 /* ----------------------------------------------------------- backward */
 

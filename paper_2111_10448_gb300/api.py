@@ -104,6 +104,19 @@ class TTSketch:
                                          _stream(stream)), "tt_pstt2_batched")
         return self
 
+    def batch_config(self, ta=64, chunk=4, ctas_per_sm=4):
+        N.check(N.lib().tt_plan_batch_config(self.plan, int(ta), int(chunk), int(ctas_per_sm)),
+                "tt_plan_batch_config")
+
+    def autotune(self, Xs, stream=None):
+        """Pick the batched sketch launch shape by timing the candidates on Xs;
+        returns (ta, chunk, ctas_per_sm).  Leaves a valid decomposition."""
+        arr = (C.c_void_p * len(Xs))(*[x.data_ptr() for x in Xs])
+        best = (C.c_int * 3)()
+        N.check(N.lib().tt_plan_autotune(self.plan, arr, _ptr(self.ws), _ptr(self.cores), _ptr(self.ranks),
+                                         _stream(stream), best), "tt_plan_autotune")
+        return tuple(best)
+
     def backward(self, dcores, dX, stream=None):
         N.check(N.lib().tt_pstt2_backward(self.plan, _ptr(self.ws), _ptr(dcores), _ptr(dX), _stream(stream)),
                 "tt_pstt2_backward")

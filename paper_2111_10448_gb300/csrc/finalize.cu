@@ -375,7 +375,9 @@ __global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int L,
 
 // --------------------------------------------------------- one-pass middle
 // B = P_{d*}^T Omega_{d*}  (r x l), summed over row chunks with atomics.
-__global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item, const int* ranks) {
+// item < 0: batched launch, item = blockIdx.y
+__global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item_arg, const int* ranks) {
+  const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
   constexpr int CH = 32;
   __shared__ double Ps[CH * TT_MAXL];
   __shared__ double Gs[CH * (TT_MAXL + 1)];
@@ -413,7 +415,9 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
 }
 
 // QR of B^T (l x r) -> QB (l x r), RB (r x r); singular B is flagged.
-__global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item, const int* ranks) {
+// item < 0: batched launch, item = blockIdx.y
+__global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item_arg, const int* ranks) {
+  const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
   __shared__ double A[TT_MAXL * (TT_MAXL + 1)];
   __shared__ double beta[TT_MAXL], rdiag[TT_MAXL], red[32];
   const DevItem& it = ditems(wsb)[item];
@@ -465,7 +469,9 @@ __global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item, c
 }
 
 // H = S_{d*} QB RB^{-T}  (N_{d*} x rpad), one thread per row.
-__global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item, const int* ranks) {
+// item < 0: batched launch, item = blockIdx.y
+__global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item_arg, const int* ranks) {
+  const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
   __shared__ double QBs[TT_MAXL * TT_MAXL];
   __shared__ double RBs[TT_MAXL * TT_MAXL];
   const DevItem& it = ditems(wsb)[item];
@@ -635,6 +641,37 @@ __global__ void __launch_bounds__(kThreads) twopass_mid_kernel(char* wsb, const 
 
 cudaError_t launch_mid_b_mixed(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st);
 
+// Middle cores of every item of a batched plan; B was zeroed with the sketches.
+cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st) {
+  char* wsb = (char*)ws;
+  const int nitems = plan_num_items(&P);
+  const DevSketch* sks = plan_sketches_host(&P);
+  int64_t Mmax = 1, Nmax = 1;
+  for (int i = 0; i < nitems; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    Mmax = std::max(Mmax, sks[it.basis_of_k[it.ds]].rows);
+    Nmax = std::max(Nmax, it.N[it.ds]);
+  }
+  cudaError_t e;
+  if (plan_items_host(&P)[0].prec == TT_PREC_FP64) {
+    const unsigned gx = (unsigned)std::min<int64_t>((Mmax + 31) / 32, 64);
+    count_launch();
+    mid_b_kernel_f64<<<dim3(gx, (unsigned)nitems), kThreads, 0, st>>>(wsb, -1, ranks);
+    e = cudaGetLastError();
+  } else {
+    e = launch_mid_b_mixed_batched(P, ws, ranks, st);
+  }
+  if (e != cudaSuccess) return e;
+  count_launch();
+  mid_ls_kernel<<<dim3(1, (unsigned)nitems), kThreads, 0, st>>>(wsb, -1, ranks);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const unsigned gx = (unsigned)std::min<int64_t>((Nmax + 127) / 128, 64);
+  count_launch();
+  mid_h_kernel<<<dim3(gx, (unsigned)nitems), 128, 0, st>>>(wsb, -1, ranks);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st) {
   char* wsb = (char*)ws;
   const int max_lev = plan_max_lev(&P);
@@ -689,8 +726,12 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // one-pass middle cores
-  for (int i = 0; i < nitems; ++i) {
+  // one-pass middle cores (one launch per step over all items when batched)
+  if (nitems > 1) {
+    e = launch_finalize_mid_batched(P, ws, ranks, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < nitems && nitems == 1; ++i) {
     const DevItem& it = plan_items_host(&P)[i];
     if (it.passes != 1) continue;
     const int rp = it.rpad[it.ds];

@@ -91,7 +91,6 @@ struct DevItem {
   int64_t off_Lall[TT_MAXD + 1];  // left interfaces L_k, k = 1..d-1 (N_k x rpad_k)
   int64_t off_Rall[TT_MAXD + 2];  // right interfaces Rt_k, k = 2..d (rpad_{k-1} x M_{k-1})
   int64_t off_Y;            // max_k N_k x rpad_k
-  const void* X;            // batched: device pointer of this item's tensor (set per call)
   int64_t off_tctab;        // plane kernel: staged test-matrix blocks shared by many planes
   int64_t tctab_doubles;    // its size (0 when the plane kernel cannot serve the item)
 };
@@ -107,6 +106,24 @@ struct DevTables {
   int64_t off_items, off_sketches;   // byte offsets from ws base
   int64_t off_tasks[kMaxLev];        // byte offsets of per-level task arrays
   int ntasks[kMaxLev];
+  // batched sketch: item visiting order (largest first), the first tile of
+  // each item in that order (nitems + 1, written per call) and the work counter
+  int64_t off_border, off_bprefix, off_bcounter;
+};
+
+// Batched sketch launch: the workspace and one tensor pointer per item (by
+// value, so that a captured launch needs nothing uploaded).
+constexpr int kMaxBatchItems = 2048;
+struct BatchLaunch {
+  char* wsb;
+  int64_t chunk;                       // tiles taken from the counter at a time
+  const void* X[kMaxBatchItems];
+};
+// Launch shape of the batched sketch (chosen by tt_plan_autotune).
+struct BatchCfg {
+  int ta;            // tile rows along i_1: 32 or 64
+  int chunk;         // tiles per counter grab
+  int ctas_per_sm;   // persistent CTAs per SM
 };
 
 // Byte offset of the status word inside the workspace, and of a copy of the
@@ -118,6 +135,7 @@ constexpr int64_t kRankCopyOff = 64;
 struct Plan;
 void plan_forget_upload(Plan* p);
 const DevItem* plan_items_host(const Plan* p);
+int plan_num_items(const Plan* p);
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t first, int64_t count,
@@ -135,7 +153,15 @@ cudaError_t launch_reconstruct_backward(const Plan& P, int item, const double* c
                                         cudaStream_t st);
 cudaError_t launch_backward(const Plan& P, int item, const double* dcores, void* dX, void* ws,
                             cudaStream_t st);
-cudaError_t launch_sketch_batched(const Plan& P, void* ws, cudaStream_t st);
+cudaError_t launch_sketch_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
+                                  cudaStream_t st);
+cudaError_t launch_sketch_f64_batched(const BatchLaunch& b, const BatchCfg& cfg, int lmax, cudaStream_t st);
+cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, cudaStream_t st);
+int64_t batched_tiles_f64(int64_t W, int64_t n1, int64_t cnt, int ta);
+int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int ta);
+cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
+cudaError_t launch_batch_zero(const Plan& P, void* ws, cudaStream_t st);
+cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
 
 int device_sm_count();
 void count_launch(int n = 1);

@@ -32,6 +32,7 @@ struct Plan {
   std::vector<char> slab_seen;
   bool begun = false;
   bool forward_done = false;
+  BatchCfg bcfg{64, 4, 4};  // batched sketch launch shape (tt_plan_autotune)
 };
 
 static constexpr int64_t kTableOff = 256;  // bytes
@@ -264,6 +265,19 @@ static void build_blob(Plan& P) {
     t.ntasks[L] = (int)P.tasks[L].size();
     off += align_up((int64_t)(sizeof(Task) * P.tasks[L].size()), 64);
   }
+  // batched sketch: items largest first (entries x sketches; ties by index)
+  std::vector<int> order(P.items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const DevItem &A = P.items[(size_t)a], &B = P.items[(size_t)b];
+    return A.N[A.d] * A.nsk > B.N[B.d] * B.nsk;
+  });
+  t.off_border = off;
+  off += align_up((int64_t)(sizeof(int) * order.size()), 64);
+  t.off_bprefix = off;
+  off += align_up((int64_t)(sizeof(int64_t) * (order.size() + 1)), 64);
+  t.off_bcounter = off;
+  off += 64;
   P.blob.assign((size_t)(off - kTableOff), 0);
   auto put = [&](int64_t at, const void* src, size_t n) {
     if (n) std::memcpy(P.blob.data() + (at - kTableOff), src, n);
@@ -272,6 +286,7 @@ static void build_blob(Plan& P) {
   put(t.off_items, P.items.data(), sizeof(DevItem) * P.items.size());
   put(t.off_sketches, P.sketches.data(), sizeof(DevSketch) * P.sketches.size());
   for (int L = 0; L < kMaxLev; ++L) put(t.off_tasks[L], P.tasks[L].data(), sizeof(Task) * P.tasks[L].size());
+  put(t.off_border, order.data(), sizeof(int) * order.size());
 }
 
 static tt_status build_all(Plan& P, const tt_problem* probs, int count, int64_t base_doubles) {
@@ -311,6 +326,10 @@ static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
     return st != TT_OK ? st : TT_ERR_INVALID_ARG;
   }
   if (count == 1) P->slab_seen.assign((size_t)P->items[0].n[P->items[0].d - 1], 0);
+  // batched default: tiles as tall as the largest n_1 needs (32 or 64 rows)
+  int64_t n1max = 1;
+  for (const DevItem& it : P->items) n1max = std::max(n1max, it.n[0]);
+  P->bcfg = BatchCfg{n1max <= 32 ? 32 : 64, 4, 4};
   *out = reinterpret_cast<tt_plan_t>(P);
   return TT_OK;
 }
@@ -518,31 +537,103 @@ tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* 
   return TT_OK;
 }
 
+static tt_status batched_check(const Plan* P, const void* const* X_ptrs) {
+  const DevItem& i0 = P->items[0];
+  if (P->items.size() > (size_t)kMaxBatchItems) return TT_ERR_UNSUPPORTED;
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    const DevItem& it = P->items[i];
+    if (it.passes != 1 || it.prec != i0.prec) return TT_ERR_UNSUPPORTED;
+    if (it.prec != TT_PREC_FP64 && it.x_f64) return TT_ERR_UNSUPPORTED;
+    if (!X_ptrs[i]) return TT_ERR_INVALID_ARG;
+  }
+  return TT_OK;
+}
+
+static tt_status batched_run(Plan& P, const void* const* X_ptrs, const BatchCfg& cfg, void* ws, double* cores,
+                             int* ranks, cudaStream_t st) {
+  tt_status s = ensure_uploaded(P, ws, st);
+  if (s != TT_OK) return s;
+  s = cuda_status(launch_batch_zero(P, ws, st));
+  if (s != TT_OK) return s;
+  s = cuda_status(launch_sketch_batched(P, X_ptrs, cfg, ws, st));
+  if (s != TT_OK) return s;
+  return cuda_status(launch_finalize(P, ws, cores, ranks, st));
+}
+
 tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores,
                            int* ranks, tt_stream_t stream) {
   Plan* P = as_plan(plan);
   if (!P || !X_ptrs || !ws || !cores || !ranks) return TT_ERR_INVALID_ARG;
-  for (const DevItem& it : P->items)
-    if (it.passes != 1) return TT_ERR_UNSUPPORTED;
-  cudaStream_t st = (cudaStream_t)stream;
-  for (size_t i = 0; i < P->items.size(); ++i) {
-    if (!X_ptrs[i]) return TT_ERR_INVALID_ARG;
-    P->items[i].X = X_ptrs[i];
-  }
-  // item pointers live in the device tables: rebuild and (re)upload
-  build_blob(*P);
-  P->uploaded_ws = nullptr;
-  tt_status s = ensure_uploaded(*P, ws, st);
+  tt_status s = batched_check(P, X_ptrs);
   if (s != TT_OK) return s;
-  for (size_t i = 0; i < P->items.size(); ++i) {
-    s = zero_sketches(*P, (int)i, ws, st);
-    if (s != TT_OK) return s;
-  }
-  s = cuda_status(launch_sketch_batched(*P, ws, st));
-  if (s != TT_OK) return s;
-  s = cuda_status(launch_finalize(*P, ws, cores, ranks, st));
+  s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, (cudaStream_t)stream);
   if (s != TT_OK) return s;
   P->forward_done = true;
+  return TT_OK;
+}
+
+tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores, int* ranks,
+                           tt_stream_t stream, int* best_out) {
+  Plan* P = as_plan(plan);
+  if (!P || !X_ptrs || !ws || !cores || !ranks) return TT_ERR_INVALID_ARG;
+  tt_status s = batched_check(P, X_ptrs);
+  if (s != TT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return TT_ERR_STATE;
+  s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, st);  // warm-up (uploads the tables)
+  if (s != TT_OK) return s;
+  const bool f64 = P->items[0].prec == TT_PREC_FP64;
+  std::vector<BatchCfg> cands;
+  for (int ta : {32, 64}) {
+    if (!f64 && ta == 32) continue;
+    for (int chunk : {1, 4, 16})
+      for (int cps : {2, 4, 8}) cands.push_back(BatchCfg{ta, chunk, cps});
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return TT_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int best_i = -1;
+  for (size_t c = 0; c < cands.size() && s == TT_OK; ++c) {
+    float acc = 0.0f;
+    for (int rep = 0; rep < 2 && s == TT_OK; ++rep) {
+      s = cuda_status(launch_batch_zero(*P, ws, st));
+      if (s == TT_OK) s = cuda_status(cudaEventRecord(e0, st));
+      if (s == TT_OK) s = cuda_status(launch_sketch_batched(*P, X_ptrs, cands[c], ws, st));
+      if (s == TT_OK) s = cuda_status(cudaEventRecord(e1, st));
+      if (s == TT_OK) s = cuda_status(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      if (s == TT_OK) s = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1) acc = ms;  // the second run (the first warms the launch shape)
+    }
+    if (s == TT_OK && acc < best) {
+      best = acc;
+      best_i = (int)c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != TT_OK) return s;
+  P->bcfg = cands[(size_t)best_i];
+  if (best_out) {
+    best_out[0] = P->bcfg.ta;
+    best_out[1] = P->bcfg.chunk;
+    best_out[2] = P->bcfg.ctas_per_sm;
+  }
+  // leave a complete decomposition with the chosen shape in the buffers
+  s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, st);
+  if (s == TT_OK) P->forward_done = true;
+  return s;
+}
+
+tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_sm) {
+  Plan* P = as_plan(plan);
+  if (!P || (ta != 32 && ta != 64) || chunk < 1 || ctas_per_sm < 1 || ctas_per_sm > 32) return TT_ERR_INVALID_ARG;
+  P->bcfg = BatchCfg{ta, chunk, ctas_per_sm};
   return TT_OK;
 }
 

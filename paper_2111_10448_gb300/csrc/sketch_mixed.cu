@@ -33,7 +33,9 @@ __global__ void test_matrix_mixed_kernel(uint64_t seed, int sid, int64_t row0, i
 constexpr int64_t kTableOffB = 256;
 
 // B = P_{d*}^T Omega^_{d*}, Omega^ = the rounded FP32 entries the sketch used.
-__global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item, const int* ranks) {
+// item < 0: batched launch, item = blockIdx.y
+__global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_arg, const int* ranks) {
+  const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
   constexpr int CH = 32;
   __shared__ double Ps[CH * TT_MAXL];
   __shared__ double Gs[CH * (TT_MAXL + 1)];
@@ -81,6 +83,18 @@ cudaError_t launch_test_matrix_mixed(uint64_t seed, int sid, int64_t row0, int64
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * device_sm_count()));
   count_launch();
   test_matrix_mixed_kernel<<<grid, 256, 0, st>>>(seed, sid, row0, nrows, ncols, prec, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st) {
+  int64_t Mmax = 1;
+  for (int i = 0; i < plan_num_items(&P); ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    Mmax = std::max(Mmax, plan_sketches_host(&P)[it.basis_of_k[it.ds]].rows);
+  }
+  const unsigned gx = (unsigned)std::min<int64_t>((Mmax + 31) / 32, 64);
+  count_launch();
+  mid_b_kernel_mixed<<<dim3(gx, (unsigned)plan_num_items(&P)), 256, 0, st>>>((char*)ws, -1, ranks);
   return cudaGetLastError();
 }
 
@@ -186,8 +200,8 @@ __device__ __forceinline__ void tile_mma(int prec, const float* Gs, int LDG, con
   }
 }
 
-__global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
-  extern __shared__ float fsm[];
+// One tile (gTA rows of i_1 x gTB columns of i_d of plane w) into every sketch.
+__device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
   constexpr int LDX = gTA + 1;
   float* Xh = fsm;                  // LDX x gTB  (X[a + LDX b])
   float* Xl = Xh + LDX * gTB;
@@ -195,8 +209,7 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nA = (a.n1 + gTA - 1) / gTA;
   const int64_t nB = (a.cnt + gTB - 1) / gTB;
-  const int64_t total = a.W * nA * nB;
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+  {
     const int64_t w = item / (nA * nB);
     const int64_t rem = item - w * nA * nB;
     const int64_t bb = rem / nA, ab = rem - bb * nA;
@@ -254,6 +267,77 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
         }
       }
     }
+  }
+}
+
+
+__global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
+  extern __shared__ float fsm[];
+  const int64_t total = a.W * ((a.n1 + gTA - 1) / gTA) * ((a.cnt + gTB - 1) / gTB);
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) mma_tile(a, item, fsm);
+}
+
+// Batched form (same scheduling as the FP64 batched kernel): persistent CTAs
+// take `chunk` consecutive tiles of the cost-ordered tile sequence at a time.
+__global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const BatchLaunch b) {
+  extern __shared__ float fsm[];
+  __shared__ MixArgs sa;
+  __shared__ int64_t s_base;
+  __shared__ int s_pos;
+  const DevTables& T = *reinterpret_cast<const DevTables*>(b.wsb + kTableOffB);
+  const DevItem* items = reinterpret_cast<const DevItem*>(b.wsb + T.off_items);
+  const DevSketch* sks = reinterpret_cast<const DevSketch*>(b.wsb + T.off_sketches);
+  const int* order = reinterpret_cast<const int*>(b.wsb + T.off_border);
+  const int64_t* prefix = reinterpret_cast<const int64_t*>(b.wsb + T.off_bprefix);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(b.wsb + T.off_bcounter);
+  const int64_t total = prefix[T.nitems];
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_base = (int64_t)atomicAdd(counter, (unsigned long long)b.chunk);
+      int lo = 0, hi = T.nitems - 1;
+      if (s_base < total) {
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (prefix[mid] <= s_base) lo = mid;
+          else hi = mid - 1;
+        }
+      }
+      s_pos = lo;
+    }
+    __syncthreads();
+    const int64_t base = s_base;
+    int pos = s_pos;
+    if (base >= total) break;
+    const int64_t end = imin64(base + b.chunk, total);
+    for (int64_t t = base; t < end; ++t) {
+      while (prefix[pos + 1] <= t) ++pos;
+      const int it_idx = order[pos];
+      if (it_idx != cur) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const DevItem& it = items[it_idx];
+          sa.X = reinterpret_cast<const float*>(b.X[it_idx]);
+          sa.ws = reinterpret_cast<double*>(b.wsb);
+          sa.n1 = it.n[0];
+          sa.cnt = it.n[it.d - 1];
+          sa.first = 0;
+          sa.W = it.W;
+          sa.Nd1 = it.N[it.d - 1];
+          sa.seed = it.seed;
+          sa.nsk = it.nsk;
+          sa.prec = it.prec;
+          for (int s = 0; s < it.nsk; ++s) {
+            const DevSketch& d = sks[it.sk0 + s];
+            sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, 0};
+          }
+        }
+        __syncthreads();
+        cur = it_idx;
+      }
+      mma_tile(sa, t - prefix[pos], fsm);
+    }
+    __syncthreads();
   }
 }
 
@@ -1172,6 +1256,24 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   const int64_t grid = std::min<int64_t>(total, (int64_t)device_sm_count() * 8);
   count_launch();
   sketch_mma_kernel<<<(unsigned)grid, gThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int) {
+  return W * ((n1 + gTA - 1) / gTA) * ((cnt + gTB - 1) / gTB);
+}
+
+cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, cudaStream_t st) {
+  const size_t smem = sizeof(float) * (2 * (gTA + 1) * gTB + (size_t)gTA * (TT_MAXL + 4));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sketch_mma_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  count_launch();
+  sketch_mma_batched_kernel<<<cfg.ctas_per_sm * device_sm_count(), gThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

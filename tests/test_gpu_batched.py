@@ -1,0 +1,115 @@
+"""Batched form: tensors of uneven order, size and rank sketched by one
+persistent launch and finalized together; per-item parity with the oracle,
+equality with single-tensor plans, CUDA-graph capture and the autotuner.
+
+Batch recipe (uneven shapes as in the batched workload: d in {3..6},
+n in {8..32} clamped so that n^d stays under the entry cap, ranks in {2..16}
+per bond, 1e-7 relative noise); item b uses data seed 1000 + b and
+test-matrix seed 1000 + b; eps = 1e-5, p = 5, rmax = 16."""
+import numpy as np
+import pytest
+import torch
+
+import ttinputs as ti
+from oracle import pstt2 as OP, tt as OT
+from paper_2111_10448_gb300 import TTSketch
+
+EPS, P, RMAX = 1e-5, 5, 16
+
+
+def make_batch(count, cap, seed=5, dtype=np.float64):
+    specs = ti.batch_specs(count=count, seed=seed, cap=cap)
+    xs, probs = [], []
+    for b, (dims, r) in enumerate(specs):
+        xs.append(ti.random_tt(dims, r, seed=1000 + b, noise=1e-7, dtype=dtype))
+        probs.append(dict(dims=dims, eps=EPS, rmax=RMAX, p=P, seed=1000 + b))
+    return xs, probs
+
+
+def run_batched(xs, probs, prec="fp64", x_dtype=torch.float64):
+    t = TTSketch(None, batch=probs, x_dtype=x_dtype, prec=prec)
+    dev = [torch.tensor(x, dtype=x_dtype, device="cuda") for x in xs]
+    t.batched(dev)
+    torch.cuda.synchronize()
+    return t, dev
+
+
+def full(cores):
+    return OT.tt_full([np.asarray(G) for G in cores])
+
+
+@pytest.mark.gpu
+def test_batched_fp64_matches_oracle_per_item():
+    xs, probs = make_batch(12, cap=20_000)
+    t, _ = run_batched(xs, probs)
+    st, ranks = t.status()
+    assert st in (0, 7)
+    worst = 0.0
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        o = OP.pstt2(x, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
+        got = full(t.core_list(b))
+        err = np.linalg.norm(got - OT.tt_full(o["cores"])) / np.linalg.norm(x)
+        worst = max(worst, err)
+        assert err <= 1e-10, (b, pr["dims"], err)
+    print(f"batched FP64 vs oracle: worst {worst:.2e} over {len(xs)} items")
+
+
+@pytest.mark.gpu
+def test_batched_bf16_within_10eps_of_oracle():
+    xs, probs = make_batch(10, cap=30_000, seed=7, dtype=np.float32)
+    t, _ = run_batched(xs, probs, prec="bf16", x_dtype=torch.float32)
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        x64 = x.astype(np.float64)
+        o = OP.pstt2(x64, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
+        got = full(t.core_list(b))
+        err = np.linalg.norm(got - OT.tt_full(o["cores"])) / np.linalg.norm(x64)
+        assert err <= 10 * EPS, (b, pr["dims"], err)
+
+
+@pytest.mark.gpu
+def test_batched_equals_single_tensor_plans():
+    xs, probs = make_batch(24, cap=200_000, seed=11)
+    t, dev = run_batched(xs, probs)
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float64)
+        s.pstt2(dev[b])
+        torch.cuda.synchronize()
+        a, c = full(t.core_list(b)), full(s.core_list(0))
+        assert np.linalg.norm(a - c) <= 1e-11 * np.linalg.norm(x), b
+
+
+@pytest.mark.gpu
+def test_batched_graph_capture_replays():
+    xs, probs = make_batch(16, cap=100_000, seed=13)
+    t, dev = run_batched(xs, probs)          # first call: tables go to the workspace
+    ref_cores, ref_ranks = t.cores.clone(), t.ranks.clone()
+    refs = [full(t.core_list(b)) for b in range(len(xs))]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        t.batched(dev, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        t.cores.fill_(float("nan"))
+        t.ranks.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(t.ranks, ref_ranks)
+        for b in range(len(xs)):
+            got = full(t.core_list(b))
+            assert np.linalg.norm(got - refs[b]) <= 1e-11 * np.linalg.norm(refs[b]), b
+    del ref_cores
+
+
+@pytest.mark.gpu
+def test_autotuner_picks_a_candidate_and_keeps_results():
+    xs, probs = make_batch(32, cap=300_000, seed=17)
+    t, dev = run_batched(xs, probs)
+    refs = [full(t.core_list(b)) for b in range(len(xs))]
+    best = t.autotune(dev)
+    assert best[0] in (32, 64) and best[1] in (1, 4, 16) and best[2] in (2, 4, 8), best
+    for b in range(len(xs)):
+        assert np.linalg.norm(full(t.core_list(b)) - refs[b]) <= 1e-11 * np.linalg.norm(refs[b]), b
+    t.batched(dev)
+    torch.cuda.synchronize()
+    for b in range(len(xs)):
+        assert np.linalg.norm(full(t.core_list(b)) - refs[b]) <= 1e-11 * np.linalg.norm(refs[b]), b
+    print("autotuned batched launch shape (ta, chunk, ctas/SM):", best)
