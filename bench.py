@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
     return ap.parse_args()
 
 
@@ -136,14 +138,14 @@ def traffic_record(kernel_tag):
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_sample(steps=1):
+def cpu_sample(steps=1, n=128):
     """The FP64 oracle as it stands, on a bounded sample of the workload: the
-    same Hilbert-type function at d = 4, n = 128 (268M entries), same eps, p,
-    rmax, one-pass.  Returns entries/s and the sample description."""
+    same Hilbert-type function at d = 4 with a smaller n (n = 128: 268M
+    entries), same eps, p, rmax, one-pass.  Returns entries/s, the threads
+    used, the sample description and the per-step times."""
     import numpy as np
     import ttinputs as ti
     from oracle import pstt2 as OP
-    n = 128
     dims = [n] * 4
     x = ti.hilbert_type(dims, np.float32).astype(np.float64)
     times = []
@@ -162,25 +164,113 @@ def cpu_sample(steps=1):
         f"p=10, rmax=6; entries/s = entries / wall time"), times
 
 
+def reference_sample_n(steps, budget_s=150.0):
+    """Largest sample size n in {32, 48, 64, 96, 128} whose `steps` oracle
+    runs fit the time budget (cost scales with n^4; measured at n = 32)."""
+    t32 = cpu_sample(1, 32)[3][0]
+    best = 32
+    for n in (48, 64, 96, 128):
+        if t32 * (n / 32) ** 4 * steps <= budget_s:
+            best = n
+    return best
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     steps = max(1, a.steps)
+    n = reference_sample_n(steps + min(a.warmup, 1))
     for _ in range(min(a.warmup, 1)):
-        cpu_sample(1)
-    v, cores, sample, times = cpu_sample(steps)
+        cpu_sample(1, n)
+    v, cores, sample, times = cpu_sample(steps, n)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "entries/s", "n_gpus": a.gpus,
             "steps": steps, "warmup": a.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "Hilbert-type d=4 n=256 FP32 (bounded sample: n=128)",
-                                            "sample": sample},
+            "data": "synthetic",
+            "config": {"workload": f"Hilbert-type d=4 n=256 FP32 (bounded sample per step: n={n})",
+                       "sample": sample},
             "cpu_baseline": {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- GPU arm
+def batched_inputs(count, dev, seed=5):
+    """The batched workload on the device: `count` FP32 tensors, d in {3..6},
+    n in {8..32} (n^d <= 2e6), random N(0,1) TT cores of ranks in {2..16}
+    (data seed 1000 + b), plus 1e-7 relative Gaussian noise; eps = 1e-5,
+    p = 5, rmax = 16, test-matrix seed 1000 + b."""
+    import numpy as np
+    import torch
+    import ttinputs as ti
+    xs, probs = [], []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    for b, (dims, r) in enumerate(ti.batch_specs(count=count, seed=seed, cap=2_000_000)):
+        L = torch.ones(1, 1, dtype=torch.float64, device=dev)
+        for G in ti.random_tt_cores(dims, r, seed=1000 + b):
+            a_, n_, c_ = G.shape
+            Gd = torch.from_numpy(np.asfortranarray(G).reshape(a_, n_ * c_, order="F")).to(dev)
+            L = (L @ Gd).T.reshape(c_, n_, -1).permute(1, 2, 0).reshape(-1, c_)  # rows u + N i
+        x = L[:, 0]
+        e = torch.randn(x.numel(), dtype=torch.float64, device=dev, generator=gen)
+        x = x + e * (1e-7 * x.norm() / e.norm())
+        xs.append(x.to(torch.float32).contiguous())
+        probs.append(dict(dims=dims, eps=1e-5, rmax=16, p=5, seed=1000 + b))
+    return xs, probs
+
+
+def run_batched(a, dev, P, stream):
+    """Batched workload: one plan, one persistent sketch launch over all
+    tensors + batched finalize, per precision; autotuned launch shape."""
+    import numpy as np
+    import torch
+    import ttinputs as ti
+    xs, probs = batched_inputs(a.batch, dev)
+    ntot = sum(x.numel() for x in xs)
+    out = {"workload": f"{a.batch} FP32 tensors, d in 3..6, n in 8..32 (n^d <= 2e6), TT ranks 2..16 + 1e-7 noise; "
+                       f"eps=1e-5 p=5 rmax=16; {ntot} entries ({ntot * 4 / 1e9:.2f} GB)", "entries": ntot}
+    for prec in ("bf16", "fp64"):
+        t = P.TTSketch(None, batch=probs, x_dtype=torch.float32, prec=prec)
+        best = t.autotune(xs, stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, min(a.steps, 10))
+        t.batched(xs, stream)
+        e0.record(stream)
+        for _ in range(k):
+            t.batched(xs, stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        # accuracy on a sample of items (host contraction of the cores)
+        errs = []
+        for b in range(0, len(xs), max(1, len(xs) // 8)):
+            xt = ti.contract_tt(t.core_list(b))
+            xh = xs[b].double().cpu().numpy()
+            errs.append(float(np.linalg.norm(xt - xh) / np.linalg.norm(xh)))
+        out[prec] = {"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+                     "launch_shape": {"ta": best[0], "chunk": best[1], "ctas_per_sm": best[2]},
+                     "max_rel_err_sampled": max(errs), "items_sampled": len(errs)}
+        del t
+    return out
+
+
+def whole_job(ms_local, units_local, world, device=None):
+    """Whole-job rate over `world` ranks: the step time is the MAX over ranks,
+    the units are the SUM over ranks.  Returns (ms, units, units/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms_local, units_local = float(t.item()), float(u.item())
+    return ms_local, units_local, units_local / (ms_local * 1e-3)
+
+
 def run_gpu(a):
     import torch
     import paper_2111_10448_gb300 as P
@@ -235,20 +325,19 @@ def run_gpu(a):
     time.sleep(0.3)
     l0 = L.tt_kernel_launches()
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     e0.record(stream)
     for i in range(a.steps):
         step(evs[i])
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     l1 = L.tt_kernel_launches()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    if world > 1:
-        tt_ = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt_.item())
+    ms, _, value = whole_job(e0.elapsed_time(e1) / a.steps, ntot, world, dev)
     sketch_ms = statistics.mean(s.elapsed_time(e) for s, e in evs)
-    value = world * ntot / (ms * 1e-3)
     st, ranks = t.status(stream)
 
     # accuracy of this run: ||X - X~|| / ||X|| on the device
@@ -329,6 +418,9 @@ def run_gpu(a):
                 "traffic": traffic_record(f"sketch_{a.prec}_{n}x{m}x{m}x{n}"), "peak_kind": f"{peak_kind} hbm_gbs",
                 "kernel_ms": sketch_ms, "algorithmic_bytes": ntot * 4}
 
+    if not a.no_batched:
+        out["batched"] = run_batched(a, dev, P, stream)
+
     cpu = None
     if rank == 0 and not a.no_cpu:
         v, cores, sample, _ = cpu_sample(1)
@@ -345,7 +437,8 @@ def run_gpu(a):
                            "ranks": ranks, "status": st, "rel_err_vs_X": rel_err,
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": out.get("e2e"),
-                "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu")}
+                "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
+                "batched": out.get("batched")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
