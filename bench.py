@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched workload (profiling); prints its own JSON line")
+    ap.add_argument("--batch-prec", default="bf16,fp64", help="precisions of the batched workload")
+    ap.add_argument("--batch-shape", default="",
+                    help="fixed launch shape 'ta,chunk,ctas_per_sm' instead of the autotuner")
     return ap.parse_args()
 
 
@@ -231,9 +236,13 @@ def run_batched(a, dev, P, stream):
     ntot = sum(x.numel() for x in xs)
     out = {"workload": f"{a.batch} FP32 tensors, d in 3..6, n in 8..32 (n^d <= 2e6), TT ranks 2..16 + 1e-7 noise; "
                        f"eps=1e-5 p=5 rmax=16; {ntot} entries ({ntot * 4 / 1e9:.2f} GB)", "entries": ntot}
-    for prec in ("bf16", "fp64"):
+    for prec in a.batch_prec.split(","):
         t = P.TTSketch(None, batch=probs, x_dtype=torch.float32, prec=prec)
-        best = t.autotune(xs, stream)
+        if a.batch_shape:
+            best = tuple(int(v) for v in a.batch_shape.split(","))
+            t.batch_config(*best)
+        else:
+            best = t.autotune(xs, stream)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k = max(3, min(a.steps, 10))
@@ -269,6 +278,16 @@ def whole_job(ms_local, units_local, world, device=None):
         dist.all_reduce(u, op=dist.ReduceOp.SUM)
         ms_local, units_local = float(t.item()), float(u.item())
     return ms_local, units_local, units_local / (ms_local * 1e-3)
+
+
+def run_batched_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = run_batched(a, dev, P, stream)
+    print(json.dumps({"batched": out}), flush=True)
 
 
 def run_gpu(a):
@@ -448,6 +467,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.batched_only:
+        run_batched_only(a)
     else:
         run_gpu(a)
 

@@ -16,22 +16,29 @@ namespace {
 constexpr int64_t kTableOffB = 256;
 
 // First tile of every item in visiting order, for tiles of ta x tb entries of
-// each plane; resets the work counter and the status word.
-__global__ void batch_prep_kernel(char* wsb, int ta, int tb) {
+// each plane; resets the work counter and the status word.  One block: the
+// tile counts are loaded in parallel, then scanned in shared memory.
+__global__ void __launch_bounds__(1024) batch_prep_kernel(char* wsb, int ta, int tb) {
+  __shared__ int64_t cnt[kMaxBatchItems];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const DevItem* items = reinterpret_cast<const DevItem*>(wsb + T.off_items);
   const int* order = reinterpret_cast<const int*>(wsb + T.off_border);
   int64_t* prefix = reinterpret_cast<int64_t*>(wsb + T.off_bprefix);
-  int64_t acc = 0;
-  for (int i = 0; i < T.nitems; ++i) {
-    prefix[i] = acc;
+  for (int i = threadIdx.x; i < T.nitems; i += blockDim.x) {
     const DevItem& it = items[order[i]];
-    acc += it.W * ((it.n[0] + ta - 1) / ta) * ((it.n[it.d - 1] + tb - 1) / tb);
+    cnt[i] = it.W * ((it.n[0] + ta - 1) / ta) * ((it.n[it.d - 1] + tb - 1) / tb);
   }
-  prefix[T.nitems] = acc;
-  *reinterpret_cast<unsigned long long*>(wsb + T.off_bcounter) = 0ull;
-  *reinterpret_cast<int*>(wsb + kStatusOff) = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int i = 0; i < T.nitems; ++i) {
+      prefix[i] = acc;
+      acc += cnt[i];
+    }
+    prefix[T.nitems] = acc;
+    *reinterpret_cast<unsigned long long*>(wsb + T.off_bcounter) = 0ull;
+    *reinterpret_cast<int*>(wsb + kStatusOff) = 0;
+  }
 }
 
 // Zero every sketch (blockIdx.y < nsk) and every one-pass B (blockIdx.y >= nsk).
@@ -80,7 +87,7 @@ cudaError_t launch_sketch_batched(const Plan& P, const void* const* X, const Bat
   const bool f64 = plan_items_host(&P)[0].prec == TT_PREC_FP64;
   const int ta = f64 ? cfg.ta : 64;
   count_launch();
-  batch_prep_kernel<<<1, 32, 0, st>>>((char*)ws, ta, 32);
+  batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws, ta, 32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   BatchCfg c = cfg;
