@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision and differentiation forms")
     ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
@@ -210,18 +211,8 @@ def batched_inputs(count, dev, seed=5):
     import torch
     import ttinputs as ti
     xs, probs = [], []
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(seed)
     for b, (dims, r) in enumerate(ti.batch_specs(count=count, seed=seed, cap=2_000_000)):
-        L = torch.ones(1, 1, dtype=torch.float64, device=dev)
-        for G in ti.random_tt_cores(dims, r, seed=1000 + b):
-            a_, n_, c_ = G.shape
-            Gd = torch.from_numpy(np.asfortranarray(G).reshape(a_, n_ * c_, order="F")).to(dev)
-            L = (L @ Gd).T.reshape(c_, n_, -1).permute(1, 2, 0).reshape(-1, c_)  # rows u + N i
-        x = L[:, 0]
-        e = torch.randn(x.numel(), dtype=torch.float64, device=dev, generator=gen)
-        x = x + e * (1e-7 * x.norm() / e.norm())
-        xs.append(x.to(torch.float32).contiguous())
+        xs.append(device_tt(dims, r, 1000 + b, 1e-7, dev, noise_seed=seed + b))
         probs.append(dict(dims=dims, eps=1e-5, rmax=16, p=5, seed=1000 + b))
     return xs, probs
 
@@ -278,6 +269,108 @@ def whole_job(ms_local, units_local, world, device=None):
         dist.all_reduce(u, op=dist.ReduceOp.SUM)
         ms_local, units_local = float(t.item()), float(u.item())
     return ms_local, units_local, units_local / (ms_local * 1e-3)
+
+
+def device_tt(dims, ranks, seed, noise, dev, noise_seed=2):
+    """Random-TT tensor (cores of ttinputs.random_tt_cores, contracted on the
+    device in FP64) plus relative Gaussian noise from a seeded torch
+    generator, as FP32 (column-major flat)."""
+    import numpy as np
+    import torch
+    import ttinputs as ti
+    L = torch.ones(1, 1, dtype=torch.float64, device=dev)
+    for G in ti.random_tt_cores(dims, ranks, seed=seed):
+        a_, n_, c_ = G.shape
+        Gd = torch.from_numpy(np.asfortranarray(G).reshape(a_, n_ * c_, order="F")).to(dev)
+        L = (L @ Gd).T.reshape(c_, n_, -1).permute(1, 2, 0).reshape(-1, c_)  # rows u + N i
+    x = L[:, 0]
+    if noise > 0:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(noise_seed)
+        e = torch.randn(x.numel(), dtype=torch.float64, device=dev, generator=gen)
+        x = x + e * (noise * x.norm() / e.norm())
+    return x.to(torch.float32).contiguous()
+
+
+def run_precision(a, dev, P, stream):
+    """Precision form: d = 6, n = 24 random TT (internal ranks 10) + 1e-6
+    relative noise, FP32; eps = 1e-5, p = 10, rmax = 16.  FP64 GPU path, TF32
+    and BF16 sketches; errors against X and against the FP64 GPU result."""
+    import torch
+    dims = [24] * 6
+    X = device_tt(dims, [1, 10, 10, 10, 10, 10, 1], 0, 1e-6, dev)
+    out = {"workload": "random TT d=6 n=24 (1.91e8 FP32 entries), ranks 10, +1e-6 noise; eps=1e-5 p=10 rmax=16"}
+    ref = None
+    for prec in ("fp64", "tf32", "bf16"):
+        t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec)
+        t.pstt2(X, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t.pstt2(X, stream)
+        e1.record(stream)
+        err = t.error(X, stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        err = err.cpu().numpy()
+        r = {"value": X.numel() / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+             "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": t.status(stream)[1],
+             "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane"][t.kernel_kind()]}
+        if prec == "fp64":
+            ref = t.reconstruct(torch.float32, stream=stream)
+        else:
+            d2 = t.error(ref, stream)
+            stream.synchronize()
+            d2 = d2.cpu().numpy()
+            r["rel_err_vs_fp64_gpu"] = float((d2[0] / err[1]) ** 0.5)
+        out[prec] = r
+        del t
+    del X, ref
+    return out
+
+
+def run_diff(a, dev, P, stream):
+    """Differentiation form: d = 5, n = 32 FP32 random TT (rank 8, seed 0),
+    loss ||TT_pstt2(X) - T||^2 with a fixed N(0,1) target (seed 3), target
+    ranks 8, p = 5; forward + hand-written backward through autograd."""
+    import torch
+    import ttinputs as ti
+    dims = [32] * 5
+    X = device_tt(dims, [1, 8, 8, 8, 8, 1], 0, 0.0, dev)
+    T = torch.tensor(ti.target_tensor(X.numel(), seed=3), device=dev)
+    out = {"workload": "random TT d=5 n=32 (3.36e7 FP32 entries), rank 8; target ranks 8, p=5"}
+    for prec in ("fp64", "bf16"):
+        t = P.TTSketch(dims, ranks=[1, 8, 8, 8, 8, 1], p=5, seed=1, x_dtype=torch.float32, prec=prec, diff=True)
+
+        def fwd_bwd():
+            Xg = X.detach().requires_grad_(True)
+            cores = P.PSTT2Fn.apply(Xg, t)
+            Xt = P.TTReconstructFn.apply(cores, t, torch.float32)
+            L = torch.sum((Xt.double() - T) ** 2)
+            L.backward()
+            return Xg.grad
+
+        with torch.cuda.stream(stream):
+            fwd_bwd()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = fwd_bwd()
+            e1.record(stream)
+        stream.synchronize()
+        # the sketch adjoint alone: dX written once (4 bytes per entry)
+        dcores = torch.randn(t.cores.numel(), dtype=torch.float64, device=dev)
+        dX = torch.empty_like(X)
+        t.backward(dcores, dX, stream)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        t.backward(dcores, dX, stream)
+        b1.record(stream)
+        stream.synchronize()
+        bms = b0.elapsed_time(b1)
+        out[prec] = {"fwd_bwd_ms": e0.elapsed_time(e1), "backward_ms": bms,
+                     "backward_dX_write_GBs": X.numel() * 4 / (bms * 1e-3) / 1e9,
+                     "grad_norm": float(g.double().norm())}
+        del t
+    return out
 
 
 def run_batched_only(a):
@@ -418,17 +511,36 @@ def run_gpu(a):
                 cores_h.copy_(t.cores, non_blocking=True)
                 ranks_h.copy_(t.ranks, non_blocking=True)
 
-        e2e_step()
-        torch.cuda.synchronize(dev)
-        h0 = time.perf_counter()
-        k = max(1, min(a.steps, 3))
-        for _ in range(k):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        e_ms = (time.perf_counter() - h0) * 1e3 / k
+        def e2e_direct_step():
+            # the sketch kernel reads the pinned host slabs itself (over the
+            # host link), no staging copy
+            t.begin(stream)
+            for g0_ in range(0, n, group):
+                t.accumulate(Xh[g0_ * Nd1:(g0_ + group) * Nd1], g0_, group, stream)
+            t.finalize(stream)
+            with torch.cuda.stream(stream):
+                cores_h.copy_(t.cores, non_blocking=True)
+                ranks_h.copy_(t.ranks, non_blocking=True)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize(dev)
+            h0 = time.perf_counter()
+            k = max(1, min(a.steps, 3))
+            for _ in range(k):
+                fn()
+            torch.cuda.synchronize(dev)
+            return (time.perf_counter() - h0) * 1e3 / k
+
+        e_copy = timed(e2e_step)
+        e_direct = timed(e2e_direct_step)
+        e_ms = min(e_copy, e_direct)
         out["e2e"] = {"value": world * ntot / (e_ms * 1e-3), "unit": "entries/s", "ms_per_step": e_ms,
                       "h2d_bytes_per_step": ntot * 4,
-                      "d2h_bytes_per_step": t.cores.numel() * 8 + t.ranks.numel() * 4}
+                      "d2h_bytes_per_step": t.cores.numel() * 8 + t.ranks.numel() * 4,
+                      "mode": "kernel reads pinned host X directly" if e_direct <= e_copy
+                      else "1 GiB pinned-host slabs copied on a second stream",
+                      "ms_copy_slabs": e_copy, "ms_direct_host_reads": e_direct}
         del Xh, Xd
 
     peak, peak_kind = measured_peaks()
@@ -439,6 +551,9 @@ def run_gpu(a):
 
     if not a.no_batched:
         out["batched"] = run_batched(a, dev, P, stream)
+    if not a.no_forms:
+        out["precision_form"] = run_precision(a, dev, P, stream)
+        out["diff_form"] = run_diff(a, dev, P, stream)
 
     cpu = None
     if rank == 0 and not a.no_cpu:
@@ -457,7 +572,8 @@ def run_gpu(a):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
-                "batched": out.get("batched")}
+                "batched": out.get("batched"),
+                "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

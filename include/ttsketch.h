@@ -279,6 +279,14 @@ tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last,
                                    int64_t count_last, void* out, tt_dtype dtype,
                                    tt_stream_t stream);
 
+/* Self-test of failure detection (no counterpart in the paper): launches one
+ * CTA whose thread waits, with the bounded wait every kernel of this library
+ * uses, on an mbarrier that nothing arrives at; after limit_cycles SM clock
+ * cycles (1 .. 4e9) the wait gives up and ORs 4 (the timeout bit, reported as
+ * TT_ERR_TIMEOUT by tt_query_status) into the device int *status_dev, and the
+ * kernel returns normally; the context stays usable.  Asynchronous on stream. */
+tt_status tt_selftest_wait_timeout(int64_t limit_cycles, int* status_dev, tt_stream_t stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (host-side counter, incremented at every launch; for benchmarks that
  * report how many of the library's kernels ran inside a timed region). */

@@ -64,6 +64,7 @@ _SIGS = {
     "tt_pstt2": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "tt_pstt2_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "tt_plan_batch_config": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "tt_selftest_wait_timeout": (C.c_int, [C.c_int64, _P, _P]),
     "tt_plan_autotune": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "tt_pstt2_begin": (C.c_int, [_P, _P, _P]),
     "tt_pstt2_accumulate": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),

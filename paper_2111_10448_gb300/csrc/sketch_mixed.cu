@@ -445,19 +445,37 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait; on give-up raises the abort flag and the timeout status bit.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status) {
+__device__ bool mbar_wait_for(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status,
+                              long long limit) {
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(a, parity)) return true;
     if ((it & 63) == 0) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         atomicOr(status, ST_TIMEOUT);
         return false;
       }
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status) {
+  return mbar_wait_for(a, parity, abort_flag, status, kWaitCycles);
+}
+
+// Self-test of the give-up path: one thread waits, with the kernels' own
+// bounded wait, on an mbarrier that nothing will ever arrive at.
+__global__ void wait_timeout_kernel(long long limit, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_for(smem_u32(&bar), 0, &abort_flag, status, limit);
 }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -489,6 +507,17 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t dtmem, uint64_t ad, uint64_
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       ::"r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+// Same, with the descriptors given as 32-bit halves (a k-step only moves the
+// start-address field, which lives in the low half).
+__device__ __forceinline__ void mma_bf16_ss_lo(uint32_t dtmem, uint32_t alo, uint32_t ahi, uint32_t blo,
+                                               uint32_t bhi, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\t"
+      "mov.b64 ad, {%1, %2};\n\tmov.b64 bd, {%3, %4};\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n\t}"
+      ::"r"(dtmem), "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -669,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     }
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
-    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..255
+    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..223
     const int qps = ell / 4;                      // column quads per sketch
     const int jobsL = 16 * qps * g.ngenL, jobsR = 16 * qps * g.ngenR;  // per 128-row block
     const int total = g.H4 * jobsL + g.H1 * jobsR;
@@ -824,16 +853,19 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
               // field (16-byte units) by a constant
               const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
               const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4);
+              const uint32_t aLl = (uint32_t)aL0, aLh = (uint32_t)(aL0 >> 32), aRl = (uint32_t)aR0,
+                             aRh = (uint32_t)(aR0 >> 32), bLl = (uint32_t)bL0, bLh = (uint32_t)(bL0 >> 32),
+                             bRl = (uint32_t)bR0, bRh = (uint32_t)(bR0 >> 32);
               const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> slotR) & 1u;
 #pragma unroll
               for (int ks = 0; ks < 8; ++ks) {
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                  const uint64_t po = (uint64_t)((part * kTileB) >> 4);
-                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4),
-                              idL, accL0 | (uint32_t)(ks | part));
-                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4),
-                              idR, accR0 | (uint32_t)(ks | part));
+                  const uint32_t po = (uint32_t)((part * kTileB) >> 4);
+                  mma_bf16_ss_lo(dL, aLl + po + (uint32_t)((ks * 2 * kS4) >> 4), aLh,
+                                 bLl + (uint32_t)((ks * 2 * kS1) >> 4), bLh, idL, accL0 | (uint32_t)(ks | part));
+                  mma_bf16_ss_lo(dR, aRl + po + (uint32_t)((ks * 2 * kS1) >> 4), aRh,
+                                 bRl + (uint32_t)((ks * 2 * kS1) >> 4), bRh, idR, accR0 | (uint32_t)(ks | part));
                 }
               }
               initL |= 1u << slotL;
@@ -1324,6 +1356,17 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
   tc::sketch_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
   return cudaGetLastError();
 }
+
+}  // namespace tts
+
+extern "C" tt_status tt_selftest_wait_timeout(int64_t limit_cycles, int* status_dev, tt_stream_t stream) {
+  if (!status_dev || limit_cycles < 1 || limit_cycles > (int64_t)tts::tc::kWaitCycles) return TT_ERR_INVALID_ARG;
+  tts::count_launch();
+  tts::tc::wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles, status_dev);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+namespace tts {
 
 // Which mixed kernel a launch uses: the tcgen05 plane kernel when its shape
 // rules hold (TT_SKETCH_KERNEL=mma forces the generic one, for comparisons).

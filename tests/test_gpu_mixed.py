@@ -240,3 +240,23 @@ def test_tcgen05_multitile_pipeline_within_10eps(dims):
     rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
     print(f"multi-tile pipeline {dims}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
     assert rx <= 1e-5 and rf <= 1e-5
+
+
+@pytest.mark.gpu
+def test_pinned_host_tensor_read_directly_equals_device_tensor():
+    """X in pinned host memory passed straight to the library (the kernels read
+    it over the host link) gives the same decomposition as X on the device."""
+    dims = [128, 16, 24, 128]
+    x = ti.hilbert_type(dims)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    xh = torch.tensor(x, dtype=torch.float32).pin_memory()
+    kw = dict(eps=1e-6, rmax=6, p=10, seed=1, x_dtype=torch.float32, prec="bf16")
+    a = TTSketch(dims, **kw).pstt2(xd)
+    b = TTSketch(dims, **kw)
+    b.begin()
+    b.accumulate(xh, 0, dims[-1])
+    b.finalize()
+    torch.cuda.synchronize()
+    ra, rb = a.reconstruct(torch.float64).cpu().numpy(), b.reconstruct(torch.float64).cpu().numpy()
+    assert a.status()[1] == b.status()[1]
+    assert np.linalg.norm(ra - rb) <= 1e-9 * np.linalg.norm(ra)
