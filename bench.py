@@ -224,6 +224,7 @@ def run_batched(a, dev, P, stream):
     import torch
     import ttinputs as ti
     xs, probs = batched_inputs(a.batch, dev)
+    torch.cuda.synchronize(dev)  # inputs come from torch's stream; the library runs on `stream`
     ntot = sum(x.numel() for x in xs)
     out = {"workload": f"{a.batch} FP32 tensors, d in 3..6, n in 8..32 (n^d <= 2e6), TT ranks 2..16 + 1e-7 noise; "
                        f"eps=1e-5 p=5 rmax=16; {ntot} entries ({ntot * 4 / 1e9:.2f} GB)", "entries": ntot}
@@ -299,6 +300,7 @@ def run_precision(a, dev, P, stream):
     import torch
     dims = [24] * 6
     X = device_tt(dims, [1, 10, 10, 10, 10, 10, 1], 0, 1e-6, dev)
+    torch.cuda.synchronize(dev)  # X comes from torch's stream; the library runs on `stream`
     out = {"workload": "random TT d=6 n=24 (1.91e8 FP32 entries), ranks 10, +1e-6 noise; eps=1e-5 p=10 rmax=16"}
     ref = None
     for prec in ("fp64", "tf32", "bf16"):
@@ -323,6 +325,7 @@ def run_precision(a, dev, P, stream):
             d2 = d2.cpu().numpy()
             r["rel_err_vs_fp64_gpu"] = float((d2[0] / err[1]) ** 0.5)
         out[prec] = r
+        stream.synchronize()  # nothing of t may still run when its buffers go back to torch
         del t
     del X, ref
     return out
@@ -337,6 +340,7 @@ def run_diff(a, dev, P, stream):
     dims = [32] * 5
     X = device_tt(dims, [1, 8, 8, 8, 8, 1], 0, 0.0, dev)
     T = torch.tensor(ti.target_tensor(X.numel(), seed=3), device=dev)
+    torch.cuda.synchronize(dev)
     out = {"workload": "random TT d=5 n=32 (3.36e7 FP32 entries), rank 8; target ranks 8, p=5"}
     for prec in ("fp64", "bf16"):
         t = P.TTSketch(dims, ranks=[1, 8, 8, 8, 8, 1], p=5, seed=1, x_dtype=torch.float32, prec=prec, diff=True)
@@ -369,6 +373,7 @@ def run_diff(a, dev, P, stream):
         out[prec] = {"fwd_bwd_ms": e0.elapsed_time(e1), "backward_ms": bms,
                      "backward_dX_write_GBs": X.numel() * 4 / (bms * 1e-3) / 1e9,
                      "grad_norm": float(g.double().norm())}
+        stream.synchronize()
         del t
     return out
 
