@@ -1118,7 +1118,8 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
 // as the forward sketch of the item's precision).
 namespace {
 
-__device__ __forceinline__ void test_row(int prec, uint64_t seed, int sid, uint64_t row, int l, double* out) {
+template <typename Real>
+__device__ __forceinline__ void test_row(int prec, uint64_t seed, int sid, uint64_t row, int l, Real* out) {
   for (int q = 0; q < (l + 3) / 4; ++q) {
     double z[4];
     if (prec == TT_PREC_FP64) {
@@ -1131,7 +1132,7 @@ __device__ __forceinline__ void test_row(int prec, uint64_t seed, int sid, uint6
       z[3] = round_prec(f.w, prec);
     }
     for (int t = 0; t < 4; ++t)
-      if (4 * q + t < l) out[4 * q + t] = z[t];
+      if (4 * q + t < l) out[4 * q + t] = (Real)z[t];
   }
 }
 
@@ -1162,10 +1163,14 @@ __global__ void pbar_ls_kernel(char* wsb, int item, const int* ranks) {
 // dX(a, w, b) = sum_col sum_j Sbar_k[a + n1 wlo, j] Omega_k[whi + hs b, j]
 //             + sum_row sum_j Psi_k[a + n1 wlo, j] Rbar_k[whi + hs b, j]
 // (one tile of 64 x 32 entries of one plane per iteration; written once).
+// Real = double for the FP64 path; float for the TF32 / BF16 paths, whose
+// test-matrix entries are exact in FP32 and whose forward sketch accumulates
+// in FP32 (the adjoints S-bar / R-bar are rounded to FP32 on load).
+template <typename Real>
 __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item, void* dX) {
   constexpr int TA = 64, TB = 32, LD = TT_MAXL + 1;
-  __shared__ double Lf[TA * LD];
-  __shared__ double Rf[TB * LD];
+  __shared__ Real Lf[TA * LD];
+  __shared__ Real Rf[TB * LD];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + 256);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
   const DevSketch* S = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
@@ -1181,7 +1186,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
     const int64_t bb = rem / nA, ab = rem - bb * nA;
     const int64_t a0 = ab * TA, b0 = bb * TB;
     const int ta = (int)imin64(TA, n1 - a0), tb = (int)imin64(TB, nd - b0);
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Real acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int s = 0; s < it.nsk; ++s) {
       const DevSketch& sk = S[it.sk0 + s];
       const int l = sk.width;
@@ -1191,7 +1196,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
       if (sk.type == SK_COL) {
         for (int o = tid; o < ta * l; o += blockDim.x) {
           const int a = o % ta, j = o / ta;
-          Lf[a * LD + j] = bar[(a0 + a + n1 * wlo) + sk.rows * j];
+          Lf[a * LD + j] = (Real)bar[(a0 + a + n1 * wlo) + sk.rows * j];
         }
         for (int b = tid; b < tb; b += blockDim.x)
           test_row(it.prec, it.seed, sk.stream_id, (uint64_t)(whi + sk.hstride * (b0 + b)), l, Rf + b * LD);
@@ -1200,7 +1205,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
           test_row(it.prec, it.seed, sk.stream_id, (uint64_t)((a0 + a) + n1 * wlo), l, Lf + a * LD);
         for (int o = tid; o < tb * l; o += blockDim.x) {
           const int b = o % tb, j = o / tb;
-          Rf[b * LD + j] = bar[(whi + sk.hstride * (b0 + b)) + sk.rows * j];
+          Rf[b * LD + j] = (Real)bar[(whi + sk.hstride * (b0 + b)) + sk.rows * j];
         }
       }
       __syncthreads();
@@ -1209,7 +1214,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
         for (int m = 0; m < 8; ++m) {
           const int b = ib0 + 4 * m;
           if (b < tb) {
-            double v = 0.0;
+            Real v = 0;
             for (int j = 0; j < l; ++j) v += Lf[ia * LD + j] * Rf[b * LD + j];
             acc[m] += v;
           }
@@ -1222,7 +1227,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
         const int b = ib0 + 4 * m;
         if (b < tb) {
           const int64_t idx = (a0 + ia) + n1 * w + Nd1 * (b0 + b);
-          if (it.x_f64) ((double*)dX)[idx] = acc[m];
+          if (it.x_f64) ((double*)dX)[idx] = (double)acc[m];
           else ((float*)dX)[idx] = (float)acc[m];
         }
       }
@@ -1247,7 +1252,8 @@ cudaError_t launch_sketch_adjoint(const Plan& P, int item, void* dX, void* ws, c
   const int64_t total = it.W * nA * nB;
   const int grid = (int)std::min<int64_t>(total, 8LL * device_sm_count());
   count_launch();
-  sketch_adjoint_kernel<<<grid, 256, 0, st>>>((char*)ws, item, dX);
+  if (it.prec == TT_PREC_FP64) sketch_adjoint_kernel<double><<<grid, 256, 0, st>>>((char*)ws, item, dX);
+  else sketch_adjoint_kernel<float><<<grid, 256, 0, st>>>((char*)ws, item, dX);
   return cudaGetLastError();
 }
 

@@ -132,3 +132,26 @@ def test_reconstruct_backward_matches_autograd():
     Lt.backward()
     want = cc.grad.numpy()
     assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_vjp_mixed_precision_matches_rounded_oracle(prec):
+    """Mixed paths: the adjoint runs in FP32 with the rounded test matrices;
+    compared with the oracle gradient of the map whose test matrices are
+    rounded to the same type (the FP32 generator flips a few rounding
+    decisions, and X is FP32, so the bar is looser than the FP64 path's)."""
+    dims, r, target, p = [6, 5, 7, 4], [1, 3, 4, 3, 1], [1, 2, 3, 2, 1], 4
+    x = ti.random_tt(dims, r, seed=4, noise=1e-2).astype(np.float32).astype(np.float64)
+    t = TTSketch(dims, ranks=target, p=p, seed=2, x_dtype=torch.float32, prec=prec)
+    t.pstt2(to_dev(x, torch.float32))
+    _, ranks = t.status()
+    ref = OG.forward_ref(x, dims, ranks=target, p=p, seed=2, test_fmt=prec)
+    assert ranks == ref["r"]
+    dc, lst = padded_dcores(t, ranks, np.random.default_rng(1))
+    dX = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    t.backward(torch.tensor(dc, device="cuda"), dX)
+    got = dX.double().cpu().numpy()
+    want = OG.cores_vjp(x, dims, ref, lst)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print(f"{prec} VJP rel err vs rounded oracle: {err:.2e}")
+    assert err <= 1e-4, err

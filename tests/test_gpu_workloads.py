@@ -21,11 +21,11 @@ def _run(x, dims, prec, **kw):
 @pytest.mark.gpu
 @pytest.mark.parametrize("name,dims,eps,rmax", [
     ("hilbert", [20, 20, 20, 20], 1e-8, 12),
-    ("bumps", [24, 24, 24], 1e-6, 16),
+    ("bumps", [24, 24, 24], 1e-6, 12),
     ("hilbert", [12, 12, 12, 12, 12], 1e-6, 10),
 ])
 def test_fp64_matches_oracle(name, dims, eps, rmax):
-    x = ti.hilbert_paper(dims) if name == "hilbert" else ti.gaussian_bumps(dims)
+    x = ti.hilbert_paper(dims) if name == "hilbert" else ti.gaussian_bumps(dims, nbumps=6)
     t = _run(x, dims, "fp64", eps=eps, rmax=rmax, p=6, seed=2)
     o = OP.pstt2(x, dims, eps=eps, rmax=rmax, p=6, seed=2)
     st, ranks = t.status()
@@ -43,10 +43,12 @@ def test_bf16_plane_kernel_within_10eps(name):
     dims = [128, 12, 12, 128]
     x = (ti.hilbert_paper(dims) if name == "hilbert" else ti.gaussian_bumps(dims, nbumps=5)).astype(np.float32)
     eps = 1e-5
-    t = _run(x, dims, "bf16", eps=eps, rmax=14, p=10, seed=2)
+    t = _run(x, dims, "bf16", eps=eps, rmax=10, p=6, seed=2)     # l = 16: the plane kernel's shape
     assert t.kernel_kind() == 2
     x64 = x.astype(np.float64)
-    o = OP.pstt2(x64, dims, eps=eps, rmax=14, p=10, seed=2)
+    o = OP.pstt2(x64, dims, eps=eps, rmax=10, p=6, seed=2)
     got = OT.tt_full(t.core_list(0))
     nx = np.linalg.norm(x64)
-    assert np.linalg.norm(got - OT.tt_full(o["cores"])) <= 10 * eps * nx
+    err = np.linalg.norm(got - OT.tt_full(o["cores"])) / nx
+    print(f"{name}: bf16 plane kernel vs oracle {err:.2e}, ranks {t.status()[1]} / {o['r']}")
+    assert err <= 10 * eps
