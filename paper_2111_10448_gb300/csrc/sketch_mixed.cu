@@ -463,6 +463,12 @@ __device__ bool mbar_wait_for(uint32_t a, uint32_t parity, volatile int* abort_f
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status) {
   return mbar_wait_for(a, parity, abort_flag, status, kWaitCycles);
 }
+// Wait by every lane of a warp; the result is the same on all lanes (false if
+// any lane gave up), so control flow after it stays converged.
+__device__ __forceinline__ bool warp_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int* status) {
+  const bool ok = mbar_wait_for(a, parity, abort_flag, status, kWaitCycles);
+  return __all_sync(0xffffffffu, ok);
+}
 
 // Self-test of the give-up path: one thread waits, with the kernels' own
 // bounded wait, on an mbarrier that nothing will ever arrive at.
@@ -519,6 +525,18 @@ __device__ __forceinline__ void mma_bf16_ss_lo(uint32_t dtmem, uint32_t alo, uin
       "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %5, p;\n\t}"
       ::"r"(dtmem), "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
 }
+// One lane of a converged warp (the lowest active lane) is elected; the MMA
+// warp runs its control flow on all lanes and issues through the elected lane,
+// so descriptors and loop state stay warp-uniform.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "elect.sync _|P, 0xffffffff;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(pred));
+  return pred != 0;
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -533,6 +551,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int ELL>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float v[ELL]) {
+  static_assert(ELL == 8 || ELL == 16, "sketch width of the plane kernel");
+  if constexpr (ELL == 16) tmem_ld16(taddr, v);
+  else tmem_ld8(taddr, v);
 }
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
@@ -585,6 +618,7 @@ __device__ __forceinline__ int64_t row_key(const TcArgs& g, const SkTc& sk, int6
   return w % sk.wdiv;
 }
 
+template <int ELL>
 __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -594,9 +628,19 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
             TMR_FULL = 11, TMR_EMPTY = 13, TAB_FULL = 15;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
+  // sketch descriptors in shared memory: every role indexes them by a runtime
+  // sketch number
+  __shared__ SkTc s_col[4], s_row[4];
+  __shared__ int s_gen[8];  // generated sketches: column side 0..3, row side 4..7
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
 
+  if (threadIdx.x < 4) {
+    s_col[threadIdx.x] = g.col[threadIdx.x];
+    s_row[threadIdx.x] = g.row[threadIdx.x];
+    s_gen[threadIdx.x] = g.genL[threadIdx.x];
+    s_gen[4 + threadIdx.x] = g.genR[threadIdx.x];
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(bar(FULL_A + s), kProdWarps);
@@ -630,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   const int64_t ntiles = ntiles_all * (blockIdx.x + 1) / gridDim.x;
   const uint32_t sA = smem_u32(sm);
   const uint32_t sB = smem_u32(sm + kOffB);
-  const int ell = g.ell;
+  constexpr int ell = ELL;
 
   if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
     // ------------------------------------------------------------ producers
@@ -699,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
     const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..223
-    const int qps = ell / 4;                      // column quads per sketch
+    constexpr int qps = ell / 4;                  // column quads per sketch
     const int jobsL = 16 * qps * g.ngenL, jobsR = 16 * qps * g.ngenR;  // per 128-row block
     const int total = g.H4 * jobsL + g.H1 * jobsR;
     uint32_t pi = 0;
@@ -715,28 +759,25 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
           // blocks: 0..H4-1 = column side (k = i_d), 2..2+H1-1 = row side (k = i_1)
           if (rt == 0 && g.tab_tx) {
             // blocks shared by many planes come from the staged tables
-            {
-              mbar_arrive_expect_tx(bar(TAB_FULL + buf), g.tab_tx);
-              tab_last[buf] = pi;
-              const char* wsb = reinterpret_cast<const char*>(g.ws);
-              for (int s = 0; s < g.nL; ++s) {
-                const SkTc sk = g.col[s];
-                if (sk.tab < 0) continue;
-                const uint32_t bytes = (uint32_t)(ell / 8) * kS4;
-                for (int h4 = 0; h4 < g.H4; ++h4)
-                  bulk_g2s(sB + (buf * kBBlks + h4) * kBBlkB + (s * ell / 8) * kS4,
-                           wsb + sk.tab + (col_key(g, sk, w, kRp) * g.H4 + h4) * (int64_t)bytes, bytes,
-                           bar(TAB_FULL + buf));
-              }
-              for (int s = 0; s < g.nR; ++s) {
-                const SkTc sk = g.row[s];
-                if (sk.tab < 0) continue;
-                const uint32_t bytes = (uint32_t)(ell / 8) * kS4;
-                for (int h1 = 0; h1 < g.H1; ++h1)
-                  bulk_g2s(sB + (buf * kBBlks + 2 + h1) * kBBlkB + (s * ell / 8) * kS4,
-                           wsb + sk.tab + (row_key(g, sk, w, kLp) * g.H1 + h1) * (int64_t)bytes, bytes,
-                           bar(TAB_FULL + buf));
-              }
+            mbar_arrive_expect_tx(bar(TAB_FULL + buf), g.tab_tx);
+            tab_last[buf] = pi;
+            const char* wsb = reinterpret_cast<const char*>(g.ws);
+            constexpr uint32_t bytes = (uint32_t)(ell / 8) * kS4;
+            for (int s = 0; s < g.nL; ++s) {
+              const SkTc& sk = s_col[s];
+              if (sk.tab < 0) continue;
+              for (int h4 = 0; h4 < g.H4; ++h4)
+                bulk_g2s(sB + (buf * kBBlks + h4) * kBBlkB + (s * ell / 8) * kS4,
+                         wsb + sk.tab + (col_key(g, sk, w, kRp) * g.H4 + h4) * (int64_t)bytes, bytes,
+                         bar(TAB_FULL + buf));
+            }
+            for (int s = 0; s < g.nR; ++s) {
+              const SkTc& sk = s_row[s];
+              if (sk.tab < 0) continue;
+              for (int h1 = 0; h1 < g.H1; ++h1)
+                bulk_g2s(sB + (buf * kBBlks + 2 + h1) * kBBlkB + (s * ell / 8) * kS4,
+                         wsb + sk.tab + (row_key(g, sk, w, kLp) * g.H1 + h1) * (int64_t)bytes, bytes,
+                         bar(TAB_FULL + buf));
             }
           }
           for (int job = rt; job < total; job += kRngWarps * 32) {
@@ -753,9 +794,9 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
             }
             const int kg = jj & 15, rest = jj >> 4;
             const int gi = rest / qps, nq = rest % qps;
-            const int s = colside ? g.genL[gi] : g.genR[gi];
+            const int s = s_gen[(colside ? 0 : 4) + gi];
             const int n0 = s * ell + 4 * nq;
-            const SkTc sk = colside ? g.col[s] : g.row[s];
+            const SkTc& sk = colside ? s_col[s] : s_row[s];
             const uint32_t sid = (uint32_t)sk.sid;
             // column side: row = key + hstride * i_d; row side: row = i_1 + n1 * key
             const int64_t rbase = colside ? col_key(g, sk, w, kRp) + sk.hstride * (g.first + blk * 128 + 8 * kg)
@@ -802,86 +843,97 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
         }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
-    if (lane == 0) {
-      const uint32_t idL = make_idesc(g.NL, true), idR = make_idesc(g.NR, false);
-      const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
-      const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);  // one R buffer
-      uint32_t qi = 0, pi = 0, lf = 0, ti = 0;
-      int64_t cur_tl = -1;
-      uint32_t initL = 0;
-      bool ok = true;
-      for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti) {
-        const TileInfo tinf = tile_info(g, t);
-        const int64_t tl = l_group(g, t);
-        if (tl != cur_tl) {
-          // a new L group: the previous group's L slots go to the epilogue
-          if (cur_tl >= 0) {
-            mma_commit(bar(TML_FULL));
-            ++lf;
-          }
-          ok = mbar_wait(bar(TML_EMPTY), (lf & 1) ^ 1, abort_flag, g.status);
-          if (!ok) break;
-          tc_fence_after();
-          initL = 0;
-          cur_tl = tl;
+    // Every lane runs the schedule and waits; the elected lane issues the
+    // MMAs and commits (the same lane each time: the warp is converged).
+    const uint32_t idL = make_idesc(g.NL, true), idR = make_idesc(g.NR, false);
+    const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
+    const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);  // one R buffer
+    uint32_t qi = 0, pi = 0, lf = 0, ti = 0;
+    int64_t cur_tl = -1;
+    uint32_t initL = 0;
+    bool ok = true;
+    for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti) {
+      const TileInfo tinf = tile_info(g, t);
+      const int64_t tl = l_group(g, t);
+      if (tl != cur_tl) {
+        // a new L group: the previous group's L slots go to the epilogue
+        if (cur_tl >= 0) {
+          if (elect_one()) mma_commit(bar(TML_FULL));
+          __syncwarp();
+          ++lf;
         }
-        const uint32_t rb = ti & 1;
-        ok = mbar_wait(bar(TMR_EMPTY + rb), ((ti >> 1) & 1) ^ 1, abort_flag, g.status);
+        ok = warp_wait(bar(TML_EMPTY), (lf & 1) ^ 1, abort_flag, g.status);
         if (!ok) break;
         tc_fence_after();
-        uint32_t initR = 0;
-        for (int b = 0; b < tinf.nB && ok; ++b)
-          for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
-            const int buf = pi & 1;
-            ok = mbar_wait(bar(FULL_B + buf), (pi >> 1) & 1, abort_flag, g.status);
-            if (ok && g.tab_tx) ok = mbar_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
+        initL = 0;
+        cur_tl = tl;
+      }
+      const uint32_t rb = ti & 1;
+      ok = warp_wait(bar(TMR_EMPTY + rb), ((ti >> 1) & 1) ^ 1, abort_flag, g.status);
+      if (!ok) break;
+      tc_fence_after();
+      uint32_t initR = 0;
+      for (int b = 0; b < tinf.nB && ok; ++b)
+        for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
+          const int buf = pi & 1;
+          ok = warp_wait(bar(FULL_B + buf), (pi >> 1) & 1, abort_flag, g.status);
+          if (ok && g.tab_tx) ok = warp_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
+          if (!ok) break;
+          tc_fence_after();
+          for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
+            const int h1 = q % g.H1, h4 = q / g.H1;
+            const int st = qi & 1;
+            ok = warp_wait(bar(FULL_A + st), (qi >> 1) & 1, abort_flag, g.status);
             if (!ok) break;
             tc_fence_after();
-            for (int q = 0; q < g.H1 * g.H4; ++q, ++qi) {
-              const int h1 = q % g.H1, h4 = q / g.H1;
-              const int st = qi & 1;
-              ok = mbar_wait(bar(FULL_A + st), (qi >> 1) & 1, abort_flag, g.status);
-              if (!ok) break;
-              tc_fence_after();
-              const uint32_t tileA = sA + st * kStageB;
-              const uint32_t bL = sB + (buf * kBBlks + h4) * kBBlkB;
-              const uint32_t bR = sB + (buf * kBBlks + 2 + h1) * kBBlkB;
-              const int slotL = a * g.H1 + h1, slotR = b * g.H4 + h4;
-              const uint32_t dL = tmem + (uint32_t)(slotL * g.NL);
-              const uint32_t dR = tmem + colR0 + rb * colRB + (uint32_t)(slotR * g.NR);
-              // descriptors of k-step 0; a k-step advances the start address
-              // field (16-byte units) by a constant
-              const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
-              const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4);
-              const uint32_t aLl = (uint32_t)aL0, aLh = (uint32_t)(aL0 >> 32), aRl = (uint32_t)aR0,
-                             aRh = (uint32_t)(aR0 >> 32), bLl = (uint32_t)bL0, bLh = (uint32_t)(bL0 >> 32),
-                             bRl = (uint32_t)bR0, bRh = (uint32_t)(bR0 >> 32);
-              const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> slotR) & 1u;
+            const uint32_t tileA = sA + st * kStageB;
+            const uint32_t bL = sB + (buf * kBBlks + h4) * kBBlkB;
+            const uint32_t bR = sB + (buf * kBBlks + 2 + h1) * kBBlkB;
+            const int slotL = a * g.H1 + h1, slotR = b * g.H4 + h4;
+            const uint32_t dL = tmem + (uint32_t)(slotL * g.NL);
+            const uint32_t dR = tmem + colR0 + rb * colRB + (uint32_t)(slotR * g.NR);
+            // descriptors of k-step 0; a k-step advances the start address
+            // field (16-byte units) by a constant
+            const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
+            const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4);
+            const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> slotR) & 1u;
+            if (elect_one()) {
 #pragma unroll
               for (int ks = 0; ks < 8; ++ks) {
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                  const uint32_t po = (uint32_t)((part * kTileB) >> 4);
-                  mma_bf16_ss_lo(dL, aLl + po + (uint32_t)((ks * 2 * kS4) >> 4), aLh,
-                                 bLl + (uint32_t)((ks * 2 * kS1) >> 4), bLh, idL, accL0 | (uint32_t)(ks | part));
-                  mma_bf16_ss_lo(dR, aRl + po + (uint32_t)((ks * 2 * kS1) >> 4), aRh,
-                                 bRl + (uint32_t)((ks * 2 * kS1) >> 4), bRh, idR, accR0 | (uint32_t)(ks | part));
+                  const uint64_t po = (uint64_t)((part * kTileB) >> 4);
+                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                              idL, accL0 | (uint32_t)(ks | part));
+                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                              idR, accR0 | (uint32_t)(ks | part));
                 }
               }
-              initL |= 1u << slotL;
-              initR |= 1u << slotR;
               mma_commit(bar(EMPTY_A + st));
             }
-            if (ok) mma_commit(bar(EMPTY_B + buf));
+            __syncwarp();
+            initL |= 1u << slotL;
+            initR |= 1u << slotR;
           }
-        if (ok) mma_commit(bar(TMR_FULL + rb));
+          if (ok) {
+            if (elect_one()) mma_commit(bar(EMPTY_B + buf));
+            __syncwarp();
+          }
+        }
+      if (ok) {
+        if (elect_one()) mma_commit(bar(TMR_FULL + rb));
+        __syncwarp();
       }
-      if (ok && cur_tl >= 0) mma_commit(bar(TML_FULL));
-      // drain this thread's MMAs before the tensor memory is freed
-      mma_commit(bar(DRAIN));
-      const long long t0 = clock64();
-      while (!mbar_try(bar(DRAIN), 0) && clock64() - t0 < kWaitCycles) {
-      }
+    }
+    if (ok && cur_tl >= 0) {
+      if (elect_one()) mma_commit(bar(TML_FULL));
+      __syncwarp();
+    }
+    // drain the issued MMAs before the tensor memory is freed
+    if (elect_one()) mma_commit(bar(DRAIN));
+    __syncwarp();
+    const long long t0 = clock64();
+    while (!mbar_try(bar(DRAIN), 0) && clock64() - t0 < kWaitCycles) {
     }
     __syncwarp();
   } else if (warp < kEpiWarps) {
@@ -890,32 +942,38 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
     const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
     const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);
-    // L slots of kL block [kL0, kL0 + nA) -> column sketches
+    // L slots of kL block [kL0, kL0 + nA) -> column sketches.  A sketch whose
+    // rows do not depend on the plane (wdiv = 1) is pre-summed in FP32 over
+    // the few slots of one flush; the others go to their rows directly.
     auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
       if (!mbar_wait(bar(TML_FULL), lf & 1, abort_flag, g.status)) return false;
       tc_fence_after();
       for (int h1 = 0; h1 < g.H1; ++h1) {
         const int64_t i1 = h1 * 128 + lrow;
-        float acc1[32];  // FP32 pre-sum over the few slots of one flush
-        for (int j = 0; j < g.NL; ++j) acc1[j] = 0.0f;
-        for (int a = 0; a < nA; ++a) {
-          const int64_t kL = kL0 + a;
-          float v[32];
-          const uint32_t c0 = tmem + lane_addr + (uint32_t)((a * g.H1 + h1) * g.NL);
-          for (int c = 0; c < g.NL; c += 16) tmem_ld16(c0 + c, v + c);
-          for (int s = 0; s < g.nL; ++s) {
-            const SkTc sk = g.col[s];
-            if (sk.wdiv == 1) {
-              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += v[s * ell + j];
+        for (int s = 0; s < g.nL; ++s) {
+          const SkTc& sk = s_col[s];
+          const bool presum = sk.wdiv == 1;
+          double* dst = g.ws + sk.off;
+          float acc[ell];
+#pragma unroll
+          for (int j = 0; j < ell; ++j) acc[j] = 0.0f;
+          for (int a = 0; a < nA; ++a) {
+            float v[ell];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)((a * g.H1 + h1) * g.NL + s * ell), v);
+            if (presum) {
+#pragma unroll
+              for (int j = 0; j < ell; ++j) acc[j] += v[j];
             } else {
-              const int64_t row = i1 + g.n1 * (kL % sk.wdiv);
-              for (int j = 0; j < ell; ++j) atomicAdd(g.ws + sk.off + row + sk.rows * j, (double)v[s * ell + j]);
+              const int64_t row = i1 + g.n1 * ((kL0 + a) % sk.wdiv);
+#pragma unroll
+              for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
             }
           }
+          if (presum) {
+#pragma unroll
+            for (int j = 0; j < ell; ++j) atomicAdd(dst + i1 + sk.rows * j, (double)acc[j]);
+          }
         }
-        for (int s = 0; s < g.nL; ++s)
-          if (g.col[s].wdiv == 1)
-            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.col[s].off + i1 + g.col[s].rows * j, (double)acc1[s * ell + j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -939,34 +997,38 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
         cur_kL0 = tinf.kL0;
         cur_nA = tinf.nA;
       }
-      // R slots of this tile (buffer ti & 1) -> row sketches
+      // R slots of this tile (buffer ti & 1) -> row sketches; a sketch whose
+      // rows do not depend on the plane (wdiv = W) is pre-summed over the tile
       const uint32_t rb = ti & 1;
       if (!mbar_wait(bar(TMR_FULL + rb), (ti >> 1) & 1, abort_flag, g.status)) break;
       tc_fence_after();
       for (int h4 = 0; h4 < g.H4; ++h4) {
         const int64_t bg = g.first + h4 * 128 + lrow;
-        float acc1[32];  // FP32 pre-sum over the few slots of one flush
-        for (int j = 0; j < g.NR; ++j) acc1[j] = 0.0f;
-        for (int b = 0; b < tinf.nB; ++b) {
-          const int64_t kR = tinf.kR0 + b;
-          float v[32];
-          const uint32_t c0 = tmem + lane_addr + colR0 + rb * colRB + (uint32_t)((b * g.H4 + h4) * g.NR);
-          for (int c = 0; c < g.NR; c += 16) tmem_ld16(c0 + c, v + c);
-          for (int s = 0; s < g.nR; ++s) {
-            const SkTc sk = g.row[s];
-            if (sk.wdiv == g.W) {
-              for (int j = 0; j < ell; ++j) acc1[s * ell + j] += v[s * ell + j];
+        for (int s = 0; s < g.nR; ++s) {
+          const SkTc& sk = s_row[s];
+          const bool presum = sk.wdiv == g.W;
+          double* dst = g.ws + sk.off;
+          float acc[ell];
+#pragma unroll
+          for (int j = 0; j < ell; ++j) acc[j] = 0.0f;
+          for (int b = 0; b < tinf.nB; ++b) {
+            float v[ell];
+            tmem_ld_cols<ell>(tmem + lane_addr + colR0 + rb * colRB + (uint32_t)((b * g.H4 + h4) * g.NR + s * ell), v);
+            if (presum) {
+#pragma unroll
+              for (int j = 0; j < ell; ++j) acc[j] += v[j];
             } else {
-              const int64_t whi = kR / (sk.wdiv / g.WL);
+              const int64_t whi = (tinf.kR0 + b) / (sk.wdiv / g.WL);
               const int64_t row = whi + sk.hstride * bg;
-              for (int j = 0; j < ell; ++j) atomicAdd(g.ws + sk.off + row + sk.rows * j, (double)v[s * ell + j]);
+#pragma unroll
+              for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
             }
           }
+          if (presum) {
+#pragma unroll
+            for (int j = 0; j < ell; ++j) atomicAdd(dst + bg * sk.hstride + sk.rows * j, (double)acc[j]);
+          }
         }
-        for (int s = 0; s < g.nR; ++s)
-          if (g.row[s].wdiv == g.W)
-            for (int j = 0; j < ell; ++j) atomicAdd(g.ws + g.row[s].off + bg * g.row[s].hstride + g.row[s].rows * j,
-                                                    (double)acc1[s * ell + j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -1040,7 +1102,7 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
       g.row[nR++] = t;
     }
   }
-  if (ell % 4 != 0) return false;
+  if (ell != 8 && ell != 16) return false;  // the kernel is compiled for these widths
   const int NL = nL * ell, NR = nR * ell;
   if (NL < 16 || NR < 16 || NL > 32 || NR > 32 || NL % 16 || NR % 16) return false;
   g.n1 = it.n[0];
@@ -1320,9 +1382,11 @@ cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg,
 static bool tc_kernel_launchable() {
   static int ok = -1;
   if (ok < 0) {
-    cudaFuncAttributes fa;
+    cudaFuncAttributes fa, fb;
     int dev = 0, smem_optin = 0;
-    ok = cudaFuncGetAttributes(&fa, tc::sketch_tc_kernel) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+    ok = cudaFuncGetAttributes(&fa, tc::sketch_tc_kernel<16>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fb, tc::sketch_tc_kernel<8>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+         fb.maxThreadsPerBlock >= tc::kThreads &&
          cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
          fa.maxThreadsPerBlock >= tc::kThreads && smem_optin >= tc::kSmemBytes;
   }
@@ -1339,8 +1403,10 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
   g.first = first;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc::sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tc::sketch_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tc::kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc::sketch_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1359,7 +1425,8 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
-  tc::sketch_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
+  if (g.ell == 16) tc::sketch_tc_kernel<16><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
+  else tc::sketch_tc_kernel<8><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
   return cudaGetLastError();
 }
 
