@@ -387,7 +387,7 @@ constexpr int kStages = 2;
 constexpr int kBBlkB = 4 * kS4;          // one test-matrix block, N <= 32
 constexpr int kBBlks = 4;                // L[h4=0,1], R[h1=0,1] per plane
 constexpr int kBBufs = 2;
-constexpr int kWarps = 20;
+constexpr int kWarps = 20;  // 5 per scheduler: 96 registers per thread
 constexpr int kThreads = kWarps * 32;
 constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 7;
 constexpr int kOffB = kStages * kStageB;
@@ -571,6 +571,12 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&b);
 }
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void st_shared_b32(uint32_t a, uint32_t x) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(x) : "memory");
+}
 __device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
@@ -683,13 +689,38 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     // The loads of the next quarter are issued before waiting for its stage,
     // so their latency overlaps the tensor-core work on the stage.
     const int nq = g.H1 * g.H4;
+    // Cursor over (quarter, plane, tile) in the order every role uses; it runs
+    // two quarters ahead of the quarter held in registers.
     int64_t t = t_beg;
     int a = 0, b = 0, q = 0;
     TileInfo ti = tile_info(g, t);
-    auto quarter_src = [&](int64_t tt, const TileInfo& tinf, int aa, int bb, int qq) {
-      const int64_t w = (tinf.kL0 + aa) + g.WL * (tinf.kR0 + bb);
-      const int h1 = qq % g.H1, h4 = qq / g.H1;
+    auto advance = [&]() {
+      if (++q == nq) {
+        q = 0;
+        if (++a == ti.nA) {
+          a = 0;
+          if (++b == ti.nB) {
+            b = 0;
+            t += 1;
+            if (t < ntiles) ti = tile_info(g, t);
+          }
+        }
+      }
+    };
+    // this thread's first element of the quarter at the cursor
+    auto cursor_src = [&]() -> const float* {
+      if (t >= ntiles) return nullptr;
+      const int64_t w = (ti.kL0 + a) + g.WL * (ti.kR0 + b);
+      const int h1 = q % g.H1, h4 = q / g.H1;
       return g.X + (h1 * 128 + cb1 * 8) + g.n1 * w + g.Nd1 * (int64_t)(h4 * 128 + rsub);
+    };
+    // L2 prefetch of a quarter: the four threads that share a 128-byte line
+    // (cb1 & 3 = 0..3) take two of its eight rows each.
+    auto prefetch = [&](const float* src) {
+      const int c = cb1 & 3;
+      const float* line = src - c * 8;
+      prefetch_l2(line + g.Nd1 * (int64_t)(16 * (2 * c)));
+      prefetch_l2(line + g.Nd1 * (int64_t)(16 * (2 * c + 1)));
     };
     float4 v[16];
     auto issue = [&](const float* src) {
@@ -700,9 +731,19 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
         v[2 * m + 1] = __ldcs(p4 + 1);
       }
     };
-    if (t < ntiles) issue(quarter_src(t, ti, 0, 0, 0));
+    // The loads of the next quarter are issued before waiting for its stage,
+    // so their latency overlaps the tensor-core work on the stage; the one
+    // after it is prefetched into L2, which puts more of X in flight than the
+    // registers can hold.
+    const float* src0 = cursor_src();
+    bool have = src0 != nullptr;
+    if (have) issue(src0);
+    advance();
+    const float* src1 = cursor_src();
+    if (src1) prefetch(src1);
+    advance();
     uint32_t qi = 0;
-    while (t < ntiles && !*abort_flag) {
+    while (have && !*abort_flag) {
       const int st = qi & 1;
       if (!mbar_wait(bar(EMPTY_A + st), ((qi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
       const uint32_t tileA = sA + st * kStageB;
@@ -726,26 +767,50 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(FULL_A + st));
       ++qi;
-      // advance (quarter, plane, tile) in the order every role uses
-      if (++q == nq) {
-        q = 0;
-        if (++a == ti.nA) {
-          a = 0;
-          if (++b == ti.nB) {
-            b = 0;
-            t += 1;
-            if (t < ntiles) ti = tile_info(g, t);
-          }
-        }
-      }
-      if (t < ntiles) issue(quarter_src(t, ti, a, b, q));
+      have = src1 != nullptr;
+      if (have) issue(src1);
+      src1 = cursor_src();
+      if (src1) prefetch(src1);
+      advance();
     }
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
     const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..223
     constexpr int qps = ell / 4;                  // column quads per sketch
-    const int jobsL = 16 * qps * g.ngenL, jobsR = 16 * qps * g.ngenR;  // per 128-row block
-    const int total = g.H4 * jobsL + g.H1 * jobsR;
+    // Work of one plane: 2-row units (two rows x four columns, two Philox
+    // calls) of the generated 128-row blocks, column-side blocks first; each
+    // thread takes a contiguous range of units, so no thread does more than
+    // one unit above the average.
+    constexpr int upb = 64 * qps;                 // units per block
+    const int nbL = g.H4 * g.ngenL, nbR = g.H1 * g.ngenR;
+    const int nunits = (nbL + nbR) * upb;
+    const int u_beg = nunits * rt / (kRngWarps * 32), u_end = nunits * (rt + 1) / (kRngWarps * 32);
+    // position of the first unit (the same on every plane)
+    const int bi_beg = u_beg / upb, rp_beg = (u_beg % upb) / qps, nq_beg = u_beg % qps;
+    // Per-plane state of the block a unit lies in: unit (rp, nq) covers rows
+    // row0 + rstep * {2 rp, 2 rp + 1} of stream sid, columns n0 .. n0 + 3.
+    struct Blk {
+      int64_t row0, rstep;
+      uint32_t dst0, sid;
+      int n0;
+    };
+    auto block_state = [&](int bi, int64_t w, int64_t kLp, int64_t kRp, int buf) {
+      Blk bs;
+      const bool colside = bi < nbL;
+      const int bj = colside ? bi : bi - nbL;
+      const int H = colside ? g.H4 : g.H1;
+      const int blk = bj % H, gi = bj / H;
+      const int sn = s_gen[(colside ? 0 : 4) + gi];
+      const SkTc& sk = colside ? s_col[sn] : s_row[sn];
+      // column side: row = key + hstride * i_d; row side: row = i_1 + n1 * key
+      bs.row0 = colside ? col_key(g, sk, w, kRp) + sk.hstride * (g.first + blk * 128)
+                        : blk * 128 + g.n1 * row_key(g, sk, w, kLp);
+      bs.rstep = colside ? sk.hstride : 1;
+      bs.sid = (uint32_t)sk.sid;
+      bs.n0 = sn * ell;
+      bs.dst0 = sB + (buf * kBBlks + (colside ? blk : 2 + blk)) * kBBlkB;
+      return bs;
+    };
     uint32_t pi = 0;
     int64_t tab_last[2] = {-1, -1};  // last plane whose staged copies used each buffer
     for (int64_t t = t_beg; t < ntiles && !*abort_flag; ++t) {
@@ -780,51 +845,29 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
                          bar(TAB_FULL + buf));
             }
           }
-          for (int job = rt; job < total; job += kRngWarps * 32) {
-            bool colside;
-            int blk, jj;
-            if (job < g.H4 * jobsL) {
-              colside = true;
-              blk = job / jobsL;
-              jj = job % jobsL;
-            } else {
-              colside = false;
-              blk = (job - g.H4 * jobsL) / jobsR;
-              jj = (job - g.H4 * jobsL) % jobsR;
-            }
-            const int kg = jj & 15, rest = jj >> 4;
-            const int gi = rest / qps, nq = rest % qps;
-            const int s = s_gen[(colside ? 0 : 4) + gi];
-            const int n0 = s * ell + 4 * nq;
-            const SkTc& sk = colside ? s_col[s] : s_row[s];
-            const uint32_t sid = (uint32_t)sk.sid;
-            // column side: row = key + hstride * i_d; row side: row = i_1 + n1 * key
-            const int64_t rbase = colside ? col_key(g, sk, w, kRp) + sk.hstride * (g.first + blk * 128 + 8 * kg)
-                                          : blk * 128 + 8 * kg + g.n1 * row_key(g, sk, w, kLp);
-            const int64_t rstep = colside ? sk.hstride : 1;
-            // four rows are generated together (independent chains) and packed
-            // to BF16 pairs
-            uint32_t pk[4][4];
-#pragma unroll
-            for (int kk = 0; kk < 8; kk += 4) {
-              float4 r4[4];
-#pragma unroll
-              for (int h = 0; h < 4; ++h)
-                r4[h] = normals4_f32(g.seed, sid, (uint64_t)(rbase + rstep * (kk + h)), (uint32_t)nq);
-#pragma unroll
-              for (int h = 0; h < 4; h += 2) {
-                pk[0][(kk + h) >> 1] = bf16x2_bits(r4[h].x, r4[h + 1].x);
-                pk[1][(kk + h) >> 1] = bf16x2_bits(r4[h].y, r4[h + 1].y);
-                pk[2][(kk + h) >> 1] = bf16x2_bits(r4[h].z, r4[h + 1].z);
-                pk[3][(kk + h) >> 1] = bf16x2_bits(r4[h].w, r4[h + 1].w);
+          // this thread's units in order: two Philox chains per unit
+          if (u_beg < u_end) {
+            int bi = bi_beg, rp = rp_beg, nq = nq_beg;
+            Blk bs = block_state(bi, w, kLp, kRp, buf);
+            for (int u = u_beg; u < u_end; ++u) {
+              const int k = 2 * rp;  // row of the block (i_d or i_1 offset)
+              const int64_t row = bs.row0 + bs.rstep * k;
+              const float4 ra = normals4_f32(g.seed, bs.sid, (uint64_t)row, (uint32_t)nq);
+              const float4 rb = normals4_f32(g.seed, bs.sid, (uint64_t)(row + bs.rstep), (uint32_t)nq);
+              const int n0 = bs.n0 + 4 * nq;  // a multiple of 4: one core matrix holds n0 .. n0 + 3
+              const uint32_t dst = bs.dst0 + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
+              st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
+              st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
+              st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
+              st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+              if (++nq == qps) {
+                nq = 0;
+                if (++rp == 64) {
+                  rp = 0;
+                  ++bi;
+                  if (u + 1 < u_end) bs = block_state(bi, w, kLp, kRp, buf);
+                }
               }
-            }
-            const uint32_t base = sB + (buf * kBBlks + (colside ? blk : 2 + blk)) * kBBlkB;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int n = n0 + u;
-              const uint32_t off = kg * kS1 + (n >> 3) * kS4 + (n & 7) * 16;
-              st_shared_v4(base + off, pk[u][0], pk[u][1], pk[u][2], pk[u][3]);
             }
           }
           fence_async_smem();
