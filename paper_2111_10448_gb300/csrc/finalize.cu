@@ -129,6 +129,21 @@ __device__ void apply_q(const double* V, int64_t ldv, const double* beta, int nr
   }
 }
 
+// Copies an nr x w column-major block (leading dimension ldy) into shared
+// memory (leading dimension lda); eight independent loads per thread are in
+// flight at a time.
+__device__ void load_block(double* A, int lda, const double* Y, int64_t ldy, int nr, int w) {
+  for (int c0 = 0; c0 < w; c0 += 8)
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (c0 + u < w) ? Y[r + ldy * (c0 + u)] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < w) A[r + lda * (c0 + u)] = v[u];
+    }
+}
+
 __device__ __forceinline__ void flag_status(char* wsb, int bits) {
   atomicOr(reinterpret_cast<int*>(wsb + kStatusOff), bits);
 }
@@ -154,14 +169,11 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, 
   double* beta = red + 32;                // w
   double* rdiag = beta + TT_MAXL;         // w
   double* Rs = rdiag + TT_MAXL;           // w x w (root only)
-  double* Q2 = Rs + TT_MAXL * TT_MAXL;    // w x w (root only)
+  double* Q2 = Rs + w * w;                // w x w (root only), then w x w of rank sums
   __shared__ int piv[TT_MAXL];
   __shared__ int s_rank;
   double* Y = ws + s.lev_mat[L];
-  for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
-    const int r = o % nr, c = o / nr;
-    A[r + lda * c] = Y[r0 + r + m * c];
-  }
+  load_block(A, lda, Y + r0, m, nr, w);
   __syncthreads();
   house_qr(A, lda, nr, w, beta, rdiag, red);
   const int kmax = min(nr, w);
@@ -287,7 +299,25 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, 
   }
   for (int c = threadIdx.x; c < w; c += blockDim.x) reinterpret_cast<int*>(ws + s.off_piv)[c] = piv[c];
   __syncthreads();
-  // rank decision
+  // rank decision.  tail(r) = ||Rt(r:, r:)||_F^2 = sum_{c >= r} t_c(r) with
+  // t_c(r) = sum_{i = r..c} Rt(i, c)^2; thread c forms t_c(.) by a running sum
+  // from the diagonal up, then tail(r) is summed over the columns.
+  double* tcol = Q2 + w * w;  // t_c(r) at [r + w c] (r <= c), w x w
+  __shared__ double tails[TT_MAXL + 1];
+  for (int c = threadIdx.x; c < w; c += blockDim.x) {
+    double run = 0.0;
+    for (int i2 = c; i2 >= 0; --i2) {
+      run += Rt[i2 + w * c] * Rt[i2 + w * c];
+      tcol[i2 + w * c] = run;
+    }
+  }
+  __syncthreads();
+  for (int cand = threadIdx.x; cand <= w; cand += blockDim.x) {
+    double tail = 0.0;
+    for (int c = cand; c < w; ++c) tail += tcol[cand + w * c];
+    tails[cand] = tail;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const int limit = min(s.rpad, w);
     int r = s.target_rank;
@@ -296,10 +326,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, 
       r = limit;
       bool met = false;
       for (int cand = 1; cand <= limit; ++cand) {
-        double tail = 0.0;
-        for (int c = cand; c < w; ++c)
-          for (int i2 = cand; i2 <= c; ++i2) tail += Rt[i2 + w * c] * Rt[i2 + w * c];
-        if (sqrt(tail) <= thr) {
+        if (sqrt(tails[cand]) <= thr) {
           r = cand;
           met = true;
           break;
@@ -356,10 +383,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int L,
   double* V = sm;
   double* beta = V + (size_t)lda * w;
   const double* Y = ws + s.lev_mat[L];
-  for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
-    const int rr = o % nr, c = o / nr;
-    V[rr + lda * c] = Y[r0 + rr + m * c];
-  }
+  load_block(V, lda, Y + r0, m, nr, w);
   for (int i = threadIdx.x; i < w; i += blockDim.x) beta[i] = ws[s.lev_beta[L] + (int64_t)task.blk * w + i];
   const int64_t m1 = s.lev_rows[L + 1];
   const double* Zin = ws + s.lev_z[L + 1];
@@ -559,28 +583,38 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
       ldb = sb.rows;
     }
   }
-  for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.y * blockDim.x) {
+  const bool copy = left ? (A == nullptr) : (B == nullptr);
+  if (copy) {
+    // G_1 = Q_1 or G_d = P_{d-1}^T: one thread per entry
+    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.y * blockDim.x) {
+      const int a = (int)(e % rpa);
+      const int64_t i = (e / rpa) % nk;
+      const int c = (int)(e / (rpa * nk));
+      double v = 0.0;
+      if (a < ra && c < rc) v = left ? B[i + ldb * c] : A[i + lda * a];
+      G[e] = v;
+    }
+    return;
+  }
+  // one warp per entry, the lanes split the contraction (coalesced along u
+  // on the left side, along v for B on the right side)
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.y * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5); e < total; e += nwarps) {
     const int a = (int)(e % rpa);
     const int64_t i = (e / rpa) % nk;
     const int c = (int)(e / (rpa * nk));
     double acc = 0.0;
     if (a < ra && c < rc) {
       if (left) {
-        if (A == nullptr) {
-          acc = B[i + ldb * c];
-        } else {
-          for (int64_t u = 0; u < inner; ++u) acc += A[u + lda * a] * B[u + inner * i + ldb * c];
-        }
+        for (int64_t u = lane; u < inner; u += 32) acc += A[u + lda * a] * B[u + inner * i + ldb * c];
       } else {
-        if (B == nullptr) {
-          acc = A[i + lda * a];
-        } else {
-          for (int64_t v = 0; v < inner; ++v) acc += A[i + nk * v + lda * a] * B[v + ldb * c];
-        }
+        for (int64_t v = lane; v < inner; v += 32) acc += A[i + nk * v + lda * a] * B[v + ldb * c];
       }
+      acc = warp_sum(acc);
     }
-    G[e] = acc;
+    if (lane == 0) G[e] = acc;
   }
 }
 
@@ -705,7 +739,7 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
       const DevSketch& d = sks[it.sk0 + s];
       if (!d.basis) continue;
       const size_t need = sizeof(double) * ((size_t)(d.bl + 1) * d.width + 32 + 2 * TT_MAXL +
-                                            2 * TT_MAXL * TT_MAXL);
+                                            3 * (size_t)d.width * d.width);
       smem_up = std::max(smem_up, need);
     }
   }
@@ -758,7 +792,7 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)(nitems * TT_MAXD), 16);
+  dim3 grid((unsigned)(nitems * TT_MAXD), 64);
   count_launch();
   cores_kernel<<<grid, kThreads, 0, st>>>(wsb, cores, ranks, 0, nitems, 0);
   return cudaGetLastError();

@@ -159,8 +159,10 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     DevSketch& s = P.sketches[si];
     if (!s.basis) continue;
     const int w = s.width;
-    int bl = (int)((98304 / (8 * w)) / 32 * 32);
-    bl = std::max(bl, 2 * w);
+    // Row blocks of 256 (at least 2 l, a multiple of 32): a 65536-row sketch
+    // gives 256 leaf blocks of ~33 KB each, several resident per SM, so the
+    // leaf level spreads its FP64 work over the whole GPU.
+    const int bl = std::max(256, (2 * w + 31) / 32 * 32);
     s.bl = bl;
     int64_t m = s.rows;
     int L = 0;
