@@ -57,6 +57,8 @@ struct DevSketch {
   int64_t off_rt;      // CPQR R factor of the root R (width x width)
   int64_t off_q2;      // CPQR Q factor (width x width)
   int64_t off_piv;     // pivots (width ints, stored as int in a double slot area)
+  int64_t sp_tab;      // small-plane kernel: byte offset of this sketch's staged
+                       // test-matrix rows (BF16), -1 when it is generated per plane
 };
 
 struct DevItem {
@@ -93,6 +95,8 @@ struct DevItem {
   int64_t off_Y;            // max_k N_k x rpad_k
   int64_t off_tctab;        // plane kernel: staged test-matrix blocks shared by many planes
   int64_t tctab_doubles;    // its size (0 when the plane kernel cannot serve the item)
+  int64_t off_sptab;        // small-plane kernel: staged test-matrix rows of the sketches
+  int64_t sptab_doubles;    // its size (0 when the small-plane kernel cannot serve the item)
 };
 
 struct Task {               // one block of one TSQR level (finalize)
@@ -144,6 +148,9 @@ cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t 
                                 int64_t count, void* ws, cudaStream_t st);
 bool mixed_tc_supported(const Plan& P, int item, int64_t count);
 bool use_tc_kernel(const Plan& P, int item, int64_t count);
+bool use_sp_kernel(const Plan& P, int item, int64_t count);
+cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                             cudaStream_t st);
 cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st);
 cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, void* Xt, int x_f64,
                                const void* Xcmp, int cmp_f64, double* out2, void* ws,

@@ -215,6 +215,33 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.tctab_doubles = (bytes + 7) / 8;
   }
   it.off_tctab = it.tctab_doubles ? ws.take(it.tctab_doubles) : 0;
+  // Staging area of the small-plane kernel (BF16, n_1 and n_d <= 32, one
+  // width l <= 32): the rows of every test matrix that many planes share
+  // (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches with
+  // wdiv < W: wdiv keys x n_1 rows), rounded to BF16, 2 * lpad bytes per row.
+  // A sketch whose table would exceed 512 MB is generated per plane instead.
+  it.sptab_doubles = 0;
+  {
+    bool ok = q.prec == TT_PREC_BF16 && q.x_dtype == TT_F32 && q.n[0] <= 32 && q.n[d - 1] <= 32;
+    for (int si = it.sk0; si < it.sk0 + it.nsk && ok; ++si)
+      ok = P.sketches[si].width == P.sketches[it.sk0].width && P.sketches[si].width <= 32;
+    int64_t bytes = 0;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+      DevSketch& s = P.sketches[si];
+      s.sp_tab = -1;
+      if (!ok) continue;
+      const int64_t lpad = s.width <= 16 ? 16 : 32;
+      int64_t tb = 0;
+      if (s.type == SK_COL && s.wdiv > 1) tb = (it.W / s.wdiv) * q.n[d - 1] * lpad * 2;
+      if (s.type == SK_ROW && s.wdiv < it.W) tb = s.wdiv * q.n[0] * lpad * 2;
+      if (tb > 0 && tb <= (512LL << 20)) {
+        s.sp_tab = bytes;
+        bytes += (tb + 255) / 256 * 256;
+      }
+    }
+    it.sptab_doubles = ok ? std::max<int64_t>(1, (bytes + 7) / 8) : 0;
+  }
+  it.off_sptab = it.sptab_doubles ? ws.take(it.sptab_doubles) : 0;
   // reconstruction interfaces
   for (int k = 1; k <= ds; ++k) it.off_L[k] = ws.take(it.N[k] * it.rpad[k]);
   for (int k = ds + 1; k <= d; ++k) it.off_Rt[k] = ws.take((int64_t)it.rpad[k - 1] * (it.N[d] / it.N[k - 1]));
@@ -459,7 +486,8 @@ int tt_sketch_kernel_kind(tt_plan_t plan, int64_t count_last) {
   Plan* P = as_plan(plan);
   if (!P || P->items.empty()) return -1;
   if (P->items[0].prec == TT_PREC_FP64) return 0;
-  return use_tc_kernel(*P, 0, count_last) ? 2 : 1;
+  if (use_tc_kernel(*P, 0, count_last)) return 2;
+  return use_sp_kernel(*P, 0, count_last) ? 3 : 1;
 }
 
 tt_status tt_plan_problem(tt_plan_t plan, int item, tt_problem* out) {

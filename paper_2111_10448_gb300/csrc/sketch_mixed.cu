@@ -1499,6 +1499,7 @@ bool use_tc_kernel(const Plan& P, int item, int64_t count) {
 cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t first, int64_t count,
                                 void* ws, cudaStream_t st) {
   if (use_tc_kernel(P, item, count)) return launch_sketch_tc(P, item, X, first, count, ws, st);
+  if (use_sp_kernel(P, item, count)) return launch_sketch_sp(P, item, X, first, count, ws, st);
   return launch_sketch_mma(P, item, X, first, count, ws, st);
 }
 

@@ -1,0 +1,397 @@
+// Small-plane fused multi-sketch (BF16 tensor cores, X split into hi + lo)
+// for tensors whose first and last modes are small (n_1, n_d <= 32), e.g. the
+// d = 6, n = 24 random-TT workload and the many small tensors of a batch.
+//
+// Every plane X(:, w, :) (n_1 x n_d, w = kL + WL kR with WL = N_{d*}/n_1)
+// contributes a plain product to every sketch of the one-pass sketch
+// (Sec. 3.2): column sketch k, S_k[a + n_1 (w mod N_k/n_1), j] +=
+// sum_b X(a, w, b) Omega_k[w div (N_k/n_1) + hs b, j], and row sketch k,
+// R_k[w div (N_k/n_1) + hs b, j] += sum_a X(a, w, b) Psi_k[a + n_1 (w mod
+// N_k/n_1), j].  Column-sketch rows depend on w only through kL and row-sketch
+// rows only through kR (N_k/n_1 divides WL for k <= d*, and WL divides it
+// for k >= d*).
+//
+// Why a separate kernel: with n = 24 and l = 26 a plane holds 576 entries but
+// each sketch needs 24 test-matrix rows of 26 normals.  Only the outermost
+// sketches (Omega_1: rows w + W b; Psi_{d-1}: rows a + n_1 w) have rows no
+// other plane uses; every other test matrix row is shared by many planes, so
+// those rows are generated once per call into a BF16 table (L2-resident for
+// the workloads here) and copied per plane.  That leaves about 2 l / n normals
+// per entry, the least any dense Gaussian sketch of these unfoldings needs.
+//
+// Organisation: one CTA of 16 warps per SM takes a contiguous run of blocks of
+// kT2 x kT3 planes (kL-major), one plane per warp; a warp converts its plane
+// to BF16 hi / lo in shared memory ([b][a], a contiguous), then for each
+// sketch builds the test-matrix block [k][j] and runs mma.sync m16n8k16 with
+// ldmatrix fragments (A = block^T, B = the plane or its transpose), adding
+// the FP32 results into shared accumulators with shared-memory atomics.
+// Accumulator slots: a column sketch has one slot per kL of the block (one if
+// its rows do not depend on w), a row sketch one per kR (one if its rows do not
+// depend on w).  Row slots are added into the FP64 sketches after every
+// block; column slots (and plane-independent row slots) when the kL block
+// changes or after kColFlushBlocks blocks, which bounds the FP32 chains.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace tts {
+
+const DevItem* plan_items_host(const Plan* p);
+const DevSketch* plan_sketches_host(const Plan* p);
+
+namespace sp {
+
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr int kT2 = 4, kT3 = 4;                 // planes per block: kT2 values of kL x kT3 values of kR
+constexpr int kLD = 40;                         // BF16 row stride of the 32-row tiles (80 bytes)
+constexpr int kTileElems = 32 * kLD;
+constexpr int kWarpBytes = 3 * kTileElems * 2;  // plane hi, plane lo, test-matrix block
+constexpr int kColFlushBlocks = 16;
+constexpr int kMaxSmem = 227 * 1024 - 2048;  // dynamic shared memory; the static part is below 2 KB
+
+struct SpSk {
+  int64_t rows, off, wdiv, hstride, tab;  // tab: byte offset of the staged rows, -1: generated per plane
+  int col, sid, nslot, slot0, lflush;     // lflush: flushed on the column-side schedule
+  int pad_;
+};
+
+struct SpArgs {
+  const float* X;
+  char* wsb;
+  uint64_t seed;
+  int64_t n1, cnt, first, W, WL, WR, Nd1, tilesL, tilesR, tab0;
+  int nsk, ell, nq, nslots, ldo;
+  SpSk sk[kMaxSk];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t a, uint32_t r[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t a, uint32_t r[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t a, uint32_t r[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Staged test-matrix rows of one sketch: entry (key, r, j), r < nr, j < lpad,
+// at byte ((key nr + r) lpad + j) 2 of `tab`: the BF16-rounded normal of row
+// key + hstride (first + r) (column side) or r + n1 key (row side), zero for
+// j >= l.
+__global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
+                                int64_t nkeys, char* tab) {
+  const int qpr = lpad / 4;
+  const int64_t total = nkeys * nr * qpr;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % qpr);
+    const int64_t rest = e / qpr;
+    const int r = (int)(rest % nr);
+    const int64_t key = rest / nr;
+    const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (first + r)) : (uint64_t)(r + n1 * key);
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * q < ell) z = normals4_f32(seed, (uint32_t)s.sid, row, (uint32_t)q);
+    const uint32_t lo = bf16x2(4 * q < ell ? z.x : 0.f, 4 * q + 1 < ell ? z.y : 0.f);
+    const uint32_t hi = bf16x2(4 * q + 2 < ell ? z.z : 0.f, 4 * q + 3 < ell ? z.w : 0.f);
+    *reinterpret_cast<uint2*>(tab + ((key * nr + r) * lpad + 4 * q) * 2) = make_uint2(lo, hi);
+  }
+}
+
+template <int LPAD>
+__global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ SpSk s_sk[kMaxSk];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < kMaxSk; ++s)
+    if (threadIdx.x == s && s < g.nsk) s_sk[s] = g.sk[s];
+  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(smraw + warp * kWarpBytes);
+  __nv_bfloat16* Xl = Xh + kTileElems;
+  __nv_bfloat16* Gs = Xl + kTileElems;
+  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
+  const int slot_elems = LPAD * g.ldo;
+  // zero the tiles (their padding rows and columns stay zero) and the slots
+  for (int i = threadIdx.x; i < kWarps * kWarpBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = threadIdx.x; i < g.nslots * slot_elems; i += kThreads) acc[i] = 0.0f;
+  __syncthreads();
+
+  const int n1 = (int)g.n1, cnt = (int)g.cnt;
+  double* ws = reinterpret_cast<double*>(g.wsb);
+
+  // Adds the slots of one flush class into the FP64 sketches and clears them.
+  auto flush = [&](bool long_class, int64_t bL, int64_t bR) {
+    for (int si = 0; si < g.nsk; ++si) {
+      const SpSk& s = s_sk[si];
+      if ((s.lflush != 0) != long_class) continue;
+      const int nout = s.col ? n1 : cnt;
+      const int n = s.nslot * slot_elems;
+      float* base = acc + (size_t)s.slot0 * slot_elems;
+      for (int e = threadIdx.x; e < n; e += kThreads) {
+        const float v = base[e];
+        if (v == 0.0f) continue;
+        base[e] = 0.0f;
+        const int sl = e / slot_elems, rem = e - sl * slot_elems;
+        const int j = rem / g.ldo, o = rem - j * g.ldo;
+        if (j >= g.ell || o >= nout) continue;
+        int64_t row;
+        if (s.col) {
+          const int64_t kL = bL * kT2 + sl;
+          row = o + g.n1 * (s.nslot > 1 ? kL % s.wdiv : 0);
+        } else {
+          const int64_t kR = bR * kT3 + sl;
+          const int64_t whi = s.nslot > 1 ? kR / (s.wdiv / g.WL) : 0;
+          row = whi + s.hstride * (g.first + o);
+        }
+        atomicAdd(ws + s.off + row + s.rows * j, (double)v);
+      }
+    }
+  };
+
+  const int64_t nblocks = g.tilesL * g.tilesR;
+  const int64_t b_beg = nblocks * blockIdx.x / gridDim.x, b_end = nblocks * (blockIdx.x + 1) / gridDim.x;
+  int64_t cur_bL = -1;
+  int age = 0;
+  for (int64_t t = b_beg; t < b_end; ++t) {
+    const int64_t bL = t / g.tilesR, bR = t - bL * g.tilesR;
+    if (bL != cur_bL || age == kColFlushBlocks) {
+      if (cur_bL >= 0) {
+        flush(true, cur_bL, 0);
+        __syncthreads();
+      }
+      cur_bL = bL;
+      age = 0;
+    }
+    ++age;
+    const int64_t kL0 = bL * kT2, kR0 = bR * kT3;
+    const int nA = (int)imin64(kT2, g.WL - kL0), nB = (int)imin64(kT3, g.WR - kR0);
+    for (int p = warp; p < nA * nB; p += kWarps) {
+      const int sa = p % nA, sb = p / nA;
+      const int64_t w = (kL0 + sa) + g.WL * (kR0 + sb);
+      // ---- the plane, split into BF16 hi + lo, [b][a]
+      {
+        const float* xp = g.X + g.n1 * w + lane;
+        float v[32];
+#pragma unroll
+        for (int b = 0; b < 32; ++b) v[b] = (b < cnt && lane < n1) ? __ldcs(xp + g.Nd1 * b) : 0.0f;
+        if (lane < n1) {
+#pragma unroll
+          for (int b = 0; b < 32; ++b) {
+            if (b < cnt) {
+              const __nv_bfloat16 h = __float2bfloat16_rn(v[b]);
+              Xh[b * kLD + lane] = h;
+              Xl[b * kLD + lane] = __float2bfloat16_rn(__fsub_rn(v[b], __bfloat162float(h)));
+            }
+          }
+        }
+      }
+      __syncwarp();
+      for (int si = 0; si < g.nsk; ++si) {
+        const SpSk& s = s_sk[si];
+        const int nr = s.col ? cnt : n1;     // contraction extent
+        const int nout = s.col ? n1 : cnt;   // output extent
+        const int kext = (nr + 15) & ~15;
+        // ---- test-matrix block Gs[k][j]
+        if (s.tab >= 0) {
+          const int64_t key = s.col ? w / s.wdiv : w % s.wdiv;
+          constexpr int cpr = LPAD / 8;  // 16-byte chunks per row
+          const uint4* src = reinterpret_cast<const uint4*>(g.wsb + g.tab0 + s.tab + key * nr * LPAD * 2);
+          for (int c = lane; c < nr * cpr; c += 32) {
+            const int r = c / cpr, q = c - r * cpr;
+            *reinterpret_cast<uint4*>(Gs + r * kLD + 8 * q) = __ldg(src + c);
+          }
+        } else {
+          const int64_t key = s.col ? w / s.wdiv : w % s.wdiv;
+          for (int c = lane; c < nr * g.nq; c += 32) {
+            const int r = c / g.nq, q = c - r * g.nq;
+            const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + r)) : (uint64_t)(r + g.n1 * key);
+            const float4 z = normals4_f32(g.seed, (uint32_t)s.sid, row, (uint32_t)q);
+            const uint32_t lo = bf16x2(4 * q < g.ell ? z.x : 0.f, 4 * q + 1 < g.ell ? z.y : 0.f);
+            const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z.z : 0.f, 4 * q + 3 < g.ell ? z.w : 0.f);
+            *reinterpret_cast<uint2*>(Gs + r * kLD + 4 * q) = make_uint2(lo, hi);
+          }
+        }
+        // contraction padding rows [nr, kext) (another sketch may have left rows there)
+        for (int c = lane; c < (kext - nr) * (LPAD / 8); c += 32) {
+          const int r = nr + c / (LPAD / 8), q = c % (LPAD / 8);
+          *reinterpret_cast<uint4*>(Gs + r * kLD + 8 * q) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncwarp();
+        // ---- D[j][o] = sum_k Gs[k][j] Xs'[k][o], hi and lo parts
+        const int ntn = (nout + 7) >> 3;
+        const int sl = s.nslot > 1 ? (s.col ? sa : sb) : 0;
+        float* slot = acc + (size_t)(s.slot0 + sl) * slot_elems;
+        const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+        for (int mt = 0; mt < LPAD / 16; ++mt) {
+          float c[4][4];
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+          for (int k0 = 0; k0 < kext; k0 += 16) {
+            uint32_t a[4];
+            ldsm_x4_trans(smem_u32(Gs + (k0 + (lane & 7) + 8 * (lane >> 4)) * kLD + mt * 16 + 8 * ((lane >> 3) & 1)), a);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              if (nt < ntn) {
+                uint32_t bh[2], bl[2];
+                if (s.col) {  // B[k][o] = X(o, k): the [b][a] tile read transposed
+                  const int off = (k0 + (lane & 7) + 8 * ((lane >> 3) & 1)) * kLD + nt * 8;
+                  ldsm_x2_trans(smem_u32(Xh + off), bh);
+                  ldsm_x2_trans(smem_u32(Xl + off), bl);
+                } else {      // B[k][o] = X(k, o): the [b][a] tile read as is
+                  const int off = (nt * 8 + (lane & 7)) * kLD + k0 + 8 * ((lane >> 3) & 1);
+                  ldsm_x2(smem_u32(Xh + off), bh);
+                  ldsm_x2(smem_u32(Xl + off), bl);
+                }
+                mma_bf16(c[nt], a, bh);
+                mma_bf16(c[nt], a, bl);
+              }
+            }
+          }
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            if (nt < ntn) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
+                if (j < g.ell && o < nout) atomicAdd(slot + j * g.ldo + o, c[nt][e]);
+              }
+            }
+          }
+        }
+        __syncwarp();  // every lane is done with Gs before the next sketch overwrites it
+      }
+    }
+    __syncthreads();
+    flush(false, cur_bL, bR);
+    __syncthreads();
+  }
+  if (cur_bL >= 0) flush(true, cur_bL, 0);
+}
+
+bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) {
+  const DevItem& it = plan_items_host(&P)[item];
+  if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sptab_doubles == 0) return false;
+  if (count < 1 || count > 32 || it.n[0] > 32) return false;
+  const DevSketch* sks = plan_sketches_host(&P);
+  SpArgs g;
+  memset(&g, 0, sizeof(g));
+  const int ell = sks[it.sk0].width;
+  const int lpad = ell <= 16 ? 16 : 32;
+  g.n1 = it.n[0];
+  g.cnt = count;
+  g.W = it.W;
+  g.WL = it.N[it.ds] / it.n[0];
+  g.WR = g.W / g.WL;
+  g.Nd1 = it.N[it.d - 1];
+  g.tilesL = (g.WL + kT2 - 1) / kT2;
+  g.tilesR = (g.WR + kT3 - 1) / kT3;
+  g.tab0 = it.off_sptab * 8;
+  g.seed = it.seed;
+  g.nsk = it.nsk;
+  g.ell = ell;
+  g.nq = (ell + 3) / 4;
+  g.ldo = (int)((std::max<int64_t>(g.n1, count) + 7) / 8 * 8);
+  int slots = 0;
+  for (int s = 0; s < it.nsk; ++s) {
+    const DevSketch& d = sks[it.sk0 + s];
+    if (d.width != ell) return false;
+    SpSk k;
+    k.rows = d.rows;
+    k.off = d.off;
+    k.wdiv = d.wdiv;
+    k.hstride = d.hstride;
+    k.tab = d.sp_tab;
+    k.col = d.type == SK_COL ? 1 : 0;
+    k.sid = d.stream_id;
+    const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
+    k.nslot = per_plane_rows ? (k.col ? kT2 : kT3) : 1;
+    k.slot0 = slots;
+    k.lflush = (k.col || k.nslot == 1) ? 1 : 0;
+    k.pad_ = 0;
+    slots += k.nslot;
+    g.sk[s] = k;
+  }
+  g.nslots = slots;
+  const size_t need = (size_t)kWarps * kWarpBytes + sizeof(float) * (size_t)slots * lpad * g.ldo;
+  if (need > (size_t)kMaxSmem) return false;
+  *out = g;
+  *smem = need;
+  return true;
+}
+
+}  // namespace sp
+
+bool use_sp_kernel(const Plan& P, int item, int64_t count) {
+  static int force = -1;
+  if (force < 0) {
+    const char* e = getenv("TT_SKETCH_KERNEL");
+    force = (e && strcmp(e, "mma") == 0) ? 1 : 0;
+  }
+  sp::SpArgs g;
+  size_t smem;
+  return force == 0 && sp::plan_sp(P, item, count, &g, &smem);
+}
+
+cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                             cudaStream_t st) {
+  sp::SpArgs g;
+  size_t smem = 0;
+  if (!sp::plan_sp(P, item, count, &g, &smem)) return cudaErrorNotSupported;
+  g.X = (const float*)X;
+  g.wsb = (char*)ws;
+  g.first = first;
+  const int lpad = g.ell <= 16 ? 16 : 32;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sp::sketch_sp_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         sp::kMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(sp::sketch_sp_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // leave no pending error for the caller's next runtime call
+      return e;
+    }
+    attr_set = true;
+  }
+  const DevItem& it = plan_items_host(&P)[item];
+  for (int s = 0; s < g.nsk; ++s) {
+    const sp::SpSk& k = g.sk[s];
+    if (k.tab < 0) continue;
+    const int nr = k.col ? (int)count : (int)g.n1;
+    const int64_t nkeys = k.col ? it.W / k.wdiv : k.wdiv;
+    const int64_t total = nkeys * nr * (lpad / 4);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count());
+    count_launch();
+    sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, g.seed, first, g.n1, nr, g.ell, lpad, nkeys,
+                                                g.wsb + g.tab0 + k.tab);
+  }
+  const int64_t nblocks = g.tilesL * g.tilesR;
+  const int grid = (int)std::min<int64_t>(nblocks, device_sm_count());
+  count_launch();
+  if (lpad == 16) sp::sketch_sp_kernel<16><<<grid, sp::kThreads, smem, st>>>(g);
+  else sp::sketch_sp_kernel<32><<<grid, sp::kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace tts

@@ -260,3 +260,49 @@ def test_pinned_host_tensor_read_directly_equals_device_tensor():
     ra, rb = a.reconstruct(torch.float64).cpu().numpy(), b.reconstruct(torch.float64).cpu().numpy()
     assert a.status()[1] == b.status()[1]
     assert np.linalg.norm(ra - rb) <= 1e-9 * np.linalg.norm(ra)
+
+
+# --------------------------------------------------------- small-plane kernel
+@pytest.mark.parametrize("dims,kw", [
+    ([9, 8, 7, 6, 5, 9], dict(eps=1e-5, rmax=6, p=6)),       # d = 6, l = 12; 56 x 30 planes (ragged blocks)
+    ([24, 6, 5, 24], dict(eps=1e-5, rmax=16, p=10)),          # l = 26; 6 x 5 planes (ragged blocks)
+    ([17, 11, 23], dict(ranks=[1, 4, 4, 1], p=5)),            # d = 3, odd sizes
+    ([30, 31], dict(ranks=[1, 5, 1], p=5)),                   # d = 2: one plane
+    ([8, 7, 6, 5, 4], dict(eps=1e-5, rmax=8, p=5)),           # d = 5
+    ([15, 15, 15, 15, 15, 15], dict(eps=1e-5, rmax=16, p=10)),  # ~21 blocks per CTA: periodic flushes
+])
+def test_small_plane_sketches_match_oracle(dims, kw):
+    """The small-plane kernel (n_1, n_d <= 32): every sketch entry against the
+    oracle's FP64 products of the split X with the rounded test matrices."""
+    d = len(dims)
+    x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", **kw)
+    assert t.kernel_kind() == 3
+    t.begin()
+    t.accumulate(to_dev(x), 0, dims[-1])
+    sk = sketch_dict(t)
+    t.finalize()
+    st, _ = t.status()
+    assert st in (0, N.TT_WARN_RANK_CAP)
+    xs = _split(x.astype(np.float64), "bf16")
+    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt="bf16", **kw)
+    for k, S in o["sketch"]["S"].items():
+        _close_sketch(sk[(0, k)], S, ("S", k))
+    for k, R in o["sketch"]["R"].items():
+        _close_sketch(sk[(1, k)], R, ("R", k))
+
+
+def test_small_plane_within_10eps_of_oracle():
+    """The precision-form shape at reduced n: X~ from the small-plane kernel
+    within 10 eps of the FP64 oracle's X~ and of X."""
+    dims, eps = [10] * 6, 1e-5
+    x = ti.random_tt(dims, [1, 10, 10, 10, 10, 10, 1], seed=0, noise=1e-6).astype(np.float32)
+    x64 = x.astype(np.float64)
+    t = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec="bf16")
+    assert t.kernel_kind() == 3
+    t.pstt2(to_dev(x))
+    o = OP.pstt2(x64, dims, eps=eps, rmax=16, p=10, seed=1)
+    xt = t.reconstruct().cpu().numpy()
+    e_or, e_x = rel(xt, OT.tt_full(o["cores"]), x64), rel(xt, x64, x64)
+    print(f"small-plane: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} ranks={t.status()[1]}")
+    assert e_or <= 10 * eps and e_x <= 10 * eps
