@@ -139,31 +139,32 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
   const int n1 = (int)g.n1, cnt = (int)g.cnt;
   double* ws = reinterpret_cast<double*>(g.wsb);
 
-  // Adds the slots of one flush class into the FP64 sketches and clears them.
+  // Adds the slots of one flush class into the FP64 sketches and clears them:
+  // warps take the (slot, j) rows, lanes the outputs o.
   auto flush = [&](bool long_class, int64_t bL, int64_t bR) {
     for (int si = 0; si < g.nsk; ++si) {
       const SpSk& s = s_sk[si];
       if ((s.lflush != 0) != long_class) continue;
       const int nout = s.col ? n1 : cnt;
-      const int n = s.nslot * slot_elems;
-      float* base = acc + (size_t)s.slot0 * slot_elems;
-      for (int e = threadIdx.x; e < n; e += kThreads) {
-        const float v = base[e];
-        if (v == 0.0f) continue;
-        base[e] = 0.0f;
-        const int sl = e / slot_elems, rem = e - sl * slot_elems;
-        const int j = rem / g.ldo, o = rem - j * g.ldo;
-        if (j >= g.ell || o >= nout) continue;
-        int64_t row;
+      const int nrow = s.nslot * g.ell;
+      for (int rr = warp; rr < nrow; rr += kWarps) {
+        const int sl = rr / g.ell, j = rr - sl * g.ell;
+        float* p = acc + (size_t)(s.slot0 + sl) * slot_elems + j * g.ldo;
+        int64_t base;
         if (s.col) {
           const int64_t kL = bL * kT2 + sl;
-          row = o + g.n1 * (s.nslot > 1 ? kL % s.wdiv : 0);
+          base = g.n1 * (s.nslot > 1 ? kL % s.wdiv : 0);
         } else {
           const int64_t kR = bR * kT3 + sl;
-          const int64_t whi = s.nslot > 1 ? kR / (s.wdiv / g.WL) : 0;
-          row = whi + s.hstride * (g.first + o);
+          base = (s.nslot > 1 ? kR / (s.wdiv / g.WL) : 0) + s.hstride * g.first;
         }
-        atomicAdd(ws + s.off + row + s.rows * j, (double)v);
+        for (int o = lane; o < nout; o += 32) {
+          const float v = p[o];
+          if (v == 0.0f) continue;
+          p[o] = 0.0f;
+          const int64_t row = s.col ? base + o : base + s.hstride * o;
+          atomicAdd(ws + s.off + row + s.rows * j, (double)v);
+        }
       }
     }
   };
@@ -206,14 +207,23 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
         }
       }
       __syncwarp();
-      for (int si = 0; si < g.nsk; ++si) {
+      const uint32_t kLp = (uint32_t)(kL0 + sa), kRp = (uint32_t)(kR0 + sb);
+      for (int sj = 0; sj < g.nsk; ++sj) {
+        // warps start at different sketches, so that at any moment they add
+        // into different accumulator slots (less shared-atomic contention)
+        const int si = (sj + warp) % g.nsk;
         const SpSk& s = s_sk[si];
         const int nr = s.col ? cnt : n1;     // contraction extent
         const int nout = s.col ? n1 : cnt;   // output extent
         const int kext = (nr + 15) & ~15;
+        // key of the plane's test-matrix rows: w div wdiv (column side) or
+        // w mod wdiv (row side); wdiv divides WL (column) or WL divides wdiv
+        // (row), so both follow from kL and kR in 32-bit arithmetic
+        const uint32_t wd = (uint32_t)s.wdiv, wl = (uint32_t)g.WL;
+        const int64_t key = s.col ? (int64_t)(kLp / wd) + (int64_t)(wl / wd) * kRp
+                                  : (int64_t)kLp + (int64_t)wl * (kRp % (wd / wl));
         // ---- test-matrix block Gs[k][j]
         if (s.tab >= 0) {
-          const int64_t key = s.col ? w / s.wdiv : w % s.wdiv;
           constexpr int cpr = LPAD / 8;  // 16-byte chunks per row
           const uint4* src = reinterpret_cast<const uint4*>(g.wsb + g.tab0 + s.tab + key * nr * LPAD * 2);
           for (int c = lane; c < nr * cpr; c += 32) {
@@ -221,14 +231,32 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
             *reinterpret_cast<uint4*>(Gs + r * kLD + 8 * q) = __ldg(src + c);
           }
         } else {
-          const int64_t key = s.col ? w / s.wdiv : w % s.wdiv;
-          for (int c = lane; c < nr * g.nq; c += 32) {
-            const int r = c / g.nq, q = c - r * g.nq;
-            const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + r)) : (uint64_t)(r + g.n1 * key);
-            const float4 z = normals4_f32(g.seed, (uint32_t)s.sid, row, (uint32_t)q);
-            const uint32_t lo = bf16x2(4 * q < g.ell ? z.x : 0.f, 4 * q + 1 < g.ell ? z.y : 0.f);
-            const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z.z : 0.f, 4 * q + 3 < g.ell ? z.w : 0.f);
-            *reinterpret_cast<uint2*>(Gs + r * kLD + 4 * q) = make_uint2(lo, hi);
+          // jobs c = (row r, column quad q), two per lane at a time (independent
+          // Philox chains); r = c div nq by a multiply-shift that is exact for
+          // c < 2^10, nq <= 8
+          const int njobs = nr * g.nq;
+          const uint32_t inv = (65536u + (uint32_t)g.nq - 1u) / (uint32_t)g.nq;
+          for (int c0 = lane; c0 < njobs; c0 += 64) {
+            float4 z[2];
+            int rr[2], qq[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c = min(c0 + 32 * h, njobs - 1);
+              rr[h] = (int)(((uint32_t)c * inv) >> 16);
+              qq[h] = c - rr[h] * g.nq;
+              const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + rr[h]))
+                                         : (uint64_t)(rr[h] + g.n1 * key);
+              z[h] = normals4_f32(g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (c0 + 32 * h < njobs) {
+                const int q = qq[h];
+                const uint32_t lo = bf16x2(4 * q < g.ell ? z[h].x : 0.f, 4 * q + 1 < g.ell ? z[h].y : 0.f);
+                const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z[h].z : 0.f, 4 * q + 3 < g.ell ? z[h].w : 0.f);
+                *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
+              }
+            }
           }
         }
         // contraction padding rows [nr, kext) (another sketch may have left rows there)
@@ -242,43 +270,63 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
         const int sl = s.nslot > 1 ? (s.col ? sa : sb) : 0;
         float* slot = acc + (size_t)(s.slot0 + sl) * slot_elems;
         const int gq = lane >> 2, tq = lane & 3;
+        constexpr int MT = LPAD / 16;
+        // every fragment of a k-step is loaded first, then the MMAs run over
+        // independent accumulators (m-tile x n-tile x hi / lo), so consecutive
+        // MMAs do not wait on each other
+        float ch[MT][4][4], cl[MT][4][4];
 #pragma unroll
-        for (int mt = 0; mt < LPAD / 16; ++mt) {
-          float c[4][4];
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-          for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-          for (int k0 = 0; k0 < kext; k0 += 16) {
-            uint32_t a[4];
-            ldsm_x4_trans(smem_u32(Gs + (k0 + (lane & 7) + 8 * (lane >> 4)) * kLD + mt * 16 + 8 * ((lane >> 3) & 1)), a);
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ch[mt][nt][e] = cl[mt][nt][e] = 0.0f;
+#pragma unroll
+        for (int k0 = 0; k0 < 32; k0 += 16) {
+          if (k0 < kext) {
+            uint32_t a[MT][4], bh[4][2], bl[4][2];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+              ldsm_x4_trans(smem_u32(Gs + (k0 + (lane & 7) + 8 * (lane >> 4)) * kLD + mt * 16 + 8 * ((lane >> 3) & 1)),
+                            a[mt]);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
               if (nt < ntn) {
-                uint32_t bh[2], bl[2];
                 if (s.col) {  // B[k][o] = X(o, k): the [b][a] tile read transposed
                   const int off = (k0 + (lane & 7) + 8 * ((lane >> 3) & 1)) * kLD + nt * 8;
-                  ldsm_x2_trans(smem_u32(Xh + off), bh);
-                  ldsm_x2_trans(smem_u32(Xl + off), bl);
+                  ldsm_x2_trans(smem_u32(Xh + off), bh[nt]);
+                  ldsm_x2_trans(smem_u32(Xl + off), bl[nt]);
                 } else {      // B[k][o] = X(k, o): the [b][a] tile read as is
                   const int off = (nt * 8 + (lane & 7)) * kLD + k0 + 8 * ((lane >> 3) & 1);
-                  ldsm_x2(smem_u32(Xh + off), bh);
-                  ldsm_x2(smem_u32(Xl + off), bl);
+                  ldsm_x2(smem_u32(Xh + off), bh[nt]);
+                  ldsm_x2(smem_u32(Xl + off), bl[nt]);
                 }
-                mma_bf16(c[nt], a, bh);
-                mma_bf16(c[nt], a, bl);
               }
             }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt)
+                if (nt < ntn) mma_bf16(ch[mt][nt], a[mt], bh[nt]);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt)
+                if (nt < ntn) mma_bf16(cl[mt][nt], a[mt], bl[nt]);
           }
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
             if (nt < ntn) {
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
-                if (j < g.ell && o < nout) atomicAdd(slot + j * g.ldo + o, c[nt][e]);
+                if (j < g.ell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
               }
             }
           }
-        }
         __syncwarp();  // every lane is done with Gs before the next sketch overwrites it
       }
     }
@@ -292,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
 bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) {
   const DevItem& it = plan_items_host(&P)[item];
   if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sptab_doubles == 0) return false;
-  if (count < 1 || count > 32 || it.n[0] > 32) return false;
+  if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
   const DevSketch* sks = plan_sketches_host(&P);
   SpArgs g;
   memset(&g, 0, sizeof(g));
