@@ -151,6 +151,9 @@ bool use_tc_kernel(const Plan& P, int item, int64_t count);
 bool use_sp_kernel(const Plan& P, int item, int64_t count);
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st);
+bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out);
+cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
+                                     cudaStream_t st);
 cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st);
 cudaError_t launch_reconstruct(const Plan& P, int item, const double* cores, void* Xt, int x_f64,
                                const void* Xcmp, int cmp_f64, double* out2, void* ws,

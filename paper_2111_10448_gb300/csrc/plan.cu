@@ -615,10 +615,15 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   if (s != TT_OK) return s;
   const bool f64 = P->items[0].prec == TT_PREC_FP64;
   std::vector<BatchCfg> cands;
-  for (int ta : {32, 64}) {
-    if (!f64 && ta == 32) continue;
-    for (int chunk : {1, 4, 16})
-      for (int cps : {2, 4, 8}) cands.push_back(BatchCfg{ta, chunk, cps});
+  if (!f64 && sp_batched_eligible(*P, nullptr, nullptr)) {
+    // small-plane batched kernel: one CTA per SM, only the units per grab vary
+    for (int chunk : {1, 2, 4, 8}) cands.push_back(BatchCfg{64, chunk, 1});
+  } else {
+    for (int ta : {32, 64}) {
+      if (!f64 && ta == 32) continue;
+      for (int chunk : {1, 4, 16})
+        for (int cps : {2, 4, 8}) cands.push_back(BatchCfg{ta, chunk, cps});
+    }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return TT_ERR_CUDA;

@@ -20,7 +20,8 @@
 // per entry, the least any dense Gaussian sketch of these unfoldings needs.
 //
 // Organisation: one CTA of 16 warps per SM takes a contiguous run of blocks of
-// kT2 x kT3 planes (kL-major), one plane per warp; a warp converts its plane
+// T2 x T3 = 16 planes (kL-major; 4 x 4, or 8 x 2 / 16 x 1 when there are only
+// two / one kR values), one plane per warp; a warp converts its plane
 // to BF16 hi / lo in shared memory ([b][a], a contiguous), then for each
 // sketch builds the test-matrix block [k][j] and runs mma.sync m16n8k16 with
 // ldmatrix fragments (A = block^T, B = the plane or its transpose), adding
@@ -42,17 +43,19 @@ namespace tts {
 
 const DevItem* plan_items_host(const Plan* p);
 const DevSketch* plan_sketches_host(const Plan* p);
+int plan_num_items(const Plan* p);
 
 namespace sp {
 
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
-constexpr int kT2 = 4, kT3 = 4;                 // planes per block: kT2 values of kL x kT3 values of kR
+constexpr int kBlockPlanes = kWarps;          // planes per block: T2 values of kL x T3 values of kR
 constexpr int kLD = 40;                         // BF16 row stride of the 32-row tiles (80 bytes)
 constexpr int kTileElems = 32 * kLD;
 constexpr int kWarpBytes = 3 * kTileElems * 2;  // plane hi, plane lo, test-matrix block
 constexpr int kColFlushBlocks = 16;
-constexpr int kMaxSmem = 227 * 1024 - 2048;  // dynamic shared memory; the static part is below 2 KB
+constexpr int kMaxSmem = 227 * 1024 - 2048;
+constexpr int64_t kTableOffB = 256;  // dynamic shared memory; the static part is below 2 KB
 
 struct SpSk {
   int64_t rows, off, wdiv, hstride, tab;  // tab: byte offset of the staged rows, -1: generated per plane
@@ -66,8 +69,18 @@ struct SpArgs {
   uint64_t seed;
   int64_t n1, cnt, first, W, WL, WR, Nd1, tilesL, tilesR, tab0;
   int nsk, ell, nq, nslots, ldo;
+  int T2, T3;  // block shape
   SpSk sk[kMaxSk];
 };
+
+// Block shape of an item: 16 planes, as many kR values as there are (up to 4).
+__host__ __device__ inline void sp_block_shape(int64_t WL, int64_t WR, int* T2, int* T3) {
+  const int t3 = WR >= 4 ? 4 : (int)WR;
+  int t2 = kBlockPlanes / t3;
+  if (t2 > WL) t2 = (int)WL;
+  *T2 = t2;
+  *T3 = t3;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -98,12 +111,12 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
 // Staged test-matrix rows of one sketch: entry (key, r, j), r < nr, j < lpad,
 // at byte ((key nr + r) lpad + j) 2 of `tab`: the BF16-rounded normal of row
 // key + hstride (first + r) (column side) or r + n1 key (row side), zero for
-// j >= l.
-__global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
-                                int64_t nkeys, char* tab) {
+// j >= l.  Threads tid0, tid0 + nthr, ... of the caller take the entries.
+__device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
+                              int64_t nkeys, char* tab, int64_t tid0, int64_t nthr) {
   const int qpr = lpad / 4;
   const int64_t total = nkeys * nr * qpr;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = tid0; e < total; e += nthr) {
     const int q = (int)(e % qpr);
     const int64_t rest = e / qpr;
     const int r = (int)(rest % nr);
@@ -117,31 +130,62 @@ __global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1
   }
 }
 
+__global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
+                                int64_t nkeys, char* tab) {
+  sp_table_fill(s, seed, first, n1, nr, ell, lpad, nkeys, tab, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+}
+
+// Launch arguments of one item (the whole last mode when count = n_d), shared
+// by the host launch and the batched kernel.
+__host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks, int64_t count, SpArgs& g) {
+  g.n1 = it.n[0];
+  g.cnt = count;
+  g.W = it.W;
+  g.WL = it.N[it.ds] / it.n[0];
+  g.WR = g.W / g.WL;
+  g.Nd1 = it.N[it.d - 1];
+  sp_block_shape(g.WL, g.WR, &g.T2, &g.T3);
+  g.tilesL = (g.WL + g.T2 - 1) / g.T2;
+  g.tilesR = (g.WR + g.T3 - 1) / g.T3;
+  g.tab0 = it.off_sptab * 8;
+  g.seed = it.seed;
+  g.nsk = it.nsk;
+  g.ell = sks[it.sk0].width;
+  g.nq = (g.ell + 3) / 4;
+  const int64_t mx = g.n1 > count ? g.n1 : count;
+  g.ldo = (int)((mx + 7) / 8 * 8);
+  int slots = 0;
+  for (int s = 0; s < it.nsk; ++s) {
+    const DevSketch& d = sks[it.sk0 + s];
+    SpSk k;
+    k.rows = d.rows;
+    k.off = d.off;
+    k.wdiv = d.wdiv;
+    k.hstride = d.hstride;
+    k.tab = d.sp_tab;
+    k.col = d.type == SK_COL ? 1 : 0;
+    k.sid = d.stream_id;
+    const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
+    k.nslot = per_plane_rows ? (k.col ? g.T2 : g.T3) : 1;
+    k.slot0 = slots;
+    k.lflush = (k.col || k.nslot == 1) ? 1 : 0;
+    k.pad_ = 0;
+    slots += k.nslot;
+    g.sk[s] = k;
+  }
+  g.nslots = slots;
+}
+
+// Adds the slots of one flush class into the FP64 sketches and clears them:
+// warps take the (slot, j) rows, lanes the outputs o.
 template <int LPAD>
-__global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ SpSk s_sk[kMaxSk];
+__device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool long_class, int64_t bL, int64_t bR) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < kMaxSk; ++s)
-    if (threadIdx.x == s && s < g.nsk) s_sk[s] = g.sk[s];
-  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(smraw + warp * kWarpBytes);
-  __nv_bfloat16* Xl = Xh + kTileElems;
-  __nv_bfloat16* Gs = Xl + kTileElems;
-  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
-  const int slot_elems = LPAD * g.ldo;
-  // zero the tiles (their padding rows and columns stay zero) and the slots
-  for (int i = threadIdx.x; i < kWarps * kWarpBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int i = threadIdx.x; i < g.nslots * slot_elems; i += kThreads) acc[i] = 0.0f;
-  __syncthreads();
-
   const int n1 = (int)g.n1, cnt = (int)g.cnt;
+  const int slot_elems = LPAD * g.ldo;
   double* ws = reinterpret_cast<double*>(g.wsb);
-
-  // Adds the slots of one flush class into the FP64 sketches and clears them:
-  // warps take the (slot, j) rows, lanes the outputs o.
-  auto flush = [&](bool long_class, int64_t bL, int64_t bR) {
+  {
     for (int si = 0; si < g.nsk; ++si) {
       const SpSk& s = s_sk[si];
       if ((s.lflush != 0) != long_class) continue;
@@ -150,13 +194,14 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
       for (int rr = warp; rr < nrow; rr += kWarps) {
         const int sl = rr / g.ell, j = rr - sl * g.ell;
         float* p = acc + (size_t)(s.slot0 + sl) * slot_elems + j * g.ldo;
+        // kL < WL and kR < WR: 32-bit arithmetic (plan_sp requires W < 2^31)
         int64_t base;
         if (s.col) {
-          const int64_t kL = bL * kT2 + sl;
-          base = g.n1 * (s.nslot > 1 ? kL % s.wdiv : 0);
+          const uint32_t kL = (uint32_t)(bL * g.T2 + sl);
+          base = g.n1 * (int64_t)(s.nslot > 1 ? kL % (uint32_t)s.wdiv : 0u);
         } else {
-          const int64_t kR = bR * kT3 + sl;
-          base = (s.nslot > 1 ? kR / (s.wdiv / g.WL) : 0) + s.hstride * g.first;
+          const uint32_t kR = (uint32_t)(bR * g.T3 + sl);
+          base = (int64_t)(s.nslot > 1 ? kR / (uint32_t)(s.wdiv / g.WL) : 0u) + s.hstride * g.first;
         }
         for (int o = lane; o < nout; o += 32) {
           const float v = p[o];
@@ -167,25 +212,20 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
         }
       }
     }
-  };
+  }
+}
 
-  const int64_t nblocks = g.tilesL * g.tilesR;
-  const int64_t b_beg = nblocks * blockIdx.x / gridDim.x, b_end = nblocks * (blockIdx.x + 1) / gridDim.x;
-  int64_t cur_bL = -1;
-  int age = 0;
-  for (int64_t t = b_beg; t < b_end; ++t) {
-    const int64_t bL = t / g.tilesR, bR = t - bL * g.tilesR;
-    if (bL != cur_bL || age == kColFlushBlocks) {
-      if (cur_bL >= 0) {
-        flush(true, cur_bL, 0);
-        __syncthreads();
-      }
-      cur_bL = bL;
-      age = 0;
-    }
-    ++age;
-    const int64_t kL0 = bL * kT2, kR0 = bR * kT3;
-    const int nA = (int)imin64(kT2, g.WL - kL0), nB = (int)imin64(kT3, g.WR - kR0);
+// The planes of block (bL, bR), one per warp; no block-wide barrier inside.
+template <int LPAD>
+__device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw, float* acc, int64_t bL, int64_t bR) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(smraw + warp * kWarpBytes);
+  __nv_bfloat16* Xl = Xh + kTileElems;
+  __nv_bfloat16* Gs = Xl + kTileElems;
+  const int slot_elems = LPAD * g.ldo;
+  const int n1 = (int)g.n1, cnt = (int)g.cnt;
+  const int64_t kL0 = bL * g.T2, kR0 = bR * g.T3;
+  const int nA = (int)imin64(g.T2, g.WL - kL0), nB = (int)imin64(g.T3, g.WR - kR0);
     for (int p = warp; p < nA * nB; p += kWarps) {
       const int sa = p % nA, sb = p / nA;
       const int64_t w = (kL0 + sa) + g.WL * (kR0 + sb);
@@ -330,11 +370,174 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs g) 
         __syncwarp();  // every lane is done with Gs before the next sketch overwrites it
       }
     }
+}
+
+// Zeroes the per-warp tiles (their padding rows and columns stay zero) and
+// the accumulator slots.
+__device__ void sp_zero(unsigned char* smraw, float* acc, int acc_elems) {
+  for (int i = threadIdx.x; i < kWarps * kWarpBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = threadIdx.x; i < acc_elems; i += kThreads) acc[i] = 0.0f;
+}
+
+template <int LPAD>
+__global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ SpArgs g;
+  if (threadIdx.x == 0) g = ga;
+  __syncthreads();
+  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
+  sp_zero(smraw, acc, g.nslots * LPAD * g.ldo);
+  __syncthreads();
+  const int64_t nblocks = g.tilesL * g.tilesR;
+  const int64_t b_beg = nblocks * blockIdx.x / gridDim.x, b_end = nblocks * (blockIdx.x + 1) / gridDim.x;
+  int64_t cur_bL = -1;
+  int age = 0;
+  for (int64_t t = b_beg; t < b_end; ++t) {
+    const int64_t bL = t / g.tilesR, bR = t - bL * g.tilesR;
+    if (bL != cur_bL || age == kColFlushBlocks) {
+      if (cur_bL >= 0) {
+        sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+        __syncthreads();
+      }
+      cur_bL = bL;
+      age = 0;
+    }
+    ++age;
+    sp_block<LPAD>(g, g.sk, smraw, acc, bL, bR);
     __syncthreads();
-    flush(false, cur_bL, bR);
+    sp_flush<LPAD>(g, g.sk, acc, false, cur_bL, bR);
     __syncthreads();
   }
-  if (cur_bL >= 0) flush(true, cur_bL, 0);
+  if (cur_bL >= 0) sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+}
+
+// Batched form: persistent CTAs take `chunk` consecutive units (item, block)
+// of the largest-first unit sequence at a time; row slots are flushed after
+// every unit, the others when the item or the kL block changes.
+template <int LPAD>
+__global__ void __launch_bounds__(kThreads, 1) sketch_sp_batched_kernel(const BatchLaunch b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ SpArgs g;
+  __shared__ int64_t s_base;
+  __shared__ int s_pos;
+  const DevTables& T = *reinterpret_cast<const DevTables*>(b.wsb + kTableOffB);
+  const DevItem* items = reinterpret_cast<const DevItem*>(b.wsb + T.off_items);
+  const DevSketch* sks = reinterpret_cast<const DevSketch*>(b.wsb + T.off_sketches);
+  const int* order = reinterpret_cast<const int*>(b.wsb + T.off_border);
+  const int64_t* prefix = reinterpret_cast<const int64_t*>(b.wsb + T.off_bprefix);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(b.wsb + T.off_bcounter);
+  const int64_t total = prefix[T.nitems];
+  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
+  sp_zero(smraw, acc, 0);
+  int cur = -1;
+  int64_t cur_bL = -1;
+  int age = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_base = (int64_t)atomicAdd(counter, (unsigned long long)b.chunk);
+      int lo = 0, hi = T.nitems - 1;
+      if (s_base < total) {
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (prefix[mid] <= s_base) lo = mid;
+          else hi = mid - 1;
+        }
+      }
+      s_pos = lo;
+    }
+    __syncthreads();
+    const int64_t base = s_base;
+    int pos = s_pos;
+    if (base >= total) break;
+    const int64_t end = imin64(base + b.chunk, total);
+    for (int64_t u = base; u < end; ++u) {
+      while (prefix[pos + 1] <= u) ++pos;
+      const int it_idx = order[pos];
+      const int64_t lu = u - prefix[pos];
+      // long-class slots (column sketches, plane-independent rows) are kept
+      // while the item and the kL block stay the same, for at most
+      // kColFlushBlocks units
+      if (cur >= 0 && (it_idx != cur || lu / g.tilesR != cur_bL || age == kColFlushBlocks)) {
+        sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+        __syncthreads();
+        age = 0;
+        cur_bL = -1;
+      }
+      if (it_idx != cur) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const DevItem& it = items[it_idx];
+          sp_fill(it, sks, it.n[it.d - 1], g);
+          g.X = reinterpret_cast<const float*>(b.X[it_idx]);
+          g.wsb = b.wsb;
+          g.first = 0;
+        }
+        __syncthreads();
+        // slots of this item start at zero (every unit is flushed completely)
+        for (int i = threadIdx.x; i < g.nslots * LPAD * g.ldo; i += kThreads) acc[i] = 0.0f;
+        __syncthreads();
+        cur = it_idx;
+      }
+      const int64_t bL = lu / g.tilesR, bR = lu - bL * g.tilesR;
+      cur_bL = bL;
+      ++age;
+      sp_block<LPAD>(g, g.sk, smraw, acc, bL, bR);
+      __syncthreads();
+      sp_flush<LPAD>(g, g.sk, acc, false, bL, bR);
+      __syncthreads();
+    }
+  }
+  if (cur >= 0 && cur_bL >= 0) sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+}
+
+// Batched tables: blockIdx.y = item; its staged sketches one after another.
+__global__ void sp_table_batched_kernel(char* wsb) {
+  const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
+  const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[blockIdx.y];
+  const DevSketch* sks = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
+  const int ell = sks[it.sk0].width;
+  const int lpad = ell <= 16 ? 16 : 32;
+  for (int si = 0; si < it.nsk; ++si) {
+    const DevSketch& d = sks[it.sk0 + si];
+    if (d.sp_tab < 0) continue;
+    SpSk k;
+    k.hstride = d.hstride;
+    k.col = d.type == SK_COL ? 1 : 0;
+    k.sid = d.stream_id;
+    const int nr = k.col ? (int)it.n[it.d - 1] : (int)it.n[0];
+    const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
+    sp_table_fill(k, it.seed, 0, it.n[0], nr, ell, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
+                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+  }
+}
+
+// Unit prefix of the batched form (largest items first); resets the work
+// counter and the status word.
+__global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb) {
+  __shared__ int64_t cnt[kMaxBatchItems];
+  const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
+  const DevItem* items = reinterpret_cast<const DevItem*>(wsb + T.off_items);
+  const int* order = reinterpret_cast<const int*>(wsb + T.off_border);
+  int64_t* prefix = reinterpret_cast<int64_t*>(wsb + T.off_bprefix);
+  for (int i = threadIdx.x; i < T.nitems; i += blockDim.x) {
+    const DevItem& it = items[order[i]];
+    const int64_t WL = it.N[it.ds] / it.n[0], WR = it.W / WL;
+    int T2, T3;
+    sp_block_shape(WL, WR, &T2, &T3);
+    cnt[i] = ((WL + T2 - 1) / T2) * ((WR + T3 - 1) / T3);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t a = 0;
+    for (int i = 0; i < T.nitems; ++i) {
+      prefix[i] = a;
+      a += cnt[i];
+    }
+    prefix[T.nitems] = a;
+    *reinterpret_cast<unsigned long long*>(wsb + T.off_bcounter) = 0ull;
+    *reinterpret_cast<int*>(wsb + kStatusOff) = 0;
+  }
 }
 
 bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) {
@@ -342,46 +545,13 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) 
   if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sptab_doubles == 0) return false;
   if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
   const DevSketch* sks = plan_sketches_host(&P);
+  for (int s = 0; s < it.nsk; ++s)
+    if (sks[it.sk0 + s].width != sks[it.sk0].width) return false;
   SpArgs g;
   memset(&g, 0, sizeof(g));
-  const int ell = sks[it.sk0].width;
-  const int lpad = ell <= 16 ? 16 : 32;
-  g.n1 = it.n[0];
-  g.cnt = count;
-  g.W = it.W;
-  g.WL = it.N[it.ds] / it.n[0];
-  g.WR = g.W / g.WL;
-  g.Nd1 = it.N[it.d - 1];
-  g.tilesL = (g.WL + kT2 - 1) / kT2;
-  g.tilesR = (g.WR + kT3 - 1) / kT3;
-  g.tab0 = it.off_sptab * 8;
-  g.seed = it.seed;
-  g.nsk = it.nsk;
-  g.ell = ell;
-  g.nq = (ell + 3) / 4;
-  g.ldo = (int)((std::max<int64_t>(g.n1, count) + 7) / 8 * 8);
-  int slots = 0;
-  for (int s = 0; s < it.nsk; ++s) {
-    const DevSketch& d = sks[it.sk0 + s];
-    if (d.width != ell) return false;
-    SpSk k;
-    k.rows = d.rows;
-    k.off = d.off;
-    k.wdiv = d.wdiv;
-    k.hstride = d.hstride;
-    k.tab = d.sp_tab;
-    k.col = d.type == SK_COL ? 1 : 0;
-    k.sid = d.stream_id;
-    const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
-    k.nslot = per_plane_rows ? (k.col ? kT2 : kT3) : 1;
-    k.slot0 = slots;
-    k.lflush = (k.col || k.nslot == 1) ? 1 : 0;
-    k.pad_ = 0;
-    slots += k.nslot;
-    g.sk[s] = k;
-  }
-  g.nslots = slots;
-  const size_t need = (size_t)kWarps * kWarpBytes + sizeof(float) * (size_t)slots * lpad * g.ldo;
+  sp_fill(it, sks, count, g);
+  const int lpad = g.ell <= 16 ? 16 : 32;
+  const size_t need = (size_t)kWarps * kWarpBytes + sizeof(float) * (size_t)g.nslots * lpad * g.ldo;
   if (need > (size_t)kMaxSmem) return false;
   *out = g;
   *smem = need;
@@ -439,6 +609,60 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
   count_launch();
   if (lpad == 16) sp::sketch_sp_kernel<16><<<grid, sp::kThreads, smem, st>>>(g);
   else sp::sketch_sp_kernel<32><<<grid, sp::kThreads, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+// Batched form: every item must fit the small-plane kernel with the same
+// padded width (the tables and tiles of a launch share it).
+bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out) {
+  const int n = plan_num_items(&P);
+  size_t smem = 0;
+  int lpad = 0;
+  for (int i = 0; i < n; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    sp::SpArgs g;
+    size_t need = 0;
+    if (!sp::plan_sp(P, i, it.n[it.d - 1], &g, &need)) return false;
+    const int lp = g.ell <= 16 ? 16 : 32;
+    if (lpad && lp != lpad) return false;
+    lpad = lp;
+    smem = std::max(smem, need);
+  }
+  if (smem_out) *smem_out = smem;
+  if (lpad_out) *lpad_out = lpad;
+  return n > 0 && n <= kMaxBatchItems;
+}
+
+cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
+                                     cudaStream_t st) {
+  size_t smem = 0;
+  int lpad = 0;
+  if (!sp_batched_eligible(P, &smem, &lpad)) return cudaErrorNotSupported;
+  const int nitems = plan_num_items(&P);
+  static BatchLaunch b;  // 16 KB: kept off the host stack
+  b.wsb = (char*)ws;
+  b.chunk = std::max(1, cfg.chunk);
+  for (int i = 0; i < nitems; ++i) b.X[i] = X[i];
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sp::sketch_sp_batched_kernel<16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(sp::sketch_sp_batched_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               sp::kMaxSmem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    attr_set = true;
+  }
+  count_launch();
+  sp::sp_batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws);
+  count_launch();
+  sp::sp_table_batched_kernel<<<dim3(16, (unsigned)nitems), 256, 0, st>>>((char*)ws);
+  count_launch();
+  if (lpad == 16) sp::sketch_sp_batched_kernel<16><<<device_sm_count(), sp::kThreads, smem, st>>>(b);
+  else sp::sketch_sp_batched_kernel<32><<<device_sm_count(), sp::kThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

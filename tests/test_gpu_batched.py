@@ -113,3 +113,46 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
     for b in range(len(xs)):
         assert np.linalg.norm(full(t.core_list(b)) - refs[b]) <= 1e-11 * np.linalg.norm(refs[b]), b
     print("autotuned batched launch shape (ta, chunk, ctas/SM):", best)
+
+
+@pytest.mark.gpu
+def test_batched_bf16_small_plane_matches_single_plans_and_oracle():
+    """BF16 batch whose items all fit the small-plane kernel (n_1, n_d <= 32):
+    each item within 10 eps of the FP64 oracle and of its own single-tensor
+    BF16 plan (the two differ only in FP32 accumulation order)."""
+    xs, probs = make_batch(24, cap=200_000, seed=19, dtype=np.float32)
+    t, dev = run_batched(xs, probs, prec="bf16", x_dtype=torch.float32)
+    st, _ = t.status()
+    assert st in (0, 7)
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        x64 = x.astype(np.float64)
+        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float32, prec="bf16")
+        s.pstt2(dev[b])
+        torch.cuda.synchronize()
+        got, single = full(t.core_list(b)), full(s.core_list(0))
+        o = OP.pstt2(x64, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
+        nx = np.linalg.norm(x64)
+        assert np.linalg.norm(got - OT.tt_full(o["cores"])) <= 10 * EPS * nx, (b, pr["dims"])
+        assert np.linalg.norm(got - single) <= 10 * EPS * nx, (b, pr["dims"])
+
+
+@pytest.mark.gpu
+def test_batched_bf16_graph_capture_replays():
+    xs, probs = make_batch(16, cap=100_000, seed=23, dtype=np.float32)
+    t, dev = run_batched(xs, probs, prec="bf16", x_dtype=torch.float32)
+    ref_ranks = t.ranks.clone()
+    refs = [full(t.core_list(b)) for b in range(len(xs))]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        t.batched(dev, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        t.cores.fill_(float("nan"))
+        t.ranks.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(t.ranks, ref_ranks)
+        for b in range(len(xs)):
+            got = full(t.core_list(b))
+            # the same launch replayed: FP32 slot sums are added into the FP64
+            # sketches by atomics, so only their order may differ
+            assert np.linalg.norm(got - refs[b]) <= 1e-6 * np.linalg.norm(refs[b]), b
