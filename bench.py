@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
     ap.add_argument("--batch-prec", default="bf16,fp64", help="precisions of the batched workload")
+    ap.add_argument("--precision-only", default="",
+                    help="run only the precision form in these precisions, e.g. 'bf16' or 'fp64,tf32,bf16' "
+                         "(profiling); prints its own JSON line")
     ap.add_argument("--batch-shape", default="",
                     help="fixed launch shape 'ta,chunk,ctas_per_sm' instead of the autotuner")
     return ap.parse_args()
@@ -303,7 +306,8 @@ def run_precision(a, dev, P, stream):
     torch.cuda.synchronize(dev)  # X comes from torch's stream; the library runs on `stream`
     out = {"workload": "random TT d=6 n=24 (1.91e8 FP32 entries), ranks 10, +1e-6 noise; eps=1e-5 p=10 rmax=16"}
     ref = None
-    for prec in ("fp64", "tf32", "bf16"):
+    precs = a.precision_only.split(",") if a.precision_only else ["fp64", "tf32", "bf16"]
+    for prec in precs:
         t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec)
         t.pstt2(X, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,10 +320,10 @@ def run_precision(a, dev, P, stream):
         err = err.cpu().numpy()
         r = {"value": X.numel() / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
              "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": t.status(stream)[1],
-             "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane"][t.kernel_kind()]}
+             "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()]}
         if prec == "fp64":
             ref = t.reconstruct(torch.float32, stream=stream)
-        else:
+        elif ref is not None:
             d2 = t.error(ref, stream)
             stream.synchronize()
             d2 = d2.cpu().numpy()
@@ -376,6 +380,15 @@ def run_diff(a, dev, P, stream):
         stream.synchronize()
         del t
     return out
+
+
+def run_precision_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    print(json.dumps({"precision_form": run_precision(a, dev, P, stream)}), flush=True)
 
 
 def run_batched_only(a):
@@ -590,6 +603,8 @@ def main():
         run_reference(a)
     elif a.batched_only:
         run_batched_only(a)
+    elif a.precision_only:
+        run_precision_only(a)
     else:
         run_gpu(a)
 

@@ -104,54 +104,80 @@ __global__ void __launch_bounds__(kThreads) dense_kernel(const double* L, const 
   }
 }
 
-// Y(row, c) += sum_{v in chunk} dX(row + Nk v) Rt(c, v)   (Rt: rp x Mk, ld rp)
-__global__ void __launch_bounds__(kThreads) ygram_kernel(const void* dX, int dx_f64, int64_t Nk, int64_t Mk,
-                                                         const double* Rt, int rp, double* Y) {
-  constexpr int VC = 64;
-  __shared__ double Rs[VC * TT_MAXL];
-  const int64_t nrb = (Nk + kThreads - 1) / kThreads;
-  const int64_t nvc = (Mk + VC - 1) / VC;
-  for (int64_t job = blockIdx.x; job < nrb * nvc; job += gridDim.x) {
-    const int64_t rb = job % nrb, vc = job / nrb;
-    const int64_t v0 = vc * VC;
-    const int nv = (int)imin64(VC, Mk - v0);
-    __syncthreads();
-    for (int o = threadIdx.x; o < nv * rp; o += blockDim.x) {
-      const int v = o / rp, c = o % rp;
-      Rs[v * TT_MAXL + c] = Rt ? Rt[c + (int64_t)rp * (v0 + v)] : 1.0;
+// Y(row, c) += sum_v dX(row + Nk v) Rt(c, v)   (Rt: rp x Mk, ld rp; Rt = null: 1).
+// A job is 32 consecutive rows (the lanes) x vc consecutive v; the four warps
+// of a block take consecutive jobs of the same rows, add their partial sums in
+// shared memory and the block adds them into Y (FP64 atomics).  RP >= rp is a
+// compile-time bound so that the accumulators stay in registers.
+template <int RP>
+__global__ void __launch_bounds__(128) ygram_kernel(const void* dX, int dx_f64, int64_t Nk, int64_t Mk,
+                                                    const double* Rt, int rp, double* Y, int64_t vc) {
+  extern __shared__ double part[];  // 4 x RP x 32
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nrb = (Nk + 31) / 32, nvc = (Mk + vc - 1) / vc;
+  const int64_t nvg = (nvc + 3) / 4;  // groups of four v chunks, one per warp
+  for (int64_t job = blockIdx.x; job < nrb * nvg; job += gridDim.x) {
+    const int64_t rb = job % nrb, vg = job / nrb;
+    const int64_t row = rb * 32 + lane;
+    const int64_t v0 = (vg * 4 + warp) * vc, v1 = imin64(Mk, v0 + vc);
+    double acc[RP];
+#pragma unroll
+    for (int c = 0; c < RP; ++c) acc[c] = 0.0;
+    if (row < Nk) {
+      for (int64_t v = v0; v < v1; ++v) {
+        const int64_t idx = row + Nk * v;
+        const double x = dx_f64 ? __ldg((const double*)dX + idx) : (double)__ldg((const float*)dX + idx);
+#pragma unroll
+        for (int c = 0; c < RP; ++c)
+          if (c < rp) acc[c] += x * (Rt ? __ldg(Rt + c + (int64_t)rp * v) : 1.0);
+      }
     }
     __syncthreads();
-    const int64_t row = rb * kThreads + threadIdx.x;
-    if (row < Nk) {
-      double acc[TT_MAXL];
-      for (int c = 0; c < rp; ++c) acc[c] = 0.0;
-      for (int v = 0; v < nv; ++v) {
-        const int64_t idx = row + Nk * (v0 + v);
-        const double x = dx_f64 ? ((const double*)dX)[idx] : (double)((const float*)dX)[idx];
-        for (int c = 0; c < rp; ++c) acc[c] += x * Rs[v * TT_MAXL + c];
+#pragma unroll
+    for (int c = 0; c < RP; ++c) part[(warp * RP + c) * 32 + lane] = acc[c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < rp * 32; e += blockDim.x) {
+      const int c = e >> 5, l = e & 31;
+      const int64_t r = rb * 32 + l;
+      if (r < Nk) {
+        const double sum = part[(0 * RP + c) * 32 + l] + part[(1 * RP + c) * 32 + l] +
+                           part[(2 * RP + c) * 32 + l] + part[(3 * RP + c) * 32 + l];
+        atomicAdd(Y + r + Nk * c, sum);
       }
-      for (int c = 0; c < rp; ++c) atomicAdd(Y + row + Nk * c, acc[c]);
     }
   }
 }
 
 // dG_k(a, i, c) = sum_u L_{k-1}(u, a) Y_k(u + N_{k-1} i, c);  L_0 = [1].
+// dG is zeroed first; a warp takes one entry and one chunk of u (lanes split
+// the chunk) and adds its sum with an atomic.
 __global__ void dcore_kernel(const double* Lp, int64_t Np, int rpa, const double* Y, int64_t nk, int rpc,
-                             double* dG) {
+                             double* dG, int64_t uc) {
   const int64_t total = (int64_t)rpa * nk * rpc;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t Nk = Np * nk;
+  if (Lp == nullptr) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = (e / rpa) % nk;
+      const int c = (int)(e / (rpa * nk));
+      dG[e] = Y[i + Nk * c];
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nuc = (Np + uc - 1) / uc;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); job < total * nuc; job += nwarps) {
+    const int64_t e = job % total, ch = job / total;
     const int a = (int)(e % rpa);
     const int64_t i = (e / rpa) % nk;
     const int c = (int)(e / (rpa * nk));
-    const int64_t Nk = Np * nk;
+    const int64_t u0 = ch * uc, u1 = imin64(Np, u0 + uc);
     double acc = 0.0;
-    if (Lp == nullptr) {
-      acc = Y[i + Nk * c];
-    } else {
-      for (int64_t u = 0; u < Np; ++u) acc += Lp[u + Np * a] * Y[u + Np * i + Nk * c];
-    }
-    dG[e] = acc;
+    for (int64_t u = u0 + lane; u < u1; u += 32) acc += Lp[u + Np * a] * Y[u + Np * i + Nk * c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicAdd(dG + e, acc);
   }
 }
 
@@ -224,20 +250,43 @@ cudaError_t launch_reconstruct_backward(const Plan& P, int item, const double* c
     iface_right_kernel<<<grid_for((int64_t)it.rpad[k - 1] * it.n[k - 1] * Mn), kThreads, 0, st>>>(
         Rn, Mn, it.rpad[k], cores + it.core_off[k], it.n[k - 1], it.rpad[k - 1], W + it.off_Rall[k]);
   }
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(ygram_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         4 * 64 * 32 * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   for (int k = 1; k <= d; ++k) {
     const int64_t Nk = it.N[k], Mk = it.N[d] / it.N[k];
     const int rpk = it.rpad[k];
     cudaError_t e = cudaMemsetAsync(W + it.off_Y, 0, sizeof(double) * Nk * rpk, st);
     if (e != cudaSuccess) return e;
-    const int64_t jobs = ((Nk + kThreads - 1) / kThreads) * ((Mk + 63) / 64);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(jobs, 16LL * device_sm_count()));
+    // v chunks sized so that about 32k warp jobs cover the entries
+    const int64_t vc = std::max<int64_t>(16, (Nk * Mk) / (32LL * 32768));
+    const int64_t nrb = (Nk + 31) / 32, nvg = ((Mk + vc - 1) / vc + 3) / 4;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(nrb * nvg, 16LL * device_sm_count()));
+    const double* Rt = k == d ? nullptr : W + it.off_Rall[k + 1];
     count_launch();
-    ygram_kernel<<<g, kThreads, 0, st>>>(dXt, dx_f64, Nk, Mk, k == d ? nullptr : W + it.off_Rall[k + 1], rpk,
-                                         W + it.off_Y);
+    if (rpk <= 8)
+      ygram_kernel<8><<<g, 128, 4 * 8 * 32 * sizeof(double), st>>>(dXt, dx_f64, Nk, Mk, Rt, rpk, W + it.off_Y, vc);
+    else if (rpk <= 16)
+      ygram_kernel<16><<<g, 128, 4 * 16 * 32 * sizeof(double), st>>>(dXt, dx_f64, Nk, Mk, Rt, rpk, W + it.off_Y, vc);
+    else if (rpk <= 32)
+      ygram_kernel<32><<<g, 128, 4 * 32 * 32 * sizeof(double), st>>>(dXt, dx_f64, Nk, Mk, Rt, rpk, W + it.off_Y, vc);
+    else
+      ygram_kernel<64><<<g, 128, 4 * 64 * 32 * sizeof(double), st>>>(dXt, dx_f64, Nk, Mk, Rt, rpk, W + it.off_Y, vc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nout = (int64_t)it.rpad[k - 1] * it.n[k - 1] * rpk;
+    e = cudaMemsetAsync(dcores + it.core_off[k], 0, sizeof(double) * nout, st);
+    if (e != cudaSuccess) return e;
+    const int64_t Np = it.N[k - 1];
+    const int64_t uc = std::max<int64_t>(256, (nout * Np) / 32768);
     count_launch();
-    dcore_kernel<<<grid_for((int64_t)it.rpad[k - 1] * it.n[k - 1] * rpk), kThreads, 0, st>>>(
-        k == 1 ? nullptr : W + it.off_Lall[k - 1], it.N[k - 1], it.rpad[k - 1], W + it.off_Y, it.n[k - 1], rpk,
-        dcores + it.core_off[k]);
+    dcore_kernel<<<grid_for(nout * ((Np + uc - 1) / uc) * 32), kThreads, 0, st>>>(
+        k == 1 ? nullptr : W + it.off_Lall[k - 1], Np, it.rpad[k - 1], W + it.off_Y, it.n[k - 1], rpk,
+        dcores + it.core_off[k], uc);
   }
   return cudaGetLastError();
 }
