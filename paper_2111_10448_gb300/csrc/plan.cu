@@ -215,14 +215,17 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.tctab_doubles = (bytes + 7) / 8;
   }
   it.off_tctab = it.tctab_doubles ? ws.take(it.tctab_doubles) : 0;
-  // Staging area of the small-plane kernel (BF16, n_1 and n_d <= 32, one
-  // width l <= 32): the rows of every test matrix that many planes share
+  // Staging area of the small-plane kernel (BF16 or TF32, n_1 and n_d <= 32,
+  // one width l <= 32): the rows of every test matrix that many planes share
   // (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches with
-  // wdiv < W: wdiv keys x n_1 rows), rounded to BF16, 2 * lpad bytes per row.
+  // wdiv < W: wdiv keys x n_1 rows), rounded to the MMA type, lpad elements of
+  // 2 (BF16) or 4 (TF32) bytes per row.
   // A sketch whose table would exceed 512 MB is generated per plane instead.
   it.sptab_doubles = 0;
   {
-    bool ok = q.prec == TT_PREC_BF16 && q.x_dtype == TT_F32 && q.n[0] <= 32 && q.n[d - 1] <= 32;
+    bool ok = (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 && q.n[0] <= 32 &&
+              q.n[d - 1] <= 32;
+    const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
     for (int si = it.sk0; si < it.sk0 + it.nsk && ok; ++si)
       ok = P.sketches[si].width == P.sketches[it.sk0].width && P.sketches[si].width <= 32;
     int64_t bytes = 0;
@@ -232,8 +235,8 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
       if (!ok) continue;
       const int64_t lpad = s.width <= 16 ? 16 : 32;
       int64_t tb = 0;
-      if (s.type == SK_COL && s.wdiv > 1) tb = (it.W / s.wdiv) * q.n[d - 1] * lpad * 2;
-      if (s.type == SK_ROW && s.wdiv < it.W) tb = s.wdiv * q.n[0] * lpad * 2;
+      if (s.type == SK_COL && s.wdiv > 1) tb = (it.W / s.wdiv) * q.n[d - 1] * lpad * esz;
+      if (s.type == SK_ROW && s.wdiv < it.W) tb = s.wdiv * q.n[0] * lpad * esz;
       if (tb > 0 && tb <= (512LL << 20)) {
         s.sp_tab = bytes;
         bytes += (tb + 255) / 256 * 256;

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -47,13 +48,20 @@ int plan_num_items(const Plan* p);
 
 namespace sp {
 
-constexpr int kWarps = 16;
-constexpr int kThreads = kWarps * 32;
-constexpr int kBlockPlanes = kWarps;          // planes per block: T2 values of kL x T3 values of kR
-constexpr int kLD = 40;                         // BF16 row stride of the 32-row tiles (80 bytes)
+constexpr int kBlockPlanes = 16;  // planes per block: T2 values of kL x T3 values of kR
+constexpr int kLD = 40;           // element row stride of the 32-row tiles
 constexpr int kTileElems = 32 * kLD;
-constexpr int kWarpBytes = 3 * kTileElems * 2;  // plane hi, plane lo, test-matrix block
 constexpr int kColFlushBlocks = 16;
+// Per precision: BF16 tiles (80-byte rows) leave room for 16 warps, one plane
+// each per block; TF32 tiles hold FP32 words (160-byte rows), 8 warps, two
+// planes each per block.
+template <bool TF>
+struct Prec {
+  static constexpr int kWarps = TF ? 8 : 16;
+  static constexpr int kThreads = kWarps * 32;
+  static constexpr int kEsz = TF ? 4 : 2;
+  static constexpr int kWarpBytes = 3 * kTileElems * kEsz;  // plane hi, plane lo, test-matrix block
+};
 constexpr int kMaxSmem = 227 * 1024 - 2048;
 constexpr int64_t kTableOffB = 256;  // dynamic shared memory; the static part is below 2 KB
 
@@ -103,17 +111,25 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+__device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
 // Staged test-matrix rows of one sketch: entry (key, r, j), r < nr, j < lpad,
-// at byte ((key nr + r) lpad + j) 2 of `tab`: the BF16-rounded normal of row
-// key + hstride (first + r) (column side) or r + n1 key (row side), zero for
-// j >= l.  Threads tid0, tid0 + nthr, ... of the caller take the entries.
+// at element (key nr + r) lpad + j of `tab`: the normal of row key + hstride
+// (first + r) (column side) or r + n1 key (row side) rounded to BF16 (2-byte
+// elements) or TF32 (`tf`: 4-byte FP32 words), zero for j >= l.  Threads
+// tid0, tid0 + nthr, ... of the caller take the entries.
 __device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
-                              int64_t nkeys, char* tab, int64_t tid0, int64_t nthr) {
+                              int64_t nkeys, char* tab, int64_t tid0, int64_t nthr, bool tf) {
   const int qpr = lpad / 4;
   const int64_t total = nkeys * nr * qpr;
   for (int64_t e = tid0; e < total; e += nthr) {
@@ -124,16 +140,23 @@ __device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64
     const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (first + r)) : (uint64_t)(r + n1 * key);
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     if (4 * q < ell) z = normals4_f32(seed, (uint32_t)s.sid, row, (uint32_t)q);
-    const uint32_t lo = bf16x2(4 * q < ell ? z.x : 0.f, 4 * q + 1 < ell ? z.y : 0.f);
-    const uint32_t hi = bf16x2(4 * q + 2 < ell ? z.z : 0.f, 4 * q + 3 < ell ? z.w : 0.f);
-    *reinterpret_cast<uint2*>(tab + ((key * nr + r) * lpad + 4 * q) * 2) = make_uint2(lo, hi);
+    const int64_t el = (key * nr + r) * lpad + 4 * q;
+    if (tf) {
+      *reinterpret_cast<float4*>(tab + el * 4) =
+          make_float4(4 * q < ell ? round_tf32(z.x) : 0.f, 4 * q + 1 < ell ? round_tf32(z.y) : 0.f,
+                      4 * q + 2 < ell ? round_tf32(z.z) : 0.f, 4 * q + 3 < ell ? round_tf32(z.w) : 0.f);
+    } else {
+      const uint32_t lo = bf16x2(4 * q < ell ? z.x : 0.f, 4 * q + 1 < ell ? z.y : 0.f);
+      const uint32_t hi = bf16x2(4 * q + 2 < ell ? z.z : 0.f, 4 * q + 3 < ell ? z.w : 0.f);
+      *reinterpret_cast<uint2*>(tab + el * 2) = make_uint2(lo, hi);
+    }
   }
 }
 
 __global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
-                                int64_t nkeys, char* tab) {
+                                int64_t nkeys, char* tab, int tf) {
   sp_table_fill(s, seed, first, n1, nr, ell, lpad, nkeys, tab, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                (int64_t)gridDim.x * blockDim.x);
+                (int64_t)gridDim.x * blockDim.x, tf != 0);
 }
 
 // Launch arguments of one item (the whole last mode when count = n_d), shared
@@ -179,8 +202,9 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
 
 // Adds the slots of one flush class into the FP64 sketches and clears them:
 // warps take the (slot, j) rows, lanes the outputs o.
-template <int LPAD>
+template <int LPAD, bool TF>
 __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool long_class, int64_t bL, int64_t bR) {
+  constexpr int kWarps = Prec<TF>::kWarps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n1 = (int)g.n1, cnt = (int)g.cnt;
   const int slot_elems = LPAD * g.ldo;
@@ -216,12 +240,14 @@ __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool lon
 }
 
 // The planes of block (bL, bR), one per warp; no block-wide barrier inside.
-template <int LPAD>
+template <int LPAD, bool TF>
 __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw, float* acc, int64_t bL, int64_t bR) {
+  using E = typename std::conditional<TF, float, __nv_bfloat16>::type;
+  constexpr int kWarps = Prec<TF>::kWarps, kEsz = Prec<TF>::kEsz;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(smraw + warp * kWarpBytes);
-  __nv_bfloat16* Xl = Xh + kTileElems;
-  __nv_bfloat16* Gs = Xl + kTileElems;
+  E* Xh = reinterpret_cast<E*>(smraw + warp * Prec<TF>::kWarpBytes);
+  E* Xl = Xh + kTileElems;
+  E* Gs = Xl + kTileElems;
   const int slot_elems = LPAD * g.ldo;
   const int n1 = (int)g.n1, cnt = (int)g.cnt;
   const int64_t kL0 = bL * g.T2, kR0 = bR * g.T3;
@@ -229,7 +255,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
     for (int p = warp; p < nA * nB; p += kWarps) {
       const int sa = p % nA, sb = p / nA;
       const int64_t w = (kL0 + sa) + g.WL * (kR0 + sb);
-      // ---- the plane, split into BF16 hi + lo, [b][a]
+      // ---- the plane, split into hi + lo in the MMA type, [b][a]
       {
         const float* xp = g.X + g.n1 * w + lane;
         float v[32];
@@ -239,9 +265,15 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
           for (int b = 0; b < 32; ++b) {
             if (b < cnt) {
-              const __nv_bfloat16 h = __float2bfloat16_rn(v[b]);
-              Xh[b * kLD + lane] = h;
-              Xl[b * kLD + lane] = __float2bfloat16_rn(__fsub_rn(v[b], __bfloat162float(h)));
+              if constexpr (TF) {
+                const float h = round_tf32(v[b]);
+                Xh[b * kLD + lane] = h;
+                Xl[b * kLD + lane] = round_tf32(__fsub_rn(v[b], h));
+              } else {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[b]);
+                Xh[b * kLD + lane] = h;
+                Xl[b * kLD + lane] = __float2bfloat16_rn(__fsub_rn(v[b], __bfloat162float(h)));
+              }
             }
           }
         }
@@ -255,7 +287,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
         const SpSk& s = s_sk[si];
         const int nr = s.col ? cnt : n1;     // contraction extent
         const int nout = s.col ? n1 : cnt;   // output extent
-        const int kext = (nr + 15) & ~15;
+        const int kext = TF ? (nr + 7) & ~7 : (nr + 15) & ~15;
         // key of the plane's test-matrix rows: w div wdiv (column side) or
         // w mod wdiv (row side); wdiv divides WL (column) or WL divides wdiv
         // (row), so both follow from kL and kR in 32-bit arithmetic
@@ -264,11 +296,11 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                                   : (int64_t)kLp + (int64_t)wl * (kRp % (wd / wl));
         // ---- test-matrix block Gs[k][j]
         if (s.tab >= 0) {
-          constexpr int cpr = LPAD / 8;  // 16-byte chunks per row
-          const uint4* src = reinterpret_cast<const uint4*>(g.wsb + g.tab0 + s.tab + key * nr * LPAD * 2);
+          constexpr int cpr = LPAD * kEsz / 16;  // 16-byte chunks per row
+          const uint4* src = reinterpret_cast<const uint4*>(g.wsb + g.tab0 + s.tab + key * nr * LPAD * kEsz);
           for (int c = lane; c < nr * cpr; c += 32) {
             const int r = c / cpr, q = c - r * cpr;
-            *reinterpret_cast<uint4*>(Gs + r * kLD + 8 * q) = __ldg(src + c);
+            *reinterpret_cast<uint4*>(Gs + r * kLD + (16 / kEsz) * q) = __ldg(src + c);
           }
         } else {
           // jobs c = (row r, column quad q), two per lane at a time (independent
@@ -292,17 +324,24 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
             for (int h = 0; h < 2; ++h) {
               if (c0 + 32 * h < njobs) {
                 const int q = qq[h];
-                const uint32_t lo = bf16x2(4 * q < g.ell ? z[h].x : 0.f, 4 * q + 1 < g.ell ? z[h].y : 0.f);
-                const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z[h].z : 0.f, 4 * q + 3 < g.ell ? z[h].w : 0.f);
-                *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
+                if constexpr (TF) {
+                  *reinterpret_cast<float4*>(Gs + rr[h] * kLD + 4 * q) = make_float4(
+                      4 * q < g.ell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < g.ell ? round_tf32(z[h].y) : 0.f,
+                      4 * q + 2 < g.ell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < g.ell ? round_tf32(z[h].w) : 0.f);
+                } else {
+                  const uint32_t lo = bf16x2(4 * q < g.ell ? z[h].x : 0.f, 4 * q + 1 < g.ell ? z[h].y : 0.f);
+                  const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z[h].z : 0.f, 4 * q + 3 < g.ell ? z[h].w : 0.f);
+                  *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
+                }
               }
             }
           }
         }
         // contraction padding rows [nr, kext) (another sketch may have left rows there)
-        for (int c = lane; c < (kext - nr) * (LPAD / 8); c += 32) {
-          const int r = nr + c / (LPAD / 8), q = c % (LPAD / 8);
-          *reinterpret_cast<uint4*>(Gs + r * kLD + 8 * q) = make_uint4(0u, 0u, 0u, 0u);
+        constexpr int zpr = LPAD * kEsz / 16;  // 16-byte chunks per row
+        for (int c = lane; c < (kext - nr) * zpr; c += 32) {
+          const int r = nr + c / zpr, q = c % zpr;
+          *reinterpret_cast<uint4*>(Gs + r * kLD + (16 / kEsz) * q) = make_uint4(0u, 0u, 0u, 0u);
         }
         __syncwarp();
         // ---- D[j][o] = sum_k Gs[k][j] Xs'[k][o], hi and lo parts
@@ -321,6 +360,47 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
           for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
             for (int e = 0; e < 4; ++e) ch[mt][nt][e] = cl[mt][nt][e] = 0.0f;
+        if constexpr (TF) {
+          // m16n8k8 TF32 fragments straight from the FP32 tiles (row stride 40
+          // words: the A loads and the column-product B loads are conflict-free)
+          for (int k0 = 0; k0 < kext; k0 += 8) {
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+              const float* gp = reinterpret_cast<const float*>(Gs) + (k0 + tq) * kLD + mt * 16 + gq;
+              a[mt][0] = __float_as_uint(gp[0]);
+              a[mt][1] = __float_as_uint(gp[8]);
+              a[mt][2] = __float_as_uint(gp[4 * kLD]);
+              a[mt][3] = __float_as_uint(gp[4 * kLD + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+              if (nt < ntn) {
+                uint32_t bh0, bh1, bl0, bl1;
+                const float* xh = reinterpret_cast<const float*>(Xh);
+                const float* xl = reinterpret_cast<const float*>(Xl);
+                if (s.col) {  // B[k][o] = X(o, k) = tile[k][o]
+                  const int off = (k0 + tq) * kLD + nt * 8 + gq;
+                  bh0 = __float_as_uint(xh[off]);
+                  bh1 = __float_as_uint(xh[off + 4 * kLD]);
+                  bl0 = __float_as_uint(xl[off]);
+                  bl1 = __float_as_uint(xl[off + 4 * kLD]);
+                } else {      // B[k][o] = X(k, o) = tile[o][k]
+                  const int off = (nt * 8 + gq) * kLD + k0 + tq;
+                  bh0 = __float_as_uint(xh[off]);
+                  bh1 = __float_as_uint(xh[off + 4]);
+                  bl0 = __float_as_uint(xl[off]);
+                  bl1 = __float_as_uint(xl[off + 4]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                  mma_tf32(ch[mt][nt], a[mt], bh0, bh1);
+                  mma_tf32(cl[mt][nt], a[mt], bl0, bl1);
+                }
+              }
+            }
+          }
+        } else {
 #pragma unroll
         for (int k0 = 0; k0 < 32; k0 += 16) {
           if (k0 < kext) {
@@ -355,6 +435,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                 if (nt < ntn) mma_bf16(cl[mt][nt], a[mt], bl[nt]);
           }
         }
+        }
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -374,20 +455,21 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 
 // Zeroes the per-warp tiles (their padding rows and columns stay zero) and
 // the accumulator slots.
+template <bool TF>
 __device__ void sp_zero(unsigned char* smraw, float* acc, int acc_elems) {
-  for (int i = threadIdx.x; i < kWarps * kWarpBytes / 16; i += kThreads)
+  for (int i = threadIdx.x; i < Prec<TF>::kWarps * Prec<TF>::kWarpBytes / 16; i += Prec<TF>::kThreads)
     reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int i = threadIdx.x; i < acc_elems; i += kThreads) acc[i] = 0.0f;
+  for (int i = threadIdx.x; i < acc_elems; i += Prec<TF>::kThreads) acc[i] = 0.0f;
 }
 
-template <int LPAD>
-__global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
+template <int LPAD, bool TF>
+__global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ SpArgs g;
   if (threadIdx.x == 0) g = ga;
   __syncthreads();
-  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
-  sp_zero(smraw, acc, g.nslots * LPAD * g.ldo);
+  float* acc = reinterpret_cast<float*>(smraw + Prec<TF>::kWarps * Prec<TF>::kWarpBytes);
+  sp_zero<TF>(smraw, acc, g.nslots * LPAD * g.ldo);
   __syncthreads();
   const int64_t nblocks = g.tilesL * g.tilesR;
   const int64_t b_beg = nblocks * blockIdx.x / gridDim.x, b_end = nblocks * (blockIdx.x + 1) / gridDim.x;
@@ -397,26 +479,26 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_kernel(const SpArgs ga)
     const int64_t bL = t / g.tilesR, bR = t - bL * g.tilesR;
     if (bL != cur_bL || age == kColFlushBlocks) {
       if (cur_bL >= 0) {
-        sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+        sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
         __syncthreads();
       }
       cur_bL = bL;
       age = 0;
     }
     ++age;
-    sp_block<LPAD>(g, g.sk, smraw, acc, bL, bR);
+    sp_block<LPAD, TF>(g, g.sk, smraw, acc, bL, bR);
     __syncthreads();
-    sp_flush<LPAD>(g, g.sk, acc, false, cur_bL, bR);
+    sp_flush<LPAD, TF>(g, g.sk, acc, false, cur_bL, bR);
     __syncthreads();
   }
-  if (cur_bL >= 0) sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+  if (cur_bL >= 0) sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
 }
 
 // Batched form: persistent CTAs take `chunk` consecutive units (item, block)
 // of the largest-first unit sequence at a time; row slots are flushed after
 // every unit, the others when the item or the kL block changes.
-template <int LPAD>
-__global__ void __launch_bounds__(kThreads, 1) sketch_sp_batched_kernel(const BatchLaunch b) {
+template <int LPAD, bool TF>
+__global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kernel(const BatchLaunch b) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ SpArgs g;
   __shared__ int64_t s_base;
@@ -428,8 +510,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_batched_kernel(const Ba
   const int64_t* prefix = reinterpret_cast<const int64_t*>(b.wsb + T.off_bprefix);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(b.wsb + T.off_bcounter);
   const int64_t total = prefix[T.nitems];
-  float* acc = reinterpret_cast<float*>(smraw + kWarps * kWarpBytes);
-  sp_zero(smraw, acc, 0);
+  float* acc = reinterpret_cast<float*>(smraw + Prec<TF>::kWarps * Prec<TF>::kWarpBytes);
+  sp_zero<TF>(smraw, acc, 0);
   int cur = -1;
   int64_t cur_bL = -1;
   int age = 0;
@@ -459,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_batched_kernel(const Ba
       // while the item and the kL block stay the same, for at most
       // kColFlushBlocks units
       if (cur >= 0 && (it_idx != cur || lu / g.tilesR != cur_bL || age == kColFlushBlocks)) {
-        sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+        sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
         __syncthreads();
         age = 0;
         cur_bL = -1;
@@ -475,20 +557,20 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_sp_batched_kernel(const Ba
         }
         __syncthreads();
         // slots of this item start at zero (every unit is flushed completely)
-        for (int i = threadIdx.x; i < g.nslots * LPAD * g.ldo; i += kThreads) acc[i] = 0.0f;
+        for (int i = threadIdx.x; i < g.nslots * LPAD * g.ldo; i += Prec<TF>::kThreads) acc[i] = 0.0f;
         __syncthreads();
         cur = it_idx;
       }
       const int64_t bL = lu / g.tilesR, bR = lu - bL * g.tilesR;
       cur_bL = bL;
       ++age;
-      sp_block<LPAD>(g, g.sk, smraw, acc, bL, bR);
+      sp_block<LPAD, TF>(g, g.sk, smraw, acc, bL, bR);
       __syncthreads();
-      sp_flush<LPAD>(g, g.sk, acc, false, bL, bR);
+      sp_flush<LPAD, TF>(g, g.sk, acc, false, bL, bR);
       __syncthreads();
     }
   }
-  if (cur >= 0 && cur_bL >= 0) sp_flush<LPAD>(g, g.sk, acc, true, cur_bL, 0);
+  if (cur >= 0 && cur_bL >= 0) sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
 }
 
 // Batched tables: blockIdx.y = item; its staged sketches one after another.
@@ -508,7 +590,8 @@ __global__ void sp_table_batched_kernel(char* wsb) {
     const int nr = k.col ? (int)it.n[it.d - 1] : (int)it.n[0];
     const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
     sp_table_fill(k, it.seed, 0, it.n[0], nr, ell, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
-                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                  it.prec == TT_PREC_TF32);
   }
 }
 
@@ -542,7 +625,7 @@ __global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb) {
 
 bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) {
   const DevItem& it = plan_items_host(&P)[item];
-  if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sptab_doubles == 0) return false;
+  if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_TF32) || it.x_f64 || it.sptab_doubles == 0) return false;
   if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
   const DevSketch* sks = plan_sketches_host(&P);
   for (int s = 0; s < it.nsk; ++s)
@@ -551,7 +634,9 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) 
   memset(&g, 0, sizeof(g));
   sp_fill(it, sks, count, g);
   const int lpad = g.ell <= 16 ? 16 : 32;
-  const size_t need = (size_t)kWarps * kWarpBytes + sizeof(float) * (size_t)g.nslots * lpad * g.ldo;
+  const size_t tiles = it.prec == TT_PREC_TF32 ? (size_t)Prec<true>::kWarps * Prec<true>::kWarpBytes
+                                               : (size_t)Prec<false>::kWarps * Prec<false>::kWarpBytes;
+  const size_t need = tiles + sizeof(float) * (size_t)g.nslots * lpad * g.ldo;
   if (need > (size_t)kMaxSmem) return false;
   *out = g;
   *smem = need;
@@ -580,19 +665,20 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
   g.wsb = (char*)ws;
   g.first = first;
   const int lpad = g.ell <= 16 ? 16 : 32;
+  const DevItem& it = plan_items_host(&P)[item];
+  const bool tf = it.prec == TT_PREC_TF32;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sp::sketch_sp_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         sp::kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(sp::sketch_sp_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
+    cudaError_t e = cudaSuccess;
+    for (const void* f : {(const void*)sp::sketch_sp_kernel<16, false>, (const void*)sp::sketch_sp_kernel<32, false>,
+                          (const void*)sp::sketch_sp_kernel<16, true>, (const void*)sp::sketch_sp_kernel<32, true>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
     if (e != cudaSuccess) {
       cudaGetLastError();  // leave no pending error for the caller's next runtime call
       return e;
     }
     attr_set = true;
   }
-  const DevItem& it = plan_items_host(&P)[item];
   for (int s = 0; s < g.nsk; ++s) {
     const sp::SpSk& k = g.sk[s];
     if (k.tab < 0) continue;
@@ -602,13 +688,18 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count());
     count_launch();
     sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, g.seed, first, g.n1, nr, g.ell, lpad, nkeys,
-                                                g.wsb + g.tab0 + k.tab);
+                                                g.wsb + g.tab0 + k.tab, tf ? 1 : 0);
   }
   const int64_t nblocks = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(nblocks, device_sm_count());
   count_launch();
-  if (lpad == 16) sp::sketch_sp_kernel<16><<<grid, sp::kThreads, smem, st>>>(g);
-  else sp::sketch_sp_kernel<32><<<grid, sp::kThreads, smem, st>>>(g);
+  if (tf) {
+    if (lpad == 16) sp::sketch_sp_kernel<16, true><<<grid, sp::Prec<true>::kThreads, smem, st>>>(g);
+    else sp::sketch_sp_kernel<32, true><<<grid, sp::Prec<true>::kThreads, smem, st>>>(g);
+  } else {
+    if (lpad == 16) sp::sketch_sp_kernel<16, false><<<grid, sp::Prec<false>::kThreads, smem, st>>>(g);
+    else sp::sketch_sp_kernel<32, false><<<grid, sp::Prec<false>::kThreads, smem, st>>>(g);
+  }
   return cudaGetLastError();
 }
 
@@ -620,6 +711,7 @@ bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out) {
   int lpad = 0;
   for (int i = 0; i < n; ++i) {
     const DevItem& it = plan_items_host(&P)[i];
+    if (it.prec != plan_items_host(&P)[0].prec) return false;
     sp::SpArgs g;
     size_t need = 0;
     if (!sp::plan_sp(P, i, it.n[it.d - 1], &g, &need)) return false;
@@ -645,24 +737,31 @@ cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const 
   for (int i = 0; i < nitems; ++i) b.X[i] = X[i];
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sp::sketch_sp_batched_kernel<16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(sp::sketch_sp_batched_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               sp::kMaxSmem);
+    cudaError_t e = cudaSuccess;
+    for (const void* f :
+         {(const void*)sp::sketch_sp_batched_kernel<16, false>, (const void*)sp::sketch_sp_batched_kernel<32, false>,
+          (const void*)sp::sketch_sp_batched_kernel<16, true>, (const void*)sp::sketch_sp_batched_kernel<32, true>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;
     }
     attr_set = true;
   }
+  const bool tf = plan_items_host(&P)[0].prec == TT_PREC_TF32;
   count_launch();
   sp::sp_batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws);
   count_launch();
   sp::sp_table_batched_kernel<<<dim3(16, (unsigned)nitems), 256, 0, st>>>((char*)ws);
   count_launch();
-  if (lpad == 16) sp::sketch_sp_batched_kernel<16><<<device_sm_count(), sp::kThreads, smem, st>>>(b);
-  else sp::sketch_sp_batched_kernel<32><<<device_sm_count(), sp::kThreads, smem, st>>>(b);
+  const int nsm = device_sm_count();
+  if (tf) {
+    if (lpad == 16) sp::sketch_sp_batched_kernel<16, true><<<nsm, sp::Prec<true>::kThreads, smem, st>>>(b);
+    else sp::sketch_sp_batched_kernel<32, true><<<nsm, sp::Prec<true>::kThreads, smem, st>>>(b);
+  } else {
+    if (lpad == 16) sp::sketch_sp_batched_kernel<16, false><<<nsm, sp::Prec<false>::kThreads, smem, st>>>(b);
+    else sp::sketch_sp_batched_kernel<32, false><<<nsm, sp::Prec<false>::kThreads, smem, st>>>(b);
+  }
   return cudaGetLastError();
 }
 

@@ -116,17 +116,18 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
 
 
 @pytest.mark.gpu
-def test_batched_bf16_small_plane_matches_single_plans_and_oracle():
-    """BF16 batch whose items all fit the small-plane kernel (n_1, n_d <= 32):
-    each item within 10 eps of the FP64 oracle and of its own single-tensor
-    BF16 plan (the two differ only in FP32 accumulation order)."""
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_batched_small_plane_matches_single_plans_and_oracle(prec):
+    """Mixed-precision batch whose items all fit the small-plane kernel
+    (n_1, n_d <= 32): each item within 10 eps of the FP64 oracle and of its
+    own single-tensor plan (the two differ only in FP32 accumulation order)."""
     xs, probs = make_batch(24, cap=200_000, seed=19, dtype=np.float32)
-    t, dev = run_batched(xs, probs, prec="bf16", x_dtype=torch.float32)
+    t, dev = run_batched(xs, probs, prec=prec, x_dtype=torch.float32)
     st, _ = t.status()
     assert st in (0, 7)
     for b, (x, pr) in enumerate(zip(xs, probs)):
         x64 = x.astype(np.float64)
-        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float32, prec="bf16")
+        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float32, prec=prec)
         s.pstt2(dev[b])
         torch.cuda.synchronize()
         got, single = full(t.core_list(b)), full(s.core_list(0))

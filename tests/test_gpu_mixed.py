@@ -271,12 +271,13 @@ def test_pinned_host_tensor_read_directly_equals_device_tensor():
     ([8, 7, 6, 5, 4], dict(eps=1e-5, rmax=8, p=5)),           # d = 5
     ([15, 15, 15, 15, 15, 15], dict(eps=1e-5, rmax=16, p=10)),  # ~21 blocks per CTA: periodic flushes
 ])
-def test_small_plane_sketches_match_oracle(dims, kw):
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_small_plane_sketches_match_oracle(dims, kw, prec):
     """The small-plane kernel (n_1, n_d <= 32): every sketch entry against the
     oracle's FP64 products of the split X with the rounded test matrices."""
     d = len(dims)
     x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", **kw)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, **kw)
     assert t.kernel_kind() == 3
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
@@ -284,25 +285,26 @@ def test_small_plane_sketches_match_oracle(dims, kw):
     t.finalize()
     st, _ = t.status()
     assert st in (0, N.TT_WARN_RANK_CAP)
-    xs = _split(x.astype(np.float64), "bf16")
-    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt="bf16", **kw)
+    xs = _split(x.astype(np.float64), prec)
+    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt=prec, **kw)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
     for k, R in o["sketch"]["R"].items():
         _close_sketch(sk[(1, k)], R, ("R", k))
 
 
-def test_small_plane_within_10eps_of_oracle():
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_small_plane_within_10eps_of_oracle(prec):
     """The precision-form shape at reduced n: X~ from the small-plane kernel
     within 10 eps of the FP64 oracle's X~ and of X."""
     dims, eps = [10] * 6, 1e-5
     x = ti.random_tt(dims, [1, 10, 10, 10, 10, 10, 1], seed=0, noise=1e-6).astype(np.float32)
     x64 = x.astype(np.float64)
-    t = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec="bf16")
+    t = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec)
     assert t.kernel_kind() == 3
     t.pstt2(to_dev(x))
     o = OP.pstt2(x64, dims, eps=eps, rmax=16, p=10, seed=1)
     xt = t.reconstruct().cpu().numpy()
     e_or, e_x = rel(xt, OT.tt_full(o["cores"]), x64), rel(xt, x64, x64)
-    print(f"small-plane: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} ranks={t.status()[1]}")
+    print(f"small-plane {prec}: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} ranks={t.status()[1]}")
     assert e_or <= 10 * eps and e_x <= 10 * eps
