@@ -149,13 +149,16 @@ __device__ __forceinline__ void flag_status(char* wsb, int bits) {
 }
 
 // ------------------------------------------------------------------ TSQR up
-// One task = one row block of level L of one basis sketch.  Non-root blocks
-// write their R into the next level's matrix; the root block also does the
-// CPQR of R, the rank decision and the first expansion step.
-__global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, int* ranks) {
+// One task = one row block of level L of one basis sketch (launch Lg holds
+// the tasks whose tree has Lg - L more levels above them than the deepest
+// tree, so that every root runs in the last launch).  Non-root blocks write
+// their R into the next level's matrix; the root block also does the CPQR of
+// R, the rank decision and the first expansion step.
+__global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg, int* ranks) {
   extern __shared__ double sm[];
   const DevTables& T = tables(wsb);
-  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[L])[blockIdx.x];
+  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[Lg])[blockIdx.x];
+  const int L = task.lev;
   const DevSketch s = dsk(wsb)[task.sk];
   const DevItem& it = ditems(wsb)[s.item];
   double* ws = reinterpret_cast<double*>(wsb);
@@ -366,10 +369,11 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int L, 
 
 // ---------------------------------------------------------------- TSQR down
 // Z_L(block) = Q_block [Z_{L+1}(rows of this block's R); 0].
-__global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int L, const int* ranks) {
+__global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int Lg, const int* ranks) {
   extern __shared__ double sm[];
   const DevTables& T = tables(wsb);
-  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[L])[blockIdx.x];
+  const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[Lg])[blockIdx.x];
+  const int L = task.lev;
   const DevSketch s = dsk(wsb)[task.sk];
   if (s.nlev - 1 <= L) return;  // root of this tree, already expanded
   const DevItem& it = ditems(wsb)[s.item];

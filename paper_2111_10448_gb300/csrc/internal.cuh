@@ -102,6 +102,8 @@ struct DevItem {
 struct Task {               // one block of one TSQR level (finalize)
   int sk;                   // sketch index
   int blk;                  // block index
+  int lev;                  // level within the sketch's own tree (the launches are aligned
+                            // so that every tree's root is in the last one)
 };
 
 // Device-resident tables, stored at the start of the workspace.

@@ -281,7 +281,8 @@ static void build_blob(Plan& P) {
     const DevSketch& s = P.sketches[si];
     if (!s.basis) continue;
     for (int L = 0; L < s.nlev; ++L)
-      for (int64_t b = 0; b < s.lev_nblk[L]; ++b) P.tasks[L].push_back(Task{si, (int)b});
+      for (int64_t b = 0; b < s.lev_nblk[L]; ++b)
+        P.tasks[L + P.max_lev - s.nlev].push_back(Task{si, (int)b, L});
   }
   DevTables t;
   std::memset(&t, 0, sizeof(t));
