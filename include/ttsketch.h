@@ -200,15 +200,19 @@ tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
                            int* ranks, tt_stream_t stream);
 
 /* Launch shape of the batched sketch: ta = tile rows along i_1 (32 or 64;
- * used by FP64 plans, TF32 / BF16 tiles are 64 rows), chunk = tiles a CTA
- * takes from the work counter at a time (>= 1), ctas_per_sm = persistent CTAs
- * per SM (1..32).  Host only. */
+ * used by FP64 plans, TF32 / BF16 tiles are 64 rows); for a TF32 / BF16 batch
+ * whose items all fit the small-plane kernel (n_1, n_d <= 32) ta is instead
+ * the largest number of kR values in a 16-plane block (1, 2, 4 or 8; other
+ * values mean 4); chunk = tiles (blocks) a CTA takes from the work counter at
+ * a time (>= 1), ctas_per_sm = persistent CTAs per SM (1..32; the small-plane
+ * kernel always runs one).  Host only. */
 tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_sm);
 
 /* Autotuner of the batched sketch (not in the paper): runs the batched
  * decomposition of X_ptrs once, times the batched sketch launch for every
  * candidate shape (ta in {32, 64} for FP64 plans, chunk in {1, 4, 16},
- * ctas_per_sm in {2, 4, 8}; CUDA events on `stream`, the second of two runs
+ * ctas_per_sm in {2, 4, 8}; small-plane batches: ta in {1, 2, 4, 8}, chunk
+ * in {1, 4, 8}; CUDA events on `stream`, the second of two runs
  * each) and keeps the fastest in the plan, then runs the decomposition once
  * more with it so that cores and ranks hold a valid result.  Synchronises;
  * refused during stream capture (TT_ERR_STATE).  best_out (host, 3 ints, may

@@ -74,7 +74,8 @@ cudaError_t launch_sketch_batched(const Plan& P, const void* const* X, const Bat
                                   cudaStream_t st) {
   const int nitems = plan_num_items(&P);
   if (nitems > kMaxBatchItems) return cudaErrorNotSupported;
-  if (plan_items_host(&P)[0].prec != TT_PREC_FP64 && sp_batched_eligible(P, nullptr, nullptr))
+  const int t3max = (cfg.ta == 1 || cfg.ta == 2 || cfg.ta == 4 || cfg.ta == 8) ? cfg.ta : 4;
+  if (plan_items_host(&P)[0].prec != TT_PREC_FP64 && sp_batched_eligible(P, nullptr, nullptr, t3max))
     return launch_sketch_sp_batched(P, X, cfg, ws, st);
   static BatchLaunch b;  // 16 KB: kept off the host stack
   b.wsb = (char*)ws;

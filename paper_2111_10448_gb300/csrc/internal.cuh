@@ -123,6 +123,7 @@ constexpr int kMaxBatchItems = 2048;
 struct BatchLaunch {
   char* wsb;
   int64_t chunk;                       // tiles taken from the counter at a time
+  int t3max;                           // small-plane kernel: largest kR values per block
   const void* X[kMaxBatchItems];
 };
 // Launch shape of the batched sketch (chosen by tt_plan_autotune).
@@ -153,7 +154,7 @@ bool use_tc_kernel(const Plan& P, int item, int64_t count);
 bool use_sp_kernel(const Plan& P, int item, int64_t count);
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st);
-bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out);
+bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out, int t3max = 4);
 cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
                                      cudaStream_t st);
 cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, cudaStream_t st);

@@ -620,8 +620,11 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   const bool f64 = P->items[0].prec == TT_PREC_FP64;
   std::vector<BatchCfg> cands;
   if (!f64 && sp_batched_eligible(*P, nullptr, nullptr)) {
-    // small-plane batched kernel: one CTA per SM, only the units per grab vary
-    for (int chunk : {1, 2, 4, 8}) cands.push_back(BatchCfg{64, chunk, 1});
+    // small-plane batched kernel (one CTA per SM): the block shape (ta = the
+    // largest number of kR values in a 16-plane block) and the units per grab
+    for (int t3 : {1, 2, 4, 8})
+      if (sp_batched_eligible(*P, nullptr, nullptr, t3))
+        for (int chunk : {1, 4, 8}) cands.push_back(BatchCfg{t3, chunk, 1});
   } else {
     for (int ta : {32, 64}) {
       if (!f64 && ta == 32) continue;
@@ -671,7 +674,9 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
 
 tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_sm) {
   Plan* P = as_plan(plan);
-  if (!P || (ta != 32 && ta != 64) || chunk < 1 || ctas_per_sm < 1 || ctas_per_sm > 32) return TT_ERR_INVALID_ARG;
+  if (!P || (ta != 32 && ta != 64 && ta != 1 && ta != 2 && ta != 4 && ta != 8) || chunk < 1 || ctas_per_sm < 1 ||
+      ctas_per_sm > 32)
+    return TT_ERR_INVALID_ARG;
   P->bcfg = BatchCfg{ta, chunk, ctas_per_sm};
   return TT_OK;
 }

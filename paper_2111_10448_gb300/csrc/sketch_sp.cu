@@ -68,7 +68,7 @@ constexpr int64_t kTableOffB = 256;  // dynamic shared memory; the static part i
 struct SpSk {
   int64_t rows, off, wdiv, hstride, tab;  // tab: byte offset of the staged rows, -1: generated per plane
   int col, sid, nslot, slot0, lflush;     // lflush: flushed on the column-side schedule
-  int pad_;
+  int dep;                                // output rows depend on the plane (through kL or kR)
 };
 
 struct SpArgs {
@@ -81,9 +81,11 @@ struct SpArgs {
   SpSk sk[kMaxSk];
 };
 
-// Block shape of an item: 16 planes, as many kR values as there are (up to 4).
-__host__ __device__ inline void sp_block_shape(int64_t WL, int64_t WR, int* T2, int* T3) {
-  const int t3 = WR >= 4 ? 4 : (int)WR;
+// Block shape of an item: 16 planes, as many kR values as there are, at
+// most t3max (1, 2, 4 or 8; the batched autotuner chooses it, single calls
+// use 4).
+__host__ __device__ inline void sp_block_shape(int64_t WL, int64_t WR, int t3max, int* T2, int* T3) {
+  const int t3 = WR >= t3max ? t3max : (int)WR;
   int t2 = kBlockPlanes / t3;
   if (t2 > WL) t2 = (int)WL;
   *T2 = t2;
@@ -161,14 +163,15 @@ __global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1
 
 // Launch arguments of one item (the whole last mode when count = n_d), shared
 // by the host launch and the batched kernel.
-__host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks, int64_t count, SpArgs& g) {
+__host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks, int64_t count, SpArgs& g,
+                                        int t3max = 4) {
   g.n1 = it.n[0];
   g.cnt = count;
   g.W = it.W;
   g.WL = it.N[it.ds] / it.n[0];
   g.WR = g.W / g.WL;
   g.Nd1 = it.N[it.d - 1];
-  sp_block_shape(g.WL, g.WR, &g.T2, &g.T3);
+  sp_block_shape(g.WL, g.WR, t3max, &g.T2, &g.T3);
   g.tilesL = (g.WL + g.T2 - 1) / g.T2;
   g.tilesR = (g.WR + g.T3 - 1) / g.T3;
   g.tab0 = it.off_sptab * 8;
@@ -190,10 +193,12 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
     k.col = d.type == SK_COL ? 1 : 0;
     k.sid = d.stream_id;
     const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
+    k.dep = per_plane_rows ? 1 : 0;
     k.nslot = per_plane_rows ? (k.col ? g.T2 : g.T3) : 1;
     k.slot0 = slots;
-    k.lflush = (k.col || k.nslot == 1) ? 1 : 0;
-    k.pad_ = 0;
+    // row slots of plane-dependent rows go out after every block (kR changes);
+    // everything else is kept while the kL block stays
+    k.lflush = (k.col || !k.dep) ? 1 : 0;
     slots += k.nslot;
     g.sk[s] = k;
   }
@@ -222,10 +227,10 @@ __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool lon
         int64_t base;
         if (s.col) {
           const uint32_t kL = (uint32_t)(bL * g.T2 + sl);
-          base = g.n1 * (int64_t)(s.nslot > 1 ? kL % (uint32_t)s.wdiv : 0u);
+          base = g.n1 * (int64_t)(s.dep ? kL % (uint32_t)s.wdiv : 0u);
         } else {
           const uint32_t kR = (uint32_t)(bR * g.T3 + sl);
-          base = (int64_t)(s.nslot > 1 ? kR / (uint32_t)(s.wdiv / g.WL) : 0u) + s.hstride * g.first;
+          base = (int64_t)(s.dep ? kR / (uint32_t)(s.wdiv / g.WL) : 0u) + s.hstride * g.first;
         }
         for (int o = lane; o < nout; o += 32) {
           const float v = p[o];
@@ -346,7 +351,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
         __syncwarp();
         // ---- D[j][o] = sum_k Gs[k][j] Xs'[k][o], hi and lo parts
         const int ntn = (nout + 7) >> 3;
-        const int sl = s.nslot > 1 ? (s.col ? sa : sb) : 0;
+        const int sl = s.dep ? (s.col ? sa : sb) : 0;
         float* slot = acc + (size_t)(s.slot0 + sl) * slot_elems;
         const int gq = lane >> 2, tq = lane & 3;
         constexpr int MT = LPAD / 16;
@@ -550,7 +555,7 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kerne
         __syncthreads();
         if (threadIdx.x == 0) {
           const DevItem& it = items[it_idx];
-          sp_fill(it, sks, it.n[it.d - 1], g);
+          sp_fill(it, sks, it.n[it.d - 1], g, b.t3max);
           g.X = reinterpret_cast<const float*>(b.X[it_idx]);
           g.wsb = b.wsb;
           g.first = 0;
@@ -597,7 +602,7 @@ __global__ void sp_table_batched_kernel(char* wsb) {
 
 // Unit prefix of the batched form (largest items first); resets the work
 // counter and the status word.
-__global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb) {
+__global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb, int t3max) {
   __shared__ int64_t cnt[kMaxBatchItems];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem* items = reinterpret_cast<const DevItem*>(wsb + T.off_items);
@@ -607,7 +612,7 @@ __global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb) {
     const DevItem& it = items[order[i]];
     const int64_t WL = it.N[it.ds] / it.n[0], WR = it.W / WL;
     int T2, T3;
-    sp_block_shape(WL, WR, &T2, &T3);
+    sp_block_shape(WL, WR, t3max, &T2, &T3);
     cnt[i] = ((WL + T2 - 1) / T2) * ((WR + T3 - 1) / T3);
   }
   __syncthreads();
@@ -623,7 +628,7 @@ __global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb) {
   }
 }
 
-bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) {
+bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, int t3max = 4) {
   const DevItem& it = plan_items_host(&P)[item];
   if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_TF32) || it.x_f64 || it.sptab_doubles == 0) return false;
   if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
@@ -632,7 +637,7 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem) 
     if (sks[it.sk0 + s].width != sks[it.sk0].width) return false;
   SpArgs g;
   memset(&g, 0, sizeof(g));
-  sp_fill(it, sks, count, g);
+  sp_fill(it, sks, count, g, t3max);
   const int lpad = g.ell <= 16 ? 16 : 32;
   const size_t tiles = it.prec == TT_PREC_TF32 ? (size_t)Prec<true>::kWarps * Prec<true>::kWarpBytes
                                                : (size_t)Prec<false>::kWarps * Prec<false>::kWarpBytes;
@@ -705,7 +710,7 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
 
 // Batched form: every item must fit the small-plane kernel with the same
 // padded width (the tables and tiles of a launch share it).
-bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out) {
+bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out, int t3max) {
   const int n = plan_num_items(&P);
   size_t smem = 0;
   int lpad = 0;
@@ -714,7 +719,7 @@ bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out) {
     if (it.prec != plan_items_host(&P)[0].prec) return false;
     sp::SpArgs g;
     size_t need = 0;
-    if (!sp::plan_sp(P, i, it.n[it.d - 1], &g, &need)) return false;
+    if (!sp::plan_sp(P, i, it.n[it.d - 1], &g, &need, t3max)) return false;
     const int lp = g.ell <= 16 ? 16 : 32;
     if (lpad && lp != lpad) return false;
     lpad = lp;
@@ -727,13 +732,16 @@ bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out) {
 
 cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
                                      cudaStream_t st) {
+  // ta of the launch shape is the largest number of kR values per block here
+  const int t3max = (cfg.ta == 1 || cfg.ta == 2 || cfg.ta == 4 || cfg.ta == 8) ? cfg.ta : 4;
   size_t smem = 0;
   int lpad = 0;
-  if (!sp_batched_eligible(P, &smem, &lpad)) return cudaErrorNotSupported;
+  if (!sp_batched_eligible(P, &smem, &lpad, t3max)) return cudaErrorNotSupported;
   const int nitems = plan_num_items(&P);
   static BatchLaunch b;  // 16 KB: kept off the host stack
   b.wsb = (char*)ws;
   b.chunk = std::max(1, cfg.chunk);
+  b.t3max = t3max;
   for (int i = 0; i < nitems; ++i) b.X[i] = X[i];
   static bool attr_set = false;
   if (!attr_set) {
@@ -750,7 +758,7 @@ cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const 
   }
   const bool tf = plan_items_host(&P)[0].prec == TT_PREC_TF32;
   count_launch();
-  sp::sp_batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws);
+  sp::sp_batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws, t3max);
   count_launch();
   sp::sp_table_batched_kernel<<<dim3(16, (unsigned)nitems), 256, 0, st>>>((char*)ws);
   count_launch();

@@ -157,3 +157,39 @@ def test_batched_bf16_graph_capture_replays():
             # the same launch replayed: FP32 slot sums are added into the FP64
             # sketches by atomics, so only their order may differ
             assert np.linalg.norm(got - refs[b]) <= 1e-6 * np.linalg.norm(refs[b]), b
+
+
+@pytest.mark.gpu
+def test_autotuner_small_plane_block_shape():
+    """BF16 small-plane batch: the autotuner picks a block shape (largest kR
+    count per 16-plane block) and units per grab among its candidates, and
+    the decomposition it leaves stays within 10 eps of the oracle."""
+    xs, probs = make_batch(20, cap=200_000, seed=29, dtype=np.float32)
+    t, dev = run_batched(xs, probs, prec="bf16", x_dtype=torch.float32)
+    best = t.autotune(dev)
+    assert best[0] in (1, 2, 4, 8) and best[1] in (1, 4, 8) and best[2] == 1, best
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        x64 = x.astype(np.float64)
+        o = OP.pstt2(x64, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
+        err = np.linalg.norm(full(t.core_list(b)) - OT.tt_full(o["cores"])) / np.linalg.norm(x64)
+        assert err <= 10 * EPS, (b, pr["dims"], err)
+    print("autotuned small-plane batched shape (kR per block, chunk, ctas/SM):", best)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [1, 2, 4, 8])
+def test_batched_small_plane_every_block_shape(shape):
+    """Every block shape of the small-plane batched kernel (largest number of
+    kR values per 16-plane block, so one-kR blocks of items with several kR
+    values too) gives a decomposition within 10 eps of the oracle."""
+    xs, probs = make_batch(16, cap=200_000, seed=31, dtype=np.float32)
+    t = TTSketch(None, batch=probs, x_dtype=torch.float32, prec="bf16")
+    t.batch_config(shape, 4, 1)
+    dev = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in xs]
+    t.batched(dev)
+    torch.cuda.synchronize()
+    for b, (x, pr) in enumerate(zip(xs, probs)):
+        x64 = x.astype(np.float64)
+        o = OP.pstt2(x64, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
+        err = np.linalg.norm(full(t.core_list(b)) - OT.tt_full(o["cores"])) / np.linalg.norm(x64)
+        assert err <= 10 * EPS, (shape, b, pr["dims"], err)
