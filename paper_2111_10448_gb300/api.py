@@ -163,7 +163,8 @@ class TTSketch:
         return out
 
     def kernel_kind(self, count_last=None):
-        """0 = FP64 SIMT, 1 = generic tensor-core (mma.sync), 2 = tcgen05 plane kernel."""
+        """0 = FP64 SIMT, 1 = generic tensor-core (mma.sync), 2 = tcgen05 plane kernel,
+        3 = small-plane tensor-core kernel."""
         c = self.dims[-1] if count_last is None else count_last
         return N.lib().tt_sketch_kernel_kind(self.plan, int(c))
 

@@ -324,3 +324,14 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(P, "lstsq_right", lambda S, B: (S[:, :B.shape[0]], np.ones(B.shape[0])))
     bad2 = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=3, seed=4)
     assert np.linalg.norm(x - tt.tt_full(bad2["cores"])) > 1e-3 * np.linalg.norm(x)
+
+
+def test_hilbert_type_block_equals_slices_of_the_whole_tensor():
+    """The sub-tensor generator used for sampled checks at full size gives the
+    same values, entry for entry, as slicing the whole generated tensor."""
+    d = [5, 4, 3, 6]
+    x = ti.hilbert_type(d).reshape(d, order="F")
+    b = ti.hilbert_type_block(d, [[2], None, [0, 2], None]).reshape((1, 4, 2, 6), order="F")
+    assert np.array_equal(b, x[2:3, :, [0, 2], :])
+    y = ti.hilbert_type(d, first_last=2, count_last=3).reshape((5, 4, 3, 3), order="F")
+    assert np.array_equal(y, x[..., 2:5])

@@ -59,13 +59,21 @@ def hilbert_type(dims, dtype=np.float32, first_last=0, count_last=None):
     the last mode [first_last, first_last + count_last).  The sum is formed in
     FP64 left to right (i_1 first), then 1/sum is rounded to `dtype`."""
     dims = [int(n) for n in dims]
-    d = len(dims)
     if count_last is None:
         count_last = dims[-1] - first_last
+    idx = [None] * (len(dims) - 1) + [np.arange(first_last, first_last + count_last)]
+    return hilbert_type_block(dims, idx, dtype)
+
+
+def hilbert_type_block(dims, idx, dtype=np.float32):
+    """The sub-tensor of hilbert_type(dims) at the index sets idx[k] of each
+    mode (None = the whole mode), column-major flat, with the same values
+    entry for entry (same FP64 summation order and rounding)."""
+    dims = [int(n) for n in dims]
     grids = [1.0 + np.arange(n, dtype=np.float64) / max(n - 1, 1) for n in dims]
-    grids[-1] = grids[-1][first_last:first_last + count_last]
+    grids = [g if ix is None else g[np.asarray(ix, dtype=np.int64)] for g, ix in zip(grids, idx)]
     s = grids[0]
-    for k in range(1, d):
+    for k in range(1, len(dims)):
         s = (s[:, None] + grids[k][None, :]).reshape(-1, order='F')
     return (1.0 / s).astype(dtype)
 
