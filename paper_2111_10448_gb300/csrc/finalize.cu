@@ -64,42 +64,139 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
-// In-shared-memory Householder QR of an nr x w block A (ld = lda), nr >= 1.
-// On exit column i holds v_i in rows i..nr-1 (v_i(0) at the diagonal), beta[i]
-// = 2 / (v_i^T v_i) (0 for a zero column), rdiag[i] = R(i, i); the strict
-// upper triangle holds R.
-__device__ void house_qr(double* A, int lda, int nr, int w, double* beta, double* rdiag,
-                         double* red) {
-  const int kmax = min(nr, w);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = 0; i < kmax; ++i) {
-    double part = 0.0;
-    for (int r = i + threadIdx.x; r < nr; r += blockDim.x) part += A[r + lda * i] * A[r + lda * i];
-    const double nsq = block_sum(part, red);
+// Sums over the 32 lanes of two or four per-lane values at once (halving
+// butterflies: 5 or 6 additions instead of 2 x 5 or 4 x 5).  warp_sum2: lane
+// L returns the sum of p[(L >> 4) & 1]; warp_sum4: of p[(L >> 3) & 3].
+__device__ __forceinline__ double warp_sum2(double p0, double p1) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16;
+  double k = h16 ? p1 : p0;
+  k += __shfl_xor_sync(0xffffffffu, h16 ? p0 : p1, 16);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  return k;
+}
+__device__ __forceinline__ double warp_sum4(double p0, double p1, double p2, double p3) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  double k0 = h16 ? p2 : p0, k1 = h16 ? p3 : p1;
+  k0 += __shfl_xor_sync(0xffffffffu, h16 ? p0 : p2, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, h16 ? p1 : p3, 16);
+  double k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// FP64 instructions on this GPU hold their sub-partition's FP64 pipe for 64
+// cycles each, and guarding one with a run-time condition costs several times
+// that even when the guard is false.  So the per-warp column groups below are
+// templates on their column count NC (1..4), dispatched by a switch, and
+// their FP64 arithmetic is unconditional.
+
+// Gram row entries g_c = sum_{r >= i} A(r, i) A(r, c) of the NC columns
+// c = cb + nw j, written to gram[c]; the group holding column i also forms the
+// reflector of step i (beta, R(i, i), head v0).
+template <int NC>
+__device__ __forceinline__ void gram_group(const double* A, int lda, int nr, int i, int cb, int nw,
+                                           double* gram, double* beta, double* rdiag, double* v0s) {
+  const int lane = threadIdx.x & 31;
+  double p[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int r = i + lane; r < nr; r += 32) {
+    const double a = A[r + lda * i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) p[j] = fma(a, A[r + lda * (cb + nw * j)], p[j]);
+  }
+  double g;
+  int q;
+  bool wr;
+  if (NC == 1) {
+    g = warp_sum(p[0]), q = 0, wr = lane == 0;
+  } else if (NC == 2) {
+    g = warp_sum2(p[0], p[1]), q = lane >> 4, wr = (lane & 15) == 0;
+  } else {
+    g = warp_sum4(p[0], p[1], p[2], p[3]), q = lane >> 3, wr = (lane & 7) == 0 && q < NC;
+  }
+  if (wr) gram[cb + nw * q] = g;
+  if (cb == i && lane == 0) {
     const double x0 = A[i + lda * i];
-    const double nx = sqrt(nsq);
+    const double nx = sqrt(g);
     double alpha = 0.0, b = 0.0;
     if (nx > 0.0) {
       alpha = -copysign(nx, x0);
       const double v0 = x0 - alpha;
-      const double vn2 = nsq - x0 * x0 + v0 * v0;
+      const double vn2 = g - x0 * x0 + v0 * v0;
       b = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      A[i + lda * i] = (nx > 0.0) ? x0 - alpha : 0.0;
-      beta[i] = b;
-      rdiag[i] = alpha;
+    beta[i] = b;
+    rdiag[i] = alpha;
+    *v0s = nx > 0.0 ? x0 - alpha : 0.0;
+  }
+}
+
+// A(i:, c) -= b v (v^T A(i:, c)) for the NC columns c = cb + nw j, with
+// v^T A(i:, c) = g_c - alpha A(i, c) and v = (v0, A(i+1:, i)).
+template <int NC>
+__device__ __forceinline__ void update_group(double* A, int lda, int nr, int i, int cb, int nw,
+                                             const double* gram, double b, double alpha, double v0) {
+  const int lane = threadIdx.x & 31;
+  double coef[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int c = cb + nw * j;
+    coef[j] = b * fma(-alpha, A[i + lda * c], gram[c]);
+  }
+  __syncwarp();
+  for (int r = i + lane; r < nr; r += 32) {
+    const double v = r == i ? v0 : A[r + lda * i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      double* e = A + r + lda * (cb + nw * j);
+      *e = fma(-coef[j], v, *e);
     }
-    __syncthreads();
-    if (b != 0.0) {
-      for (int c = i + 1 + wid; c < w; c += nw) {
-        double dot = 0.0;
-        for (int r = i + lane; r < nr; r += 32) dot += A[r + lda * i] * A[r + lda * c];
-        dot = warp_sum(dot) * b;
-        for (int r = i + lane; r < nr; r += 32) A[r + lda * c] -= dot * A[r + lda * i];
+  }
+}
+
+// In-shared-memory Householder QR of an nr x w block A (ld = lda), nr >= 1.
+// On exit column i holds v_i in rows i..nr-1 (v_i(0) at the diagonal), beta[i]
+// = 2 / (v_i^T v_i) (0 for a zero column), rdiag[i] = R(i, i); the strict
+// upper triangle holds R.
+//
+// Step i works from the Gram row g_c = sum_{r >= i} A(r, i) A(r, c), c >= i:
+// g_i is the squared norm of the pivot column, and with v = A(i:, i) - alpha
+// e_1 the reflector products are v^T A(i:, c) = g_c - alpha A(i, c).  So a
+// step is one reduction pass (every column's dot at once; the warp owning
+// columns c, c+8, c+16, c+24 sums them with one butterfly) and one update
+// pass, two barriers in all.
+__device__ __forceinline__ void house_qr(double* A, int lda, int nr, int w, double* beta, double* rdiag) {
+  const int kmax = min(nr, w);
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double v0s;
+  __shared__ double gram[TT_MAXL];
+  for (int i = 0; i < kmax; ++i) {
+    for (int cb = i + wid; cb < w; cb += 4 * nw) {
+      switch (min(4, (w - 1 - cb) / nw + 1)) {
+        case 1: gram_group<1>(A, lda, nr, i, cb, nw, gram, beta, rdiag, &v0s); break;
+        case 2: gram_group<2>(A, lda, nr, i, cb, nw, gram, beta, rdiag, &v0s); break;
+        case 3: gram_group<3>(A, lda, nr, i, cb, nw, gram, beta, rdiag, &v0s); break;
+        default: gram_group<4>(A, lda, nr, i, cb, nw, gram, beta, rdiag, &v0s); break;
       }
     }
+    __syncthreads();
+    const double b = beta[i], alpha = rdiag[i], v0 = v0s;
+    if (b != 0.0) {
+      for (int cb = i + 1 + wid; cb < w; cb += 4 * nw) {
+        switch (min(4, (w - 1 - cb) / nw + 1)) {
+          case 1: update_group<1>(A, lda, nr, i, cb, nw, gram, b, alpha, v0); break;
+          case 2: update_group<2>(A, lda, nr, i, cb, nw, gram, b, alpha, v0); break;
+          case 3: update_group<3>(A, lda, nr, i, cb, nw, gram, b, alpha, v0); break;
+          default: update_group<4>(A, lda, nr, i, cb, nw, gram, b, alpha, v0); break;
+        }
+      }
+    }
+    if (threadIdx.x == 0) A[i + lda * i] = v0;
     __syncthreads();
   }
   for (int i = kmax + threadIdx.x; i < w; i += blockDim.x) {
@@ -129,6 +226,64 @@ __device__ void apply_q(const double* V, int64_t ldv, const double* beta, int nr
   }
 }
 
+// Z(:, c) = H_0 ... H_{kmax-1} [Z0(0:kmax, c); 0] for the nr-row block of
+// reflectors V (ld ldv, heads v_i(0) on the diagonal) and beta, columns c <
+// ncol; columns ncol..npad-1 of Z are zero.  Z0 = Zin (ld ldzin).  One warp
+// per column keeps the column in registers through all reflectors (no barrier
+// between reflectors); NT = ceil(nr / 32) rows per lane, nr <= 256.
+constexpr int kRowsPerLane = 8;
+template <int NT>
+__device__ __forceinline__ void expand_cols_nt(const double* V, int64_t ldv, const double* beta, int nr, int w,
+                                               const double* Zin, int64_t ldzin, int ncol, int npad, double* Z,
+                                               int64_t ldz) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int kmax = min(nr, w);
+  for (int c = wid; c < npad; c += nw) {
+    double z[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = lane + 32 * t;
+      z[t] = (c < ncol && r < kmax) ? Zin[r + ldzin * c] : 0.0;
+    }
+    if (c < ncol) {
+      for (int i = kmax - 1; i >= 0; --i) {
+        const double b = beta[i];
+        if (b == 0.0) continue;
+        double v[NT];
+        double p = 0.0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          const int r = lane + 32 * t;
+          v[t] = (r >= i && r < nr) ? V[r + ldv * i] : 0.0;
+          p = fma(v[t], z[t], p);
+        }
+        p = warp_sum(p) * b;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) z[t] = fma(-p, v[t], z[t]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = lane + 32 * t;
+      if (r < nr) Z[r + ldz * c] = z[t];
+    }
+  }
+}
+__device__ __forceinline__ void expand_cols(const double* V, int64_t ldv, const double* beta, int nr, int w,
+                                            const double* Zin, int64_t ldzin, int ncol, int npad, double* Z,
+                                            int64_t ldz) {
+  switch ((nr + 31) / 32) {
+    case 1: expand_cols_nt<1>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 2: expand_cols_nt<2>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 3: expand_cols_nt<3>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 4: expand_cols_nt<4>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 5: expand_cols_nt<5>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 6: expand_cols_nt<6>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    case 7: expand_cols_nt<7>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+    default: expand_cols_nt<kRowsPerLane>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
+  }
+}
+
 // Copies an nr x w column-major block (leading dimension ldy) into shared
 // memory (leading dimension lda); eight independent loads per thread are in
 // flight at a time.
@@ -154,12 +309,12 @@ __device__ __forceinline__ void flag_status(char* wsb, int bits) {
 // tree, so that every root runs in the last launch).  Non-root blocks write
 // their R into the next level's matrix; the root block also does the CPQR of
 // R, the rank decision and the first expansion step.
-__global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg, int* ranks) {
+__global__ void __launch_bounds__(kThreads, 4) tsqr_level_kernel(char* wsb, int Lg, int* ranks) {
   extern __shared__ double sm[];
   const DevTables& T = tables(wsb);
   const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[Lg])[blockIdx.x];
   const int L = task.lev;
-  const DevSketch s = dsk(wsb)[task.sk];
+  const DevSketch& s = dsk(wsb)[task.sk];
   const DevItem& it = ditems(wsb)[s.item];
   double* ws = reinterpret_cast<double*>(wsb);
   const int w = s.width;
@@ -178,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg,
   double* Y = ws + s.lev_mat[L];
   load_block(A, lda, Y + r0, m, nr, w);
   __syncthreads();
-  house_qr(A, lda, nr, w, beta, rdiag, red);
+  house_qr(A, lda, nr, w, beta, rdiag);
   const int kmax = min(nr, w);
   // Householder vectors back in place, scalars to the level's beta array
   for (int o = threadIdx.x; o < nr * w; o += blockDim.x) {
@@ -200,7 +355,10 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg,
     }
     return;
   }
-  // ---- root: CPQR of R (w x w) in shared memory
+  // ---- root: CPQR of R (w x w) in shared memory.  Per step: warp 0 picks
+  // the pivot (largest recomputed trailing norm, lowest index on ties), swaps
+  // it into place and forms the reflector; then each warp applies it to its
+  // own columns and recomputes their trailing norms for the next step.
   for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
     const int i = o % w, c = o / w;
     Rs[i + w * c] = rval(i, c);
@@ -212,77 +370,87 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg,
   double total2 = 0.0;
   for (int o = threadIdx.x; o < w * w; o += blockDim.x) total2 += Rs[o] * Rs[o];
   total2 = block_sum(total2, red);
-  for (int i = 0; i < w; ++i) {
-    for (int c = i + threadIdx.x; c < w; c += blockDim.x) {
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < w; c += nw) {  // trailing norms of step 0
       double t = 0.0;
-      for (int r = i; r < w; ++r) t += Rs[r + w * c] * Rs[r + w * c];
-      nrm[c] = t;
+      for (int r = lane; r < w; r += 32) t = fma(Rs[r + w * c], Rs[r + w * c], t);
+      t = warp_sum(t);
+      if (lane == 0) nrm[c] = t;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int j = i;
-      for (int c = i + 1; c < w; ++c)
-        if (nrm[c] > nrm[j]) j = c;
-      if (j != i) {
-        for (int r = 0; r < w; ++r) {
-          const double t = Rs[r + w * i];
-          Rs[r + w * i] = Rs[r + w * j];
-          Rs[r + w * j] = t;
+    for (int i = 0; i < w; ++i) {
+      if (wid == 0) {
+        // argmax over c >= i; norms are >= 0, so their bit patterns order like them
+        long long key = -1;
+        int arg = w;
+        for (int c = i + lane; c < w; c += 32) {
+          const long long k2 = __double_as_longlong(nrm[c]);
+          if (k2 > key) key = k2, arg = c;
         }
-        const int t = piv[i];
-        piv[i] = piv[j];
-        piv[j] = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+          const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
+          if (k2 > key || (k2 == key && a2 < arg)) key = k2, arg = a2;
+        }
+        const int j = arg;
+        if (j != i) {
+          for (int r = lane; r < w; r += 32) {
+            const double t = Rs[r + w * i];
+            Rs[r + w * i] = Rs[r + w * j];
+            Rs[r + w * j] = t;
+          }
+          if (lane == 0) {
+            const int t = piv[i];
+            piv[i] = piv[j];
+            piv[j] = t;
+            const double tn = nrm[i];
+            nrm[i] = nrm[j];
+            nrm[j] = tn;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {  // Householder on column i, rows i..w-1
+          const double nsq = nrm[i];
+          const double x0 = Rs[i + w * i];
+          const double nx = sqrt(nsq);
+          double alpha = 0.0, b = 0.0;
+          if (nx > 0.0) {
+            alpha = -copysign(nx, x0);
+            const double v0 = x0 - alpha;
+            const double vn2 = nsq - x0 * x0 + v0 * v0;
+            b = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+          }
+          Rs[i + w * i] = nx > 0.0 ? x0 - alpha : 0.0;
+          qb[i] = b;
+          qd[i] = alpha;
+        }
       }
-    }
-    __syncthreads();
-    // Householder on column i, rows i..w-1 (w <= 64: one warp is enough)
-    if (threadIdx.x < 32) {
-      double part = 0.0;
-      for (int r = i + threadIdx.x; r < w; r += 32) part += Rs[r + w * i] * Rs[r + w * i];
-      const double nsq = warp_sum(part);
-      const double x0 = Rs[i + w * i];
-      const double nx = sqrt(nsq);
-      double alpha = 0.0, b = 0.0;
-      if (nx > 0.0) {
-        alpha = -copysign(nx, x0);
-        const double v0 = x0 - alpha;
-        const double vn2 = nsq - x0 * x0 + v0 * v0;
-        b = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
-      }
-      __syncwarp();
-      if (threadIdx.x == 0) {
-        Rs[i + w * i] = nx > 0.0 ? x0 - alpha : 0.0;
-        qb[i] = b;
-        qd[i] = alpha;
-      }
-    }
-    __syncthreads();
-    const double b = qb[i];
-    if (b != 0.0) {
-      for (int c = i + 1 + threadIdx.x; c < w; c += blockDim.x) {
+      __syncthreads();
+      const double b = qb[i];
+      for (int c = i + 1 + wid; c < w; c += nw) {
         double dot = 0.0;
-        for (int r = i; r < w; ++r) dot += Rs[r + w * i] * Rs[r + w * c];
-        dot *= b;
-        for (int r = i; r < w; ++r) Rs[r + w * c] -= dot * Rs[r + w * i];
+        for (int r = i + lane; r < w; r += 32) dot = fma(Rs[r + w * i], Rs[r + w * c], dot);
+        dot = warp_sum(dot) * b;
+        double t = 0.0;
+        for (int r = i + lane; r < w; r += 32) {
+          const double v = fma(-dot, Rs[r + w * i], Rs[r + w * c]);
+          Rs[r + w * c] = v;
+          const double vt = r > i ? v : 0.0;
+          t = fma(vt, vt, t);
+        }
+        t = warp_sum(t);
+        if (lane == 0) nrm[c] = t;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   // Q2 = H_0 ... H_{w-1} I
   for (int o = threadIdx.x; o < w * w; o += blockDim.x) Q2[o] = (o % w == o / w) ? 1.0 : 0.0;
   __syncthreads();
-  for (int i = w - 1; i >= 0; --i) {
-    const double b = qb[i];
-    if (b != 0.0) {
-      for (int c = threadIdx.x; c < w; c += blockDim.x) {
-        double dot = 0.0;
-        for (int r = i; r < w; ++r) dot += Rs[r + w * i] * Q2[r + w * c];
-        dot *= b;
-        for (int r = i; r < w; ++r) Q2[r + w * c] -= dot * Rs[r + w * i];
-      }
-    }
-    __syncthreads();
-  }
+  expand_cols(Rs, w, qb, w, w, Q2, w, w, w, Q2, w);
+  __syncthreads();
   // Rt with signs normalised (diag >= 0), Q2 columns likewise
   double* Rt = ws + s.off_rt;
   for (int o = threadIdx.x; o < w * w; o += blockDim.x) {
@@ -358,13 +526,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_level_kernel(char* wsb, int Lg,
     ws[it.off_rr[s.k] + o] = (i < r && c < r) ? Rt[i + w * c] : 0.0;
   }
   // Z_root = Q_root [Q2(:, 1:r); 0]  (m x rpad, columns >= r are zero)
-  double* Z = ws + s.lev_z[L];
-  for (int o = threadIdx.x; o < nr * s.rpad; o += blockDim.x) {
-    const int rr = o % nr, c = o / nr;
-    Z[rr + m * c] = (c < r && rr < w) ? Q2[rr + w * c] : 0.0;
-  }
-  __syncthreads();
-  apply_q(A, lda, beta, nr, w, Z, m, r);
+  expand_cols(A, lda, beta, nr, w, Q2, w, r, s.rpad, ws + s.lev_z[L], m);
 }
 
 // ---------------------------------------------------------------- TSQR down
@@ -374,7 +536,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int Lg
   const DevTables& T = tables(wsb);
   const Task task = reinterpret_cast<const Task*>(wsb + T.off_tasks[Lg])[blockIdx.x];
   const int L = task.lev;
-  const DevSketch s = dsk(wsb)[task.sk];
+  const DevSketch& s = dsk(wsb)[task.sk];
   if (s.nlev - 1 <= L) return;  // root of this tree, already expanded
   const DevItem& it = ditems(wsb)[s.item];
   double* ws = reinterpret_cast<double*>(wsb);
@@ -390,15 +552,9 @@ __global__ void __launch_bounds__(kThreads) tsqr_expand_kernel(char* wsb, int Lg
   load_block(V, lda, Y + r0, m, nr, w);
   for (int i = threadIdx.x; i < w; i += blockDim.x) beta[i] = ws[s.lev_beta[L] + (int64_t)task.blk * w + i];
   const int64_t m1 = s.lev_rows[L + 1];
-  const double* Zin = ws + s.lev_z[L + 1];
-  double* Z = ws + s.lev_z[L];
-  const int kmax = min(nr, w);
-  for (int o = threadIdx.x; o < nr * s.rpad; o += blockDim.x) {
-    const int rr = o % nr, c = o / nr;
-    Z[r0 + rr + m * c] = (c < r && rr < kmax) ? Zin[(int64_t)task.blk * w + rr + m1 * c] : 0.0;
-  }
   __syncthreads();
-  apply_q(V, lda, beta, nr, w, Z + r0, m, r);
+  expand_cols(V, lda, beta, nr, w, ws + s.lev_z[L + 1] + (int64_t)task.blk * w, m1, r, s.rpad,
+              ws + s.lev_z[L] + r0, m);
 }
 
 // --------------------------------------------------------- one-pass middle
@@ -447,7 +603,7 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
 __global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item_arg, const int* ranks) {
   const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
   __shared__ double A[TT_MAXL * (TT_MAXL + 1)];
-  __shared__ double beta[TT_MAXL], rdiag[TT_MAXL], red[32];
+  __shared__ double beta[TT_MAXL], rdiag[TT_MAXL];
   const DevItem& it = ditems(wsb)[item];
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.ds];
@@ -459,7 +615,7 @@ __global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item_ar
     A[j + lda * c] = ws[it.off_B + c + (int64_t)rp * j];  // B^T(j, c) = B(c, j)
   }
   __syncthreads();
-  house_qr(A, lda, l, r, beta, rdiag, red);
+  house_qr(A, lda, l, r, beta, rdiag);
   // RB (rp x rp) with diag >= 0; QB = H_0..H_{r-1} [I_r; 0] with matching signs
   double* RB = ws + it.off_RB;
   double* QB = ws + it.off_QB;
@@ -539,11 +695,20 @@ __global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item_arg
 //            (identity 1x1 for k = 1), B = Q_k or H (middle core, one-pass).
 // Right type (k > d*):  G(a,i,c) = sum_v A(i + n_k v, a) B(v, c),   A = P_{k-1},
 //            B = P_k (identity 1x1 for k = d).
+//
+// Both are G(:, i, :) = A_i^T B_i (ra x rc) over a contraction of length
+// `inner`: left A_i = A, B_i = rows [inner i, inner (i + 1)) of B; right A_i =
+// rows {i + n_k v} of A, B_i = B; an absent factor is the 1 x 1 identity.  One
+// block per (item, k, slice i): chunks of A_i and B_i are staged in shared
+// memory and the threads split the (a, c) pairs and the contraction index, so
+// the FP64 work is the plain multiply-adds with one short reduction per pair.
+constexpr int kCoreChunk = 32;
 __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* cores, const int* ranks,
-                                                         int item0, int nitems, int only_k) {
-  const int pair = blockIdx.x;
-  const int item = item0 + pair / TT_MAXD;
-  const int k = pair % TT_MAXD + 1;
+                                                         int item0, int nitems, int only_k, int dmax) {
+  __shared__ double sA[kCoreChunk * TT_MAXL], sB[kCoreChunk * TT_MAXL];
+  __shared__ double red[kThreads];
+  const int item = item0 + (int)blockIdx.x / dmax;
+  const int k = (int)blockIdx.x % dmax + 1;
   if (item >= item0 + nitems) return;
   const DevItem& it = ditems(wsb)[item];
   if (k > it.d) return;
@@ -555,7 +720,6 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
   const int ra = rk[k - 1], rc = rk[k];
   const int rpa = it.rpad[k - 1], rpc = it.rpad[k];
   const int64_t nk = it.n[k - 1];
-  const int64_t total = (int64_t)rpa * nk * rpc;
   double* G = cores + it.core_off[k];
   const bool left = k <= it.ds;
   const double* A = nullptr;
@@ -587,38 +751,42 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
       ldb = sb.rows;
     }
   }
-  const bool copy = left ? (A == nullptr) : (B == nullptr);
-  if (copy) {
-    // G_1 = Q_1 or G_d = P_{d-1}^T: one thread per entry
-    for (int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.y * blockDim.x) {
-      const int a = (int)(e % rpa);
-      const int64_t i = (e / rpa) % nk;
-      const int c = (int)(e / (rpa * nk));
-      double v = 0.0;
-      if (a < ra && c < rc) v = left ? B[i + ldb * c] : A[i + lda * a];
-      G[e] = v;
-    }
-    return;
-  }
-  // one warp per entry, the lanes split the contraction (coalesced along u
-  // on the left side, along v for B on the right side)
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.y * (blockDim.x >> 5);
-  for (int64_t e = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5); e < total; e += nwarps) {
-    const int a = (int)(e % rpa);
-    const int64_t i = (e / rpa) % nk;
-    const int c = (int)(e / (rpa * nk));
-    double acc = 0.0;
-    if (a < ra && c < rc) {
-      if (left) {
-        for (int64_t u = lane; u < inner; u += 32) acc += A[u + lda * a] * B[u + inner * i + ldb * c];
-      } else {
-        for (int64_t v = lane; v < inner; v += 32) acc += A[i + nk * v + lda * a] * B[v + ldb * c];
+  const int P = ra * rc;
+  for (int64_t i = blockIdx.y; i < nk; i += gridDim.y) {
+    double* Gi = G + rpa * i;  // G(a, i, c) = Gi[a + rpa nk c]
+    for (int pg = 0; pg < P; pg += blockDim.x) {
+      const int Pg = min(P - pg, (int)blockDim.x), nsplit = blockDim.x / Pg;
+      const int p = pg + (int)threadIdx.x % Pg, sp = (int)threadIdx.x / Pg;
+      const int a = p % ra, c = p / ra;
+      double acc = 0.0;
+      for (int64_t u0 = 0; u0 < inner; u0 += kCoreChunk) {
+        const int uc = (int)imin64(kCoreChunk, inner - u0);
+        __syncthreads();
+        for (int o = threadIdx.x; o < uc * ra; o += blockDim.x) {
+          const int u = o % uc, aa = o / uc;
+          sA[u + kCoreChunk * aa] = left ? (A ? A[u0 + u + lda * aa] : 1.0) : A[i + nk * (u0 + u) + lda * aa];
+        }
+        for (int o = threadIdx.x; o < uc * rc; o += blockDim.x) {
+          const int u = o % uc, cc = o / uc;
+          sB[u + kCoreChunk * cc] = left ? B[u0 + u + inner * i + ldb * cc] : (B ? B[u0 + u + ldb * cc] : 1.0);
+        }
+        __syncthreads();
+        if (sp < nsplit)
+          for (int u = sp; u < uc; u += nsplit) acc = fma(sA[u + kCoreChunk * a], sB[u + kCoreChunk * c], acc);
       }
-      acc = warp_sum(acc);
+      red[threadIdx.x] = sp < nsplit ? acc : 0.0;
+      __syncthreads();
+      if ((int)threadIdx.x < Pg) {
+        double t = 0.0;
+        for (int q = 0; q < nsplit; ++q) t += red[threadIdx.x + Pg * q];
+        Gi[a + rpa * nk * c] = t;
+      }
+      __syncthreads();
     }
-    if (lane == 0) G[e] = acc;
+    for (int o = threadIdx.x; o < rpa * rpc; o += blockDim.x) {
+      const int a = o % rpa, c = o / rpa;
+      if (a >= ra || c >= rc) Gi[a + rpa * nk * c] = 0.0;
+    }
   }
 }
 
@@ -718,9 +886,9 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
   cudaError_t e;
   static bool attr = false;
   if (!attr) {
-    e = cudaFuncSetAttribute(tsqr_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(tsqr_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsqrSmemMax);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tsqr_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    e = cudaFuncSetAttribute(tsqr_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsqrSmemMax);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -796,18 +964,27 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)(nitems * TT_MAXD), 64);
+  int dmax = 1;
+  int64_t nmax = 1;
+  for (int i = 0; i < nitems; ++i) {
+    const DevItem& it = plan_items_host(&P)[i];
+    dmax = std::max(dmax, it.d);
+    for (int k = 0; k < it.d; ++k) nmax = std::max(nmax, it.n[k]);
+  }
+  const int64_t gy = std::min<int64_t>(nmax, std::max<int64_t>(1, 2048 / ((int64_t)nitems * dmax)));
+  dim3 grid((unsigned)(nitems * dmax), (unsigned)gy);
   count_launch();
-  cores_kernel<<<grid, kThreads, 0, st>>>(wsb, cores, ranks, 0, nitems, 0);
+  cores_kernel<<<grid, kThreads, 0, st>>>(wsb, cores, ranks, 0, nitems, 0, dmax);
   return cudaGetLastError();
 }
 
 // Cores of one item only (k = only_k), used by the two-pass middle core.
 cudaError_t launch_cores_one(const Plan& P, int item, int only_k, void* ws, double* cores,
                              const int* ranks, cudaStream_t st) {
-  dim3 grid((unsigned)TT_MAXD, 16);
+  const DevItem& it = plan_items_host(&P)[item];
+  dim3 grid((unsigned)it.d, (unsigned)std::min<int64_t>(it.n[only_k - 1], 512));
   count_launch();
-  cores_kernel<<<grid, kThreads, 0, st>>>((char*)ws, cores, ranks, item, 1, only_k);
+  cores_kernel<<<grid, kThreads, 0, st>>>((char*)ws, cores, ranks, item, 1, only_k, it.d);
   return cudaGetLastError();
 }
 

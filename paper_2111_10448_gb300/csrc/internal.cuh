@@ -22,7 +22,8 @@ namespace tts {
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-constexpr int kMaxLev = 8;        // TSQR tree depth limit
+constexpr int kMaxLev = 12;       // TSQR tree depth limit
+constexpr int64_t kTsqrSmemMax = 200 * 1024;  // dynamic shared memory of a TSQR level block
 constexpr int kTcGroupBytes = 2304;  // plane kernel: one 8-column group of a 128-row BF16 block image
 constexpr int kMaxSk = TT_MAXD;   // sketches per item (d of them at most)
 

@@ -159,10 +159,14 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     DevSketch& s = P.sketches[si];
     if (!s.basis) continue;
     const int w = s.width;
-    // Row blocks of 256 (at least 2 l, a multiple of 32): a 65536-row sketch
-    // gives 256 leaf blocks of ~33 KB each, several resident per SM, so the
-    // leaf level spreads its FP64 work over the whole GPU.
-    const int bl = std::max(256, (2 * w + 31) / 32 * 32);
+    // Row blocks of 128 rows, or 4 l when that is more (a multiple of 32,
+    // capped at 192 so that a root block and its l x l work matrices fit in
+    // shared memory for l <= 64): each tree level shrinks the rows 3-8x, and a
+    // block's QR -- a chain of FP64 steps on one SM -- stays short.  A
+    // 65536-row sketch of width 16 gives 512 leaf blocks (16 KB each, several
+    // resident per SM) and four levels.
+    const int bl = std::min(192, std::max(128, (4 * w + 31) / 32 * 32));
+    if (8 * ((int64_t)(bl + 1) * w + 32 + 2 * TT_MAXL + 3LL * w * w) > kTsqrSmemMax) return TT_ERR_UNSUPPORTED;
     s.bl = bl;
     int64_t m = s.rows;
     int L = 0;
