@@ -566,12 +566,16 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
   __shared__ double Ps[CH * TT_MAXL];
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevItem& it = ditems(wsb)[item];
-  const DevSketch sp = dsk(wsb)[it.basis_of_k[it.ds]];
+  const DevSketch& sp = dsk(wsb)[it.basis_of_k[it.ds]];
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.ds];
   const int l = it.lmid;
   const int64_t M = sp.rows;
   const double* Pm = ws + sp.lev_z[0];
+  // with r l <= blockDim pairs each thread keeps its pair's sum across the
+  // block's row chunks and adds it to B once
+  const bool keep = r * l <= (int)blockDim.x;
+  double kept = 0.0;
   for (int64_t v0 = (int64_t)blockIdx.x * CH; v0 < M; v0 += (int64_t)gridDim.x * CH) {
     const int nv = (int)imin64(CH, M - v0);
     __syncthreads();
@@ -592,9 +596,14 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
     for (int o = threadIdx.x; o < r * l; o += blockDim.x) {
       const int c = o % r, j = o / r;
       double acc = 0.0;
-      for (int v = 0; v < nv; ++v) acc += Ps[v + CH * c] * Gs[v + CH * j];
-      atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
+      for (int v = 0; v < nv; ++v) acc = fma(Ps[v + CH * c], Gs[v + CH * j], acc);
+      if (keep) kept += acc;
+      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
     }
+  }
+  if (keep && (int)threadIdx.x < r * l) {
+    const int c = (int)threadIdx.x % r, j = (int)threadIdx.x / r;
+    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, kept);
   }
 }
 
@@ -646,47 +655,48 @@ __global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item_ar
   }
   __syncthreads();
   apply_q(A, lda, beta, l, r, QB, l, r);
-  for (int o = threadIdx.x; o < l * r; o += blockDim.x) {
-    const int c = o / l;
-    QB[o] *= sgn[c];
+  // M = QB RB^{-T}, stored over QB: row j solves m RB^T = QB(j, :) from the
+  // last column (a zero diagonal of RB gives a zero column, as flagged above),
+  // so that H = S_{d*} M is a plain product.
+  __shared__ double rinv[TT_MAXL];
+  for (int c = threadIdx.x; c < r; c += blockDim.x) {
+    const double dg = RB[c + rp * c];
+    rinv[c] = dg != 0.0 ? 1.0 / dg : 0.0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < l; j += blockDim.x) {
+    for (int c = r - 1; c >= 0; --c) {
+      double t = QB[j + (int64_t)l * c] * sgn[c];
+      for (int c2 = c + 1; c2 < r; ++c2) t = fma(-QB[j + (int64_t)l * c2], RB[c + rp * c2], t);
+      QB[j + (int64_t)l * c] = t * rinv[c];
+    }
   }
 }
 
-// H = S_{d*} QB RB^{-T}  (N_{d*} x rpad), one thread per row.
+// H = S_{d*} M  (N_{d*} x rpad, columns >= r zero), M = QB RB^{-T} (l x r)
+// from mid_ls_kernel; one thread per entry of H.
 // item < 0: batched launch, item = blockIdx.y
 __global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item_arg, const int* ranks) {
   const int item = item_arg >= 0 ? item_arg : (int)blockIdx.y;
-  __shared__ double QBs[TT_MAXL * TT_MAXL];
-  __shared__ double RBs[TT_MAXL * TT_MAXL];
+  __shared__ double Ms[TT_MAXL * TT_MAXL];
   const DevItem& it = ditems(wsb)[item];
-  const DevSketch sm_ = dsk(wsb)[it.mid_sk];
+  const DevSketch& sm_ = dsk(wsb)[it.mid_sk];
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.ds];
   const int rp = it.rpad[it.ds];
   const int l = it.lmid;
-  for (int o = threadIdx.x; o < l * r; o += blockDim.x) QBs[o] = ws[it.off_QB + o];
-  for (int o = threadIdx.x; o < rp * rp; o += blockDim.x) RBs[o] = ws[it.off_RB + o];
+  for (int o = threadIdx.x; o < l * r; o += blockDim.x) Ms[o] = ws[it.off_QB + o];
   __syncthreads();
   const int64_t Nm = sm_.rows;
   const double* S = ws + sm_.off;
   double* H = ws + it.off_H;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < Nm; u += (int64_t)gridDim.x * blockDim.x) {
-    double h[TT_MAXL];
-    double srow[TT_MAXL];
-    for (int j = 0; j < l; ++j) srow[j] = S[u + Nm * j];
-    for (int c = 0; c < r; ++c) {
-      double t = 0.0;
-      for (int j = 0; j < l; ++j) t += srow[j] * QBs[j + l * c];
-      h[c] = t;
-    }
-    // H RB^T = T with RB upper triangular: back substitution from the last column
-    for (int c = r - 1; c >= 0; --c) {
-      double t = h[c];
-      for (int c2 = c + 1; c2 < r; ++c2) t -= h[c2] * RBs[c + rp * c2];
-      const double dgn = RBs[c + rp * c];
-      h[c] = dgn != 0.0 ? t / dgn : 0.0;
-    }
-    for (int c = 0; c < rp; ++c) H[u + Nm * c] = c < r ? h[c] : 0.0;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < Nm * rp; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = o % Nm;
+    const int c = (int)(o / Nm);
+    double h = 0.0;
+    if (c < r)
+      for (int j = 0; j < l; ++j) h = fma(S[u + Nm * j], Ms[j + l * c], h);
+    H[o] = h;
   }
 }
 
@@ -872,9 +882,9 @@ cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* rank
   mid_ls_kernel<<<dim3(1, (unsigned)nitems), kThreads, 0, st>>>(wsb, -1, ranks);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const unsigned gx = (unsigned)std::min<int64_t>((Nmax + 127) / 128, 64);
+  const unsigned gx = (unsigned)std::min<int64_t>((Nmax * TT_MAXL + kThreads - 1) / kThreads, 64);
   count_launch();
-  mid_h_kernel<<<dim3(gx, (unsigned)nitems), 128, 0, st>>>(wsb, -1, ranks);
+  mid_h_kernel<<<dim3(gx, (unsigned)nitems), kThreads, 0, st>>>(wsb, -1, ranks);
   return cudaGetLastError();
 }
 
@@ -945,7 +955,7 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     if (e != cudaSuccess) return e;
     if (it.prec == TT_PREC_FP64) {
       const int64_t M = sks[it.basis_of_k[it.ds]].rows;
-      const int grid = (int)std::min<int64_t>((M + 31) / 32, 4LL * device_sm_count());
+      const int grid = (int)std::min<int64_t>((M + 31) / 32, 2LL * device_sm_count());
       count_launch();
       mid_b_kernel_f64<<<grid, kThreads, 0, st>>>(wsb, i, ranks);
       e = cudaGetLastError();
@@ -958,9 +968,9 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t Nm = it.N[it.ds];
-    const int grid = (int)std::min<int64_t>((Nm + 127) / 128, 8LL * device_sm_count());
+    const int grid = (int)std::min<int64_t>((Nm * it.rpad[it.ds] + kThreads - 1) / kThreads, 8LL * device_sm_count());
     count_launch();
-    mid_h_kernel<<<grid, 128, 0, st>>>(wsb, i, ranks);
+    mid_h_kernel<<<grid, kThreads, 0, st>>>(wsb, i, ranks);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

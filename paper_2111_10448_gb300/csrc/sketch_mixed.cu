@@ -41,12 +41,16 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
-  const DevSketch sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.ds]];
+  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.ds]];
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.ds];
   const int l = it.lmid;
   const int64_t M = sp.rows;
   const double* Pm = ws + sp.lev_z[0];
+  // with r l <= blockDim pairs each thread keeps its pair's sum across the
+  // block's row chunks and adds it to B once
+  const bool keep = r * l <= (int)blockDim.x;
+  double kept = 0.0;
   for (int64_t v0 = (int64_t)blockIdx.x * CH; v0 < M; v0 += (int64_t)gridDim.x * CH) {
     const int nv = (int)imin64(CH, M - v0);
     __syncthreads();
@@ -67,9 +71,14 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
     for (int o = threadIdx.x; o < r * l; o += blockDim.x) {
       const int c = o % r, j = o / r;
       double acc = 0.0;
-      for (int v = 0; v < nv; ++v) acc += Ps[v + CH * c] * Gs[v + CH * j];
-      atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
+      for (int v = 0; v < nv; ++v) acc = fma(Ps[v + CH * c], Gs[v + CH * j], acc);
+      if (keep) kept += acc;
+      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
     }
+  }
+  if (keep && (int)threadIdx.x < r * l) {
+    const int c = (int)threadIdx.x % r, j = (int)threadIdx.x / r;
+    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, kept);
   }
 }
 
@@ -101,7 +110,7 @@ cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks
 cudaError_t launch_mid_b_mixed(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st) {
   const DevItem& it = plan_items_host(&P)[item];
   const int64_t M = plan_sketches_host(&P)[it.basis_of_k[it.ds]].rows;
-  const int grid = (int)std::min<int64_t>((M + 31) / 32, 4LL * device_sm_count());
+  const int grid = (int)std::min<int64_t>((M + 31) / 32, 2LL * device_sm_count());
   count_launch();
   mid_b_kernel_mixed<<<grid, 256, 0, st>>>((char*)ws, item, ranks);
   return cudaGetLastError();
