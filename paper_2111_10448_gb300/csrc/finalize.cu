@@ -228,46 +228,86 @@ __device__ void apply_q(const double* V, int64_t ldv, const double* beta, int nr
 
 // Z(:, c) = H_0 ... H_{kmax-1} [Z0(0:kmax, c); 0] for the nr-row block of
 // reflectors V (ld ldv, heads v_i(0) on the diagonal) and beta, columns c <
-// ncol; columns ncol..npad-1 of Z are zero.  Z0 = Zin (ld ldzin).  One warp
-// per column keeps the column in registers through all reflectors (no barrier
-// between reflectors); NT = ceil(nr / 32) rows per lane, nr <= 256.
+// ncol; columns ncol..npad-1 of Z are zero.  Z0 = Zin (ld ldzin).  A warp
+// keeps NC columns c = cb + nw j in registers through all reflectors (no
+// barrier between reflectors; one butterfly per reflector for the NC dots;
+// NC > 1 only for blocks of at most 64 rows); NT = ceil(nr / 32) rows per
+// lane, nr <= 256.
 constexpr int kRowsPerLane = 8;
+template <int NC>
+__device__ __forceinline__ void warp_sums(const double (&p)[4], double (&d)[4]) {
+  if (NC == 1) {
+    d[0] = warp_sum(p[0]);
+  } else if (NC == 2) {
+    const double g = warp_sum2(p[0], p[1]);
+    d[0] = __shfl_sync(0xffffffffu, g, 0);
+    d[1] = __shfl_sync(0xffffffffu, g, 16);
+  } else {
+    const double g = warp_sum4(p[0], p[1], p[2], p[3]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = __shfl_sync(0xffffffffu, g, 8 * j);
+  }
+}
+template <int NT, int NC>
+__device__ __forceinline__ void expand_group(const double* V, int64_t ldv, const double* beta, int nr, int kmax,
+                                             const double* Zin, int64_t ldzin, int cb, int nw, double* Z,
+                                             int64_t ldz) {
+  const int lane = threadIdx.x & 31;
+  double z[NC][NT];
+#pragma unroll
+  for (int j = 0; j < NC; ++j)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = lane + 32 * t;
+      z[j][t] = r < kmax ? Zin[r + ldzin * (cb + nw * j)] : 0.0;
+    }
+  for (int i = kmax - 1; i >= 0; --i) {
+    const double b = beta[i];
+    if (b == 0.0) continue;
+    double v[NT];
+    double p[4] = {0.0, 0.0, 0.0, 0.0}, d[4];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = lane + 32 * t;
+      v[t] = (r >= i && r < nr) ? V[r + ldv * i] : 0.0;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) p[j] = fma(v[t], z[j][t], p[j]);
+    }
+    warp_sums<NC>(p, d);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const double s = d[j] * b;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) z[j][t] = fma(-s, v[t], z[j][t]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NC; ++j)
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int r = lane + 32 * t;
+      if (r < nr) Z[r + ldz * (cb + nw * j)] = z[j][t];
+    }
+}
 template <int NT>
 __device__ __forceinline__ void expand_cols_nt(const double* V, int64_t ldv, const double* beta, int nr, int w,
                                                const double* Zin, int64_t ldzin, int ncol, int npad, double* Z,
                                                int64_t ldz) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int kmax = min(nr, w);
-  for (int c = wid; c < npad; c += nw) {
-    double z[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int r = lane + 32 * t;
-      z[t] = (c < ncol && r < kmax) ? Zin[r + ldzin * c] : 0.0;
-    }
-    if (c < ncol) {
-      for (int i = kmax - 1; i >= 0; --i) {
-        const double b = beta[i];
-        if (b == 0.0) continue;
-        double v[NT];
-        double p = 0.0;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          const int r = lane + 32 * t;
-          v[t] = (r >= i && r < nr) ? V[r + ldv * i] : 0.0;
-          p = fma(v[t], z[t], p);
-        }
-        p = warp_sum(p) * b;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) z[t] = fma(-p, v[t], z[t]);
+  if (NT > 2) {  // tall blocks: one column per warp keeps the registers in bounds
+    for (int c = wid; c < ncol; c += nw) expand_group<NT, 1>(V, ldv, beta, nr, kmax, Zin, ldzin, c, nw, Z, ldz);
+  } else {
+    for (int cb = wid; cb < ncol; cb += 4 * nw) {
+      switch (min(4, (ncol - 1 - cb) / nw + 1)) {
+        case 1: expand_group<NT, 1>(V, ldv, beta, nr, kmax, Zin, ldzin, cb, nw, Z, ldz); break;
+        case 2: expand_group<NT, 2>(V, ldv, beta, nr, kmax, Zin, ldzin, cb, nw, Z, ldz); break;
+        case 3: expand_group<NT, 3>(V, ldv, beta, nr, kmax, Zin, ldzin, cb, nw, Z, ldz); break;
+        default: expand_group<NT, 4>(V, ldv, beta, nr, kmax, Zin, ldzin, cb, nw, Z, ldz); break;
       }
     }
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int r = lane + 32 * t;
-      if (r < nr) Z[r + ldz * c] = z[t];
-    }
   }
+  for (int o = threadIdx.x; o < nr * (npad - ncol); o += blockDim.x) Z[o % nr + ldz * (ncol + o / nr)] = 0.0;
 }
 __device__ __forceinline__ void expand_cols(const double* V, int64_t ldv, const double* beta, int nr, int w,
                                             const double* Zin, int64_t ldzin, int ncol, int npad, double* Z,
@@ -282,6 +322,36 @@ __device__ __forceinline__ void expand_cols(const double* V, int64_t ldv, const 
     case 7: expand_cols_nt<7>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
     default: expand_cols_nt<kRowsPerLane>(V, ldv, beta, nr, w, Zin, ldzin, ncol, npad, Z, ldz); break;
   }
+}
+
+// One pivoted-QR step's update of the NC root columns c = cb + nw j > i by
+// reflector i (v = Rs(i:, i), beta b), and their trailing norms over rows > i.
+template <int NC>
+__device__ __forceinline__ void cpqr_group(double* Rs, int w, int i, int cb, int nw, double b, double* nrm) {
+  const int lane = threadIdx.x & 31;
+  double p[4] = {0.0, 0.0, 0.0, 0.0}, d[4];
+  for (int r = i + lane; r < w; r += 32) {
+    const double v = Rs[r + w * i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) p[j] = fma(v, Rs[r + w * (cb + nw * j)], p[j]);
+  }
+  warp_sums<NC>(p, d);
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int r = i + lane; r < w; r += 32) {
+    const double v = Rs[r + w * i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      double* e = Rs + r + w * (cb + nw * j);
+      const double x = fma(-d[j] * b, v, *e);
+      *e = x;
+      const double xt = r > i ? x : 0.0;
+      t[j] = fma(xt, xt, t[j]);
+    }
+  }
+  warp_sums<NC>(t, d);
+  if (lane == 0)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) nrm[cb + nw * j] = d[j];
 }
 
 // Copies an nr x w column-major block (leading dimension ldy) into shared
@@ -429,19 +499,13 @@ __global__ void __launch_bounds__(kThreads, 4) tsqr_level_kernel(char* wsb, int 
       }
       __syncthreads();
       const double b = qb[i];
-      for (int c = i + 1 + wid; c < w; c += nw) {
-        double dot = 0.0;
-        for (int r = i + lane; r < w; r += 32) dot = fma(Rs[r + w * i], Rs[r + w * c], dot);
-        dot = warp_sum(dot) * b;
-        double t = 0.0;
-        for (int r = i + lane; r < w; r += 32) {
-          const double v = fma(-dot, Rs[r + w * i], Rs[r + w * c]);
-          Rs[r + w * c] = v;
-          const double vt = r > i ? v : 0.0;
-          t = fma(vt, vt, t);
+      for (int cb = i + 1 + wid; cb < w; cb += 4 * nw) {
+        switch (min(4, (w - 1 - cb) / nw + 1)) {
+          case 1: cpqr_group<1>(Rs, w, i, cb, nw, b, nrm); break;
+          case 2: cpqr_group<2>(Rs, w, i, cb, nw, b, nrm); break;
+          case 3: cpqr_group<3>(Rs, w, i, cb, nw, b, nrm); break;
+          default: cpqr_group<4>(Rs, w, i, cb, nw, b, nrm); break;
         }
-        t = warp_sum(t);
-        if (lane == 0) nrm[c] = t;
       }
       __syncthreads();
     }
