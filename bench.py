@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision and differentiation forms")
+    ap.add_argument("--no-second", action="store_true", help="skip the paper's second workloads (Table 1 shapes)")
+    ap.add_argument("--second-only", default="",
+                    help="run only these second workloads (comma list of hilbert3,hilbert5,hilbert9,bumps3)")
     ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
@@ -382,6 +385,84 @@ def run_diff(a, dev, P, stream):
     return out
 
 
+SECOND = {
+    # the paper's Hilbert tensor at the three Table 1 shapes with its ranks, and
+    # the Gaussian-bumps tensor of Sec. 4.4 (100 bumps, gamma = 10) at d = 3
+    "hilbert3": dict(kind="hilbert", dims=[960] * 3, ranks=[1, 25, 25, 1]),
+    "hilbert5": dict(kind="hilbert", dims=[96] * 5, ranks=[1, 17, 18, 18, 17, 1]),
+    "hilbert9": dict(kind="hilbert", dims=[12] * 9, ranks=[1, 12, 18, 18, 19, 19, 18, 18, 12, 1]),
+    "bumps3": dict(kind="bumps", dims=[960] * 3, eps=1e-5, rmax=54),
+}
+
+
+def run_second(a, dev, P, stream):
+    """The paper's second workloads (Sec. 4.3-4.4) at full size, FP32 X
+    generated on the device (not timed), BF16 sketches, p = 10: one untimed
+    and one timed pstt2 each, error against X."""
+    import ctypes as C
+    import torch
+    import ttinputs as ti
+    from paper_2111_10448_gb300 import _native as N
+    L = P.lib()
+    out = {}
+    names = a.second_only.split(",") if a.second_only else list(SECOND)
+    for name in names:
+        w = SECOND[name]
+        dims = w["dims"]
+        d = len(dims)
+        ntot = 1
+        for v in dims:
+            ntot *= v
+        r = {"dims": dims, "entries": ntot}
+        try:
+            X = torch.empty(ntot, dtype=torch.float32, device=dev)
+            nn = (C.c_int64 * d)(*dims)
+            sp = C.c_void_p(stream.cuda_stream)
+            if w["kind"] == "hilbert":
+                N.check(L.tt_generate_hilbert(d, nn, 0, dims[-1], C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
+                kw = dict(ranks=w["ranks"])
+            else:
+                import numpy as np
+                c = np.ascontiguousarray(ti.bump_centres(d, 100, seed=4))
+                N.check(L.tt_generate_gaussian_bumps(d, nn, 100, 10.0, c.ctypes.data_as(C.c_void_p), 0, dims[-1],
+                                                     C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
+                kw = dict(eps=w["eps"], rmax=w["rmax"])
+            stream.synchronize()
+            t = P.TTSketch(dims, p=10, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, **kw)
+            t.pstt2(X, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.pstt2(X, stream)
+            e1.record(stream)
+            err = t.error(X, stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            err = err.cpu().numpy()
+            st, ranks = t.status(stream)
+            r.update({"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+                      "hbm_frac_of_measured": ntot * 4 / (ms * 1e-3) / 1e9 / measured_peaks()[0],
+                      "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": ranks, "status": st,
+                      "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()],
+                      "mode": {k: v for k, v in kw.items()}})
+            stream.synchronize()
+            del t
+        except Exception as ex:  # reported in the line, the rest of the bench goes on
+            r["error"] = f"{type(ex).__name__}: {ex}"
+        X = None
+        torch.cuda.empty_cache()
+        out[name] = r
+    return out
+
+
+def run_second_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    print(json.dumps({"second_workloads": run_second(a, dev, P, stream)}), flush=True)
+
+
 def run_precision_only(a):
     import torch
     import paper_2111_10448_gb300 as P
@@ -572,6 +653,8 @@ def run_gpu(a):
     if not a.no_forms:
         out["precision_form"] = run_precision(a, dev, P, stream)
         out["diff_form"] = run_diff(a, dev, P, stream)
+    if not a.no_second:
+        out["second_workloads"] = run_second(a, dev, P, stream)
 
     cpu = None
     if rank == 0 and not a.no_cpu:
@@ -591,7 +674,8 @@ def run_gpu(a):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
                 "batched": out.get("batched"),
-                "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form")}
+                "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form"),
+                "second_workloads": out.get("second_workloads")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -605,6 +689,8 @@ def main():
         run_batched_only(a)
     elif a.precision_only:
         run_precision_only(a)
+    elif a.second_only:
+        run_second_only(a)
     else:
         run_gpu(a)
 

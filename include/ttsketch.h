@@ -285,6 +285,30 @@ tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last,
                                    int64_t count_last, void* out, tt_dtype dtype,
                                    tt_stream_t stream);
 
+/* Synthetic input: the paper's Hilbert tensor 1/(1 - d + i_1 + ... + i_d)
+ * with 1-based indices (Sec. 4.3, the tensor of its memory and timing
+ * experiments, Table 1), for the slab [first_last, first_last + count_last)
+ * of the last mode, written to out (device, dtype): the integer sum is exact,
+ * then one FP64 division, rounded to dtype.  Errors: TT_ERR_INVALID_ARG for
+ * bad sizes or a slab outside n[d-1]. */
+tt_status tt_generate_hilbert(int d, const int64_t* n, int64_t first_last, int64_t count_last,
+                              void* out, tt_dtype dtype, tt_stream_t stream);
+
+/* Synthetic input: the Gaussian-bumps tensor of Sec. 4.4,
+ *   X(i) = sum_{j < nbumps} exp(-gamma sum_k (x_k - c_{j,k})^2),
+ *   x_k = 2 i_k / n_k - 1 (0-based i_k),
+ * evaluated in FP64 as sum_j prod_k exp(-gamma (x_k - c_{j,k})^2) (products
+ * over k in increasing order, sum over j in increasing order) and rounded to
+ * dtype, for the slab [first_last, first_last + count_last) of the last mode.
+ * centres: HOST array of nbumps x d doubles, row j = (c_{j,1} .. c_{j,d}),
+ * copied before the call returns.  Uses stream-ordered scratch for the
+ * per-mode factor tables (sum_k n_k nbumps doubles) and synchronizes the
+ * stream before returning.  Errors: TT_ERR_INVALID_ARG, TT_ERR_CUDA (also when
+ * the scratch cannot be allocated). */
+tt_status tt_generate_gaussian_bumps(int d, const int64_t* n, int nbumps, double gamma,
+                                     const double* centres, int64_t first_last, int64_t count_last,
+                                     void* out, tt_dtype dtype, tt_stream_t stream);
+
 /* Self-test of failure detection (no counterpart in the paper): launches one
  * CTA whose thread waits, with the bounded wait every kernel of this library
  * uses, on an mbarrier that nothing arrives at; after limit_cycles SM clock

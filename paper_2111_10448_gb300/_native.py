@@ -80,6 +80,9 @@ _SIGS = {
     "tt_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64, _P]),
     "tt_generate_hilbert_type": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int64, C.c_int64, _P,
                                            C.c_int, _P]),
+    "tt_generate_hilbert": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int64, C.c_int64, _P, C.c_int, _P]),
+    "tt_generate_gaussian_bumps": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_double, _P,
+                                             C.c_int64, C.c_int64, _P, C.c_int, _P]),
     "tt_kernel_launches": (C.c_int64, []),
     "tt_version": (C.c_char_p, []),
 }

@@ -40,6 +40,70 @@ __global__ void hilbert_type_kernel(Dims D, int64_t first, int64_t count, void* 
   }
 }
 
+// The paper's Hilbert tensor 1 / (1 - d + i_1 + ... + i_d) with 1-based
+// indices (Sec. 4.3), i.e. 1 / (1 + sum of the 0-based indices): an exact
+// integer sum and one FP64 division, rounded to the output dtype.
+__global__ void hilbert_paper_kernel(Dims D, int64_t first, int64_t count, void* out, int f64) {
+  int64_t inner = 1;
+  for (int k = 0; k < D.d - 1; ++k) inner *= D.n[k];
+  const int64_t total = inner * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e, s = 1;
+    for (int k = 0; k < D.d - 1; ++k) {
+      s += rem % D.n[k];
+      rem /= D.n[k];
+    }
+    s += rem + first;
+    const double v = 1.0 / (double)s;
+    if (f64) ((double*)out)[e] = v;
+    else ((float*)out)[e] = (float)v;
+  }
+}
+
+// Gaussian bumps (Sec. 4.4): X(i) = sum_j prod_k E_k[j][i_k] with the factor
+// tables E_k[j][i] = exp(-gamma (x_i - c_{j,k})^2), x_i = 2 i / n_k - 1 (one
+// table entry per mode, bump and index: the exponential of the sum is the
+// product of the exponentials).  Tables: tab + toff[k] + n_k j + i.
+__global__ void bumps_table_kernel(Dims D, int nb, double gamma, const double* centres, const int64_t* toff,
+                                   double* tab) {
+  for (int k = 0; k < D.d; ++k) {
+    const int64_t n = D.n[k];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * nb;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e % n;
+      const int j = (int)(e / n);
+      const double x = 2.0 * (double)i / (double)n - 1.0;
+      const double t = x - centres[(int64_t)j * D.d + k];
+      tab[toff[k] + e] = exp(-gamma * (t * t));
+    }
+  }
+}
+__global__ void bumps_kernel(Dims D, int nb, const int64_t* toff, const double* tab, int64_t first,
+                             int64_t count, void* out, int f64) {
+  int64_t inner = 1;
+  for (int k = 0; k < D.d - 1; ++k) inner *= D.n[k];
+  const int64_t total = inner * count;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t idx[TT_MAXD];
+    int64_t rem = e;
+    for (int k = 0; k < D.d - 1; ++k) {
+      idx[k] = rem % D.n[k];
+      rem /= D.n[k];
+    }
+    idx[D.d - 1] = rem + first;
+    double v = 0.0;
+    for (int j = 0; j < nb; ++j) {
+      double f = 1.0;
+      for (int k = 0; k < D.d; ++k) f *= tab[toff[k] + D.n[k] * j + idx[k]];
+      v += f;
+    }
+    if (f64) ((double*)out)[e] = v;
+    else ((float*)out)[e] = (float)v;
+  }
+}
+
 __global__ void test_matrix_f64_kernel(uint64_t seed, int sid, int64_t row0, int64_t nrows, int ncols,
                                        double* out) {
   const int nq = (ncols + 3) / 4;
@@ -101,6 +165,73 @@ tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last, 
   hilbert_type_kernel<<<grid_for(inner * count_last), 256, 0, (cudaStream_t)stream>>>(
       D, first_last, count_last, out, dtype == TT_F64);
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+tt_status tt_generate_hilbert(int d, const int64_t* n, int64_t first_last, int64_t count_last, void* out,
+                              tt_dtype dtype, tt_stream_t stream) {
+  if (d < 1 || d > TT_MAXD || !n || !out || first_last < 0 || count_last < 0) return TT_ERR_INVALID_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  Dims D;
+  D.d = d;
+  int64_t inner = 1;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1) return TT_ERR_INVALID_ARG;
+    D.n[k] = n[k];
+    if (k < d - 1) inner *= n[k];
+  }
+  if (first_last + count_last > n[d - 1]) return TT_ERR_INVALID_ARG;
+  if (count_last == 0) return TT_OK;
+  count_launch();
+  hilbert_paper_kernel<<<grid_for(inner * count_last), 256, 0, (cudaStream_t)stream>>>(
+      D, first_last, count_last, out, dtype == TT_F64);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+tt_status tt_generate_gaussian_bumps(int d, const int64_t* n, int nbumps, double gamma, const double* centres,
+                                     int64_t first_last, int64_t count_last, void* out, tt_dtype dtype,
+                                     tt_stream_t stream) {
+  if (d < 1 || d > TT_MAXD || !n || !out || !centres || nbumps < 1 || !(gamma >= 0.0) || first_last < 0 ||
+      count_last < 0)
+    return TT_ERR_INVALID_ARG;
+  if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
+  Dims D;
+  D.d = d;
+  int64_t inner = 1, toff[TT_MAXD], tsz = 0;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1) return TT_ERR_INVALID_ARG;
+    D.n[k] = n[k];
+    if (k < d - 1) inner *= n[k];
+    toff[k] = tsz;
+    tsz += n[k] * nbumps;
+  }
+  if (first_last + count_last > n[d - 1]) return TT_ERR_INVALID_ARG;
+  if (count_last == 0) return TT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // scratch: centres, table offsets and the factor tables (stream-ordered, freed on return)
+  const size_t cbytes = sizeof(double) * (size_t)nbumps * d, obytes = sizeof(int64_t) * TT_MAXD;
+  char* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, cbytes + obytes + sizeof(double) * (size_t)tsz, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
+  double* dc = reinterpret_cast<double*>(scratch);
+  int64_t* dto = reinterpret_cast<int64_t*>(scratch + cbytes);
+  double* tab = reinterpret_cast<double*>(scratch + cbytes + obytes);
+  cudaError_t e = cudaMemcpyAsync(dc, centres, cbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dto, toff, sizeof(int64_t) * d, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    count_launch();
+    bumps_table_kernel<<<grid_for(tsz / d + 1), 256, 0, st>>>(D, nbumps, gamma, dc, dto, tab);
+    count_launch();
+    bumps_kernel<<<grid_for(inner * count_last), 256, 0, st>>>(D, nbumps, dto, tab, first_last, count_last, out,
+                                                              dtype == TT_F64);
+    e = cudaGetLastError();
+  }
+  // the host copies read pageable memory: finish them before returning
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFreeAsync(scratch, st);
+  if (e == cudaSuccess) e = e2;
+  return e == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
 tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nrows, int ncols,

@@ -88,12 +88,16 @@ def hilbert_paper(dims, dtype=np.float64):
     return (1.0 / (1.0 - d + s)).astype(dtype)
 
 
+def bump_centres(d, nbumps=100, seed=4):
+    """Centres of the Gaussian bumps: nbumps x d, uniform in (-1, 1)."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(nbumps, d))
+
+
 def gaussian_bumps(dims, nbumps=100, gamma=10.0, seed=4, dtype=np.float64):
     """sum_j exp(-gamma sum_k (x_k - c_{j,k})^2), x_k = 2 i_k / n_k - 1,
     centres uniform in (-1, 1)."""
     dims = [int(n) for n in dims]
-    rng = np.random.default_rng(seed)
-    C = rng.uniform(-1.0, 1.0, size=(nbumps, len(dims)))
+    C = bump_centres(len(dims), nbumps, seed)
     out = np.zeros(_prod(dims))
     for j in range(nbumps):
         f = np.ones(1)
