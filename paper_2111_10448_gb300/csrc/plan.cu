@@ -230,14 +230,17 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     bool ok = (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 && q.n[0] <= 32 &&
               q.n[d - 1] <= 32;
     const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
-    for (int si = it.sk0; si < it.sk0 + it.nsk && ok; ++si)
-      ok = P.sketches[si].width == P.sketches[it.sk0].width && P.sketches[si].width <= 32;
+    // sketch widths may differ (fixed ranks); the tables share the padding of
+    // the widest one, which the small-plane launch uses for every sketch
+    int lmax = 0;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) lmax = std::max(lmax, P.sketches[si].width);
+    ok = ok && lmax <= 32;
     int64_t bytes = 0;
     for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
       DevSketch& s = P.sketches[si];
       s.sp_tab = -1;
       if (!ok) continue;
-      const int64_t lpad = s.width <= 16 ? 16 : 32;
+      const int64_t lpad = lmax <= 16 ? 16 : 32;
       int64_t tb = 0;
       if (s.type == SK_COL && s.wdiv > 1) tb = (it.W / s.wdiv) * q.n[d - 1] * lpad * esz;
       if (s.type == SK_ROW && s.wdiv < it.W) tb = s.wdiv * q.n[0] * lpad * esz;

@@ -69,6 +69,7 @@ struct SpSk {
   int64_t rows, off, wdiv, hstride, tab;  // tab: byte offset of the staged rows, -1: generated per plane
   int col, sid, nslot, slot0, lflush;     // lflush: flushed on the column-side schedule
   int dep;                                // output rows depend on the plane (through kL or kR)
+  int ell;                                // this sketch's width (<= the padded width of the launch)
 };
 
 struct SpArgs {
@@ -76,7 +77,7 @@ struct SpArgs {
   char* wsb;
   uint64_t seed;
   int64_t n1, cnt, first, W, WL, WR, Nd1, tilesL, tilesR, tab0;
-  int nsk, ell, nq, nslots, ldo;
+  int nsk, ell, nq, nslots, ldo;  // ell: the largest sketch width (sets the padding), nq its column quads
   int T2, T3;  // block shape
   SpSk sk[kMaxSk];
 };
@@ -177,7 +178,8 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
   g.tab0 = it.off_sptab * 8;
   g.seed = it.seed;
   g.nsk = it.nsk;
-  g.ell = sks[it.sk0].width;
+  g.ell = 0;
+  for (int s = 0; s < it.nsk; ++s) g.ell = sks[it.sk0 + s].width > g.ell ? sks[it.sk0 + s].width : g.ell;
   g.nq = (g.ell + 3) / 4;
   const int64_t mx = g.n1 > count ? g.n1 : count;
   g.ldo = (int)((mx + 7) / 8 * 8);
@@ -192,6 +194,7 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
     k.tab = d.sp_tab;
     k.col = d.type == SK_COL ? 1 : 0;
     k.sid = d.stream_id;
+    k.ell = d.width;
     const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
     k.dep = per_plane_rows ? 1 : 0;
     k.nslot = per_plane_rows ? (k.col ? g.T2 : g.T3) : 1;
@@ -219,9 +222,9 @@ __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool lon
       const SpSk& s = s_sk[si];
       if ((s.lflush != 0) != long_class) continue;
       const int nout = s.col ? n1 : cnt;
-      const int nrow = s.nslot * g.ell;
+      const int nrow = s.nslot * s.ell;
       for (int rr = warp; rr < nrow; rr += kWarps) {
-        const int sl = rr / g.ell, j = rr - sl * g.ell;
+        const int sl = rr / s.ell, j = rr - sl * s.ell;
         float* p = acc + (size_t)(s.slot0 + sl) * slot_elems + j * g.ldo;
         // kL < WL and kR < WR: 32-bit arithmetic (plan_sp requires W < 2^31)
         int64_t base;
@@ -331,11 +334,11 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                 const int q = qq[h];
                 if constexpr (TF) {
                   *reinterpret_cast<float4*>(Gs + rr[h] * kLD + 4 * q) = make_float4(
-                      4 * q < g.ell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < g.ell ? round_tf32(z[h].y) : 0.f,
-                      4 * q + 2 < g.ell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < g.ell ? round_tf32(z[h].w) : 0.f);
+                      4 * q < s.ell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < s.ell ? round_tf32(z[h].y) : 0.f,
+                      4 * q + 2 < s.ell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < s.ell ? round_tf32(z[h].w) : 0.f);
                 } else {
-                  const uint32_t lo = bf16x2(4 * q < g.ell ? z[h].x : 0.f, 4 * q + 1 < g.ell ? z[h].y : 0.f);
-                  const uint32_t hi = bf16x2(4 * q + 2 < g.ell ? z[h].z : 0.f, 4 * q + 3 < g.ell ? z[h].w : 0.f);
+                  const uint32_t lo = bf16x2(4 * q < s.ell ? z[h].x : 0.f, 4 * q + 1 < s.ell ? z[h].y : 0.f);
+                  const uint32_t hi = bf16x2(4 * q + 2 < s.ell ? z[h].z : 0.f, 4 * q + 3 < s.ell ? z[h].w : 0.f);
                   *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
                 }
               }
@@ -449,7 +452,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
-                if (j < g.ell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
+                if (j < s.ell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
               }
             }
           }
@@ -583,8 +586,9 @@ __global__ void sp_table_batched_kernel(char* wsb) {
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[blockIdx.y];
   const DevSketch* sks = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
-  const int ell = sks[it.sk0].width;
-  const int lpad = ell <= 16 ? 16 : 32;
+  int lmax = 0;
+  for (int si = 0; si < it.nsk; ++si) lmax = sks[it.sk0 + si].width > lmax ? sks[it.sk0 + si].width : lmax;
+  const int lpad = lmax <= 16 ? 16 : 32;
   for (int si = 0; si < it.nsk; ++si) {
     const DevSketch& d = sks[it.sk0 + si];
     if (d.sp_tab < 0) continue;
@@ -594,7 +598,7 @@ __global__ void sp_table_batched_kernel(char* wsb) {
     k.sid = d.stream_id;
     const int nr = k.col ? (int)it.n[it.d - 1] : (int)it.n[0];
     const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
-    sp_table_fill(k, it.seed, 0, it.n[0], nr, ell, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
+    sp_table_fill(k, it.seed, 0, it.n[0], nr, d.width, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
                   (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
                   it.prec == TT_PREC_TF32);
   }
@@ -633,11 +637,10 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, 
   if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_TF32) || it.x_f64 || it.sptab_doubles == 0) return false;
   if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
   const DevSketch* sks = plan_sketches_host(&P);
-  for (int s = 0; s < it.nsk; ++s)
-    if (sks[it.sk0 + s].width != sks[it.sk0].width) return false;
   SpArgs g;
   memset(&g, 0, sizeof(g));
   sp_fill(it, sks, count, g, t3max);
+  if (g.ell > 32) return false;
   const int lpad = g.ell <= 16 ? 16 : 32;
   const size_t tiles = it.prec == TT_PREC_TF32 ? (size_t)Prec<true>::kWarps * Prec<true>::kWarpBytes
                                                : (size_t)Prec<false>::kWarps * Prec<false>::kWarpBytes;
@@ -692,7 +695,7 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
     const int64_t total = nkeys * nr * (lpad / 4);
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count());
     count_launch();
-    sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, g.seed, first, g.n1, nr, g.ell, lpad, nkeys,
+    sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, g.seed, first, g.n1, nr, k.ell, lpad, nkeys,
                                                 g.wsb + g.tab0 + k.tab, tf ? 1 : 0);
   }
   const int64_t nblocks = g.tilesL * g.tilesR;

@@ -308,3 +308,31 @@ def test_small_plane_within_10eps_of_oracle(prec):
     e_or, e_x = rel(xt, OT.tt_full(o["cores"]), x64), rel(xt, x64, x64)
     print(f"small-plane {prec}: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} ranks={t.status()[1]}")
     assert e_or <= 10 * eps and e_x <= 10 * eps
+
+
+@pytest.mark.parametrize("dims,ranks", [
+    ([9, 8, 7, 6, 5, 9], [1, 3, 5, 7, 5, 3, 1]),           # widths 8..12 (padding 16)
+    ([4] * 9, [1, 4, 12, 18, 19, 19, 18, 12, 4, 1]),       # the paper's d = 9 rank profile, clamped: widths 14..29
+])
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_small_plane_unequal_widths_match_oracle(dims, ranks, prec):
+    """Fixed ranks give each sketch its own width l_k = r_k + p; the
+    small-plane kernel pads them all to the widest and writes each sketch's
+    own columns: every sketch entry against the oracle."""
+    d = len(dims)
+    x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
+    kw = dict(ranks=ranks, p=10)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, **kw)
+    assert t.kernel_kind() == 3
+    t.begin()
+    t.accumulate(to_dev(x), 0, dims[-1])
+    sk = sketch_dict(t)
+    t.finalize()
+    widths = {v.shape[1] for v in sk.values()}
+    assert len(widths) > 1
+    xs = _split(x.astype(np.float64), prec)
+    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt=prec, **kw)
+    for k, S in o["sketch"]["S"].items():
+        _close_sketch(sk[(0, k)], S, ("S", k))
+    for k, R in o["sketch"]["R"].items():
+        _close_sketch(sk[(1, k)], R, ("R", k))
