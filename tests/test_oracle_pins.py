@@ -335,3 +335,94 @@ def test_hilbert_type_block_equals_slices_of_the_whole_tensor():
     assert np.array_equal(b, x[2:3, :, [0, 2], :])
     y = ti.hilbert_type(d, first_last=2, count_last=3).reshape((5, 4, 3, 3), order="F")
     assert np.array_equal(y, x[..., 2:5])
+
+
+# ------------------------------------------------- one-sided PSTT-onepass
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_pstt_onepass_exact_recovery(d):
+    """Exact TT ranks within the sketch: X~ = X to 1e-12 (every Q_j spans the
+    column space of X_j, and the last core's least squares is consistent)."""
+    from oracle import pstt as PO
+    dims = [4 + (k % 3) for k in range(d)]
+    r = [1] + [2 + (k % 2) for k in range(d - 1)] + [1]
+    x = ti.random_tt(dims, r, seed=30 + d)
+    o = PO.pstt_onepass(x, dims, ranks=[1] + [4] * (d - 1) + [1], p=3, seed=d + 40)
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_pstt_onepass_d2_closed_form():
+    """d = 2: X~ = Q (Psi^T Q)^+ Psi^T X with Q the first r columns of a
+    pivoted QR (LAPACK) of X Omega -- the one-pass range-finder form of
+    eq. onepass_final_core, computed here without the oracle's code."""
+    from oracle import pstt as PO
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 6)) @ rng.standard_normal((6, 25)) + 1e-3 * rng.standard_normal((30, 25))
+    r, p, seed = 4, 3, 5
+    o = PO.pstt_onepass(A.ravel(order="F"), [30, 25], ranks=[1, r, 1], p=p, seed=seed)
+    Om = philox.test_matrix(seed, 1, 25, r + p)
+    Psi = philox.test_matrix(seed, 64 + 1, 30, r + p)
+    Qs, _, _ = scipy.linalg.qr(A @ Om, pivoting=True, mode="economic")
+    Q = Qs[:, :r]
+    ref = Q @ np.linalg.lstsq(Psi.T @ Q, Psi.T @ A, rcond=None)[0]
+    np.testing.assert_allclose(tt.tt_full(o["cores"]), ref.ravel(order="F"), atol=1e-11)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pstt_onepass_deterministic_bound(seed):
+    """The bound of the one-pass theorem's proof, per run:
+    ||X - X~||^2 <= sum_{j <= d-2} ||(I - Q_j Q_j^T) X_j||^2 + ||Z_{d-1} - X_{d-1}||^2
+    with Z_{d-1} = Q_{d-1} (Psi^T Q_{d-1})^+ Psi^T X_{d-1} (formed here with lstsq)."""
+    from oracle import pstt as PO
+    dims = [5, 6, 4, 5]
+    d = 4
+    x = ti.random_tt(dims, [1, 4, 5, 3, 1], seed=seed, noise=1e-2)
+    o = PO.pstt_onepass(x, dims, ranks=[1, 2, 3, 2, 1], p=3, seed=300 + seed)
+    terms = []
+    for j in range(1, d - 1):
+        Xj = tt.unfold(x, dims, j)
+        Qj = o["Q"][j]
+        terms.append(np.linalg.norm(Xj - Qj @ (Qj.T @ Xj)) ** 2)
+    Xl = tt.unfold(x, dims, d - 1)
+    Ql = o["Q"][d - 1]
+    Z = Ql @ np.linalg.lstsq(o["Psi"].T @ Ql, o["Psi"].T @ Xl, rcond=None)[0]
+    terms.append(np.linalg.norm(Z - Xl) ** 2)
+    err2 = np.linalg.norm(x - tt.tt_full(o["cores"])) ** 2
+    assert err2 <= sum(terms) * (1 + 1e-10)
+
+
+def test_pstt_onepass_expected_error_bound():
+    """The one-pass theorem: E||X - X~||^2 <= sum_{j <= d-2} (1 + r_j/(p-1)) tail_j
+    + (1 + r_{d-1}/(p-1))^2 tail_{d-1}, tail_j = sum_{k > r_j} sigma_k^2(X_j),
+    on a seed average."""
+    from oracle import pstt as PO
+    dims = [6, 5, 6]
+    x = ti.random_tt(dims, [1, 5, 5, 1], seed=3, noise=5e-2)
+    ranks, p = [1, 2, 2, 1], 4
+    rhs = 0.0
+    for k in (1, 2):
+        s = np.linalg.svd(tt.unfold(x, dims, k), compute_uv=False)
+        f = (1 + ranks[k] / (p - 1)) ** (2 if k == 2 else 1)
+        rhs += f * np.sum(s[ranks[k]:] ** 2)
+    errs = [np.linalg.norm(x - tt.tt_full(PO.pstt_onepass(x, dims, ranks=ranks, p=p, seed=s)["cores"])) ** 2
+            for s in range(40)]
+    assert np.mean(errs) <= rhs
+
+
+def test_pstt_onepass_sketches_match_brute_force():
+    """The sketches it uses, entry by entry as sums over the tensor's entries
+    (S_1 and T_{d-1} = Psi_{d-1}^T X_{d-1} at d = 3)."""
+    from oracle import pstt as PO
+    dims = [3, 4, 2]
+    x = ti.random_tt(dims, [1, 2, 2, 1], seed=9)
+    o = PO.pstt_onepass(x, dims, ranks=[1, 2, 2, 1], p=2, seed=4)
+    X = x.reshape(dims, order="F")
+    Om1 = philox.test_matrix(4, 1, 8, 4)
+    Ps2 = philox.test_matrix(4, 64 + 2, 12, 4)
+    for i1 in range(3):
+        for j in range(4):
+            ref = sum(X[i1, i2, i3] * Om1[i2 + 4 * i3, j] for i2 in range(4) for i3 in range(2))
+            assert abs(o["S"][1][i1, j] - ref) <= 1e-12 * (1 + abs(ref))
+    for j in range(4):
+        for i3 in range(2):
+            ref = sum(Ps2[i1 + 3 * i2, j] * X[i1, i2, i3] for i1 in range(3) for i2 in range(4))
+            assert abs(o["T"][j, i3] - ref) <= 1e-12 * (1 + abs(ref))
