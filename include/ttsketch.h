@@ -94,6 +94,15 @@ typedef struct {
 /* Reserve the workspace that tt_reconstruct_backward needs (all left and
  * right interfaces of the train, about 2 r prod(n) / n bytes x 8). */
 #define TT_FLAG_DIFF 1
+/* One-sided PSTT-onepass instead of the two-sided PSTT2-onepass (Algorithm
+ * 2 and the single-pass last core of the paragraph after Theorem 3.3): every
+ * unfolding is sketched from the right, S_k = X_k Omega_k (k = 1..d-1, the
+ * bases Q_k), plus T_{d-1} = Psi_{d-1}^T X_{d-1}; the cores are eq. (3.1) and
+ * G_d = (Psi_{d-1}^T Q_{d-1})^+ T_{d-1}.  Sketch storage grows to
+ * O(l n^{d-1}) (the two-sided form needs O(l n^{ceil(d/2)})).  Requires
+ * passes = 1 and a single-problem plan; not with TT_FLAG_DIFF
+ * (TT_ERR_UNSUPPORTED otherwise). */
+#define TT_FLAG_ONESIDED 2
 
 /* ---------------------------------------------------------------- plans */
 

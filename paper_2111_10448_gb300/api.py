@@ -24,13 +24,16 @@ class TTSketch:
     dims: mode sizes; ranks (fixed-rank mode, [1, r_1, .., r_{d-1}, 1]) or eps
     (> 0, tolerance mode, with rmax); p: oversampling; seed: Philox key;
     passes: 1 (one-pass, the hot path) or 2; x_dtype: torch.float32/float64;
-    prec: 'fp64' | 'tf32' | 'bf16'.
+    prec: 'fp64' | 'tf32' | 'bf16'; one_sided: the one-sided PSTT-onepass
+    (every unfolding sketched from the right, last core by least squares)
+    instead of the two-sided PSTT2-onepass.
     """
 
     PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
 
     def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
-                 x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False):
+                 x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False,
+                 one_sided=False):
         L = N.lib()
         self.device = torch.device(device)
         if batch is None:
@@ -43,7 +46,8 @@ class TTSketch:
                                     rmax=pr.get("rmax", rmax), p=pr.get("p", p),
                                     seed=pr.get("seed", seed), passes=passes,
                                     x_dtype=_DT[x_dtype], prec=self.PRECS[prec],
-                                    flags=N.TT_FLAG_DIFF if diff else 0)
+                                    flags=(N.TT_FLAG_DIFF if diff else 0) |
+                                    (N.TT_FLAG_ONESIDED if one_sided else 0))
         h = C.c_void_p()
         if batch is None:
             N.check(L.tt_sketch_plan(C.byref(arr[0]), C.byref(h)), "tt_sketch_plan")

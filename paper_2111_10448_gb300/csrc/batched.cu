@@ -54,7 +54,7 @@ __global__ void batch_zero_kernel(char* wsb) {
     const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[blockIdx.y - T.nsk];
     if (it.passes != 1) return;
     off = it.off_B;
-    n = (int64_t)it.rpad[it.ds] * it.lmid;
+    n = (int64_t)it.rpad[it.mbk] * it.lmid;
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     ws[off + i] = 0.0;

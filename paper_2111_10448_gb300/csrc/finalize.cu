@@ -630,9 +630,9 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
   __shared__ double Ps[CH * TT_MAXL];
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevItem& it = ditems(wsb)[item];
-  const DevSketch& sp = dsk(wsb)[it.basis_of_k[it.ds]];
+  const DevSketch& sp = dsk(wsb)[it.basis_of_k[it.mbk]];
   double* ws = reinterpret_cast<double*>(wsb);
-  const int r = ranks[it.rank_off + it.ds];
+  const int r = ranks[it.rank_off + it.mbk];
   const int l = it.lmid;
   const int64_t M = sp.rows;
   const double* Pm = ws + sp.lev_z[0];
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
       double z[4];
-      normals4_f64(it.seed, (uint32_t)it.ds, (uint64_t)(v0 + v), (uint32_t)q, z);
+      normals4_f64(it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q, z);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = z[t];
@@ -662,12 +662,12 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
       double acc = 0.0;
       for (int v = 0; v < nv; ++v) acc = fma(Ps[v + CH * c], Gs[v + CH * j], acc);
       if (keep) kept += acc;
-      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
+      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.mbk] * j, acc);
     }
   }
   if (keep && (int)threadIdx.x < r * l) {
     const int c = (int)threadIdx.x % r, j = (int)threadIdx.x / r;
-    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, kept);
+    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.mbk] * j, kept);
   }
 }
 
@@ -679,9 +679,9 @@ __global__ void __launch_bounds__(kThreads) mid_ls_kernel(char* wsb, int item_ar
   __shared__ double beta[TT_MAXL], rdiag[TT_MAXL];
   const DevItem& it = ditems(wsb)[item];
   double* ws = reinterpret_cast<double*>(wsb);
-  const int r = ranks[it.rank_off + it.ds];
+  const int r = ranks[it.rank_off + it.mbk];
   const int l = it.lmid;
-  const int rp = it.rpad[it.ds];
+  const int rp = it.rpad[it.mbk];
   const int lda = l + 1;
   for (int o = threadIdx.x; o < l * r; o += blockDim.x) {
     const int j = o % l, c = o / l;
@@ -746,8 +746,8 @@ __global__ void __launch_bounds__(kThreads) mid_h_kernel(char* wsb, int item_arg
   const DevItem& it = ditems(wsb)[item];
   const DevSketch& sm_ = dsk(wsb)[it.mid_sk];
   double* ws = reinterpret_cast<double*>(wsb);
-  const int r = ranks[it.rank_off + it.ds];
-  const int rp = it.rpad[it.ds];
+  const int r = ranks[it.rank_off + it.mbk];
+  const int rp = it.rpad[it.mbk];
   const int l = it.lmid;
   for (int o = threadIdx.x; o < l * r; o += blockDim.x) Ms[o] = ws[it.off_QB + o];
   __syncthreads();
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
   const DevItem& it = ditems(wsb)[item];
   if (k > it.d) return;
   if (only_k > 0 && k != only_k) return;
-  if (only_k == 0 && k == it.ds && it.passes == 2) return;  // second pass computes it
+  if (only_k == 0 && k == it.mcore && it.passes == 2) return;  // second pass computes it
   const DevSketch* S = dsk(wsb);
   const double* ws = reinterpret_cast<const double*>(wsb);
   const int* rk = ranks + it.rank_off;
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
       A = ws + sa.lev_z[0];
       lda = sa.rows;
     }
-    if (k == it.ds) {
+    if (k == it.mcore) {
       B = ws + it.off_H;
       ldb = it.N[k];
     } else {
@@ -816,9 +816,14 @@ __global__ void __launch_bounds__(kThreads) cores_kernel(char* wsb, double* core
     }
   } else {
     inner = it.N[it.d] / it.N[k];
-    const DevSketch& sa = S[it.basis_of_k[k - 1]];
-    A = ws + sa.lev_z[0];
-    lda = sa.rows;
+    if (k == it.mcore) {  // one-sided last core: G_d(a, i, 0) = H(i, a)
+      A = ws + it.off_H;
+      lda = S[it.mid_sk].rows;
+    } else {
+      const DevSketch& sa = S[it.basis_of_k[k - 1]];
+      A = ws + sa.lev_z[0];
+      lda = sa.rows;
+    }
     if (k < it.d) {
       const DevSketch& sb = S[it.basis_of_k[k]];
       B = ws + sb.lev_z[0];
@@ -929,8 +934,8 @@ cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* rank
   int64_t Mmax = 1, Nmax = 1;
   for (int i = 0; i < nitems; ++i) {
     const DevItem& it = plan_items_host(&P)[i];
-    Mmax = std::max(Mmax, sks[it.basis_of_k[it.ds]].rows);
-    Nmax = std::max(Nmax, it.N[it.ds]);
+    Mmax = std::max(Mmax, sks[it.basis_of_k[it.mbk]].rows);
+    Nmax = std::max(Nmax, sks[it.mid_sk].rows);
   }
   cudaError_t e;
   if (plan_items_host(&P)[0].prec == TT_PREC_FP64) {
@@ -1014,11 +1019,11 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
   for (int i = 0; i < nitems && nitems == 1; ++i) {
     const DevItem& it = plan_items_host(&P)[i];
     if (it.passes != 1) continue;
-    const int rp = it.rpad[it.ds];
+    const int rp = it.rpad[it.mbk];
     e = cudaMemsetAsync((double*)ws + it.off_B, 0, sizeof(double) * rp * it.lmid, st);
     if (e != cudaSuccess) return e;
     if (it.prec == TT_PREC_FP64) {
-      const int64_t M = sks[it.basis_of_k[it.ds]].rows;
+      const int64_t M = sks[it.basis_of_k[it.mbk]].rows;
       const int grid = (int)std::min<int64_t>((M + 31) / 32, 2LL * device_sm_count());
       count_launch();
       mid_b_kernel_f64<<<grid, kThreads, 0, st>>>(wsb, i, ranks);
@@ -1031,8 +1036,8 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     mid_ls_kernel<<<1, kThreads, 0, st>>>(wsb, i, ranks);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t Nm = it.N[it.ds];
-    const int grid = (int)std::min<int64_t>((Nm * it.rpad[it.ds] + kThreads - 1) / kThreads, 8LL * device_sm_count());
+    const int64_t Nm = sks[it.mid_sk].rows;
+    const int grid = (int)std::min<int64_t>((Nm * it.rpad[it.mbk] + kThreads - 1) / kThreads, 8LL * device_sm_count());
     count_launch();
     mid_h_kernel<<<grid, kThreads, 0, st>>>(wsb, i, ranks);
     e = cudaGetLastError();

@@ -66,6 +66,12 @@ struct DevItem {
   int d, ds, passes, prec, x_f64, nsk, eps_mode;
   int sk0;                 // first sketch index in the sketch table
   int mid_sk;              // index of the one-pass middle sketch (-1 in two-pass)
+  // The one-pass least-squares core: B = V^T G (V the basis of bond mbk, G the
+  // test matrix of stream mstream), H = S_mid B^+, and core mcore takes H.
+  // Two-sided: mbk = mcore = ds, mstream = ds (Omega_{d*}), S_mid = S_{d*};
+  // one-sided (sided1): ds = d-1, mbk = d-1, mstream = 64 + d-1 (Psi_{d-1}),
+  // S_mid = T_{d-1}^T, mcore = d.
+  int sided1, mbk, mstream, mcore;
   int basis_of_k[TT_MAXD + 1];  // sketch index of the basis of unfolding k (1..d-1)
   int64_t n[TT_MAXD];
   int64_t N[TT_MAXD + 1];

@@ -91,7 +91,13 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   std::memset(&it, 0, sizeof(it));
   const int d = q.d;
   it.d = d;
-  it.ds = (d + 1) / 2;
+  it.sided1 = (q.flags & TT_FLAG_ONESIDED) ? 1 : 0;
+  if (it.sided1 && (q.passes != 1 || (q.flags & TT_FLAG_DIFF) || !single)) return TT_ERR_UNSUPPORTED;
+  // split: d* = ceil(d/2) (two-sided); one-sided puts every basis on the column side
+  it.ds = it.sided1 ? d - 1 : (d + 1) / 2;
+  it.mbk = it.ds;
+  it.mstream = it.sided1 ? 64 + d - 1 : it.ds;
+  it.mcore = it.sided1 ? d : it.ds;
   it.passes = q.passes;
   it.prec = q.prec;
   it.x_f64 = q.x_dtype == TT_F64;
@@ -123,7 +129,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     }
     if (width[k] > TT_MAXL) return TT_ERR_INVALID_ARG;
   }
-  it.lmid = width[ds];
+  it.lmid = width[it.mbk];
   P.probs.push_back(q);
 
   // sketches
@@ -149,9 +155,14 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     P.sketches.push_back(s);
     return (int)P.sketches.size() - 1;
   };
-  for (int k = 1; k < ds; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
-  if (q.passes == 1) it.mid_sk = add(SK_COL, ds, 0);
-  for (int k = ds; k < d; ++k) it.basis_of_k[k] = add(SK_ROW, k, 1);
+  if (it.sided1) {
+    for (int k = 1; k < d; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
+    it.mid_sk = add(SK_ROW, d - 1, 0);  // T_{d-1}^T = X_{d-1}^T Psi_{d-1}
+  } else {
+    for (int k = 1; k < ds; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
+    if (q.passes == 1) it.mid_sk = add(SK_COL, ds, 0);
+    for (int k = ds; k < d; ++k) it.basis_of_k[k] = add(SK_ROW, k, 1);
+  }
   it.nsk = (int)P.sketches.size() - it.sk0;
 
   // TSQR trees of the basis sketches
@@ -196,11 +207,11 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   rank_top += d + 1;
   // one-pass middle core
   if (q.passes == 1) {
-    const int r = it.rpad[ds];
+    const int r = it.rpad[it.mbk];
     it.off_B = ws.take((int64_t)r * it.lmid);
     it.off_QB = ws.take((int64_t)it.lmid * r);
     it.off_RB = ws.take((int64_t)r * r);
-    it.off_H = ws.take(it.N[ds] * r);
+    it.off_H = ws.take(P.sketches[it.mid_sk].rows * r);
   }
   // Staging area of the BF16 plane kernel: test-matrix blocks whose rows do
   // not depend on the plane (column sketches with wdiv > 1, row sketches with

@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
-  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.ds]];
+  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.mbk]];
   double* ws = reinterpret_cast<double*>(wsb);
-  const int r = ranks[it.rank_off + it.ds];
+  const int r = ranks[it.rank_off + it.mbk];
   const int l = it.lmid;
   const int64_t M = sp.rows;
   const double* Pm = ws + sp.lev_z[0];
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
     const int nq = (l + 3) / 4;
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
-      const float4 z4 = normals4_f32(it.seed, (uint32_t)it.ds, (uint64_t)(v0 + v), (uint32_t)q);
+      const float4 z4 = normals4_f32(it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q);
       const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -73,12 +73,12 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
       double acc = 0.0;
       for (int v = 0; v < nv; ++v) acc = fma(Ps[v + CH * c], Gs[v + CH * j], acc);
       if (keep) kept += acc;
-      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, acc);
+      else atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.mbk] * j, acc);
     }
   }
   if (keep && (int)threadIdx.x < r * l) {
     const int c = (int)threadIdx.x % r, j = (int)threadIdx.x / r;
-    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.ds] * j, kept);
+    atomicAdd(ws + it.off_B + c + (int64_t)it.rpad[it.mbk] * j, kept);
   }
 }
 
@@ -99,7 +99,7 @@ cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks
   int64_t Mmax = 1;
   for (int i = 0; i < plan_num_items(&P); ++i) {
     const DevItem& it = plan_items_host(&P)[i];
-    Mmax = std::max(Mmax, plan_sketches_host(&P)[it.basis_of_k[it.ds]].rows);
+    Mmax = std::max(Mmax, plan_sketches_host(&P)[it.basis_of_k[it.mbk]].rows);
   }
   const unsigned gx = (unsigned)std::min<int64_t>((Mmax + 31) / 32, 64);
   count_launch();
@@ -109,7 +109,7 @@ cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks
 
 cudaError_t launch_mid_b_mixed(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st) {
   const DevItem& it = plan_items_host(&P)[item];
-  const int64_t M = plan_sketches_host(&P)[it.basis_of_k[it.ds]].rows;
+  const int64_t M = plan_sketches_host(&P)[it.basis_of_k[it.mbk]].rows;
   const int grid = (int)std::min<int64_t>((M + 31) / 32, 2LL * device_sm_count());
   count_launch();
   mid_b_kernel_mixed<<<grid, 256, 0, st>>>((char*)ws, item, ranks);
@@ -1501,6 +1501,9 @@ bool use_tc_kernel(const Plan& P, int item, int64_t count) {
     const char* e = getenv("TT_SKETCH_KERNEL");
     force = (e && strcmp(e, "mma") == 0) ? 1 : 0;
   }
+  // the plane kernel is built for the two-sided split (at most two sketches
+  // per side); one-sided plans go to the other kernels
+  if (plan_items_host(&P)[item].sided1) return false;
   tc::TcArgs g;
   return force == 0 && tc::plan_tc(P, item, count, &g);
 }

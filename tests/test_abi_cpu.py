@@ -163,3 +163,30 @@ def test_batched_plan_slices():
     assert offs[1][1] == offs[0][3] + 2 * 6 * 1
     assert ce == offs[2][2] + 2 * 9 * 1
     N.lib().tt_plan_destroy(h)
+
+
+def test_one_sided_plans_refuse_what_they_do_not_support():
+    """TT_FLAG_ONESIDED: one-pass, single-problem plans only (host-side
+    checks, no device needed); the sketch list is every right sketch plus
+    the left sketch of X_{d-1}."""
+    import ctypes as C
+    from paper_2111_10448_gb300 import _native as N
+    L = N.lib()
+    h = C.c_void_p()
+    base = dict(ranks=[1, 2, 3, 2, 1], p=3, seed=1, x_dtype=N.TT_F32, prec=N.TT_PREC_FP64)
+    ok = N.make_problem([6, 5, 4, 7], passes=1, flags=N.TT_FLAG_ONESIDED, **base)
+    assert L.tt_sketch_plan(C.byref(ok), C.byref(h)) == N.TT_OK
+    got = []
+    for i in range(8):
+        ty, k, w = C.c_int(), C.c_int(), C.c_int()
+        rows, off = C.c_int64(), C.c_int64()
+        if L.tt_plan_sketch_info(h, 0, i, C.byref(ty), C.byref(k), C.byref(rows), C.byref(w), C.byref(off)) != 0:
+            break
+        got.append((ty.value, k.value, rows.value, w.value))
+    assert got == [(0, 1, 6, 5), (0, 2, 30, 6), (0, 3, 120, 5), (1, 3, 7, 5)]
+    L.tt_plan_destroy(h)
+    for kw in (dict(passes=2, flags=N.TT_FLAG_ONESIDED), dict(passes=1, flags=N.TT_FLAG_ONESIDED | N.TT_FLAG_DIFF)):
+        bad = N.make_problem([6, 5, 4, 7], **kw, **base)
+        assert L.tt_sketch_plan(C.byref(bad), C.byref(h)) == N.TT_ERR_UNSUPPORTED
+    arr = (N.tt_problem * 2)(ok, ok)
+    assert L.tt_sketch_plan_batched(arr, 2, C.byref(h)) == N.TT_ERR_UNSUPPORTED
