@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-second", action="store_true", help="skip the paper's second workloads (Table 1 shapes)")
     ap.add_argument("--second-only", default="",
                     help="run only these second workloads (comma list of hilbert3,hilbert5,hilbert9,bumps3)")
+    ap.add_argument("--no-onesided", action="store_true", help="skip the one-sided PSTT-onepass sub-line")
+    ap.add_argument("--onesided-only", action="store_true", help="run only the one-sided PSTT-onepass sub-line")
     ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
@@ -458,6 +460,68 @@ def run_second(a, dev, P, stream):
     return out
 
 
+def run_onesided(a, dev, P, stream):
+    """One-sided PSTT-onepass (every unfolding sketched from the right, last
+    core by least squares) against the two-sided PSTT2-onepass on the same X:
+    the precision-form tensor (random TT d=6 n=24, eps 1e-5, rmax 16, p 10)
+    and the streaming Hilbert-type tensor (d=4 n=256, eps 1e-6, rmax 6, p 10);
+    BF16 sketches, one untimed and one timed pstt2 each, errors against X."""
+    import ctypes as C
+    import torch
+    from paper_2111_10448_gb300 import _native as N
+    out = {}
+    cases = [("randomtt_d6_n24", [24] * 6, dict(eps=1e-5, rmax=16, p=10)),
+             ("hilbert_type_d4_n256", [256] * 4, dict(eps=1e-6, rmax=6, p=10))]
+    for name, dims, kw in cases:
+        ntot = 1
+        for v in dims:
+            ntot *= v
+        r = {"dims": dims, "entries": ntot, **{k: v for k, v in kw.items()}}
+        try:
+            if name.startswith("randomtt"):
+                X = device_tt(dims, [1, 10, 10, 10, 10, 10, 1], 0, 1e-6, dev)
+                torch.cuda.synchronize(dev)
+            else:
+                X = torch.empty(ntot, dtype=torch.float32, device=dev)
+                nn = (C.c_int64 * 4)(*dims)
+                N.check(P.lib().tt_generate_hilbert_type(4, nn, 0, dims[-1], C.c_void_p(X.data_ptr()), N.TT_F32,
+                                                         C.c_void_p(stream.cuda_stream)), "gen")
+                stream.synchronize()
+            for label, one in (("one_sided", True), ("two_sided", False)):
+                t = P.TTSketch(dims, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, one_sided=one, **kw)
+                t.pstt2(X, stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t.pstt2(X, stream)
+                e1.record(stream)
+                err = t.error(X, stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                err = err.cpu().numpy()
+                r[label] = {"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+                            "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": t.status(stream)[1],
+                            "sketch_MB": sum(S.numel() for _, _, S in t.sketches(0)) * 8 / 1e6,
+                            "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][
+                                t.kernel_kind()]}
+                stream.synchronize()
+                del t
+        except Exception as ex:  # reported in the line, the rest of the bench goes on
+            r["error"] = f"{type(ex).__name__}: {ex}"
+        X = None
+        torch.cuda.empty_cache()
+        out[name] = r
+    return out
+
+
+def run_onesided_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    print(json.dumps({"one_sided": run_onesided(a, dev, P, stream)}), flush=True)
+
+
 def run_second_only(a):
     import torch
     import paper_2111_10448_gb300 as P
@@ -659,6 +723,8 @@ def run_gpu(a):
         out["diff_form"] = run_diff(a, dev, P, stream)
     if not a.no_second:
         out["second_workloads"] = run_second(a, dev, P, stream)
+    if not a.no_onesided:
+        out["one_sided"] = run_onesided(a, dev, P, stream)
 
     cpu = None
     if rank == 0 and not a.no_cpu:
@@ -679,7 +745,7 @@ def run_gpu(a):
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
                 "batched": out.get("batched"),
                 "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form"),
-                "second_workloads": out.get("second_workloads")}
+                "second_workloads": out.get("second_workloads"), "one_sided": out.get("one_sided")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -695,6 +761,8 @@ def main():
         run_precision_only(a)
     elif a.second_only:
         run_second_only(a)
+    elif a.onesided_only:
+        run_onesided_only(a)
     else:
         run_gpu(a)
 
