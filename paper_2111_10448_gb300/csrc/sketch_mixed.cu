@@ -146,11 +146,6 @@ struct MixArgs {
   SkArgM sk[kMaxSk];
 };
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
-  // two bf16-exact floats -> bf16x2 (first argument in the low half)
-  return (__float_as_uint(lo_k) >> 16) | (__float_as_uint(hi_k) & 0xFFFF0000u);
-}
-
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -167,54 +162,67 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One (m-tile, n-tile) of D^T = G^T X' for the current tile and sketch.
-// Gs: rows x LDG (row = contraction index k, col = j).  Xh/Xl: LDX layout with
-// X'[k][o] = col sketch: X[o + LDX k] ... see callers (getx).
+// One (m-tile, n-tile) of D^T = G^T X' for the current tile and sketch, TF32
+// (m16n8k8) fragments read element by element from the FP32 tiles.
+// Gs: rows x LDG (row = contraction index k, col = j).  X'[k][o] = X(o, k)
+// (column sketch, X[o + LDX k]) or X(k, o) (row sketch, X[k + LDX o]).
 template <bool COL>
-__device__ __forceinline__ void tile_mma(int prec, const float* Gs, int LDG, const float* Xh, const float* Xl,
-                                         int LDX, int kreal, int kext, int m0, int n0, float acc[4]) {
+__device__ __forceinline__ void tile_mma_tf32(const float* Gs, int LDG, const float* Xh, const float* Xl, int LDX,
+                                              int kreal, int kext, int m0, int n0, float acc[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // element accessors: A[j][k] = G[k][j];  B[k][o] = X(o, k) (COL) or X(k, o) (ROW)
   auto Aj = [&](int j, int k) -> float { return (k < kreal) ? Gs[k * LDG + j] : 0.0f; };
   auto Bx = [&](const float* Xs, int k, int o) -> float {
     if (k >= kreal) return 0.0f;
     return COL ? Xs[o + LDX * k] : Xs[k + LDX * o];
   };
-  if (prec == TT_PREC_BF16) {
-    for (int k0 = 0; k0 < kext; k0 += 16) {
-      uint32_t a[4];
-      a[0] = pack_bf16(Aj(m0 + g, k0 + 2 * t), Aj(m0 + g, k0 + 2 * t + 1));
-      a[1] = pack_bf16(Aj(m0 + g + 8, k0 + 2 * t), Aj(m0 + g + 8, k0 + 2 * t + 1));
-      a[2] = pack_bf16(Aj(m0 + g, k0 + 2 * t + 8), Aj(m0 + g, k0 + 2 * t + 9));
-      a[3] = pack_bf16(Aj(m0 + g + 8, k0 + 2 * t + 8), Aj(m0 + g + 8, k0 + 2 * t + 9));
-      const int o = n0 + g;
-      const uint32_t bh0 = pack_bf16(Bx(Xh, k0 + 2 * t, o), Bx(Xh, k0 + 2 * t + 1, o));
-      const uint32_t bh1 = pack_bf16(Bx(Xh, k0 + 2 * t + 8, o), Bx(Xh, k0 + 2 * t + 9, o));
-      const uint32_t bl0 = pack_bf16(Bx(Xl, k0 + 2 * t, o), Bx(Xl, k0 + 2 * t + 1, o));
-      const uint32_t bl1 = pack_bf16(Bx(Xl, k0 + 2 * t + 8, o), Bx(Xl, k0 + 2 * t + 9, o));
-      mma_bf16(acc, a, bh0, bh1);
-      mma_bf16(acc, a, bl0, bl1);
-    }
-  } else {
-    for (int k0 = 0; k0 < kext; k0 += 8) {
-      uint32_t a[4];
-      a[0] = __float_as_uint(Aj(m0 + g, k0 + t));
-      a[1] = __float_as_uint(Aj(m0 + g + 8, k0 + t));
-      a[2] = __float_as_uint(Aj(m0 + g, k0 + t + 4));
-      a[3] = __float_as_uint(Aj(m0 + g + 8, k0 + t + 4));
-      const int o = n0 + g;
-      mma_tf32(acc, a, __float_as_uint(Bx(Xh, k0 + t, o)), __float_as_uint(Bx(Xh, k0 + t + 4, o)));
-      mma_tf32(acc, a, __float_as_uint(Bx(Xl, k0 + t, o)), __float_as_uint(Bx(Xl, k0 + t + 4, o)));
-    }
+  for (int k0 = 0; k0 < kext; k0 += 8) {
+    uint32_t a[4];
+    a[0] = __float_as_uint(Aj(m0 + g, k0 + t));
+    a[1] = __float_as_uint(Aj(m0 + g + 8, k0 + t));
+    a[2] = __float_as_uint(Aj(m0 + g, k0 + t + 4));
+    a[3] = __float_as_uint(Aj(m0 + g + 8, k0 + t + 4));
+    const int o = n0 + g;
+    mma_tf32(acc, a, __float_as_uint(Bx(Xh, k0 + t, o)), __float_as_uint(Bx(Xh, k0 + t + 4, o)));
+    mma_tf32(acc, a, __float_as_uint(Bx(Xl, k0 + t, o)), __float_as_uint(Bx(Xl, k0 + t + 4, o)));
   }
 }
+
+__device__ __forceinline__ uint32_t g_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void g_ldsm_x4_trans(const void* p, uint32_t r[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(g_smem_u32(p)));
+}
+__device__ __forceinline__ void g_ldsm_x2(const void* p, uint32_t r[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(g_smem_u32(p)));
+}
+__device__ __forceinline__ void g_ldsm_x2_trans(const void* p, uint32_t r[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(g_smem_u32(p)));
+}
+
+// BF16 operand tiles (in the same dynamic shared memory as the FP32 ones):
+// X hi / lo as [b][a] (a contiguous) and the test-matrix rows as [k][j] (j
+// contiguous), rows of 72 elements (144 bytes: the eight row addresses of an
+// ldmatrix fall on distinct banks).  The MMA fragments come from ldmatrix:
+// A = G^T from [k][j] transposed, B from [b][a] transposed (column sketches,
+// k = b) or as stored (row sketches, k = a).
+constexpr int gLDX = gTA + 8;
+constexpr int gLDG = TT_MAXL + 8;
 
 // One tile (gTA rows of i_1 x gTB columns of i_d of plane w) into every sketch.
 __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
   constexpr int LDX = gTA + 1;
-  float* Xh = fsm;                  // LDX x gTB  (X[a + LDX b])
+  float* Xh = fsm;                  // LDX x gTB  (X[a + LDX b])        (TF32)
   float* Xl = Xh + LDX * gTB;
-  float* Gs = Xl + LDX * gTB;       // rows (<= gTA) x LDG
+  float* Gs = Xl + LDX * gTB;       // rows (<= gTA) x LDG              (TF32)
+  __nv_bfloat16* XhB = reinterpret_cast<__nv_bfloat16*>(fsm);   // gTB x gLDX (BF16)
+  __nv_bfloat16* XlB = XhB + gLDX * gTB;
+  __nv_bfloat16* GsB = XlB + gLDX * gTB;                        // gTA x gLDG (BF16)
+  const bool bf = a.prec == TT_PREC_BF16;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nA = (a.n1 + gTA - 1) / gTA;
   const int64_t nB = (a.cnt + gTB - 1) / gTB;
@@ -232,8 +240,13 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
       if (ia < ta && ib < tb) v = __ldg(a.X + (a0 + ia) + a.n1 * w + a.Nd1 * (b0 + ib));
       const float hi = round_prec(v, a.prec);
       const float lo = round_prec(__fsub_rn(v, hi), a.prec);
-      Xh[ia + LDX * ib] = hi;
-      Xl[ia + LDX * ib] = lo;
+      if (bf) {
+        XhB[ib * gLDX + ia] = __float2bfloat16_rn(hi);  // exact: hi, lo are BF16 values
+        XlB[ib * gLDX + ia] = __float2bfloat16_rn(lo);
+      } else {
+        Xh[ia + LDX * ib] = hi;
+        Xl[ia + LDX * ib] = lo;
+      }
     }
     for (int s = 0; s < a.nsk; ++s) {
       const SkArgM sk = a.sk[s];
@@ -245,6 +258,7 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
       const int nr = col ? tb : ta;          // contraction extent of this product
       const int nout = col ? ta : tb;        // output extent (N)
       const int nq = lpad / 4;
+      const int kext = bf ? ((nr + 15) & ~15) : ((nr + 7) & ~7);
       __syncthreads();
       for (int o = tid; o < nr * nq; o += gThreads) {
         const int r = o % nr, q = o / nr;
@@ -252,18 +266,49 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
                                   : (uint64_t)((a0 + r) + a.n1 * wlo);
         const float4 z4 = normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
         const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+        if (bf) {
+          float zz[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+          for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+          __nv_bfloat162* gp = reinterpret_cast<__nv_bfloat162*>(GsB + r * gLDG + 4 * q);
+          gp[0] = __floats2bfloat162_rn(zz[0], zz[1]);
+          gp[1] = __floats2bfloat162_rn(zz[2], zz[3]);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+        }
       }
+      if (bf)  // contraction padding rows [nr, kext) (another sketch may have left rows there)
+        for (int o = tid; o < (kext - nr) * (lpad / 2); o += gThreads) {
+          const int r = nr + o / (lpad / 2), c2 = o % (lpad / 2);
+          reinterpret_cast<uint32_t*>(GsB + r * gLDG)[c2] = 0u;
+        }
       __syncthreads();
       const int mt = lpad / 16, nt = (nout + 7) / 8;
       double* out = a.ws + sk.off;
-      const int kext = (a.prec == TT_PREC_BF16) ? ((nr + 15) & ~15) : ((nr + 7) & ~7);
       for (int job = warp; job < mt * nt; job += gThreads / 32) {
         const int m0 = (job % mt) * 16, n0 = (job / mt) * 8;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        if (col) tile_mma<true>(a.prec, Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
-        else tile_mma<false>(a.prec, Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
+        if (bf) {
+          for (int k0 = 0; k0 < kext; k0 += 16) {
+            uint32_t af[4], bh[2], bl[2];
+            g_ldsm_x4_trans(GsB + (k0 + (lane & 7) + 8 * (lane >> 4)) * gLDG + m0 + 8 * ((lane >> 3) & 1), af);
+            if (col) {  // B[k][o] = X(o, k), k = b: the [b][a] tile read transposed
+              const int off = (k0 + (lane & 7) + 8 * ((lane >> 3) & 1)) * gLDX + n0;
+              g_ldsm_x2_trans(XhB + off, bh);
+              g_ldsm_x2_trans(XlB + off, bl);
+            } else {    // B[k][o] = X(k, o), k = a: the [b][a] tile read as stored
+              const int off = (n0 + (lane & 7)) * gLDX + k0 + 8 * ((lane >> 3) & 1);
+              g_ldsm_x2(XhB + off, bh);
+              g_ldsm_x2(XlB + off, bl);
+            }
+            mma_bf16(acc, af, bh[0], bh[1]);
+            mma_bf16(acc, af, bl[0], bl[1]);
+          }
+        } else {
+          if (col) tile_mma_tf32<true>(Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
+          else tile_mma_tf32<false>(Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
+        }
         const int g = lane >> 2, t = lane & 3;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
