@@ -293,6 +293,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
         // into different accumulator slots (less shared-atomic contention)
         const int si = (sj + warp) % g.nsk;
         const SpSk& s = s_sk[si];
+        const int sell = s.ell;  // in a register: the tile stores below may alias s_sk
         const int nr = s.col ? cnt : n1;     // contraction extent
         const int nout = s.col ? n1 : cnt;   // output extent
         const int kext = TF ? (nr + 7) & ~7 : (nr + 15) & ~15;
@@ -334,11 +335,11 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                 const int q = qq[h];
                 if constexpr (TF) {
                   *reinterpret_cast<float4*>(Gs + rr[h] * kLD + 4 * q) = make_float4(
-                      4 * q < s.ell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < s.ell ? round_tf32(z[h].y) : 0.f,
-                      4 * q + 2 < s.ell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < s.ell ? round_tf32(z[h].w) : 0.f);
+                      4 * q < sell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < sell ? round_tf32(z[h].y) : 0.f,
+                      4 * q + 2 < sell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < sell ? round_tf32(z[h].w) : 0.f);
                 } else {
-                  const uint32_t lo = bf16x2(4 * q < s.ell ? z[h].x : 0.f, 4 * q + 1 < s.ell ? z[h].y : 0.f);
-                  const uint32_t hi = bf16x2(4 * q + 2 < s.ell ? z[h].z : 0.f, 4 * q + 3 < s.ell ? z[h].w : 0.f);
+                  const uint32_t lo = bf16x2(4 * q < sell ? z[h].x : 0.f, 4 * q + 1 < sell ? z[h].y : 0.f);
+                  const uint32_t hi = bf16x2(4 * q + 2 < sell ? z[h].z : 0.f, 4 * q + 3 < sell ? z[h].w : 0.f);
                   *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
                 }
               }
@@ -452,7 +453,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
-                if (j < s.ell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
+                if (j < sell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
               }
             }
           }
