@@ -1,4 +1,4 @@
-"""One-sided PSTT-onepass of the oracle (plain NumPy, FP64).
+"""One-sided PSTT and PSTT-onepass of the oracle (plain NumPy, FP64).
 
 TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
@@ -23,6 +23,19 @@ from . import philox
 from .linalg import householder_cpqr, lstsq_right
 from .pstt2 import clamp_ranks, pick_rank_eps, sketch_widths
 from .tt import prods, unfold
+
+
+def pstt(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64'):
+    """PSTT (Algorithm 2, two passes): the bases and cores 1..d-1 of
+    pstt_onepass, and the last core G_d = Q_{d-1}^T X_{d-1} from a second
+    pass over X."""
+    o = pstt_onepass(x, dims, ranks=ranks, eps=eps, rmax=rmax, p=p, seed=seed, test_fmt=test_fmt)
+    dims = [int(n) for n in dims]
+    d = len(dims)
+    r = o['r']
+    G = o['Q'][d - 1].T @ unfold(x, dims, d - 1)           # r_{d-1} x n_d
+    o['cores'][d - 1] = G.reshape((r[d - 1], dims[d - 1], 1), order='F')
+    return o
 
 
 def pstt_onepass(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64'):

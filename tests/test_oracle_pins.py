@@ -426,3 +426,42 @@ def test_pstt_onepass_sketches_match_brute_force():
         for i3 in range(2):
             ref = sum(Ps2[i1 + 3 * i2, j] * X[i1, i2, i3] for i1 in range(3) for i2 in range(4))
             assert abs(o["T"][j, i3] - ref) <= 1e-12 * (1 + abs(ref))
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_pstt_twopass_exact_recovery(d):
+    from oracle import pstt as PO
+    dims = [4 + (k % 3) for k in range(d)]
+    r = [1] + [2 + (k % 2) for k in range(d - 1)] + [1]
+    x = ti.random_tt(dims, r, seed=50 + d)
+    o = PO.pstt(x, dims, ranks=[1] + [4] * (d - 1) + [1], p=3, seed=d + 60)
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pstt_twopass_deterministic_bound_eq_proj_acc(seed):
+    """Algorithm 2 has Q_j with ON columns for every j, so eq. (proj_acc)
+    bounds its error by the projection tails, per run."""
+    from oracle import pstt as PO
+    dims = [5, 6, 4, 5]
+    x = ti.random_tt(dims, [1, 4, 5, 3, 1], seed=seed, noise=1e-2)
+    o = PO.pstt(x, dims, ranks=[1, 2, 3, 2, 1], p=2, seed=400 + seed)
+    terms = [np.linalg.norm(tt.unfold(x, dims, j) - o["Q"][j] @ (o["Q"][j].T @ tt.unfold(x, dims, j))) ** 2
+             for j in range(1, 4)]
+    err2 = np.linalg.norm(x - tt.tt_full(o["cores"])) ** 2
+    assert err2 <= sum(terms) * (1 + 1e-10)
+
+
+def test_pstt_twopass_expected_error_bound():
+    """Theorem 3.3, eq. (sketch_bound), for Algorithm 2 on a seed average."""
+    from oracle import pstt as PO
+    dims = [6, 5, 6]
+    x = ti.random_tt(dims, [1, 5, 5, 1], seed=3, noise=5e-2)
+    ranks, p = [1, 2, 2, 1], 3
+    rhs = 0.0
+    for k in (1, 2):
+        s = np.linalg.svd(tt.unfold(x, dims, k), compute_uv=False)
+        rhs += (1 + ranks[k] / (p - 1)) * np.sum(s[ranks[k]:] ** 2)
+    errs = [np.linalg.norm(x - tt.tt_full(PO.pstt(x, dims, ranks=ranks, p=p, seed=s)["cores"])) ** 2
+            for s in range(40)]
+    assert np.mean(errs) <= rhs
