@@ -462,7 +462,8 @@ def run_second(a, dev, P, stream):
 
 def run_onesided(a, dev, P, stream):
     """One-sided PSTT-onepass (every unfolding sketched from the right, last
-    core by least squares) against the two-sided PSTT2-onepass on the same X:
+    core by least squares) and two-pass PSTT (last core Q^T X_{d-1} from a
+    second pass) against the two-sided PSTT2-onepass on the same X:
     the precision-form tensor (random TT d=6 n=24, eps 1e-5, rmax 16, p 10)
     and the streaming Hilbert-type tensor (d=4 n=256, eps 1e-6, rmax 6, p 10);
     BF16 sketches, one untimed and one timed pstt2 each, errors against X."""
@@ -487,8 +488,9 @@ def run_onesided(a, dev, P, stream):
                 N.check(P.lib().tt_generate_hilbert_type(4, nn, 0, dims[-1], C.c_void_p(X.data_ptr()), N.TT_F32,
                                                          C.c_void_p(stream.cuda_stream)), "gen")
                 stream.synchronize()
-            for label, one in (("one_sided", True), ("two_sided", False)):
-                t = P.TTSketch(dims, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, one_sided=one, **kw)
+            for label, one, passes in (("one_sided", True, 1), ("one_sided_twopass", True, 2), ("two_sided", False, 1)):
+                t = P.TTSketch(dims, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, one_sided=one,
+                               passes=passes, **kw)
                 t.pstt2(X, stream)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)

@@ -98,10 +98,11 @@ typedef struct {
  * 2 and the single-pass last core of the paragraph after Theorem 3.3): every
  * unfolding is sketched from the right, S_k = X_k Omega_k (k = 1..d-1, the
  * bases Q_k), plus T_{d-1} = Psi_{d-1}^T X_{d-1}; the cores are eq. (3.1) and
- * G_d = (Psi_{d-1}^T Q_{d-1})^+ T_{d-1}.  Sketch storage grows to
- * O(l n^{d-1}) (the two-sided form needs O(l n^{ceil(d/2)})).  Requires
- * passes = 1 and a single-problem plan; not with TT_FLAG_DIFF
- * (TT_ERR_UNSUPPORTED otherwise). */
+ * G_d = (Psi_{d-1}^T Q_{d-1})^+ T_{d-1}.  With passes = 2 it is Algorithm 2
+ * itself: no T_{d-1}, and G_d = Q_{d-1}^T X_{d-1} from a second pass over X
+ * (tt_pstt2 only, as for the two-sided two-pass core).  Sketch storage grows
+ * to O(l n^{d-1}) (the two-sided form needs O(l n^{ceil(d/2)})).  Requires a
+ * single-problem plan; not with TT_FLAG_DIFF (TT_ERR_UNSUPPORTED otherwise). */
 #define TT_FLAG_ONESIDED 2
 
 /* ---------------------------------------------------------------- plans */

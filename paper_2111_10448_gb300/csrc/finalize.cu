@@ -922,6 +922,44 @@ __global__ void __launch_bounds__(kThreads) twopass_mid_kernel(char* wsb, const 
   }
 }
 
+// One-sided two-pass last core (Algorithm 2): G_d(a, i, 0) = sum_u
+// Q_{d-1}(u, a) X(u + N_{d-1} i).  Block (i, row chunk): the threads stride
+// over the chunk's rows (coalesced in X and in each column of Q), eight
+// columns a at a time with unconditional FMAs (columns past r_{d-1} read
+// column r_{d-1} - 1 and are dropped), then a block sum and one atomic per a.
+__global__ void __launch_bounds__(kThreads) twopass_last_kernel(char* wsb, const void* X, double* cores,
+                                                                const int* ranks, int64_t chunk) {
+  __shared__ double red[32];
+  const DevItem& it = ditems(wsb)[0];
+  const DevSketch& sq = dsk(wsb)[it.basis_of_k[it.d - 1]];
+  const double* ws = reinterpret_cast<const double*>(wsb);
+  const double* Q = ws + sq.lev_z[0];
+  const int64_t ldq = sq.rows;
+  const int ra = ranks[it.rank_off + it.d - 1];
+  const int rpa = it.rpad[it.d - 1];
+  const int64_t Np = it.N[it.d - 1];
+  const int64_t i = blockIdx.x;
+  const int64_t u0 = (int64_t)blockIdx.y * chunk, u1 = imin64(Np, u0 + chunk);
+  double* G = cores + it.core_off[it.d];
+  for (int a0 = 0; a0 < ra; a0 += 8) {
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const double* qc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) qc[j] = Q + ldq * min(a0 + j, ra - 1);
+    for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+      const int64_t e = u + Np * i;
+      const double x = it.x_f64 ? reinterpret_cast<const double*>(X)[e] : (double)reinterpret_cast<const float*>(X)[e];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = fma(qc[j][u], x, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const double t = block_sum(acc[j], red);
+      if (threadIdx.x == 0 && a0 + j < ra) atomicAdd(G + (a0 + j) + (int64_t)rpa * i, t);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_mid_b_mixed(const Plan& P, int item, void* ws, const int* ranks, cudaStream_t st);
@@ -1073,6 +1111,16 @@ namespace tts {
 cudaError_t launch_twopass_mid(const Plan& P, const void* X, void* ws, double* cores, const int* ranks,
                                cudaStream_t st) {
   const DevItem& it = plan_items_host(&P)[0];
+  if (it.sided1) {  // the last core G_d = Q_{d-1}^T X_{d-1}
+    const int d = it.d;
+    cudaError_t e = cudaMemsetAsync(cores + it.core_off[d], 0, sizeof(double) * it.rpad[d - 1] * it.n[d - 1], st);
+    if (e != cudaSuccess) return e;
+    const int64_t Np = it.N[d - 1], chunk = 65536;
+    const dim3 grid((unsigned)it.n[d - 1], (unsigned)((Np + chunk - 1) / chunk));
+    count_launch();
+    twopass_last_kernel<<<grid, kThreads, 0, st>>>((char*)ws, X, cores, ranks, chunk);
+    return cudaGetLastError();
+  }
   const int ds = it.ds;
   cudaError_t e = cudaMemsetAsync(cores + it.core_off[ds], 0,
                                   sizeof(double) * it.rpad[ds - 1] * it.n[ds - 1] * it.rpad[ds], st);

@@ -92,7 +92,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   const int d = q.d;
   it.d = d;
   it.sided1 = (q.flags & TT_FLAG_ONESIDED) ? 1 : 0;
-  if (it.sided1 && (q.passes != 1 || (q.flags & TT_FLAG_DIFF) || !single)) return TT_ERR_UNSUPPORTED;
+  if (it.sided1 && ((q.flags & TT_FLAG_DIFF) || !single)) return TT_ERR_UNSUPPORTED;
   // split: d* = ceil(d/2) (two-sided); one-sided puts every basis on the column side
   it.ds = it.sided1 ? d - 1 : (d + 1) / 2;
   it.mbk = it.ds;
@@ -157,7 +157,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   };
   if (it.sided1) {
     for (int k = 1; k < d; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
-    it.mid_sk = add(SK_ROW, d - 1, 0);  // T_{d-1}^T = X_{d-1}^T Psi_{d-1}
+    if (q.passes == 1) it.mid_sk = add(SK_ROW, d - 1, 0);  // T_{d-1}^T = X_{d-1}^T Psi_{d-1}
   } else {
     for (int k = 1; k < ds; ++k) it.basis_of_k[k] = add(SK_COL, k, 1);
     if (q.passes == 1) it.mid_sk = add(SK_COL, ds, 0);

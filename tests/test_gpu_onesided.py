@@ -79,3 +79,25 @@ def test_mixed_within_10eps_of_oracle(prec):
     e_or, e_x = rel(xt, OT.tt_full(o["cores"]), x64), rel(xt, x64, x64)
     print(f"one-sided {prec}: |X~-X~oracle|={e_or:.2e} |X~-X|={e_x:.2e} ranks={t.status()[1]} / {o['r']}")
     assert e_or <= 10 * eps and e_x <= 10 * eps
+
+
+@pytest.mark.parametrize("dims,kw", [
+    ([30, 25], dict(ranks=[1, 4, 1], p=3)),
+    ([6, 5, 4, 7], dict(ranks=[1, 2, 3, 2, 1], p=3)),
+    ([8, 7, 6, 5, 9], dict(eps=1e-6, rmax=8, p=4)),
+    ([40, 36, 50], dict(ranks=[1, 5, 6, 1], p=5)),
+])
+@pytest.mark.parametrize("xdt", [torch.float64, torch.float32])
+def test_twopass_fp64_matches_oracle(dims, kw, xdt):
+    """Algorithm 2 proper (one-sided, two passes): the last core from a second
+    pass over X, G_d = Q_{d-1}^T X_{d-1}; FP64 within 1e-10 of the oracle."""
+    d = len(dims)
+    x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=13, noise=1e-6)
+    if xdt == torch.float32:
+        x = x.astype(np.float32).astype(np.float64)
+    t = TTSketch(dims, seed=5, x_dtype=xdt, prec="fp64", one_sided=True, passes=2, **kw)
+    t.pstt2(to_dev(x, xdt))
+    o = PO.pstt(x, dims, seed=5, **kw)
+    assert t.status()[1] == o["r"]
+    got = OT.tt_full(t.core_list(0))
+    assert np.linalg.norm(got - OT.tt_full(o["cores"])) <= 1e-10 * np.linalg.norm(x)
