@@ -465,3 +465,61 @@ def test_pstt_twopass_expected_error_bound():
     errs = [np.linalg.norm(x - tt.tt_full(PO.pstt(x, dims, ranks=ranks, p=p, seed=s)["cores"])) ** 2
             for s in range(40)]
     assert np.mean(errs) <= rhs
+
+
+# ------------------------------------------------------------- Tucker2TT
+def _tucker_tensor(s, n, tt_ranks, seed):
+    rng = np.random.default_rng(seed)
+    G = ti.random_tt(s, tt_ranks, seed=seed)
+    A = [np.linalg.qr(rng.standard_normal((nk, sk)))[0] for nk, sk in zip(n, s)]
+    X = G.reshape(s, order="F")
+    for k, Ak in enumerate(A):  # dense mode-k products, written independently of the oracle
+        X = np.moveaxis(np.tensordot(Ak, X, axes=([1], [k])), 0, k)
+    return G, A, X.reshape(-1, order="F")
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_tucker2tt_exact_for_exact_core_ranks(passes):
+    """Algorithm 3: a Tucker tensor whose core has exact TT ranks within the
+    sketch is reproduced to 1e-12 without forming X."""
+    from oracle import tucker as TU
+    s, n = [4, 5, 3, 4], [9, 7, 8, 6]
+    G, A, X = _tucker_tensor(s, n, [1, 2, 3, 2, 1], seed=21)
+    cores, o = TU.tucker2tt(G, A, ranks=[1, 3, 3, 3, 1], p=3, seed=7, passes=passes)
+    assert [c.shape[1] for c in cores] == n
+    assert np.linalg.norm(tt.tt_full(cores) - X) <= 1e-12 * np.linalg.norm(X)
+
+
+def test_tucker2tt_ranks_lemma_and_error_equality():
+    """The lemma after Algorithm 3 (rank X_j = rank G_j for ON factors), and
+    ||X - X~|| = ||G - G~|| (the factors are isometries)."""
+    from oracle import tucker as TU
+    s, n = [5, 4, 6], [9, 8, 10]
+    G, A, X = _tucker_tensor(s, n, [1, 4, 3, 1], seed=22)
+    G = G + 1e-3 * np.random.default_rng(3).standard_normal(G.size)
+    Xn = G.reshape(s, order="F")
+    for k, Ak in enumerate(A):
+        Xn = np.moveaxis(np.tensordot(Ak, Xn, axes=([1], [k])), 0, k)
+    X = Xn.reshape(-1, order="F")
+    for j in (1, 2):
+        assert np.linalg.matrix_rank(tt.unfold(X, n, j), tol=1e-10) == \
+            np.linalg.matrix_rank(tt.unfold(G, s, j), tol=1e-10)
+    cores, o = TU.tucker2tt(G, A, ranks=[1, 2, 2, 1], p=3, seed=8)
+    eX = np.linalg.norm(tt.tt_full(cores) - X)
+    eG = np.linalg.norm(tt.tt_full(o["cores"]) - G)
+    assert abs(eX - eG) <= 1e-12 * np.linalg.norm(X)
+
+
+def test_mode2_product_matches_dense_mode_product():
+    """T_j = H_j x_2 A_j: contracting the new train equals the dense mode-j
+    products of the core train's full tensor."""
+    from oracle import tucker as TU
+    rng = np.random.default_rng(5)
+    s, n, r = [3, 4, 2], [5, 6, 7], [1, 2, 3, 1]
+    H = [rng.standard_normal((r[k], s[k], r[k + 1])) for k in range(3)]
+    A = [rng.standard_normal((n[k], s[k])) for k in range(3)]
+    Xg = tt.tt_full(H).reshape(s, order="F")
+    for k, Ak in enumerate(A):
+        Xg = np.moveaxis(np.tensordot(Ak, Xg, axes=([1], [k])), 0, k)
+    got = tt.tt_full([TU.mode2(Hk, Ak) for Hk, Ak in zip(H, A)])
+    np.testing.assert_allclose(got, Xg.reshape(-1, order="F"), rtol=0, atol=1e-12)
