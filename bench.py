@@ -53,6 +53,8 @@ def parse():
                     help="run only these second workloads (comma list of hilbert3,hilbert5,hilbert9,bumps3)")
     ap.add_argument("--no-onesided", action="store_true", help="skip the one-sided PSTT-onepass sub-line")
     ap.add_argument("--onesided-only", action="store_true", help="run only the one-sided PSTT-onepass sub-line")
+    ap.add_argument("--no-tucker", action="store_true", help="skip the Tucker2TT sub-line")
+    ap.add_argument("--tucker-only", action="store_true", help="run only the Tucker2TT sub-line")
     ap.add_argument("--batch", type=int, default=512, help="tensors in the batched workload")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
@@ -515,6 +517,51 @@ def run_onesided(a, dev, P, stream):
     return out
 
 
+def run_tucker(a, dev, P, stream):
+    """Tucker2TT (Algorithm 3) of X = G x_1 A_1 ... x_4 A_4 with a 64^4 FP64
+    Tucker core G (random TT, ranks 8, + 1e-6 noise) and orthonormal 256 x 64
+    factors: X (256^4) is never formed.  FP64, eps 1e-6, rmax 12, p 10; one
+    untimed and one timed call; the error ||G - G~|| / ||G|| equals ||X - X~|| /
+    ||X|| since the factors are isometries."""
+    import torch
+    s, n = [64] * 4, 256
+    G = device_tt(s, [1, 8, 8, 8, 1], 0, 1e-6, dev).double()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    A = [torch.linalg.qr(torch.randn(n, s[k], dtype=torch.float64, device=dev, generator=gen))[0] for k in range(4)]
+    torch.cuda.synchronize(dev)
+    kw = dict(eps=1e-6, rmax=12, p=10, seed=1)
+    out = {"workload": "Tucker core 64^4 FP64 (random TT ranks 8 + 1e-6 noise), factors 256 x 64 orthonormal: "
+                       "X = 256^4 never formed; eps=1e-6 rmax=12 p=10, FP64"}
+    try:
+        P.tucker2tt(G, A, prec="fp64", stream=stream, **kw)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cores, t = P.tucker2tt(G, A, prec="fp64", stream=stream, **kw)
+        e1.record(stream)
+        err = t.error(G, stream)
+        stream.synchronize()
+        err = err.cpu().numpy()
+        out.update({"ms": e0.elapsed_time(e1), "rel_err_vs_X": float((err[0] / err[1]) ** 0.5),
+                    "ranks": t.status(stream)[1], "x_entries_not_formed": n ** 4, "core_entries": G.numel(),
+                    "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()]})
+        stream.synchronize()
+        del t, cores
+    except Exception as ex:  # reported in the line, the rest of the bench goes on
+        out["error"] = f"{type(ex).__name__}: {ex}"
+    return out
+
+
+def run_tucker_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    print(json.dumps({"tucker2tt": run_tucker(a, dev, P, stream)}), flush=True)
+
+
 def run_onesided_only(a):
     import torch
     import paper_2111_10448_gb300 as P
@@ -727,6 +774,8 @@ def run_gpu(a):
         out["second_workloads"] = run_second(a, dev, P, stream)
     if not a.no_onesided:
         out["one_sided"] = run_onesided(a, dev, P, stream)
+    if not a.no_tucker:
+        out["tucker2tt"] = run_tucker(a, dev, P, stream)
 
     cpu = None
     if rank == 0 and not a.no_cpu:
@@ -747,7 +796,8 @@ def run_gpu(a):
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
                 "batched": out.get("batched"),
                 "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form"),
-                "second_workloads": out.get("second_workloads"), "one_sided": out.get("one_sided")}
+                "second_workloads": out.get("second_workloads"), "one_sided": out.get("one_sided"),
+                "tucker2tt": out.get("tucker2tt")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -765,6 +815,8 @@ def main():
         run_second_only(a)
     elif a.onesided_only:
         run_onesided_only(a)
+    elif a.tucker_only:
+        run_tucker_only(a)
     else:
         run_gpu(a)
 

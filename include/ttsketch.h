@@ -319,6 +319,16 @@ tt_status tt_generate_gaussian_bumps(int d, const int64_t* n, int nbumps, double
                                      const double* centres, int64_t first_last, int64_t count_last,
                                      void* out, tt_dtype dtype, tt_stream_t stream);
 
+/* Tucker2TT (Algorithm 3), second step: T = H x_2 A for one TT core.  H: the
+ * core (r0 x s x r1, column-major, device FP64), e.g. a core of the train that
+ * tt_pstt2 computed for a Tucker core tensor; A: the Tucker factor of that mode
+ * (n x s, column-major, device FP64); T: output r0 x n x r1 (column-major,
+ * device FP64), T(a, i, c) = sum_k A(i, k) H(a, k, c).  Zero rows of padded
+ * ranks stay zero.  Asynchronous on stream.  Errors: TT_ERR_INVALID_ARG for
+ * null pointers or sizes < 1, TT_ERR_CUDA. */
+tt_status tt_core_mode2(const double* H, int r0, int64_t s, int r1, const double* A, int64_t n,
+                        double* T, tt_stream_t stream);
+
 /* Self-test of failure detection (no counterpart in the paper): launches one
  * CTA whose thread waits, with the bounded wait every kernel of this library
  * uses, on an mbarrier that nothing arrives at; after limit_cycles SM clock

@@ -247,3 +247,28 @@ def tt_entries_from_cores(cores, idx):
             v = v @ G[:, int(i), :]
         out[m] = v[0]
     return out
+
+
+def tucker2tt(G, factors, *, prec="fp64", stream=None, **kw):
+    """Tucker2TT (Algorithm 3): TT cores of X = G x_1 A_1 ... x_d A_d without
+    forming X.  G: the Tucker core on the device (column-major flat, dims
+    [A.shape[1] for A in factors]); factors: device tensors A_k of shape
+    (n_k, s_k) with orthonormal columns; kw: the TTSketch arguments of the
+    decomposition of G (ranks or eps/rmax, p, seed, passes, ...).  Returns
+    (cores, sketch): cores[k] is a device float64 tensor of shape
+    (rpad_{k-1}, n_k, rpad_k) (column-major; rows and columns past the ranks
+    are zero), sketch the TTSketch of G (ranks: sketch.status()[1])."""
+    s = [int(A.shape[1]) for A in factors]
+    t = TTSketch(s, x_dtype=G.dtype, prec=prec, device=G.device, **kw).pstt2(G, stream)
+    it = t.items[0]
+    out = []
+    for k, A in enumerate(factors, start=1):
+        n = int(A.shape[0])
+        rp0, rp1 = it["rpad"][k - 1], it["rpad"][k]
+        Acm = A.to(torch.float64).t().contiguous()  # column-major n x s
+        H = t.cores[it["core_off"][k]:it["core_off"][k] + rp0 * s[k - 1] * rp1]
+        T = torch.empty(rp0 * n * rp1, dtype=torch.float64, device=G.device)
+        N.check(N.lib().tt_core_mode2(_ptr(H), rp0, s[k - 1], rp1, _ptr(Acm), n, _ptr(T), _stream(stream)),
+                "tt_core_mode2")
+        out.append(T.view(rp1, n, rp0).permute(2, 1, 0))
+    return out, t
