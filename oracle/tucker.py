@@ -25,3 +25,29 @@ def tucker2tt(G, factors, **pstt2_kw):
     dims = [int(A.shape[1]) for A in factors]
     o = pstt2(np.asarray(G), dims, **pstt2_kw)
     return [mode2(H, A) for H, A in zip(o['cores'], factors)], o
+
+
+def unfold2(core):
+    """The mode-2 matricization of a TT core: M(i, a + r0 c) = T(a, i, c)."""
+    r0, n, r1 = core.shape
+    return np.transpose(core, (1, 0, 2)).reshape((n, r0 * r1), order='F')
+
+
+def tt2tucker(cores, tranks, *, p=5, seed=1):
+    """TT2Tucker (Algorithm 4) with the basis of step 2 from sketching: for
+    core k, A_k = Q_1 and H_k = Q_1^T (T_k)_(2) (folded back to r_{k-1} x t_k x
+    r_k) of the one-sided two-pass PSTT (Algorithm 2, d = 2) of the matrix
+    (T_k)_(2) with target rank t_k and test-matrix key seed + k.  Returns
+    (H cores, factors A)."""
+    from .pstt import pstt
+    Hs, As = [], []
+    for k, T in enumerate(cores, start=1):
+        r0, n, r1 = T.shape
+        M = unfold2(T)
+        t = min(int(tranks[k - 1]), n, r0 * r1)
+        o = pstt(M.reshape(-1, order='F'), [n, r0 * r1], ranks=[1, t, 1], p=p, seed=seed + k)
+        A = o['cores'][0].reshape((n, -1), order='F')          # n x t
+        H2 = o['cores'][1].reshape((A.shape[1], r0 * r1), order='F')
+        Hs.append(np.transpose(H2.reshape((A.shape[1], r0, r1), order='F'), (1, 0, 2)))
+        As.append(A)
+    return Hs, As

@@ -523,3 +523,43 @@ def test_mode2_product_matches_dense_mode_product():
         Xg = np.moveaxis(np.tensordot(Ak, Xg, axes=([1], [k])), 0, k)
     got = tt.tt_full([TU.mode2(Hk, Ak) for Hk, Ak in zip(H, A)])
     np.testing.assert_allclose(got, Xg.reshape(-1, order="F"), rtol=0, atol=1e-12)
+
+
+def test_tt2tucker_exact_and_orthonormal():
+    """Algorithm 4 with t_k >= rank (T_k)_(2): the Tucker format reproduces the
+    TT tensor to 1e-12 (X = TT(H) x_1 A_1 ... x_d A_d, formed with dense mode
+    products), every A_k has orthonormal columns, H_k = T_k x_2 A_k^T."""
+    from oracle import tucker as TU
+    rng = np.random.default_rng(11)
+    n, r = [9, 8, 10, 7], [1, 2, 3, 2, 1]
+    T = [rng.standard_normal((r[k], n[k], r[k + 1])) for k in range(4)]
+    Hs, As = TU.tt2tucker(T, [r[k] * r[k + 1] for k in range(4)], p=3, seed=5)
+    X = tt.tt_full(T)
+    Xt = tt.tt_full(Hs).reshape([A.shape[1] for A in As], order="F")
+    for k, A in enumerate(As):
+        np.testing.assert_allclose(A.T @ A, np.eye(A.shape[1]), atol=1e-12)
+        np.testing.assert_allclose(Hs[k], TU.mode2(T[k], A.T), atol=1e-12)
+        Xt = np.moveaxis(np.tensordot(A, Xt, axes=([1], [k])), 0, k)
+    assert np.linalg.norm(Xt.reshape(-1, order="F") - X) <= 1e-12 * np.linalg.norm(X)
+
+
+def test_tt2tucker_truncation_error_is_the_projection_error():
+    """With orthonormal cores to the left and right of core k (a train in
+    mixed-canonical form at k), truncating only A_k costs exactly
+    ||(I - A_k A_k^T)(T_k)_(2)||_F."""
+    from oracle import tucker as TU
+    rng = np.random.default_rng(12)
+    n, r = [6, 12, 5], [1, 4, 4, 1]
+    T0 = np.linalg.qr(rng.standard_normal((n[0], r[1])))[0].reshape((1, n[0], r[1]), order="F")
+    T2 = np.linalg.qr(rng.standard_normal((n[2], r[2])))[0].T.reshape((r[2], n[2], 1), order="F")
+    T1 = rng.standard_normal((r[1], n[1], r[2]))
+    T = [T0, T1, T2]
+    Hs, As = TU.tt2tucker(T, [n[0], 5, n[2]], p=4, seed=9)
+    Xt = tt.tt_full(Hs).reshape([A.shape[1] for A in As], order="F")
+    for k, A in enumerate(As):
+        Xt = np.moveaxis(np.tensordot(A, Xt, axes=([1], [k])), 0, k)
+    err = np.linalg.norm(Xt.reshape(-1, order="F") - tt.tt_full(T))
+    M = TU.unfold2(T1)
+    proj = np.linalg.norm(M - As[1] @ (As[1].T @ M))
+    assert abs(err - proj) <= 1e-12 * np.linalg.norm(M)
+    assert proj > 0
