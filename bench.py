@@ -522,7 +522,8 @@ def run_tucker(a, dev, P, stream):
     Tucker core G (random TT, ranks 8, + 1e-6 noise) and orthonormal 256 x 64
     factors: X (256^4) is never formed.  FP64, eps 1e-6, rmax 12, p 10; one
     untimed and one timed call; the error ||G - G~|| / ||G|| equals ||X - X~|| /
-    ||X|| since the factors are isometries."""
+    ||X|| since the factors are isometries.  Then TT2Tucker (Algorithm 4) of
+    the resulting train with multilinear ranks 64, timed the same way."""
     import torch
     s, n = [64] * 4, 256
     G = device_tt(s, [1, 8, 8, 8, 1], 0, 1e-6, dev).double()
@@ -543,6 +544,15 @@ def run_tucker(a, dev, P, stream):
         err = t.error(G, stream)
         stream.synchronize()
         err = err.cpu().numpy()
+        # and back (Algorithm 4): the TT cores to a Tucker format with multilinear ranks 64
+        P.tt2tucker(cores, [64] * 4, p=10, seed=3, stream=stream)
+        stream.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        Hs, As = P.tt2tucker(cores, [64] * 4, p=10, seed=3, stream=stream)
+        f1.record(stream)
+        stream.synchronize()
+        out.update({"tt2tucker_ms": f0.elapsed_time(f1), "tt2tucker_tucker_ranks": [int(A.shape[1]) for A in As]})
         out.update({"ms": e0.elapsed_time(e1), "rel_err_vs_X": float((err[0] / err[1]) ** 0.5),
                     "ranks": t.status(stream)[1], "x_entries_not_formed": n ** 4, "core_entries": G.numel(),
                     "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()]})

@@ -329,6 +329,15 @@ tt_status tt_generate_gaussian_bumps(int d, const int64_t* n, int nbumps, double
 tt_status tt_core_mode2(const double* H, int r0, int64_t s, int r1, const double* A, int64_t n,
                         double* T, tt_stream_t stream);
 
+/* TT2Tucker (Algorithm 4) layout step: out(j, i, k) = in(i, j, k) for a
+ * column-major in of n0 x n1 x n2 doubles (device; out is n1 x n0 x n2 and
+ * must not overlap in).  With (n0, n1, n2) = (r_{k-1}, n_k, r_k) it gives the
+ * mode-2 matricization (T_k)_(2) (n_k x r_{k-1} r_k); with (t_k, r_{k-1},
+ * r_k) it folds t_k x r_{k-1} r_k back into a core.  Asynchronous on stream.
+ * Errors: TT_ERR_INVALID_ARG (null, sizes < 1, in == out), TT_ERR_CUDA. */
+tt_status tt_swap12(const double* in, int64_t n0, int64_t n1, int64_t n2, double* out,
+                    tt_stream_t stream);
+
 /* Self-test of failure detection (no counterpart in the paper): launches one
  * CTA whose thread waits, with the bounded wait every kernel of this library
  * uses, on an mbarrier that nothing arrives at; after limit_cycles SM clock

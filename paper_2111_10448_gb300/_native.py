@@ -85,6 +85,7 @@ _SIGS = {
     "tt_generate_gaussian_bumps": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_double, _P,
                                              C.c_int64, C.c_int64, _P, C.c_int, _P]),
     "tt_core_mode2": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int, _P, C.c_int64, _P, _P]),
+    "tt_swap12": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P]),
     "tt_kernel_launches": (C.c_int64, []),
     "tt_version": (C.c_char_p, []),
 }

@@ -272,3 +272,34 @@ def tucker2tt(G, factors, *, prec="fp64", stream=None, **kw):
                 "tt_core_mode2")
         out.append(T.view(rp1, n, rp0).permute(2, 1, 0))
     return out, t
+
+
+def tt2tucker(cores, tranks, *, p=5, seed=1, stream=None):
+    """TT2Tucker (Algorithm 4): an orthogonal Tucker format of the TT tensor
+    with the given cores.  cores: device float64 tensors T_k of shape
+    (r_{k-1}, n_k, r_k) (contiguous in the column-major sense: T.permute(2, 1,
+    0) contiguous, as tucker2tt returns them, or plain row-major tensors of that
+    shape, which are converted); tranks: the multilinear target ranks t_k.
+    Step 2 for core k is the one-sided two-pass PSTT (d = 2) of the mode-2
+    matricization (T_k)_(2) with target rank t_k, test-matrix key seed + k:
+    A_k is its first core, H_k its second, folded back.  Returns (H, A): H[k]
+    of shape (r_{k-1}, tpad_k, r_k) and A[k] of shape (n_k, tpad_k), both
+    device float64 (columns past the found rank zero)."""
+    Hs, As = [], []
+    for k, T in enumerate(cores, start=1):
+        r0, n, r1 = (int(v) for v in T.shape)
+        Tcm = T.to(torch.float64).permute(2, 1, 0).contiguous()  # column-major r0 x n x r1
+        M = torch.empty(n * r0 * r1, dtype=torch.float64, device=Tcm.device)
+        N.check(N.lib().tt_swap12(_ptr(Tcm), r0, n, r1, _ptr(M), _stream(stream)), "tt_swap12")
+        t = min(int(tranks[k - 1]), n, r0 * r1)
+        sk = TTSketch([n, r0 * r1], ranks=[1, t, 1], p=p, seed=seed + k, passes=2, one_sided=True,
+                      x_dtype=torch.float64, prec="fp64", device=Tcm.device).pstt2(M, stream)
+        it = sk.items[0]
+        tp = it["rpad"][1]
+        A = sk.cores[it["core_off"][1]:it["core_off"][1] + n * tp].view(tp, n).t()      # n x tp
+        H2 = sk.cores[it["core_off"][2]:it["core_off"][2] + tp * r0 * r1]               # tp x (r0 r1), column-major
+        H = torch.empty(r0 * tp * r1, dtype=torch.float64, device=Tcm.device)
+        N.check(N.lib().tt_swap12(_ptr(H2), tp, r0, r1, _ptr(H), _stream(stream)), "tt_swap12")
+        Hs.append(H.view(r1, tp, r0).permute(2, 1, 0))
+        As.append(A.clone())
+    return Hs, As

@@ -58,3 +58,30 @@ def test_core_mode2_padded_rows_stay_zero():
     T = Td.cpu().numpy().reshape((4, 7, 5), order="F")
     np.testing.assert_allclose(T, TU.mode2(H, A), rtol=0, atol=1e-13)
     assert not T[2:].any() and not T[:, :, 3:].any()
+
+
+@pytest.mark.parametrize("tr", [[2, 6, 6, 2], [2, 4, 3, 2]])
+def test_tt2tucker_matches_oracle(tr):
+    """TT2Tucker (Algorithm 4): the factors and Tucker-core train against the
+    oracle (FP64 within 1e-10), exact when t_k >= rank (T_k)_(2)."""
+    from paper_2111_10448_gb300 import tt2tucker
+    rng = np.random.default_rng(4)
+    n, r = [9, 12, 10, 7], [1, 2, 3, 2, 1]
+    T = [rng.standard_normal((r[k], n[k], r[k + 1])) for k in range(4)]
+    Hs, As = tt2tucker([torch.tensor(t, device="cuda") for t in T], tr, p=4, seed=3)
+    Hr, Ar = TU.tt2tucker(T, tr, p=4, seed=3)
+    for k in range(4):
+        t = Ar[k].shape[1]
+        A = As[k].cpu().numpy()
+        H = Hs[k].cpu().numpy()
+        assert np.abs(A[:, t:]).max(initial=0.0) == 0.0 and np.abs(H[:, t:, :]).max(initial=0.0) == 0.0
+        np.testing.assert_allclose(A[:, :t], Ar[k], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(H[:, :t, :], Hr[k], rtol=0, atol=1e-10 * np.abs(Hr[k]).max())
+    Xt = OT.tt_full([h.cpu().numpy() for h in Hs]).reshape([a.shape[1] for a in As], order="F")
+    for k, A in enumerate(As):
+        Xt = np.moveaxis(np.tensordot(A.cpu().numpy(), Xt, axes=([1], [k])), 0, k)
+    X = OT.tt_full(T)
+    err = np.linalg.norm(Xt.reshape(-1, order="F") - X) / np.linalg.norm(X)
+    if tr == [2, 6, 6, 2]:
+        assert err <= 1e-12
+    print(f"tt2tucker t={tr}: |X~-X|/|X| = {err:.2e}")
