@@ -12,7 +12,7 @@ What it follows (Sec. 3.2 of the paper):
   by an extra sketch of the middle unfolding and a pseudo-inverse as in
   eq. (3.3) ("onepass_final_core").
 
-Readings of the paper taken here (every one is listed in the design doc):
+Readings of the paper taken here (the CUDA path takes the same ones):
 * A1  P-indexing: the paper's "P_j for j > d*" is the row basis of X_{j-1};
   row sketches R_k = X_k^T Psi_k cover k = d*..d-1 (the only dimensionally
   consistent reading of eq. (3.5)).

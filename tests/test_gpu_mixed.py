@@ -1,6 +1,6 @@
 """GPU parity of the mixed-precision (TF32 / BF16 tensor-core) sketch path.
 
-Bars (derived from the arithmetic, see DESIGN.md):
+Bars (derived from the arithmetic):
 * test-matrix entries: the FP32 generator differs from the FP64 definition by
   about 1e-7 relative (at most ~1e-5 absolute, only where u is within 1e-5 of
   1 so that |z| is tiny), so after rounding to the MMA type an entry equals
