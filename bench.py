@@ -132,6 +132,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_tensor_peak(prec):
+    """Dense tensor peak (TFLOP/s) for the sketch's MMA type: the measured BF16
+    burst figure, or for TF32 that figure times the nominal TF32/BF16 ratio
+    (1.1 / 2.25)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16, kind = 1900.0, "fallback"
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("bf16_tflops"):
+            bf16, kind = d["bf16_tflops"], "measured"
+    return (bf16, f"{kind} bf16_tflops") if prec == "bf16" else (bf16 * 1.1 / 2.25, f"{kind} bf16_tflops x 1.1/2.25")
+
+
 def traffic_record(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
     on the current source of that kernel (else None)."""
@@ -771,9 +785,20 @@ def run_gpu(a):
 
     peak, peak_kind = measured_peaks()
     achieved = ntot * 4 / (sketch_ms * 1e-3) / 1e9
+    # the two other ceilings of the sketch, beside HBM: tensor pipe (every entry
+    # feeds l MACs per sketch, twice for the hi + lo split of X) and test-matrix
+    # generation (each test-matrix row once: sum over sketches of l * rows)
+    shapes = [tuple(S.shape) for _, _, S in t.sketches(0)]
+    flops_pe = 2 * 2 * sum(w for _, w in shapes)
+    normals = sum((ntot // rows) * w for rows, w in shapes)
+    tpeak, tkind = measured_tensor_peak(a.prec)
+    tflops = ntot * flops_pe / (sketch_ms * 1e-3) / 1e12
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_record(f"sketch_{a.prec}_{n}x{m}x{m}x{n}"), "peak_kind": f"{peak_kind} hbm_gbs",
-                "kernel_ms": sketch_ms, "algorithmic_bytes": ntot * 4}
+                "kernel_ms": sketch_ms, "algorithmic_bytes": ntot * 4,
+                "tensor": {"flops_per_entry": flops_pe, "achieved_tflops": tflops, "peak_tflops": tpeak,
+                           "peak_kind": tkind, "frac": tflops / tpeak},
+                "rng": {"normals_per_entry": normals / ntot, "normals_per_step": normals}}
 
     if not a.no_batched:
         out["batched"] = run_batched(a, dev, P, stream)
