@@ -198,6 +198,21 @@ def cpu_sample(steps=1, n=128):
         f"p=10, rmax=6; entries/s = entries / wall time"), times
 
 
+def cpu_sample_one_core(n=64):
+    """The same oracle sample on one host core: a child process with every
+    BLAS / OpenMP pool limited to one thread (n = 64, 16.8M entries)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = f"import json, bench; v, _, s, _ = bench.cpu_sample(1, {n}); print(json.dumps([v, s]))"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=300)
+        v, sample = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": v, "unit": "entries/s", "cores": 1, "sample": sample}
+    except Exception as ex:  # a baseline figure only; the line goes on without it
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
 def reference_sample_n(steps, budget_s=150.0):
     """Largest sample size n in {32, 48, 64, 96, 128} whose `steps` oracle
     runs fit the time budget (cost scales with n^4; measured at n = 32)."""
@@ -815,7 +830,8 @@ def run_gpu(a):
     cpu = None
     if rank == 0 and not a.no_cpu:
         v, cores, sample, _ = cpu_sample(1)
-        cpu = {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "one_core": cpu_sample_one_core()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
