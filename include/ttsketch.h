@@ -143,7 +143,8 @@ tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, in
 
 /* Which sketch kernel an accumulate of `count_last` last-mode slices runs for
  * item 0: 0 = FP64 SIMT kernel, 1 = generic tensor-core kernel (mma.sync,
- * any shape), 2 = tcgen05 plane kernel (n_1 and count_last in {128, 256},
+ * any shape; test-matrix rows that several tiles read are staged once per
+ * call, up to 256 MB a sketch), 2 = tcgen05 plane kernel (n_1 and count_last in {128, 256},
  * d in {3, 4}, BF16, two-sided, equal widths with 16 <= l * #sketches per
  * side <= 32), 3 = small-plane kernel (BF16 or TF32, n_1 and count_last <= 32,
  * widths l_k <= 32, padded to the widest; mma.sync with test-matrix rows
@@ -167,7 +168,10 @@ tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* 
  * [first_last, first_last + count_last) of the LAST mode (device pointer to
  * count_last * N_{d-1} entries), in any order, each index exactly once;
  * finalize forms the cores.  The host checks the slab bookkeeping (a repeated
- * or out-of-range index is TT_ERR_STATE / TT_ERR_INVALID_ARG). */
+ * or out-of-range index is TT_ERR_STATE / TT_ERR_INVALID_ARG).  The tensor-
+ * core kernels stage test-matrix rows in the workspace during an accumulate,
+ * so accumulates on one workspace must not overlap: issue them on one stream
+ * (or order them with events). */
 tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream);
 tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_last,
                               int64_t count_last, void* ws, tt_stream_t stream);

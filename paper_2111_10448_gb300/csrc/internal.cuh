@@ -58,6 +58,8 @@ struct DevSketch {
   int64_t off_rt;      // CPQR R factor of the root R (width x width)
   int64_t off_q2;      // CPQR Q factor (width x width)
   int64_t off_piv;     // pivots (width ints, stored as int in a double slot area)
+  int64_t gen_tab;     // generic tile kernel: byte offset (in the item's table area) of
+                       // this sketch's staged test-matrix rows, -1: regenerated per tile
   int64_t sp_tab;      // small-plane kernel: byte offset of this sketch's staged
                        // test-matrix rows (BF16), -1 when it is generated per plane
 };
@@ -104,6 +106,8 @@ struct DevItem {
   int64_t tctab_doubles;    // its size (0 when the plane kernel cannot serve the item)
   int64_t off_sptab;        // small-plane kernel: staged test-matrix rows of the sketches
   int64_t sptab_doubles;    // its size (0 when the small-plane kernel cannot serve the item)
+  int64_t off_gentab;       // generic tile kernel: staged test-matrix rows of the sketches whose
+  int64_t gentab_doubles;   // rows repeat across planes (0: none)
 };
 
 struct Task {               // one block of one TSQR level (finalize)
@@ -159,6 +163,12 @@ cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t 
 bool mixed_tc_supported(const Plan& P, int item, int64_t count);
 bool use_tc_kernel(const Plan& P, int item, int64_t count);
 bool use_sp_kernel(const Plan& P, int item, int64_t count);
+// Fill the staged test-matrix rows of one sketch: entry (key, r, j), r < nr,
+// j < lpad, at element (key nr + r) lpad + j of tab (BF16, or FP32 rounded to
+// TF32 when tf), rows as the sketch's test matrix numbers them for the slab
+// starting at `first` (column side) or for plane key (row side).
+cudaError_t launch_rows_table(const DevSketch& d, uint64_t seed, int64_t first, int64_t n1, int nr, int lpad,
+                              int64_t nkeys, char* tab, bool tf, cudaStream_t st);
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st);
 bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out, int t3max = 4);

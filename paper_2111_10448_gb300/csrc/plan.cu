@@ -263,6 +263,45 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.sptab_doubles = ok ? std::max<int64_t>(1, (bytes + 7) / 8) : 0;
   }
   it.off_sptab = it.sptab_doubles ? ws.take(it.sptab_doubles) : 0;
+  // Staging area of the generic tile kernel (items that neither the plane
+  // kernel nor the small-plane kernel serves): the test-matrix rows of each
+  // sketch whose rows the tiles would otherwise draw more than once.  A
+  // column-side row (key w / wdiv, i_d) is drawn by wdiv planes times the
+  // 64-row tiles of i_1; a row-side row (key w % wdiv, i_1) by W / wdiv planes
+  // times the 32-column tiles of i_d.  Rows for the whole last mode (column
+  // side) or n_1 (row side), padded width round16(l); up to 256 MB a sketch
+  // and 1 GB an item, sketches past that draw their rows per tile.  The
+  // planes that share a column-side key are neighbours in the tile order, so
+  // those rows stay in L2; the planes that share a row-side key lie wdiv
+  // planes apart, so a row-side table is read from HBM once a plane unless it
+  // fits in L2 (16 MB here): it is kept only then or when at least four
+  // column tiles of the plane share the fetch.
+  it.gentab_doubles = 0;
+  {
+    const bool ok = (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 &&
+                    it.tctab_doubles == 0 && it.sptab_doubles == 0;
+    const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
+    const int64_t tilesA = (q.n[0] + 63) / 64, tilesB = (q.n[d - 1] + 31) / 32;
+    int64_t bytes = 0;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+      DevSketch& s = P.sketches[si];
+      s.gen_tab = -1;
+      if (!ok) continue;
+      const int64_t lpad = (s.width + 15) / 16 * 16;
+      int64_t tb = 0;
+      if (s.type == SK_COL && s.wdiv * tilesA >= 2) tb = (it.W / s.wdiv) * q.n[d - 1] * lpad * esz;
+      if (s.type == SK_ROW && (it.W / s.wdiv) * tilesB >= 2) {
+        tb = s.wdiv * q.n[0] * lpad * esz;
+        if (tilesB < 4 && tb > (16LL << 20)) tb = 0;
+      }
+      if (tb > 0 && tb <= (256LL << 20) && bytes + tb <= (1LL << 30)) {
+        s.gen_tab = bytes;
+        bytes += (tb + 255) / 256 * 256;
+      }
+    }
+    it.gentab_doubles = (bytes + 7) / 8;
+  }
+  it.off_gentab = it.gentab_doubles ? ws.take(it.gentab_doubles) : 0;
   // reconstruction interfaces
   for (int k = 1; k <= ds; ++k) it.off_L[k] = ws.take(it.N[k] * it.rpad[k]);
   for (int k = ds + 1; k <= d; ++k) it.off_Rt[k] = ws.take((int64_t)it.rpad[k - 1] * (it.N[d] / it.N[k - 1]));

@@ -134,6 +134,7 @@ constexpr int gThreads = 256;
 
 struct SkArgM {
   int64_t rows, off, wdiv, hstride;
+  int64_t tab;  // byte offset (from the workspace base) of the staged test-matrix rows, -1: none
   int type, width, sid, pad_;
 };
 
@@ -260,6 +261,22 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
       const int nq = lpad / 4;
       const int kext = bf ? ((nr + 15) & ~15) : ((nr + 7) & ~7);
       __syncthreads();
+      if (sk.tab >= 0) {
+        // staged rows: (key, row) at element (key nrows + row) lpad, where the
+        // column side keys by w / wdiv over the slab's i_d and the row side by
+        // w % wdiv over i_1
+        const int64_t trow = col ? whi * a.cnt + b0 : wlo * a.n1 + a0;
+        const int esz = bf ? 2 : 4;
+        const int cpr = lpad * esz / 16;  // 16-byte chunks a row
+        const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(a.ws) + sk.tab +
+                                                          trow * lpad * esz);
+        for (int o = tid; o < nr * cpr; o += gThreads) {
+          const int r = o / cpr, c = o - r * cpr;
+          const uint4 v = __ldg(src + (int64_t)r * cpr + c);
+          if (bf) reinterpret_cast<uint4*>(GsB + r * gLDG)[c] = v;
+          else reinterpret_cast<uint4*>(Gs + r * LDG)[c] = v;
+        }
+      } else
       for (int o = tid; o < nr * nq; o += gThreads) {
         const int r = o % nr, q = o / nr;
         const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
@@ -383,7 +400,7 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const Batc
           sa.prec = it.prec;
           for (int s = 0; s < it.nsk; ++s) {
             const DevSketch& d = sks[it.sk0 + s];
-            sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, 0};
+            sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, 0};
           }
         }
         __syncthreads();
@@ -1438,7 +1455,17 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   a.prec = it.prec;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
-    a.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, 0};
+    a.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, 0};
+    if (d.gen_tab >= 0 && it.gentab_doubles > 0) {
+      // stage the sketch's rows for this call: the slab's i_d (column side) or i_1 (row side)
+      const int lpad = (d.width + 15) / 16 * 16;
+      const bool col = d.type == SK_COL;
+      a.sk[s].tab = it.off_gentab * 8 + d.gen_tab;
+      cudaError_t e = launch_rows_table(d, it.seed, first, a.n1, col ? (int)count : (int)a.n1, lpad,
+                                        col ? it.W / d.wdiv : d.wdiv, (char*)ws + a.sk[s].tab,
+                                        it.prec == TT_PREC_TF32, st);
+      if (e != cudaSuccess) return e;
+    }
   }
   const size_t smem = sizeof(float) * (2 * (gTA + 1) * gTB + (size_t)gTA * (TT_MAXL + 4));
   static bool attr_set = false;

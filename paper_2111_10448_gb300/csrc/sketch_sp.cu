@@ -654,6 +654,20 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, 
 
 }  // namespace sp
 
+cudaError_t launch_rows_table(const DevSketch& d, uint64_t seed, int64_t first, int64_t n1, int nr, int lpad,
+                              int64_t nkeys, char* tab, bool tf, cudaStream_t st) {
+  sp::SpSk k;
+  memset(&k, 0, sizeof(k));
+  k.hstride = d.hstride;
+  k.col = d.type == SK_COL ? 1 : 0;
+  k.sid = d.stream_id;
+  const int64_t total = nkeys * nr * (lpad / 4);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count()));
+  count_launch();
+  sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, seed, first, n1, nr, d.width, lpad, nkeys, tab, tf ? 1 : 0);
+  return cudaGetLastError();
+}
+
 bool use_sp_kernel(const Plan& P, int item, int64_t count) {
   static int force = -1;
   if (force < 0) {

@@ -117,6 +117,29 @@ def test_mixed_streaming_equals_one_shot():
     assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_generic_staged_rows_streaming_match_oracle(prec):
+    # n_1 = 70, n_d = 45: the generic tile kernel with staged test-matrix rows
+    # (column side: 2 row tiles of i_1 read each row; row side: planes and
+    # column tiles), slabs that cut the 32-wide tiles of i_d raggedly
+    dims, r = [70, 3, 5, 45], [1, 4, 5, 4, 1]
+    x = ti.random_tt(dims, r, seed=8, noise=1e-6).astype(np.float32)
+    X = to_dev(x)
+    Nd1 = 70 * 3 * 5
+    t = TTSketch(dims, ranks=r, p=6, seed=9, x_dtype=torch.float32, prec=prec)
+    assert t.kernel_kind(15) == 1
+    t.begin()
+    for first, cnt in [(30, 15), (0, 13), (13, 17)]:
+        t.accumulate(X[first * Nd1:(first + cnt) * Nd1].clone(), first, cnt)
+    sk = sketch_dict(t)
+    t.finalize()
+    o = OP.pstt2(_split(x.astype(np.float64), prec), dims, ranks=r, p=6, seed=9, passes=1, test_fmt=prec)
+    for k, S in o["sketch"]["S"].items():
+        _close_sketch(sk[(0, k)], S, ("S", k))
+    for k, R in o["sketch"]["R"].items():
+        _close_sketch(sk[(1, k)], R, ("R", k))
+
+
 # ----------------------------------------------------------- tcgen05 kernel
 @pytest.mark.parametrize("dims,kw", [
     ([128, 5, 6, 128], dict(ranks=[1, 4, 4, 4, 1], p=4)),            # ragged tiles (5 x 6 planes), l = 8
