@@ -14,7 +14,9 @@
  *  - d* = ceil(d/2).  Column sketches S_k = X_k Omega_k (k < d*, plus k = d*
  *    in one-pass mode), row sketches R_k = X_k^T Psi_k (k = d*..d-1).
  *  - Omega_k / Psi_k are i.i.d. N(0,1) test matrices regenerated on the fly
- *    from a Philox4x32-10 counter stream keyed by `seed` (never stored).
+ *    from a Philox4x32-10 counter stream keyed by `seed`: never kept across
+ *    calls (rows that many tiles read are staged in the workspace for the
+ *    duration of one accumulate).
  *  - Cores are FP64, written into ONE caller buffer: core k (1-based) lives
  *    at element offset core_off[k] with the padded shape
  *    rpad[k-1] x n_k x rpad[k], entry (a, i, c) at a + rpad[k-1] (i + n_k c);
