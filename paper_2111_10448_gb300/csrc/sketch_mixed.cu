@@ -276,23 +276,24 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
           if (bf) reinterpret_cast<uint4*>(GsB + r * gLDG)[c] = v;
           else reinterpret_cast<uint4*>(Gs + r * LDG)[c] = v;
         }
-      } else
-      for (int o = tid; o < nr * nq; o += gThreads) {
-        const int r = o % nr, q = o / nr;
-        const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
-                                  : (uint64_t)((a0 + r) + a.n1 * wlo);
-        const float4 z4 = normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
-        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
-        if (bf) {
-          float zz[4];
+      } else {  // regenerate the rows
+        for (int o = tid; o < nr * nq; o += gThreads) {
+          const int r = o % nr, q = o / nr;
+          const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
+                                    : (uint64_t)((a0 + r) + a.n1 * wlo);
+          const float4 z4 = normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
+          const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+          if (bf) {
+            float zz[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
-          __nv_bfloat162* gp = reinterpret_cast<__nv_bfloat162*>(GsB + r * gLDG + 4 * q);
-          gp[0] = __floats2bfloat162_rn(zz[0], zz[1]);
-          gp[1] = __floats2bfloat162_rn(zz[2], zz[3]);
-        } else {
+            for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+            __nv_bfloat162* gp = reinterpret_cast<__nv_bfloat162*>(GsB + r * gLDG + 4 * q);
+            gp[0] = __floats2bfloat162_rn(zz[0], zz[1]);
+            gp[1] = __floats2bfloat162_rn(zz[2], zz[3]);
+          } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+            for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+          }
         }
       }
       if (bf)  // contraction padding rows [nr, kext) (another sketch may have left rows there)
