@@ -190,3 +190,52 @@ def test_one_sided_plans_refuse_what_they_do_not_support():
         assert L.tt_sketch_plan(C.byref(bad), C.byref(h)) == N.TT_ERR_UNSUPPORTED
     arr = (N.tt_problem * 2)(ok, ok)
     assert L.tt_sketch_plan_batched(arr, 2, C.byref(h)) == N.TT_ERR_UNSUPPORTED
+
+
+def _staged_bytes(dims, sk, esz):
+    """Staging tables of the generic tile kernel by the rule the plan states:
+    column side keys w / wdiv over i_d, row side keys w % wdiv over i_1,
+    staged when more than one tile would draw the rows; row-side tables over
+    16 MiB need four column tiles of a plane; 256 MiB a table, 1 GiB an item."""
+    d, n1, nd = len(dims), dims[0], dims[-1]
+    Nk = [1]
+    for v in dims:
+        Nk.append(Nk[-1] * v)
+    W = Nk[d - 1] // n1
+    tiles_a, tiles_b = -(-n1 // 64), -(-nd // 32)
+    total = 0
+    for ty, k, rows, width, _ in sk:
+        lpad = -(-width // 16) * 16
+        wdiv = Nk[k] // n1
+        tb = 0
+        if ty == 0 and wdiv * tiles_a >= 2:
+            tb = (W // wdiv) * nd * lpad * esz
+        if ty == 1 and (W // wdiv) * tiles_b >= 2:
+            tb = wdiv * n1 * lpad * esz
+            if tiles_b < 4 and tb > 16 << 20:
+                tb = 0
+        if 0 < tb <= 256 << 20 and total + tb <= 1 << 30:
+            total += -(-tb // 256) * 256
+    return total
+
+
+@pytest.mark.parametrize("dims,r", [([200] * 4, [1, 40, 40, 40, 1]), ([960] * 3, [1, 25, 25, 1]),
+                                    ([96] * 5, [1, 17, 18, 18, 17, 1]), ([70, 3, 5, 45], [1, 4, 5, 4, 1]),
+                                    ([48, 40, 36, 40, 64], [1, 20, 30, 30, 20, 1]),
+                                    ([100] * 4, [1, 40, 40, 40, 1])])
+def test_generic_kernel_staging_tables_follow_their_rule(dims, r):
+    """The BF16 / TF32 workspace of a shape on the generic tile kernel exceeds
+    the FP64 one by exactly its staged test-matrix rows (2 or 4 bytes an
+    entry), capped per sketch and per item."""
+    ws = {}
+    for prec in (N.TT_PREC_FP64, N.TT_PREC_BF16, N.TT_PREC_TF32):
+        st, h = plan(dims, ranks=r, p=10, x_dtype=N.TT_F32, prec=prec)
+        assert st == N.TT_OK
+        ws[prec] = sizes(h)[0]
+        if prec == N.TT_PREC_BF16:
+            sk = sketch_list(h)
+            assert N.lib().tt_sketch_kernel_kind(h, dims[-1]) == 1
+        N.lib().tt_plan_destroy(h)
+    assert ws[N.TT_PREC_BF16] - ws[N.TT_PREC_FP64] == _staged_bytes(dims, sk, 2)
+    assert ws[N.TT_PREC_TF32] - ws[N.TT_PREC_FP64] == _staged_bytes(dims, sk, 4)
+    assert ws[N.TT_PREC_TF32] - ws[N.TT_PREC_FP64] <= 1 << 30
