@@ -239,3 +239,30 @@ def test_generic_kernel_staging_tables_follow_their_rule(dims, r):
     assert ws[N.TT_PREC_BF16] - ws[N.TT_PREC_FP64] == _staged_bytes(dims, sk, 2)
     assert ws[N.TT_PREC_TF32] - ws[N.TT_PREC_FP64] == _staged_bytes(dims, sk, 4)
     assert ws[N.TT_PREC_TF32] - ws[N.TT_PREC_FP64] <= 1 << 30
+
+
+def test_readme_c_example_compiles_and_links(tmp_path):
+    """The C quick start of the README compiles warning-free against
+    include/ttsketch.h and links against the built library."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if gcc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("gcc or the CUDA headers are not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "README.md")).read()
+    m = re.search(r"## Quick start \(C\)\s*```c\n(.*?)```", text, re.S)
+    assert m, "no C quick start in the README"
+    src = tmp_path / "app.c"
+    src.write_text(m.group(1))
+    N.lib()  # the library is built
+    libdir = os.path.dirname(N.LIB_PATH)
+    cudalib = next((p for p in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib")) if os.path.isdir(p)), None)
+    cmd = [gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(root, "include"),
+           "-I", os.path.join(cuda, "include"), str(src), "-L", libdir, "-lttsketch"]
+    if cudalib:
+        cmd += ["-L", cudalib]
+    cmd += ["-lcudart", "-o", str(tmp_path / "app")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
