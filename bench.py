@@ -432,10 +432,25 @@ SECOND = {
 }
 
 
+def median_ms(call, stream, reps=3):
+    """Device time of `call` on `stream`: `reps` runs enqueued back to back
+    (the host stays ahead of the GPU), each bracketed by CUDA events; the
+    median and every run in ms."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        call()
+        e1.record(stream)
+    stream.synchronize()
+    runs = [e0.elapsed_time(e1) for e0, e1 in ev]
+    return sorted(runs)[reps // 2], runs
+
+
 def run_second(a, dev, P, stream):
     """The paper's second workloads (Sec. 4.3-4.4) at full size, FP32 X
     generated on the device (not timed), BF16 sketches, p = 10: one untimed
-    and one timed pstt2 each, error against X."""
+    pstt2 and the median of three timed ones each, error against X."""
     import ctypes as C
     import torch
     import ttinputs as ti
@@ -467,16 +482,12 @@ def run_second(a, dev, P, stream):
             stream.synchronize()
             t = P.TTSketch(dims, p=10, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, **kw)
             t.pstt2(X, stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            t.pstt2(X, stream)
-            e1.record(stream)
+            ms, runs = median_ms(lambda: t.pstt2(X, stream), stream)
             err = t.error(X, stream)
             stream.synchronize()
-            ms = e0.elapsed_time(e1)
             err = err.cpu().numpy()
             st, ranks = t.status(stream)
-            r.update({"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+            r.update({"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "ms_runs": runs,
                       "hbm_frac_of_measured": ntot * 4 / (ms * 1e-3) / 1e9 / measured_peaks()[0],
                       "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": ranks, "status": st,
                       "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()],
@@ -497,7 +508,8 @@ def run_onesided(a, dev, P, stream):
     second pass) against the two-sided PSTT2-onepass on the same X:
     the precision-form tensor (random TT d=6 n=24, eps 1e-5, rmax 16, p 10)
     and the streaming Hilbert-type tensor (d=4 n=256, eps 1e-6, rmax 6, p 10);
-    BF16 sketches, one untimed and one timed pstt2 each, errors against X."""
+    BF16 sketches, one untimed pstt2 and the median of three timed ones
+    each, errors against X."""
     import ctypes as C
     import torch
     from paper_2111_10448_gb300 import _native as N
@@ -523,15 +535,11 @@ def run_onesided(a, dev, P, stream):
                 t = P.TTSketch(dims, seed=1, x_dtype=torch.float32, prec="bf16", device=dev, one_sided=one,
                                passes=passes, **kw)
                 t.pstt2(X, stream)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                t.pstt2(X, stream)
-                e1.record(stream)
+                ms, runs = median_ms(lambda: t.pstt2(X, stream), stream)
                 err = t.error(X, stream)
                 stream.synchronize()
-                ms = e0.elapsed_time(e1)
                 err = err.cpu().numpy()
-                r[label] = {"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
+                r[label] = {"value": ntot / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "ms_runs": runs,
                             "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": t.status(stream)[1],
                             "sketch_MB": sum(S.numel() for _, _, S in t.sketches(0)) * 8 / 1e6,
                             "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][
