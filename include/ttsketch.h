@@ -284,19 +284,22 @@ const char* tt_status_string(tt_status s);
  * [row0, row0 + nrows) and columns [0, ncols) of stream `stream_id`, written
  * column-major to out (device, FP64, nrows x ncols) exactly as the sketch of
  * precision `prec` uses them (FP64 values, or the FP32 generator rounded to
- * TF32 / BF16). */
+ * TF32 / BF16).  Errors: TT_ERR_INVALID_ARG (null out, negative sizes or
+ * row0, ncols > TT_MAXL, unknown prec), TT_ERR_CUDA; empty ranges are TT_OK. */
 tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nrows, int ncols,
                          tt_prec prec, double* out, tt_stream_t stream);
 
 /* Raw Philox4x32-10 on `count` counters (device uint32 arrays of 4*count,
- * key = (key0, key1)); out gets 4*count words. */
+ * key = (key0, key1)); out gets 4*count words.  Errors: TT_ERR_INVALID_ARG
+ * (null pointer, count < 0), TT_ERR_CUDA; count = 0 is TT_OK. */
 tt_status tt_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,
                            int64_t count, tt_stream_t stream);
 
 /* Synthetic input: the Hilbert-type tensor 1/(x_{i_1} + ... + x_{i_d}),
  * x_i = 1 + i/(n-1), for the slab [first_last, first_last + count_last) of
  * the last mode, written to out (device, dtype).  The sum is formed in FP64
- * from i_1 upwards, then rounded to dtype. */
+ * from i_1 upwards, then rounded to dtype.  Errors: TT_ERR_INVALID_ARG for
+ * bad sizes or a slab outside n[d-1], TT_ERR_CUDA. */
 tt_status tt_generate_hilbert_type(int d, const int64_t* n, int64_t first_last,
                                    int64_t count_last, void* out, tt_dtype dtype,
                                    tt_stream_t stream);

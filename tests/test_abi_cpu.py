@@ -266,3 +266,49 @@ def test_readme_c_example_compiles_and_links(tmp_path):
     cmd += ["-lcudart", "-o", str(tmp_path / "app")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_device_calls_check_their_arguments_on_the_host():
+    """Argument errors of the generator, test-matrix and Tucker calls come back
+    synchronously as TT_ERR_INVALID_ARG before anything is launched, and empty
+    ranges are TT_OK without a launch (no device needed for either)."""
+    L = N.lib()
+    BAD, OK = N.TT_ERR_INVALID_ARG, N.TT_OK
+    dummy = C.c_void_p(256)  # never dereferenced: every case returns before a launch
+    null = C.c_void_p(None)
+    n3 = (C.c_int64 * 3)(4, 5, 6)
+    n0 = (C.c_int64 * 3)(4, 0, 6)
+    # test matrix
+    assert L.tt_test_matrix(1, 0, 0, 10, 4, N.TT_PREC_BF16, null, null) == BAD
+    assert L.tt_test_matrix(1, 0, 0, -1, 4, N.TT_PREC_BF16, dummy, null) == BAD
+    assert L.tt_test_matrix(1, 0, -3, 10, 4, N.TT_PREC_BF16, dummy, null) == BAD
+    assert L.tt_test_matrix(1, 0, 0, 10, N.TT_MAXL + 1, N.TT_PREC_BF16, dummy, null) == BAD
+    assert L.tt_test_matrix(1, 0, 0, 10, 4, 7, dummy, null) == BAD
+    assert L.tt_test_matrix(1, 0, 0, 0, 4, N.TT_PREC_BF16, dummy, null) == OK
+    # raw Philox
+    assert L.tt_philox4x32_10(null, 1, 2, dummy, 4, null) == BAD
+    assert L.tt_philox4x32_10(dummy, 1, 2, dummy, -1, null) == BAD
+    assert L.tt_philox4x32_10(dummy, 1, 2, dummy, 0, null) == OK
+    # generators: bad order, zero mode, slab outside the last mode, dtype, empty slab
+    for gen in (L.tt_generate_hilbert, L.tt_generate_hilbert_type):
+        assert gen(0, n3, 0, 1, dummy, N.TT_F32, null) == BAD
+        assert gen(N.TT_MAXD + 1, n3, 0, 1, dummy, N.TT_F32, null) == BAD
+        assert gen(3, n0, 0, 1, dummy, N.TT_F32, null) == BAD
+        assert gen(3, n3, 4, 3, dummy, N.TT_F32, null) == BAD
+        assert gen(3, n3, 0, 1, null, N.TT_F32, null) == BAD
+        assert gen(3, n3, 0, 1, dummy, 5, null) == BAD
+        assert gen(3, n3, 6, 0, dummy, N.TT_F32, null) == OK
+    cen = (C.c_double * 6)(0.0, 0.1, 0.2, 0.3, 0.4, 0.5)
+    bumps = L.tt_generate_gaussian_bumps
+    assert bumps(3, n3, 0, 10.0, cen, 0, 1, dummy, N.TT_F32, null) == BAD          # no bumps
+    assert bumps(3, n3, 2, float("nan"), cen, 0, 1, dummy, N.TT_F32, null) == BAD  # gamma
+    assert bumps(3, n3, 2, -1.0, cen, 0, 1, dummy, N.TT_F32, null) == BAD
+    assert bumps(3, n3, 2, 10.0, null, 0, 1, dummy, N.TT_F32, null) == BAD         # centres
+    assert bumps(3, n3, 2, 10.0, cen, 5, 2, dummy, N.TT_F32, null) == BAD          # slab outside
+    assert bumps(3, n3, 2, 10.0, cen, 0, 0, dummy, N.TT_F32, null) == OK
+    # Tucker steps
+    assert L.tt_core_mode2(null, 2, 3, 2, dummy, 5, dummy, null) == BAD
+    assert L.tt_core_mode2(dummy, 0, 3, 2, dummy, 5, dummy, null) == BAD
+    assert L.tt_core_mode2(dummy, 2, 3, 2, dummy, 0, dummy, null) == BAD
+    assert L.tt_swap12(dummy, 2, 3, 4, dummy, null) == BAD                         # in == out
+    assert L.tt_swap12(dummy, 0, 3, 4, C.c_void_p(512), null) == BAD
