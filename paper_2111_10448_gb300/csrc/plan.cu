@@ -263,8 +263,9 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.sptab_doubles = ok ? std::max<int64_t>(1, (bytes + 7) / 8) : 0;
   }
   it.off_sptab = it.sptab_doubles ? ws.take(it.sptab_doubles) : 0;
-  // Staging area of the generic tile kernel (items that neither the plane
-  // kernel nor the small-plane kernel serves): the test-matrix rows of each
+  // Staging area of the generic tile kernel (single-problem plans whose item
+  // neither the plane kernel nor the small-plane kernel serves; the batched
+  // kernel draws its rows per tile): the test-matrix rows of each
   // sketch whose rows the tiles would otherwise draw more than once.  A
   // column-side row (key w / wdiv, i_d) is drawn by wdiv planes times the
   // 64-row tiles of i_1; a row-side row (key w % wdiv, i_1) by W / wdiv planes
@@ -278,7 +279,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   // column tiles of the plane share the fetch.
   it.gentab_doubles = 0;
   {
-    const bool ok = (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 &&
+    const bool ok = single && (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 &&
                     it.tctab_doubles == 0 && it.sptab_doubles == 0;
     const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
     const int64_t tilesA = (q.n[0] + 63) / 64, tilesB = (q.n[d - 1] + 31) / 32;

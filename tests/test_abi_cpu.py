@@ -312,3 +312,21 @@ def test_device_calls_check_their_arguments_on_the_host():
     assert L.tt_core_mode2(dummy, 2, 3, 2, dummy, 0, dummy, null) == BAD
     assert L.tt_swap12(dummy, 2, 3, 4, dummy, null) == BAD                         # in == out
     assert L.tt_swap12(dummy, 0, 3, 4, C.c_void_p(512), null) == BAD
+
+
+def test_batched_plans_stage_no_generic_rows():
+    """The batched sketch kernel draws its test-matrix rows per tile, so a
+    batched plan reserves no staging tables: its BF16 / TF32 workspace equals
+    the FP64 one for shapes outside the plane and small-plane kernels."""
+    probs = [([70, 3, 5, 45], [1, 4, 5, 4, 1]), ([200] * 3, [1, 20, 20, 1])]
+
+    def ws_of(prec):
+        arr = (N.tt_problem * len(probs))(*[N.make_problem(d, ranks=r, p=10, x_dtype=N.TT_F32, prec=prec)
+                                             for d, r in probs])
+        h = C.c_void_p()
+        assert N.lib().tt_sketch_plan_batched(arr, len(probs), C.byref(h)) == N.TT_OK
+        w = sizes(h)[0]
+        N.lib().tt_plan_destroy(h)
+        return w
+
+    assert ws_of(N.TT_PREC_BF16) == ws_of(N.TT_PREC_FP64) == ws_of(N.TT_PREC_TF32)
