@@ -145,8 +145,8 @@ tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, in
 
 /* Which sketch kernel an accumulate of `count_last` last-mode slices runs for
  * item 0: 0 = FP64 SIMT kernel, 1 = generic tensor-core kernel (mma.sync,
- * any shape; test-matrix rows that several tiles read are staged once per
- * call, up to 256 MB a sketch), 2 = tcgen05 plane kernel (n_1 and count_last in {128, 256},
+ * any shape; in single-problem plans the test-matrix rows that several
+ * tiles read are staged once per call, up to 256 MB a sketch), 2 = tcgen05 plane kernel (n_1 and count_last in {128, 256},
  * d in {3, 4}, BF16, two-sided, equal widths with 16 <= l * #sketches per
  * side <= 32), 3 = small-plane kernel (BF16 or TF32, n_1 and count_last <= 32,
  * widths l_k <= 32, padded to the widest; mma.sync with test-matrix rows
