@@ -38,6 +38,18 @@
  * memory.  No call allocates device memory.  The workspace holds all state
  * between the calls of one decomposition (sketches, bases, factorisations)
  * and stays valid until the next tt_pstt2* call on the same workspace.
+ *
+ * Sharing a workspace: the workspace also holds a copy of the plan's device
+ * tables (shapes and offsets the kernels read).  The library remembers, per
+ * workspace address, which plan's tables it holds and re-sends them (a small
+ * host-synchronous copy) whenever a plan uses a workspace that last held
+ * another plan's, so several plans may take turns on one workspace.  Each
+ * such switch ends the saved state of the previous plan there: a streaming
+ * decomposition whose workspace another plan used after tt_pstt2_begin, or a
+ * backward whose forward state was replaced, is refused with TT_ERR_STATE.
+ * Memory freed and allocated again at the same address is a new workspace to
+ * the caller but not to the library: call tt_workspace_release(ws) before
+ * freeing a workspace (tt_plan_destroy releases every workspace of its plan).
  */
 #ifndef TTSKETCH_H
 #define TTSKETCH_H
@@ -119,7 +131,15 @@ tt_status tt_sketch_plan(const tt_problem* prob, tt_plan_t* out);
  * its own slice of the workspace, core buffer and rank array. */
 tt_status tt_sketch_plan_batched(const tt_problem* probs, int count, tt_plan_t* out);
 
+/* Destroy a plan and forget every workspace it used (tt_workspace_release). */
 void tt_plan_destroy(tt_plan_t plan);
+
+/* Forget which plan's tables and state the workspace at `ws` holds (host
+ * only; touches no device).  Call it before freeing a workspace that a plan
+ * of a live plan object used, so that memory allocated later at the same
+ * address is treated as new: the next call on it sends its plan's tables.
+ * Unknown addresses and NULL are ignored. */
+void tt_workspace_release(const void* ws);
 
 /* Sizes the caller must allocate: workspace bytes (device, 256-byte aligned
  * base) and the number of FP64 entries of the core buffer (all items of a
@@ -243,7 +263,11 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
  * same padded layout as the cores), write dL/dX (device, x_dtype, prod(n)
  * entries; overwritten).  X enters only through the sketches, so
  * dX = sum_k Sbar_k Omega_k^T + sum_k Psi_k Rbar_k^T, with the test matrices
- * regenerated from Philox.  Uses the state saved in ws by the forward call. */
+ * regenerated from Philox.  Uses the state saved in ws by the forward call:
+ * ws must be the workspace of this plan's last completed forward call
+ * (tt_pstt2, tt_pstt2_finalize), and no other plan may have used it since;
+ * otherwise TT_ERR_STATE (also after tt_pstt2_noalloc, whose state is not in
+ * any caller workspace). */
 tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void* dX,
                             tt_stream_t stream);
 

@@ -8,9 +8,9 @@ its thin binding.  PyTorch is used only for device memory and streams.
 from . import _native
 from ._native import (TT_F32, TT_F64, TT_PREC_BF16, TT_PREC_FP64, TT_PREC_TF32, TTError, check,
                       lib, make_problem)
-from .api import PSTT2Fn, TTReconstructFn, TTSketch, pstt2, tt_entries_from_cores, tt2tucker, tucker2tt
+from .api import PSTT2Fn, TTReconstructFn, TTSketch, pstt2, tt2tucker, tucker2tt
 
 __all__ = [
-    "TTSketch", "PSTT2Fn", "TTReconstructFn", "pstt2", "tt_entries_from_cores", "tt2tucker", "tucker2tt", "TTError", "lib", "make_problem", "check",
+    "TTSketch", "PSTT2Fn", "TTReconstructFn", "pstt2", "tt2tucker", "tucker2tt", "TTError", "lib", "make_problem", "check",
     "TT_F32", "TT_F64", "TT_PREC_FP64", "TT_PREC_TF32", "TT_PREC_BF16", "_native",
 ]

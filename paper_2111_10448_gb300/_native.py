@@ -56,6 +56,7 @@ _SIGS = {
     "tt_sketch_plan": (C.c_int, [C.POINTER(tt_problem), C.POINTER(_P)]),
     "tt_sketch_plan_batched": (C.c_int, [C.POINTER(tt_problem), C.c_int, C.POINTER(_P)]),
     "tt_plan_destroy": (None, [_P]),
+    "tt_workspace_release": (None, [_P]),
     "tt_plan_sizes": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "tt_plan_core_layout": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "tt_plan_problem": (C.c_int, [_P, C.c_int, C.POINTER(tt_problem)]),

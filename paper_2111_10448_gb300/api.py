@@ -237,18 +237,6 @@ def pstt2(X, dims, **kw):
     return t.pstt2(X)
 
 
-def tt_entries_from_cores(cores, idx):
-    """Evaluate a TT at given multi-indices on the host (float64), for checks."""
-    import numpy as np
-    out = np.empty(len(idx))
-    for m, ii in enumerate(idx):
-        v = np.ones((1,))
-        for G, i in zip(cores, ii):
-            v = v @ G[:, int(i), :]
-        out[m] = v[0]
-    return out
-
-
 def tucker2tt(G, factors, *, prec="fp64", stream=None, **kw):
     """Tucker2TT (Algorithm 3): TT cores of X = G x_1 A_1 ... x_d A_d without
     forming X.  G: the Tucker core on the device (column-major flat, dims

@@ -151,7 +151,6 @@ constexpr int64_t kRankCopyOff = 64;
 
 // ---------------------------------------------------------------- host side
 struct Plan;
-void plan_forget_upload(Plan* p);
 const DevItem* plan_items_host(const Plan* p);
 int plan_num_items(const Plan* p);
 

@@ -19,8 +19,7 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 std::mutex g_mu;
-void* g_ptr[kMaxDevices] = {};              // address of the array on each device
-const void* g_last_plan[kMaxDevices] = {};  // plan whose tables were last uploaded there
+void* g_ptr[kMaxDevices] = {};  // address of the array on each device
 
 }  // namespace
 
@@ -45,13 +44,11 @@ extern "C" tt_status tt_pstt2_noalloc(tt_plan_t plan, const void* X, double* cor
       g_ptr[dev] = p;
     }
     ws = g_ptr[dev];
-    // The plan tables sit in the workspace; another plan may have replaced
-    // them since this plan last used the array, so they are re-sent then.
-    if (g_last_plan[dev] != plan) {
-      tts::plan_forget_upload(reinterpret_cast<tts::Plan*>(plan));
-      g_last_plan[dev] = plan;
-    }
   }
+  // tt_pstt2 re-sends the plan tables whenever another plan used the array
+  // last (the library's workspace registry), and records the array as the
+  // workspace of this plan's last forward call, so a later tt_pstt2_backward
+  // on any caller workspace is refused (TT_ERR_STATE).
   s = tt_pstt2(plan, X, ws, cores, ranks, stream);
   if (s != TT_OK) return s;
   if (status_dev) {

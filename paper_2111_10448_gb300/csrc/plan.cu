@@ -10,7 +10,9 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -27,15 +29,40 @@ struct Plan {
   int64_t core_entries = 0;
   int rank_entries = 0;
   std::vector<unsigned char> blob;  // device tables (uploaded to ws + kTableOff)
-  const void* uploaded_ws = nullptr;
+  uint64_t id = 0;                  // process-unique plan id (workspace registry key)
   // streaming bookkeeping (single-item plans)
   std::vector<char> slab_seen;
   bool begun = false;
-  bool forward_done = false;
+  const void* stream_ws = nullptr;   // workspace of the streaming decomposition begun last
+  const void* forward_ws = nullptr;  // workspace of the last completed forward call
   BatchCfg bcfg{64, 4, 4};  // batched sketch launch shape (tt_plan_autotune)
 };
 
 static constexpr int64_t kTableOff = 256;  // bytes
+
+// Workspace registry: for every workspace address a plan has used, which plan's
+// tables it holds and whether it holds that plan's saved forward state (the
+// state the backward reads).  A call of plan P on workspace W re-sends P's
+// tables whenever W last held another plan's (or none), so plans can share a
+// workspace in any order; a workspace that is freed and reallocated at the
+// same address must be released first (tt_workspace_release).
+namespace {
+struct WsEntry {
+  uint64_t plan_id;
+  bool forward_valid;
+};
+std::mutex g_ws_mu;
+std::unordered_map<const void*, WsEntry> g_ws;
+std::atomic<uint64_t> g_next_plan_id{1};
+}  // namespace
+
+void plan_mark_forward(Plan* p, const void* ws, bool valid) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  if (it != g_ws.end() && it->second.plan_id == p->id) it->second.forward_valid = valid;
+  p->forward_ws = valid ? ws : nullptr;
+}
+
 
 const DevItem* plan_items_host(const Plan* p) { return p->items.data(); }
 const DevSketch* plan_sketches_host(const Plan* p) { return p->sketches.data(); }
@@ -417,6 +444,7 @@ static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
     return st != TT_OK ? st : TT_ERR_INVALID_ARG;
   }
   if (count == 1) P->slab_seen.assign((size_t)P->items[0].n[P->items[0].d - 1], 0);
+  P->id = g_next_plan_id.fetch_add(1);
   // batched default: tiles as tall as the largest n_1 needs (32 or 64 rows)
   int64_t n1max = 1;
   for (const DevItem& it : P->items) n1max = std::max(n1max, it.n[0]);
@@ -427,9 +455,26 @@ static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
 
 static Plan* as_plan(tt_plan_t p) { return reinterpret_cast<Plan*>(p); }
 
-// The next call re-sends the plan tables to its workspace (used when the same
-// workspace address may have held another plan's tables in between).
-void plan_forget_upload(Plan* p) { p->uploaded_ws = nullptr; }
+static bool plan_owns(const Plan* p, const void* ws) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  return it != g_ws.end() && it->second.plan_id == p->id;
+}
+
+static bool plan_forward_valid(const Plan* p, const void* ws) {
+  if (p->forward_ws != ws) return false;
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  return it != g_ws.end() && it->second.plan_id == p->id && it->second.forward_valid;
+}
+
+static void plan_release_all(const Plan* p) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->second.plan_id == p->id) it = g_ws.erase(it);
+    else ++it;
+  }
+}
 
 static tt_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return TT_OK;
@@ -438,16 +483,20 @@ static tt_status cuda_status(cudaError_t e) {
 }
 
 static tt_status ensure_uploaded(Plan& P, void* ws, cudaStream_t st) {
-  if (P.uploaded_ws == ws) return TT_OK;
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  if (it != g_ws.end() && it->second.plan_id == P.id) return TT_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
-    return TT_ERR_STATE;  // first use of a workspace must happen outside capture
+    return TT_ERR_STATE;  // first use of a workspace by a plan must happen outside capture
+  // the workspace no longer holds any plan's tables until the copy has landed
+  if (it != g_ws.end()) g_ws.erase(it);
   cudaError_t e = cudaMemcpyAsync((char*)ws + kTableOff, P.blob.data(), P.blob.size(),
                                   cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(st);  // the host blob must stay unchanged until copied
   if (e != cudaSuccess) return cuda_status(e);
-  P.uploaded_ws = ws;
+  g_ws[ws] = WsEntry{P.id, false};
   return TT_OK;
 }
 
@@ -506,7 +555,17 @@ tt_status tt_sketch_plan_batched(const tt_problem* probs, int count, tt_plan_t* 
   return make_plan(probs, count, out);
 }
 
-void tt_plan_destroy(tt_plan_t plan) { delete as_plan(plan); }
+void tt_plan_destroy(tt_plan_t plan) {
+  Plan* P = as_plan(plan);
+  if (!P) return;
+  plan_release_all(P);
+  delete P;
+}
+
+void tt_workspace_release(const void* ws) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  g_ws.erase(ws);
+}
 
 tt_status tt_plan_sizes(tt_plan_t plan, size_t* workspace_bytes, int64_t* core_entries,
                         int* rank_entries) {
@@ -570,7 +629,8 @@ tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream) {
   if (s != TT_OK) return s;
   std::fill(P->slab_seen.begin(), P->slab_seen.end(), 0);
   P->begun = true;
-  P->forward_done = false;
+  P->stream_ws = ws;
+  plan_mark_forward(P, ws, false);
   return TT_OK;
 }
 
@@ -579,7 +639,9 @@ tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_la
   Plan* P = as_plan(plan);
   if (!P || !ws || !slab || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   const DevItem& it = P->items[0];
-  if (!P->begun) return TT_ERR_STATE;
+  // the decomposition begun on this workspace, whose tables and sketches no
+  // other plan has replaced since
+  if (!P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_ERR_STATE;
   if (first_last < 0 || count_last < 1 || first_last + count_last > it.n[it.d - 1])
     return TT_ERR_INVALID_ARG;
   for (int64_t i = first_last; i < first_last + count_last; ++i)
@@ -594,13 +656,13 @@ tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
                             tt_stream_t stream) {
   Plan* P = as_plan(plan);
   if (!P || !ws || !cores || !ranks || P->items.size() != 1) return TT_ERR_INVALID_ARG;
-  if (!P->begun) return TT_ERR_STATE;
+  if (!P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_ERR_STATE;
   for (char c : P->slab_seen)
     if (!c) return TT_ERR_STATE;
   tt_status s = cuda_status(launch_finalize(*P, ws, cores, ranks, (cudaStream_t)stream));
   if (s != TT_OK) return s;
   P->begun = false;
-  P->forward_done = true;
+  plan_mark_forward(P, ws, true);
   return TT_OK;
 }
 
@@ -625,7 +687,7 @@ tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* 
   }
   if (s != TT_OK) return s;
   P->begun = false;
-  P->forward_done = true;
+  plan_mark_forward(P, ws, true);
   return TT_OK;
 }
 
@@ -660,7 +722,7 @@ tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   if (s != TT_OK) return s;
   s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, (cudaStream_t)stream);
   if (s != TT_OK) return s;
-  P->forward_done = true;
+  plan_mark_forward(P, ws, true);
   return TT_OK;
 }
 
@@ -726,7 +788,7 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   }
   // leave a complete decomposition with the chosen shape in the buffers
   s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, st);
-  if (s == TT_OK) P->forward_done = true;
+  if (s == TT_OK) plan_mark_forward(P, ws, true);
   return s;
 }
 
@@ -743,7 +805,8 @@ tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void
                             tt_stream_t stream) {
   Plan* P = as_plan(plan);
   if (!P || !ws || !dcores || !dX || P->items.size() != 1) return TT_ERR_INVALID_ARG;
-  if (!P->forward_done) return TT_ERR_STATE;
+  // the saved state of this plan's last forward call must still be in ws
+  if (!plan_forward_valid(P, ws)) return TT_ERR_STATE;
   if (P->items[0].passes != 1) return TT_ERR_UNSUPPORTED;
   return cuda_status(launch_backward(*P, 0, dcores, dX, ws, (cudaStream_t)stream));
 }

@@ -1567,18 +1567,13 @@ extern "C" tt_status tt_selftest_wait_timeout(int64_t limit_cycles, int* status_
 namespace tts {
 
 // Which mixed kernel a launch uses: the tcgen05 plane kernel when its shape
-// rules hold (TT_SKETCH_KERNEL=mma forces the generic one, for comparisons).
+// rules hold.
 bool use_tc_kernel(const Plan& P, int item, int64_t count) {
-  static int force = -1;
-  if (force < 0) {
-    const char* e = getenv("TT_SKETCH_KERNEL");
-    force = (e && strcmp(e, "mma") == 0) ? 1 : 0;
-  }
   // the plane kernel is built for the two-sided split (at most two sketches
   // per side); one-sided plans go to the other kernels
   if (plan_items_host(&P)[item].sided1) return false;
   tc::TcArgs g;
-  return force == 0 && tc::plan_tc(P, item, count, &g);
+  return tc::plan_tc(P, item, count, &g);
 }
 
 cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t first, int64_t count,

@@ -669,14 +669,9 @@ cudaError_t launch_rows_table(const DevSketch& d, uint64_t seed, int64_t first, 
 }
 
 bool use_sp_kernel(const Plan& P, int item, int64_t count) {
-  static int force = -1;
-  if (force < 0) {
-    const char* e = getenv("TT_SKETCH_KERNEL");
-    force = (e && strcmp(e, "mma") == 0) ? 1 : 0;
-  }
   sp::SpArgs g;
   size_t smem;
-  return force == 0 && sp::plan_sp(P, item, count, &g, &smem);
+  return sp::plan_sp(P, item, count, &g, &smem);
 }
 
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,

@@ -359,3 +359,33 @@ def test_small_plane_unequal_widths_match_oracle(dims, ranks, prec):
         _close_sketch(sk[(0, k)], S, ("S", k))
     for k, R in o["sketch"]["R"].items():
         _close_sketch(sk[(1, k)], R, ("R", k))
+
+
+@pytest.mark.parametrize("dims", [[256, 64, 48, 256], [128, 64, 96, 128]])
+def test_tcgen05_multitile_every_sketch_entry(dims):
+    """Every entry of every sketch of one multi-tile launch of the plane kernel
+    against the oracle's dense FP64 products (the split X, the BF16-rounded
+    test matrices).  At these shapes each CTA walks two to three tiles: the
+    change of kL block inside a run, the flush of the column accumulators
+    after at most 256 MMAs, the double-buffered row accumulators and the
+    ragged last kL block (64 = 5 x 12 + 4 at n_1 = 128) all take part."""
+    n1, n2, n3, n4 = dims
+    Xd = torch.empty(n1 * n2 * n3 * n4, dtype=torch.float32, device="cuda")
+    nn = (C.c_int64 * 4)(*dims)
+    N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, n4, C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
+    kw = dict(eps=1e-6, rmax=6, p=10)
+    t = TTSketch(dims, seed=7, prec="bf16", **kw)
+    assert t.kernel_kind() == 2
+    t.begin()
+    t.accumulate(Xd, 0, n4)
+    sk = sketch_dict(t)
+    del Xd
+    x = ti.hilbert_type(dims, np.float32).astype(np.float64)
+    xs = _split(x, "bf16")
+    del x
+    widths = OP.sketch_widths(4, None, kw["p"], True, kw["rmax"])
+    o = OP.sketches(xs, dims, widths, 7, 1, test_fmt="bf16")
+    for k, S in o["S"].items():
+        _close_sketch(sk[(0, k)], S, ("S", k))
+    for k, R in o["R"].items():
+        _close_sketch(sk[(1, k)], R, ("R", k))

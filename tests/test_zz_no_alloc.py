@@ -23,7 +23,8 @@ def _ptr(t):
 
 
 def _noalloc(t, X, cores, ranks, status):
-    return N.lib().tt_pstt2_noalloc(t.plan, _ptr(X), _ptr(cores), _ptr(ranks), _ptr(status), None)
+    return N.lib().tt_pstt2_noalloc(t.plan, _ptr(X), _ptr(cores), _ptr(ranks),
+                                    _ptr(status) if status is not None else None, None)
 
 
 def _cases():
@@ -61,6 +62,25 @@ def test_noalloc_matches_caller_workspace_two_calls_in_a_row():
             got = t.reconstruct(torch.float64, cores=cores).cpu().numpy()
             err = np.linalg.norm(got - ref) / nrm
             assert err <= tol, (name, call, err)
+
+
+@pytest.mark.gpu
+def test_backward_after_noalloc_is_refused():
+    """The no-alloc call keeps its saved state in the library array, which no
+    caller can name: a backward on any caller workspace afterwards is
+    refused, even one that held this plan's state from an earlier forward."""
+    name, X, kw = next(_cases())
+    dims = kw.pop("dims")
+    t = TTSketch(dims, **kw).pstt2(X)
+    dc = torch.zeros_like(t.cores)
+    dX = torch.empty_like(X)
+    t.backward(dc, dX)  # accepted: the forward state is in t.ws
+    cores = torch.zeros_like(t.cores)
+    ranks = torch.zeros_like(t.ranks)
+    N.check(_noalloc(t, X, cores, ranks, None), "tt_pstt2_noalloc")
+    st = N.lib().tt_pstt2_backward(t.plan, _ptr(t.ws), _ptr(dc), _ptr(dX), None)
+    assert st == N.TT_ERR_STATE
+    torch.cuda.synchronize()
 
 
 @pytest.mark.gpu
