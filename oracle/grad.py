@@ -103,6 +103,6 @@ def cores_vjp(x, dims, ref, dcores):
     return xt.grad.numpy().copy()
 
 
-def forward_ref(x, dims, *, ranks, p, seed, test_fmt="f64"):
+def forward_ref(x, dims, *, ranks, p, seed, test_fmt="f64", drm="gauss"):
     """A forward oracle run whose pivots and ranks freeze the map."""
-    return pstt2(x, dims, ranks=ranks, p=p, seed=seed, passes=1, test_fmt=test_fmt)
+    return pstt2(x, dims, ranks=ranks, p=p, seed=seed, passes=1, test_fmt=test_fmt, drm=drm)

@@ -26,6 +26,21 @@ CUDA side, which implements the same definition in its own code):
       z_{4q+2} = rho_b cos theta_b,  z_{4q+3} = rho_b sin theta_b.
 * Stream ids: the right test matrix Omega_k of unfolding k (column sketch) is
   s = k; the left test matrix Psi_k (row sketch) is s = 64 + k.
+
+Khatri-Rao test matrices (Sec. 3.2, the substitute for dense Phi_j that the
+paragraph after Theorem 3.3 describes, eq. (sketch_orig)): the test matrix of
+one sketch is a row-wise Khatri-Rao product of small i.i.d. Gaussian factors,
+one per mode its rows run over.  Here the factor of mode m (1-based) of the
+sketch with stream s is the n_m x l matrix whose row i is row
+i + (2^31 + m) 2^32 of stream s (the row-high word has its top bit set, so no
+factor row coincides with a row of a dense test matrix), and the entry of the
+product at the column-major multi-index (i_{m_1}, i_{m_2}, ...) (first listed
+mode fastest, modes in increasing order) is
+    F_{m_1}(i_{m_1}, j) * F_{m_2}(i_{m_2}, j) * ...
+multiplied in that order.  The paper writes the product Psi_d (.) ... (.)
+Psi_{j+1} for the column space of X_j; with the Kronecker convention of the
+Khatri-Rao product (the last factor's index fastest) its rows run over
+(i_{j+1}, ..., i_d) column-major, the column index of X_j.
 """
 import numpy as np
 
@@ -96,6 +111,29 @@ def gaussian(seed, stream, rows, ncols):
 def test_matrix(seed, stream, nrows, ncols):
     """The full nrows x ncols test matrix of one stream (dense, FP64)."""
     return gaussian(seed, stream, np.arange(nrows, dtype=np.uint64), ncols)
+
+
+KR_ROW_HI = 0x80000000
+
+
+def kr_factor(seed, stream, mode, n, ncols):
+    """Gaussian factor of mode `mode` (1-based) of a Khatri-Rao test matrix:
+    n x ncols, row i = row i + (2^31 + mode) 2^32 of the stream."""
+    base = np.uint64((KR_ROW_HI + int(mode)) << 32)
+    return gaussian(seed, stream, np.arange(n, dtype=np.uint64) + base, ncols)
+
+
+def kr_test_matrix(seed, stream, modes, sizes, ncols):
+    """The Khatri-Rao test matrix over `modes` (increasing, 1-based) of sizes
+    `sizes`: prod(sizes) x ncols, row = column-major multi-index with the first
+    mode fastest, entry = product of the factor entries in mode order (FP64).
+    This is the dense form of F_{m_last} (.) ... (.) F_{m_1}."""
+    out = np.ones((1, ncols))
+    for m, n in zip(modes, sizes):
+        F = kr_factor(seed, stream, m, n, ncols)
+        # rows of the product so far are the faster index: new row = r + R i
+        out = (out[None, :, :] * F[:, None, :]).reshape(-1, ncols)
+    return out
 
 
 def round_to(a, fmt):

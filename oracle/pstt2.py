@@ -25,6 +25,9 @@ Readings of the paper taken here (the CUDA path takes the same ones):
 * A5  eps-mode rank: smallest r >= 1 with ||R_22^(r)||_F <= eps/sqrt(d-1) ||S||_F,
   capped at rmax (flagged) and at min(N_k, M_k).
 * Test matrices: Omega_k = stream k, Psi_k = stream 64 + k (oracle.philox).
+  drm='gauss': i.i.d. Gaussian entries (Algorithm 2); drm='kr': Khatri-Rao
+  products of per-mode Gaussian factors (eq. (sketch_orig)): Omega_k over the
+  modes k+1..d of its rows, Psi_k over the modes 1..k.
 """
 import math
 import numpy as np
@@ -66,25 +69,42 @@ def sketch_widths(d, ranks, p, eps_mode, rmax):
     return [None] + [int(ranks[k]) + p for k in range(1, d)] + [None]
 
 
-def sketches(x, dims, widths, seed, passes, test_fmt='f64'):
+def omega(seed, dims, k, l, drm='gauss'):
+    """Omega_k (M_k x l, FP64): the right test matrix of X_k."""
+    d = len(dims)
+    N = prods(dims)
+    if drm == 'kr':
+        return philox.kr_test_matrix(seed, philox.STREAM_OMEGA + k, list(range(k + 1, d + 1)), dims[k:], l)
+    return philox.test_matrix(seed, philox.STREAM_OMEGA + k, N[d] // N[k], l)
+
+
+def psi(seed, dims, k, l, drm='gauss'):
+    """Psi_k (N_k x l, FP64): the left test matrix of X_k."""
+    N = prods(dims)
+    if drm == 'kr':
+        return philox.kr_test_matrix(seed, philox.STREAM_PSI + k, list(range(1, k + 1)), dims[:k], l)
+    return philox.test_matrix(seed, philox.STREAM_PSI + k, N[k], l)
+
+
+def sketches(x, dims, widths, seed, passes, test_fmt='f64', drm='gauss'):
     """Step 2: dense sketches, materialising the test matrices.
 
     Returns dict with 'S' {k: N_k x l_k} for k < d* (and k = d* in one-pass),
     'R' {k: M_k x l_k} for k = d*..d-1, and the test matrices used.
-    test_fmt rounds the Gaussian entries ('f64' keeps them exact).
+    test_fmt rounds the test-matrix entries ('f64' keeps them exact); drm
+    selects dense Gaussian ('gauss') or Khatri-Rao ('kr') test matrices.
     """
     d = len(dims)
     ds = split_index(d)
-    N = prods(dims)
     S, R, Om, Ps = {}, {}, {}, {}
     last_col = ds if passes == 1 else ds - 1
     for k in range(1, last_col + 1):
         l = widths[k] if k < ds else widths[ds]
-        Om[k] = philox.round_to(philox.test_matrix(seed, philox.STREAM_OMEGA + k, N[d] // N[k], l), test_fmt)
+        Om[k] = philox.round_to(omega(seed, dims, k, l, drm), test_fmt)
         S[k] = unfold(x, dims, k) @ Om[k]
     for k in range(ds, d):
         l = widths[k]
-        Ps[k] = philox.round_to(philox.test_matrix(seed, philox.STREAM_PSI + k, N[k], l), test_fmt)
+        Ps[k] = philox.round_to(psi(seed, dims, k, l, drm), test_fmt)
         R[k] = unfold(x, dims, k).T @ Ps[k]
     return {'S': S, 'R': R, 'Omega': Om, 'Psi': Ps}
 
@@ -162,7 +182,7 @@ def middle_core_twopass(x, dims, r, Q, P):
 
 
 def pstt2(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, passes=1,
-          test_fmt='f64'):
+          test_fmt='f64', drm='gauss'):
     """PSTT2 (passes=2) or PSTT2-onepass (passes=1) of the column-major tensor x.
 
     Either fixed ranks (ranks = [1, r_1, ..., r_{d-1}, 1]) or tolerance mode
@@ -181,7 +201,7 @@ def pstt2(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, passes=1,
         ranks = clamp_ranks(dims, ranks)
     ds = split_index(d)
     widths = sketch_widths(d, ranks, p, eps_mode, rmax)
-    sk = sketches(x, dims, widths, seed, passes, test_fmt)
+    sk = sketches(x, dims, widths, seed, passes, test_fmt, drm)
     r, Q, P, piv, Rf, capped = bases(sk, dims, ranks, eps if eps_mode else None, rmax)
     cores = outer_cores(dims, r, Q, P)
     out = {'r': r, 'Q': Q, 'P': P, 'piv': piv, 'Rfac': Rf, 'capped': capped,
@@ -196,7 +216,7 @@ def pstt2(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, passes=1,
     return out
 
 
-def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1):
+def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, drm='gauss'):
     """PSTT2-onepass over slabs of the last mode (Sec. 4.2, Algorithm 5's
     single stream): each slab (first, count, values) adds its contribution to
     every sketch; only one slab is held at a time.  Same result as pstt2 on
@@ -211,7 +231,7 @@ def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1):
     widths = sketch_widths(d, ranks, p, eps_mode, rmax)
     S = {k: np.zeros((N[k], widths[k] if k < ds else widths[ds])) for k in range(1, ds + 1)}
     R = {k: np.zeros((N[d] // N[k], widths[k])) for k in range(ds, d)}
-    Ps = {k: philox.test_matrix(seed, philox.STREAM_PSI + k, N[k], widths[k]) for k in range(ds, d)}
+    Ps = {k: psi(seed, dims, k, widths[k], drm) for k in range(ds, d)}
     Nd1 = N[d - 1]
     for first, count, vals in slabs:
         vals = np.asarray(vals, dtype=np.float64)
@@ -219,7 +239,10 @@ def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1):
             l = S[k].shape[1]
             Mk_slab = (Nd1 // N[k]) * count
             rows = np.arange(Mk_slab, dtype=np.uint64) + np.uint64((Nd1 // N[k]) * first)
-            Om = philox.gaussian(seed, philox.STREAM_OMEGA + k, rows, l)
+            if drm == 'kr':
+                Om = omega(seed, dims, k, l, drm)[rows.astype(np.int64)]
+            else:
+                Om = philox.gaussian(seed, philox.STREAM_OMEGA + k, rows, l)
             S[k] += vals.reshape((N[k], Mk_slab), order='F') @ Om
         for k in range(ds, d):
             Mk_slab = (Nd1 // N[k]) * count
@@ -228,7 +251,7 @@ def pstt2_stream(slabs, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1):
     sk = {'S': S, 'R': R, 'Omega': {}, 'Psi': Ps}
     r, Q, P, piv, Rf, capped = bases(sk, dims, ranks, eps if eps_mode else None, rmax)
     cores = outer_cores(dims, r, Q, P)
-    Om_mid = philox.test_matrix(seed, philox.STREAM_OMEGA + ds, N[d] // N[ds], widths[ds])
+    Om_mid = omega(seed, dims, ds, widths[ds], drm)
     Gm, B, H, rdiag = middle_core_onepass(dims, r, Q, P, S[ds], Om_mid)
     cores[ds] = Gm
     return {'r': r, 'Q': Q, 'P': P, 'piv': piv, 'cores': cores[1:], 'sketch': sk,

@@ -64,3 +64,27 @@ def test_planted_gradient_mistake_is_caught(monkeypatch):
     o = OP.pstt2(x, dims, ranks=target, p=p, seed=1, passes=1)
     L0 = float(np.sum((OT.tt_full(o["cores"]) - T) ** 2))
     assert abs(L1 - L0) > 1e-6 * L0
+
+
+def test_gradient_with_khatri_rao_test_matrices_matches_finite_differences():
+    """The same pin with Khatri-Rao test matrices (the map depends on them only
+    through the sketches, so the adjoint has the same form)."""
+    dims, x, target, p = fd_instance()
+    T = ti.target_tensor(x.size, seed=3)
+    ref = OG.forward_ref(x, dims, ranks=target, p=p, seed=1, drm="kr")
+    L0, g = OG.loss_and_grad(x, dims, ref, T)
+
+    def loss_np(xx):
+        o = OP.pstt2(xx, dims, ranks=target, p=p, seed=1, passes=1, drm="kr")
+        return float(np.sum((OT.tt_full(o["cores"]) - T) ** 2))
+
+    assert abs(loss_np(x) - L0) <= 1e-12 * L0
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    v = rng.standard_normal(x.size)
+    dd = (loss_np(x + h * v) - loss_np(x - h * v)) / (2 * h)
+    assert abs(dd - g @ v) <= 1e-6 * abs(dd)
+    idx = rng.choice(x.size, size=20, replace=False)
+    fd = np.array([(loss_np(x + h * np.eye(1, x.size, i)[0]) - loss_np(x - h * np.eye(1, x.size, i)[0])) / (2 * h)
+                   for i in idx])
+    np.testing.assert_allclose(g[idx], fd, rtol=1e-6, atol=1e-6 * np.abs(g).max())

@@ -563,3 +563,138 @@ def test_tt2tucker_truncation_error_is_the_projection_error():
     proj = np.linalg.norm(M - As[1] @ (As[1].T @ M))
     assert abs(err - proj) <= 1e-12 * np.linalg.norm(M)
     assert proj > 0
+
+
+# ------------------------------------------------- Khatri-Rao test matrices
+def _modewise_column_sketch(x, dims, k, F):
+    """X_k (F_d (.) ... (.) F_{k+1}) evaluated as eq. (sketch_orig) writes it:
+    for every multi-index (l_{k+2}, ..., l_d) the N_k x n_{k+1} block of X_k with
+    those indices, times F_{k+1}, times the diagonal matrices of rows l_q of
+    F_q, summed -- the Khatri-Rao product is never formed."""
+    d = len(dims)
+    N = tt.prods(dims)
+    nk1 = dims[k]
+    rest = dims[k + 1:]
+    Xk = tt.unfold(x, dims, k).reshape((N[k], nk1, int(np.prod(rest)) if rest else 1), order="F")
+    l = F[k + 1].shape[1]
+    out = np.zeros((N[k], l))
+    for b, idx in enumerate(np.ndindex(*reversed(rest)) if rest else [()]):
+        idx = tuple(reversed(idx))  # (l_{k+2}, ..., l_d), column-major block order
+        diag = np.ones(l)
+        for q, lq in zip(range(k + 2, d + 1), idx):
+            diag = diag * F[q][lq]
+        out += (Xk[:, :, b] @ F[k + 1]) * diag[None, :]
+    return out
+
+
+def _modewise_row_sketch(x, dims, k, F):
+    """The row-space mirror (X_k^T (F_k (.) ... (.) F_1)): blocks of X_k^T with
+    fixed (l_1, ..., l_{k-1}) times F_k, scaled by the rows l_q of F_q."""
+    N = tt.prods(dims)
+    d = len(dims)
+    Xk = tt.unfold(x, dims, k)           # rows (i_1..i_k), i_1 fastest
+    lead = dims[:k - 1]
+    nk = dims[k - 1]
+    Xr = Xk.reshape((N[k - 1], nk, N[d] // N[k]), order="F")
+    l = F[k].shape[1]
+    out = np.zeros((N[d] // N[k], l))
+    for a, idx in enumerate(np.ndindex(*reversed(lead)) if lead else [()]):
+        idx = tuple(reversed(idx))  # (l_1, ..., l_{k-1})
+        diag = np.ones(l)
+        for q, lq in zip(range(1, k), idx):
+            diag = diag * F[q][lq]
+        out += (Xr[a].T @ F[k]) * diag[None, :]
+    return out
+
+
+@pytest.mark.parametrize("dims", [[3, 4, 2, 3], [2, 3, 2, 3, 2]])
+def test_kr_sketches_equal_modewise_products_eq_sketch_orig(dims):
+    """The oracle's Khatri-Rao sketches (dense product with the materialised
+    test matrix) against eq. (sketch_orig)'s mode-by-mode evaluation with the
+    same factors; a Khatri-Rao product with the mode order reversed fails."""
+    d = len(dims)
+    x = ti.random_tt(dims, [1] + [2] * (d - 1) + [1], seed=11, noise=1e-2)
+    l, seed = 5, 13
+    sk = P.sketches(x, dims, [None] + [l] * d, seed, 1, drm="kr")
+    ds = P.split_index(d)
+    for k, S in sk["S"].items():
+        F = {q: philox.kr_factor(seed, k, q, dims[q - 1], l) for q in range(k + 1, d + 1)}
+        np.testing.assert_allclose(S, _modewise_column_sketch(x, dims, k, F), rtol=1e-12, atol=1e-12)
+        if d - k >= 2:
+            bad = philox.kr_test_matrix(seed, k, list(range(d, k, -1)), dims[k:][::-1], l)
+            assert np.abs(tt.unfold(x, dims, k) @ bad - S).max() > 1e-3
+    for k, R in sk["R"].items():
+        F = {q: philox.kr_factor(seed, 64 + k, q, dims[q - 1], l) for q in range(1, k + 1)}
+        np.testing.assert_allclose(R, _modewise_row_sketch(x, dims, k, F), rtol=1e-12, atol=1e-12)
+    assert ds in sk["S"]
+
+
+def test_kr_factor_rows_are_not_dense_rows():
+    """A factor row is a Gaussian row of the same stream at a counter no dense
+    test matrix uses (row-high word with the top bit set)."""
+    f = philox.kr_factor(5, 3, 2, 7, 6)
+    g = philox.gaussian(5, 3, np.arange(7, dtype=np.uint64) + np.uint64((0x80000000 + 2) << 32), 6)
+    np.testing.assert_array_equal(f, g)
+    dense = philox.test_matrix(5, 3, 7, 6)
+    assert not np.any(np.isclose(f, dense))
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("passes", [1, 2])
+def test_kr_exact_recovery(d, passes):
+    """With target ranks at least the TT ranks, PSTT2 with Khatri-Rao test
+    matrices reproduces X (the sketches span the unfoldings' ranges with
+    probability one, as with dense Gaussians)."""
+    dims = [4 + (k % 3) for k in range(d)]
+    r = [1] + [2 + (k % 2) for k in range(d - 1)] + [1]
+    x = ti.random_tt(dims, r, seed=d + 20)
+    o = P.pstt2(x, dims, ranks=[1] + [4] * (d - 1) + [1], p=3, seed=d + 30, passes=passes, drm="kr")
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_kr_config1_exact_and_different_from_dense():
+    dims = [16] * 4
+    x = ti.random_tt(dims, [1, 3, 4, 3, 1], seed=0)
+    o = P.pstt2(x, dims, ranks=[1, 4, 4, 4, 1], p=5, seed=1, drm="kr")
+    g = P.pstt2(x, dims, ranks=[1, 4, 4, 4, 1], p=5, seed=1)
+    assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+    assert np.abs(o["sketch"]["S"][1] - g["sketch"]["S"][1]).max() > 1e-3
+
+
+def test_kr_d2_is_the_range_finder_with_the_factor():
+    """d = 2: each test matrix has a single factor, so PSTT2 with Khatri-Rao
+    test matrices is the randomized range finder with those n x l Gaussian
+    factors (two-pass: A P P^T with P from the pivoted QR of A^T F)."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((20, 5)) @ rng.standard_normal((5, 18)) + 1e-3 * rng.standard_normal((20, 18))
+    x = A.ravel(order="F")
+    r, p = 4, 3
+    o2 = P.pstt2(x, [20, 18], ranks=[1, r, 1], p=p, seed=4, passes=2, drm="kr")
+    Fp = philox.kr_factor(4, 64 + 1, 1, 20, r + p)
+    Qs, _, _ = scipy.linalg.qr(A.T @ Fp, pivoting=True, mode="economic")
+    Pr = Qs[:, :r]
+    np.testing.assert_allclose(tt.tt_full(o2["cores"]), (A @ Pr @ Pr.T).ravel(order="F"), atol=1e-12)
+    o1 = P.pstt2(x, [20, 18], ranks=[1, r, 1], p=p, seed=4, passes=1, drm="kr")
+    Fo = philox.kr_factor(4, 1, 2, 18, r + p)
+    H = (A @ Fo) @ np.linalg.pinv(Pr.T @ Fo)
+    np.testing.assert_allclose(tt.tt_full(o1["cores"]), (H @ Pr.T).ravel(order="F"), atol=1e-11)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_kr_twopass_deterministic_bound_eq_proj_acc(seed):
+    """Theorem 3.2's bound holds for any test matrices, Khatri-Rao included."""
+    dims = [5, 6, 4, 5, 3]
+    x = ti.random_tt(dims, [1, 4, 5, 5, 3, 1], seed=seed, noise=1e-2)
+    o = P.pstt2(x, dims, ranks=[1, 2, 3, 3, 2, 1], p=2, seed=300 + seed, passes=2, drm="kr")
+    err2 = np.linalg.norm(x - tt.tt_full(o["cores"])) ** 2
+    assert err2 <= sum(_proj_terms(x, dims, o)) * (1 + 1e-10)
+
+
+def test_kr_streaming_equals_one_shot():
+    dims = [6, 5, 4, 7]
+    x = ti.random_tt(dims, [1, 3, 3, 3, 1], seed=8, noise=1e-3)
+    full = P.pstt2(x, dims, ranks=[1, 3, 3, 3, 1], p=4, seed=2, passes=1, drm="kr")
+    Nd1 = 6 * 5 * 4
+    slabs = [(a, c, x[a * Nd1:(a + c) * Nd1]) for a, c in [(4, 3), (0, 2), (2, 2)]]
+    st = P.pstt2_stream(slabs, dims, ranks=[1, 3, 3, 3, 1], p=4, seed=2, drm="kr")
+    np.testing.assert_allclose(tt.tt_full(st["cores"]), tt.tt_full(full["cores"]), atol=1e-12)
