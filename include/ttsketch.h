@@ -118,6 +118,20 @@ typedef struct {
  * to O(l n^{d-1}) (the two-sided form needs O(l n^{ceil(d/2)})).  Requires a
  * single-problem plan; not with TT_FLAG_DIFF (TT_ERR_UNSUPPORTED otherwise). */
 #define TT_FLAG_ONESIDED 2
+/* Khatri-Rao test matrices (Sec. 3.2, the paragraph after Theorem 3.3,
+ * eq. (sketch_orig)) instead of dense i.i.d. Gaussian ones: the test matrix of
+ * each sketch is the row-wise Khatri-Rao product of small i.i.d. N(0,1)
+ * factors, one n_m x l factor per mode m its rows run over (Omega_k: modes
+ * k+1..d; Psi_k: modes 1..k).  Row i of the factor of mode m (1-based) is row
+ * i + (2^31 + m) 2^32 of the sketch's Philox stream, so it never coincides
+ * with a dense row.  The entry at the column-major multi-index of the modes is
+ * the product of the factor entries, multiplied in increasing mode order (in
+ * FP64 on the FP64 path; in FP32 from the FP32 generator, then rounded once
+ * to the MMA type, on the TF32 / BF16 paths).  The factors (sum of n_m l
+ * entries per sketch) are staged in the workspace by tt_pstt2 and
+ * tt_pstt2_begin.  Single-problem plans only (TT_ERR_UNSUPPORTED in batched
+ * plans). */
+#define TT_FLAG_KR 4
 
 /* ---------------------------------------------------------------- plans */
 

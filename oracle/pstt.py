@@ -15,21 +15,23 @@ The readings of the two-sided oracle apply unchanged: test matrices
 Omega_j = stream j and Psi_{d-1} = stream 64 + d - 1 of oracle.philox (A6),
 widths l_j = r_j + p or rmax + p (A3), CPQR pivoting and the eps rank rule
 (A4, A5).  The least-squares solve is the same QR of the small factor as the
-two-sided middle core.
+two-sided middle core.  drm='kr' takes the Khatri-Rao test matrices of
+oracle.pstt2 (Omega_j over the modes j+1..d, Psi_{d-1} over 1..d-1): Algorithm 2
+"with the Khatri-Rao DRMs" of the paragraph after Theorem 3.3.
 """
 import numpy as np
 
 from . import philox
 from .linalg import householder_cpqr, lstsq_right
-from .pstt2 import clamp_ranks, pick_rank_eps, sketch_widths
+from .pstt2 import clamp_ranks, omega, pick_rank_eps, psi, sketch_widths
 from .tt import prods, unfold
 
 
-def pstt(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64'):
+def pstt(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64', drm='gauss'):
     """PSTT (Algorithm 2, two passes): the bases and cores 1..d-1 of
     pstt_onepass, and the last core G_d = Q_{d-1}^T X_{d-1} from a second
     pass over X."""
-    o = pstt_onepass(x, dims, ranks=ranks, eps=eps, rmax=rmax, p=p, seed=seed, test_fmt=test_fmt)
+    o = pstt_onepass(x, dims, ranks=ranks, eps=eps, rmax=rmax, p=p, seed=seed, test_fmt=test_fmt, drm=drm)
     dims = [int(n) for n in dims]
     d = len(dims)
     r = o['r']
@@ -38,7 +40,7 @@ def pstt(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64
     return o
 
 
-def pstt_onepass(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64'):
+def pstt_onepass(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_fmt='f64', drm='gauss'):
     """PSTT-onepass of the column-major tensor x: fixed ranks
     ([1, r_1, ..., r_{d-1}, 1]) or tolerance mode (eps > 0 with cap rmax).
     Returns a dict with the cores (0-based list, shapes (r_{k-1}, n_k, r_k)),
@@ -58,9 +60,9 @@ def pstt_onepass(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_
     # one pass: the right sketches of every unfolding and the left sketch of X_{d-1}
     S, Om = {}, {}
     for k in range(1, d):
-        Om[k] = philox.round_to(philox.test_matrix(seed, philox.STREAM_OMEGA + k, N[d] // N[k], widths[k]), test_fmt)
+        Om[k] = philox.round_to(omega(seed, dims, k, widths[k], drm), test_fmt)
         S[k] = unfold(x, dims, k) @ Om[k]
-    Psi = philox.round_to(philox.test_matrix(seed, philox.STREAM_PSI + d - 1, N[d - 1], widths[d - 1]), test_fmt)
+    Psi = philox.round_to(psi(seed, dims, d - 1, widths[d - 1], drm), test_fmt)
     T = Psi.T @ unfold(x, dims, d - 1)                    # l x n_d
     # bases: CPQR of every S_k, rank per A5 in tolerance mode
     r = [1] * (d + 1)

@@ -19,6 +19,7 @@ TT_F32, TT_F64 = 0, 1
 TT_PREC_FP64, TT_PREC_TF32, TT_PREC_BF16 = 0, 1, 2
 TT_FLAG_DIFF = 1
 TT_FLAG_ONESIDED = 2
+TT_FLAG_KR = 4
 
 STATUS_NAMES = {
     0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_UNSUPPORTED", 3: "TT_ERR_CUDA",

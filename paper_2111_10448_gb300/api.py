@@ -26,14 +26,15 @@ class TTSketch:
     passes: 1 (one-pass, the hot path) or 2; x_dtype: torch.float32/float64;
     prec: 'fp64' | 'tf32' | 'bf16'; one_sided: the one-sided PSTT-onepass
     (every unfolding sketched from the right, last core by least squares)
-    instead of the two-sided PSTT2-onepass.
+    instead of the two-sided PSTT2-onepass; drm: 'gauss' (dense Gaussian test
+    matrices) or 'kr' (Khatri-Rao products of per-mode Gaussian factors).
     """
 
     PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
 
     def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
                  x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False,
-                 one_sided=False):
+                 one_sided=False, drm="gauss"):
         L = N.lib()
         self.device = torch.device(device)
         if batch is None:
@@ -47,7 +48,8 @@ class TTSketch:
                                     seed=pr.get("seed", seed), passes=passes,
                                     x_dtype=_DT[x_dtype], prec=self.PRECS[prec],
                                     flags=(N.TT_FLAG_DIFF if diff else 0) |
-                                    (N.TT_FLAG_ONESIDED if one_sided else 0))
+                                    (N.TT_FLAG_ONESIDED if one_sided else 0) |
+                                    (N.TT_FLAG_KR if drm == "kr" else 0))
         h = C.c_void_p()
         if batch is None:
             N.check(L.tt_sketch_plan(C.byref(arr[0]), C.byref(h)), "tt_sketch_plan")

@@ -19,6 +19,7 @@
 
 #include "internal.cuh"
 #include "philox.cuh"
+#include "testmat.cuh"
 
 namespace tts {
 
@@ -631,6 +632,8 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevItem& it = ditems(wsb)[item];
   const DevSketch& sp = dsk(wsb)[it.basis_of_k[it.mbk]];
+  // the middle test matrix is the one the least-squares sketch used
+  const DevSketch* kr_mid = dsk(wsb)[it.mid_sk].kr_nm ? &dsk(wsb)[it.mid_sk] : nullptr;
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.mbk];
   const int l = it.lmid;
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(kThreads) mid_b_kernel_f64(char* wsb, int item
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
       double z[4];
-      normals4_f64(it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q, z);
+      tm_quad_f64(wsb, kr_mid, it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q, z);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = z[t];

@@ -62,6 +62,16 @@ struct DevSketch {
                        // this sketch's staged test-matrix rows, -1: regenerated per tile
   int64_t sp_tab;      // small-plane kernel: byte offset of this sketch's staged
                        // test-matrix rows (BF16), -1 when it is generated per plane
+  // ---- Khatri-Rao test matrix (TT_FLAG_KR; kr_nm = 0: dense Gaussian).  The
+  // test-matrix row runs over kr_nm modes (kr_mode0, kr_mode0 + 1, ...; the
+  // first fastest); its entry is the product of one row of each mode's
+  // Gaussian factor, staged per call in the workspace: factor t is kr_n[t] x
+  // kr_lp elements (FP64 for FP64 plans, FP32 otherwise) at byte offset
+  // kr_tab + kr_off[t] * element size.
+  int kr_nm, kr_mode0, kr_lp, kr_pad_;
+  int64_t kr_tab;
+  int64_t kr_n[TT_MAXD];
+  int64_t kr_off[TT_MAXD];
 };
 
 struct DevItem {
@@ -166,8 +176,8 @@ bool use_sp_kernel(const Plan& P, int item, int64_t count);
 // j < lpad, at element (key nr + r) lpad + j of tab (BF16, or FP32 rounded to
 // TF32 when tf), rows as the sketch's test matrix numbers them for the slab
 // starting at `first` (column side) or for plane key (row side).
-cudaError_t launch_rows_table(const DevSketch& d, uint64_t seed, int64_t first, int64_t n1, int nr, int lpad,
-                              int64_t nkeys, char* tab, bool tf, cudaStream_t st);
+cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint64_t seed, int64_t first, int64_t n1,
+                              int nr, int lpad, int64_t nkeys, char* tab, bool tf, cudaStream_t st);
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st);
 bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out, int t3max = 4);
@@ -190,6 +200,7 @@ int64_t batched_tiles_f64(int64_t W, int64_t n1, int64_t cnt, int ta);
 int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int ta);
 cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
 cudaError_t launch_batch_zero(const Plan& P, void* ws, cudaStream_t st);
+cudaError_t launch_kr_tables(const Plan& P, int item, void* ws, cudaStream_t st);
 cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
 
 int device_sm_count();

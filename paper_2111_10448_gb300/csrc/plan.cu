@@ -120,6 +120,8 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   it.d = d;
   it.sided1 = (q.flags & TT_FLAG_ONESIDED) ? 1 : 0;
   if (it.sided1 && ((q.flags & TT_FLAG_DIFF) || !single)) return TT_ERR_UNSUPPORTED;
+  const bool kr = (q.flags & TT_FLAG_KR) != 0;
+  if (kr && !single) return TT_ERR_UNSUPPORTED;
   // split: d* = ceil(d/2) (two-sided); one-sided puts every basis on the column side
   it.ds = it.sided1 ? d - 1 : (d + 1) / 2;
   it.mbk = it.ds;
@@ -191,6 +193,29 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     for (int k = ds; k < d; ++k) it.basis_of_k[k] = add(SK_ROW, k, 1);
   }
   it.nsk = (int)P.sketches.size() - it.sk0;
+  // Khatri-Rao test matrices: one Gaussian factor per mode of each sketch's
+  // rows (column sketch k: modes k+1..d; row sketch k: modes 1..k).  Factor
+  // rows are padded to the widest sketch of the item rounded up to 16, the
+  // widest column range any kernel reads (entries past a sketch's width are
+  // zero).
+  int kr_lp = 0;
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) kr_lp = std::max(kr_lp, (P.sketches[si].width + 15) / 16 * 16);
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
+    DevSketch& s = P.sketches[si];
+    s.kr_nm = 0;
+    if (!kr) continue;
+    s.kr_mode0 = s.type == SK_COL ? s.k + 1 : 1;
+    s.kr_nm = s.type == SK_COL ? d - s.k : s.k;
+    s.kr_lp = kr_lp;
+    int64_t elems = 0;
+    for (int t = 0; t < s.kr_nm; ++t) {
+      s.kr_n[t] = it.n[s.kr_mode0 - 1 + t];
+      s.kr_off[t] = elems;
+      elems += s.kr_n[t] * s.kr_lp;
+    }
+    const int64_t esz = q.prec == TT_PREC_FP64 ? 8 : 4;
+    s.kr_tab = ws.take((elems * esz + 7) / 8) * 8;
+  }
 
   // TSQR trees of the basis sketches
   for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
@@ -527,7 +552,8 @@ static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(base + s.off, 0, sizeof(double) * s.rows * s.width, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  return TT_OK;
+  // Khatri-Rao factors of the call (every later kernel of the call reads them)
+  return cuda_status(launch_kr_tables(P, item, ws, st));
 }
 
 static tt_status accumulate(Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,

@@ -13,6 +13,7 @@
 
 #include "internal.cuh"
 #include "philox.cuh"
+#include "testmat.cuh"
 
 namespace tts {
 const DevSketch* plan_sketches_host(const Plan* p);
@@ -25,7 +26,8 @@ constexpr int kThreads = 256;
 
 struct SkArg {
   int64_t rows, off, wdiv, hstride;
-  int type, width, sid, pad_;
+  int type, width, sid;
+  int kr;  // global sketch index when the test matrix is Khatri-Rao, -1: dense
 };
 
 struct F64Args {
@@ -82,7 +84,7 @@ __device__ void f64_tile(const F64Args& a, int64_t item, double* smem) {
                                 ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
                                 : (uint64_t)((a0 + r) + a.n1 * wlo);
       double z[4];
-      normals4_f64(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q, z);
+      tm_quad_f64(a.ws, kr_of(a.ws, sk.kr), a.seed, (uint32_t)sk.sid, grow, (uint32_t)q, z);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (4 * q + t < l) Gs[r * LDG + 4 * q + t] = z[t];
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) sketch_f64_batched_kernel(const Batc
           sa.nsk = it.nsk;
           for (int s = 0; s < it.nsk; ++s) {
             const DevSketch& d = sks[it.sk0 + s];
-            sa.sk[s] = SkArg{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, 0};
+            sa.sk[s] = SkArg{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, -1};
           }
         }
         __syncthreads();
@@ -208,7 +210,7 @@ cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t fi
   int lmax = 1;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
-    a.sk[s] = SkArg{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, 0};
+    a.sk[s] = SkArg{d.rows, d.off, d.wdiv, d.hstride, d.type, d.width, d.stream_id, d.kr_nm ? it.sk0 + s : -1};
     lmax = d.width > lmax ? d.width : lmax;
   }
   const size_t smem = f64_smem<kTA, kTB>(lmax);

@@ -10,6 +10,7 @@
 
 #include "internal.cuh"
 #include "philox.cuh"
+#include "testmat.cuh"
 
 namespace tts {
 
@@ -41,7 +42,10 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
   __shared__ double Gs[CH * (TT_MAXL + 1)];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
-  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.mbk]];
+  const DevSketch* sks = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
+  const DevSketch& sp = sks[it.basis_of_k[it.mbk]];
+  // the middle test matrix is the one the least-squares sketch used
+  const DevSketch* kr_mid = sks[it.mid_sk].kr_nm ? &sks[it.mid_sk] : nullptr;
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.mbk];
   const int l = it.lmid;
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
     const int nq = (l + 3) / 4;
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
-      const float4 z4 = normals4_f32(it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q);
+      const float4 z4 = tm_quad_f32(wsb, kr_mid, it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q);
       const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -135,7 +139,8 @@ constexpr int gThreads = 256;
 struct SkArgM {
   int64_t rows, off, wdiv, hstride;
   int64_t tab;  // byte offset (from the workspace base) of the staged test-matrix rows, -1: none
-  int type, width, sid, pad_;
+  int type, width, sid;
+  int kr;       // global sketch index when the test matrix is Khatri-Rao, -1: dense
 };
 
 struct MixArgs {
@@ -281,7 +286,7 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
           const int r = o % nr, q = o / nr;
           const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
                                     : (uint64_t)((a0 + r) + a.n1 * wlo);
-          const float4 z4 = normals4_f32(a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
+          const float4 z4 = tm_quad_f32(a.ws, kr_of(a.ws, sk.kr), a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
           const float z[4] = {z4.x, z4.y, z4.z, z4.w};
           if (bf) {
             float zz[4];
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const Batc
           sa.prec = it.prec;
           for (int s = 0; s < it.nsk; ++s) {
             const DevSketch& d = sks[it.sk0 + s];
-            sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, 0};
+            sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, -1};
           }
         }
         __syncthreads();
@@ -471,7 +476,8 @@ constexpr int kMaxChainL = 256;                   // accumulating MMAs per L slo
 struct SkTc {
   int64_t rows, off, wdiv, hstride;
   int64_t tab;  // byte offset of the staged blocks in the workspace, -1: generated per plane
-  int sid, pad_;
+  int sid;
+  int kr;       // global sketch index when the test matrix is Khatri-Rao, -1: dense
 };
 
 struct TcArgs {
@@ -865,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       int64_t row0, rstep;
       uint32_t dst0, sid;
       int n0;
+      const DevSketch* kr;  // Khatri-Rao record, nullptr: dense stream
     };
     auto block_state = [&](int bi, int64_t w, int64_t kLp, int64_t kRp, int buf) {
       Blk bs;
@@ -879,6 +886,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
                         : blk * 128 + g.n1 * row_key(g, sk, w, kLp);
       bs.rstep = colside ? sk.hstride : 1;
       bs.sid = (uint32_t)sk.sid;
+      bs.kr = kr_of(g.ws, sk.kr);
       bs.n0 = sn * ell;
       bs.dst0 = sB + (buf * kBBlks + (colside ? blk : 2 + blk)) * kBBlkB;
       return bs;
@@ -924,8 +932,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
             for (int u = u_beg; u < u_end; ++u) {
               const int k = 2 * rp;  // row of the block (i_d or i_1 offset)
               const int64_t row = bs.row0 + bs.rstep * k;
-              const float4 ra = normals4_f32(g.seed, bs.sid, (uint64_t)row, (uint32_t)nq);
-              const float4 rb = normals4_f32(g.seed, bs.sid, (uint64_t)(row + bs.rstep), (uint32_t)nq);
+              const float4 ra = tm_quad_f32(g.ws, bs.kr, g.seed, bs.sid, (uint64_t)row, (uint32_t)nq);
+              const float4 rb = tm_quad_f32(g.ws, bs.kr, g.seed, bs.sid, (uint64_t)(row + bs.rstep), (uint32_t)nq);
               const int n0 = bs.n0 + 4 * nq;  // a multiple of 4: one core matrix holds n0 .. n0 + 3
               const uint32_t dst = bs.dst0 + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
               st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
@@ -1181,7 +1189,7 @@ __global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, 
     const int64_t v = rest / H;
     const int64_t k = 128 * h + 8 * kg + r8;
     const uint64_t row = colside ? (uint64_t)(v + sk.hstride * (g.first + k)) : (uint64_t)(k + g.n1 * v);
-    const float4 z = normals4_f32(g.seed, (uint32_t)sk.sid, row, (uint32_t)q);
+    const float4 z = tm_quad_f32(g.ws, kr_of(g.ws, sk.kr), g.seed, (uint32_t)sk.sid, row, (uint32_t)q);
     const float zz[4] = {z.x, z.y, z.z, z.w};
     char* blk = tab + (v * H + h) * blkB;
 #pragma unroll
@@ -1208,7 +1216,7 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
     if (d.width != ell) return false;
-    SkTc t{d.rows, d.off, d.wdiv, d.hstride, -1, d.stream_id, 0};
+    SkTc t{d.rows, d.off, d.wdiv, d.hstride, -1, d.stream_id, d.kr_nm ? it.sk0 + s : -1};
     if (d.type == SK_COL) {
       if (nL >= 4) return false;
       g.col[nL++] = t;
@@ -1296,13 +1304,14 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
 namespace {
 
 template <typename Real>
-__device__ __forceinline__ void test_row(int prec, uint64_t seed, int sid, uint64_t row, int l, Real* out) {
+__device__ __forceinline__ void test_row(const void* wsb, const DevSketch* kr, int prec, uint64_t seed, int sid,
+                                         uint64_t row, int l, Real* out) {
   for (int q = 0; q < (l + 3) / 4; ++q) {
     double z[4];
     if (prec == TT_PREC_FP64) {
-      normals4_f64(seed, (uint32_t)sid, row, (uint32_t)q, z);
+      tm_quad_f64(wsb, kr, seed, (uint32_t)sid, row, (uint32_t)q, z);
     } else {
-      const float4 f = normals4_f32(seed, (uint32_t)sid, row, (uint32_t)q);
+      const float4 f = tm_quad_f32(wsb, kr, seed, (uint32_t)sid, row, (uint32_t)q);
       z[0] = round_prec(f.x, prec);
       z[1] = round_prec(f.y, prec);
       z[2] = round_prec(f.z, prec);
@@ -1318,7 +1327,9 @@ __global__ void pbar_ls_kernel(char* wsb, int item, const int* ranks) {
   __shared__ double Bb[TT_MAXL * TT_MAXL];
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + 256);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
-  const DevSketch& sp = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches)[it.basis_of_k[it.ds]];
+  const DevSketch* sks = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
+  const DevSketch& sp = sks[it.basis_of_k[it.ds]];
+  const DevSketch* kr_mid = sks[it.mid_sk].kr_nm ? &sks[it.mid_sk] : nullptr;
   double* ws = reinterpret_cast<double*>(wsb);
   const int r = ranks[it.rank_off + it.ds];
   const int rp = it.rpad[it.ds];
@@ -1328,7 +1339,7 @@ __global__ void pbar_ls_kernel(char* wsb, int item, const int* ranks) {
   double* Pb = ws + it.off_qbar[it.ds];
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < sp.rows; v += (int64_t)gridDim.x * blockDim.x) {
     double om[TT_MAXL];
-    test_row(it.prec, it.seed, it.ds, (uint64_t)v, l, om);
+    test_row(wsb, kr_mid, it.prec, it.seed, it.ds, (uint64_t)v, l, om);
     for (int c = 0; c < r; ++c) {
       double acc = 0.0;
       for (int j = 0; j < l; ++j) acc += om[j] * Bb[c + rp * j];
@@ -1366,6 +1377,7 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
     Real acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int s = 0; s < it.nsk; ++s) {
       const DevSketch& sk = S[it.sk0 + s];
+      const DevSketch* kr = sk.kr_nm ? &sk : nullptr;
       const int l = sk.width;
       const int64_t wlo = w % sk.wdiv, whi = w / sk.wdiv;
       const double* bar = ws + it.off_sbar[s];
@@ -1376,10 +1388,10 @@ __global__ void __launch_bounds__(256) sketch_adjoint_kernel(char* wsb, int item
           Lf[a * LD + j] = (Real)bar[(a0 + a + n1 * wlo) + sk.rows * j];
         }
         for (int b = tid; b < tb; b += blockDim.x)
-          test_row(it.prec, it.seed, sk.stream_id, (uint64_t)(whi + sk.hstride * (b0 + b)), l, Rf + b * LD);
+          test_row(wsb, kr, it.prec, it.seed, sk.stream_id, (uint64_t)(whi + sk.hstride * (b0 + b)), l, Rf + b * LD);
       } else {
         for (int a = tid; a < ta; a += blockDim.x)
-          test_row(it.prec, it.seed, sk.stream_id, (uint64_t)((a0 + a) + n1 * wlo), l, Lf + a * LD);
+          test_row(wsb, kr, it.prec, it.seed, sk.stream_id, (uint64_t)((a0 + a) + n1 * wlo), l, Lf + a * LD);
         for (int o = tid; o < tb * l; o += blockDim.x) {
           const int b = o % tb, j = o / tb;
           Rf[b * LD + j] = (Real)bar[(whi + sk.hstride * (b0 + b)) + sk.rows * j];
@@ -1456,13 +1468,14 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   a.prec = it.prec;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
-    a.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, 0};
+    a.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, d.kr_nm ? it.sk0 + s : -1};
     if (d.gen_tab >= 0 && it.gentab_doubles > 0) {
       // stage the sketch's rows for this call: the slab's i_d (column side) or i_1 (row side)
       const int lpad = (d.width + 15) / 16 * 16;
       const bool col = d.type == SK_COL;
       a.sk[s].tab = it.off_gentab * 8 + d.gen_tab;
-      cudaError_t e = launch_rows_table(d, it.seed, first, a.n1, col ? (int)count : (int)a.n1, lpad,
+      cudaError_t e = launch_rows_table(d, it.sk0 + s, (const char*)ws, it.seed, first, a.n1,
+                                        col ? (int)count : (int)a.n1, lpad,
                                         col ? it.W / d.wdiv : d.wdiv, (char*)ws + a.sk[s].tab,
                                         it.prec == TT_PREC_TF32, st);
       if (e != cudaSuccess) return e;

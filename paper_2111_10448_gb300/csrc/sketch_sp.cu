@@ -39,6 +39,7 @@
 
 #include "internal.cuh"
 #include "philox.cuh"
+#include "testmat.cuh"
 
 namespace tts {
 
@@ -70,6 +71,7 @@ struct SpSk {
   int col, sid, nslot, slot0, lflush;     // lflush: flushed on the column-side schedule
   int dep;                                // output rows depend on the plane (through kL or kR)
   int ell;                                // this sketch's width (<= the padded width of the launch)
+  int kr;                                 // global sketch index of a Khatri-Rao test matrix, -1: dense
 };
 
 struct SpArgs {
@@ -131,8 +133,9 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
 // (first + r) (column side) or r + n1 key (row side) rounded to BF16 (2-byte
 // elements) or TF32 (`tf`: 4-byte FP32 words), zero for j >= l.  Threads
 // tid0, tid0 + nthr, ... of the caller take the entries.
-__device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
-                              int64_t nkeys, char* tab, int64_t tid0, int64_t nthr, bool tf) {
+__device__ void sp_table_fill(const char* wsb, const SpSk& s, uint64_t seed, int64_t first, int64_t n1, int nr,
+                              int ell, int lpad, int64_t nkeys, char* tab, int64_t tid0, int64_t nthr, bool tf) {
+  const DevSketch* kr = kr_of(wsb, s.kr);
   const int qpr = lpad / 4;
   const int64_t total = nkeys * nr * qpr;
   for (int64_t e = tid0; e < total; e += nthr) {
@@ -142,7 +145,7 @@ __device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64
     const int64_t key = rest / nr;
     const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (first + r)) : (uint64_t)(r + n1 * key);
     float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (4 * q < ell) z = normals4_f32(seed, (uint32_t)s.sid, row, (uint32_t)q);
+    if (4 * q < ell) z = tm_quad_f32(wsb, kr, seed, (uint32_t)s.sid, row, (uint32_t)q);
     const int64_t el = (key * nr + r) * lpad + 4 * q;
     if (tf) {
       *reinterpret_cast<float4*>(tab + el * 4) =
@@ -156,10 +159,10 @@ __device__ void sp_table_fill(const SpSk& s, uint64_t seed, int64_t first, int64
   }
 }
 
-__global__ void sp_table_kernel(SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell, int lpad,
-                                int64_t nkeys, char* tab, int tf) {
-  sp_table_fill(s, seed, first, n1, nr, ell, lpad, nkeys, tab, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                (int64_t)gridDim.x * blockDim.x, tf != 0);
+__global__ void sp_table_kernel(const char* wsb, SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell,
+                                int lpad, int64_t nkeys, char* tab, int tf) {
+  sp_table_fill(wsb, s, seed, first, n1, nr, ell, lpad, nkeys, tab,
+                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, tf != 0);
 }
 
 // Launch arguments of one item (the whole last mode when count = n_d), shared
@@ -195,6 +198,7 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
     k.col = d.type == SK_COL ? 1 : 0;
     k.sid = d.stream_id;
     k.ell = d.width;
+    k.kr = d.kr_nm ? it.sk0 + s : -1;
     const bool per_plane_rows = k.col ? d.wdiv > 1 : d.wdiv < it.W;
     k.dep = per_plane_rows ? 1 : 0;
     k.nslot = per_plane_rows ? (k.col ? g.T2 : g.T3) : 1;
@@ -327,7 +331,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
               qq[h] = c - rr[h] * g.nq;
               const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + rr[h]))
                                          : (uint64_t)(rr[h] + g.n1 * key);
-              z[h] = normals4_f32(g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
+              z[h] = tm_quad_f32(g.wsb, kr_of(g.wsb, s.kr), g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -597,9 +601,10 @@ __global__ void sp_table_batched_kernel(char* wsb) {
     k.hstride = d.hstride;
     k.col = d.type == SK_COL ? 1 : 0;
     k.sid = d.stream_id;
+    k.kr = -1;  // batched plans draw dense test matrices
     const int nr = k.col ? (int)it.n[it.d - 1] : (int)it.n[0];
     const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
-    sp_table_fill(k, it.seed, 0, it.n[0], nr, d.width, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
+    sp_table_fill(wsb, k, it.seed, 0, it.n[0], nr, d.width, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
                   (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
                   it.prec == TT_PREC_TF32);
   }
@@ -654,17 +659,18 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, 
 
 }  // namespace sp
 
-cudaError_t launch_rows_table(const DevSketch& d, uint64_t seed, int64_t first, int64_t n1, int nr, int lpad,
-                              int64_t nkeys, char* tab, bool tf, cudaStream_t st) {
+cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint64_t seed, int64_t first, int64_t n1,
+                              int nr, int lpad, int64_t nkeys, char* tab, bool tf, cudaStream_t st) {
   sp::SpSk k;
   memset(&k, 0, sizeof(k));
   k.hstride = d.hstride;
   k.col = d.type == SK_COL ? 1 : 0;
   k.sid = d.stream_id;
+  k.kr = d.kr_nm ? gsk : -1;
   const int64_t total = nkeys * nr * (lpad / 4);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count()));
   count_launch();
-  sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, seed, first, n1, nr, d.width, lpad, nkeys, tab, tf ? 1 : 0);
+  sp::sp_table_kernel<<<blocks, 256, 0, st>>>(wsb, k, seed, first, n1, nr, d.width, lpad, nkeys, tab, tf ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -705,7 +711,7 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
     const int64_t total = nkeys * nr * (lpad / 4);
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count());
     count_launch();
-    sp::sp_table_kernel<<<blocks, 256, 0, st>>>(k, g.seed, first, g.n1, nr, k.ell, lpad, nkeys,
+    sp::sp_table_kernel<<<blocks, 256, 0, st>>>(g.wsb, k, g.seed, first, g.n1, nr, k.ell, lpad, nkeys,
                                                 g.wsb + g.tab0 + k.tab, tf ? 1 : 0);
   }
   const int64_t nblocks = g.tilesL * g.tilesR;

@@ -1,0 +1,95 @@
+// Test-matrix entries as every kernel of the library regenerates them: the
+// dense Gaussian stream of philox.cuh, or (TT_FLAG_KR) the Khatri-Rao product
+// of per-mode Gaussian factors (Sec. 3.2, eq. (sketch_orig)) whose factors
+// were staged in the workspace at the start of the call (krdrm.cu).
+//
+// A Khatri-Rao row index is the column-major multi-index over the sketch's
+// factor modes (first mode fastest); its entry j is the product
+// F_0(i_0, j) F_1(i_1, j) ... taken in that order.  The FP32 product uses
+// explicitly rounded multiplies, so every kernel computes the same bits.
+#pragma once
+#include <cstdint>
+
+#include "internal.cuh"
+#include "philox.cuh"
+
+namespace tts {
+
+// The device sketch table of a workspace (uploaded with the plan tables).
+__device__ __forceinline__ const DevSketch* ws_sketches(const void* wsb) {
+  const char* b = reinterpret_cast<const char*>(wsb);
+  const DevTables& T = *reinterpret_cast<const DevTables*>(b + 256);
+  return reinterpret_cast<const DevSketch*>(b + T.off_sketches);
+}
+
+// Index of mode t of the row (and the rest of the row for the next modes).
+__device__ __forceinline__ int64_t kr_digit(uint64_t& row, int64_t n, bool last) {
+  if (last) return (int64_t)row;
+  if (row < 0x100000000ull && n < 0x100000000ll) {
+    const uint32_t r = (uint32_t)row, nn = (uint32_t)n;
+    const uint32_t q = r / nn;
+    row = q;
+    return (int64_t)(r - q * nn);
+  }
+  const uint64_t q = row / (uint64_t)n;
+  const int64_t i = (int64_t)(row - q * (uint64_t)n);
+  row = q;
+  return i;
+}
+
+// Columns 4q..4q+3 of Khatri-Rao row `row` (FP32 factors, FP32 product).
+__device__ __forceinline__ float4 kr_quad_f32(const void* wsb, const DevSketch& s, uint64_t row, uint32_t q) {
+  const float* tab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
+  float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
+  for (int t = 0; t < s.kr_nm; ++t) {
+    const int64_t i = kr_digit(row, s.kr_n[t], t + 1 == s.kr_nm);
+    const float4 f = *reinterpret_cast<const float4*>(tab + s.kr_off[t] + i * s.kr_lp + 4 * q);
+    if (t == 0) {
+      v = f;
+    } else {
+      v.x = __fmul_rn(v.x, f.x);
+      v.y = __fmul_rn(v.y, f.y);
+      v.z = __fmul_rn(v.z, f.z);
+      v.w = __fmul_rn(v.w, f.w);
+    }
+  }
+  return v;
+}
+
+// Same in FP64 (FP64 factors and product).
+__device__ __forceinline__ void kr_quad_f64(const void* wsb, const DevSketch& s, uint64_t row, uint32_t q,
+                                            double z[4]) {
+  const double* tab = reinterpret_cast<const double*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
+  for (int t = 0; t < s.kr_nm; ++t) {
+    const int64_t i = kr_digit(row, s.kr_n[t], t + 1 == s.kr_nm);
+    const double2* f = reinterpret_cast<const double2*>(tab + s.kr_off[t] + i * s.kr_lp + 4 * q);
+    const double2 a = f[0], b = f[1];
+    if (t == 0) {
+      z[0] = a.x; z[1] = a.y; z[2] = b.x; z[3] = b.y;
+    } else {
+      z[0] = __dmul_rn(z[0], a.x);
+      z[1] = __dmul_rn(z[1], a.y);
+      z[2] = __dmul_rn(z[2], b.x);
+      z[3] = __dmul_rn(z[3], b.y);
+    }
+  }
+}
+
+// The quad a kernel uses: kr = the sketch's device record when its test
+// matrix is Khatri-Rao, nullptr for the dense stream.
+__device__ __forceinline__ float4 tm_quad_f32(const void* wsb, const DevSketch* kr, uint64_t seed, uint32_t sid,
+                                              uint64_t row, uint32_t q) {
+  if (kr) return kr_quad_f32(wsb, *kr, row, q);
+  return normals4_f32(seed, sid, row, q);
+}
+__device__ __forceinline__ void tm_quad_f64(const void* wsb, const DevSketch* kr, uint64_t seed, uint32_t sid,
+                                            uint64_t row, uint32_t q, double z[4]) {
+  if (kr) kr_quad_f64(wsb, *kr, row, q, z);
+  else normals4_f64(seed, sid, row, q, z);
+}
+// Device record of sketch gsk of the workspace, or nullptr (gsk < 0: dense).
+__device__ __forceinline__ const DevSketch* kr_of(const void* wsb, int gsk) {
+  return gsk >= 0 ? ws_sketches(wsb) + gsk : nullptr;
+}
+
+}  // namespace tts

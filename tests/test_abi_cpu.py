@@ -330,3 +330,25 @@ def test_batched_plans_stage_no_generic_rows():
         return w
 
     assert ws_of(N.TT_PREC_BF16) == ws_of(N.TT_PREC_FP64) == ws_of(N.TT_PREC_TF32)
+
+
+def test_khatri_rao_plans():
+    """TT_FLAG_KR: single-problem plans only; the workspace grows by the staged
+    factors (sum over sketches of the factor sizes of their modes)."""
+    L = N.lib()
+    base = N.make_problem([16] * 4, ranks=[1, 4, 4, 4, 1], p=5, seed=1)
+    krq = N.make_problem([16] * 4, ranks=[1, 4, 4, 4, 1], p=5, seed=1, flags=N.TT_FLAG_KR)
+    sizes = []
+    for q in (base, krq):
+        h = C.c_void_p()
+        N.check(L.tt_sketch_plan(C.byref(q), C.byref(h)), "plan")
+        ws = C.c_size_t()
+        N.check(L.tt_plan_sizes(h, C.byref(ws), None, None), "sizes")
+        sizes.append(ws.value)
+        L.tt_plan_destroy(h)
+    # S_1: modes 2..4, S_2: 3..4, R_2: 1..2, R_3: 1..3; width 9, factor rows of 16
+    factors = (3 + 2 + 2 + 3) * 16 * 16 * 8
+    assert factors <= sizes[1] - sizes[0] <= factors + 4 * 256
+    arr = (N.tt_problem * 2)(krq, krq)
+    h = C.c_void_p()
+    assert L.tt_sketch_plan_batched(arr, 2, C.byref(h)) == N.TT_ERR_UNSUPPORTED

@@ -698,3 +698,17 @@ def test_kr_streaming_equals_one_shot():
     slabs = [(a, c, x[a * Nd1:(a + c) * Nd1]) for a, c in [(4, 3), (0, 2), (2, 2)]]
     st = P.pstt2_stream(slabs, dims, ranks=[1, 3, 3, 3, 1], p=4, seed=2, drm="kr")
     np.testing.assert_allclose(tt.tt_full(st["cores"]), tt.tt_full(full["cores"]), atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_kr_one_sided_exact_recovery(d):
+    """Algorithm 2 and PSTT-onepass with Khatri-Rao DRMs (the paper's
+    substitute for the dense Phi_j) reproduce a random TT of lower rank."""
+    dims = [5 + (k % 2) for k in range(d)]
+    r = [1] + [2 + (k % 2) for k in range(d - 1)] + [1]
+    x = ti.random_tt(dims, r, seed=d + 40)
+    tgt = [1] + [4] * (d - 1) + [1]
+    from oracle import pstt as PS
+    for fn in (PS.pstt_onepass, PS.pstt):
+        o = fn(x, dims, ranks=tgt, p=3, seed=d + 50, drm="kr")
+        assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
