@@ -37,7 +37,8 @@ factor row coincides with a row of a dense test matrix), and the entry of the
 product at the column-major multi-index (i_{m_1}, i_{m_2}, ...) (first listed
 mode fastest, modes in increasing order) is
     F_{m_1}(i_{m_1}, j) * F_{m_2}(i_{m_2}, j) * ...
-multiplied in that order.  The paper writes the product Psi_d (.) ... (.)
+(rounding order: increasing modes for a column sketch's Omega_k, decreasing
+for a row sketch's Psi_k; in FP64 the order changes the last bit only).  The paper writes the product Psi_d (.) ... (.)
 Psi_{j+1} for the column space of X_j; with the Kronecker convention of the
 Khatri-Rao product (the last factor's index fastest) its rows run over
 (i_{j+1}, ..., i_d) column-major, the column index of X_j.
@@ -123,16 +124,23 @@ def kr_factor(seed, stream, mode, n, ncols):
     return gaussian(seed, stream, np.arange(n, dtype=np.uint64) + base, ncols)
 
 
-def kr_test_matrix(seed, stream, modes, sizes, ncols):
+def kr_test_matrix(seed, stream, modes, sizes, ncols, decreasing=False):
     """The Khatri-Rao test matrix over `modes` (increasing, 1-based) of sizes
     `sizes`: prod(sizes) x ncols, row = column-major multi-index with the first
-    mode fastest, entry = product of the factor entries in mode order (FP64).
-    This is the dense form of F_{m_last} (.) ... (.) F_{m_1}."""
+    mode fastest, entry = product of the factor entries (FP64), multiplied in
+    increasing mode order (decreasing=True: decreasing order).  This is the
+    dense form of F_{m_last} (.) ... (.) F_{m_1}."""
+    Fs = [kr_factor(seed, stream, m, n, ncols) for m, n in zip(modes, sizes)]
+    if not decreasing:
+        out = np.ones((1, ncols))
+        for F in Fs:
+            # rows of the product so far are the faster index: new row = r + R i
+            out = (out[None, :, :] * F[:, None, :]).reshape(-1, ncols)
+        return out
     out = np.ones((1, ncols))
-    for m, n in zip(modes, sizes):
-        F = kr_factor(seed, stream, m, n, ncols)
-        # rows of the product so far are the faster index: new row = r + R i
-        out = (out[None, :, :] * F[:, None, :]).reshape(-1, ncols)
+    for F in reversed(Fs):
+        # the product so far runs over the slower modes: new row = i + n r
+        out = (F[None, :, :] * out[:, None, :]).reshape(-1, ncols)
     return out
 
 

@@ -82,7 +82,8 @@ def psi(seed, dims, k, l, drm='gauss'):
     """Psi_k (N_k x l, FP64): the left test matrix of X_k."""
     N = prods(dims)
     if drm == 'kr':
-        return philox.kr_test_matrix(seed, philox.STREAM_PSI + k, list(range(1, k + 1)), dims[:k], l)
+        return philox.kr_test_matrix(seed, philox.STREAM_PSI + k, list(range(1, k + 1)), dims[:k], l,
+                                     decreasing=True)
     return philox.test_matrix(seed, philox.STREAM_PSI + k, N[k], l)
 
 

@@ -64,14 +64,19 @@ struct DevSketch {
                        // test-matrix rows (BF16), -1 when it is generated per plane
   // ---- Khatri-Rao test matrix (TT_FLAG_KR; kr_nm = 0: dense Gaussian).  The
   // test-matrix row runs over kr_nm modes (kr_mode0, kr_mode0 + 1, ...; the
-  // first fastest); its entry is the product of one row of each mode's
-  // Gaussian factor, staged per call in the workspace: factor t is kr_n[t] x
-  // kr_lp elements (FP64 for FP64 plans, FP32 otherwise) at byte offset
-  // kr_tab + kr_off[t] * element size.
-  int kr_nm, kr_mode0, kr_lp, kr_pad_;
+  // first fastest, kr_stride[t] = product of the sizes of the faster ones);
+  // its entry is the product of one row of each mode's Gaussian factor,
+  // staged per call in the workspace: factor t is kr_n[t] x kr_lp elements
+  // (FP64 for FP64 plans, FP32 otherwise) at byte offset kr_tab + kr_off[t] *
+  // element size.  The factors are multiplied in increasing mode order for a
+  // column sketch and in decreasing order for a row sketch (kr_dec), so that
+  // the mode a plane's rows vary in (the last for a column sketch, the first
+  // for a row sketch) is always the final factor.
+  int kr_nm, kr_mode0, kr_lp, kr_dec;
   int64_t kr_tab;
   int64_t kr_n[TT_MAXD];
   int64_t kr_off[TT_MAXD];
+  int64_t kr_stride[TT_MAXD];
 };
 
 struct DevItem {
@@ -172,6 +177,9 @@ cudaError_t launch_sketch_mixed(const Plan& P, int item, const void* X, int64_t 
 bool mixed_tc_supported(const Plan& P, int item, int64_t count);
 bool use_tc_kernel(const Plan& P, int item, int64_t count);
 bool use_sp_kernel(const Plan& P, int item, int64_t count);
+bool use_slab_kernel(const Plan& P, int item, int64_t count);
+cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                               cudaStream_t st);
 // Fill the staged test-matrix rows of one sketch: entry (key, r, j), r < nr,
 // j < lpad, at element (key nr + r) lpad + j of tab (BF16, or FP32 rounded to
 // TF32 when tf), rows as the sketch's test matrix numbers them for the slab

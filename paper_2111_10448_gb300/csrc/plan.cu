@@ -207,10 +207,13 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     s.kr_mode0 = s.type == SK_COL ? s.k + 1 : 1;
     s.kr_nm = s.type == SK_COL ? d - s.k : s.k;
     s.kr_lp = kr_lp;
-    int64_t elems = 0;
+    s.kr_dec = s.type == SK_ROW ? 1 : 0;
+    int64_t elems = 0, stride = 1;
     for (int t = 0; t < s.kr_nm; ++t) {
       s.kr_n[t] = it.n[s.kr_mode0 - 1 + t];
       s.kr_off[t] = elems;
+      s.kr_stride[t] = stride;
+      stride *= s.kr_n[t];
       elems += s.kr_n[t] * s.kr_lp;
     }
     const int64_t esz = q.prec == TT_PREC_FP64 ? 8 : 4;
@@ -633,7 +636,7 @@ int tt_sketch_kernel_kind(tt_plan_t plan, int64_t count_last) {
   Plan* P = as_plan(plan);
   if (!P || P->items.empty()) return -1;
   if (P->items[0].prec == TT_PREC_FP64) return 0;
-  if (use_tc_kernel(*P, 0, count_last)) return 2;
+  if (use_tc_kernel(*P, 0, count_last) || use_slab_kernel(*P, 0, count_last)) return 2;
   return use_sp_kernel(*P, 0, count_last) ? 3 : 1;
 }
 

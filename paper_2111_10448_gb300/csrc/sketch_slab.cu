@@ -1,0 +1,728 @@
+// Slab form of the tcgen05 plane kernel: the fused multi-sketch of one slab of
+// c = 16, 32 or 64 slices of the last mode of a 4-way tensor -- the unit of
+// the paper's single stream over sub-tensors (Sec. 4.2, Algorithm 5; a 1 GiB
+// slab of the 256^4 FP32 tensor is 16 slices).  BF16 with X split into hi +
+// lo, FP32 accumulators in tensor memory, FP64 flush, as the plane kernel.
+//
+// The plane kernel contracts a plane X(:, w, :) (n_1 x slab) over its 128-row
+// quarters of i_4; a slab of 16 slices has no such quarter.  Here G = 128 / c
+// planes that share i_2 (= kL) and have consecutive i_3 (kR) form one
+// super-plane, an n_1 x 128 matrix whose column k = i_4' + c g (i_4' < c the
+// slice within the slab, g < G the plane).  With w_g = kL + n_2 (G kRg + g):
+//  * S_1 (rows i_1, test-matrix rows w_g + n_2 n_3 i_4) and S_2 (rows
+//    i_1 + n_1 kL, rows kR_g + n_3 i_4): D_L = X_sp [B_1 | B_2], M = i_1,
+//    K = k -- both sketches' output rows are the same for every k, so the
+//    super-plane is an ordinary product;
+//  * R_2 (rows kR_g + n_3 i_4, test-matrix rows i_1 + n_1 kL): D_R = X_sp^T C_2,
+//    M = k, K = i_1 -- the test-matrix rows are the same for every k;
+//  * R_3 (rows i_4, test-matrix rows i_1 + n_1 w_g): the test-matrix rows
+//    depend on g, which runs along M, so the product is taken against all G
+//    blocks side by side, D_Y = X_sp^T [C_3(g=0) | ... | C_3(g=G-1)]
+//    (N = G l), and only its diagonal blocks (row group g, column block g) are
+//    kept.  The tensor pipe does G times the R_3 work it needs; it has the
+//    room (the kernel is bound by HBM).
+// Test-matrix blocks: the L block (S_1, S_2; 128 composite rows) and the R_3
+// blocks (128 rows of i_1 x G planes, regenerated for every quarter into a
+// single buffer) come from the RNG warps; the R_2 block comes from a staged
+// table (one per kL, generated once per call).  With dense Gaussian test
+// matrices the R_3 blocks cost l / c normals per entry of X (1 at c = l = 16),
+// which binds the kernel; with Khatri-Rao test matrices (TT_FLAG_KR) an R_3
+// entry is the product of the plane's two fixed factor entries (formed once
+// per quarter) and one row of the mode-1 factor, a few instructions.
+//
+// Accumulators: one L slot per (kL of the tile, i_1 half), kept for runL
+// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block of a
+// tile are double-buffered and flushed after every tile (a tile of
+// T2 x T3 super-planes x H1 quarters gives each at most 256 accumulating MMAs).
+// Warp roles, barriers and bounded waits as in the plane kernel.
+#include <algorithm>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "philox.cuh"
+#include "tc_common.cuh"
+#include "testmat.cuh"
+
+namespace tts {
+
+const DevSketch* plan_sketches_host(const Plan* p);
+
+namespace tc {
+namespace slab {
+
+constexpr int kWarps = 20;
+constexpr int kThreads = kWarps * 32;
+constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 7;
+constexpr int kLBlkB = 4 * kS4;   // L block: 128 rows x N <= 32
+constexpr int kRBlkB = 2 * kS4;   // R_2 block: 128 rows x N <= 16
+constexpr int kYBlkB = 16 * kS4;  // R_3 blocks side by side: 128 rows x N <= 128
+constexpr int kOffL = 2 * kStageB;
+constexpr int kOffR = kOffL + 2 * kLBlkB;
+constexpr int kOffY = kOffR + 4 * kRBlkB;
+constexpr int kOffBar = kOffY + kYBlkB;
+constexpr int kSmemBytes = kOffBar + 256 + 1024;
+constexpr int kTmemY = 0;         // D_Y buffers at columns 0 and 128, then the L slots, then R_2
+constexpr int64_t kTableOffB = 256;
+
+struct SlabArgs {
+  const float* X;
+  double* ws;
+  int* status;
+  int64_t n1, first, W, WL, WR, Nd1;
+  int64_t WRg;             // kR groups: WR / G
+  int64_t tilesL, tilesR;  // tiles of T2 kL values x T3 kR groups
+  uint64_t seed;
+  int H1, T2, T3, ell, c, lc, G;
+  int colL, colR;          // tensor-memory columns of the L slots and of the R_2 buffers
+  int64_t runL;            // tiles of one kL block accumulated in the L slots before a flush
+  uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
+  SkTc col[2], row[2];     // S_1, S_2 | R_2, R_3
+};
+
+struct TileInfo {
+  int64_t kL0, kRg0;
+  int nA, nB;
+};
+__device__ __forceinline__ TileInfo tile_info(const SlabArgs& g, int64_t t) {
+  TileInfo ti;
+  const int64_t tl = t / g.tilesR, tr = t % g.tilesR;  // kL-block-major
+  ti.kL0 = tl * g.T2;
+  ti.kRg0 = tr * g.T3;
+  ti.nA = (int)imin64(g.T2, g.WL - ti.kL0);
+  ti.nB = (int)imin64(g.T3, g.WRg - ti.kRg0);
+  return ti;
+}
+__device__ __forceinline__ int64_t l_group(const SlabArgs& g, int64_t t) {
+  const int64_t tl = t / g.tilesR, tr = t % g.tilesR;
+  return tl * ((g.tilesR + g.runL - 1) / g.runL) + tr / g.runL;
+}
+
+template <int ELL, int C>
+__global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs g) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
+  // barrier indices
+  const int FULL_A = 0, EMPTY_A = 2, FULL_L = 4, EMPTY_L = 6, TAB_FULL = 8, FULL_Y = 10, EMPTY_Y = 11,
+            TML_FULL = 12, TML_EMPTY = 13, TMR_FULL = 14, TMR_EMPTY = 16, DRAIN = 18;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
+  __shared__ SkTc s_col[2], s_row[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+  constexpr int ell = ELL;
+  constexpr int NL = 2 * ELL;
+
+  if (threadIdx.x < 2) {
+    s_col[threadIdx.x] = g.col[threadIdx.x];
+    s_row[threadIdx.x] = g.row[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(bar(FULL_A + s), kProdWarps);
+      mbar_init(bar(EMPTY_A + s), 1);
+      mbar_init(bar(FULL_L + s), kRngWarps);
+      mbar_init(bar(EMPTY_L + s), 1);
+      mbar_init(bar(TAB_FULL + s), 1);
+      mbar_init(bar(TMR_FULL + s), 1);
+      mbar_init(bar(TMR_EMPTY + s), kEpiWarps);
+    }
+    mbar_init(bar(FULL_Y), kRngWarps);
+    mbar_init(bar(EMPTY_Y), 1);
+    mbar_init(bar(TML_FULL), 1);
+    mbar_init(bar(TML_EMPTY), kEpiWarps);
+    mbar_init(bar(DRAIN), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t ntiles_all = g.tilesL * g.tilesR;
+  const int64_t t_beg = ntiles_all * blockIdx.x / gridDim.x;
+  const int64_t ntiles = ntiles_all * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t sA = smem_u32(sm);
+  const uint32_t sL = smem_u32(sm + kOffL);
+  const uint32_t sR = smem_u32(sm + kOffR);
+  const uint32_t sY = smem_u32(sm + kOffY);
+  constexpr int cmask = C - 1;
+  constexpr int lc = C == 16 ? 4 : C == 32 ? 5 : 6;
+  const int64_t gstride = g.n1 * g.WL;  // elements between the planes of a super-plane (kR + 1)
+
+  if (warp >= kProdWarp0 && warp < kProdWarp0 + kProdWarps) {
+    // ------------------------------------------------------------ producers
+    const int pt = threadIdx.x - kProdWarp0 * 32;
+    const int cb1 = pt & 15, rsub = pt >> 4;
+    // composite row k = rsub + 16 m of a quarter: slice k & (c-1) of plane k >> lc
+    auto rowoff = [&](int m) -> int64_t {
+      const int k = rsub + 16 * m;
+      return (int64_t)(k & cmask) * g.Nd1 + (int64_t)(k >> lc) * gstride;
+    };
+    int64_t t = t_beg;
+    int a = 0, b = 0, q = 0;
+    TileInfo ti = tile_info(g, t);
+    auto advance = [&]() {
+      if (++q == g.H1) {
+        q = 0;
+        if (++a == ti.nA) {
+          a = 0;
+          if (++b == ti.nB) {
+            b = 0;
+            t += 1;
+            if (t < ntiles) ti = tile_info(g, t);
+          }
+        }
+      }
+    };
+    auto cursor_src = [&]() -> const float* {
+      if (t >= ntiles) return nullptr;
+      const int64_t w0 = (ti.kL0 + a) + g.WL * ((ti.kRg0 + b) * g.G);
+      return g.X + (q * 128 + cb1 * 8) + g.n1 * w0;
+    };
+    auto prefetch = [&](const float* src) {
+      const int cc = cb1 & 3;
+      const float* line = src - cc * 8;
+      prefetch_l2(line + rowoff(2 * cc));
+      prefetch_l2(line + rowoff(2 * cc + 1));
+    };
+    float4 v[16];
+    auto issue = [&](const float* src) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const float4* p4 = reinterpret_cast<const float4*>(src + rowoff(m));
+        v[2 * m] = __ldcs(p4);
+        v[2 * m + 1] = __ldcs(p4 + 1);
+      }
+    };
+    const float* src0 = cursor_src();
+    bool have = src0 != nullptr;
+    if (have) issue(src0);
+    advance();
+    const float* src1 = cursor_src();
+    if (src1) prefetch(src1);
+    advance();
+    uint32_t qi = 0;
+    while (have && !*abort_flag) {
+      const int st = qi & 1;
+      if (!mbar_wait(bar(EMPTY_A + st), ((qi >> 1) & 1) ^ 1, abort_flag, g.status)) break;
+      const uint32_t tileA = sA + st * kStageB;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k = rsub + 16 * m;
+        const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
+                            v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
+        uint32_t hb[4], lb[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
+          const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
+          lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
+        }
+        const uint32_t off = cb1 * kS1 + (k >> 3) * kS4 + (k & 7) * 16;
+        st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
+        st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(FULL_A + st));
+      ++qi;
+      have = src1 != nullptr;
+      if (have) issue(src1);
+      src1 = cursor_src();
+      if (src1) prefetch(src1);
+      advance();
+    }
+  } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
+    // ------------------------------------------------- test-matrix blocks
+    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..223
+    constexpr int qps = ell / 4;
+    constexpr int upb = 64 * qps;  // 2-row units of one 128-row block
+    // L block: S_1 then S_2, rows k = composite; contiguous unit ranges
+    const int lu_beg = 2 * upb * rt / (kRngWarps * 32), lu_end = 2 * upb * (rt + 1) / (kRngWarps * 32);
+    // R_3 blocks of a quarter: G blocks of 128 rows of i_1
+    const int yn = g.G * upb;
+    const int yu_beg = yn * rt / (kRngWarps * 32), yu_end = yn * (rt + 1) / (kRngWarps * 32);
+    const DevSketch* kr3 = kr_of(g.ws, s_row[1].kr);
+    const DevSketch* krL0 = kr_of(g.ws, s_col[0].kr);
+    const DevSketch* krL1 = kr_of(g.ws, s_col[1].kr);
+    uint32_t pi = 0, qy = 0;
+    int64_t tab_last[2] = {-1, -1};
+    bool ok = true;
+    for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t) {
+      const TileInfo ti = tile_info(g, t);
+      for (int b = 0; b < ti.nB && ok; ++b)
+        for (int a = 0; a < ti.nA && ok; ++a, ++pi) {
+          const int64_t kL = ti.kL0 + a, kR0 = (ti.kRg0 + b) * g.G;
+          const int64_t w0 = kL + g.WL * kR0;
+          const int buf = pi & 1;
+          if (!mbar_wait(bar(EMPTY_L + buf), ((pi >> 1) & 1) ^ 1, abort_flag, g.status)) {
+            ok = false;
+            break;
+          }
+          if (rt == 0 && g.tab_tx) {
+            // the R_2 blocks of this kL from the staged table
+            mbar_arrive_expect_tx(bar(TAB_FULL + buf), g.tab_tx);
+            tab_last[buf] = pi;
+            constexpr uint32_t bytes = (uint32_t)(ell / 8) * kS4;
+            const char* wsb = reinterpret_cast<const char*>(g.ws);
+            for (int h1 = 0; h1 < g.H1; ++h1)
+              bulk_g2s(sR + (buf * 2 + h1) * kRBlkB, wsb + s_row[0].tab + (kL * g.H1 + h1) * (int64_t)bytes, bytes,
+                       bar(TAB_FULL + buf));
+          }
+          // L block: S_1 rows w_g + W (first + i4'), S_2 rows kR_g + n3 (first + i4'),
+          // k = i4' + c g
+          for (int u = lu_beg; u < lu_end; ++u) {
+            const int bi = u / upb, rp = (u % upb) / qps, nq = u % qps;
+            const SkTc& sk = s_col[bi];
+            const int k = 2 * rp;
+            const int64_t gg = k >> lc, kk = k & cmask;
+            const int64_t key = bi == 0 ? w0 + g.WL * gg : kR0 + gg;  // w / wdiv for wdiv = 1, n2
+            const int64_t row = key + sk.hstride * (g.first + kk);
+            const DevSketch* krb = bi == 0 ? krL0 : krL1;
+            const float4 ra = tm_quad_f32(g.ws, krb, g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
+            const float4 rb =
+                tm_quad_f32(g.ws, krb, g.seed, (uint32_t)sk.sid, (uint64_t)(row + sk.hstride), (uint32_t)nq);
+            const int n0 = bi * ell + 4 * nq;
+            const uint32_t dst = sL + buf * kLBlkB + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
+            st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
+            st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
+            st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
+            st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(FULL_L + buf));
+          // R_3 blocks, one quarter (half of i_1) at a time
+          for (int h1 = 0; h1 < g.H1; ++h1, ++qy) {
+            if (!mbar_wait(bar(EMPTY_Y), (qy & 1) ^ 1, abort_flag, g.status)) {
+              ok = false;
+              break;
+            }
+            const float* ktab =
+                kr3 ? reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab) : nullptr;
+            for (int u = yu_beg; u < yu_end; ++u) {
+              const int gp = u / upb, rp = (u % upb) / qps, nq = u % qps;
+              const int k = 2 * rp;
+              const int64_t i1 = h1 * 128 + k;
+              float4 ra, rb;
+              if (kr3) {
+                // Khatri-Rao entry of row i1 + n1 w: (F_3(i3) F_2(i2)) F_1(i1),
+                // the row sketch's decreasing mode order, i2 = kL, i3 = kR_g
+                const int lp = kr3->kr_lp;
+                const float4 f3 = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[2] + (kR0 + gp) * lp + 4 * nq);
+                const float4 f2 = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[1] + kL * lp + 4 * nq);
+                const float4 fa = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[0] + i1 * lp + 4 * nq);
+                const float4 fb = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[0] + (i1 + 1) * lp + 4 * nq);
+                const float4 cy = make_float4(__fmul_rn(f3.x, f2.x), __fmul_rn(f3.y, f2.y), __fmul_rn(f3.z, f2.z),
+                                              __fmul_rn(f3.w, f2.w));
+                ra = make_float4(__fmul_rn(cy.x, fa.x), __fmul_rn(cy.y, fa.y), __fmul_rn(cy.z, fa.z),
+                                 __fmul_rn(cy.w, fa.w));
+                rb = make_float4(__fmul_rn(cy.x, fb.x), __fmul_rn(cy.y, fb.y), __fmul_rn(cy.z, fb.z),
+                                 __fmul_rn(cy.w, fb.w));
+              } else {
+                const int64_t row = i1 + g.n1 * (w0 + g.WL * gp);
+                const SkTc& sk = s_row[1];
+                ra = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
+                rb = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)(row + 1), (uint32_t)nq);
+              }
+              const int n0 = gp * ell + 4 * nq;
+              const uint32_t dst = sY + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
+              st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
+              st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
+              st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
+              st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(FULL_Y));
+          }
+        }
+    }
+    // copies still in flight when the CTA gave up must land before it exits
+    if (rt == 0)
+      for (int b2 = 0; b2 < 2; ++b2)
+        if (tab_last[b2] >= 0) {
+          const long long t0 = clock64();
+          while (!mbar_try(bar(TAB_FULL + b2), (uint32_t)((tab_last[b2] >> 1) & 1)) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA issue
+    const uint32_t idL = make_idesc(NL, true), idR = make_idesc(ell, false), idY = make_idesc(g.G * ell, false);
+    const uint32_t colYB = (uint32_t)(g.G * ell);
+    uint32_t qi = 0, pi = 0, lf = 0, ti_n = 0;
+    int64_t cur_tl = -1;
+    uint32_t initL = 0;
+    bool ok = true;
+    for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti_n) {
+      const TileInfo tinf = tile_info(g, t);
+      const int64_t tl = l_group(g, t);
+      if (tl != cur_tl) {
+        if (cur_tl >= 0) {
+          if (elect_one()) mma_commit(bar(TML_FULL));
+          __syncwarp();
+          ++lf;
+        }
+        ok = warp_wait(bar(TML_EMPTY), (lf & 1) ^ 1, abort_flag, g.status);
+        if (!ok) break;
+        tc_fence_after();
+        initL = 0;
+        cur_tl = tl;
+      }
+      const uint32_t rb = ti_n & 1;
+      ok = warp_wait(bar(TMR_EMPTY + rb), ((ti_n >> 1) & 1) ^ 1, abort_flag, g.status);
+      if (!ok) break;
+      tc_fence_after();
+      uint32_t initR = 0;
+      bool initY = false;
+      const uint32_t dY = tmem + (uint32_t)kTmemY + rb * colYB;
+      for (int b = 0; b < tinf.nB && ok; ++b)
+        for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
+          const int buf = pi & 1;
+          ok = warp_wait(bar(FULL_L + buf), (pi >> 1) & 1, abort_flag, g.status);
+          if (ok && g.tab_tx) ok = warp_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
+          if (!ok) break;
+          tc_fence_after();
+          for (int h1 = 0; h1 < g.H1; ++h1, ++qi) {
+            const int st = qi & 1;
+            ok = warp_wait(bar(FULL_A + st), (qi >> 1) & 1, abort_flag, g.status);
+            if (ok) ok = warp_wait(bar(FULL_Y), qi & 1, abort_flag, g.status);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t tileA = sA + st * kStageB;
+            const uint32_t bL = sL + buf * kLBlkB;
+            const uint32_t bR = sR + (buf * 2 + h1) * kRBlkB;
+            const int slotL = a * g.H1 + h1;
+            const uint32_t dL = tmem + (uint32_t)g.colL + (uint32_t)(slotL * NL);
+            const uint32_t dR = tmem + (uint32_t)g.colR + rb * (uint32_t)(g.T3 * ell) + (uint32_t)(b * ell);
+            const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
+            const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4), bY0 = make_desc(sY, kS1, kS4);
+            const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> b) & 1u, accY0 = initY ? 1u : 0u;
+            if (elect_one()) {
+              // the R_3 products first, so that the RNG warps can refill their
+              // single buffer while the rest of the quarter runs
+#pragma unroll
+              for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                  const uint64_t po = (uint64_t)((part * kTileB) >> 4);
+                  mma_bf16_ss(dY, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bY0 + (uint64_t)((ks * 2 * kS1) >> 4), idY,
+                              accY0 | (uint32_t)(ks | part));
+                }
+              mma_commit(bar(EMPTY_Y));
+#pragma unroll
+              for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                  const uint64_t po = (uint64_t)((part * kTileB) >> 4);
+                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4), idL,
+                              accL0 | (uint32_t)(ks | part));
+                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4), idR,
+                              accR0 | (uint32_t)(ks | part));
+                }
+              mma_commit(bar(EMPTY_A + st));
+            }
+            __syncwarp();
+            initL |= 1u << slotL;
+            initR |= 1u << b;
+            initY = true;
+          }
+          if (ok) {
+            if (elect_one()) mma_commit(bar(EMPTY_L + buf));
+            __syncwarp();
+          }
+        }
+      if (ok) {
+        if (elect_one()) mma_commit(bar(TMR_FULL + rb));
+        __syncwarp();
+      }
+    }
+    if (ok && cur_tl >= 0) {
+      if (elect_one()) mma_commit(bar(TML_FULL));
+      __syncwarp();
+    }
+    if (elect_one()) mma_commit(bar(DRAIN));
+    __syncwarp();
+    const long long t0 = clock64();
+    while (!mbar_try(bar(DRAIN), 0) && clock64() - t0 < kWaitCycles) {
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    const int lrow = warp * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+    const uint32_t colYB = (uint32_t)(g.G * ell);
+    // L slots of kL block [kL0, kL0 + nA): S_1 (rows i_1, pre-summed over the
+    // kL values) and S_2 (rows i_1 + n_1 kL)
+    auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
+      if (!mbar_wait(bar(TML_FULL), lf & 1, abort_flag, g.status)) return false;
+      tc_fence_after();
+      for (int h1 = 0; h1 < g.H1; ++h1) {
+        const int64_t i1 = h1 * 128 + lrow;
+        for (int s = 0; s < 2; ++s) {
+          const SkTc& sk = s_col[s];
+          double* dst = g.ws + sk.off;
+          float acc[ell];
+#pragma unroll
+          for (int j = 0; j < ell; ++j) acc[j] = 0.0f;
+          for (int a = 0; a < nA; ++a) {
+            float v[ell];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + s * ell), v);
+            if (s == 0) {
+#pragma unroll
+              for (int j = 0; j < ell; ++j) acc[j] += v[j];
+            } else {
+              const int64_t row = i1 + g.n1 * (kL0 + a);
+#pragma unroll
+              for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
+            }
+          }
+          if (s == 0) {
+#pragma unroll
+            for (int j = 0; j < ell; ++j) atomicAdd(dst + i1 + sk.rows * j, (double)acc[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(TML_EMPTY));
+      return true;
+    };
+    uint32_t lf = 0, ti_n = 0;
+    int64_t cur_tl = -1, cur_kL0 = 0;
+    int cur_nA = 0;
+    bool ok = true;
+    // composite row of this lane: slice kk of plane gl of the super-plane
+    const int gl = lrow >> lc, kk = lrow & cmask;
+    for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t, ++ti_n) {
+      const TileInfo tinf = tile_info(g, t);
+      const int64_t tl = l_group(g, t);
+      if (tl != cur_tl) {
+        if (cur_tl >= 0) {
+          ok = flush_L(cur_kL0, cur_nA, lf);
+          ++lf;
+          if (!ok) break;
+        }
+        cur_tl = tl;
+        cur_kL0 = tinf.kL0;
+        cur_nA = tinf.nA;
+      }
+      const uint32_t rb = ti_n & 1;
+      if (!mbar_wait(bar(TMR_FULL + rb), (ti_n >> 1) & 1, abort_flag, g.status)) break;
+      tc_fence_after();
+      // R_2: rows kR_g + n_3 (first + kk), one slot per kR group of the tile
+      {
+        const SkTc& sk = s_row[0];
+        double* dst = g.ws + sk.off;
+        for (int b = 0; b < tinf.nB; ++b) {
+          float v[ell];
+          tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colR + rb * (uint32_t)(g.T3 * ell) + (uint32_t)(b * ell), v);
+          const int64_t row = ((tinf.kRg0 + b) * g.G + gl) + sk.hstride * (g.first + kk);
+#pragma unroll
+          for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
+        }
+      }
+      // R_3: the diagonal block of D_Y (row group gl, column block gl), rows
+      // first + kk; the lanes of a warp span 32 / c planes (2 at c = 16)
+      {
+        const SkTc& sk = s_row[1];
+        double* dst = g.ws + sk.off;
+        const int g_lo = (warp * 32) >> lc;  // first plane of this warp's lanes
+        float y[ell];
+        tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + rb * colYB + (uint32_t)(g_lo * ell), y);
+        if constexpr (C == 16) {
+          // lanes 16..31 belong to the warp's second plane; lanes l and l + 16
+          // hold the same slice, so the two diagonal blocks are summed there
+          float v1[ell];
+          tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + rb * colYB + (uint32_t)((g_lo + 1) * ell), v1);
+#pragma unroll
+          for (int j = 0; j < ell; ++j) {
+            const float mine = lane >= 16 ? v1[j] : y[j];
+            y[j] = mine + __shfl_down_sync(0xffffffffu, mine, 16);
+          }
+        }
+        if (C != 16 || lane < 16) {
+          const int64_t row = sk.hstride * (g.first + kk);
+#pragma unroll
+          for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)y[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(TMR_EMPTY + rb));
+    }
+    if (ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+  }
+}
+
+// Staged R_2 blocks: block (v, h) holds the 128 rows 128 h + k + n_1 v of the
+// test matrix (v = kL) as the BF16 K-major core-matrix image the MMA reads.
+__global__ void slab_table_kernel(const SlabArgs g, int64_t nv) {
+  const SkTc sk = g.row[0];
+  const int qps = g.ell / 4;
+  const int64_t blkB = (int64_t)(g.ell / 8) * kS4;
+  const int64_t total = nv * g.H1 * 16 * qps * 8;
+  char* tab = reinterpret_cast<char*>(g.ws) + sk.tab;
+  const DevSketch* kr = kr_of(g.ws, sk.kr);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r8 = (int)(e & 7);
+    int64_t rest = e >> 3;
+    const int q = (int)(rest % qps);
+    rest /= qps;
+    const int kg = (int)(rest & 15);
+    rest >>= 4;
+    const int h = (int)(rest % g.H1);
+    const int64_t v = rest / g.H1;
+    const int64_t k = 128 * h + 8 * kg + r8;
+    const float4 z = tm_quad_f32(g.ws, kr, g.seed, (uint32_t)sk.sid, (uint64_t)(k + g.n1 * v), (uint32_t)q);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    char* blk = tab + (v * g.H1 + h) * blkB;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * q + u;
+      *reinterpret_cast<__nv_bfloat16*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          __float2bfloat16_rn(zz[u]);
+    }
+  }
+}
+
+}  // namespace slab
+
+// Shape rules of the slab kernel; fills the launch arguments when it applies.
+bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
+  const DevItem& it = plan_items_host(&P)[item];
+  if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sided1 || it.passes != 1) return false;
+  if (it.d != 4 || it.nsk != 4) return false;
+  if (it.n[0] != 128 && it.n[0] != 256) return false;
+  if (count != 16 && count != 32 && count != 64) return false;
+  const int G = (int)(128 / count);
+  const DevSketch* sks = plan_sketches_host(&P);
+  const DevSketch &s1 = sks[it.sk0], &s2 = sks[it.sk0 + 1], &r2 = sks[it.sk0 + 2], &r3 = sks[it.sk0 + 3];
+  if (s1.type != SK_COL || s1.k != 1 || s2.type != SK_COL || s2.k != 2 || r2.type != SK_ROW || r2.k != 2 ||
+      r3.type != SK_ROW || r3.k != 3)
+    return false;
+  const int ell = s1.width;
+  if ((ell != 8 && ell != 16) || s2.width != ell || r2.width != ell || r3.width != ell) return false;
+  slab::SlabArgs g;
+  memset(&g, 0, sizeof(g));
+  g.n1 = it.n[0];
+  g.W = it.W;
+  g.WL = it.n[1];
+  g.WR = it.n[2];
+  if (g.WR % G) return false;
+  g.WRg = g.WR / G;
+  g.Nd1 = it.N[3];
+  g.H1 = (int)(it.n[0] / 128);
+  g.ell = ell;
+  g.c = (int)count;
+  g.lc = count == 16 ? 4 : count == 32 ? 5 : 6;
+  g.G = G;
+  // tensor memory: D_Y (two buffers of G l columns), L slots (T2 H1 x 2l),
+  // R_2 (two buffers of T3 l); every accumulator sees at most 256 MMAs
+  auto fits = [&](int t2, int t3) {
+    return 2 * G * ell + t2 * g.H1 * 2 * ell + 2 * t3 * ell <= 512 && t2 * t3 * g.H1 * 16 <= kMaxChainL;
+  };
+  int T2 = 1, T3 = 1;
+  for (int t2 = 1; t2 <= 8; ++t2)
+    for (int t3 = 1; t3 <= 8; ++t3)
+      if (t2 <= g.WL && t3 <= g.WRg && fits(t2, t3) && t2 * t3 > T2 * T3) {
+        T2 = t2;
+        T3 = t3;
+      }
+  if (!fits(T2, T3)) return false;
+  g.T2 = T2;
+  g.T3 = T3;
+  g.colL = 2 * G * ell;
+  g.colR = g.colL + T2 * g.H1 * 2 * ell;
+  g.tilesL = (g.WL + T2 - 1) / T2;
+  g.tilesR = (g.WRg + T3 - 1) / T3;
+  g.runL = std::max<int64_t>(1, kMaxChainL / (T3 * 16));
+  g.col[0] = SkTc{s1.rows, s1.off, s1.wdiv, s1.hstride, -1, s1.stream_id, s1.kr_nm ? it.sk0 : -1};
+  g.col[1] = SkTc{s2.rows, s2.off, s2.wdiv, s2.hstride, -1, s2.stream_id, s2.kr_nm ? it.sk0 + 1 : -1};
+  g.row[0] = SkTc{r2.rows, r2.off, r2.wdiv, r2.hstride, -1, r2.stream_id, r2.kr_nm ? it.sk0 + 2 : -1};
+  g.row[1] = SkTc{r3.rows, r3.off, r3.wdiv, r3.hstride, -1, r3.stream_id, r3.kr_nm ? it.sk0 + 3 : -1};
+  // the staged R_2 blocks live in the plane kernel's staging area (one 128-row
+  // block per kL and half of i_1)
+  const int64_t blk = (int64_t)(ell / 8) * kS4;
+  if (it.tctab_doubles * 8 < g.WL * g.H1 * blk) return false;
+  g.row[0].tab = it.off_tctab * 8;
+  g.tab_tx = (uint32_t)(g.H1 * blk);
+  g.seed = it.seed;
+  *out = g;
+  return true;
+}
+
+static bool slab_kernel_launchable() {
+  static int ok = -1;
+  if (ok < 0) {
+    cudaFuncAttributes fa, fb;
+    int dev = 0, smem_optin = 0;
+    ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+         fa.maxThreadsPerBlock >= slab::kThreads && fb.maxThreadsPerBlock >= slab::kThreads &&
+         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+         smem_optin >= slab::kSmemBytes;
+  }
+  return ok == 1;
+}
+
+}  // namespace tc
+
+bool use_slab_kernel(const Plan& P, int item, int64_t count) {
+  tc::slab::SlabArgs g;
+  return tc::plan_slab(P, item, count, &g);
+}
+
+cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                               cudaStream_t st) {
+  tc::slab::SlabArgs g;
+  if (!tc::plan_slab(P, item, count, &g)) return cudaErrorNotSupported;
+  if (!tc::slab_kernel_launchable()) return cudaErrorNotSupported;
+  g.X = (const float*)X;
+  g.ws = (double*)ws;
+  g.status = reinterpret_cast<int*>((char*)ws + kStatusOff);
+  g.first = first;
+  using KernelFn = void (*)(tc::slab::SlabArgs);
+  const KernelFn kernels[2][3] = {
+      {tc::slab::sketch_slab_kernel<8, 16>, tc::slab::sketch_slab_kernel<8, 32>, tc::slab::sketch_slab_kernel<8, 64>},
+      {tc::slab::sketch_slab_kernel<16, 16>, tc::slab::sketch_slab_kernel<16, 32>,
+       tc::slab::sketch_slab_kernel<16, 64>}};
+  static bool attr_set = false;
+  if (!attr_set) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 3; ++j) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kernels[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, tc::slab::kSmemBytes);
+        if (e != cudaSuccess) return e;
+      }
+    attr_set = true;
+  }
+  {
+    const int64_t total = g.WL * g.H1 * 16 * (g.ell / 4) * 8;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8LL * device_sm_count());
+    count_launch();
+    tc::slab::slab_table_kernel<<<blocks, 256, 0, st>>>(g, g.WL);
+  }
+  const int64_t ntiles = g.tilesL * g.tilesR;
+  const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
+  count_launch();
+  const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
+  k<<<grid, tc::slab::kThreads, tc::slab::kSmemBytes, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace tts

@@ -4,8 +4,9 @@
 // were staged in the workspace at the start of the call (krdrm.cu).
 //
 // A Khatri-Rao row index is the column-major multi-index over the sketch's
-// factor modes (first mode fastest); its entry j is the product
-// F_0(i_0, j) F_1(i_1, j) ... taken in that order.  The FP32 product uses
+// factor modes (first mode fastest); its entry j is the product of the factor
+// entries F_t(i_t, j), taken in increasing mode order for a column sketch and
+// in decreasing order for a row sketch (DevSketch::kr_dec).  The products use
 // explicitly rounded multiplies, so every kernel computes the same bits.
 #pragma once
 #include <cstdint>
@@ -22,8 +23,10 @@ __device__ __forceinline__ const DevSketch* ws_sketches(const void* wsb) {
   return reinterpret_cast<const DevSketch*>(b + T.off_sketches);
 }
 
-// Index of mode t of the row (and the rest of the row for the next modes).
-__device__ __forceinline__ int64_t kr_digit(uint64_t& row, int64_t n, bool last) {
+// Digit of mode t of a Khatri-Rao row: increasing order peels the fastest
+// mode off by a remainder, decreasing order the slowest by a quotient (32-bit
+// arithmetic when the row fits, which it does for every shape up to 2^32 rows).
+__device__ __forceinline__ int64_t kr_digit_inc(uint64_t& row, int64_t n, bool last) {
   if (last) return (int64_t)row;
   if (row < 0x100000000ull && n < 0x100000000ll) {
     const uint32_t r = (uint32_t)row, nn = (uint32_t)n;
@@ -36,15 +39,25 @@ __device__ __forceinline__ int64_t kr_digit(uint64_t& row, int64_t n, bool last)
   row = q;
   return i;
 }
+__device__ __forceinline__ int64_t kr_digit_dec(uint64_t& row, int64_t stride, bool last) {
+  if (last) return (int64_t)row;
+  uint64_t i;
+  if (row < 0x100000000ull && stride < 0x100000000ll) i = (uint32_t)row / (uint32_t)stride;
+  else i = row / (uint64_t)stride;
+  row -= i * (uint64_t)stride;
+  return (int64_t)i;
+}
 
 // Columns 4q..4q+3 of Khatri-Rao row `row` (FP32 factors, FP32 product).
 __device__ __forceinline__ float4 kr_quad_f32(const void* wsb, const DevSketch& s, uint64_t row, uint32_t q) {
   const float* tab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
   float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
-  for (int t = 0; t < s.kr_nm; ++t) {
-    const int64_t i = kr_digit(row, s.kr_n[t], t + 1 == s.kr_nm);
+  for (int u = 0; u < s.kr_nm; ++u) {
+    const int t = s.kr_dec ? s.kr_nm - 1 - u : u;
+    const bool last = u + 1 == s.kr_nm;
+    const int64_t i = s.kr_dec ? kr_digit_dec(row, s.kr_stride[t], last) : kr_digit_inc(row, s.kr_n[t], last);
     const float4 f = *reinterpret_cast<const float4*>(tab + s.kr_off[t] + i * s.kr_lp + 4 * q);
-    if (t == 0) {
+    if (u == 0) {
       v = f;
     } else {
       v.x = __fmul_rn(v.x, f.x);
@@ -60,11 +73,13 @@ __device__ __forceinline__ float4 kr_quad_f32(const void* wsb, const DevSketch& 
 __device__ __forceinline__ void kr_quad_f64(const void* wsb, const DevSketch& s, uint64_t row, uint32_t q,
                                             double z[4]) {
   const double* tab = reinterpret_cast<const double*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
-  for (int t = 0; t < s.kr_nm; ++t) {
-    const int64_t i = kr_digit(row, s.kr_n[t], t + 1 == s.kr_nm);
+  for (int u = 0; u < s.kr_nm; ++u) {
+    const int t = s.kr_dec ? s.kr_nm - 1 - u : u;
+    const bool last = u + 1 == s.kr_nm;
+    const int64_t i = s.kr_dec ? kr_digit_dec(row, s.kr_stride[t], last) : kr_digit_inc(row, s.kr_n[t], last);
     const double2* f = reinterpret_cast<const double2*>(tab + s.kr_off[t] + i * s.kr_lp + 4 * q);
     const double2 a = f[0], b = f[1];
-    if (t == 0) {
+    if (u == 0) {
       z[0] = a.x; z[1] = a.y; z[2] = b.x; z[3] = b.y;
     } else {
       z[0] = __dmul_rn(z[0], a.x);

@@ -1,0 +1,127 @@
+"""GPU parity of the slab form of the tcgen05 plane kernel: a slab of 16, 32
+or 64 last-mode slices of a 4-way tensor (the 1 GiB slabs of the 256^4
+streaming workload are 16 slices), accumulated slab by slab in any order.
+
+Every sketch entry after a stream of slabs is compared with the oracle's
+dense FP64 products of the split X (hi + lo in BF16) with its BF16-rounded
+test matrices, dense Gaussian and Khatri-Rao: Frobenius 1e-4 and max 2e-3 of
+max |S| (the bars and their derivation are those of test_gpu_mixed.py: the
+FP32 generator flips a rare rounding decision).  The slab kernel takes the
+R_3 products against G planes' blocks at once and keeps the diagonal; a
+wrong block choice, row map or flush shows up as O(1) errors here."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import ttinputs as ti
+from oracle import philox, pstt2 as OP, tt as OT
+from paper_2111_10448_gb300 import TTSketch, _native as N
+from tests.gpu_util import rel, sketch_dict, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _split(x):
+    hi = philox.round_to(x, "bf16")
+    return hi + philox.round_to(x - hi, "bf16")
+
+
+def _close(G, S, what):
+    fro = np.linalg.norm(G - S) / np.linalg.norm(S)
+    mx = np.max(np.abs(G - S)) / np.max(np.abs(S))
+    assert fro <= 1e-4 and mx <= 2e-3, (what, fro, mx)
+
+
+def _slabs(n4, c, seed):
+    order = list(range(0, n4, c))
+    np.random.default_rng(seed).shuffle(order)
+    return [(a, c) for a in order]
+
+
+@pytest.mark.parametrize("dims,c,kw", [
+    ([128, 8, 16, 32], 16, dict(eps=1e-6, rmax=6, p=10)),      # l = 16, one tile
+    ([256, 6, 16, 48], 16, dict(ranks=[1, 4, 4, 4, 1], p=4)),  # l = 8, two halves of i_1, ragged kL block
+    ([128, 8, 16, 64], 32, dict(eps=1e-6, rmax=6, p=10)),      # c = 32 (G = 4)
+    ([256, 4, 8, 64], 64, dict(eps=1e-6, rmax=6, p=10)),       # c = 64 (G = 2)
+    ([256, 64, 64, 32], 16, dict(eps=1e-6, rmax=6, p=10)),     # two halves of i_1, 64 tiles
+])
+@pytest.mark.parametrize("drm", ["gauss", "kr"])
+def test_slab_sketches_match_oracle(dims, c, kw, drm):
+    _check_slab(dims, c, kw, drm)
+
+
+def test_slab_multitile_every_sketch_entry():
+    """320 tiles (40 kL blocks x 8 kR-group blocks, the last one ragged) over
+    the GPU's CTAs: each CTA walks two or three tiles, changes kL block inside
+    its run and flushes the column accumulators; every entry against the
+    oracle."""
+    _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10), "gauss")
+
+
+def _check_slab(dims, c, kw, drm):
+    n1, n2, n3, n4 = dims
+    x = ti.random_tt(dims, [1, 3, 3, 3, 1], seed=5, noise=1e-5).astype(np.float32)
+    X = to_dev(x)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", drm=drm, **kw)
+    assert t.kernel_kind(c) == 2
+    nd1 = n1 * n2 * n3
+    t.begin()
+    for a, cnt in _slabs(n4, c, 1):
+        t.accumulate(X[a * nd1:(a + cnt) * nd1].clone(), a, cnt)
+    sk = sketch_dict(t)
+    t.finalize()
+    st, _ = t.status()
+    assert st in (0, N.TT_WARN_RANK_CAP)
+    widths = OP.sketch_widths(4, OP.clamp_ranks(dims, kw["ranks"]) if "ranks" in kw else None, kw["p"],
+                              "eps" in kw, kw.get("rmax"))
+    o = OP.sketches(_split(x.astype(np.float64)), dims, widths, 7, 1, test_fmt="bf16", drm=drm)
+    for k, S in o["S"].items():
+        _close(sk[(0, k)], S, ("S", k))
+    for k, R in o["R"].items():
+        _close(sk[(1, k)], R, ("R", k))
+
+
+@pytest.mark.parametrize("drm", ["gauss", "kr"])
+def test_slab_stream_equals_whole_tensor(drm):
+    """Sixteen-slice slabs in shuffled order against one accumulate of the
+    whole last mode (the plane kernel): the decompositions agree to the FP32
+    accumulation differences of the two tilings."""
+    dims = [256, 16, 16, 256]
+    x = ti.hilbert_type(dims, np.float32)
+    X = to_dev(x)
+    kw = dict(eps=1e-6, rmax=6, p=10, seed=1, prec="bf16", drm=drm)
+    one = TTSketch(dims, **kw)
+    assert one.kernel_kind(256) == 2 and one.kernel_kind(16) == 2
+    one.pstt2(X)
+    t = TTSketch(dims, **kw)
+    nd1 = 256 * 16 * 16
+    t.begin()
+    for a, cnt in _slabs(256, 16, 3):
+        t.accumulate(X[a * nd1:(a + cnt) * nd1], a, cnt)
+    t.finalize()
+    assert t.status()[1] == one.status()[1]
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
+
+
+@pytest.mark.parametrize("drm", ["gauss", "kr"])
+def test_slab_pipeline_within_10eps(drm):
+    """The one-pass pipeline fed by 16-slice slabs: X~ within 10 eps of X and
+    of the FP64 path with the same test matrices."""
+    dims = [256, 32, 32, 128]
+    Xd = torch.empty(int(np.prod(dims)), dtype=torch.float32, device="cuda")
+    nn = (C.c_int64 * 4)(*dims)
+    N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, dims[-1], C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
+    t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="bf16", drm=drm)
+    nd1 = 256 * 32 * 32
+    t.begin()
+    for a, cnt in _slabs(128, 16, 5):
+        t.accumulate(Xd[a * nd1:(a + cnt) * nd1], a, cnt)
+    t.finalize()
+    f = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="fp64", drm=drm).pstt2(Xd)
+    e_x = t.error(Xd).cpu().numpy()
+    e_f = t.error(f.reconstruct(torch.float32)).cpu().numpy()
+    rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
+    print(f"slab pipeline {drm}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
+    assert rx <= 1e-5 and rf <= 1e-5
