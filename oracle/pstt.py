@@ -23,7 +23,7 @@ import numpy as np
 
 from . import philox
 from .linalg import householder_cpqr, lstsq_right
-from .pstt2 import clamp_ranks, omega, pick_rank_eps, psi, sketch_widths
+from .pstt2 import clamp_ranks, omega, pick_rank_eps, psi_rounded, sketch_widths
 from .tt import prods, unfold
 
 
@@ -62,7 +62,7 @@ def pstt_onepass(x, dims, *, ranks=None, eps=None, rmax=None, p=5, seed=1, test_
     for k in range(1, d):
         Om[k] = philox.round_to(omega(seed, dims, k, widths[k], drm), test_fmt)
         S[k] = unfold(x, dims, k) @ Om[k]
-    Psi = philox.round_to(psi(seed, dims, d - 1, widths[d - 1], drm), test_fmt)
+    Psi = psi_rounded(seed, dims, d - 1, widths[d - 1], drm, test_fmt)
     T = Psi.T @ unfold(x, dims, d - 1)                    # l x n_d
     # bases: CPQR of every S_k, rank per A5 in tolerance mode
     r = [1] * (d + 1)

@@ -27,7 +27,9 @@ Readings of the paper taken here (the CUDA path takes the same ones):
 * Test matrices: Omega_k = stream k, Psi_k = stream 64 + k (oracle.philox).
   drm='gauss': i.i.d. Gaussian entries (Algorithm 2); drm='kr': Khatri-Rao
   products of per-mode Gaussian factors (eq. (sketch_orig)): Omega_k over the
-  modes k+1..d of its rows, Psi_k over the modes 1..k.
+  modes k+1..d of its rows, Psi_k over the modes 1..k.  With test_fmt rounding
+  (the mixed-precision paths) every entry is rounded, except the Khatri-Rao
+  Psi_{d-1}, taken mode by mode (psi_rounded).
 """
 import math
 import numpy as np
@@ -87,6 +89,23 @@ def psi(seed, dims, k, l, drm='gauss'):
     return philox.test_matrix(seed, philox.STREAM_PSI + k, N[k], l)
 
 
+def psi_rounded(seed, dims, k, l, drm, fmt):
+    """Psi_k as a sketch in arithmetic `fmt` uses it.  Entries are rounded to
+    fmt, except the Khatri-Rao Psi_{d-1} of a rounded format, which is taken
+    mode by mode as eq. (sketch_orig) writes the Khatri-Rao sketch: the mode-1
+    factor rounded to fmt (it enters the product with X) times the rounded
+    product of the other factors' rows (the diagonal scaling D), i.e.
+    round(F_1(i_1, j)) * round(F_{d-1}(i_{d-1}, j) ... F_2(i_2, j))."""
+    d = len(dims)
+    if drm == 'kr' and k == d - 1 and fmt not in ('f64', 'f32') and k >= 2:
+        s = philox.STREAM_PSI + k
+        F1 = philox.round_to(philox.kr_factor(seed, s, 1, dims[0], l), fmt)
+        rest = philox.round_to(philox.kr_test_matrix(seed, s, list(range(2, k + 1)), dims[1:k], l,
+                                                     decreasing=True), fmt)
+        return (F1[None, :, :] * rest[:, None, :]).reshape(-1, l)
+    return philox.round_to(psi(seed, dims, k, l, drm), fmt)
+
+
 def sketches(x, dims, widths, seed, passes, test_fmt='f64', drm='gauss'):
     """Step 2: dense sketches, materialising the test matrices.
 
@@ -105,7 +124,7 @@ def sketches(x, dims, widths, seed, passes, test_fmt='f64', drm='gauss'):
         S[k] = unfold(x, dims, k) @ Om[k]
     for k in range(ds, d):
         l = widths[k]
-        Ps[k] = philox.round_to(psi(seed, dims, k, l, drm), test_fmt)
+        Ps[k] = psi_rounded(seed, dims, k, l, drm, test_fmt)
         R[k] = unfold(x, dims, k).T @ Ps[k]
     return {'S': S, 'R': R, 'Omega': Om, 'Psi': Ps}
 

@@ -73,6 +73,12 @@ struct DevSketch {
   // the mode a plane's rows vary in (the last for a column sketch, the first
   // for a row sketch) is always the final factor.
   int kr_nm, kr_mode0, kr_lp, kr_dec;
+  // 1: the row sketch of X_{d-1} on a TF32 / BF16 path, evaluated mode by
+  // mode (eq. (sketch_orig)): its entry is round(F_1(i_1, j)) times
+  // round(F_{d-1}(i_{d-1}, j) ... F_2(i_2, j)), the rounded mode-1 factor in the
+  // tensor-core product and the rounded product of the other rows as a
+  // column scale of the partial sums
+  int kr_mbm, kr_pad2_;
   int64_t kr_tab;
   int64_t kr_n[TT_MAXD];
   int64_t kr_off[TT_MAXD];
@@ -178,6 +184,7 @@ bool mixed_tc_supported(const Plan& P, int item, int64_t count);
 bool use_tc_kernel(const Plan& P, int item, int64_t count);
 bool use_sp_kernel(const Plan& P, int item, int64_t count);
 bool use_slab_kernel(const Plan& P, int item, int64_t count);
+int64_t slab_chunk(const Plan& P, int item, int64_t count);
 cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                                cudaStream_t st);
 // Fill the staged test-matrix rows of one sketch: entry (key, r, j), r < nr,

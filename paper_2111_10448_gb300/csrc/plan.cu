@@ -208,6 +208,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     s.kr_nm = s.type == SK_COL ? d - s.k : s.k;
     s.kr_lp = kr_lp;
     s.kr_dec = s.type == SK_ROW ? 1 : 0;
+    s.kr_mbm = (q.prec != TT_PREC_FP64 && s.type == SK_ROW && s.k == d - 1 && s.k >= 2) ? 1 : 0;
     int64_t elems = 0, stride = 1;
     for (int t = 0; t < s.kr_nm; ++t) {
       s.kr_n[t] = it.n[s.kr_mode0 - 1 + t];
@@ -350,7 +351,8 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
         tb = s.wdiv * q.n[0] * lpad * esz;
         if (tilesB < 4 && tb > (16LL << 20)) tb = 0;
       }
-      if (tb > 0 && tb <= (256LL << 20) && bytes + tb <= (1LL << 30)) {
+      // a mode-by-mode Khatri-Rao sketch reads one factor row per tile row: nothing to stage
+      if (tb > 0 && tb <= (256LL << 20) && bytes + tb <= (1LL << 30) && !s.kr_mbm) {
         s.gen_tab = bytes;
         bytes += (tb + 255) / 256 * 256;
       }

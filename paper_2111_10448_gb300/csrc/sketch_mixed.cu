@@ -66,11 +66,12 @@ __global__ void __launch_bounds__(256) mid_b_kernel_mixed(char* wsb, int item_ar
     const int nq = (l + 3) / 4;
     for (int o = threadIdx.x; o < nv * nq; o += blockDim.x) {
       const int v = o % nv, q = o / nv;
-      const float4 z4 = tm_quad_f32(wsb, kr_mid, it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q);
+      const float4 z4 =
+          tm_quad_mixed(wsb, kr_mid, it.seed, (uint32_t)it.mstream, (uint64_t)(v0 + v), (uint32_t)q, it.prec);
       const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = (double)round_prec(z[t], it.prec);
+        if (4 * q + t < l) Gs[v + CH * (4 * q + t)] = (double)z[t];
     }
     __syncthreads();
     for (int o = threadIdx.x; o < r * l; o += blockDim.x) {
@@ -287,7 +288,10 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
           const int r = o % nr, q = o / nr;
           const uint64_t grow = col ? (uint64_t)(whi + sk.hstride * (a.first + b0 + r))
                                     : (uint64_t)((a0 + r) + a.n1 * wlo);
-          const float4 z4 = tm_quad_f32(a.ws, kr_of(a.ws, sk.kr), a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
+          const DevSketch* krs = kr_of(a.ws, sk.kr);
+          // a mode-by-mode sketch takes its mode-1 factor here (scaled at the flush)
+          const float4 z4 = (krs && krs->kr_mbm) ? kr_f1_quad(a.ws, *krs, a0 + r, (uint32_t)q)
+                                                 : tm_quad_f32(a.ws, krs, a.seed, (uint32_t)sk.sid, grow, (uint32_t)q);
           const float z[4] = {z4.x, z4.y, z4.z, z4.w};
           if (bf) {
             float zz[4];
@@ -334,13 +338,25 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
           else tile_mma_tf32<false>(Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
         }
         const int g = lane >> 2, t = lane & 3;
+        // mode-by-mode Khatri-Rao sketch: scale column j by the rounded product
+        // of the other modes' rows of this plane
+        float sc[2] = {1.0f, 1.0f};
+        const DevSketch* krs = kr_of(a.ws, sk.kr);
+        if (krs && krs->kr_mbm) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = min(m0 + g + 8 * h, lpad - 1);
+            const float4 c = kr_scale_quad(a.ws, *krs, (uint64_t)wlo, (uint32_t)(j >> 2), a.prec);
+            sc[h] = (j & 3) == 0 ? c.x : (j & 3) == 1 ? c.y : (j & 3) == 2 ? c.z : c.w;
+          }
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int j = m0 + g + ((e >> 1) << 3);
           const int oo = n0 + 2 * t + (e & 1);
           if (j < l && oo < nout) {
             const int64_t row = col ? (a0 + oo + a.n1 * wlo) : (whi + sk.hstride * (a.first + b0 + oo));
-            atomicAdd(out + row + sk.rows * j, (double)acc[e]);
+            atomicAdd(out + row + sk.rows * j, (double)(acc[e] * sc[e >> 1]));
           }
         }
       }
@@ -1040,6 +1056,9 @@ __global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, 
 bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   const DevItem& it = plan_items_host(&P)[item];
   if (it.prec != TT_PREC_BF16 || it.x_f64) return false;
+  // Khatri-Rao plans go to the slab kernel (the mode-by-mode last row sketch
+  // needs a per-plane scale that this kernel's accumulators cannot take)
+  if (plan_sketches_host(&P)[it.sk0].kr_nm) return false;
   if (it.d != 3 && it.d != 4) return false;
   if (it.n[0] != 128 && it.n[0] != 256) return false;
   if (count != 128 && count != 256) return false;
@@ -1146,11 +1165,11 @@ __device__ __forceinline__ void test_row(const void* wsb, const DevSketch* kr, i
     if (prec == TT_PREC_FP64) {
       tm_quad_f64(wsb, kr, seed, (uint32_t)sid, row, (uint32_t)q, z);
     } else {
-      const float4 f = tm_quad_f32(wsb, kr, seed, (uint32_t)sid, row, (uint32_t)q);
-      z[0] = round_prec(f.x, prec);
-      z[1] = round_prec(f.y, prec);
-      z[2] = round_prec(f.z, prec);
-      z[3] = round_prec(f.w, prec);
+      const float4 f = tm_quad_mixed(wsb, kr, seed, (uint32_t)sid, row, (uint32_t)q, prec);
+      z[0] = f.x;
+      z[1] = f.y;
+      z[2] = f.z;
+      z[3] = f.w;
     }
     for (int t = 0; t < 4; ++t)
       if (4 * q + t < l) out[4 * q + t] = (Real)z[t];

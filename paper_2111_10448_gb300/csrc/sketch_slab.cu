@@ -76,6 +76,7 @@ struct SlabArgs {
   uint64_t seed;
   int H1, T2, T3, ell, c, lc, G;
   int colL, colR;          // tensor-memory columns of the L slots and of the R_2 buffers
+  int kry;                 // Khatri-Rao test matrices: R_3 mode by mode (fixed mode-1 block)
   int64_t runL;            // tiles of one kL block accumulated in the L slots before a flush
   uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
   SkTc col[2], row[2];     // S_1, S_2 | R_2, R_3
@@ -99,14 +100,15 @@ __device__ __forceinline__ int64_t l_group(const SlabArgs& g, int64_t t) {
   return tl * ((g.tilesR + g.runL - 1) / g.runL) + tr / g.runL;
 }
 
-template <int ELL, int C>
+template <int ELL, int C, bool KRY>
 __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs g) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
   // barrier indices
   const int FULL_A = 0, EMPTY_A = 2, FULL_L = 4, EMPTY_L = 6, TAB_FULL = 8, FULL_Y = 10, EMPTY_Y = 11,
-            TML_FULL = 12, TML_EMPTY = 13, TMR_FULL = 14, TMR_EMPTY = 16, DRAIN = 18;
+            TML_FULL = 12, TML_EMPTY = 13, TMR_FULL = 14, TMR_EMPTY = 16, DRAIN = 18, TMY_FULL = 19,
+            TMY_EMPTY = 21;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
   __shared__ SkTc s_col[2], s_row[2];
@@ -131,6 +133,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     }
     mbar_init(bar(FULL_Y), kRngWarps);
     mbar_init(bar(EMPTY_Y), 1);
+    for (int s2 = 0; s2 < 2; ++s2) {
+      mbar_init(bar(TMY_FULL + s2), 1);
+      mbar_init(bar(TMY_EMPTY + s2), kEpiWarps);
+    }
     mbar_init(bar(TML_FULL), 1);
     mbar_init(bar(TML_EMPTY), kEpiWarps);
     mbar_init(bar(DRAIN), 1);
@@ -141,6 +147,21 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(512u));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // Khatri-Rao test matrices: R_3 is taken mode by mode (eq. (sketch_orig)),
+  // X_sp^T round(F_1) -- one fixed B block for the whole launch, here in the
+  // R_3 block area -- with the rounded product of the plane's mode-2 and
+  // mode-3 rows applied by the epilogue to each super-plane's partial sums.
+  const DevSketch* kr3 = kr_of(g.ws, g.row[1].kr);
+  if constexpr (KRY) {
+    const float* f1 = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab) +
+                      kr3->kr_off[0];
+    for (int e = threadIdx.x; e < g.H1 * 128 * ell; e += kThreads) {
+      const int j = e % ell, i1 = e / ell, h1 = i1 >> 7, k = i1 & 127;
+      *reinterpret_cast<__nv_bfloat16*>(sm + kOffY + h1 * kRBlkB + (k >> 3) * kS1 + (j >> 3) * kS4 + (j & 7) * 16 +
+                                        (k & 7) * 2) = __float2bfloat16_rn(f1[(int64_t)i1 * kr3->kr_lp + j]);
+    }
+    fence_async_smem();
   }
   tc_fence_before();
   __syncthreads();
@@ -250,7 +271,6 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     // R_3 blocks of a quarter: G blocks of 128 rows of i_1
     const int yn = g.G * upb;
     const int yu_beg = yn * rt / (kRngWarps * 32), yu_end = yn * (rt + 1) / (kRngWarps * 32);
-    const DevSketch* kr3 = kr_of(g.ws, s_row[1].kr);
     const DevSketch* krL0 = kr_of(g.ws, s_col[0].kr);
     const DevSketch* krL1 = kr_of(g.ws, s_col[1].kr);
     uint32_t pi = 0, qy = 0;
@@ -284,12 +304,32 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
             const SkTc& sk = s_col[bi];
             const int k = 2 * rp;
             const int64_t gg = k >> lc, kk = k & cmask;
-            const int64_t key = bi == 0 ? w0 + g.WL * gg : kR0 + gg;  // w / wdiv for wdiv = 1, n2
-            const int64_t row = key + sk.hstride * (g.first + kk);
-            const DevSketch* krb = bi == 0 ? krL0 : krL1;
-            const float4 ra = tm_quad_f32(g.ws, krb, g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
-            const float4 rb =
-                tm_quad_f32(g.ws, krb, g.seed, (uint32_t)sk.sid, (uint64_t)(row + sk.hstride), (uint32_t)nq);
+            float4 ra, rb;
+            if (krL0) {
+              // Khatri-Rao, increasing mode order: S_1 (F_2(kL) F_3(kR_g)) F_4(i4),
+              // S_2 F_3(kR_g) F_4(i4)
+              const DevSketch* kb = bi == 0 ? krL0 : krL1;
+              const float* tb = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kb->kr_tab);
+              const int lp = kb->kr_lp, t4 = bi == 0 ? 2 : 1;
+              float4 cw = *reinterpret_cast<const float4*>(tb + kb->kr_off[t4 - 1] + (kR0 + gg) * lp + 4 * nq);
+              if (bi == 0) {
+                const float4 f2 = *reinterpret_cast<const float4*>(tb + kb->kr_off[0] + kL * lp + 4 * nq);
+                cw = make_float4(__fmul_rn(f2.x, cw.x), __fmul_rn(f2.y, cw.y), __fmul_rn(f2.z, cw.z),
+                                 __fmul_rn(f2.w, cw.w));
+              }
+              const float* f4 = tb + kb->kr_off[t4] + (g.first + kk) * lp + 4 * nq;
+              const float4 fa = *reinterpret_cast<const float4*>(f4);
+              const float4 fb = *reinterpret_cast<const float4*>(f4 + lp);
+              ra = make_float4(__fmul_rn(cw.x, fa.x), __fmul_rn(cw.y, fa.y), __fmul_rn(cw.z, fa.z),
+                               __fmul_rn(cw.w, fa.w));
+              rb = make_float4(__fmul_rn(cw.x, fb.x), __fmul_rn(cw.y, fb.y), __fmul_rn(cw.z, fb.z),
+                               __fmul_rn(cw.w, fb.w));
+            } else {
+              const int64_t key = bi == 0 ? w0 + g.WL * gg : kR0 + gg;  // w / wdiv for wdiv = 1, n2
+              const int64_t row = key + sk.hstride * (g.first + kk);
+              ra = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
+              rb = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)(row + sk.hstride), (uint32_t)nq);
+            }
             const int n0 = bi * ell + 4 * nq;
             const uint32_t dst = sL + buf * kLBlkB + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
             st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
@@ -300,45 +340,40 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
           fence_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar(FULL_L + buf));
+          // Khatri-Rao: R_3 needs no regenerated blocks (fixed mode-1 block)
+          if constexpr (KRY) continue;
           // R_3 blocks, one quarter (half of i_1) at a time
           for (int h1 = 0; h1 < g.H1; ++h1, ++qy) {
             if (!mbar_wait(bar(EMPTY_Y), (qy & 1) ^ 1, abort_flag, g.status)) {
               ok = false;
               break;
             }
-            const float* ktab =
-                kr3 ? reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab) : nullptr;
-            for (int u = yu_beg; u < yu_end; ++u) {
-              const int gp = u / upb, rp = (u % upb) / qps, nq = u % qps;
-              const int k = 2 * rp;
-              const int64_t i1 = h1 * 128 + k;
-              float4 ra, rb;
-              if (kr3) {
-                // Khatri-Rao entry of row i1 + n1 w: (F_3(i3) F_2(i2)) F_1(i1),
-                // the row sketch's decreasing mode order, i2 = kL, i3 = kR_g
-                const int lp = kr3->kr_lp;
-                const float4 f3 = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[2] + (kR0 + gp) * lp + 4 * nq);
-                const float4 f2 = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[1] + kL * lp + 4 * nq);
-                const float4 fa = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[0] + i1 * lp + 4 * nq);
-                const float4 fb = *reinterpret_cast<const float4*>(ktab + kr3->kr_off[0] + (i1 + 1) * lp + 4 * nq);
-                const float4 cy = make_float4(__fmul_rn(f3.x, f2.x), __fmul_rn(f3.y, f2.y), __fmul_rn(f3.z, f2.z),
-                                              __fmul_rn(f3.w, f2.w));
-                ra = make_float4(__fmul_rn(cy.x, fa.x), __fmul_rn(cy.y, fa.y), __fmul_rn(cy.z, fa.z),
-                                 __fmul_rn(cy.w, fa.w));
-                rb = make_float4(__fmul_rn(cy.x, fb.x), __fmul_rn(cy.y, fb.y), __fmul_rn(cy.z, fb.z),
-                                 __fmul_rn(cy.w, fb.w));
-              } else {
-                const int64_t row = i1 + g.n1 * (w0 + g.WL * gp);
-                const SkTc& sk = s_row[1];
-                ra = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
-                rb = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)(row + 1), (uint32_t)nq);
+            // two units at a time: four independent Philox chains in flight
+            const SkTc& sk = s_row[1];
+            for (int u0 = yu_beg; u0 < yu_end; u0 += 2) {
+              float4 z[2][2];
+              int kk2[2], nn2[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int u = min(u0 + h, yu_end - 1);
+                const int gp = u / upb, rp = (u % upb) / qps, nq = u % qps;
+                kk2[h] = 2 * rp;
+                nn2[h] = gp * ell + 4 * nq;
+                const int64_t row = h1 * 128 + kk2[h] + g.n1 * (w0 + g.WL * gp);
+                z[h][0] = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)row, (uint32_t)nq);
+                z[h][1] = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)(row + 1), (uint32_t)nq);
               }
-              const int n0 = gp * ell + 4 * nq;
-              const uint32_t dst = sY + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
-              st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
-              st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
-              st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
-              st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if (u0 + h >= yu_end) break;
+                const int k = kk2[h], n0 = nn2[h];
+                const float4 ra = z[h][0], rb = z[h][1];
+                const uint32_t dst = sY + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
+                st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
+                st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
+                st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
+                st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+              }
             }
             fence_async_smem();
             __syncwarp();
@@ -356,8 +391,9 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
         }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
-    const uint32_t idL = make_idesc(NL, true), idR = make_idesc(ell, false), idY = make_idesc(g.G * ell, false);
-    const uint32_t colYB = (uint32_t)(g.G * ell);
+    const uint32_t idL = make_idesc(NL, true), idR = make_idesc(ell, false),
+                   idY = make_idesc(KRY ? ell : g.G * ell, false);
+    const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     uint32_t qi = 0, pi = 0, lf = 0, ti_n = 0;
     int64_t cur_tl = -1;
     uint32_t initL = 0;
@@ -389,12 +425,16 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
           const int buf = pi & 1;
           ok = warp_wait(bar(FULL_L + buf), (pi >> 1) & 1, abort_flag, g.status);
           if (ok && g.tab_tx) ok = warp_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
+          // Khatri-Rao: one D_Y accumulator per super-plane, double-buffered
+          // with the epilogue (which scales it by the plane's factor rows)
+          const uint32_t yb = pi & 1;
+          if (KRY && ok) ok = warp_wait(bar(TMY_EMPTY + yb), ((pi >> 1) & 1) ^ 1, abort_flag, g.status);
           if (!ok) break;
           tc_fence_after();
           for (int h1 = 0; h1 < g.H1; ++h1, ++qi) {
             const int st = qi & 1;
             ok = warp_wait(bar(FULL_A + st), (qi >> 1) & 1, abort_flag, g.status);
-            if (ok) ok = warp_wait(bar(FULL_Y), qi & 1, abort_flag, g.status);
+            if (!KRY && ok) ok = warp_wait(bar(FULL_Y), qi & 1, abort_flag, g.status);
             if (!ok) break;
             tc_fence_after();
             const uint32_t tileA = sA + st * kStageB;
@@ -404,8 +444,13 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
             const uint32_t dL = tmem + (uint32_t)g.colL + (uint32_t)(slotL * NL);
             const uint32_t dR = tmem + (uint32_t)g.colR + rb * (uint32_t)(g.T3 * ell) + (uint32_t)(b * ell);
             const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
-            const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4), bY0 = make_desc(sY, kS1, kS4);
-            const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> b) & 1u, accY0 = initY ? 1u : 0u;
+            // Khatri-Rao: the fixed mode-1 block of this half of i_1, into the
+            // super-plane's D_Y; dense: the G planes' R_3 blocks into the tile's
+            const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4),
+                           bY0 = make_desc(KRY ? sY + (uint32_t)(h1 * kRBlkB) : sY, kS1, kS4);
+            const uint32_t dYq = KRY ? tmem + (uint32_t)kTmemY + yb * colYB : dY;
+            const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> b) & 1u,
+                           accY0 = KRY ? (h1 > 0 ? 1u : 0u) : (initY ? 1u : 0u);
             if (elect_one()) {
               // the R_3 products first, so that the RNG warps can refill their
               // single buffer while the rest of the quarter runs
@@ -414,10 +459,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                   const uint64_t po = (uint64_t)((part * kTileB) >> 4);
-                  mma_bf16_ss(dY, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bY0 + (uint64_t)((ks * 2 * kS1) >> 4), idY,
-                              accY0 | (uint32_t)(ks | part));
+                  mma_bf16_ss(dYq, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bY0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                              idY, accY0 | (uint32_t)(ks | part));
                 }
-              mma_commit(bar(EMPTY_Y));
+              if (!KRY) mma_commit(bar(EMPTY_Y));
 #pragma unroll
               for (int ks = 0; ks < 8; ++ks)
 #pragma unroll
@@ -436,7 +481,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
             initY = true;
           }
           if (ok) {
-            if (elect_one()) mma_commit(bar(EMPTY_L + buf));
+            if (elect_one()) {
+              mma_commit(bar(EMPTY_L + buf));
+              if (KRY) mma_commit(bar(TMY_FULL + yb));
+            }
             __syncwarp();
           }
         }
@@ -459,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     // ------------------------------------------------------------ epilogue
     const int lrow = warp * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-    const uint32_t colYB = (uint32_t)(g.G * ell);
+    const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     // L slots of kL block [kL0, kL0 + nA): S_1 (rows i_1, pre-summed over the
     // kL values) and S_2 (rows i_1 + n_1 kL)
     auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
@@ -502,6 +550,31 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     bool ok = true;
     // composite row of this lane: slice kk of plane gl of the super-plane
     const int gl = lrow >> lc, kk = lrow & cmask;
+    constexpr int kYTiles = 16;   // dense: tiles per R_3 flush
+    constexpr int kYSuper = 16;   // Khatri-Rao: super-planes per R_3 flush
+    int ytiles = 0;
+    uint32_t spn = 0;             // super-planes handed over by the MMA warp so far
+    float yacc[ell];
+#pragma unroll
+    for (int j = 0; j < ell; ++j) yacc[j] = 0.0f;
+    // R_3 rows first + kk: at c = 16 lanes l and l + 16 hold the same slice of
+    // two planes and are summed first
+    auto flush_Y = [&]() {
+      const SkTc& sk = s_row[1];
+      double* dst = g.ws + sk.off;
+      float y[ell];
+#pragma unroll
+      for (int j = 0; j < ell; ++j) {
+        y[j] = yacc[j];
+        if constexpr (C == 16) y[j] += __shfl_down_sync(0xffffffffu, y[j], 16);
+        yacc[j] = 0.0f;
+      }
+      if (C != 16 || lane < 16) {
+        const int64_t row = sk.hstride * (g.first + kk);
+#pragma unroll
+        for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)y[j]);
+      }
+    };
     for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t, ++ti_n) {
       const TileInfo tinf = tile_info(g, t);
       const int64_t tl = l_group(g, t);
@@ -514,6 +587,42 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
         cur_tl = tl;
         cur_kL0 = tinf.kL0;
         cur_nA = tinf.nA;
+      }
+      if constexpr (KRY) {
+        // Khatri-Rao R_3, super-plane by super-plane in the MMA's order: the
+        // lane's row of D_Y (plane gl, slice kk) times the rounded product of
+        // the plane's mode-3 and mode-2 rows, summed into the lane's R_3 row
+        bool yok = true;
+        for (int b = 0; b < tinf.nB && yok; ++b)
+          for (int a = 0; a < tinf.nA; ++a, ++spn) {
+            const uint32_t yb = spn & 1;
+            const uint64_t wg = (uint64_t)((tinf.kL0 + a) + g.WL * ((tinf.kRg0 + b) * g.G + gl));
+            float4 sc[ell / 4];
+#pragma unroll
+            for (int q = 0; q < ell / 4; ++q) sc[q] = kr_scale_quad(g.ws, *kr3, wg, (uint32_t)q, TT_PREC_BF16);
+            if (!mbar_wait(bar(TMY_FULL + yb), (spn >> 1) & 1, abort_flag, g.status)) {
+              yok = false;
+              break;
+            }
+            tc_fence_after();
+            float y[ell];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + yb * colYB, y);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(TMY_EMPTY + yb));
+#pragma unroll
+            for (int q = 0; q < ell / 4; ++q) {
+              yacc[4 * q] = fmaf(y[4 * q], sc[q].x, yacc[4 * q]);
+              yacc[4 * q + 1] = fmaf(y[4 * q + 1], sc[q].y, yacc[4 * q + 1]);
+              yacc[4 * q + 2] = fmaf(y[4 * q + 2], sc[q].z, yacc[4 * q + 2]);
+              yacc[4 * q + 3] = fmaf(y[4 * q + 3], sc[q].w, yacc[4 * q + 3]);
+            }
+            if (++ytiles == kYSuper) {
+              flush_Y();
+              ytiles = 0;
+            }
+          }
+        if (!yok) break;
       }
       const uint32_t rb = ti_n & 1;
       if (!mbar_wait(bar(TMR_FULL + rb), (ti_n >> 1) & 1, abort_flag, g.status)) break;
@@ -530,36 +639,35 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
           for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
         }
       }
-      // R_3: the diagonal block of D_Y (row group gl, column block gl), rows
-      // first + kk; the lanes of a warp span 32 / c planes (2 at c = 16)
-      {
-        const SkTc& sk = s_row[1];
-        double* dst = g.ws + sk.off;
+      // R_3 (dense): the diagonal block of D_Y (row group gl, column block gl).
+      // Every tile adds to the same c rows (first + kk), so the lane keeps its
+      // row's sum over the tiles of its run and adds it to the sketch once per
+      // kYTiles tiles (an FP32 chain of at most that many tile sums): the
+      // rows are few, and per-tile atomics would all meet at them.
+      if constexpr (!KRY) {
         const int g_lo = (warp * 32) >> lc;  // first plane of this warp's lanes
         float y[ell];
         tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + rb * colYB + (uint32_t)(g_lo * ell), y);
         if constexpr (C == 16) {
-          // lanes 16..31 belong to the warp's second plane; lanes l and l + 16
-          // hold the same slice, so the two diagonal blocks are summed there
           float v1[ell];
           tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + rb * colYB + (uint32_t)((g_lo + 1) * ell), v1);
+          // lanes 16..31 belong to the warp's second plane
 #pragma unroll
-          for (int j = 0; j < ell; ++j) {
-            const float mine = lane >= 16 ? v1[j] : y[j];
-            y[j] = mine + __shfl_down_sync(0xffffffffu, mine, 16);
-          }
+          for (int j = 0; j < ell; ++j) y[j] = lane >= 16 ? v1[j] : y[j];
         }
-        if (C != 16 || lane < 16) {
-          const int64_t row = sk.hstride * (g.first + kk);
 #pragma unroll
-          for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)y[j]);
-        }
+        for (int j = 0; j < ell; ++j) yacc[j] += y[j];
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(TMR_EMPTY + rb));
+      if (!KRY && ++ytiles == kYTiles) {
+        flush_Y();
+        ytiles = 0;
+      }
     }
     if (ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
+    if (ok && !*abort_flag && ytiles > 0) flush_Y();
   }
   tc_fence_before();
   __syncthreads();
@@ -631,10 +739,15 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   g.c = (int)count;
   g.lc = count == 16 ? 4 : count == 32 ? 5 : 6;
   g.G = G;
-  // tensor memory: D_Y (two buffers of G l columns), L slots (T2 H1 x 2l),
-  // R_2 (two buffers of T3 l); every accumulator sees at most 256 MMAs
+  // tensor memory: D_Y (two buffers: of G l columns for a tile, or of l
+  // columns for a super-plane with Khatri-Rao test matrices), L slots
+  // (T2 H1 x 2l), R_2 (two buffers of T3 l); every accumulator sees at most
+  // 256 MMAs (a tile's D_Y T2 T3 H1 x 16, an R_2 slot T2 H1 x 16)
+  g.kry = r3.kr_nm ? 1 : 0;
+  const int ycols = g.kry ? ell : G * ell;
   auto fits = [&](int t2, int t3) {
-    return 2 * G * ell + t2 * g.H1 * 2 * ell + 2 * t3 * ell <= 512 && t2 * t3 * g.H1 * 16 <= kMaxChainL;
+    return 2 * ycols + t2 * g.H1 * 2 * ell + 2 * t3 * ell <= 512 && t2 * g.H1 * 16 <= kMaxChainL &&
+           (g.kry || t2 * t3 * g.H1 * 16 <= kMaxChainL);
   };
   int T2 = 1, T3 = 1;
   for (int t2 = 1; t2 <= 8; ++t2)
@@ -646,7 +759,7 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   if (!fits(T2, T3)) return false;
   g.T2 = T2;
   g.T3 = T3;
-  g.colL = 2 * G * ell;
+  g.colL = 2 * ycols;
   g.colR = g.colL + T2 * g.H1 * 2 * ell;
   g.tilesL = (g.WL + T2 - 1) / T2;
   g.tilesR = (g.WRg + T3 - 1) / T3;
@@ -671,8 +784,8 @@ static bool slab_kernel_launchable() {
   if (ok < 0) {
     cudaFuncAttributes fa, fb;
     int dev = 0, smem_optin = 0;
-    ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16>) == cudaSuccess &&
-         cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+    ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16, false>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16, true>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
          fa.maxThreadsPerBlock >= slab::kThreads && fb.maxThreadsPerBlock >= slab::kThreads &&
          cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
          smem_optin >= slab::kSmemBytes;
@@ -682,13 +795,37 @@ static bool slab_kernel_launchable() {
 
 }  // namespace tc
 
-bool use_slab_kernel(const Plan& P, int item, int64_t count) {
+bool use_slab_kernel(const Plan& P, int item, int64_t count) { return slab_chunk(P, item, count) > 0; }
+
+// Slices per slab-kernel launch for an accumulate of `count` slices: count
+// itself (16, 32 or 64), or 64 for a Khatri-Rao plan's longer slabs (a
+// multiple of 64: those shapes would otherwise go to the plane kernel, which
+// does not take Khatri-Rao test matrices); 0 when the slab kernel does not apply.
+int64_t slab_chunk(const Plan& P, int item, int64_t count) {
   tc::slab::SlabArgs g;
-  return tc::plan_slab(P, item, count, &g);
+  if (tc::plan_slab(P, item, count, &g)) return count;
+  if (count > 64 && count % 64 == 0 && tc::plan_slab(P, item, 64, &g) && g.kry) return 64;
+  return 0;
 }
+
+static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                                   cudaStream_t st);
 
 cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                                cudaStream_t st) {
+  const int64_t chunk = slab_chunk(P, item, count);
+  if (chunk <= 0) return cudaErrorNotSupported;
+  const int64_t nd1 = plan_items_host(&P)[item].N[3];
+  for (int64_t a = 0; a < count; a += chunk) {
+    const cudaError_t e =
+        launch_slab_one(P, item, reinterpret_cast<const float*>(X) + a * nd1, first + a, chunk, ws, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
+                                   cudaStream_t st) {
   tc::slab::SlabArgs g;
   if (!tc::plan_slab(P, item, count, &g)) return cudaErrorNotSupported;
   if (!tc::slab_kernel_launchable()) return cudaErrorNotSupported;
@@ -697,18 +834,21 @@ cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t f
   g.status = reinterpret_cast<int*>((char*)ws + kStatusOff);
   g.first = first;
   using KernelFn = void (*)(tc::slab::SlabArgs);
-  const KernelFn kernels[2][3] = {
-      {tc::slab::sketch_slab_kernel<8, 16>, tc::slab::sketch_slab_kernel<8, 32>, tc::slab::sketch_slab_kernel<8, 64>},
-      {tc::slab::sketch_slab_kernel<16, 16>, tc::slab::sketch_slab_kernel<16, 32>,
-       tc::slab::sketch_slab_kernel<16, 64>}};
+  using namespace tc::slab;
+  const KernelFn kernels[2][2][3] = {
+      {{sketch_slab_kernel<8, 16, false>, sketch_slab_kernel<8, 32, false>, sketch_slab_kernel<8, 64, false>},
+       {sketch_slab_kernel<8, 16, true>, sketch_slab_kernel<8, 32, true>, sketch_slab_kernel<8, 64, true>}},
+      {{sketch_slab_kernel<16, 16, false>, sketch_slab_kernel<16, 32, false>, sketch_slab_kernel<16, 64, false>},
+       {sketch_slab_kernel<16, 16, true>, sketch_slab_kernel<16, 32, true>, sketch_slab_kernel<16, 64, true>}}};
   static bool attr_set = false;
   if (!attr_set) {
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 3; ++j) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kernels[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, tc::slab::kSmemBytes);
-        if (e != cudaSuccess) return e;
-      }
+      for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 3; ++j) {
+          const cudaError_t e =
+              cudaFuncSetAttribute(kernels[i][k][j], cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+          if (e != cudaSuccess) return e;
+        }
     attr_set = true;
   }
   {
@@ -720,7 +860,7 @@ cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t f
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
-  const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
+  const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.kry][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
   k<<<grid, tc::slab::kThreads, tc::slab::kSmemBytes, st>>>(g);
   return cudaGetLastError();
 }

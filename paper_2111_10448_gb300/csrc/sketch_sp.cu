@@ -331,7 +331,10 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
               qq[h] = c - rr[h] * g.nq;
               const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + rr[h]))
                                          : (uint64_t)(rr[h] + g.n1 * key);
-              z[h] = tm_quad_f32(g.wsb, kr_of(g.wsb, s.kr), g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
+              const DevSketch* krs = kr_of(g.wsb, s.kr);
+              // a mode-by-mode sketch takes its mode-1 factor here (scaled below)
+              z[h] = (krs && krs->kr_mbm) ? kr_f1_quad(g.wsb, *krs, rr[h], (uint32_t)qq[h])
+                                          : tm_quad_f32(g.wsb, krs, g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -449,6 +452,25 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
           }
         }
         }
+        // mode-by-mode Khatri-Rao sketch: column j scaled by the rounded product
+        // of the other modes' rows of this plane (rows of the lane: gq, gq + 8
+        // of each m-tile)
+        float sc[MT][2];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) sc[mt][0] = sc[mt][1] = 1.0f;
+        {
+          const DevSketch* krs = kr_of(g.wsb, s.kr);
+          if (krs && krs->kr_mbm) {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int j = mt * 16 + gq + 8 * h;
+                const float4 c = kr_scale_quad(g.wsb, *krs, (uint64_t)key, (uint32_t)(j >> 2), TF ? TT_PREC_TF32 : TT_PREC_BF16);
+                sc[mt][h] = (j & 3) == 0 ? c.x : (j & 3) == 1 ? c.y : (j & 3) == 2 ? c.z : c.w;
+              }
+          }
+        }
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -457,7 +479,8 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
-                if (j < sell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] + cl[mt][nt][e]);
+                if (j < sell && o < nout)
+                  atomicAdd(slot + j * g.ldo + o, (ch[mt][nt][e] + cl[mt][nt][e]) * sc[mt][e >> 1]);
               }
             }
           }

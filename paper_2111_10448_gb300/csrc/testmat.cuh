@@ -90,6 +90,35 @@ __device__ __forceinline__ void kr_quad_f64(const void* wsb, const DevSketch& s,
   }
 }
 
+// Mode-by-mode row sketch of X_{d-1} (DevSketch::kr_mbm): the mode-1 factor
+// quad of i_1 (FP32, unrounded; an MMA operand after rounding) ...
+__device__ __forceinline__ float4 kr_f1_quad(const void* wsb, const DevSketch& s, int64_t i1, uint32_t q) {
+  const float* tab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
+  return *reinterpret_cast<const float4*>(tab + s.kr_off[0] + i1 * s.kr_lp + 4 * q);
+}
+// ... and the column scale of block `rest` (the row index divided by n_1): the
+// product of the rows of modes k..2 (decreasing order), FP32, rounded to the
+// MMA type `prec`.
+__device__ __forceinline__ float4 kr_scale_quad(const void* wsb, const DevSketch& s, uint64_t rest, uint32_t q,
+                                                int prec) {
+  const float* tab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(wsb) + s.kr_tab);
+  uint64_t row = rest * (uint64_t)s.kr_n[0];
+  float4 v = make_float4(1.f, 1.f, 1.f, 1.f);
+  for (int t = s.kr_nm - 1; t >= 1; --t) {
+    const int64_t i = kr_digit_dec(row, s.kr_stride[t], false);
+    const float4 f = *reinterpret_cast<const float4*>(tab + s.kr_off[t] + i * s.kr_lp + 4 * q);
+    if (t == s.kr_nm - 1) {
+      v = f;
+    } else {
+      v.x = __fmul_rn(v.x, f.x);
+      v.y = __fmul_rn(v.y, f.y);
+      v.z = __fmul_rn(v.z, f.z);
+      v.w = __fmul_rn(v.w, f.w);
+    }
+  }
+  return make_float4(round_prec(v.x, prec), round_prec(v.y, prec), round_prec(v.z, prec), round_prec(v.w, prec));
+}
+
 // The quad a kernel uses: kr = the sketch's device record when its test
 // matrix is Khatri-Rao, nullptr for the dense stream.
 __device__ __forceinline__ float4 tm_quad_f32(const void* wsb, const DevSketch* kr, uint64_t seed, uint32_t sid,
@@ -102,6 +131,24 @@ __device__ __forceinline__ void tm_quad_f64(const void* wsb, const DevSketch* kr
   if (kr) kr_quad_f64(wsb, *kr, row, q, z);
   else normals4_f64(seed, sid, row, q, z);
 }
+// Final test-matrix entries of a TF32 / BF16 path as FP32 values (for the
+// kernels that use them in FP32 / FP64 arithmetic: the middle-core matrix B
+// and the backward): entries rounded to the MMA type, except a mode-by-mode
+// Khatri-Rao sketch, whose entry is the exact FP32 product of its two rounded
+// parts.
+__device__ __forceinline__ float4 tm_quad_mixed(const void* wsb, const DevSketch* kr, uint64_t seed, uint32_t sid,
+                                                uint64_t row, uint32_t q, int prec) {
+  if (kr && kr->kr_mbm) {
+    const uint64_t rest = row / (uint64_t)kr->kr_n[0];
+    const float4 f = kr_f1_quad(wsb, *kr, (int64_t)(row - rest * (uint64_t)kr->kr_n[0]), q);
+    const float4 c = kr_scale_quad(wsb, *kr, rest, q, prec);
+    return make_float4(__fmul_rn(round_prec(f.x, prec), c.x), __fmul_rn(round_prec(f.y, prec), c.y),
+                       __fmul_rn(round_prec(f.z, prec), c.z), __fmul_rn(round_prec(f.w, prec), c.w));
+  }
+  const float4 z = tm_quad_f32(wsb, kr, seed, sid, row, q);
+  return make_float4(round_prec(z.x, prec), round_prec(z.y, prec), round_prec(z.z, prec), round_prec(z.w, prec));
+}
+
 // Device record of sketch gsk of the workspace, or nullptr (gsk < 0: dense).
 __device__ __forceinline__ const DevSketch* kr_of(const void* wsb, int gsk) {
   return gsk >= 0 ? ws_sketches(wsb) + gsk : nullptr;

@@ -712,3 +712,31 @@ def test_kr_one_sided_exact_recovery(d):
     for fn in (PS.pstt_onepass, PS.pstt):
         o = fn(x, dims, ranks=tgt, p=3, seed=d + 50, drm="kr")
         assert np.linalg.norm(x - tt.tt_full(o["cores"])) <= 1e-12 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "tf32"])
+def test_kr_last_row_sketch_mode_by_mode_in_rounded_arithmetic(fmt):
+    """The rounded Khatri-Rao Psi_{d-1} of the mixed paths equals eq.
+    (sketch_orig)'s mode-by-mode evaluation: each block X(:, w, :)^T times the
+    rounded mode-1 factor, scaled column-wise by the rounded product of the
+    other modes' rows for that block, summed over the blocks."""
+    dims = [5, 3, 4, 6]
+    d = len(dims)
+    x = ti.random_tt(dims, [1, 2, 2, 2, 1], seed=3, noise=1e-2)
+    l, seed = 6, 21
+    sk = P.sketches(x, dims, [None] + [l] * d, seed, 1, test_fmt=fmt, drm="kr")
+    s = 64 + d - 1
+    F1 = philox.round_to(philox.kr_factor(seed, s, 1, dims[0], l), fmt)
+    F2 = philox.kr_factor(seed, s, 2, dims[1], l)
+    F3 = philox.kr_factor(seed, s, 3, dims[2], l)
+    X = x.reshape(dims, order="F")
+    ref = np.zeros((dims[3], l))
+    for i2 in range(dims[1]):
+        for i3 in range(dims[2]):
+            scale = philox.round_to(F3[i3] * F2[i2], fmt)
+            ref += (X[:, i2, i3, :].T @ F1) * scale[None, :]
+    np.testing.assert_allclose(sk["R"][d - 1], ref, rtol=1e-12, atol=1e-12)
+    # entries are products of two rounded numbers: exact in FP32, not in fmt
+    Ps = sk["Psi"][d - 1]
+    assert np.array_equal(Ps.astype(np.float32).astype(np.float64), Ps)
+    assert not np.array_equal(philox.round_to(Ps, fmt), Ps)
