@@ -30,6 +30,8 @@ if ROOT not in sys.path:
 METRIC = "PSTT2 tensor entries/s and HBM roofline fraction, mixed vs FP64 GPU at eps=1e-6"
 WORKLOAD = dict(dims=[256, 256, 256, 256], eps=1e-6, p=10, rmax=6, seed=1)
 SLAB = 16  # last-mode slices per 1 GiB slab (256^3 * 4 B * 16 = 1 GiB)
+HEADLINE_DRM = "kr"  # the paper's test matrices for its streaming implementation (Sec. 4.2)
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure on this machine)
 
 
 def parse():
@@ -39,6 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--drm", default=HEADLINE_DRM, choices=["gauss", "kr"],
+                    help="test matrices of the headline: dense Gaussian or Khatri-Rao")
+    ap.add_argument("--slab", type=int, default=SLAB, help="last-mode slices per accumulate (16 = 1 GiB at n=256)")
     ap.add_argument("--n", type=int, default=256, help="mode size (default: the 17 GB workload)")
     ap.add_argument("--mid", type=int, default=0,
                     help="size of the two middle modes (default n); a smaller value keeps the kernel's "
@@ -677,23 +682,58 @@ def run_gpu(a):
 
     kw = dict(eps=WORKLOAD["eps"], rmax=WORKLOAD["rmax"], p=WORKLOAD["p"], seed=WORKLOAD["seed"] + rank,
               x_dtype=torch.float32, device=dev)
-    t = P.TTSketch(dims, prec=a.prec, **kw)
+    slab = a.slab if n % a.slab == 0 else n
 
-    def step(ev=None):
+    def stream_step(t, sl, evs=None):
+        """begin + one accumulate per slab of `sl` last-mode slices + finalize;
+        evs: a (start, end) event pair per slab around its accumulate."""
         t.begin(stream)
-        if ev is not None:
-            ev[0].record(stream)
-        t.accumulate(X, 0, n, stream)
-        if ev is not None:
-            ev[1].record(stream)
+        for k, s0 in enumerate(range(0, n, sl)):
+            if evs is not None:
+                evs[k][0].record(stream)
+            t.accumulate(X[s0 * Nd1:(s0 + sl) * Nd1], s0, sl, stream)
+            if evs is not None:
+                evs[k][1].record(stream)
         t.finalize(stream)
 
+    STATUS = {0: "TT_OK", 5: "TT_ERR_RANK_DEFICIENT", 6: "TT_ERR_TIMEOUT", 7: "TT_WARN_RANK_CAP"}
+
+    def measure_form(t, sl, steps, warmup):
+        """Whole-step and per-slab sketch times of one form (CUDA events on
+        the launching stream), its status, ranks and error against X."""
+        for _ in range(warmup):
+            stream_step(t, sl)
+        stream.synchronize()
+        nsl = n // sl
+        evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsl)]
+               for _ in range(steps)]
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(steps):
+            stream_step(t, sl, evs[i])
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        per_slab = [s_.elapsed_time(e_) for ev in evs for s_, e_ in ev]
+        st_, rk_ = t.status(stream)
+        e2 = t.error(X, stream)
+        stream.synchronize()
+        e2 = e2.cpu().numpy()
+        sk_ms = sum(per_slab) / steps
+        return {"step_ms": f0.elapsed_time(f1) / steps, "sketch_ms": sk_ms,
+                "sketch_ms_per_launch": statistics.mean(per_slab), "launches_per_step": nsl,
+                "hbm_frac_of_measured": ntot * 4 / (sk_ms * 1e-3) / 1e9 / measured_peaks()[0],
+                "status": STATUS.get(st_, st_), "ranks": rk_, "rel_err_vs_X": float((e2[0] / e2[1]) ** 0.5)}
+
+    # the headline: the test matrices of --drm, 1 GiB slabs (16 slices) streamed
+    t = P.TTSketch(dims, prec=a.prec, drm=a.drm, **kw)
     for _ in range(a.warmup):
-        step()
+        stream_step(t, slab)
     stream.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    nsl = n // slab
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsl)]
+           for _ in range(a.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(torch.cuda.get_device_properties(dev).index if hasattr(torch.cuda.get_device_properties(dev), "index") else local)
     clk.start()
@@ -704,7 +744,7 @@ def run_gpu(a):
         torch.distributed.barrier()
     e0.record(stream)
     for i in range(a.steps):
-        step(evs[i])
+        stream_step(t, slab, evs[i])
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -712,7 +752,9 @@ def run_gpu(a):
     l1 = L.tt_kernel_launches()
     clocks = clk.stop()
     ms, _, value = whole_job(e0.elapsed_time(e1) / a.steps, ntot, world, dev)
-    sketch_ms = statistics.mean(s.elapsed_time(e) for s, e in evs)
+    per_slab = [s_.elapsed_time(e_) for ev in evs for s_, e_ in ev]
+    sketch_ms = sum(per_slab) / a.steps
+    launch_ms = statistics.mean(per_slab)
     st, ranks = t.status(stream)
 
     # accuracy of this run: ||X - X~|| / ||X|| on the device
@@ -722,14 +764,26 @@ def run_gpu(a):
     rel_err = float((err2[0] / err2[1]) ** 0.5)
 
     out = {}
-    # ---- FP64 GPU path, same eps (one step after one warm-up)
+    # ---- the other forms of the same workload: dense Gaussian / Khatri-Rao
+    # test matrices, 1 GiB slabs / the whole last mode in one accumulate
+    if not a.no_forms:
+        forms = {}
+        for drm_, sl_ in (("gauss", n), ("gauss", slab), ("kr", slab), ("kr", n)):
+            if drm_ == a.drm and sl_ == slab:
+                continue
+            tf = P.TTSketch(dims, prec=a.prec, drm=drm_, **kw)
+            forms[f"{drm_}_{sl_}_slices_per_accumulate"] = measure_form(tf, sl_, max(3, min(a.steps, 10)), 2)
+            del tf
+        out["forms"] = forms
+
+    # ---- FP64 GPU path, same eps, same slabs (one step after one warm-up)
     if not a.no_fp64:
-        f = P.TTSketch(dims, prec="fp64", **kw)
-        f.pstt2(X, stream)
+        f = P.TTSketch(dims, prec="fp64", drm=a.drm, **kw)
+        stream_step(f, slab)
         stream.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        f.pstt2(X, stream)
+        stream_step(f, slab)
         g1.record(stream)
         torch.cuda.synchronize(dev)
         f_ms = g0.elapsed_time(g1)
@@ -740,13 +794,19 @@ def run_gpu(a):
         stream.synchronize()
         fe, d2 = fe.cpu().numpy(), d2.cpu().numpy()
         del Xf
+        shapes64 = [tuple(S.shape) for _, _, S in f.sketches(0)]
+        fl64 = 2 * sum(w for _, w in shapes64)  # FP64 FMA flops per entry, every sketch
         out["fp64_gpu"] = {"value": ntot / (f_ms * 1e-3), "unit": "entries/s", "ms_per_step": f_ms,
                            "rel_err_vs_X": float((fe[0] / fe[1]) ** 0.5),
                            "mixed_vs_fp64_rel": float((d2[0] / err2[1]) ** 0.5),
-                           "ranks": f.status(stream)[1]}
+                           "ranks": f.status(stream)[1],
+                           "roofline": {"bound": "fp64 alu", "flops_per_entry": fl64,
+                                        "achieved_tflops": ntot * fl64 / (f_ms * 1e-3) / 1e12,
+                                        "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "nominal GB300 FP64",
+                                        "frac": ntot * fl64 / (f_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}}
         del f
 
-    # ---- e2e: X from pinned host memory in 1 GiB slabs, cores back to host
+    # ---- e2e: X from pinned host memory, one 1 GiB slab at a time, cores back
     if not a.no_e2e:
         Xh = torch.empty(ntot, dtype=torch.float32, pin_memory=True)
         Xh.copy_(X)
@@ -754,32 +814,30 @@ def run_gpu(a):
         cores_h = torch.empty(t.cores.numel(), dtype=torch.float64, pin_memory=True)
         ranks_h = torch.empty(t.ranks.numel(), dtype=torch.int32, pin_memory=True)
         copy = torch.cuda.Stream(device=dev)
-        slab = SLAB * Nd1
-        group = 128 if n % 128 == 0 else n   # slices per accumulate (tensor-core M tile)
+        SL = SLAB if n % SLAB == 0 else n
 
         def e2e_step():
-            done = []
-            for s0 in range(0, n, SLAB):
+            # each slab is copied on a second stream and sketched as soon as
+            # its copy has landed
+            t.begin(stream)
+            for s0 in range(0, n, SL):
                 with torch.cuda.stream(copy):
-                    Xd[s0 * Nd1:(s0 + SLAB) * Nd1].copy_(Xh[s0 * Nd1:(s0 + SLAB) * Nd1], non_blocking=True)
+                    Xd[s0 * Nd1:(s0 + SL) * Nd1].copy_(Xh[s0 * Nd1:(s0 + SL) * Nd1], non_blocking=True)
                     ev = torch.cuda.Event()
                     ev.record(copy)
-                done.append(ev)
-            t.begin(stream)
-            for g0_ in range(0, n, group):
-                stream.wait_event(done[(g0_ + group) // SLAB - 1])
-                t.accumulate(Xd[g0_ * Nd1:(g0_ + group) * Nd1], g0_, group, stream)
+                stream.wait_event(ev)
+                t.accumulate(Xd[s0 * Nd1:(s0 + SL) * Nd1], s0, SL, stream)
             t.finalize(stream)
             with torch.cuda.stream(stream):
                 cores_h.copy_(t.cores, non_blocking=True)
                 ranks_h.copy_(t.ranks, non_blocking=True)
 
         def e2e_direct_step():
-            # the sketch kernel reads the pinned host slabs itself (over the
+            # the sketch kernel reads each pinned host slab itself (over the
             # host link), no staging copy
             t.begin(stream)
-            for g0_ in range(0, n, group):
-                t.accumulate(Xh[g0_ * Nd1:(g0_ + group) * Nd1], g0_, group, stream)
+            for s0 in range(0, n, SL):
+                t.accumulate(Xh[s0 * Nd1:(s0 + SL) * Nd1], s0, SL, stream)
             t.finalize(stream)
             with torch.cuda.stream(stream):
                 cores_h.copy_(t.cores, non_blocking=True)
@@ -801,13 +859,14 @@ def run_gpu(a):
         out["e2e"] = {"value": world * ntot / (e_ms * 1e-3), "unit": "entries/s", "ms_per_step": e_ms,
                       "h2d_bytes_per_step": ntot * 4,
                       "d2h_bytes_per_step": t.cores.numel() * 8 + t.ranks.numel() * 4,
-                      "mode": "kernel reads pinned host X directly" if e_direct <= e_copy
-                      else "1 GiB pinned-host slabs copied on a second stream",
+                      "mode": "kernel reads each pinned host slab directly" if e_direct <= e_copy
+                      else "1 GiB pinned-host slabs copied on a second stream, each sketched when it lands",
                       "ms_copy_slabs": e_copy, "ms_direct_host_reads": e_direct}
         del Xh, Xd
 
     peak, peak_kind = measured_peaks()
-    achieved = ntot * 4 / (sketch_ms * 1e-3) / 1e9
+    # the dominant kernel: one launch sketches one slab (4 bytes per entry read once)
+    achieved = ntot // nsl * 4 / (launch_ms * 1e-3) / 1e9
     # the two other ceilings of the sketch, beside HBM: tensor pipe (every entry
     # feeds l MACs per sketch, twice for the hi + lo split of X) and test-matrix
     # generation (each test-matrix row once: sum over sketches of l * rows)
@@ -816,9 +875,13 @@ def run_gpu(a):
     normals = sum((ntot // rows) * w for rows, w in shapes)
     tpeak, tkind = measured_tensor_peak(a.prec)
     tflops = ntot * flops_pe / (sketch_ms * 1e-3) / 1e12
+    kind = t.kernel_kind(slab)
+    kname = {2: "sketch_slab_kernel" if slab < 128 else "sketch_tc_kernel", 3: "sketch_sp_kernel",
+             1: "sketch_mma_kernel", 0: "sketch_f64_kernel"}[kind]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_record(f"sketch_{a.prec}_{n}x{m}x{m}x{n}"), "peak_kind": f"{peak_kind} hbm_gbs",
-                "kernel_ms": sketch_ms, "algorithmic_bytes": ntot * 4,
+                "traffic": traffic_record(f"{kname}_{a.prec}_{a.drm}_{n}x{m}x{m}x{slab}"),
+                "peak_kind": f"{peak_kind} hbm_gbs", "kernel": kname,
+                "kernel_ms": launch_ms, "algorithmic_bytes": ntot // nsl * 4,
                 "tensor": {"flops_per_entry": flops_pe, "achieved_tflops": tflops, "peak_tflops": tpeak,
                            "peak_kind": tkind, "frac": tflops / tpeak},
                 "rng": {"normals_per_entry": normals / ntot, "normals_per_step": normals}}
@@ -846,14 +909,21 @@ def run_gpu(a):
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": a.prec, "data": "synthetic",
                 "config": {"workload": f"Hilbert-type d=4 dims={dims} FP32 ({ntot * 4 / 1e9:.2f} GB) one-pass PSTT2, "
-                                       f"eps=1e-6 p=10 rmax=6, {a.prec} tensor-core sketch with X split hi+lo, "
-                                       "FP64 solves",
+                                       f"streamed in {n // slab} slabs of {slab} last-mode slices "
+                                       f"({slab * Nd1 * 4 / 2 ** 30:.2f} GiB each), eps=1e-6 p=10 rmax=6, "
+                                       f"{'Khatri-Rao' if a.drm == 'kr' else 'dense Gaussian'} test matrices, "
+                                       f"{a.prec} tensor-core sketch with X split hi+lo, FP64 solves",
+                           "test_matrices": a.drm, "slab_slices": slab,
                            "l2": "inputs larger than L2 (no flush needed)",
-                           "ranks": ranks, "status": st, "rel_err_vs_X": rel_err,
+                           "ranks": ranks, "status": STATUS.get(st, st), "rel_err_vs_X": rel_err,
+                           "meets_eps": rel_err <= WORKLOAD["eps"],
+                           "status_note": None if st == 0 else (
+                               "the rank rule stopped at rmax: the BF16 hi+lo sketch (about 2^-17 relative) "
+                               "cannot resolve the threshold eps/sqrt(d-1); the result is within 10 eps"),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),
-                "batched": out.get("batched"),
+                "batched": out.get("batched"), "forms": out.get("forms"),
                 "precision_form": out.get("precision_form"), "diff_form": out.get("diff_form"),
                 "second_workloads": out.get("second_workloads"), "one_sided": out.get("one_sided"),
                 "tucker2tt": out.get("tucker2tt")}

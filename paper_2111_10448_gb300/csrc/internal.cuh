@@ -174,6 +174,7 @@ constexpr int64_t kRankCopyOff = 64;
 struct Plan;
 const DevItem* plan_items_host(const Plan* p);
 int plan_num_items(const Plan* p);
+bool& plan_stream_tables(Plan& P);
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t first, int64_t count,

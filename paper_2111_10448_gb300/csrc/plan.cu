@@ -33,6 +33,7 @@ struct Plan {
   // streaming bookkeeping (single-item plans)
   std::vector<char> slab_seen;
   bool begun = false;
+  bool stream_tables = false;        // staged tables of the slab kernel valid for this decomposition
   const void* stream_ws = nullptr;   // workspace of the streaming decomposition begun last
   const void* forward_ws = nullptr;  // workspace of the last completed forward call
   BatchCfg bcfg{64, 4, 4};  // batched sketch launch shape (tt_plan_autotune)
@@ -543,6 +544,11 @@ int device_sm_count() {
   return n;
 }
 
+// The staged tables of the slab kernel that do not depend on the slab are
+// generated by the first accumulate of a decomposition and reused by the
+// others (begin / tt_pstt2 clear the flag).
+bool& plan_stream_tables(Plan& P) { return P.stream_tables; }
+
 // Start of a decomposition: clear the status word (so that a bit raised by
 // the sketch kernels survives until tt_query_status) and the sketches.
 static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
@@ -660,6 +666,7 @@ tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream) {
   if (s != TT_OK) return s;
   std::fill(P->slab_seen.begin(), P->slab_seen.end(), 0);
   P->begun = true;
+  P->stream_tables = false;
   P->stream_ws = ws;
   plan_mark_forward(P, ws, false);
   return TT_OK;
@@ -707,6 +714,7 @@ tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* 
   if (s != TT_OK) return s;
   s = zero_sketches(*P, 0, ws, st);
   if (s != TT_OK) return s;
+  P->stream_tables = false;
   s = accumulate(*P, 0, X, 0, it.n[it.d - 1], ws, st);
   if (s != TT_OK) return s;
   if (it.passes == 2) {

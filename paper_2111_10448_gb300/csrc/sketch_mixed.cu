@@ -1403,6 +1403,9 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
     attr_set = true;
   }
   if (!tc_kernel_launchable()) return launch_sketch_mma(P, item, X, first, count, ws, st);
+  // the staging area is rewritten here in this kernel's layout: a later slab-
+  // kernel launch of the same decomposition must stage its own blocks again
+  plan_stream_tables(const_cast<Plan&>(P)) = false;
   for (int side = 0; side < 2; ++side)
     for (int s = 0; s < (side ? g.nR : g.nL); ++s) {
       const tc::SkTc& sk = side ? g.row[s] : g.col[s];

@@ -596,10 +596,23 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
         for (int b = 0; b < tinf.nB && yok; ++b)
           for (int a = 0; a < tinf.nA; ++a, ++spn) {
             const uint32_t yb = spn & 1;
-            const uint64_t wg = (uint64_t)((tinf.kL0 + a) + g.WL * ((tinf.kRg0 + b) * g.G + gl));
-            float4 sc[ell / 4];
+            // the plane's rows of the mode-3 and mode-2 factors (i_3 = kR_g,
+            // i_2 = kL), all loads issued together; product in the row sketch's
+            // decreasing mode order, rounded to BF16 (the column scale)
+            const float* ktab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab);
+            const float4* f3 =
+                reinterpret_cast<const float4*>(ktab + kr3->kr_off[2] + ((tinf.kRg0 + b) * g.G + gl) * kr3->kr_lp);
+            const float4* f2 = reinterpret_cast<const float4*>(ktab + kr3->kr_off[1] + (tinf.kL0 + a) * kr3->kr_lp);
+            float4 sc[ell / 4], s2[ell / 4];
 #pragma unroll
-            for (int q = 0; q < ell / 4; ++q) sc[q] = kr_scale_quad(g.ws, *kr3, wg, (uint32_t)q, TT_PREC_BF16);
+            for (int q = 0; q < ell / 4; ++q) {
+              sc[q] = f3[q];
+              s2[q] = f2[q];
+            }
+#pragma unroll
+            for (int q = 0; q < ell / 4; ++q)
+              sc[q] = make_float4(round_bf16(__fmul_rn(sc[q].x, s2[q].x)), round_bf16(__fmul_rn(sc[q].y, s2[q].y)),
+                                  round_bf16(__fmul_rn(sc[q].z, s2[q].z)), round_bf16(__fmul_rn(sc[q].w, s2[q].w)));
             if (!mbar_wait(bar(TMY_FULL + yb), (spn >> 1) & 1, abort_flag, g.status)) {
               yok = false;
               break;
@@ -749,14 +762,25 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
     return 2 * ycols + t2 * g.H1 * 2 * ell + 2 * t3 * ell <= 512 && t2 * g.H1 * 16 <= kMaxChainL &&
            (g.kry || t2 * t3 * g.H1 * 16 <= kMaxChainL);
   };
-  int T2 = 1, T3 = 1;
+  // Each CTA takes a contiguous run of tiles, so the launch lasts as long as
+  // the CTA with the most super-planes: pick the shape that minimises that,
+  // weighted by the R_2 flush traffic (2048 FP64 atomics per kR group and tile,
+  // i.e. about 1 / T2 of a super-plane's own cost); ties: the larger T2.
+  const int64_t sms = device_sm_count();
+  int T2 = 0, T3 = 0;
+  double best = 1e300;
   for (int t2 = 1; t2 <= 8; ++t2)
-    for (int t3 = 1; t3 <= 8; ++t3)
-      if (t2 <= g.WL && t3 <= g.WRg && fits(t2, t3) && t2 * t3 > T2 * T3) {
+    for (int t3 = 1; t3 <= 8; ++t3) {
+      if (t2 > g.WL || t3 > g.WRg || !fits(t2, t3)) continue;
+      const int64_t tiles = ((g.WL + t2 - 1) / t2) * ((g.WRg + t3 - 1) / t3);
+      const double cost = (double)((tiles + sms - 1) / sms * t2 * t3) * (1.0 + 0.5 / t2);
+      if (cost < best || (cost == best && t2 > T2)) {
+        best = cost;
         T2 = t2;
         T3 = t3;
       }
-  if (!fits(T2, T3)) return false;
+    }
+  if (T2 == 0) return false;
   g.T2 = T2;
   g.T3 = T3;
   g.colL = 2 * ycols;
@@ -851,11 +875,15 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
         }
     attr_set = true;
   }
-  {
+  // the R_2 blocks (rows i_1 + n_1 kL) are the same for every slab: staged by
+  // the first launch of a decomposition
+  bool& ready = plan_stream_tables(const_cast<Plan&>(P));
+  if (!ready) {
     const int64_t total = g.WL * g.H1 * 16 * (g.ell / 4) * 8;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8LL * device_sm_count());
     count_launch();
     tc::slab::slab_table_kernel<<<blocks, 256, 0, st>>>(g, g.WL);
+    ready = true;
   }
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());

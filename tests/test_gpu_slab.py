@@ -125,3 +125,24 @@ def test_slab_pipeline_within_10eps(drm):
     rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
     print(f"slab pipeline {drm}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
     assert rx <= 1e-5 and rf <= 1e-5
+
+
+@pytest.mark.parametrize("drm", ["gauss", "kr"])
+def test_mixed_slab_sizes_in_one_stream(drm):
+    """Slabs of 16, 128 and 32 slices in one decomposition: the plane kernel
+    and the slab kernel share the staging area, and each restages what it
+    needs; the result equals one accumulate of the whole tensor up to FP32
+    accumulation order."""
+    dims = [256, 8, 16, 256]
+    x = ti.hilbert_type(dims, np.float32)
+    X = to_dev(x)
+    kw = dict(eps=1e-6, rmax=6, p=10, seed=1, prec="bf16", drm=drm)
+    one = TTSketch(dims, **kw).pstt2(X)
+    t = TTSketch(dims, **kw)
+    nd1 = 256 * 8 * 16
+    t.begin()
+    for a, cnt in [(0, 16), (128, 128), (16, 32), (48, 16), (64, 64)]:
+        t.accumulate(X[a * nd1:(a + cnt) * nd1], a, cnt)
+    t.finalize()
+    assert t.status()[1] == one.status()[1]
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
