@@ -129,6 +129,8 @@ struct DevItem {
   int64_t sptab_doubles;    // its size (0 when the small-plane kernel cannot serve the item)
   int64_t off_gentab;       // generic tile kernel: staged test-matrix rows of the sketches whose
   int64_t gentab_doubles;   // rows repeat across planes (0: none)
+  int64_t off_adjtab;       // tensor-core sketch adjoint: the sketch adjoints split into hi + lo in
+  int64_t adjtab_doubles;   // the MMA type, every sketch's rows x lpad (0: that kernel does not apply)
 };
 
 struct Task {               // one block of one TSQR level (finalize)
@@ -217,6 +219,13 @@ int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int ta);
 cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
 cudaError_t launch_batch_zero(const Plan& P, void* ws, cudaStream_t st);
 cudaError_t launch_kr_tables(const Plan& P, int item, void* ws, cudaStream_t st);
+// Terms of the MMA type that each FP64 sketch adjoint is split into for the
+// tensor-core sketch adjoint: three capture the FP32 value (8 + 8 + 8 bits
+// in BF16, 11 + 11 + 2 in TF32), so the products are as exact as the FP32
+// accumulation.
+constexpr int kAdjParts = 3;
+bool adjoint_sp_eligible(const Plan& P, int item);
+cudaError_t launch_adjoint_sp(const Plan& P, int item, void* dX, void* ws, cudaStream_t st);
 cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);
 
 int device_sm_count();

@@ -320,6 +320,20 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.sptab_doubles = ok ? std::max<int64_t>(1, (bytes + 7) / 8) : 0;
   }
   it.off_sptab = it.sptab_doubles ? ws.take(it.sptab_doubles) : 0;
+  // The tensor-core sketch adjoint of the backward (single-problem, two-sided,
+  // dense Gaussian TF32 / BF16 plans whose planes the small-plane kernel
+  // serves): each sketch adjoint split into kAdjParts terms of the MMA type,
+  // row-major rows x lpad (lpad = 16 or 32 elements of 2 or 4 bytes).
+  it.adjtab_doubles = 0;
+  if (single && it.sptab_doubles > 0 && !it.sided1 && !kr && q.passes == 1) {
+    int lmax = 0;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) lmax = std::max(lmax, P.sketches[si].width);
+    const int64_t lpad = lmax <= 16 ? 16 : 32, esz = q.prec == TT_PREC_TF32 ? 4 : 2;
+    int64_t bytes = 0;
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) bytes += P.sketches[si].rows * lpad * esz * kAdjParts;
+    it.adjtab_doubles = (bytes + 7) / 8;
+  }
+  it.off_adjtab = it.adjtab_doubles ? ws.take(it.adjtab_doubles) : 0;
   // Staging area of the generic tile kernel (single-problem plans whose item
   // neither the plane kernel nor the small-plane kernel serves; the batched
   // kernel draws its rows per tile): the test-matrix rows of each

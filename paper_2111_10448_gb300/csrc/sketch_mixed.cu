@@ -1290,6 +1290,9 @@ cudaError_t launch_pbar_ls(const Plan& P, int item, void* ws, const int* ranks, 
 }
 
 cudaError_t launch_sketch_adjoint(const Plan& P, int item, void* dX, void* ws, cudaStream_t st) {
+  // planes of at most 32 x 32 with dense TF32 / BF16 test matrices: the
+  // tensor-core form (one warp a plane, rank-l products on mma.sync)
+  if (adjoint_sp_eligible(P, item)) return launch_adjoint_sp(P, item, dX, ws, st);
   const DevItem& it = plan_items_host(&P)[item];
   const int64_t nA = (it.n[0] + 63) / 64, nB = (it.n[it.d - 1] + 31) / 32;
   const int64_t total = it.W * nA * nB;

@@ -3,13 +3,16 @@ reconstruction, through the C ABI, against the torch-autograd oracle gradient
 (oracle/grad.py, itself pinned by finite differences) and against central
 finite differences of the GPU forward map.  Bar: 1e-6 relative (the FP64
 path; the FP32 storage of X is the same on both sides)."""
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
 
 import ttinputs as ti
-from oracle import grad as OG
+from oracle import grad as OG, philox
 from paper_2111_10448_gb300 import PSTT2Fn, TTReconstructFn, TTSketch
+from paper_2111_10448_gb300 import _native as NN
 from tests.gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
@@ -155,3 +158,74 @@ def test_vjp_mixed_precision_matches_rounded_oracle(prec):
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     print(f"{prec} VJP rel err vs rounded oracle: {err:.2e}")
     assert err <= 1e-4, err
+
+
+def _gpu_test_matrices(ref, dims, seed, prec):
+    """The test matrices exactly as the GPU draws them (tt_test_matrix: the
+    FP32 generator rounded to the MMA type), in the oracle's layout."""
+    code = {"bf16": NN.TT_PREC_BF16, "tf32": NN.TT_PREC_TF32}[prec]
+    out = {"Omega": {}, "Psi": {}}
+    for key, mats in (("Omega", ref["sketch"]["Omega"]), ("Psi", ref["sketch"]["Psi"])):
+        for k, M in mats.items():
+            rows, l = M.shape
+            sid = k if key == "Omega" else 64 + k
+            buf = torch.empty(rows * l, dtype=torch.float64, device="cuda")
+            NN.check(NN.lib().tt_test_matrix(seed, sid, 0, rows, l, code, C.c_void_p(buf.data_ptr()),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream)), "tm")
+            out[key][k] = buf.cpu().numpy().reshape(l, rows).T.copy()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("dims,r,target,p,slabs", [
+    ([12, 10, 9, 8, 14], [1, 3, 4, 4, 3, 1], [1, 2, 3, 3, 2, 1], 5, None),   # widths 7..8, lpad 16
+    ([32, 6, 5, 32], [1, 4, 5, 4, 1], [1, 4, 8, 4, 1], 20, [(16, 16), (0, 16)]),  # widths 24..28, lpad 32, streamed
+])
+def test_tensor_core_sketch_adjoint_matches_rounded_oracle(prec, dims, r, target, p, slabs):
+    """The tensor-core sketch adjoint (planes of at most 32 x 32: one warp a
+    plane, the split sketch adjoints times the test-matrix rows on mma.sync).
+    (1) Against the oracle gradient of the map whose test matrices are the
+    GPU's own (exported with tt_test_matrix), linearised where the forward
+    linearised: the mixed sketches see X as its two-term split hi + lo in the
+    MMA type, so the oracle takes x' = hi + lo.  Only the kernel's arithmetic
+    is left -- the FP32 rounding of each FP64 adjoint (split exactly into
+    three terms of the MMA type) and FP32 accumulation, 2^-24 relative to the
+    sum of the magnitudes -- bar 1e-5.  (2) Against the oracle with its own
+    rounded FP64 normals at x: the FP32 generator lands on the other BF16
+    neighbour in under 0.5% of the entries (one ulp, 2^-8 relative), which
+    moves the gradient by about sqrt(0.005) 2^-8 = 3e-4, and the split of X
+    (2^-17) moves it by up to 3e-4 on the second instance, whose middle rank
+    of 8 lies above the tensor's rank (the map is ill-conditioned there);
+    TF32 is 8 to 40 times closer -- bar 1e-3.  A forward streamed in slabs leaves
+    slab-sized staging tables, which the backward restages for the whole
+    last mode."""
+    x = ti.random_tt(dims, r, seed=4, noise=1e-2).astype(np.float32).astype(np.float64)
+    t = TTSketch(dims, ranks=target, p=p, seed=2, x_dtype=torch.float32, prec=prec)
+    X = to_dev(x, torch.float32)
+    if slabs is None:
+        t.pstt2(X)
+    else:
+        nd1 = int(np.prod(dims[:-1]))
+        t.begin()
+        for a, c in slabs:
+            t.accumulate(X[a * nd1:(a + c) * nd1].clone(), a, c)
+        t.finalize()
+    _, ranks = t.status()
+    ref = OG.forward_ref(x, dims, ranks=target, p=p, seed=2, test_fmt=prec)
+    assert ranks == ref["r"]
+    dc, lst = padded_dcores(t, ranks, np.random.default_rng(3))
+    dX = torch.full((x.size,), float("nan"), dtype=torch.float32, device="cuda")
+    t.backward(torch.tensor(dc, device="cuda"), dX)
+    got = dX.double().cpu().numpy()
+    assert np.all(np.isfinite(got))
+    want = OG.cores_vjp(x, dims, ref, lst)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    own = dict(ref)
+    own["sketch"] = dict(ref["sketch"], **_gpu_test_matrices(ref, dims, 2, prec))
+    hi = philox.round_to(x, prec)
+    want_own = OG.cores_vjp(hi + philox.round_to(x - hi, prec), dims, own, lst)
+    err_own = np.linalg.norm(got - want_own) / np.linalg.norm(want_own)
+    print(f"{prec} {dims} tensor-core adjoint rel err: vs the oracle with the GPU's test matrices {err_own:.2e}, "
+          f"vs the oracle's own {err:.2e}")
+    assert err_own <= 1e-5, err_own
+    assert err <= 1e-3, err
