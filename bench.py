@@ -45,6 +45,9 @@ def parse():
                     help="test matrices of the headline: dense Gaussian or Khatri-Rao")
     ap.add_argument("--slab", type=int, default=SLAB, help="last-mode slices per accumulate (16 = 1 GiB at n=256)")
     ap.add_argument("--n", type=int, default=256, help="mode size (default: the 17 GB workload)")
+    ap.add_argument("--nlast", type=int, default=0,
+                    help="size of the last mode (default n); with --slab it keeps the slab shape of a launch "
+                         "on a smaller tensor (profiling)")
     ap.add_argument("--mid", type=int, default=0,
                     help="size of the two middle modes (default n); a smaller value keeps the kernel's "
                          "tile shape on a smaller tensor (profiling)")
@@ -64,6 +67,8 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload (profiling); prints its own JSON line")
     ap.add_argument("--batch-prec", default="bf16,fp64", help="precisions of the batched workload")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="run only the differentiation form (profiling); prints its own JSON line")
     ap.add_argument("--precision-only", default="",
                     help="run only the precision form in these precisions, e.g. 'bf16' or 'fp64,tf32,bf16' "
                          "(profiling); prints its own JSON line")
@@ -641,6 +646,15 @@ def run_precision_only(a):
     print(json.dumps({"precision_form": run_precision(a, dev, P, stream)}), flush=True)
 
 
+def run_diff_only(a):
+    import torch
+    import paper_2111_10448_gb300 as P
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    print(json.dumps({"diff_form": run_diff(a, dev, P, stream)}), flush=True)
+
+
 def run_batched_only(a):
     import torch
     import paper_2111_10448_gb300 as P
@@ -668,8 +682,9 @@ def run_gpu(a):
     L = P.lib()
     n = a.n
     m = a.mid or n
-    dims = [n, m, m, n]
-    ntot = n * m * m * n
+    nl = a.nlast or n
+    dims = [n, m, m, nl]
+    ntot = n * m * m * nl
     Nd1 = n * m * m
     stream = torch.cuda.Stream(device=dev)
     sp = C.c_void_p(stream.cuda_stream)
@@ -677,18 +692,18 @@ def run_gpu(a):
     # X resident in HBM (generated on the device, not timed)
     X = torch.empty(ntot, dtype=torch.float32, device=dev)
     nn = (C.c_int64 * 4)(*dims)
-    N.check(L.tt_generate_hilbert_type(4, nn, 0, n, C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
+    N.check(L.tt_generate_hilbert_type(4, nn, 0, nl, C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
     stream.synchronize()
 
     kw = dict(eps=WORKLOAD["eps"], rmax=WORKLOAD["rmax"], p=WORKLOAD["p"], seed=WORKLOAD["seed"] + rank,
               x_dtype=torch.float32, device=dev)
-    slab = a.slab if n % a.slab == 0 else n
+    slab = a.slab if nl % a.slab == 0 else nl
 
     def stream_step(t, sl, evs=None):
         """begin + one accumulate per slab of `sl` last-mode slices + finalize;
         evs: a (start, end) event pair per slab around its accumulate."""
         t.begin(stream)
-        for k, s0 in enumerate(range(0, n, sl)):
+        for k, s0 in enumerate(range(0, nl, sl)):
             if evs is not None:
                 evs[k][0].record(stream)
             t.accumulate(X[s0 * Nd1:(s0 + sl) * Nd1], s0, sl, stream)
@@ -704,7 +719,7 @@ def run_gpu(a):
         for _ in range(warmup):
             stream_step(t, sl)
         stream.synchronize()
-        nsl = n // sl
+        nsl = nl // sl
         evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsl)]
                for _ in range(steps)]
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -731,7 +746,7 @@ def run_gpu(a):
     stream.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    nsl = n // slab
+    nsl = nl // slab
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsl)]
            for _ in range(a.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -768,7 +783,7 @@ def run_gpu(a):
     # test matrices, 1 GiB slabs / the whole last mode in one accumulate
     if not a.no_forms:
         forms = {}
-        for drm_, sl_ in (("gauss", n), ("gauss", slab), ("kr", slab), ("kr", n)):
+        for drm_, sl_ in (("gauss", nl), ("gauss", slab), ("kr", slab), ("kr", nl)):
             if drm_ == a.drm and sl_ == slab:
                 continue
             tf = P.TTSketch(dims, prec=a.prec, drm=drm_, **kw)
@@ -814,13 +829,13 @@ def run_gpu(a):
         cores_h = torch.empty(t.cores.numel(), dtype=torch.float64, pin_memory=True)
         ranks_h = torch.empty(t.ranks.numel(), dtype=torch.int32, pin_memory=True)
         copy = torch.cuda.Stream(device=dev)
-        SL = SLAB if n % SLAB == 0 else n
+        SL = SLAB if nl % SLAB == 0 else nl
 
         def e2e_step():
             # each slab is copied on a second stream and sketched as soon as
             # its copy has landed
             t.begin(stream)
-            for s0 in range(0, n, SL):
+            for s0 in range(0, nl, SL):
                 with torch.cuda.stream(copy):
                     Xd[s0 * Nd1:(s0 + SL) * Nd1].copy_(Xh[s0 * Nd1:(s0 + SL) * Nd1], non_blocking=True)
                     ev = torch.cuda.Event()
@@ -836,7 +851,7 @@ def run_gpu(a):
             # the sketch kernel reads each pinned host slab itself (over the
             # host link), no staging copy
             t.begin(stream)
-            for s0 in range(0, n, SL):
+            for s0 in range(0, nl, SL):
                 t.accumulate(Xh[s0 * Nd1:(s0 + SL) * Nd1], s0, SL, stream)
             t.finalize(stream)
             with torch.cuda.stream(stream):
@@ -909,7 +924,7 @@ def run_gpu(a):
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": a.prec, "data": "synthetic",
                 "config": {"workload": f"Hilbert-type d=4 dims={dims} FP32 ({ntot * 4 / 1e9:.2f} GB) one-pass PSTT2, "
-                                       f"streamed in {n // slab} slabs of {slab} last-mode slices "
+                                       f"streamed in {nl // slab} slabs of {slab} last-mode slices "
                                        f"({slab * Nd1 * 4 / 2 ** 30:.2f} GiB each), eps=1e-6 p=10 rmax=6, "
                                        f"{'Khatri-Rao' if a.drm == 'kr' else 'dense Gaussian'} test matrices, "
                                        f"{a.prec} tensor-core sketch with X split hi+lo, FP64 solves",
@@ -938,6 +953,8 @@ def main():
         run_reference(a)
     elif a.batched_only:
         run_batched_only(a)
+    elif a.diff_only:
+        run_diff_only(a)
     elif a.precision_only:
         run_precision_only(a)
     elif a.second_only:

@@ -17,8 +17,20 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "../../include/ttsketch.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace tts {
+
+// Host-side NVTX range named after the C-ABI call that opens it, so that a
+// timeline profiler shows plan building, sketching, finalisation and the
+// backward as named spans (a few nanoseconds when no profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 

@@ -600,9 +600,13 @@ using namespace tts;
 
 extern "C" {
 
-tt_status tt_sketch_plan(const tt_problem* prob, tt_plan_t* out) { return make_plan(prob, 1, out); }
+tt_status tt_sketch_plan(const tt_problem* prob, tt_plan_t* out) {
+  NvtxRange nvtx("tt_sketch_plan");
+  return make_plan(prob, 1, out);
+}
 
 tt_status tt_sketch_plan_batched(const tt_problem* probs, int count, tt_plan_t* out) {
+  NvtxRange nvtx("tt_sketch_plan_batched");
   return make_plan(probs, count, out);
 }
 
@@ -670,6 +674,7 @@ tt_status tt_plan_problem(tt_plan_t plan, int item, tt_problem* out) {
 }
 
 tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_begin");
   Plan* P = as_plan(plan);
   if (!P || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   if (P->items[0].passes != 1) return TT_ERR_UNSUPPORTED;
@@ -688,6 +693,7 @@ tt_status tt_pstt2_begin(tt_plan_t plan, void* ws, tt_stream_t stream) {
 
 tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_last,
                               int64_t count_last, void* ws, tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_accumulate");
   Plan* P = as_plan(plan);
   if (!P || !ws || !slab || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   const DevItem& it = P->items[0];
@@ -706,6 +712,7 @@ tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_la
 
 tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
                             tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_finalize");
   Plan* P = as_plan(plan);
   if (!P || !ws || !cores || !ranks || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   if (!P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_ERR_STATE;
@@ -720,6 +727,7 @@ tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
 
 tt_status tt_pstt2(tt_plan_t plan, const void* X, void* ws, double* cores, int* ranks,
                    tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2");
   Plan* P = as_plan(plan);
   if (!P || !X || !ws || !cores || !ranks || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -769,6 +777,7 @@ static tt_status batched_run(Plan& P, const void* const* X_ptrs, const BatchCfg&
 
 tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores,
                            int* ranks, tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_batched");
   Plan* P = as_plan(plan);
   if (!P || !X_ptrs || !ws || !cores || !ranks) return TT_ERR_INVALID_ARG;
   tt_status s = batched_check(P, X_ptrs);
@@ -781,6 +790,7 @@ tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
 
 tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores, int* ranks,
                            tt_stream_t stream, int* best_out) {
+  NvtxRange nvtx("tt_plan_autotune");
   Plan* P = as_plan(plan);
   if (!P || !X_ptrs || !ws || !cores || !ranks) return TT_ERR_INVALID_ARG;
   tt_status s = batched_check(P, X_ptrs);
@@ -856,6 +866,7 @@ tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_s
 
 tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void* dX,
                             tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_backward");
   Plan* P = as_plan(plan);
   if (!P || !ws || !dcores || !dX || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   // the saved state of this plan's last forward call must still be in ws
@@ -866,6 +877,7 @@ tt_status tt_pstt2_backward(tt_plan_t plan, void* ws, const double* dcores, void
 
 tt_status tt_reconstruct(tt_plan_t plan, const double* cores, void* Xt, tt_dtype dtype, void* ws,
                          tt_stream_t stream) {
+  NvtxRange nvtx("tt_reconstruct");
   Plan* P = as_plan(plan);
   if (!P || !cores || !Xt || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;
@@ -877,6 +889,7 @@ tt_status tt_reconstruct(tt_plan_t plan, const double* cores, void* Xt, tt_dtype
 
 tt_status tt_reconstruct_error(tt_plan_t plan, const double* cores, const void* X, double* out2,
                                void* ws, tt_stream_t stream) {
+  NvtxRange nvtx("tt_reconstruct_error");
   Plan* P = as_plan(plan);
   if (!P || !cores || !X || !out2 || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -887,6 +900,7 @@ tt_status tt_reconstruct_error(tt_plan_t plan, const double* cores, const void* 
 
 tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const void* dXt,
                                   tt_dtype dtype, double* dcores, void* ws, tt_stream_t stream) {
+  NvtxRange nvtx("tt_reconstruct_backward");
   Plan* P = as_plan(plan);
   if (!P || !cores || !dXt || !dcores || !ws || P->items.size() != 1) return TT_ERR_INVALID_ARG;
   if (dtype != TT_F32 && dtype != TT_F64) return TT_ERR_INVALID_ARG;

@@ -52,9 +52,16 @@ const DevSketch* plan_sketches_host(const Plan* p);
 namespace tc {
 namespace slab {
 
-constexpr int kWarps = 20;
-constexpr int kThreads = kWarps * 32;
-constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13, kRngWarps = 7;
+constexpr int kEpiWarps = 4, kMmaWarp = 4, kProdWarp0 = 5, kProdWarps = 8, kRngWarp0 = 13;
+// Test-matrix warps: seven draw the dense Gaussian blocks (Philox); three
+// form the Khatri-Rao L blocks from factor rows.  The Khatri-Rao kernel has
+// 16 warps and so 128 registers a thread (registers go to warps four at a
+// time), which its roles need without spilling.
+template <bool KRY>
+struct Roles {
+  static constexpr int rng = KRY ? 3 : 7;
+  static constexpr int threads = (kRngWarp0 + rng) * 32;
+};
 constexpr int kLBlkB = 4 * kS4;   // L block: 128 rows x N <= 32
 constexpr int kRBlkB = 2 * kS4;   // R_2 block: 128 rows x N <= 16
 constexpr int kYBlkB = 16 * kS4;  // R_3 blocks side by side: 128 rows x N <= 128
@@ -62,6 +69,11 @@ constexpr int kOffL = 2 * kStageB;
 constexpr int kOffR = kOffL + 2 * kLBlkB;
 constexpr int kOffY = kOffR + 4 * kRBlkB;
 constexpr int kOffBar = kOffY + kYBlkB;
+// Khatri-Rao: the fixed mode-1 block takes the first two R_2-sized blocks of
+// the R_3 area; the slab's mode-4 rows of S_1 and S_2 (FP32, c x l each)
+// follow it
+constexpr int kOffF4 = kOffY + 2 * kRBlkB;
+static_assert(2 * kRBlkB + 2 * 64 * 16 * 4 <= kYBlkB, "Khatri-Rao blocks in the R_3 area");
 constexpr int kSmemBytes = kOffBar + 256 + 1024;
 constexpr int kTmemY = 0;         // D_Y buffers at columns 0 and 128, then the L slots, then R_2
 constexpr int64_t kTableOffB = 256;
@@ -99,9 +111,31 @@ __device__ __forceinline__ int64_t l_group(const SlabArgs& g, int64_t t) {
   const int64_t tl = t / g.tilesR, tr = t % g.tilesR;
   return tl * ((g.tilesR + g.runL - 1) / g.runL) + tr / g.runL;
 }
+// The super-plane after (a, b) of tile t in the order every role walks them
+// (tile, then kR group b, then kL a): its kL and first kR; false past the
+// CTA's last tile.
+__device__ __forceinline__ bool next_super_plane(const SlabArgs& g, int64_t ntiles, int64_t t, int a, int b,
+                                                 const TileInfo& ti, int64_t& kL, int64_t& kR0) {
+  if (++a == ti.nA) {
+    a = 0;
+    if (++b == ti.nB) {
+      b = 0;
+      if (++t >= ntiles) return false;
+      const TileInfo tn = tile_info(g, t);
+      kL = tn.kL0;
+      kR0 = tn.kRg0 * g.G;
+      return true;
+    }
+  }
+  kL = ti.kL0 + a;
+  kR0 = (ti.kRg0 + b) * g.G;
+  return true;
+}
 
 template <int ELL, int C, bool KRY>
-__global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs g) {
+__global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(const SlabArgs g) {
+  constexpr int kRngWarps = Roles<KRY>::rng;
+  constexpr int kThreads = Roles<KRY>::threads;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
@@ -160,6 +194,19 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
       const int j = e % ell, i1 = e / ell, h1 = i1 >> 7, k = i1 & 127;
       *reinterpret_cast<__nv_bfloat16*>(sm + kOffY + h1 * kRBlkB + (k >> 3) * kS1 + (j >> 3) * kS4 + (j & 7) * 16 +
                                         (k & 7) * 2) = __float2bfloat16_rn(f1[(int64_t)i1 * kr3->kr_lp + j]);
+    }
+    // the mode-4 rows of the slab's slices for S_1 (its mode-4 factor is its
+    // third) and S_2 (its second)
+    const DevSketch* k0 = kr_of(g.ws, g.col[0].kr);
+    const DevSketch* k1 = kr_of(g.ws, g.col[1].kr);
+    if (k0 && k1) {
+      float* f4s = reinterpret_cast<float*>(sm + kOffF4);
+      for (int e = threadIdx.x; e < 2 * C * ell; e += kThreads) {
+        const int sk = e / (C * ell), r = (e / ell) % C, j = e % ell;
+        const DevSketch* kb = sk ? k1 : k0;
+        const float* tb = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kb->kr_tab);
+        f4s[e] = tb[kb->kr_off[sk ? 1 : 2] + (g.first + r) * kb->kr_lp + j];
+      }
     }
     fence_async_smem();
   }
@@ -263,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     }
   } else if (warp >= kRngWarp0 && warp < kRngWarp0 + kRngWarps) {
     // ------------------------------------------------- test-matrix blocks
-    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0..223
+    const int rt = threadIdx.x - kRngWarp0 * 32;  // 0 .. 32 kRngWarps - 1
     constexpr int qps = ell / 4;
     constexpr int upb = 64 * qps;  // 2-row units of one 128-row block
     // L block: S_1 then S_2, rows k = composite; contiguous unit ranges
@@ -273,6 +320,53 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     const int yu_beg = yn * rt / (kRngWarps * 32), yu_end = yn * (rt + 1) / (kRngWarps * 32);
     const DevSketch* krL0 = kr_of(g.ws, s_col[0].kr);
     const DevSketch* krL1 = kr_of(g.ws, s_col[1].kr);
+    // Khatri-Rao L blocks by task: task u = (rp, nq) (u = qps rp + nq) is rows
+    // k = 2 rp, 2 rp + 1 and column quad nq of both S_1 and S_2; thread rt
+    // takes u = rt + 96 i, all with the same quad.  The mode-4 rows (slices
+    // first + k mod c, + 1) come from shared memory, staged at the start; the
+    // mode-2 / mode-3 rows of the next super-plane are loaded while this one
+    // is stored.
+    constexpr int kNT = Roles<true>::rng * 32;
+    constexpr int kTasks = KRY ? (64 * qps + kNT - 1) / kNT : 1;
+    static_assert(!KRY || kNT % qps == 0, "Khatri-Rao L tasks keep their quad");
+    const bool kr_tasks = KRY && krL0 != nullptr && krL1 != nullptr;
+    const int kq = rt % qps;
+    int task_k[kTasks];
+    bool task_on[kTasks];
+    float4 f3r[2][kTasks], f2r = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* f4s = reinterpret_cast<const float4*>(sm + kOffF4);  // [sketch][slice][l / 4]
+    const float *kt0 = nullptr, *kt1 = nullptr;
+    int64_t o2_0 = 0, o3_0 = 0, o3_1 = 0, lp0 = 0, lp1 = 0;
+    auto kr_load_sp = [&](int64_t kL, int64_t kR0) {
+      f2r = *reinterpret_cast<const float4*>(kt0 + o2_0 + kL * lp0 + 4 * kq);
+#pragma unroll
+      for (int i = 0; i < kTasks; ++i)
+        if (task_on[i]) {
+          const int64_t gg = task_k[i] >> lc;
+          f3r[0][i] = *reinterpret_cast<const float4*>(kt0 + o3_0 + (kR0 + gg) * lp0 + 4 * kq);
+          f3r[1][i] = *reinterpret_cast<const float4*>(kt1 + o3_1 + (kR0 + gg) * lp1 + 4 * kq);
+        }
+    };
+    if (kr_tasks) {
+      kt0 = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + krL0->kr_tab);
+      kt1 = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + krL1->kr_tab);
+      lp0 = krL0->kr_lp;
+      lp1 = krL1->kr_lp;
+      // S_1 over modes 2, 3, 4; S_2 over modes 3, 4
+      o2_0 = krL0->kr_off[0];
+      o3_0 = krL0->kr_off[1];
+      o3_1 = krL1->kr_off[0];
+#pragma unroll
+      for (int i = 0; i < kTasks; ++i) {
+        const int u = rt + kNT * i;
+        task_on[i] = u < 64 * qps;
+        task_k[i] = task_on[i] ? 2 * (u / qps) : 0;
+      }
+      if (t_beg < ntiles) {
+        const TileInfo t0 = tile_info(g, t_beg);
+        kr_load_sp(t0.kL0, t0.kRg0 * g.G);
+      }
+    }
     uint32_t pi = 0, qy = 0;
     int64_t tab_last[2] = {-1, -1};
     bool ok = true;
@@ -299,7 +393,33 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
           }
           // L block: S_1 rows w_g + W (first + i4'), S_2 rows kR_g + n3 (first + i4'),
           // k = i4' + c g
-          for (int u = lu_beg; u < lu_end; ++u) {
+          auto store_pair = [&](int bi, int k, const float4& ra, const float4& rb) {
+            const int n0 = bi * ell + 4 * kq;
+            const uint32_t dst = sL + buf * kLBlkB + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
+            st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
+            st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
+            st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
+            st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+          };
+          auto mul4 = [](const float4& x, const float4& y) {
+            return make_float4(__fmul_rn(x.x, y.x), __fmul_rn(x.y, y.y), __fmul_rn(x.z, y.z), __fmul_rn(x.w, y.w));
+          };
+          if (kr_tasks) {
+            // increasing mode order: S_1 (F_2(kL) F_3(kR_g)) F_4(i4), S_2 F_3(kR_g) F_4(i4)
+#pragma unroll
+            for (int i = 0; i < kTasks; ++i)
+              if (task_on[i]) {
+                const int kk = task_k[i] & cmask;
+                const float4 a0 = f4s[(0 * C + kk) * qps + kq], a1 = f4s[(0 * C + kk + 1) * qps + kq];
+                const float4 b0 = f4s[(1 * C + kk) * qps + kq], b1 = f4s[(1 * C + kk + 1) * qps + kq];
+                const float4 c1 = mul4(f2r, f3r[0][i]);
+                store_pair(0, task_k[i], mul4(c1, a0), mul4(c1, a1));
+                store_pair(1, task_k[i], mul4(f3r[1][i], b0), mul4(f3r[1][i], b1));
+              }
+            int64_t kLn, kR0n;
+            if (next_super_plane(g, ntiles, t, a, b, ti, kLn, kR0n)) kr_load_sp(kLn, kR0n);
+          }
+          for (int u = lu_beg; u < (kr_tasks ? lu_beg : lu_end); ++u) {
             const int bi = u / upb, rp = (u % upb) / qps, nq = u % qps;
             const SkTc& sk = s_col[bi];
             const int k = 2 * rp;
@@ -557,6 +677,24 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
     float yacc[ell];
 #pragma unroll
     for (int j = 0; j < ell; ++j) yacc[j] = 0.0f;
+    // Khatri-Rao: the plane's mode-3 and mode-2 factor rows, loaded one
+    // super-plane ahead of their use
+    float4 ef3[ell / 4], ef2[ell / 4];
+    const float* ektab = KRY ? reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab) : nullptr;
+    const int64_t eo2 = KRY ? kr3->kr_off[1] : 0, eo3 = KRY ? kr3->kr_off[2] : 0, elp = KRY ? kr3->kr_lp : 0;
+    auto e_load = [&](int64_t kL, int64_t kR0) {
+      const float4* f3 = reinterpret_cast<const float4*>(ektab + eo3 + (kR0 + gl) * elp);
+      const float4* f2 = reinterpret_cast<const float4*>(ektab + eo2 + kL * elp);
+#pragma unroll
+      for (int q = 0; q < ell / 4; ++q) {
+        ef3[q] = f3[q];
+        ef2[q] = f2[q];
+      }
+    };
+    if (KRY && t_beg < ntiles) {
+      const TileInfo t0 = tile_info(g, t_beg);
+      e_load(t0.kL0, t0.kRg0 * g.G);
+    }
     // R_3 rows first + kk: at c = 16 lanes l and l + 16 hold the same slice of
     // two planes and are summed first
     auto flush_Y = [&]() {
@@ -597,22 +735,18 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_slab_kernel(const SlabArgs
           for (int a = 0; a < tinf.nA; ++a, ++spn) {
             const uint32_t yb = spn & 1;
             // the plane's rows of the mode-3 and mode-2 factors (i_3 = kR_g,
-            // i_2 = kL), all loads issued together; product in the row sketch's
-            // decreasing mode order, rounded to BF16 (the column scale)
-            const float* ktab = reinterpret_cast<const float*>(reinterpret_cast<const char*>(g.ws) + kr3->kr_tab);
-            const float4* f3 =
-                reinterpret_cast<const float4*>(ktab + kr3->kr_off[2] + ((tinf.kRg0 + b) * g.G + gl) * kr3->kr_lp);
-            const float4* f2 = reinterpret_cast<const float4*>(ktab + kr3->kr_off[1] + (tinf.kL0 + a) * kr3->kr_lp);
-            float4 sc[ell / 4], s2[ell / 4];
-#pragma unroll
-            for (int q = 0; q < ell / 4; ++q) {
-              sc[q] = f3[q];
-              s2[q] = f2[q];
-            }
+            // i_2 = kL, loaded during the previous super-plane); product in the
+            // row sketch's decreasing mode order, rounded to BF16 (the column
+            // scale); then the next super-plane's rows go out
+            float4 sc[ell / 4];
 #pragma unroll
             for (int q = 0; q < ell / 4; ++q)
-              sc[q] = make_float4(round_bf16(__fmul_rn(sc[q].x, s2[q].x)), round_bf16(__fmul_rn(sc[q].y, s2[q].y)),
-                                  round_bf16(__fmul_rn(sc[q].z, s2[q].z)), round_bf16(__fmul_rn(sc[q].w, s2[q].w)));
+              sc[q] = make_float4(round_bf16(__fmul_rn(ef3[q].x, ef2[q].x)), round_bf16(__fmul_rn(ef3[q].y, ef2[q].y)),
+                                  round_bf16(__fmul_rn(ef3[q].z, ef2[q].z)), round_bf16(__fmul_rn(ef3[q].w, ef2[q].w)));
+            {
+              int64_t kLn, kR0n;
+              if (next_super_plane(g, ntiles, t, a, b, tinf, kLn, kR0n)) e_load(kLn, kR0n);
+            }
             if (!mbar_wait(bar(TMY_FULL + yb), (spn >> 1) & 1, abort_flag, g.status)) {
               yok = false;
               break;
@@ -810,7 +944,7 @@ static bool slab_kernel_launchable() {
     int dev = 0, smem_optin = 0;
     ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16, false>) == cudaSuccess &&
          cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16, true>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
-         fa.maxThreadsPerBlock >= slab::kThreads && fb.maxThreadsPerBlock >= slab::kThreads &&
+         fa.maxThreadsPerBlock >= slab::Roles<false>::threads && fb.maxThreadsPerBlock >= slab::Roles<true>::threads &&
          cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
          smem_optin >= slab::kSmemBytes;
   }
@@ -889,7 +1023,8 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
   const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.kry][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
-  k<<<grid, tc::slab::kThreads, tc::slab::kSmemBytes, st>>>(g);
+  const int threads = g.kry ? tc::slab::Roles<true>::threads : tc::slab::Roles<false>::threads;
+  k<<<grid, threads, tc::slab::kSmemBytes, st>>>(g);
   return cudaGetLastError();
 }
 
