@@ -125,12 +125,16 @@ typedef struct {
  * k+1..d; Psi_k: modes 1..k).  Row i of the factor of mode m (1-based) is row
  * i + (2^31 + m) 2^32 of the sketch's Philox stream, so it never coincides
  * with a dense row.  The entry at the column-major multi-index of the modes is
- * the product of the factor entries, multiplied in increasing mode order (in
- * FP64 on the FP64 path; in FP32 from the FP32 generator, then rounded once
- * to the MMA type, on the TF32 / BF16 paths).  The factors (sum of n_m l
- * entries per sketch) are staged in the workspace by tt_pstt2 and
- * tt_pstt2_begin.  Single-problem plans only (TT_ERR_UNSUPPORTED in batched
- * plans). */
+ * the product of the factor entries: for Omega_k multiplied in increasing
+ * mode order, for Psi_k in decreasing mode order (in FP64 on the FP64 path;
+ * in FP32 from the FP32 generator, then rounded once to the MMA type, on the
+ * TF32 / BF16 paths).  One exception on the TF32 / BF16 paths: Psi_{d-1} with
+ * d - 1 >= 2 is taken mode by mode, each entry round(F_1) x round(F_{d-1} ..
+ * F_2) (the rounded mode-1 factor times the rounded product of the others),
+ * so that R_{d-1} = (X^T round(F_1)) scaled per plane -- the form the sketch
+ * kernels use.  The factors (sum of n_m l entries per sketch) are staged in
+ * the workspace by tt_pstt2 and tt_pstt2_begin.  Single-problem plans only
+ * (TT_ERR_UNSUPPORTED in batched plans). */
 #define TT_FLAG_KR 4
 
 /* ---------------------------------------------------------------- plans */
@@ -180,11 +184,16 @@ tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, in
 /* Which sketch kernel an accumulate of `count_last` last-mode slices runs for
  * item 0: 0 = FP64 SIMT kernel, 1 = generic tensor-core kernel (mma.sync,
  * any shape; in single-problem plans the test-matrix rows that several
- * tiles read are staged once per call, up to 256 MB a sketch), 2 = tcgen05 plane kernel (n_1 and count_last in {128, 256},
- * d in {3, 4}, BF16, two-sided, equal widths with 16 <= l * #sketches per
- * side <= 32), 3 = small-plane kernel (BF16 or TF32, n_1 and count_last <= 32,
- * widths l_k <= 32, padded to the widest; mma.sync with test-matrix rows
- * shared by many planes staged once per call).  Host only. */
+ * tiles read are staged once per call, up to 256 MB a sketch), 2 = a tcgen05
+ * kernel: the plane kernel (n_1 and count_last in {128, 256}, d in {3, 4},
+ * dense Gaussian test matrices, equal widths with 16 <= l * #sketches per
+ * side <= 32) or the slab kernel (d = 4, n_1 in {128, 256}, l in {8, 16},
+ * count_last = 16, 32 or 64 -- a 1 GiB slab of the 256^4 FP32 tensor is 16 --
+ * or, with Khatri-Rao test matrices, any multiple of 64, taken 64 slices a
+ * launch), both BF16 and two-sided; 3 = small-plane kernel (BF16 or TF32,
+ * n_1 and count_last <= 32, widths l_k <= 32, padded to the widest; mma.sync
+ * with test-matrix rows shared by many planes staged once per call).  Host
+ * only. */
 int tt_sketch_kernel_kind(tt_plan_t plan, int64_t count_last);
 
 /* Problem of item `item` as stored by the plan (ranks clamped). */
