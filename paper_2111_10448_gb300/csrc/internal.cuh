@@ -143,6 +143,8 @@ struct DevItem {
   int64_t gentab_doubles;   // rows repeat across planes (0: none)
   int64_t off_adjtab;       // tensor-core sketch adjoint: the sketch adjoints split into hi + lo in
   int64_t adjtab_doubles;   // the MMA type, every sketch's rows x lpad (0: that kernel does not apply)
+  int64_t off_s2stage;      // slab kernel: FP32 staging of the mid sketch S_2 (rows x l floats), added
+  int64_t s2stage_doubles;  // into S_2 after every launch (0: the slab kernel cannot serve the item)
 };
 
 struct Task {               // one block of one TSQR level (finalize)

@@ -287,6 +287,16 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.tctab_doubles = (bytes + 7) / 8;
   }
   it.off_tctab = it.tctab_doubles ? ws.take(it.tctab_doubles) : 0;
+  // FP32 staging of S_2 for the slab kernel (d = 4, BF16, n_1 in {128, 256},
+  // single-problem two-sided one-pass plans): its L-slot flush adds FP32
+  // partials there, and one pass after each launch adds them into the FP64
+  // sketch.
+  it.s2stage_doubles = 0;
+  if (it.tctab_doubles > 0 && d == 4 && single && !it.sided1 && q.passes == 1 && it.nsk == 4) {
+    const DevSketch& s2 = P.sketches[it.sk0 + 1];
+    if (s2.type == SK_COL && s2.k == 2) it.s2stage_doubles = (s2.rows * s2.width + 1) / 2;
+  }
+  it.off_s2stage = it.s2stage_doubles ? ws.take(it.s2stage_doubles) : 0;
   // Staging area of the small-plane kernel (BF16 or TF32, n_1 and n_d <= 32,
   // one width l <= 32): the rows of every test matrix that many planes share
   // (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches with
@@ -575,6 +585,10 @@ static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
   for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) {
     const DevSketch& s = P.sketches[si];
     cudaError_t e = cudaMemsetAsync(base + s.off, 0, sizeof(double) * s.rows * s.width, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (it.s2stage_doubles > 0) {
+    cudaError_t e = cudaMemsetAsync(base + it.off_s2stage, 0, sizeof(double) * it.s2stage_doubles, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
   // Khatri-Rao factors of the call (every later kernel of the call reads them)

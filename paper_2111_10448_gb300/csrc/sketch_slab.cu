@@ -91,6 +91,7 @@ struct SlabArgs {
   int kry;                 // Khatri-Rao test matrices: R_3 mode by mode (fixed mode-1 block)
   int64_t runL;            // tiles of one kL block accumulated in the L slots before a flush
   uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
+  float* s2stage;          // FP32 staging of S_2 (same layout), added into S_2 after the launch
   SkTc col[2], row[2];     // S_1, S_2 | R_2, R_3
 };
 
@@ -649,8 +650,11 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
               for (int j = 0; j < ell; ++j) acc[j] += v[j];
             } else {
               const int64_t row = i1 + g.n1 * (kL0 + a);
+              // S_2: FP32 atomics into the staging copy (each entry receives
+              // about four CTA partials a launch; FP64 atomics here cost the
+              // launch ~25 us of drain)
 #pragma unroll
-              for (int j = 0; j < ell; ++j) atomicAdd(dst + row + sk.rows * j, (double)v[j]);
+              for (int j = 0; j < ell; ++j) atomicAdd(g.s2stage + row + sk.rows * j, v[j]);
             }
           }
           if (s == 0) {
@@ -824,6 +828,14 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
   }
 }
 
+// S_2 += the launch's FP32 staging, which is cleared for the next launch.
+__global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stage, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    s2[e] += (double)stage[e];
+    stage[e] = 0.0f;
+  }
+}
+
 // Staged R_2 blocks: block (v, h) holds the 128 rows 128 h + k + n_1 v of the
 // test matrix (v = kL) as the BF16 K-major core-matrix image the MMA reads.
 __global__ void slab_table_kernel(const SlabArgs g, int64_t nv) {
@@ -872,6 +884,7 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
     return false;
   const int ell = s1.width;
   if ((ell != 8 && ell != 16) || s2.width != ell || r2.width != ell || r3.width != ell) return false;
+  if (it.s2stage_doubles * 2 < s2.rows * s2.width) return false;  // the FP32 staging of S_2
   slab::SlabArgs g;
   memset(&g, 0, sizeof(g));
   g.n1 = it.n[0];
@@ -991,6 +1004,8 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   g.ws = (double*)ws;
   g.status = reinterpret_cast<int*>((char*)ws + kStatusOff);
   g.first = first;
+  const DevItem& it = plan_items_host(&P)[item];
+  g.s2stage = reinterpret_cast<float*>((double*)ws + it.off_s2stage);
   using KernelFn = void (*)(tc::slab::SlabArgs);
   using namespace tc::slab;
   const KernelFn kernels[2][2][3] = {
@@ -1025,6 +1040,12 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.kry][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
   const int threads = g.kry ? tc::slab::Roles<true>::threads : tc::slab::Roles<false>::threads;
   k<<<grid, threads, tc::slab::kSmemBytes, st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n2 = g.col[1].rows * g.ell;
+  count_launch();
+  tc::slab::s2_fold_kernel<<<(unsigned)std::min<int64_t>((n2 + 255) / 256, 4LL * device_sm_count()), 256, 0, st>>>(
+      g.ws + g.col[1].off, g.s2stage, n2);
   return cudaGetLastError();
 }
 
