@@ -51,6 +51,7 @@ namespace {
 struct WsEntry {
   uint64_t plan_id;
   bool forward_valid;
+  bool ytab_valid;  // the slab kernel's staged R_3 blocks are in the workspace
 };
 std::mutex g_ws_mu;
 std::unordered_map<const void*, WsEntry> g_ws;
@@ -62,6 +63,18 @@ void plan_mark_forward(Plan* p, const void* ws, bool valid) {
   auto it = g_ws.find(ws);
   if (it != g_ws.end() && it->second.plan_id == p->id) it->second.forward_valid = valid;
   p->forward_ws = valid ? ws : nullptr;
+}
+
+bool plan_ytab_valid(const Plan* p, const void* ws) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  return it != g_ws.end() && it->second.plan_id == p->id && it->second.ytab_valid;
+}
+
+void plan_set_ytab_valid(const Plan* p, const void* ws) {
+  std::lock_guard<std::mutex> lock(g_ws_mu);
+  auto it = g_ws.find(ws);
+  if (it != g_ws.end() && it->second.plan_id == p->id) it->second.ytab_valid = true;
 }
 
 
@@ -297,6 +310,21 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     if (s2.type == SK_COL && s2.k == 2) it.s2stage_doubles = (s2.rows * s2.width + 1) / 2;
   }
   it.off_s2stage = it.s2stage_doubles ? ws.take(it.s2stage_doubles) : 0;
+  // Dense Gaussian slab streaming: R_3's test-matrix rows (i_1 + n_1 w) belong
+  // to one plane each, so a slab of c slices draws l / c normals per entry of
+  // X to regenerate them; every slab needs the same rows, so they are staged
+  // once per decomposition as BF16 block images, one per (half of i_1, kL,
+  // kR), kR fastest (2 (n_1 / 128) n_2 n_3 l bytes up to padding: 604 MB at
+  // 256^4, capped at 1 GiB).
+  it.ytab_doubles = 0;
+  if (it.s2stage_doubles > 0 && !kr) {
+    const DevSketch& r3 = P.sketches[it.sk0 + 3];
+    if (r3.type == SK_ROW && r3.k == 3 && (r3.width == 8 || r3.width == 16)) {
+      const int64_t bytes = (q.n[0] / 128) * q.n[1] * q.n[2] * (int64_t)(r3.width / 8) * kTcGroupBytes;
+      if (bytes <= (1LL << 30)) it.ytab_doubles = (bytes + 7) / 8;
+    }
+  }
+  it.off_ytab = it.ytab_doubles ? ws.take(it.ytab_doubles) : 0;
   // Staging area of the small-plane kernel (BF16 or TF32, n_1 and n_d <= 32,
   // one width l <= 32): the rows of every test matrix that many planes share
   // (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches with
@@ -551,7 +579,7 @@ static tt_status ensure_uploaded(Plan& P, void* ws, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(st);  // the host blob must stay unchanged until copied
   if (e != cudaSuccess) return cuda_status(e);
-  g_ws[ws] = WsEntry{P.id, false};
+  g_ws[ws] = WsEntry{P.id, false, false};
   return TT_OK;
 }
 

@@ -92,6 +92,7 @@ struct SlabArgs {
   int64_t runL;            // tiles of one kL block accumulated in the L slots before a flush
   uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
   float* s2stage;          // FP32 staging of S_2 (same layout), added into S_2 after the launch
+  int64_t ytab;            // dense: byte offset of the staged R_3 blocks (-1: regenerated per quarter)
   SkTc col[2], row[2];     // S_1, S_2 | R_2, R_3
 };
 
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       mbar_init(bar(TMR_FULL + s), 1);
       mbar_init(bar(TMR_EMPTY + s), kEpiWarps);
     }
-    mbar_init(bar(FULL_Y), kRngWarps);
+    mbar_init(bar(FULL_Y), g.ytab >= 0 ? 1 : kRngWarps);
     mbar_init(bar(EMPTY_Y), 1);
     for (int s2 = 0; s2 < 2; ++s2) {
       mbar_init(bar(TMY_FULL + s2), 1);
@@ -314,8 +315,13 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
     const int rt = threadIdx.x - kRngWarp0 * 32;  // 0 .. 32 kRngWarps - 1
     constexpr int qps = ell / 4;
     constexpr int upb = 64 * qps;  // 2-row units of one 128-row block
-    // L block: S_1 then S_2, rows k = composite; contiguous unit ranges
-    const int lu_beg = 2 * upb * rt / (kRngWarps * 32), lu_end = 2 * upb * (rt + 1) / (kRngWarps * 32);
+    // L block: S_1 then S_2, rows k = composite; contiguous unit ranges.  With
+    // staged R_3 blocks the first warp only issues the bulk copies (its lane
+    // 0 would otherwise hold the next quarter's copy behind its share of the
+    // L block), and the other warps generate.
+    const bool copier_warp = g.ytab >= 0 && rt < 32;
+    const int gt = g.ytab >= 0 ? rt - 32 : rt, gn = (g.ytab >= 0 ? kRngWarps - 1 : kRngWarps) * 32;
+    const int lu_beg = copier_warp ? 0 : 2 * upb * gt / gn, lu_end = copier_warp ? 0 : 2 * upb * (gt + 1) / gn;
     // R_3 blocks of a quarter: G blocks of 128 rows of i_1
     const int yn = g.G * upb;
     const int yu_beg = yn * rt / (kRngWarps * 32), yu_end = yn * (rt + 1) / (kRngWarps * 32);
@@ -369,7 +375,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       }
     }
     uint32_t pi = 0, qy = 0;
-    int64_t tab_last[2] = {-1, -1};
+    int64_t tab_last[2] = {-1, -1}, y_last = -1;
     bool ok = true;
     for (int64_t t = t_beg; t < ntiles && ok && !*abort_flag; ++t) {
       const TileInfo ti = tile_info(g, t);
@@ -464,6 +470,30 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
           // Khatri-Rao: R_3 needs no regenerated blocks (fixed mode-1 block)
           if constexpr (KRY) continue;
           // R_3 blocks, one quarter (half of i_1) at a time
+          if (g.ytab >= 0) {
+            // staged: one bulk copy of the super-plane's G blocks per quarter,
+            // and an L2 prefetch of the next super-plane's
+            constexpr uint32_t blkB = (uint32_t)(ell / 8) * kS4;
+            const uint32_t bytes = (uint32_t)g.G * blkB;
+            const char* ytab = reinterpret_cast<const char*>(g.ws) + g.ytab;
+            auto ysrc = [&](int h1, int64_t kL, int64_t kR) {
+              return ytab + ((h1 * g.WL + kL) * g.WR + kR) * (int64_t)blkB;
+            };
+            for (int h1 = 0; h1 < g.H1; ++h1, ++qy) {
+              if (rt != 0) continue;
+              if (!mbar_wait(bar(EMPTY_Y), (qy & 1) ^ 1, abort_flag, g.status)) {
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(bar(FULL_Y), bytes);
+              bulk_g2s(sY, ysrc(h1, kL, kR0), bytes, bar(FULL_Y));
+              y_last = (int64_t)qy;
+              int64_t kLn, kR0n;
+              if (h1 == 0 && next_super_plane(g, ntiles, t, a, b, ti, kLn, kR0n))
+                for (int h2 = 0; h2 < g.H1; ++h2) bulk_prefetch_l2(ysrc(h2, kLn, kR0n), bytes);
+            }
+            continue;
+          }
           for (int h1 = 0; h1 < g.H1; ++h1, ++qy) {
             if (!mbar_wait(bar(EMPTY_Y), (qy & 1) ^ 1, abort_flag, g.status)) {
               ok = false;
@@ -503,6 +533,11 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         }
     }
     // copies still in flight when the CTA gave up must land before it exits
+    if (rt == 0 && y_last >= 0) {
+      const long long t0 = clock64();
+      while (!mbar_try(bar(FULL_Y), (uint32_t)(y_last & 1)) && clock64() - t0 < kWaitCycles) {
+      }
+    }
     if (rt == 0)
       for (int b2 = 0; b2 < 2; ++b2)
         if (tab_last[b2] >= 0) {
@@ -828,6 +863,38 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
   }
 }
 
+// Staged R_3 blocks (dense test matrices): block (h, kL, kR) holds the 128
+// rows 128 h + k + n_1 (kL + WL kR) of Psi_3 as the BF16 K-major
+// core-matrix image the MMA reads, kR fastest.
+__global__ void slab_ytab_kernel(const SlabArgs g) {
+  const SkTc sk = g.row[1];
+  const int qps = g.ell / 4;
+  const int64_t blkB = (int64_t)(g.ell / 8) * kS4;
+  const int64_t nblk = (int64_t)g.H1 * g.WL * g.WR;
+  const int64_t total = nblk * 16 * qps * 8;
+  char* tab = reinterpret_cast<char*>(g.ws) + g.ytab;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r8 = (int)(e & 7);
+    int64_t rest = e >> 3;
+    const int q = (int)(rest % qps);
+    rest /= qps;
+    const int kg = (int)(rest & 15);
+    const int64_t blk = rest >> 4;  // (h WL + kL) WR + kR
+    const int64_t kR = blk % g.WR, hl = blk / g.WR;
+    const int64_t kL = hl % g.WL, h = hl / g.WL;
+    const int64_t k = 128 * h + 8 * kg + r8;
+    const float4 z = normals4_f32(g.seed, (uint32_t)sk.sid, (uint64_t)(k + g.n1 * (kL + g.WL * kR)), (uint32_t)q);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    char* bp = tab + blk * blkB;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * q + u;
+      *reinterpret_cast<__nv_bfloat16*>(bp + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          __float2bfloat16_rn(zz[u]);
+    }
+  }
+}
+
 // S_2 += the launch's FP32 staging, which is cleared for the next launch.
 __global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stage, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -1006,6 +1073,7 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   g.first = first;
   const DevItem& it = plan_items_host(&P)[item];
   g.s2stage = reinterpret_cast<float*>((double*)ws + it.off_s2stage);
+  g.ytab = (!g.kry && it.ytab_doubles > 0) ? it.off_ytab * 8 : -1;
   using KernelFn = void (*)(tc::slab::SlabArgs);
   using namespace tc::slab;
   const KernelFn kernels[2][2][3] = {
@@ -1033,6 +1101,15 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
     count_launch();
     tc::slab::slab_table_kernel<<<blocks, 256, 0, st>>>(g, g.WL);
     ready = true;
+  }
+  // the R_3 blocks of dense test matrices: staged once and kept while the
+  // workspace holds this plan's tables (not marked inside a graph capture,
+  // whose launches may never run)
+  if (g.ytab >= 0 && !plan_ytab_valid(&P, ws)) {
+    count_launch();
+    tc::slab::slab_ytab_kernel<<<(unsigned)(8 * device_sm_count()), 256, 0, st>>>(g);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) plan_set_ytab_valid(&P, ws);
   }
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());

@@ -146,3 +146,48 @@ def test_mixed_slab_sizes_in_one_stream(drm):
     t.finalize()
     assert t.status()[1] == one.status()[1]
     assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
+
+
+def test_staged_r3_blocks_kept_and_restaged():
+    """Dense test matrices on 16-slice slabs: R_3's 128-row blocks are staged
+    in the workspace once and kept while it holds the plan's tables.  Runs on
+    one caller workspace: fresh; again (blocks reused); after the workspace
+    was overwritten and released with tt_workspace_release; after another
+    plan used it and it was overwritten.  Every run must reproduce the first
+    (FP32 accumulation order only), which is within 10 eps of X."""
+    dims = [128, 8, 16, 64]
+    x = ti.hilbert_type(dims, np.float32)
+    X = to_dev(x)
+    kw = dict(eps=1e-6, rmax=6, p=10, seed=1, prec="bf16", drm="gauss")
+    A = TTSketch(dims, **kw)
+    assert A.kernel_kind(16) == 2
+    B = TTSketch([16] * 4, ranks=[1, 4, 4, 4, 1], p=5, seed=1, x_dtype=torch.float64, prec="fp64")
+    XB = torch.tensor(ti.random_tt([16] * 4, [1, 3, 4, 3, 1], seed=0), device="cuda")
+    ws = torch.empty(max(A.ws_bytes, B.ws_bytes) // 8 + 32, dtype=torch.float64, device="cuda")
+    L = N.lib()
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda t: C.c_void_p(t.data_ptr())
+    nd1 = 128 * 8 * 16
+
+    def run_A():
+        A.cores.fill_(float("nan"))
+        N.check(L.tt_pstt2_begin(A.plan, p(ws), s), "begin")
+        for a, cnt in _slabs(64, 16, 2):
+            N.check(L.tt_pstt2_accumulate(A.plan, p(X[a * nd1:]), a, cnt, p(ws), s), "accumulate")
+        N.check(L.tt_pstt2_finalize(A.plan, p(ws), p(A.cores), p(A.ranks), s), "finalize")
+        torch.cuda.synchronize()
+        return A.reconstruct(torch.float64).cpu().numpy()
+
+    first = run_A()
+    assert np.linalg.norm(first - x) / np.linalg.norm(x) <= 1e-5
+    got = [run_A()]
+    ws.fill_(float("nan"))
+    L.tt_workspace_release(p(ws))
+    got.append(run_A())
+    N.check(L.tt_pstt2(B.plan, p(XB), p(ws), p(B.cores), p(B.ranks), s), "tt_pstt2 B")
+    torch.cuda.synchronize()
+    ws.fill_(float("nan"))
+    got.append(run_A())
+    for i, g in enumerate(got):
+        assert np.all(np.isfinite(g)), i
+        assert np.linalg.norm(g - first) / np.linalg.norm(first) <= 1e-6, i
