@@ -117,7 +117,7 @@ __global__ void split_kernel(char* wsb, int item, int lpad) {
 // elements of a row-major rows x lpad source (the split adjoint, a staged
 // table or the warp's generated rows).
 template <int LPAD, bool TF>
-__global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs ga) {
+__global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const AdjArgs ga) {
   using E = typename std::conditional<TF, float, __nv_bfloat16>::type;
   constexpr int KS = TF ? 8 : 16;  // k per MMA
   __shared__ AdjArgs g;
@@ -183,12 +183,11 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs ga) {
         if (s.col) return test + (int64_t)b * ldt;
         return adj + part * pstride + (arow0 + astep * b) * LPAD;
       };
+      // fragments: A (m = a) from L rows, B (n = b) from R rows; the test side
+      // is loaded once per k-step, the adjoint side once per term
       for (int k0 = 0; k0 < LPAD; k0 += KS) {
-#pragma unroll
-        for (int part = 0; part < kAdjParts; ++part) {
-          // only the adjoint side is split; the test side is read once per
-          // term (a zero term would cost the same instructions)
-          uint32_t af[2][4], bf[4][2];
+        uint32_t af[2][4], bf[4][2];
+        auto fill_a = [&](int part) {
 #pragma unroll
           for (int mt = 0; mt < 2; ++mt) {
             const int a0 = mt * 16 + gq, a1 = a0 + 8;
@@ -208,6 +207,8 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs ga) {
               af[mt][3] = a1 < n1 ? r1[tq + 4] : 0u;
             }
           }
+        };
+        auto fill_b = [&](int part) {
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
             const int b = nt * 8 + gq;
@@ -221,6 +222,14 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs ga) {
               bf[nt][1] = b < nd ? rb[tq + 4] : 0u;
             }
           }
+        };
+        // the test side: R rows (column sketch) or L rows (row sketch), part 0
+        if (s.col) fill_b(0);
+        else fill_a(0);
+#pragma unroll
+        for (int part = 0; part < kAdjParts; ++part) {
+          if (s.col) fill_a(part);
+          else fill_b(part);
 #pragma unroll
           for (int mt = 0; mt < 2; ++mt)
 #pragma unroll

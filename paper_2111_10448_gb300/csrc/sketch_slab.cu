@@ -895,11 +895,22 @@ __global__ void slab_ytab_kernel(const SlabArgs g) {
   }
 }
 
-// S_2 += the launch's FP32 staging, which is cleared for the next launch.
+// S_2 += the launch's FP32 staging, which is cleared for the next launch;
+// four entries a thread (n = rows l is a multiple of 8, both buffers are
+// 256-byte aligned).
 __global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stage, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    s2[e] += (double)stage[e];
-    stage[e] = 0.0f;
+  double2* d = reinterpret_cast<double2*>(s2);
+  float4* f = reinterpret_cast<float4*>(stage);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n / 4; e += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = f[e];
+    double2 a = d[2 * e], b = d[2 * e + 1];
+    a.x += (double)v.x;
+    a.y += (double)v.y;
+    b.x += (double)v.z;
+    b.y += (double)v.w;
+    d[2 * e] = a;
+    d[2 * e + 1] = b;
+    f[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -1121,8 +1132,8 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   if (e != cudaSuccess) return e;
   const int64_t n2 = g.col[1].rows * g.ell;
   count_launch();
-  tc::slab::s2_fold_kernel<<<(unsigned)std::min<int64_t>((n2 + 255) / 256, 4LL * device_sm_count()), 256, 0, st>>>(
-      g.ws + g.col[1].off, g.s2stage, n2);
+  tc::slab::s2_fold_kernel<<<(unsigned)std::min<int64_t>((n2 / 4 + 255) / 256, 8LL * device_sm_count()), 256, 0,
+                             st>>>(g.ws + g.col[1].off, g.s2stage, n2);
   return cudaGetLastError();
 }
 

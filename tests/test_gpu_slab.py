@@ -87,7 +87,11 @@ def _check_slab(dims, c, kw, drm):
 def test_slab_stream_equals_whole_tensor(drm):
     """Sixteen-slice slabs in shuffled order against one accumulate of the
     whole last mode (the plane kernel): the decompositions agree to the FP32
-    accumulation differences of the two tilings."""
+    accumulation differences of the two tilings.  Bar 3e-6: both kernels sum
+    in FP32 chains of up to 256 MMAs (A14) and the slab kernel stages S_2's
+    partials in FP32; at the rank cap (ranks 4-6 resolve the 2^-17 noise of
+    the split of X) such perturbations move X~ by ~1e-6, well inside the
+    10 eps = 1e-5 that each result keeps to X."""
     dims = [256, 16, 16, 256]
     x = ti.hilbert_type(dims, np.float32)
     X = to_dev(x)
@@ -102,7 +106,7 @@ def test_slab_stream_equals_whole_tensor(drm):
         t.accumulate(X[a * nd1:(a + cnt) * nd1], a, cnt)
     t.finalize()
     assert t.status()[1] == one.status()[1]
-    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 3e-6
 
 
 @pytest.mark.parametrize("drm", ["gauss", "kr"])
@@ -132,7 +136,7 @@ def test_mixed_slab_sizes_in_one_stream(drm):
     """Slabs of 16, 128 and 32 slices in one decomposition: the plane kernel
     and the slab kernel share the staging area, and each restages what it
     needs; the result equals one accumulate of the whole tensor up to FP32
-    accumulation order."""
+    accumulation order (bar 3e-6, as for the sixteen-slice stream above)."""
     dims = [256, 8, 16, 256]
     x = ti.hilbert_type(dims, np.float32)
     X = to_dev(x)
@@ -145,7 +149,7 @@ def test_mixed_slab_sizes_in_one_stream(drm):
         t.accumulate(X[a * nd1:(a + cnt) * nd1], a, cnt)
     t.finalize()
     assert t.status()[1] == one.status()[1]
-    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
+    assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 3e-6
 
 
 def test_staged_r3_blocks_kept_and_restaged():
