@@ -367,15 +367,16 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
         const int gq = lane >> 2, tq = lane & 3;
         constexpr int MT = LPAD / 16;
         // every fragment of a k-step is loaded first, then the MMAs run over
-        // independent accumulators (m-tile x n-tile x hi / lo), so consecutive
+        // independent accumulators (m-tile x n-tile; the hi and lo parts of X
+        // go into the same one, as in the tcgen05 kernels), so consecutive
         // MMAs do not wait on each other
-        float ch[MT][4][4], cl[MT][4][4];
+        float ch[MT][4][4];
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) ch[mt][nt][e] = cl[mt][nt][e] = 0.0f;
+            for (int e = 0; e < 4; ++e) ch[mt][nt][e] = 0.0f;
         if constexpr (TF) {
           // m16n8k8 TF32 fragments straight from the FP32 tiles (row stride 40
           // words: the A loads and the column-product B loads are conflict-free)
@@ -411,7 +412,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
                 for (int mt = 0; mt < MT; ++mt) {
                   mma_tf32(ch[mt][nt], a[mt], bh0, bh1);
-                  mma_tf32(cl[mt][nt], a[mt], bl0, bl1);
+                  mma_tf32(ch[mt][nt], a[mt], bl0, bl1);
                 }
               }
             }
@@ -448,7 +449,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
               for (int nt = 0; nt < 4; ++nt)
-                if (nt < ntn) mma_bf16(cl[mt][nt], a[mt], bl[nt]);
+                if (nt < ntn) mma_bf16(ch[mt][nt], a[mt], bl[nt]);
           }
         }
         }
@@ -479,8 +480,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int j = mt * 16 + gq + 8 * (e >> 1), o = nt * 8 + 2 * tq + (e & 1);
-                if (j < sell && o < nout)
-                  atomicAdd(slot + j * g.ldo + o, (ch[mt][nt][e] + cl[mt][nt][e]) * sc[mt][e >> 1]);
+                if (j < sell && o < nout) atomicAdd(slot + j * g.ldo + o, ch[mt][nt][e] * sc[mt][e >> 1]);
               }
             }
           }

@@ -187,10 +187,15 @@ def test_tensor_core_sketch_adjoint_matches_rounded_oracle(prec, dims, r, target
     (1) Against the oracle gradient of the map whose test matrices are the
     GPU's own (exported with tt_test_matrix), linearised where the forward
     linearised: the mixed sketches see X as its two-term split hi + lo in the
-    MMA type, so the oracle takes x' = hi + lo.  Only the kernel's arithmetic
-    is left -- the FP32 rounding of each FP64 adjoint (split exactly into
-    three terms of the MMA type) and FP32 accumulation, 2^-24 relative to the
-    sum of the magnitudes -- bar 1e-5.  (2) Against the oracle with its own
+    MMA type, so the oracle takes x' = hi + lo.  What is left is FP32
+    rounding -- of each FP64 adjoint (split exactly into three terms of the
+    MMA type), of the adjoint's accumulation, and of the forward sketches'
+    accumulation, which moves the linearisation point by ~2^-24 relative --
+    times the conditioning kappa of the gradient map at this instance, which
+    the oracle measures (relative change of its gradient over relative change
+    of x from x to x'; ~3 on the first instance, ~130 on the second, whose
+    middle rank 8 exceeds the tensor's rank 5): bar max(1e-5, 4 2^-24 kappa).
+    (2) Against the oracle with its own
     rounded FP64 normals at x: the FP32 generator lands on the other BF16
     neighbour in under 0.5% of the entries (one ulp, 2^-8 relative), which
     moves the gradient by about sqrt(0.005) 2^-8 = 3e-4, and the split of X
@@ -223,9 +228,13 @@ def test_tensor_core_sketch_adjoint_matches_rounded_oracle(prec, dims, r, target
     own = dict(ref)
     own["sketch"] = dict(ref["sketch"], **_gpu_test_matrices(ref, dims, 2, prec))
     hi = philox.round_to(x, prec)
-    want_own = OG.cores_vjp(hi + philox.round_to(x - hi, prec), dims, own, lst)
+    xs = hi + philox.round_to(x - hi, prec)
+    want_own = OG.cores_vjp(xs, dims, own, lst)
     err_own = np.linalg.norm(got - want_own) / np.linalg.norm(want_own)
-    print(f"{prec} {dims} tensor-core adjoint rel err: vs the oracle with the GPU's test matrices {err_own:.2e}, "
-          f"vs the oracle's own {err:.2e}")
-    assert err_own <= 1e-5, err_own
+    at_x = OG.cores_vjp(x, dims, own, lst)
+    kappa = (np.linalg.norm(want_own - at_x) / np.linalg.norm(at_x)) / (np.linalg.norm(xs - x) / np.linalg.norm(x))
+    bar = max(1e-5, 4 * 2.0 ** -24 * kappa)
+    print(f"{prec} {dims} tensor-core adjoint rel err: vs the oracle with the GPU's test matrices {err_own:.2e} "
+          f"(kappa {kappa:.0f}, bar {bar:.1e}), vs the oracle's own {err:.2e}")
+    assert err_own <= bar, (err_own, bar)
     assert err <= 1e-3, err
