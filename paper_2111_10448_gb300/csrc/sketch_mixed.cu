@@ -365,7 +365,7 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
 }
 
 
-__global__ void __launch_bounds__(gThreads) sketch_mma_kernel(const MixArgs a) {
+__global__ void __launch_bounds__(gThreads, 4) sketch_mma_kernel(const MixArgs a) {
   extern __shared__ float fsm[];
   const int64_t total = a.W * ((a.n1 + gTA - 1) / gTA) * ((a.cnt + gTB - 1) / gTB);
   for (int64_t item = blockIdx.x; item < total; item += gridDim.x) mma_tile(a, item, fsm);
