@@ -252,7 +252,9 @@ __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool lon
 }
 
 // The planes of block (bL, bR), one per warp; no block-wide barrier inside.
-template <int LPAD, bool TF>
+// KR: the launch has Khatri-Rao test matrices (the dense instance leaves
+// their code out, which keeps it within its registers).
+template <int LPAD, bool TF, bool KR>
 __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw, float* acc, int64_t bL, int64_t bR) {
   using E = typename std::conditional<TF, float, __nv_bfloat16>::type;
   constexpr int kWarps = Prec<TF>::kWarps, kEsz = Prec<TF>::kEsz;
@@ -331,7 +333,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
               qq[h] = c - rr[h] * g.nq;
               const uint64_t row = s.col ? (uint64_t)(key + s.hstride * (g.first + rr[h]))
                                          : (uint64_t)(rr[h] + g.n1 * key);
-              const DevSketch* krs = kr_of(g.wsb, s.kr);
+              const DevSketch* krs = KR ? kr_of(g.wsb, s.kr) : nullptr;
               // a mode-by-mode sketch takes its mode-1 factor here (scaled below)
               z[h] = (krs && krs->kr_mbm) ? kr_f1_quad(g.wsb, *krs, rr[h], (uint32_t)qq[h])
                                           : tm_quad_f32(g.wsb, krs, g.seed, (uint32_t)s.sid, row, (uint32_t)qq[h]);
@@ -459,7 +461,7 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
         float sc[MT][2];
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) sc[mt][0] = sc[mt][1] = 1.0f;
-        {
+        if constexpr (KR) {
           const DevSketch* krs = kr_of(g.wsb, s.kr);
           if (krs && krs->kr_mbm) {
 #pragma unroll
@@ -498,7 +500,7 @@ __device__ void sp_zero(unsigned char* smraw, float* acc, int acc_elems) {
   for (int i = threadIdx.x; i < acc_elems; i += Prec<TF>::kThreads) acc[i] = 0.0f;
 }
 
-template <int LPAD, bool TF>
+template <int LPAD, bool TF, bool KR>
 __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ SpArgs g;
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_kernel(const 
       age = 0;
     }
     ++age;
-    sp_block<LPAD, TF>(g, g.sk, smraw, acc, bL, bR);
+    sp_block<LPAD, TF, KR>(g, g.sk, smraw, acc, bL, bR);
     __syncthreads();
     sp_flush<LPAD, TF>(g, g.sk, acc, false, cur_bL, bR);
     __syncthreads();
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kerne
       const int64_t bL = lu / g.tilesR, bR = lu - bL * g.tilesR;
       cur_bL = bL;
       ++age;
-      sp_block<LPAD, TF>(g, g.sk, smraw, acc, bL, bR);
+      sp_block<LPAD, TF, false>(g, g.sk, smraw, acc, bL, bR);  // batched plans refuse Khatri-Rao
       __syncthreads();
       sp_flush<LPAD, TF>(g, g.sk, acc, false, bL, bR);
       __syncthreads();
@@ -717,8 +719,11 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaSuccess;
-    for (const void* f : {(const void*)sp::sketch_sp_kernel<16, false>, (const void*)sp::sketch_sp_kernel<32, false>,
-                          (const void*)sp::sketch_sp_kernel<16, true>, (const void*)sp::sketch_sp_kernel<32, true>})
+    for (const void* f :
+         {(const void*)sp::sketch_sp_kernel<16, false, false>, (const void*)sp::sketch_sp_kernel<32, false, false>,
+          (const void*)sp::sketch_sp_kernel<16, true, false>, (const void*)sp::sketch_sp_kernel<32, true, false>,
+          (const void*)sp::sketch_sp_kernel<16, false, true>, (const void*)sp::sketch_sp_kernel<32, false, true>,
+          (const void*)sp::sketch_sp_kernel<16, true, true>, (const void*)sp::sketch_sp_kernel<32, true, true>})
       if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
     if (e != cudaSuccess) {
       cudaGetLastError();  // leave no pending error for the caller's next runtime call
@@ -740,13 +745,16 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
   const int64_t nblocks = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(nblocks, device_sm_count());
   count_launch();
-  if (tf) {
-    if (lpad == 16) sp::sketch_sp_kernel<16, true><<<grid, sp::Prec<true>::kThreads, smem, st>>>(g);
-    else sp::sketch_sp_kernel<32, true><<<grid, sp::Prec<true>::kThreads, smem, st>>>(g);
-  } else {
-    if (lpad == 16) sp::sketch_sp_kernel<16, false><<<grid, sp::Prec<false>::kThreads, smem, st>>>(g);
-    else sp::sketch_sp_kernel<32, false><<<grid, sp::Prec<false>::kThreads, smem, st>>>(g);
-  }
+  bool kr = false;
+  for (int s = 0; s < g.nsk; ++s) kr = kr || g.sk[s].kr >= 0;
+  using KernelFn = void (*)(const sp::SpArgs);
+  const KernelFn kernels[2][2][2] = {
+      {{sp::sketch_sp_kernel<16, false, false>, sp::sketch_sp_kernel<16, false, true>},
+       {sp::sketch_sp_kernel<32, false, false>, sp::sketch_sp_kernel<32, false, true>}},
+      {{sp::sketch_sp_kernel<16, true, false>, sp::sketch_sp_kernel<16, true, true>},
+       {sp::sketch_sp_kernel<32, true, false>, sp::sketch_sp_kernel<32, true, true>}}};
+  const KernelFn k = kernels[tf ? 1 : 0][lpad == 16 ? 0 : 1][kr ? 1 : 0];
+  k<<<grid, tf ? sp::Prec<true>::kThreads : sp::Prec<false>::kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 
