@@ -371,9 +371,12 @@ def run_precision(a, dev, P, stream):
     torch.cuda.synchronize(dev)  # X comes from torch's stream; the library runs on `stream`
     out = {"workload": "random TT d=6 n=24 (1.91e8 FP32 entries), ranks 10, +1e-6 noise; eps=1e-5 p=10 rmax=16"}
     ref = None
-    precs = a.precision_only.split(",") if a.precision_only else ["fp64", "tf32", "bf16"]
-    for prec in precs:
-        t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec)
+    # "<prec>_kr": the same with Khatri-Rao test matrices (cheap per-plane rows
+    # on the small planes of this tensor); its error is reported against X
+    precs = a.precision_only.split(",") if a.precision_only else ["fp64", "tf32", "bf16", "bf16_kr"]
+    for form in precs:
+        prec, _, drm = form.partition("_")
+        t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec, drm=drm or "gauss")
         t.pstt2(X, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -386,14 +389,14 @@ def run_precision(a, dev, P, stream):
         r = {"value": X.numel() / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms,
              "rel_err_vs_X": float((err[0] / err[1]) ** 0.5), "ranks": t.status(stream)[1],
              "kernel": ["FP64 SIMT", "mma.sync tile", "tcgen05 plane", "small-plane mma.sync"][t.kernel_kind()]}
-        if prec == "fp64":
+        if form == "fp64":
             ref = t.reconstruct(torch.float32, stream=stream)
-        elif ref is not None:
+        elif ref is not None and not drm:
             d2 = t.error(ref, stream)
             stream.synchronize()
             d2 = d2.cpu().numpy()
             r["rel_err_vs_fp64_gpu"] = float((d2[0] / err[1]) ** 0.5)
-        out[prec] = r
+        out[form] = r
         stream.synchronize()  # nothing of t may still run when its buffers go back to torch
         del t
     del X, ref
