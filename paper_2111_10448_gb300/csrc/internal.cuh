@@ -146,7 +146,7 @@ struct DevItem {
   int64_t off_s2stage;      // slab kernel: FP32 staging of the mid sketch S_2 (rows x l floats), added
   int64_t s2stage_doubles;  // into S_2 after every launch (0: the slab kernel cannot serve the item)
   int64_t off_ytab;         // slab kernel, dense test matrices: Psi_3's 128-row blocks for every
-  int64_t ytab_doubles;     // (half of i_1, kL, kR), staged once per decomposition (0: regenerated)
+  int64_t ytab_doubles;     // (half of i_1, kL, kR), generated once per decomposition (0: per quarter)
 };
 
 struct Task {               // one block of one TSQR level (finalize)
@@ -240,10 +240,6 @@ cudaError_t launch_kr_tables(const Plan& P, int item, void* ws, cudaStream_t st)
 // in BF16, 11 + 11 + 2 in TF32), so the products are as exact as the FP32
 // accumulation.
 constexpr int kAdjParts = 3;
-// The slab kernel's staged R_3 blocks (a deterministic function of the plan)
-// stay valid in a workspace until another plan uploads there.
-bool plan_ytab_valid(const Plan* p, const void* ws);
-void plan_set_ytab_valid(const Plan* p, const void* ws);
 bool adjoint_sp_eligible(const Plan& P, int item);
 cudaError_t launch_adjoint_sp(const Plan& P, int item, void* dX, void* ws, cudaStream_t st);
 cudaError_t launch_mid_b_mixed_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);

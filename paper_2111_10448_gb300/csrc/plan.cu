@@ -51,7 +51,6 @@ namespace {
 struct WsEntry {
   uint64_t plan_id;
   bool forward_valid;
-  bool ytab_valid;  // the slab kernel's staged R_3 blocks are in the workspace
 };
 std::mutex g_ws_mu;
 std::unordered_map<const void*, WsEntry> g_ws;
@@ -63,18 +62,6 @@ void plan_mark_forward(Plan* p, const void* ws, bool valid) {
   auto it = g_ws.find(ws);
   if (it != g_ws.end() && it->second.plan_id == p->id) it->second.forward_valid = valid;
   p->forward_ws = valid ? ws : nullptr;
-}
-
-bool plan_ytab_valid(const Plan* p, const void* ws) {
-  std::lock_guard<std::mutex> lock(g_ws_mu);
-  auto it = g_ws.find(ws);
-  return it != g_ws.end() && it->second.plan_id == p->id && it->second.ytab_valid;
-}
-
-void plan_set_ytab_valid(const Plan* p, const void* ws) {
-  std::lock_guard<std::mutex> lock(g_ws_mu);
-  auto it = g_ws.find(ws);
-  if (it != g_ws.end() && it->second.plan_id == p->id) it->second.ytab_valid = true;
 }
 
 
@@ -312,10 +299,11 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   it.off_s2stage = it.s2stage_doubles ? ws.take(it.s2stage_doubles) : 0;
   // Dense Gaussian slab streaming: R_3's test-matrix rows (i_1 + n_1 w) belong
   // to one plane each, so a slab of c slices draws l / c normals per entry of
-  // X to regenerate them; every slab needs the same rows, so they are staged
-  // once per decomposition as BF16 block images, one per (half of i_1, kL,
-  // kR), kR fastest (2 (n_1 / 128) n_2 n_3 l bytes up to padding: 604 MB at
-  // 256^4, capped at 1 GiB).
+  // X to regenerate them; every slab needs the same rows, so they are
+  // generated once per decomposition (at its first slab launch) as BF16 block
+  // images, one per (half of i_1, kL, kR), kR fastest (2 (n_1 / 128) n_2 n_3 l
+  // bytes up to padding: 604 MB at 256^4, capped at 1 GiB), and not kept
+  // after it.
   it.ytab_doubles = 0;
   if (it.s2stage_doubles > 0 && !kr) {
     const DevSketch& r3 = P.sketches[it.sk0 + 3];
@@ -579,7 +567,7 @@ static tt_status ensure_uploaded(Plan& P, void* ws, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamSynchronize(st);  // the host blob must stay unchanged until copied
   if (e != cudaSuccess) return cuda_status(e);
-  g_ws[ws] = WsEntry{P.id, false, false};
+  g_ws[ws] = WsEntry{P.id, false};
   return TT_OK;
 }
 

@@ -1111,16 +1111,12 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8LL * device_sm_count());
     count_launch();
     tc::slab::slab_table_kernel<<<blocks, 256, 0, st>>>(g, g.WL);
+    // the R_3 blocks of dense test matrices, likewise once per decomposition
+    if (g.ytab >= 0) {
+      count_launch();
+      tc::slab::slab_ytab_kernel<<<(unsigned)(8 * device_sm_count()), 256, 0, st>>>(g);
+    }
     ready = true;
-  }
-  // the R_3 blocks of dense test matrices: staged once and kept while the
-  // workspace holds this plan's tables (not marked inside a graph capture,
-  // whose launches may never run)
-  if (g.ytab >= 0 && !plan_ytab_valid(&P, ws)) {
-    count_launch();
-    tc::slab::slab_ytab_kernel<<<(unsigned)(8 * device_sm_count()), 256, 0, st>>>(g);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusActive;
-    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) plan_set_ytab_valid(&P, ws);
   }
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());

@@ -152,13 +152,13 @@ def test_mixed_slab_sizes_in_one_stream(drm):
     assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 3e-6
 
 
-def test_staged_r3_blocks_kept_and_restaged():
+def test_staged_r3_blocks_restaged_per_decomposition():
     """Dense test matrices on 16-slice slabs: R_3's 128-row blocks are staged
-    in the workspace once and kept while it holds the plan's tables.  Runs on
-    one caller workspace: fresh; again (blocks reused); after the workspace
-    was overwritten and released with tt_workspace_release; after another
-    plan used it and it was overwritten.  Every run must reproduce the first
-    (FP32 accumulation order only), which is within 10 eps of X."""
+    in the workspace at the first slab launch of each decomposition.  Runs on
+    one caller workspace: fresh; again; after the workspace was overwritten
+    and released with tt_workspace_release; after another plan used it and it
+    was overwritten.  Every run must reproduce the first (FP32 accumulation
+    order only), which is within 10 eps of X."""
     dims = [128, 8, 16, 64]
     x = ti.hilbert_type(dims, np.float32)
     X = to_dev(x)
