@@ -21,20 +21,31 @@
 //    (N = G l), and only its diagonal blocks (row group g, column block g) are
 //    kept.  The tensor pipe does G times the R_3 work it needs; it has the
 //    room (the kernel is bound by HBM).
-// Test-matrix blocks: the L block (S_1, S_2; 128 composite rows) and the R_3
-// blocks (128 rows of i_1 x G planes, regenerated for every quarter into a
-// single buffer) come from the RNG warps; the R_2 block comes from a staged
-// table (one per kL, generated once per call).  With dense Gaussian test
-// matrices the R_3 blocks cost l / c normals per entry of X (1 at c = l = 16),
-// which binds the kernel; with Khatri-Rao test matrices (TT_FLAG_KR) an R_3
-// entry is the product of the plane's two fixed factor entries (formed once
-// per quarter) and one row of the mode-1 factor, a few instructions.
+// Test-matrix blocks: the L block (S_1, S_2; 128 composite rows) comes from
+// the test-matrix warps for every super-plane; the R_2 block from a staged
+// table (one per kL, generated at the first launch of a decomposition).  R_3
+// with dense Gaussian test matrices: its rows belong to one plane each and
+// regenerating them costs l / c normals per entry of X (1 at c = l = 16), so
+// the G planes' blocks are generated once per decomposition into a table of
+// block images and bulk-copied per quarter by one warp (when the plan has
+// room for the table; else regenerated per quarter).  R_3 with Khatri-Rao
+// test matrices (TT_FLAG_KR) is taken mode by mode: X_sp^T round(F_1) against
+// one fixed block (the mode-1 factor), the plane's rounded mode-3 x mode-2
+// row product applied by the epilogue as a column scale per super-plane.
 //
 // Accumulators: one L slot per (kL of the tile, i_1 half), kept for runL
-// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block of a
-// tile are double-buffered and flushed after every tile (a tile of
-// T2 x T3 super-planes x H1 quarters gives each at most 256 accumulating MMAs).
-// Warp roles, barriers and bounded waits as in the plane kernel.
+// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block (of a
+// tile, or of a super-plane with Khatri-Rao) are double-buffered with the
+// epilogue; every accumulator sees at most 256 MMAs before a flush.  Flushes:
+// FP64 atomics into S_1, R_2 and R_3; FP32 atomics into a staging copy of S_2
+// (about four CTA partials per entry a launch), added into S_2 by
+// s2_fold_kernel after the launch.
+//
+// Warp roles: 4 epilogue warps (the TMEM lane quarters), 1 MMA issuer, 8
+// producers (X loads, hi / lo split into the BF16 operand stages), and 7
+// (dense) or 3 (Khatri-Rao) test-matrix warps.  Every mbarrier wait is
+// bounded; a wait that gives up raises the CTA's abort flag and the timeout
+// status bit, waits for its own copies and MMAs, frees TMEM and returns.
 #include <algorithm>
 #include <cstring>
 
