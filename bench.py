@@ -182,11 +182,11 @@ def traffic_record(kernel_tag):
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_sample(steps=1, n=128):
+def cpu_sample(steps=1, n=128, drm=HEADLINE_DRM):
     """The FP64 oracle as it stands, on a bounded sample of the workload: the
     same Hilbert-type function at d = 4 with a smaller n (n = 128: 268M
-    entries), same eps, p, rmax, one-pass.  Returns entries/s, the threads
-    used, the sample description and the per-step times."""
+    entries), same eps, p, rmax, test matrices, one-pass.  Returns entries/s,
+    the threads used, the sample description and the per-step times."""
     import numpy as np
     import ttinputs as ti
     from oracle import pstt2 as OP
@@ -196,7 +196,7 @@ def cpu_sample(steps=1, n=128):
     for _ in range(steps):
         t0 = time.perf_counter()
         OP.pstt2(x, dims, eps=WORKLOAD["eps"], rmax=WORKLOAD["rmax"], p=WORKLOAD["p"], seed=WORKLOAD["seed"],
-                 passes=1)
+                 passes=1, drm=drm)
         times.append(time.perf_counter() - t0)
     try:
         from threadpoolctl import threadpool_info
@@ -205,15 +205,16 @@ def cpu_sample(steps=1, n=128):
         cores = os.cpu_count()
     return n ** 4 / statistics.median(times), cores, (
         f"oracle.pstt2 one-pass on the Hilbert-type tensor at d=4, n={n} ({n ** 4} entries), eps=1e-6, "
-        f"p=10, rmax=6; entries/s = entries / wall time"), times
+        f"p=10, rmax=6, {'Khatri-Rao' if drm == 'kr' else 'dense Gaussian'} test matrices; "
+        f"entries/s = entries / wall time"), times
 
 
-def cpu_sample_one_core(n=64):
+def cpu_sample_one_core(n=64, drm=HEADLINE_DRM):
     """The same oracle sample on one host core: a child process with every
     BLAS / OpenMP pool limited to one thread (n = 64, 16.8M entries)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
-    code = f"import json, bench; v, _, s, _ = bench.cpu_sample(1, {n}); print(json.dumps([v, s]))"
+    code = f"import json, bench; v, _, s, _ = bench.cpu_sample(1, {n}, {drm!r}); print(json.dumps([v, s]))"
     try:
         r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                            timeout=300)
@@ -223,10 +224,10 @@ def cpu_sample_one_core(n=64):
         return {"error": f"{type(ex).__name__}: {ex}"}
 
 
-def reference_sample_n(steps, budget_s=150.0):
+def reference_sample_n(steps, drm, budget_s=150.0):
     """Largest sample size n in {32, 48, 64, 96, 128} whose `steps` oracle
     runs fit the time budget (cost scales with n^4; measured at n = 32)."""
-    t32 = cpu_sample(1, 32)[3][0]
+    t32 = cpu_sample(1, 32, drm)[3][0]
     best = 32
     for n in (48, 64, 96, 128):
         if t32 * (n / 32) ** 4 * steps <= budget_s:
@@ -239,16 +240,16 @@ def run_reference(a):
     if rank != 0:
         return
     steps = max(1, a.steps)
-    n = reference_sample_n(steps + min(a.warmup, 1))
+    n = reference_sample_n(steps + min(a.warmup, 1), a.drm)
     for _ in range(min(a.warmup, 1)):
-        cpu_sample(1, n)
-    v, cores, sample, times = cpu_sample(steps, n)
+        cpu_sample(1, n, a.drm)
+    v, cores, sample, times = cpu_sample(steps, n, a.drm)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "entries/s", "n_gpus": a.gpus,
             "steps": steps, "warmup": a.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"Hilbert-type d=4 n=256 FP32 (bounded sample per step: n={n})",
-                       "sample": sample},
+                       "test_matrices": a.drm, "sample": sample},
             "cpu_baseline": {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -933,9 +934,9 @@ def run_gpu(a):
 
     cpu = None
     if rank == 0 and not a.no_cpu:
-        v, cores, sample, _ = cpu_sample(1)
+        v, cores, sample, _ = cpu_sample(1, 128, a.drm)
         cpu = {"value": v, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample,
-               "one_core": cpu_sample_one_core()}
+               "one_core": cpu_sample_one_core(64, a.drm)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": a.steps,
