@@ -147,8 +147,11 @@ def kr_test_matrix(seed, stream, modes, sizes, ncols, decreasing=False):
 def round_to(a, fmt):
     """Round FP64 values to a narrower floating format, nearest-even.
 
-    fmt: 'f64' (identity), 'f32', 'tf32' (8-bit exponent, 10-bit mantissa) or
-    'bf16' (8-bit exponent, 7-bit mantissa).  Used by tests that mirror the
+    fmt: 'f64' (identity), 'f32', 'tf32' (8-bit exponent, 10-bit mantissa),
+    'bf16' (8-bit exponent, 7-bit mantissa) or 'fp16' (IEEE binary16: 5-bit
+    exponent, 10-bit mantissa, subnormals below 2^-14, magnitudes that round
+    above 65504 become infinite).  The value is first held in FP32 (as the
+    product path holds it), then rounded once.  Used by tests that mirror the
     precision of a mixed-precision product path on the oracle side.
     """
     a = np.asarray(a, dtype=np.float64)
@@ -157,9 +160,28 @@ def round_to(a, fmt):
     f = a.astype(np.float32)
     if fmt == 'f32':
         return f.astype(np.float64)
+    if fmt == 'fp16':
+        return _round_binary16(f.astype(np.float64))
     drop = {'tf32': 13, 'bf16': 16}[fmt]
     u = f.view(np.uint32).astype(np.uint64)
     half = np.uint64(1 << (drop - 1))
     lsb = (u >> np.uint64(drop)) & np.uint64(1)
     u = (u + half - np.uint64(1) + lsb) & ~np.uint64((1 << drop) - 1)
     return (u & _MASK32).astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _round_binary16(v):
+    """Nearest-even rounding of FP64 values to IEEE binary16, from the format:
+    the quantum of a value is 2^(e - 10) with e its binary exponent, clamped
+    below at -14 (the subnormal range has the fixed quantum 2^-24); the largest
+    finite value is 65504 = (2 - 2^-10) 2^15, and a result above it is an
+    overflow (infinite).  Infinities and NaNs pass through."""
+    v = np.asarray(v, dtype=np.float64)
+    out = v.copy()
+    fin = np.isfinite(v) & (v != 0.0)
+    m, e = np.frexp(np.abs(v[fin]))           # |v| = m 2^e, m in [0.5, 1)
+    q = np.ldexp(1.0, np.maximum(e - 1, -14) - 10)
+    r = np.round(v[fin] / q) * q               # exact scaling; np.round is half-to-even
+    r[np.abs(r) > 65504.0] = np.inf * np.sign(r[np.abs(r) > 65504.0])
+    out[fin] = r
+    return out

@@ -56,6 +56,32 @@ def test_round_to_matches_torch_bf16():
     np.testing.assert_array_equal(philox.round_to(x, "bf16"), ref)
 
 
+def test_round_to_fp16_matches_numpy_half():
+    # numpy's float16 cast (IEEE binary16, nearest-even, subnormals, overflow)
+    # as the library reference, over normals, subnormals and the range ends
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(20_000) * 2.0 ** rng.uniform(-30, 17, 20_000)
+    x = np.concatenate([x, [0.0, -0.0, 65504.0, 65519.99, 65520.0, -65520.0, 2.0 ** -24, 2.0 ** -25,
+                            3 * 2.0 ** -26, 2.0 ** -14, 2.0 ** -14 - 2.0 ** -25, np.inf, -np.inf]])
+    f32 = x.astype(np.float32)
+    ref = f32.astype(np.float16).astype(np.float64)
+    np.testing.assert_array_equal(philox.round_to(x, "fp16"), ref)
+    assert np.isnan(philox.round_to(np.array([np.nan]), "fp16")[0])
+
+
+def test_round_to_fp16_cases():
+    # ties to even at 1 (quantum 2^-10) and in the subnormal range (quantum 2^-24)
+    cases = {1.0 + 2.0 ** -11: 1.0, 1.0 + 3 * 2.0 ** -11: 1.0 + 2.0 ** -9, 2.0 ** -25: 0.0,
+             3 * 2.0 ** -25: 2.0 ** -23, 65519.0: 65504.0, 65520.0: np.inf, -(1.0 + 2.0 ** -12): -1.0}
+    for a, b in cases.items():
+        assert philox.round_to(np.array([a]), "fp16")[0] == b
+    # relative error at most 2^-11 in the normal range
+    x = np.random.default_rng(4).standard_normal(1000)
+    x = x[np.abs(x) >= 2.0 ** -14]
+    r = philox.round_to(x, "fp16")
+    assert np.all(np.abs(r - x) <= 2.0 ** -11 * np.abs(x) * 1.0000001)
+
+
 def test_round_to_tf32_cases():
     # 1 + 2^-11 is a tie between 1 and 1 + 2^-10 -> even (1); 1 + 3*2^-11 -> 1 + 2^-9
     cases = {1.0 + 2.0 ** -11: 1.0, 1.0 + 3 * 2.0 ** -11: 1.0 + 2.0 ** -9,
