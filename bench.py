@@ -31,6 +31,9 @@ METRIC = "PSTT2 tensor entries/s and HBM roofline fraction, mixed vs FP64 GPU at
 WORKLOAD = dict(dims=[256, 256, 256, 256], eps=1e-6, p=10, rmax=6, seed=1)
 SLAB = 16  # last-mode slices per 1 GiB slab (256^3 * 4 B * 16 = 1 GiB)
 HEADLINE_DRM = "kr"  # the paper's test matrices for its streaming implementation (Sec. 4.2)
+# FP16 hi + lo of X 2^s: 2^-22 relative, below the rank threshold eps / sqrt(d - 1)
+# that the BF16 split (2^-17) cannot resolve, at BF16's cost
+HEADLINE_PREC = "fp16"
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure on this machine)
 
 
@@ -40,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["bf16", "tf32"])
+    ap.add_argument("--prec", default=HEADLINE_PREC, choices=["fp16", "bf16", "tf32"],
+                    help="sketch precision of the headline (fp16: X 2^s split into FP16 hi + lo)")
     ap.add_argument("--drm", default=HEADLINE_DRM, choices=["gauss", "kr"],
                     help="test matrices of the headline: dense Gaussian or Khatri-Rao")
     ap.add_argument("--slab", type=int, default=SLAB, help="last-mode slices per accumulate (16 = 1 GiB at n=256)")
@@ -153,7 +157,9 @@ def measured_tensor_peak(prec):
             d = json.load(f)
         if d.get("bf16_tflops"):
             bf16, kind = d["bf16_tflops"], "measured"
-    return (bf16, f"{kind} bf16_tflops") if prec == "bf16" else (bf16 * 1.1 / 2.25, f"{kind} bf16_tflops x 1.1/2.25")
+    if prec in ("bf16", "fp16"):  # kind::f16: the same MMA rate for both operand types
+        return bf16, f"{kind} bf16_tflops"
+    return bf16 * 1.1 / 2.25, f"{kind} bf16_tflops x 1.1/2.25"
 
 
 def traffic_record(kernel_tag):
@@ -374,10 +380,12 @@ def run_precision(a, dev, P, stream):
     ref = None
     # "<prec>_kr": the same with Khatri-Rao test matrices (cheap per-plane rows
     # on the small planes of this tensor); its error is reported against X
-    precs = a.precision_only.split(",") if a.precision_only else ["fp64", "tf32", "bf16", "bf16_kr"]
+    precs = a.precision_only.split(",") if a.precision_only else ["fp64", "tf32", "bf16", "fp16", "bf16_kr"]
+    xs_log2 = P.x_scale_log2(X, stream)  # FP16 split scale of this tensor
     for form in precs:
         prec, _, drm = form.partition("_")
-        t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec, drm=drm or "gauss")
+        t = P.TTSketch(dims, eps=1e-5, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec, drm=drm or "gauss",
+                       x_scale_log2=xs_log2)
         t.pstt2(X, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -714,8 +722,11 @@ def run_gpu(a):
     N.check(L.tt_generate_hilbert_type(4, nn, 0, nl, C.c_void_p(X.data_ptr()), N.TT_F32, sp), "gen")
     stream.synchronize()
 
+    # FP16 split of X 2^s: s from the largest |X| (one reduction over the
+    # resident tensor, before any timing); 16 for this tensor, |X| <= 1/4
+    xs_log2 = P.x_scale_log2(X, stream) if a.prec == "fp16" else 0
     kw = dict(eps=WORKLOAD["eps"], rmax=WORKLOAD["rmax"], p=WORKLOAD["p"], seed=WORKLOAD["seed"] + rank,
-              x_dtype=torch.float32, device=dev)
+              x_dtype=torch.float32, device=dev, x_scale_log2=xs_log2)
     slab = a.slab if nl % a.slab == 0 else nl
 
     def stream_step(t, sl, evs=None):
@@ -730,7 +741,8 @@ def run_gpu(a):
                 evs[k][1].record(stream)
         t.finalize(stream)
 
-    STATUS = {0: "TT_OK", 5: "TT_ERR_RANK_DEFICIENT", 6: "TT_ERR_TIMEOUT", 7: "TT_WARN_RANK_CAP"}
+    STATUS = {0: "TT_OK", 5: "TT_ERR_RANK_DEFICIENT", 6: "TT_ERR_TIMEOUT", 7: "TT_WARN_RANK_CAP",
+              9: "TT_ERR_NONFINITE"}
 
     def measure_form(t, sl, steps, warmup):
         """Whole-step and per-slab sketch times of one form (CUDA events on
@@ -946,14 +958,16 @@ def run_gpu(a):
                                        f"streamed in {nl // slab} slabs of {slab} last-mode slices "
                                        f"({slab * Nd1 * 4 / 2 ** 30:.2f} GiB each), eps=1e-6 p=10 rmax=6, "
                                        f"{'Khatri-Rao' if a.drm == 'kr' else 'dense Gaussian'} test matrices, "
-                                       f"{a.prec} tensor-core sketch with X split hi+lo, FP64 solves",
-                           "test_matrices": a.drm, "slab_slices": slab,
+                                       f"{a.prec} tensor-core sketch with X split hi+lo"
+                                       f"{f' (X 2^{xs_log2})' if a.prec == 'fp16' else ''}, FP64 solves",
+                           "test_matrices": a.drm, "slab_slices": slab, "x_scale_log2": xs_log2,
                            "l2": "inputs larger than L2 (no flush needed)",
                            "ranks": ranks, "status": STATUS.get(st, st), "rel_err_vs_X": rel_err,
                            "meets_eps": rel_err <= WORKLOAD["eps"],
                            "status_note": None if st == 0 else (
                                "the rank rule stopped at rmax: the BF16 hi+lo sketch (about 2^-17 relative) "
-                               "cannot resolve the threshold eps/sqrt(d-1); the result is within 10 eps"),
+                               "cannot resolve the threshold eps/sqrt(d-1); the result is within 10 eps"
+                               if a.prec == "bf16" else "see status"),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": out.get("e2e"),
                 "gpu_launches": int(l1 - l0), "clocks": clocks, "fp64_gpu": out.get("fp64_gpu"),

@@ -76,7 +76,9 @@ typedef enum {
   TT_ERR_RANK_DEFICIENT = 5,  /* device: B = P^T Omega (one-pass) is singular   */
   TT_ERR_TIMEOUT = 6,         /* device: a bounded wait gave up                 */
   TT_WARN_RANK_CAP = 7,       /* device: eps not met at rmax; cores still valid */
-  TT_ERR_NO_DEVICE = 8        /* no usable CUDA device                          */
+  TT_ERR_NO_DEVICE = 8,       /* no usable CUDA device                          */
+  TT_ERR_NONFINITE = 9        /* device: an FP16 plan's sketch holds an inf or  */
+                              /* NaN (X non-finite, or |X| 2^s past FP16 range) */
 } tt_status;
 
 typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
@@ -84,12 +86,23 @@ typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
 /* Arithmetic of the sketch (the hot loop).  The small solves (QR, least
  * squares, core products) are always FP64.
  *  FP64: FP64 FMA everywhere (the correctness path).
- *  TF32 / BF16: tensor cores with FP32 accumulation, flushed into FP64 sketch
- *    accumulators.  The test-matrix entries are rounded once to the MMA type;
- *    X is split into a high and a low part of the MMA type (two products),
- *    which keeps the error of the sketch near 2^-22 (TF32) / 2^-17 (BF16)
- *    relative instead of 2^-11 / 2^-9. */
-typedef enum { TT_PREC_FP64 = 0, TT_PREC_TF32 = 1, TT_PREC_BF16 = 2 } tt_prec;
+ *  TF32 / BF16 / FP16: tensor cores with FP32 accumulation, flushed into FP64
+ *    sketch accumulators.  The test-matrix entries are rounded once to the
+ *    MMA type; X is split into a high and a low part of the MMA type (two
+ *    products), which keeps the error of the sketch near 2^-22 (TF32) /
+ *    2^-17 (BF16) / 2^-22 (FP16) relative instead of 2^-11 / 2^-9 / 2^-11.
+ *  FP16 has BF16's cost (16-bit operands, the same MMA rate) and TF32's
+ *    resolution, but a narrow range: the split is of X 2^s, s =
+ *    x_scale_log2 (a power of two, so the scaling is exact), and the FP64
+ *    sketches are scaled back by 2^-s before the bases are formed.  Full
+ *    resolution needs 2^-3 <= |X| 2^s < 65520 for the entries that matter:
+ *    below 2^-3 the low part is subnormal and the split's error is at most
+ *    2^-25 2^-s absolute; at 65520 and above the high part overflows and the
+ *    finalize reports TT_ERR_NONFINITE (tt_x_scale_log2 picks s from the
+ *    largest |X|).  Of the tensor-core kernels, the sketch adjoint of
+ *    tt_pstt2_backward is BF16 / TF32 only: FP16 plans take the SIMT
+ *    adjoint (same result, slower). */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_TF32 = 1, TT_PREC_BF16 = 2, TT_PREC_FP16 = 3 } tt_prec;
 
 typedef struct {
   int d;                     /* order, 2 <= d <= TT_MAXD                         */
@@ -103,6 +116,8 @@ typedef struct {
   tt_dtype x_dtype;          /* storage type of X                                */
   tt_prec prec;              /* arithmetic of the sketch                         */
   int flags;                 /* TT_FLAG_* bits                                   */
+  int x_scale_log2;          /* FP16 plans: s, X is split as X 2^s (-100..100);  */
+                             /* other precisions ignore it                       */
 } tt_problem;
 
 /* Reserve the workspace that tt_reconstruct_backward needs (all left and
@@ -231,8 +246,8 @@ tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
  * anything runs.  X, cores and ranks are as for tt_pstt2; status_dev, if not
  * NULL, is a device int that receives the device status bits of the call:
  * 1 = rank cap reached (TT_WARN_RANK_CAP), 2 = singular least-squares matrix
- * (TT_ERR_RANK_DEFICIENT), 4 = a bounded wait gave up (TT_ERR_TIMEOUT);
- * 0 = no condition.  Nothing has to be zeroed by the
+ * (TT_ERR_RANK_DEFICIENT), 4 = a bounded wait gave up (TT_ERR_TIMEOUT),
+ * 8 = a non-finite sketch entry (TT_ERR_NONFINITE); 0 = no condition.  Nothing has to be zeroed by the
  * caller: the call clears the sketches and the status word itself.
  * The first call on a device sets the array up (it looks up its address) and
  * the first call with a plan sends that plan's tables into it with a
@@ -318,12 +333,23 @@ tt_status tt_reconstruct_backward(tt_plan_t plan, const double* cores, const voi
 
 /* SYNCHRONOUS: waits for `stream`, then reads the workspace status word and
  * the rank array.  status_host (may be NULL) receives TT_OK,
- * TT_WARN_RANK_CAP, TT_ERR_RANK_DEFICIENT or TT_ERR_TIMEOUT (the worst seen
- * over all items); ranks_host (may be NULL) receives rank_entries ints. */
+ * TT_WARN_RANK_CAP, TT_ERR_RANK_DEFICIENT, TT_ERR_TIMEOUT or TT_ERR_NONFINITE
+ * (the worst seen over all items); ranks_host (may be NULL) receives
+ * rank_entries ints. */
 tt_status tt_query_status(tt_plan_t plan, const void* ws, const int* ranks, int* status_host,
                           int* ranks_host, tt_stream_t stream);
 
 const char* tt_status_string(tt_status s);
+
+/* SYNCHRONOUS helper for FP16 plans (not in the paper): the scale exponent s
+ * = 15 - e, where 2^(e-1) <= max |X| < 2^e, so that every |X| 2^s < 2^15
+ * (the FP16 range ends at 65504) and the low parts of the split stay normal
+ * down to |X| = 2^-18 max |X|.  X: device, dtype, count entries; reads X once
+ * with one reduction kernel on `stream` and waits for it.  *s_out = 0 when X
+ * is all zero or count = 0.  Errors: TT_ERR_INVALID_ARG (null pointer, count
+ * < 0), TT_ERR_NONFINITE (X holds an inf or NaN; *s_out unchanged),
+ * TT_ERR_CUDA. */
+tt_status tt_x_scale_log2(const void* X, tt_dtype dtype, int64_t count, int* s_out, tt_stream_t stream);
 
 /* -------------------------------------------------------- test helpers */
 
@@ -331,7 +357,7 @@ const char* tt_status_string(tt_status s);
  * [row0, row0 + nrows) and columns [0, ncols) of stream `stream_id`, written
  * column-major to out (device, FP64, nrows x ncols) exactly as the sketch of
  * precision `prec` uses them (FP64 values, or the FP32 generator rounded to
- * TF32 / BF16).  Errors: TT_ERR_INVALID_ARG (null out, negative sizes or
+ * TF32 / BF16 / FP16).  Errors: TT_ERR_INVALID_ARG (null out, negative sizes or
  * row0, ncols > TT_MAXL, unknown prec), TT_ERR_CUDA; empty ranges are TT_OK. */
 tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nrows, int ncols,
                          tt_prec prec, double* out, tt_stream_t stream);

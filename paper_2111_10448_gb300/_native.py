@@ -14,9 +14,9 @@ TT_MAXD = 16
 TT_MAXL = 64
 
 TT_OK, TT_ERR_INVALID_ARG, TT_ERR_UNSUPPORTED, TT_ERR_CUDA, TT_ERR_STATE, \
-    TT_ERR_RANK_DEFICIENT, TT_ERR_TIMEOUT, TT_WARN_RANK_CAP, TT_ERR_NO_DEVICE = range(9)
+    TT_ERR_RANK_DEFICIENT, TT_ERR_TIMEOUT, TT_WARN_RANK_CAP, TT_ERR_NO_DEVICE, TT_ERR_NONFINITE = range(10)
 TT_F32, TT_F64 = 0, 1
-TT_PREC_FP64, TT_PREC_TF32, TT_PREC_BF16 = 0, 1, 2
+TT_PREC_FP64, TT_PREC_TF32, TT_PREC_BF16, TT_PREC_FP16 = 0, 1, 2, 3
 TT_FLAG_DIFF = 1
 TT_FLAG_ONESIDED = 2
 TT_FLAG_KR = 4
@@ -24,7 +24,7 @@ TT_FLAG_KR = 4
 STATUS_NAMES = {
     0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_UNSUPPORTED", 3: "TT_ERR_CUDA",
     4: "TT_ERR_STATE", 5: "TT_ERR_RANK_DEFICIENT", 6: "TT_ERR_TIMEOUT", 7: "TT_WARN_RANK_CAP",
-    8: "TT_ERR_NO_DEVICE",
+    8: "TT_ERR_NO_DEVICE", 9: "TT_ERR_NONFINITE",
 }
 
 
@@ -41,6 +41,7 @@ class tt_problem(C.Structure):
         ("x_dtype", C.c_int),
         ("prec", C.c_int),
         ("flags", C.c_int),
+        ("x_scale_log2", C.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ _SIGS = {
     "tt_reconstruct_backward": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "tt_query_status": (C.c_int, [_P, _P, _P, C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
     "tt_status_string": (C.c_char_p, [C.c_int]),
+    "tt_x_scale_log2": (C.c_int, [_P, C.c_int, C.c_int64, C.POINTER(C.c_int), _P]),
     "tt_test_matrix": (C.c_int, [C.c_uint64, C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_int, _P, _P]),
     "tt_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64, _P]),
     "tt_generate_hilbert_type": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.c_int64, C.c_int64, _P,
@@ -120,7 +122,7 @@ def check(status, where):
 
 
 def make_problem(dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
-                 x_dtype=TT_F32, prec=TT_PREC_FP64, flags=0):
+                 x_dtype=TT_F32, prec=TT_PREC_FP64, flags=0, x_scale_log2=0):
     q = tt_problem()
     q.d = len(dims)
     if q.d > TT_MAXD:
@@ -138,4 +140,5 @@ def make_problem(dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
     q.x_dtype = int(x_dtype)
     q.prec = int(prec)
     q.flags = int(flags)
+    q.x_scale_log2 = int(x_scale_log2)
     return q

@@ -24,17 +24,20 @@ class TTSketch:
     dims: mode sizes; ranks (fixed-rank mode, [1, r_1, .., r_{d-1}, 1]) or eps
     (> 0, tolerance mode, with rmax); p: oversampling; seed: Philox key;
     passes: 1 (one-pass, the hot path) or 2; x_dtype: torch.float32/float64;
-    prec: 'fp64' | 'tf32' | 'bf16'; one_sided: the one-sided PSTT-onepass
+    prec: 'fp64' | 'tf32' | 'bf16' | 'fp16'; x_scale_log2: the power-of-two
+    scale s of X before an FP16 split (X 2^s must stay below 65520; see
+    x_scale_log2() below); one_sided: the one-sided PSTT-onepass
     (every unfolding sketched from the right, last core by least squares)
     instead of the two-sided PSTT2-onepass; drm: 'gauss' (dense Gaussian test
     matrices) or 'kr' (Khatri-Rao products of per-mode Gaussian factors).
     """
 
-    PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
+    PRECS = {"fp64": N.TT_PREC_FP64, "tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16,
+             "fp16": N.TT_PREC_FP16}
 
     def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
                  x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False,
-                 one_sided=False, drm="gauss"):
+                 one_sided=False, drm="gauss", x_scale_log2=0):
         L = N.lib()
         self.device = torch.device(device)
         if batch is None:
@@ -49,7 +52,8 @@ class TTSketch:
                                     x_dtype=_DT[x_dtype], prec=self.PRECS[prec],
                                     flags=(N.TT_FLAG_DIFF if diff else 0) |
                                     (N.TT_FLAG_ONESIDED if one_sided else 0) |
-                                    (N.TT_FLAG_KR if drm == "kr" else 0))
+                                    (N.TT_FLAG_KR if drm == "kr" else 0),
+                                    x_scale_log2=pr.get("x_scale_log2", x_scale_log2))
         h = C.c_void_p()
         if batch is None:
             N.check(L.tt_sketch_plan(C.byref(arr[0]), C.byref(h)), "tt_sketch_plan")
@@ -231,6 +235,15 @@ class TTReconstructFn(torch.autograd.Function):
     def backward(ctx, dXt):
         (cores,) = ctx.saved_tensors
         return ctx.sk.reconstruct_backward(dXt.contiguous(), cores=cores.contiguous()), None, None
+
+
+def x_scale_log2(X, stream=None):
+    """The FP16 scale exponent of tt_x_scale_log2 for the device tensor X
+    (one reduction kernel over X; waits for it)."""
+    s = C.c_int(0)
+    N.check(N.lib().tt_x_scale_log2(_ptr(X), _DT[X.dtype], X.numel(), C.byref(s), _stream(stream)),
+            "tt_x_scale_log2")
+    return s.value
 
 
 def pstt2(X, dims, **kw):

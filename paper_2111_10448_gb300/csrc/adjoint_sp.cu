@@ -34,7 +34,7 @@ namespace tts {
 
 const DevSketch* plan_sketches_host(const Plan* p);
 cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint64_t seed, int64_t first, int64_t n1,
-                              int nr, int lpad, int64_t nkeys, char* tab, bool tf, cudaStream_t st);
+                              int nr, int lpad, int64_t nkeys, char* tab, int prec, cudaStream_t st);
 
 namespace adj {
 
@@ -304,8 +304,8 @@ cudaError_t launch_adjoint_sp(const Plan& P, int item, void* dX, void* ws, cudaS
       k.tab = it.off_sptab * 8 + d.sp_tab;
       const int nr = k.col ? (int)g.nd : (int)g.n1;
       const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
-      e = launch_rows_table(d, it.sk0 + s, (const char*)ws, it.seed, 0, g.n1, nr, lpad, nkeys, (char*)ws + k.tab, tf,
-                            st);
+      e = launch_rows_table(d, it.sk0 + s, (const char*)ws, it.seed, 0, g.n1, nr, lpad, nkeys, (char*)ws + k.tab,
+                            it.prec, st);
       if (e != cudaSuccess) return e;
     }
   }

@@ -374,6 +374,33 @@ __device__ __forceinline__ void flag_status(char* wsb, int bits) {
   atomicOr(reinterpret_cast<int*>(wsb + kStatusOff), bits);
 }
 
+// FP16 plans: the sketch kernels split X 2^s (s = x_scale_log2), so every
+// sketch holds 2^s times its value.  Scale the sketches of item item0 +
+// blockIdx.y back by 2^-s (exact in FP64) and flag a non-finite entry (an
+// inf or NaN in X, or |X| 2^s past the FP16 range), which is replaced by
+// zero so that the finalize runs on finite values (its result is then
+// meaningless; the status word says so).
+__global__ void __launch_bounds__(kThreads) sketch_unscale_kernel(char* wsb, int item0) {
+  const DevItem& it = ditems(wsb)[item0 + (int)blockIdx.y];
+  if (it.prec != TT_PREC_FP16) return;
+  const DevSketch* sks = dsk(wsb);
+  double* ws = reinterpret_cast<double*>(wsb);
+  const double f = ldexp(1.0, -it.x_scale_log2);
+  int bad = 0;
+  for (int s = 0; s < it.nsk; ++s) {
+    const DevSketch& d = sks[it.sk0 + s];
+    double* p = ws + d.off;
+    const int64_t n = d.rows * d.width;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+      const double v = p[e] * f;
+      const bool fin = isfinite(v);
+      bad |= fin ? 0 : 1;
+      p[e] = fin ? v : 0.0;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) flag_status(wsb, ST_NONFINITE);
+}
+
 // ------------------------------------------------------------------ TSQR up
 // One task = one row block of level L of one basis sketch (launch Lg holds
 // the tasks whose tree has Lg - L more levels above them than the deepest
@@ -465,7 +492,9 @@ __global__ void __launch_bounds__(kThreads, 4) tsqr_level_kernel(char* wsb, int 
           const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
           if (k2 > key || (k2 == key && a2 < arg)) key = k2, arg = a2;
         }
-        const int j = arg;
+        // no key above -1 (every trailing norm a NaN with the sign bit set):
+        // keep column i, so that the swap stays inside the block
+        const int j = arg < w ? arg : i;
         if (j != i) {
           for (int r = lane; r < w; r += 32) {
             const double t = Rs[r + w * i];
@@ -1011,6 +1040,17 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     e = cudaFuncSetAttribute(tsqr_expand_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsqrSmemMax);
     if (e != cudaSuccess) return e;
     attr = true;
+  }
+  // FP16 items: sketches back to the scale of X, and the range check
+  {
+    bool any16 = false;
+    for (int i = 0; i < nitems; ++i) any16 = any16 || plan_items_host(&P)[i].prec == TT_PREC_FP16;
+    if (any16) {
+      count_launch();
+      sketch_unscale_kernel<<<dim3((unsigned)(2 * device_sm_count()), (unsigned)nitems), kThreads, 0, st>>>(wsb, 0);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   // smem: block (bl+1) x w + scalars + two w x w matrices (root)
   int maxw = 1, maxbl = 1;

@@ -1,6 +1,8 @@
 // Synthetic inputs and raw access to the Gaussian stream (test and benchmark
 // helpers of the C ABI).
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 #include "philox.cuh"
@@ -136,6 +138,23 @@ int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * device_sm_count()));
 }
 
+// max |X| as the bit pattern of an FP64 value (non-negative FP64 values order
+// like their bit patterns; an inf or NaN gives a pattern >= that of inf).
+__global__ void absmax_kernel(const void* x, int f64, int64_t n, unsigned long long* out) {
+  unsigned long long m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = f64 ? reinterpret_cast<const double*>(x)[e] : (double)reinterpret_cast<const float*>(x)[e];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 }  // namespace
 
 cudaError_t launch_test_matrix_mixed(uint64_t seed, int sid, int64_t row0, int64_t nrows, int ncols,
@@ -245,10 +264,46 @@ tt_status tt_test_matrix(uint64_t seed, int stream_id, int64_t row0, int64_t nro
                                                                                 ncols, out);
     return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
-  if (prec != TT_PREC_TF32 && prec != TT_PREC_BF16) return TT_ERR_INVALID_ARG;
+  if (prec != TT_PREC_TF32 && prec != TT_PREC_BF16 && prec != TT_PREC_FP16) return TT_ERR_INVALID_ARG;
   return launch_test_matrix_mixed(seed, stream_id, row0, nrows, ncols, prec, out, st) == cudaSuccess
              ? TT_OK
              : TT_ERR_CUDA;
+}
+
+tt_status tt_x_scale_log2(const void* X, tt_dtype dtype, int64_t count, int* s_out, tt_stream_t stream) {
+  if (!X || !s_out || count < 0 || (dtype != TT_F32 && dtype != TT_F64)) return TT_ERR_INVALID_ARG;
+  if (count == 0) {
+    *s_out = 0;
+    return TT_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  if (cudaMallocAsync(&d, sizeof(unsigned long long), st) != cudaSuccess) return TT_ERR_CUDA;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    count_launch();
+    absmax_kernel<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4LL * device_sm_count()), 256, 0, st>>>(
+        X, dtype == TT_F64 ? 1 : 0, count, d);
+    e = cudaGetLastError();
+  }
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return TT_ERR_CUDA;
+  // |v| as FP64 bits: the largest finite pattern is below that of infinity
+  if (bits >= 0x7FF0000000000000ull) return TT_ERR_NONFINITE;
+  double mx = 0.0;
+  std::memcpy(&mx, &bits, sizeof(mx));
+  if (mx == 0.0) {
+    *s_out = 0;
+    return TT_OK;
+  }
+  int ex = 0;
+  std::frexp(mx, &ex);  // 2^(ex-1) <= mx < 2^ex
+  *s_out = std::max(-100, std::min(100, 15 - ex));
+  return TT_OK;
 }
 
 tt_status tt_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out,

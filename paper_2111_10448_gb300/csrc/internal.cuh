@@ -42,7 +42,7 @@ constexpr int kMaxSk = TT_MAXD;   // sketches per item (d of them at most)
 enum SkType : int { SK_COL = 0, SK_ROW = 1 };
 
 // Status bits written on the device (workspace word 0).
-enum : int { ST_RANK_CAP = 1, ST_RANK_DEFICIENT = 2, ST_TIMEOUT = 4 };
+enum : int { ST_RANK_CAP = 1, ST_RANK_DEFICIENT = 2, ST_TIMEOUT = 4, ST_NONFINITE = 8 };
 
 struct DevSketch {
   int64_t rows;        // N_k (column) or M_k (row)
@@ -147,6 +147,8 @@ struct DevItem {
   int64_t s2stage_doubles;  // into S_2 after every launch (0: the slab kernel cannot serve the item)
   int64_t off_ytab;         // slab kernel, dense test matrices: Psi_3's 128-row blocks for every
   int64_t ytab_doubles;     // (half of i_1, kL, kR), generated once per decomposition (0: per quarter)
+  int x_scale_log2;         // FP16: s, the sketch kernels split X 2^s (0 for other precisions)
+  float xscale;             // 2^s
 };
 
 struct Task {               // one block of one TSQR level (finalize)
@@ -207,11 +209,11 @@ int64_t slab_chunk(const Plan& P, int item, int64_t count);
 cudaError_t launch_sketch_slab(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                                cudaStream_t st);
 // Fill the staged test-matrix rows of one sketch: entry (key, r, j), r < nr,
-// j < lpad, at element (key nr + r) lpad + j of tab (BF16, or FP32 rounded to
-// TF32 when tf), rows as the sketch's test matrix numbers them for the slab
-// starting at `first` (column side) or for plane key (row side).
+// j < lpad, at element (key nr + r) lpad + j of tab (BF16 or FP16, or FP32
+// rounded to TF32, by prec), rows as the sketch's test matrix numbers them for
+// the slab starting at `first` (column side) or for plane key (row side).
 cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint64_t seed, int64_t first, int64_t n1,
-                              int nr, int lpad, int64_t nkeys, char* tab, bool tf, cudaStream_t st);
+                              int nr, int lpad, int64_t nkeys, char* tab, int prec, cudaStream_t st);
 cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t first, int64_t count, void* ws,
                              cudaStream_t st);
 bool sp_batched_eligible(const Plan& P, size_t* smem_out, int* lpad_out, int t3max = 4);

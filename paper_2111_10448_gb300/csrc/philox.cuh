@@ -23,6 +23,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 namespace tts {
 
 __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
@@ -99,8 +101,9 @@ __device__ __forceinline__ float round_bf16(float x) {
   u = (u + 0x7FFFu + lsb) & ~0xFFFFu;
   return __uint_as_float(u);
 }
+__device__ __forceinline__ float round_f16(float x) { return __half2float(__float2half_rn(x)); }
 __device__ __forceinline__ float round_prec(float x, int prec) {
-  return prec == TT_PREC_TF32 ? round_tf32(x) : round_bf16(x);
+  return prec == TT_PREC_TF32 ? round_tf32(x) : prec == TT_PREC_FP16 ? round_f16(x) : round_bf16(x);
 }
 
 }  // namespace tts

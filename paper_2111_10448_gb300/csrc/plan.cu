@@ -8,6 +8,7 @@
 // widths are l_k = r_k + p (fixed ranks) or rmax + p (tolerance mode).
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -94,8 +95,9 @@ static tt_status validate(const tt_problem& q) {
   if (q.passes != 1 && q.passes != 2) return TT_ERR_INVALID_ARG;
   if (!(q.eps >= 0.0)) return TT_ERR_INVALID_ARG;
   if (q.x_dtype != TT_F32 && q.x_dtype != TT_F64) return TT_ERR_INVALID_ARG;
-  if (q.prec != TT_PREC_FP64 && q.prec != TT_PREC_TF32 && q.prec != TT_PREC_BF16)
+  if (q.prec != TT_PREC_FP64 && q.prec != TT_PREC_TF32 && q.prec != TT_PREC_BF16 && q.prec != TT_PREC_FP16)
     return TT_ERR_INVALID_ARG;
+  if (q.prec == TT_PREC_FP16 && (q.x_scale_log2 < -100 || q.x_scale_log2 > 100)) return TT_ERR_INVALID_ARG;
   if (q.prec != TT_PREC_FP64 && q.x_dtype != TT_F32) return TT_ERR_UNSUPPORTED;
   if (q.eps > 0.0) {
     if (q.rmax < 1 || q.rmax + q.p > TT_MAXL) return TT_ERR_INVALID_ARG;
@@ -130,6 +132,8 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   it.mcore = it.sided1 ? d : it.ds;
   it.passes = q.passes;
   it.prec = q.prec;
+  it.x_scale_log2 = q.prec == TT_PREC_FP16 ? q.x_scale_log2 : 0;
+  it.xscale = std::ldexp(1.0f, it.x_scale_log2);
   it.x_f64 = q.x_dtype == TT_F64;
   it.eps_mode = q.eps > 0.0;
   it.eps = q.eps;
@@ -270,11 +274,13 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.off_RB = ws.take((int64_t)r * r);
     it.off_H = ws.take(P.sketches[it.mid_sk].rows * r);
   }
-  // Staging area of the BF16 plane kernel: test-matrix blocks whose rows do
-  // not depend on the plane (column sketches with wdiv > 1, row sketches with
-  // wdiv < W), one 128-row block image per distinct value and half.
+  // Staging area of the BF16 / FP16 plane kernel: test-matrix blocks whose
+  // rows do not depend on the plane (column sketches with wdiv > 1, row
+  // sketches with wdiv < W), one 128-row block image per distinct value and
+  // half.
+  const bool op16 = q.prec == TT_PREC_BF16 || q.prec == TT_PREC_FP16;
   it.tctab_doubles = 0;
-  if (q.prec == TT_PREC_BF16 && q.x_dtype == TT_F32 && (d == 3 || d == 4) &&
+  if (op16 && q.x_dtype == TT_F32 && (d == 3 || d == 4) &&
       (q.n[0] == 128 || q.n[0] == 256)) {
     int64_t bytes = 0;
     const int64_t hd = (std::min<int64_t>(q.n[d - 1], 256) + 127) / 128, h1 = q.n[0] / 128;
@@ -287,7 +293,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     it.tctab_doubles = (bytes + 7) / 8;
   }
   it.off_tctab = it.tctab_doubles ? ws.take(it.tctab_doubles) : 0;
-  // FP32 staging of S_2 for the slab kernel (d = 4, BF16, n_1 in {128, 256},
+  // FP32 staging of S_2 for the slab kernel (d = 4, BF16 / FP16, n_1 in {128, 256},
   // single-problem two-sided one-pass plans): its L-slot flush adds FP32
   // partials there, and one pass after each launch adds them into the FP64
   // sketch.
@@ -300,7 +306,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   // Dense Gaussian slab streaming: R_3's test-matrix rows (i_1 + n_1 w) belong
   // to one plane each, so a slab of c slices draws l / c normals per entry of
   // X to regenerate them; every slab needs the same rows, so they are
-  // generated once per decomposition (at its first slab launch) as BF16 block
+  // generated once per decomposition (at its first slab launch) as 16-bit block
   // images, one per (half of i_1, kL, kR), kR fastest (2 (n_1 / 128) n_2 n_3 l
   // bytes up to padding: 604 MB at 256^4, capped at 1 GiB), and not kept
   // after it.
@@ -313,15 +319,15 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     }
   }
   it.off_ytab = it.ytab_doubles ? ws.take(it.ytab_doubles) : 0;
-  // Staging area of the small-plane kernel (BF16 or TF32, n_1 and n_d <= 32,
-  // one width l <= 32): the rows of every test matrix that many planes share
-  // (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches with
-  // wdiv < W: wdiv keys x n_1 rows), rounded to the MMA type, lpad elements of
-  // 2 (BF16) or 4 (TF32) bytes per row.
+  // Staging area of the small-plane kernel (BF16, FP16 or TF32, n_1 and n_d <=
+  // 32, one width l <= 32): the rows of every test matrix that many planes
+  // share (column sketches with wdiv > 1: W/wdiv keys x n_d rows; row sketches
+  // with wdiv < W: wdiv keys x n_1 rows), rounded to the MMA type, lpad
+  // elements of 2 (BF16, FP16) or 4 (TF32) bytes per row.
   // A sketch whose table would exceed 512 MB is generated per plane instead.
   it.sptab_doubles = 0;
   {
-    bool ok = (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 && q.n[0] <= 32 &&
+    bool ok = (op16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 && q.n[0] <= 32 &&
               q.n[d - 1] <= 32;
     const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
     // sketch widths may differ (fixed ranks); the tables share the padding of
@@ -351,7 +357,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   // serves): each sketch adjoint split into kAdjParts terms of the MMA type,
   // row-major rows x lpad (lpad = 16 or 32 elements of 2 or 4 bytes).
   it.adjtab_doubles = 0;
-  if (single && it.sptab_doubles > 0 && !it.sided1 && !kr && q.passes == 1) {
+  if (single && it.sptab_doubles > 0 && !it.sided1 && !kr && q.passes == 1 && q.prec != TT_PREC_FP16) {
     int lmax = 0;
     for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) lmax = std::max(lmax, P.sketches[si].width);
     const int64_t lpad = lmax <= 16 ? 16 : 32, esz = q.prec == TT_PREC_TF32 ? 4 : 2;
@@ -376,7 +382,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   // column tiles of the plane share the fetch.
   it.gentab_doubles = 0;
   {
-    const bool ok = single && (q.prec == TT_PREC_BF16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 &&
+    const bool ok = single && (op16 || q.prec == TT_PREC_TF32) && q.x_dtype == TT_F32 &&
                     it.tctab_doubles == 0 && it.sptab_doubles == 0;
     const int64_t esz = q.prec == TT_PREC_TF32 ? 4 : 2;
     const int64_t tilesA = (q.n[0] + 63) / 64, tilesB = (q.n[d - 1] + 31) / 32;
@@ -956,6 +962,7 @@ tt_status tt_query_status(tt_plan_t plan, const void* ws, const int* ranks, int*
     if (word & ST_RANK_CAP) s = TT_WARN_RANK_CAP;
     if (word & ST_TIMEOUT) s = TT_ERR_TIMEOUT;
     if (word & ST_RANK_DEFICIENT) s = TT_ERR_RANK_DEFICIENT;
+    if (word & ST_NONFINITE) s = TT_ERR_NONFINITE;
     *status_host = s;
   }
   if (ranks_host) {
@@ -977,6 +984,7 @@ const char* tt_status_string(tt_status s) {
     case TT_ERR_TIMEOUT: return "device wait timed out";
     case TT_WARN_RANK_CAP: return "tolerance not met at rmax";
     case TT_ERR_NO_DEVICE: return "no CUDA device";
+    case TT_ERR_NONFINITE: return "non-finite sketch entry (X, or FP16 range)";
   }
   return "unknown status";
 }

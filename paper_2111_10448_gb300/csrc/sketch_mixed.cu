@@ -1,4 +1,4 @@
-// Mixed-precision (TF32 / BF16 tensor-core) sketch path and everything that
+// Mixed-precision (TF32 / BF16 / FP16 tensor-core) sketch path and everything that
 // must regenerate its test matrices bit-identically (the middle-core matrix
 // B = P^T Omega_{d*} of the one-pass solve, and the test-matrix export).
 // All of them use the FP32 generator of philox.cuh.
@@ -151,12 +151,21 @@ struct MixArgs {
   int64_t n1, cnt, first, W, Nd1;
   uint64_t seed;
   int nsk, prec;
+  float xscale;  // FP16: 2^s, X is split as X 2^s (1 otherwise)
   SkArgM sk[kMaxSk];
 };
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_f16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -212,7 +221,8 @@ __device__ __forceinline__ void g_ldsm_x2_trans(const void* p, uint32_t r[2]) {
                : "r"(g_smem_u32(p)));
 }
 
-// BF16 operand tiles (in the same dynamic shared memory as the FP32 ones):
+// 16-bit operand tiles, BF16 or FP16 (in the same dynamic shared memory as
+// the FP32 ones):
 // X hi / lo as [b][a] (a contiguous) and the test-matrix rows as [k][j] (j
 // contiguous), rows of 72 elements (144 bytes: the eight row addresses of an
 // ldmatrix fall on distinct banks).  The MMA fragments come from ldmatrix:
@@ -227,10 +237,11 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
   float* Xh = fsm;                  // LDX x gTB  (X[a + LDX b])        (TF32)
   float* Xl = Xh + LDX * gTB;
   float* Gs = Xl + LDX * gTB;       // rows (<= gTA) x LDG              (TF32)
-  __nv_bfloat16* XhB = reinterpret_cast<__nv_bfloat16*>(fsm);   // gTB x gLDX (BF16)
-  __nv_bfloat16* XlB = XhB + gLDX * gTB;
-  __nv_bfloat16* GsB = XlB + gLDX * gTB;                        // gTA x gLDG (BF16)
-  const bool bf = a.prec == TT_PREC_BF16;
+  uint16_t* XhB = reinterpret_cast<uint16_t*>(fsm);   // gTB x gLDX (16-bit)
+  uint16_t* XlB = XhB + gLDX * gTB;
+  uint16_t* GsB = XlB + gLDX * gTB;                   // gTA x gLDG (16-bit)
+  const bool f16 = a.prec == TT_PREC_FP16;
+  const bool bf = a.prec == TT_PREC_BF16 || f16;      // 16-bit operands (m16n8k16)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nA = (a.n1 + gTA - 1) / gTA;
   const int64_t nB = (a.cnt + gTB - 1) / gTB;
@@ -245,12 +256,12 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
     for (int o = tid; o < gTA * gTB; o += gThreads) {
       const int ia = o % gTA, ib = o / gTA;
       float v = 0.0f;
-      if (ia < ta && ib < tb) v = __ldg(a.X + (a0 + ia) + a.n1 * w + a.Nd1 * (b0 + ib));
+      if (ia < ta && ib < tb) v = __fmul_rn(__ldg(a.X + (a0 + ia) + a.n1 * w + a.Nd1 * (b0 + ib)), a.xscale);
       const float hi = round_prec(v, a.prec);
       const float lo = round_prec(__fsub_rn(v, hi), a.prec);
-      if (bf) {
-        XhB[ib * gLDX + ia] = __float2bfloat16_rn(hi);  // exact: hi, lo are BF16 values
-        XlB[ib * gLDX + ia] = __float2bfloat16_rn(lo);
+      if (bf) {  // exact: hi, lo are values of the 16-bit type
+        XhB[ib * gLDX + ia] = f16 ? tc::op16_bits<true>(hi) : tc::op16_bits<false>(hi);
+        XlB[ib * gLDX + ia] = f16 ? tc::op16_bits<true>(lo) : tc::op16_bits<false>(lo);
       } else {
         Xh[ia + LDX * ib] = hi;
         Xl[ia + LDX * ib] = lo;
@@ -297,9 +308,9 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
             float zz[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
-            __nv_bfloat162* gp = reinterpret_cast<__nv_bfloat162*>(GsB + r * gLDG + 4 * q);
-            gp[0] = __floats2bfloat162_rn(zz[0], zz[1]);
-            gp[1] = __floats2bfloat162_rn(zz[2], zz[3]);
+            uint32_t* gp = reinterpret_cast<uint32_t*>(GsB + r * gLDG + 4 * q);
+            gp[0] = f16 ? tc::f16x2_bits(zz[0], zz[1]) : tc::bf16x2_bits(zz[0], zz[1]);
+            gp[1] = f16 ? tc::f16x2_bits(zz[2], zz[3]) : tc::bf16x2_bits(zz[2], zz[3]);
           } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
@@ -330,8 +341,13 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
               g_ldsm_x2(XhB + off, bh);
               g_ldsm_x2(XlB + off, bl);
             }
-            mma_bf16(acc, af, bh[0], bh[1]);
-            mma_bf16(acc, af, bl[0], bl[1]);
+            if (f16) {
+              mma_f16(acc, af, bh[0], bh[1]);
+              mma_f16(acc, af, bl[0], bl[1]);
+            } else {
+              mma_bf16(acc, af, bh[0], bh[1]);
+              mma_bf16(acc, af, bl[0], bl[1]);
+            }
           }
         } else {
           if (col) tile_mma_tf32<true>(Gs, LDG, Xh, Xl, LDX, nr, kext, m0, n0, acc);
@@ -421,6 +437,7 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const Batc
           sa.seed = it.seed;
           sa.nsk = it.nsk;
           sa.prec = it.prec;
+          sa.xscale = it.prec == TT_PREC_FP16 ? it.xscale : 1.0f;
           for (int s = 0; s < it.nsk; ++s) {
             const DevSketch& d = sks[it.sk0 + s];
             sa.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, -1};
@@ -494,6 +511,8 @@ struct TcArgs {
   int64_t runL;  // tiles of one kL block accumulated in the L slots before a flush
   int genL[4], genR[4], ngenL, ngenR;  // sketches whose blocks the RNG warps generate
   uint32_t tab_tx;                     // bytes of staged blocks copied per plane
+  float xscale;                        // FP16 operands: 2^s, X is split as X 2^s (1 with BF16)
+  int f16;                             // FP16 operands (else BF16), for the table kernel
   SkTc col[4], row[4];
 };
 
@@ -553,7 +572,7 @@ __device__ __forceinline__ int64_t row_key(const TcArgs& g, const SkTc& sk, int6
   return w % sk.wdiv;
 }
 
-template <int ELL>
+template <int ELL, bool F16>
 __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -652,6 +671,11 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
       prefetch_l2(line + g.Nd1 * (int64_t)(16 * (2 * c + 1)));
     };
     float4 v[16];
+    const float xs = g.xscale;
+    auto sx = [&](float f) -> float {
+      if constexpr (F16) return __fmul_rn(f, xs);
+      else return f;
+    };
     auto issue = [&](const float* src) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
@@ -679,15 +703,11 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
         const int i4 = rsub + 16 * m;
-        const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
-                            v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
+        const float x[8] = {sx(v[2 * m].x),     sx(v[2 * m].y),     sx(v[2 * m].z),     sx(v[2 * m].w),
+                            sx(v[2 * m + 1].x), sx(v[2 * m + 1].y), sx(v[2 * m + 1].z), sx(v[2 * m + 1].w)};
         uint32_t hb[4], lb[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
-          const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
-          lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
-        }
+        for (int e = 0; e < 4; ++e) split_hi_lo<F16>(x[2 * e], x[2 * e + 1], hb[e], lb[e]);
         const uint32_t off = cb1 * kS1 + (i4 >> 3) * kS4 + (i4 & 7) * 16;
         st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
         st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
@@ -787,10 +807,10 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
               const float4 rb = tm_quad_f32(g.ws, bs.kr, g.seed, bs.sid, (uint64_t)(row + bs.rstep), (uint32_t)nq);
               const int n0 = bs.n0 + 4 * nq;  // a multiple of 4: one core matrix holds n0 .. n0 + 3
               const uint32_t dst = bs.dst0 + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
-              st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
-              st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
-              st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
-              st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+              st_shared_b32(dst, op16x2_bits<F16>(ra.x, rb.x));
+              st_shared_b32(dst + 16, op16x2_bits<F16>(ra.y, rb.y));
+              st_shared_b32(dst + 32, op16x2_bits<F16>(ra.z, rb.z));
+              st_shared_b32(dst + 48, op16x2_bits<F16>(ra.w, rb.w));
               if (++nq == qps) {
                 nq = 0;
                 if (++rp == 64) {
@@ -819,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
     // ------------------------------------------------------------ MMA issue
     // Every lane runs the schedule and waits; the elected lane issues the
     // MMAs and commits (the same lane each time: the warp is converged).
-    const uint32_t idL = make_idesc(g.NL, true), idR = make_idesc(g.NR, false);
+    const uint32_t idL = make_idesc(g.NL, true, F16), idR = make_idesc(g.NR, false, F16);
     const uint32_t colR0 = (uint32_t)(g.T2 * g.H1 * g.NL);
     const uint32_t colRB = (uint32_t)(g.T3 * g.H4 * g.NR);  // one R buffer
     uint32_t qi = 0, pi = 0, lf = 0, ti = 0;
@@ -877,9 +897,9 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                   const uint64_t po = (uint64_t)((part * kTileB) >> 4);
-                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                  mma16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4),
                               idL, accL0 | (uint32_t)(ks | part));
-                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                  mma16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4),
                               idR, accR0 | (uint32_t)(ks | part));
                 }
               }
@@ -1020,8 +1040,8 @@ __global__ void __launch_bounds__(kThreads, 1) sketch_tc_kernel(const TcArgs g) 
 
 // Staged test-matrix blocks of sketch (side, s): block (v, h), h < H, holds the
 // 128 rows v + hstride (first + 128 h + k) (column side) or 128 h + k + n1 v
-// (row side), k = 0..127, as the BF16 K-major core-matrix image the MMA reads
-// (the same layout and rounding the RNG warps produce).
+// (row side), k = 0..127, as the K-major core-matrix image the MMA reads (BF16
+// or FP16: the same layout and rounding the RNG warps produce).
 __global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, int H) {
   const SkTc sk = colside ? g.col[s] : g.row[s];
   const int qps = g.ell / 4;
@@ -1046,8 +1066,8 @@ __global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = 4 * q + u;
-      *reinterpret_cast<__nv_bfloat16*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
-          __float2bfloat16_rn(zz[u]);
+      *reinterpret_cast<uint16_t*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          g.f16 ? op16_bits<true>(zz[u]) : op16_bits<false>(zz[u]);
     }
   }
 }
@@ -1055,7 +1075,7 @@ __global__ void tc_table_kernel(const TcArgs g, int colside, int s, int64_t nv, 
 // Shape rules of the plane kernel; fills the launch arguments when it applies.
 bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   const DevItem& it = plan_items_host(&P)[item];
-  if (it.prec != TT_PREC_BF16 || it.x_f64) return false;
+  if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_FP16) || it.x_f64) return false;
   // Khatri-Rao plans go to the slab kernel (the mode-by-mode last row sketch
   // needs a per-plane scale that this kernel's accumulators cannot take)
   if (plan_sketches_host(&P)[it.sk0].kr_nm) return false;
@@ -1146,6 +1166,8 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   g.NL = NL;
   g.NR = NR;
   g.seed = it.seed;
+  g.f16 = it.prec == TT_PREC_FP16 ? 1 : 0;
+  g.xscale = g.f16 ? it.xscale : 1.0f;
   *out = g;
   return true;
 }
@@ -1305,7 +1327,7 @@ cudaError_t launch_sketch_adjoint(const Plan& P, int item, void* dX, void* ws, c
 
 bool mixed_tc_supported(const Plan& P, int item, int64_t) {
   const DevItem& it = plan_items_host(&P)[item];
-  return it.prec == TT_PREC_TF32 || it.prec == TT_PREC_BF16;
+  return it.prec == TT_PREC_TF32 || it.prec == TT_PREC_BF16 || it.prec == TT_PREC_FP16;
 }
 
 cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t first, int64_t count,
@@ -1323,6 +1345,7 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   a.seed = it.seed;
   a.nsk = it.nsk;
   a.prec = it.prec;
+  a.xscale = it.prec == TT_PREC_FP16 ? it.xscale : 1.0f;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
     a.sk[s] = SkArgM{d.rows, d.off, d.wdiv, d.hstride, -1, d.type, d.width, d.stream_id, d.kr_nm ? it.sk0 + s : -1};
@@ -1334,7 +1357,7 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
       cudaError_t e = launch_rows_table(d, it.sk0 + s, (const char*)ws, it.seed, first, a.n1,
                                         col ? (int)count : (int)a.n1, lpad,
                                         col ? it.W / d.wdiv : d.wdiv, (char*)ws + a.sk[s].tab,
-                                        it.prec == TT_PREC_TF32, st);
+                                        it.prec, st);
       if (e != cudaSuccess) return e;
     }
   }
@@ -1379,8 +1402,9 @@ static bool tc_kernel_launchable() {
   if (ok < 0) {
     cudaFuncAttributes fa, fb;
     int dev = 0, smem_optin = 0;
-    ok = cudaFuncGetAttributes(&fa, tc::sketch_tc_kernel<16>) == cudaSuccess &&
-         cudaFuncGetAttributes(&fb, tc::sketch_tc_kernel<8>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+    ok = cudaFuncGetAttributes(&fa, tc::sketch_tc_kernel<16, false>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fb, tc::sketch_tc_kernel<8, false>) == cudaSuccess &&
+         cudaGetDevice(&dev) == cudaSuccess &&
          fb.maxThreadsPerBlock >= tc::kThreads &&
          cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
          fa.maxThreadsPerBlock >= tc::kThreads && smem_optin >= tc::kSmemBytes;
@@ -1396,13 +1420,17 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
   g.ws = (double*)ws;
   g.status = reinterpret_cast<int*>((char*)ws + kStatusOff);
   g.first = first;
+  using KernelFn = void (*)(tc::TcArgs);
+  const KernelFn kernels[2][2] = {{tc::sketch_tc_kernel<8, false>, tc::sketch_tc_kernel<16, false>},
+                                  {tc::sketch_tc_kernel<8, true>, tc::sketch_tc_kernel<16, true>}};
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc::sketch_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::kSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc::sketch_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
-    if (e != cudaSuccess) return e;
+    for (int f = 0; f < 2; ++f)
+      for (int i = 0; i < 2; ++i) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kernels[f][i], cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+        if (e != cudaSuccess) return e;
+      }
     attr_set = true;
   }
   if (!tc_kernel_launchable()) return launch_sketch_mma(P, item, X, first, count, ws, st);
@@ -1423,8 +1451,7 @@ cudaError_t launch_sketch_tc(const Plan& P, int item, const void* X, int64_t fir
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
-  if (g.ell == 16) tc::sketch_tc_kernel<16><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
-  else tc::sketch_tc_kernel<8><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
+  kernels[g.f16][g.ell == 16 ? 1 : 0]<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 // Slab form of the tcgen05 plane kernel: the fused multi-sketch of one slab of
 // c = 16, 32 or 64 slices of the last mode of a 4-way tensor -- the unit of
 // the paper's single stream over sub-tensors (Sec. 4.2, Algorithm 5; a 1 GiB
-// slab of the 256^4 FP32 tensor is 16 slices).  BF16 with X split into hi +
-// lo, FP32 accumulators in tensor memory, FP64 flush, as the plane kernel.
+// slab of the 256^4 FP32 tensor is 16 slices).  BF16 or FP16 (X scaled by
+// 2^s first) with X split into hi + lo, FP32 accumulators in tensor memory,
+// FP64 flush, as the plane kernel.
 //
 // The plane kernel contracts a plane X(:, w, :) (n_1 x slab) over its 128-row
 // quarters of i_4; a slab of 16 slices has no such quarter.  Here G = 128 / c
@@ -42,7 +43,7 @@
 // s2_fold_kernel after the launch.
 //
 // Warp roles: 4 epilogue warps (the TMEM lane quarters), 1 MMA issuer, 8
-// producers (X loads, hi / lo split into the BF16 operand stages), and 7
+// producers (X loads, hi / lo split into the 16-bit operand stages), and 7
 // (dense) or 3 (Khatri-Rao) test-matrix warps.  Every mbarrier wait is
 // bounded; a wait that gives up raises the CTA's abort flag and the timeout
 // status bit, waits for its own copies and MMAs, frees TMEM and returns.
@@ -87,7 +88,6 @@ constexpr int kOffF4 = kOffY + 2 * kRBlkB;
 static_assert(2 * kRBlkB + 2 * 64 * 16 * 4 <= kYBlkB, "Khatri-Rao blocks in the R_3 area");
 constexpr int kSmemBytes = kOffBar + 256 + 1024;
 constexpr int kTmemY = 0;         // D_Y buffers at columns 0 and 128, then the L slots, then R_2
-constexpr int64_t kTableOffB = 256;
 
 struct SlabArgs {
   const float* X;
@@ -104,6 +104,8 @@ struct SlabArgs {
   uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
   float* s2stage;          // FP32 staging of S_2 (same layout), added into S_2 after the launch
   int64_t ytab;            // dense: byte offset of the staged R_3 blocks (-1: regenerated per quarter)
+  float xscale;            // FP16 operands: 2^s, X is split as X 2^s (1 with BF16)
+  int f16;                 // FP16 operands (else BF16), for the table kernels
   SkTc col[2], row[2];     // S_1, S_2 | R_2, R_3
 };
 
@@ -145,7 +147,7 @@ __device__ __forceinline__ bool next_super_plane(const SlabArgs& g, int64_t ntil
   return true;
 }
 
-template <int ELL, int C, bool KRY>
+template <int ELL, int C, bool KRY, bool F16>
 __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(const SlabArgs g) {
   constexpr int kRngWarps = Roles<KRY>::rng;
   constexpr int kThreads = Roles<KRY>::threads;
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
                       kr3->kr_off[0];
     for (int e = threadIdx.x; e < g.H1 * 128 * ell; e += kThreads) {
       const int j = e % ell, i1 = e / ell, h1 = i1 >> 7, k = i1 & 127;
-      *reinterpret_cast<__nv_bfloat16*>(sm + kOffY + h1 * kRBlkB + (k >> 3) * kS1 + (j >> 3) * kS4 + (j & 7) * 16 +
-                                        (k & 7) * 2) = __float2bfloat16_rn(f1[(int64_t)i1 * kr3->kr_lp + j]);
+      *reinterpret_cast<uint16_t*>(sm + kOffY + h1 * kRBlkB + (k >> 3) * kS1 + (j >> 3) * kS4 + (j & 7) * 16 +
+                                   (k & 7) * 2) = op16_bits<F16>(f1[(int64_t)i1 * kr3->kr_lp + j]);
     }
     // the mode-4 rows of the slab's slices for S_1 (its mode-4 factor is its
     // third) and S_2 (its second)
@@ -275,6 +277,11 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       prefetch_l2(line + rowoff(2 * cc + 1));
     };
     float4 v[16];
+    const float xs = g.xscale;
+    auto sx = [&](float f) -> float {
+      if constexpr (F16) return __fmul_rn(f, xs);
+      else return f;
+    };
     auto issue = [&](const float* src) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
@@ -298,15 +305,11 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
         const int k = rsub + 16 * m;
-        const float x[8] = {v[2 * m].x, v[2 * m].y, v[2 * m].z, v[2 * m].w,
-                            v[2 * m + 1].x, v[2 * m + 1].y, v[2 * m + 1].z, v[2 * m + 1].w};
+        const float x[8] = {sx(v[2 * m].x),     sx(v[2 * m].y),     sx(v[2 * m].z),     sx(v[2 * m].w),
+                            sx(v[2 * m + 1].x), sx(v[2 * m + 1].y), sx(v[2 * m + 1].z), sx(v[2 * m + 1].w)};
         uint32_t hb[4], lb[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hb[e] = bf16x2_bits(x[2 * e], x[2 * e + 1]);
-          const float h0 = __uint_as_float(hb[e] << 16), h1v = __uint_as_float(hb[e] & 0xFFFF0000u);
-          lb[e] = bf16x2_bits(__fsub_rn(x[2 * e], h0), __fsub_rn(x[2 * e + 1], h1v));
-        }
+        for (int e = 0; e < 4; ++e) split_hi_lo<F16>(x[2 * e], x[2 * e + 1], hb[e], lb[e]);
         const uint32_t off = cb1 * kS1 + (k >> 3) * kS4 + (k & 7) * 16;
         st_shared_v4(tileA + off, hb[0], hb[1], hb[2], hb[3]);
         st_shared_v4(tileA + kTileB + off, lb[0], lb[1], lb[2], lb[3]);
@@ -414,10 +417,10 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
           auto store_pair = [&](int bi, int k, const float4& ra, const float4& rb) {
             const int n0 = bi * ell + 4 * kq;
             const uint32_t dst = sL + buf * kLBlkB + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
-            st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
-            st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
-            st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
-            st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+            st_shared_b32(dst, op16x2_bits<F16>(ra.x, rb.x));
+            st_shared_b32(dst + 16, op16x2_bits<F16>(ra.y, rb.y));
+            st_shared_b32(dst + 32, op16x2_bits<F16>(ra.z, rb.z));
+            st_shared_b32(dst + 48, op16x2_bits<F16>(ra.w, rb.w));
           };
           auto mul4 = [](const float4& x, const float4& y) {
             return make_float4(__fmul_rn(x.x, y.x), __fmul_rn(x.y, y.y), __fmul_rn(x.z, y.z), __fmul_rn(x.w, y.w));
@@ -470,10 +473,10 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
             }
             const int n0 = bi * ell + 4 * nq;
             const uint32_t dst = sL + buf * kLBlkB + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
-            st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
-            st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
-            st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
-            st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+            st_shared_b32(dst, op16x2_bits<F16>(ra.x, rb.x));
+            st_shared_b32(dst + 16, op16x2_bits<F16>(ra.y, rb.y));
+            st_shared_b32(dst + 32, op16x2_bits<F16>(ra.z, rb.z));
+            st_shared_b32(dst + 48, op16x2_bits<F16>(ra.w, rb.w));
           }
           fence_async_smem();
           __syncwarp();
@@ -531,10 +534,10 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
                 const int k = kk2[h], n0 = nn2[h];
                 const float4 ra = z[h][0], rb = z[h][1];
                 const uint32_t dst = sY + (k >> 3) * kS1 + (n0 >> 3) * kS4 + (n0 & 7) * 16 + (k & 7) * 2;
-                st_shared_b32(dst, bf16x2_bits(ra.x, rb.x));
-                st_shared_b32(dst + 16, bf16x2_bits(ra.y, rb.y));
-                st_shared_b32(dst + 32, bf16x2_bits(ra.z, rb.z));
-                st_shared_b32(dst + 48, bf16x2_bits(ra.w, rb.w));
+                st_shared_b32(dst, op16x2_bits<F16>(ra.x, rb.x));
+                st_shared_b32(dst + 16, op16x2_bits<F16>(ra.y, rb.y));
+                st_shared_b32(dst + 32, op16x2_bits<F16>(ra.z, rb.z));
+                st_shared_b32(dst + 48, op16x2_bits<F16>(ra.w, rb.w));
               }
             }
             fence_async_smem();
@@ -558,8 +561,8 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
-    const uint32_t idL = make_idesc(NL, true), idR = make_idesc(ell, false),
-                   idY = make_idesc(KRY ? ell : g.G * ell, false);
+    const uint32_t idL = make_idesc(NL, true, F16), idR = make_idesc(ell, false, F16),
+                   idY = make_idesc(KRY ? ell : g.G * ell, false, F16);
     const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     uint32_t qi = 0, pi = 0, lf = 0, ti_n = 0;
     int64_t cur_tl = -1;
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                   const uint64_t po = (uint64_t)((part * kTileB) >> 4);
-                  mma_bf16_ss(dYq, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bY0 + (uint64_t)((ks * 2 * kS1) >> 4),
+                  mma16_ss(dYq, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bY0 + (uint64_t)((ks * 2 * kS1) >> 4),
                               idY, accY0 | (uint32_t)(ks | part));
                 }
               if (!KRY) mma_commit(bar(EMPTY_Y));
@@ -635,9 +638,9 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                   const uint64_t po = (uint64_t)((part * kTileB) >> 4);
-                  mma_bf16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4), idL,
+                  mma16_ss(dL, aL0 + po + (uint64_t)((ks * 2 * kS4) >> 4), bL0 + (uint64_t)((ks * 2 * kS1) >> 4), idL,
                               accL0 | (uint32_t)(ks | part));
-                  mma_bf16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4), idR,
+                  mma16_ss(dR, aR0 + po + (uint64_t)((ks * 2 * kS1) >> 4), bR0 + (uint64_t)((ks * 2 * kS1) >> 4), idR,
                               accR0 | (uint32_t)(ks | part));
                 }
               mma_commit(bar(EMPTY_A + st));
@@ -786,13 +789,15 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
             const uint32_t yb = spn & 1;
             // the plane's rows of the mode-3 and mode-2 factors (i_3 = kR_g,
             // i_2 = kL, loaded during the previous super-plane); product in the
-            // row sketch's decreasing mode order, rounded to BF16 (the column
-            // scale); then the next super-plane's rows go out
+            // row sketch's decreasing mode order, rounded to the operand type
+            // (the column scale); then the next super-plane's rows go out
             float4 sc[ell / 4];
 #pragma unroll
             for (int q = 0; q < ell / 4; ++q)
-              sc[q] = make_float4(round_bf16(__fmul_rn(ef3[q].x, ef2[q].x)), round_bf16(__fmul_rn(ef3[q].y, ef2[q].y)),
-                                  round_bf16(__fmul_rn(ef3[q].z, ef2[q].z)), round_bf16(__fmul_rn(ef3[q].w, ef2[q].w)));
+              sc[q] = make_float4(round_op16<F16>(__fmul_rn(ef3[q].x, ef2[q].x)),
+                                  round_op16<F16>(__fmul_rn(ef3[q].y, ef2[q].y)),
+                                  round_op16<F16>(__fmul_rn(ef3[q].z, ef2[q].z)),
+                                  round_op16<F16>(__fmul_rn(ef3[q].w, ef2[q].w)));
             {
               int64_t kLn, kR0n;
               if (next_super_plane(g, ntiles, t, a, b, tinf, kLn, kR0n)) e_load(kLn, kR0n);
@@ -875,8 +880,8 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
 }
 
 // Staged R_3 blocks (dense test matrices): block (h, kL, kR) holds the 128
-// rows 128 h + k + n_1 (kL + WL kR) of Psi_3 as the BF16 K-major
-// core-matrix image the MMA reads, kR fastest.
+// rows 128 h + k + n_1 (kL + WL kR) of Psi_3 as the K-major core-matrix
+// image the MMA reads (BF16 or FP16), kR fastest.
 __global__ void slab_ytab_kernel(const SlabArgs g) {
   const SkTc sk = g.row[1];
   const int qps = g.ell / 4;
@@ -900,8 +905,8 @@ __global__ void slab_ytab_kernel(const SlabArgs g) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = 4 * q + u;
-      *reinterpret_cast<__nv_bfloat16*>(bp + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
-          __float2bfloat16_rn(zz[u]);
+      *reinterpret_cast<uint16_t*>(bp + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          g.f16 ? op16_bits<true>(zz[u]) : op16_bits<false>(zz[u]);
     }
   }
 }
@@ -926,7 +931,8 @@ __global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stag
 }
 
 // Staged R_2 blocks: block (v, h) holds the 128 rows 128 h + k + n_1 v of the
-// test matrix (v = kL) as the BF16 K-major core-matrix image the MMA reads.
+// test matrix (v = kL) as the K-major core-matrix image the MMA reads (BF16
+// or FP16).
 __global__ void slab_table_kernel(const SlabArgs g, int64_t nv) {
   const SkTc sk = g.row[0];
   const int qps = g.ell / 4;
@@ -950,8 +956,8 @@ __global__ void slab_table_kernel(const SlabArgs g, int64_t nv) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int j = 4 * q + u;
-      *reinterpret_cast<__nv_bfloat16*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
-          __float2bfloat16_rn(zz[u]);
+      *reinterpret_cast<uint16_t*>(blk + kg * kS1 + (j >> 3) * kS4 + (j & 7) * 16 + r8 * 2) =
+          g.f16 ? op16_bits<true>(zz[u]) : op16_bits<false>(zz[u]);
     }
   }
 }
@@ -961,7 +967,7 @@ __global__ void slab_table_kernel(const SlabArgs g, int64_t nv) {
 // Shape rules of the slab kernel; fills the launch arguments when it applies.
 bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   const DevItem& it = plan_items_host(&P)[item];
-  if (it.prec != TT_PREC_BF16 || it.x_f64 || it.sided1 || it.passes != 1) return false;
+  if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_FP16) || it.x_f64 || it.sided1 || it.passes != 1) return false;
   if (it.d != 4 || it.nsk != 4) return false;
   if (it.n[0] != 128 && it.n[0] != 256) return false;
   if (count != 16 && count != 32 && count != 64) return false;
@@ -1035,6 +1041,8 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   g.row[0].tab = it.off_tctab * 8;
   g.tab_tx = (uint32_t)(g.H1 * blk);
   g.seed = it.seed;
+  g.f16 = it.prec == TT_PREC_FP16 ? 1 : 0;
+  g.xscale = g.f16 ? it.xscale : 1.0f;
   *out = g;
   return true;
 }
@@ -1044,8 +1052,9 @@ static bool slab_kernel_launchable() {
   if (ok < 0) {
     cudaFuncAttributes fa, fb;
     int dev = 0, smem_optin = 0;
-    ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16, false>) == cudaSuccess &&
-         cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16, true>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+    ok = cudaFuncGetAttributes(&fa, slab::sketch_slab_kernel<16, 16, false, false>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fb, slab::sketch_slab_kernel<8, 16, true, false>) == cudaSuccess &&
+         cudaGetDevice(&dev) == cudaSuccess &&
          fa.maxThreadsPerBlock >= slab::Roles<false>::threads && fb.maxThreadsPerBlock >= slab::Roles<true>::threads &&
          cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
          smem_optin >= slab::kSmemBytes;
@@ -1098,20 +1107,22 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   g.ytab = (!g.kry && it.ytab_doubles > 0) ? it.off_ytab * 8 : -1;
   using KernelFn = void (*)(tc::slab::SlabArgs);
   using namespace tc::slab;
-  const KernelFn kernels[2][2][3] = {
-      {{sketch_slab_kernel<8, 16, false>, sketch_slab_kernel<8, 32, false>, sketch_slab_kernel<8, 64, false>},
-       {sketch_slab_kernel<8, 16, true>, sketch_slab_kernel<8, 32, true>, sketch_slab_kernel<8, 64, true>}},
-      {{sketch_slab_kernel<16, 16, false>, sketch_slab_kernel<16, 32, false>, sketch_slab_kernel<16, 64, false>},
-       {sketch_slab_kernel<16, 16, true>, sketch_slab_kernel<16, 32, true>, sketch_slab_kernel<16, 64, true>}}};
+#define TT_SLAB_K(E, F)                                                                                        \
+  {{sketch_slab_kernel<E, 16, false, F>, sketch_slab_kernel<E, 32, false, F>, sketch_slab_kernel<E, 64, false, F>}, \
+   {sketch_slab_kernel<E, 16, true, F>, sketch_slab_kernel<E, 32, true, F>, sketch_slab_kernel<E, 64, true, F>}}
+  const KernelFn kernels[2][2][2][3] = {{TT_SLAB_K(8, false), TT_SLAB_K(16, false)},
+                                        {TT_SLAB_K(8, true), TT_SLAB_K(16, true)}};
+#undef TT_SLAB_K
   static bool attr_set = false;
   if (!attr_set) {
-    for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 2; ++k)
-        for (int j = 0; j < 3; ++j) {
-          const cudaError_t e =
-              cudaFuncSetAttribute(kernels[i][k][j], cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-          if (e != cudaSuccess) return e;
-        }
+    for (int f = 0; f < 2; ++f)
+      for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 2; ++k)
+          for (int j = 0; j < 3; ++j) {
+            const cudaError_t e = cudaFuncSetAttribute(kernels[f][i][k][j],
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+            if (e != cudaSuccess) return e;
+          }
     attr_set = true;
   }
   // the R_2 blocks (rows i_1 + n_1 kL) are the same for every slab: staged by
@@ -1132,7 +1143,7 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   const int64_t ntiles = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(ntiles, device_sm_count());
   count_launch();
-  const KernelFn k = kernels[g.ell == 16 ? 1 : 0][g.kry][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
+  const KernelFn k = kernels[g.f16][g.ell == 16 ? 1 : 0][g.kry][g.c == 16 ? 0 : g.c == 32 ? 1 : 2];
   const int threads = g.kry ? tc::slab::Roles<true>::threads : tc::slab::Roles<false>::threads;
   k<<<grid, threads, tc::slab::kSmemBytes, st>>>(g);
   cudaError_t e = cudaGetLastError();

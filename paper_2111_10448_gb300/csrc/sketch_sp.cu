@@ -1,4 +1,5 @@
-// Small-plane fused multi-sketch (BF16 tensor cores, X split into hi + lo)
+// Small-plane fused multi-sketch (BF16, FP16 or TF32 tensor cores, X split
+// into hi + lo; the description below uses BF16)
 // for tensors whose first and last modes are small (n_1, n_d <= 32), e.g. the
 // d = 6, n = 24 random-TT workload and the many small tensors of a batch.
 //
@@ -53,11 +54,17 @@ constexpr int kBlockPlanes = 16;  // planes per block: T2 values of kL x T3 valu
 constexpr int kLD = 40;           // element row stride of the 32-row tiles
 constexpr int kTileElems = 32 * kLD;
 constexpr int kColFlushBlocks = 16;
-// Per precision: BF16 tiles (80-byte rows) leave room for 16 warps, one plane
-// each per block; TF32 tiles hold FP32 words (160-byte rows), 8 warps, two
-// planes each per block.
-template <bool TF>
+// Operand formats of a kernel instance (template argument FMT).
+constexpr int kFmtBF16 = 0, kFmtTF32 = 1, kFmtFP16 = 2;
+__host__ __device__ constexpr int fmt_of(int prec) {
+  return prec == TT_PREC_TF32 ? kFmtTF32 : prec == TT_PREC_FP16 ? kFmtFP16 : kFmtBF16;
+}
+// Per precision: BF16 / FP16 tiles (80-byte rows) leave room for 16 warps, one
+// plane each per block; TF32 tiles hold FP32 words (160-byte rows), 8 warps,
+// two planes each per block.
+template <int FMT>
 struct Prec {
+  static constexpr bool TF = FMT == kFmtTF32;
   static constexpr int kWarps = TF ? 8 : 16;
   static constexpr int kThreads = kWarps * 32;
   static constexpr int kEsz = TF ? 4 : 2;
@@ -81,6 +88,7 @@ struct SpArgs {
   int64_t n1, cnt, first, W, WL, WR, Nd1, tilesL, tilesR, tab0;
   int nsk, ell, nq, nslots, ldo;  // ell: the largest sketch width (sets the padding), nq its column quads
   int T2, T3;  // block shape
+  float xscale;  // FP16: 2^s, X is split as X 2^s (1 otherwise)
   SpSk sk[kMaxSk];
 };
 
@@ -116,6 +124,13 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
+__device__ __forceinline__ void mma_f16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
 __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -127,14 +142,23 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
+__device__ __forceinline__ uint32_t f16x2(float lo, float hi) {
+  __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t op16x2(bool f16, float lo, float hi) {
+  return f16 ? f16x2(lo, hi) : bf16x2(lo, hi);
+}
 
 // Staged test-matrix rows of one sketch: entry (key, r, j), r < nr, j < lpad,
 // at element (key nr + r) lpad + j of `tab`: the normal of row key + hstride
-// (first + r) (column side) or r + n1 key (row side) rounded to BF16 (2-byte
-// elements) or TF32 (`tf`: 4-byte FP32 words), zero for j >= l.  Threads
-// tid0, tid0 + nthr, ... of the caller take the entries.
+// (first + r) (column side) or r + n1 key (row side) rounded to the operand
+// type of precision `prec`: BF16 or FP16 (2-byte elements) or TF32 (4-byte
+// FP32 words), zero for j >= l.  Threads tid0, tid0 + nthr, ... of the caller
+// take the entries.
 __device__ void sp_table_fill(const char* wsb, const SpSk& s, uint64_t seed, int64_t first, int64_t n1, int nr,
-                              int ell, int lpad, int64_t nkeys, char* tab, int64_t tid0, int64_t nthr, bool tf) {
+                              int ell, int lpad, int64_t nkeys, char* tab, int64_t tid0, int64_t nthr, int prec) {
+  const bool tf = prec == TT_PREC_TF32, f16 = prec == TT_PREC_FP16;
   const DevSketch* kr = kr_of(wsb, s.kr);
   const int qpr = lpad / 4;
   const int64_t total = nkeys * nr * qpr;
@@ -152,17 +176,17 @@ __device__ void sp_table_fill(const char* wsb, const SpSk& s, uint64_t seed, int
           make_float4(4 * q < ell ? round_tf32(z.x) : 0.f, 4 * q + 1 < ell ? round_tf32(z.y) : 0.f,
                       4 * q + 2 < ell ? round_tf32(z.z) : 0.f, 4 * q + 3 < ell ? round_tf32(z.w) : 0.f);
     } else {
-      const uint32_t lo = bf16x2(4 * q < ell ? z.x : 0.f, 4 * q + 1 < ell ? z.y : 0.f);
-      const uint32_t hi = bf16x2(4 * q + 2 < ell ? z.z : 0.f, 4 * q + 3 < ell ? z.w : 0.f);
+      const uint32_t lo = op16x2(f16, 4 * q < ell ? z.x : 0.f, 4 * q + 1 < ell ? z.y : 0.f);
+      const uint32_t hi = op16x2(f16, 4 * q + 2 < ell ? z.z : 0.f, 4 * q + 3 < ell ? z.w : 0.f);
       *reinterpret_cast<uint2*>(tab + el * 2) = make_uint2(lo, hi);
     }
   }
 }
 
 __global__ void sp_table_kernel(const char* wsb, SpSk s, uint64_t seed, int64_t first, int64_t n1, int nr, int ell,
-                                int lpad, int64_t nkeys, char* tab, int tf) {
+                                int lpad, int64_t nkeys, char* tab, int prec) {
   sp_table_fill(wsb, s, seed, first, n1, nr, ell, lpad, nkeys, tab,
-                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, tf != 0);
+                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, prec);
 }
 
 // Launch arguments of one item (the whole last mode when count = n_d), shared
@@ -180,6 +204,7 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
   g.tilesR = (g.WR + g.T3 - 1) / g.T3;
   g.tab0 = it.off_sptab * 8;
   g.seed = it.seed;
+  g.xscale = it.prec == TT_PREC_FP16 ? it.xscale : 1.0f;
   g.nsk = it.nsk;
   g.ell = 0;
   for (int s = 0; s < it.nsk; ++s) g.ell = sks[it.sk0 + s].width > g.ell ? sks[it.sk0 + s].width : g.ell;
@@ -214,9 +239,9 @@ __host__ __device__ inline void sp_fill(const DevItem& it, const DevSketch* sks,
 
 // Adds the slots of one flush class into the FP64 sketches and clears them:
 // warps take the (slot, j) rows, lanes the outputs o.
-template <int LPAD, bool TF>
+template <int LPAD, int FMT>
 __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool long_class, int64_t bL, int64_t bR) {
-  constexpr int kWarps = Prec<TF>::kWarps;
+  constexpr int kWarps = Prec<FMT>::kWarps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n1 = (int)g.n1, cnt = (int)g.cnt;
   const int slot_elems = LPAD * g.ldo;
@@ -254,12 +279,13 @@ __device__ void sp_flush(const SpArgs& g, const SpSk* s_sk, float* acc, bool lon
 // The planes of block (bL, bR), one per warp; no block-wide barrier inside.
 // KR: the launch has Khatri-Rao test matrices (the dense instance leaves
 // their code out, which keeps it within its registers).
-template <int LPAD, bool TF, bool KR>
+template <int LPAD, int FMT, bool KR>
 __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw, float* acc, int64_t bL, int64_t bR) {
-  using E = typename std::conditional<TF, float, __nv_bfloat16>::type;
-  constexpr int kWarps = Prec<TF>::kWarps, kEsz = Prec<TF>::kEsz;
+  constexpr bool TF = FMT == kFmtTF32, F16 = FMT == kFmtFP16;
+  using E = typename std::conditional<TF, float, uint16_t>::type;
+  constexpr int kWarps = Prec<FMT>::kWarps, kEsz = Prec<FMT>::kEsz;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  E* Xh = reinterpret_cast<E*>(smraw + warp * Prec<TF>::kWarpBytes);
+  E* Xh = reinterpret_cast<E*>(smraw + warp * Prec<FMT>::kWarpBytes);
   E* Xl = Xh + kTileElems;
   E* Gs = Xl + kTileElems;
   const int slot_elems = LPAD * g.ldo;
@@ -283,10 +309,15 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                 const float h = round_tf32(v[b]);
                 Xh[b * kLD + lane] = h;
                 Xl[b * kLD + lane] = round_tf32(__fsub_rn(v[b], h));
+              } else if constexpr (F16) {
+                const float xv = __fmul_rn(v[b], g.xscale);
+                const __half h = __float2half_rn(xv);
+                Xh[b * kLD + lane] = __half_as_ushort(h);
+                Xl[b * kLD + lane] = __half_as_ushort(__float2half_rn(__fsub_rn(xv, __half2float(h))));
               } else {
                 const __nv_bfloat16 h = __float2bfloat16_rn(v[b]);
-                Xh[b * kLD + lane] = h;
-                Xl[b * kLD + lane] = __float2bfloat16_rn(__fsub_rn(v[b], __bfloat162float(h)));
+                Xh[b * kLD + lane] = __bfloat16_as_ushort(h);
+                Xl[b * kLD + lane] = __bfloat16_as_ushort(__float2bfloat16_rn(__fsub_rn(v[b], __bfloat162float(h))));
               }
             }
           }
@@ -347,8 +378,8 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
                       4 * q < sell ? round_tf32(z[h].x) : 0.f, 4 * q + 1 < sell ? round_tf32(z[h].y) : 0.f,
                       4 * q + 2 < sell ? round_tf32(z[h].z) : 0.f, 4 * q + 3 < sell ? round_tf32(z[h].w) : 0.f);
                 } else {
-                  const uint32_t lo = bf16x2(4 * q < sell ? z[h].x : 0.f, 4 * q + 1 < sell ? z[h].y : 0.f);
-                  const uint32_t hi = bf16x2(4 * q + 2 < sell ? z[h].z : 0.f, 4 * q + 3 < sell ? z[h].w : 0.f);
+                  const uint32_t lo = op16x2(F16, 4 * q < sell ? z[h].x : 0.f, 4 * q + 1 < sell ? z[h].y : 0.f);
+                  const uint32_t hi = op16x2(F16, 4 * q + 2 < sell ? z[h].z : 0.f, 4 * q + 3 < sell ? z[h].w : 0.f);
                   *reinterpret_cast<uint2*>(Gs + rr[h] * kLD + 4 * q) = make_uint2(lo, hi);
                 }
               }
@@ -446,12 +477,18 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
               for (int nt = 0; nt < 4; ++nt)
-                if (nt < ntn) mma_bf16(ch[mt][nt], a[mt], bh[nt]);
+                if (nt < ntn) {
+                  if constexpr (F16) mma_f16(ch[mt][nt], a[mt], bh[nt]);
+                  else mma_bf16(ch[mt][nt], a[mt], bh[nt]);
+                }
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
               for (int nt = 0; nt < 4; ++nt)
-                if (nt < ntn) mma_bf16(ch[mt][nt], a[mt], bl[nt]);
+                if (nt < ntn) {
+                  if constexpr (F16) mma_f16(ch[mt][nt], a[mt], bl[nt]);
+                  else mma_bf16(ch[mt][nt], a[mt], bl[nt]);
+                }
           }
         }
         }
@@ -469,7 +506,8 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 const int j = mt * 16 + gq + 8 * h;
-                const float4 c = kr_scale_quad(g.wsb, *krs, (uint64_t)key, (uint32_t)(j >> 2), TF ? TT_PREC_TF32 : TT_PREC_BF16);
+                const float4 c = kr_scale_quad(g.wsb, *krs, (uint64_t)key, (uint32_t)(j >> 2),
+                                              TF ? TT_PREC_TF32 : F16 ? TT_PREC_FP16 : TT_PREC_BF16);
                 sc[mt][h] = (j & 3) == 0 ? c.x : (j & 3) == 1 ? c.y : (j & 3) == 2 ? c.z : c.w;
               }
           }
@@ -493,21 +531,21 @@ __device__ void sp_block(const SpArgs& g, const SpSk* s_sk, unsigned char* smraw
 
 // Zeroes the per-warp tiles (their padding rows and columns stay zero) and
 // the accumulator slots.
-template <bool TF>
+template <int FMT>
 __device__ void sp_zero(unsigned char* smraw, float* acc, int acc_elems) {
-  for (int i = threadIdx.x; i < Prec<TF>::kWarps * Prec<TF>::kWarpBytes / 16; i += Prec<TF>::kThreads)
+  for (int i = threadIdx.x; i < Prec<FMT>::kWarps * Prec<FMT>::kWarpBytes / 16; i += Prec<FMT>::kThreads)
     reinterpret_cast<uint4*>(smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (int i = threadIdx.x; i < acc_elems; i += Prec<TF>::kThreads) acc[i] = 0.0f;
+  for (int i = threadIdx.x; i < acc_elems; i += Prec<FMT>::kThreads) acc[i] = 0.0f;
 }
 
-template <int LPAD, bool TF, bool KR>
-__global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
+template <int LPAD, int FMT, bool KR>
+__global__ void __launch_bounds__(Prec<FMT>::kThreads, 1) sketch_sp_kernel(const SpArgs ga) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ SpArgs g;
   if (threadIdx.x == 0) g = ga;
   __syncthreads();
-  float* acc = reinterpret_cast<float*>(smraw + Prec<TF>::kWarps * Prec<TF>::kWarpBytes);
-  sp_zero<TF>(smraw, acc, g.nslots * LPAD * g.ldo);
+  float* acc = reinterpret_cast<float*>(smraw + Prec<FMT>::kWarps * Prec<FMT>::kWarpBytes);
+  sp_zero<FMT>(smraw, acc, g.nslots * LPAD * g.ldo);
   __syncthreads();
   const int64_t nblocks = g.tilesL * g.tilesR;
   const int64_t b_beg = nblocks * blockIdx.x / gridDim.x, b_end = nblocks * (blockIdx.x + 1) / gridDim.x;
@@ -517,26 +555,26 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_kernel(const 
     const int64_t bL = t / g.tilesR, bR = t - bL * g.tilesR;
     if (bL != cur_bL || age == kColFlushBlocks) {
       if (cur_bL >= 0) {
-        sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
+        sp_flush<LPAD, FMT>(g, g.sk, acc, true, cur_bL, 0);
         __syncthreads();
       }
       cur_bL = bL;
       age = 0;
     }
     ++age;
-    sp_block<LPAD, TF, KR>(g, g.sk, smraw, acc, bL, bR);
+    sp_block<LPAD, FMT, KR>(g, g.sk, smraw, acc, bL, bR);
     __syncthreads();
-    sp_flush<LPAD, TF>(g, g.sk, acc, false, cur_bL, bR);
+    sp_flush<LPAD, FMT>(g, g.sk, acc, false, cur_bL, bR);
     __syncthreads();
   }
-  if (cur_bL >= 0) sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
+  if (cur_bL >= 0) sp_flush<LPAD, FMT>(g, g.sk, acc, true, cur_bL, 0);
 }
 
 // Batched form: persistent CTAs take `chunk` consecutive units (item, block)
 // of the largest-first unit sequence at a time; row slots are flushed after
 // every unit, the others when the item or the kL block changes.
-template <int LPAD, bool TF>
-__global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kernel(const BatchLaunch b) {
+template <int LPAD, int FMT>
+__global__ void __launch_bounds__(Prec<FMT>::kThreads, 1) sketch_sp_batched_kernel(const BatchLaunch b) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ SpArgs g;
   __shared__ int64_t s_base;
@@ -548,8 +586,8 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kerne
   const int64_t* prefix = reinterpret_cast<const int64_t*>(b.wsb + T.off_bprefix);
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(b.wsb + T.off_bcounter);
   const int64_t total = prefix[T.nitems];
-  float* acc = reinterpret_cast<float*>(smraw + Prec<TF>::kWarps * Prec<TF>::kWarpBytes);
-  sp_zero<TF>(smraw, acc, 0);
+  float* acc = reinterpret_cast<float*>(smraw + Prec<FMT>::kWarps * Prec<FMT>::kWarpBytes);
+  sp_zero<FMT>(smraw, acc, 0);
   int cur = -1;
   int64_t cur_bL = -1;
   int age = 0;
@@ -579,7 +617,7 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kerne
       // while the item and the kL block stay the same, for at most
       // kColFlushBlocks units
       if (cur >= 0 && (it_idx != cur || lu / g.tilesR != cur_bL || age == kColFlushBlocks)) {
-        sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
+        sp_flush<LPAD, FMT>(g, g.sk, acc, true, cur_bL, 0);
         __syncthreads();
         age = 0;
         cur_bL = -1;
@@ -595,20 +633,20 @@ __global__ void __launch_bounds__(Prec<TF>::kThreads, 1) sketch_sp_batched_kerne
         }
         __syncthreads();
         // slots of this item start at zero (every unit is flushed completely)
-        for (int i = threadIdx.x; i < g.nslots * LPAD * g.ldo; i += Prec<TF>::kThreads) acc[i] = 0.0f;
+        for (int i = threadIdx.x; i < g.nslots * LPAD * g.ldo; i += Prec<FMT>::kThreads) acc[i] = 0.0f;
         __syncthreads();
         cur = it_idx;
       }
       const int64_t bL = lu / g.tilesR, bR = lu - bL * g.tilesR;
       cur_bL = bL;
       ++age;
-      sp_block<LPAD, TF, false>(g, g.sk, smraw, acc, bL, bR);  // batched plans refuse Khatri-Rao
+      sp_block<LPAD, FMT, false>(g, g.sk, smraw, acc, bL, bR);  // batched plans refuse Khatri-Rao
       __syncthreads();
-      sp_flush<LPAD, TF>(g, g.sk, acc, false, bL, bR);
+      sp_flush<LPAD, FMT>(g, g.sk, acc, false, bL, bR);
       __syncthreads();
     }
   }
-  if (cur >= 0 && cur_bL >= 0) sp_flush<LPAD, TF>(g, g.sk, acc, true, cur_bL, 0);
+  if (cur >= 0 && cur_bL >= 0) sp_flush<LPAD, FMT>(g, g.sk, acc, true, cur_bL, 0);
 }
 
 // Batched tables: blockIdx.y = item; its staged sketches one after another.
@@ -630,8 +668,7 @@ __global__ void sp_table_batched_kernel(char* wsb) {
     const int nr = k.col ? (int)it.n[it.d - 1] : (int)it.n[0];
     const int64_t nkeys = k.col ? it.W / d.wdiv : d.wdiv;
     sp_table_fill(wsb, k, it.seed, 0, it.n[0], nr, d.width, lpad, nkeys, wsb + it.off_sptab * 8 + d.sp_tab,
-                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
-                  it.prec == TT_PREC_TF32);
+                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, it.prec);
   }
 }
 
@@ -665,7 +702,9 @@ __global__ void __launch_bounds__(1024) sp_batch_prep_kernel(char* wsb, int t3ma
 
 bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, int t3max = 4) {
   const DevItem& it = plan_items_host(&P)[item];
-  if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_TF32) || it.x_f64 || it.sptab_doubles == 0) return false;
+  if ((it.prec != TT_PREC_BF16 && it.prec != TT_PREC_TF32 && it.prec != TT_PREC_FP16) || it.x_f64 ||
+      it.sptab_doubles == 0)
+    return false;
   if (count < 1 || count > 32 || it.n[0] > 32 || it.W >= (1LL << 31)) return false;
   const DevSketch* sks = plan_sketches_host(&P);
   SpArgs g;
@@ -673,8 +712,8 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, 
   sp_fill(it, sks, count, g, t3max);
   if (g.ell > 32) return false;
   const int lpad = g.ell <= 16 ? 16 : 32;
-  const size_t tiles = it.prec == TT_PREC_TF32 ? (size_t)Prec<true>::kWarps * Prec<true>::kWarpBytes
-                                               : (size_t)Prec<false>::kWarps * Prec<false>::kWarpBytes;
+  const size_t tiles = it.prec == TT_PREC_TF32 ? (size_t)Prec<kFmtTF32>::kWarps * Prec<kFmtTF32>::kWarpBytes
+                                               : (size_t)Prec<kFmtBF16>::kWarps * Prec<kFmtBF16>::kWarpBytes;
   const size_t need = tiles + sizeof(float) * (size_t)g.nslots * lpad * g.ldo;
   if (need > (size_t)kMaxSmem) return false;
   *out = g;
@@ -685,7 +724,7 @@ bool plan_sp(const Plan& P, int item, int64_t count, SpArgs* out, size_t* smem, 
 }  // namespace sp
 
 cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint64_t seed, int64_t first, int64_t n1,
-                              int nr, int lpad, int64_t nkeys, char* tab, bool tf, cudaStream_t st) {
+                              int nr, int lpad, int64_t nkeys, char* tab, int prec, cudaStream_t st) {
   sp::SpSk k;
   memset(&k, 0, sizeof(k));
   k.hstride = d.hstride;
@@ -695,7 +734,7 @@ cudaError_t launch_rows_table(const DevSketch& d, int gsk, const char* wsb, uint
   const int64_t total = nkeys * nr * (lpad / 4);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count()));
   count_launch();
-  sp::sp_table_kernel<<<blocks, 256, 0, st>>>(wsb, k, seed, first, n1, nr, d.width, lpad, nkeys, tab, tf ? 1 : 0);
+  sp::sp_table_kernel<<<blocks, 256, 0, st>>>(wsb, k, seed, first, n1, nr, d.width, lpad, nkeys, tab, prec);
   return cudaGetLastError();
 }
 
@@ -715,16 +754,21 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
   g.first = first;
   const int lpad = g.ell <= 16 ? 16 : 32;
   const DevItem& it = plan_items_host(&P)[item];
-  const bool tf = it.prec == TT_PREC_TF32;
+  const int fmt = sp::fmt_of(it.prec);
+  using KernelFn = void (*)(const sp::SpArgs);
+#define TT_SP_K(F)                                                                      \
+  {{sp::sketch_sp_kernel<16, F, false>, sp::sketch_sp_kernel<16, F, true>},             \
+   {sp::sketch_sp_kernel<32, F, false>, sp::sketch_sp_kernel<32, F, true>}}
+  const KernelFn kernels[3][2][2] = {TT_SP_K(sp::kFmtBF16), TT_SP_K(sp::kFmtTF32), TT_SP_K(sp::kFmtFP16)};
+#undef TT_SP_K
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaSuccess;
-    for (const void* f :
-         {(const void*)sp::sketch_sp_kernel<16, false, false>, (const void*)sp::sketch_sp_kernel<32, false, false>,
-          (const void*)sp::sketch_sp_kernel<16, true, false>, (const void*)sp::sketch_sp_kernel<32, true, false>,
-          (const void*)sp::sketch_sp_kernel<16, false, true>, (const void*)sp::sketch_sp_kernel<32, false, true>,
-          (const void*)sp::sketch_sp_kernel<16, true, true>, (const void*)sp::sketch_sp_kernel<32, true, true>})
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
+    for (int f = 0; f < 3; ++f)
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kernels[f][i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
     if (e != cudaSuccess) {
       cudaGetLastError();  // leave no pending error for the caller's next runtime call
       return e;
@@ -740,21 +784,15 @@ cudaError_t launch_sketch_sp(const Plan& P, int item, const void* X, int64_t fir
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sm_count());
     count_launch();
     sp::sp_table_kernel<<<blocks, 256, 0, st>>>(g.wsb, k, g.seed, first, g.n1, nr, k.ell, lpad, nkeys,
-                                                g.wsb + g.tab0 + k.tab, tf ? 1 : 0);
+                                                g.wsb + g.tab0 + k.tab, it.prec);
   }
   const int64_t nblocks = g.tilesL * g.tilesR;
   const int grid = (int)std::min<int64_t>(nblocks, device_sm_count());
   count_launch();
   bool kr = false;
   for (int s = 0; s < g.nsk; ++s) kr = kr || g.sk[s].kr >= 0;
-  using KernelFn = void (*)(const sp::SpArgs);
-  const KernelFn kernels[2][2][2] = {
-      {{sp::sketch_sp_kernel<16, false, false>, sp::sketch_sp_kernel<16, false, true>},
-       {sp::sketch_sp_kernel<32, false, false>, sp::sketch_sp_kernel<32, false, true>}},
-      {{sp::sketch_sp_kernel<16, true, false>, sp::sketch_sp_kernel<16, true, true>},
-       {sp::sketch_sp_kernel<32, true, false>, sp::sketch_sp_kernel<32, true, true>}}};
-  const KernelFn k = kernels[tf ? 1 : 0][lpad == 16 ? 0 : 1][kr ? 1 : 0];
-  k<<<grid, tf ? sp::Prec<true>::kThreads : sp::Prec<false>::kThreads, smem, st>>>(g);
+  const KernelFn k = kernels[fmt][lpad == 16 ? 0 : 1][kr ? 1 : 0];
+  k<<<grid, fmt == sp::kFmtTF32 ? sp::Prec<sp::kFmtTF32>::kThreads : sp::Prec<sp::kFmtBF16>::kThreads, smem, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -793,33 +831,33 @@ cudaError_t launch_sketch_sp_batched(const Plan& P, const void* const* X, const 
   b.chunk = std::max(1, cfg.chunk);
   b.t3max = t3max;
   for (int i = 0; i < nitems; ++i) b.X[i] = X[i];
+  using KernelFn = void (*)(const BatchLaunch);
+  const KernelFn kernels[3][2] = {
+      {sp::sketch_sp_batched_kernel<16, sp::kFmtBF16>, sp::sketch_sp_batched_kernel<32, sp::kFmtBF16>},
+      {sp::sketch_sp_batched_kernel<16, sp::kFmtTF32>, sp::sketch_sp_batched_kernel<32, sp::kFmtTF32>},
+      {sp::sketch_sp_batched_kernel<16, sp::kFmtFP16>, sp::sketch_sp_batched_kernel<32, sp::kFmtFP16>}};
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaSuccess;
-    for (const void* f :
-         {(const void*)sp::sketch_sp_batched_kernel<16, false>, (const void*)sp::sketch_sp_batched_kernel<32, false>,
-          (const void*)sp::sketch_sp_batched_kernel<16, true>, (const void*)sp::sketch_sp_batched_kernel<32, true>})
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
+    for (int f = 0; f < 3; ++f)
+      for (int i = 0; i < 2; ++i)
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(kernels[f][i], cudaFuncAttributeMaxDynamicSharedMemorySize, sp::kMaxSmem);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;
     }
     attr_set = true;
   }
-  const bool tf = plan_items_host(&P)[0].prec == TT_PREC_TF32;
+  const int fmt = sp::fmt_of(plan_items_host(&P)[0].prec);
   count_launch();
   sp::sp_batch_prep_kernel<<<1, 1024, 0, st>>>((char*)ws, t3max);
   count_launch();
   sp::sp_table_batched_kernel<<<dim3(16, (unsigned)nitems), 256, 0, st>>>((char*)ws);
   count_launch();
   const int nsm = device_sm_count();
-  if (tf) {
-    if (lpad == 16) sp::sketch_sp_batched_kernel<16, true><<<nsm, sp::Prec<true>::kThreads, smem, st>>>(b);
-    else sp::sketch_sp_batched_kernel<32, true><<<nsm, sp::Prec<true>::kThreads, smem, st>>>(b);
-  } else {
-    if (lpad == 16) sp::sketch_sp_batched_kernel<16, false><<<nsm, sp::Prec<false>::kThreads, smem, st>>>(b);
-    else sp::sketch_sp_batched_kernel<32, false><<<nsm, sp::Prec<false>::kThreads, smem, st>>>(b);
-  }
+  const int threads = fmt == sp::kFmtTF32 ? sp::Prec<sp::kFmtTF32>::kThreads : sp::Prec<sp::kFmtBF16>::kThreads;
+  kernels[fmt][lpad == 16 ? 0 : 1]<<<nsm, threads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

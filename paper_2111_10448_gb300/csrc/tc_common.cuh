@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 
@@ -105,12 +106,13 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   d |= (uint64_t)1 << 46;
   return d;
 }
-// Instruction descriptor, kind::f16: BF16 x BF16 -> F32, M = 128.
-__host__ __device__ constexpr uint32_t make_idesc(int n, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor, kind::f16: BF16 x BF16 (or, f16, FP16 x FP16) ->
+// F32, M = 128.  A and B always have the same type.
+__host__ __device__ constexpr uint32_t make_idesc(int n, bool a_mn_major, bool f16 = false) {
+  return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
-__device__ __forceinline__ void mma_bf16_ss(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma16_ss(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
@@ -119,7 +121,7 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t dtmem, uint64_t ad, uint64_
 }
 // Same, with the descriptors given as 32-bit halves (a k-step only moves the
 // start-address field, which lives in the low half).
-__device__ __forceinline__ void mma_bf16_ss_lo(uint32_t dtmem, uint32_t alo, uint32_t ahi, uint32_t blo,
+__device__ __forceinline__ void mma16_ss_lo(uint32_t dtmem, uint32_t alo, uint32_t ahi, uint32_t blo,
                                                uint32_t bhi, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\t"
@@ -173,6 +175,42 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float v[ELL]) {
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
   __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&b);
+}
+__device__ __forceinline__ uint32_t f16x2_bits(float lo, float hi) {
+  __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+// The 16-bit MMA operand type of a kernel instance: BF16, or FP16 when F16.
+template <bool F16>
+__device__ __forceinline__ uint32_t op16x2_bits(float lo, float hi) {
+  if constexpr (F16) return f16x2_bits(lo, hi);
+  else return bf16x2_bits(lo, hi);
+}
+template <bool F16>
+__device__ __forceinline__ uint16_t op16_bits(float v) {
+  if constexpr (F16) return __half_as_ushort(__float2half_rn(v));
+  else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+// X = hi + lo in the 16-bit operand type, two entries at a time: hi is the
+// nearest value of the type, lo the nearest to the exact FP32 remainder.
+template <bool F16>
+__device__ __forceinline__ void split_hi_lo(float x0, float x1, uint32_t& hb, uint32_t& lb) {
+  if constexpr (F16) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
+    hb = *reinterpret_cast<const uint32_t*>(&h);
+    lb = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    hb = bf16x2_bits(x0, x1);
+    const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
+    lb = bf16x2_bits(__fsub_rn(x0, h0), __fsub_rn(x1, h1));
+  }
+}
+template <bool F16>
+__device__ __forceinline__ float round_op16(float v) {
+  if constexpr (F16) return __half2float(__float2half_rn(v));
+  else return __bfloat162float(__float2bfloat16_rn(v));
 }
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));

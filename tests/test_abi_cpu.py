@@ -145,8 +145,43 @@ def test_mixed_needs_fp32_storage():
     assert st == N.TT_ERR_UNSUPPORTED
 
 
+def test_fp16_plans():
+    """FP16 plans: FP32 storage only, a scale exponent within +-100, the same
+    workspace as the BF16 plan of the shape (16-bit operands, same staging),
+    and the scale kept in the stored problem."""
+    st, _ = plan([8, 8, 8], ranks=[1, 2, 2, 1], x_dtype=N.TT_F64, prec=N.TT_PREC_FP16)
+    assert st == N.TT_ERR_UNSUPPORTED
+    for s in (-101, 101):
+        st, h = plan([8, 8, 8], ranks=[1, 2, 2, 1], prec=N.TT_PREC_FP16, x_scale_log2=s)
+        assert st == N.TT_ERR_INVALID_ARG and not h.value
+    # other precisions ignore the field
+    st, h = plan([8, 8, 8], ranks=[1, 2, 2, 1], prec=N.TT_PREC_BF16, x_scale_log2=500)
+    assert st == N.TT_OK
+    N.lib().tt_plan_destroy(h)
+    for dims, kw in (([256, 256, 256, 256], dict(eps=1e-6, rmax=6, p=10)),
+                     ([24] * 6, dict(eps=1e-6, rmax=16, p=10)),
+                     ([40, 30, 50], dict(ranks=[1, 3, 4, 1], p=5))):
+        st16, h16 = plan(dims, prec=N.TT_PREC_FP16, x_scale_log2=12, **kw)
+        stbf, hbf = plan(dims, prec=N.TT_PREC_BF16, **kw)
+        assert st16 == N.TT_OK and stbf == N.TT_OK
+        assert sizes(h16)[1:] == sizes(hbf)[1:]
+        # no tensor-core adjoint table for FP16 (its backward takes the SIMT adjoint)
+        assert sizes(h16)[0] <= sizes(hbf)[0]
+        assert N.lib().tt_sketch_kernel_kind(h16, dims[-1]) == N.lib().tt_sketch_kernel_kind(hbf, dims[-1])
+        q = N.tt_problem()
+        N.check(N.lib().tt_plan_problem(h16, 0, C.byref(q)), "problem")
+        assert q.prec == N.TT_PREC_FP16 and q.x_scale_log2 == 12
+        N.lib().tt_plan_destroy(h16)
+        N.lib().tt_plan_destroy(hbf)
+    # the 1 GiB slab of the 256^4 tensor runs on the tcgen05 slab kernel, both test-matrix kinds
+    for flags in (0, N.TT_FLAG_KR):
+        st, h = plan([256] * 4, eps=1e-6, rmax=6, p=10, prec=N.TT_PREC_FP16, x_scale_log2=16, flags=flags)
+        assert st == N.TT_OK and N.lib().tt_sketch_kernel_kind(h, 16) == 2
+        N.lib().tt_plan_destroy(h)
+
+
 def test_status_strings():
-    for s in range(9):
+    for s in range(10):
         assert N.lib().tt_status_string(s)
     assert b"ttsketch" in N.lib().tt_version()
 
@@ -285,6 +320,14 @@ def test_device_calls_check_their_arguments_on_the_host():
     assert L.tt_test_matrix(1, 0, 0, 10, N.TT_MAXL + 1, N.TT_PREC_BF16, dummy, null) == BAD
     assert L.tt_test_matrix(1, 0, 0, 10, 4, 7, dummy, null) == BAD
     assert L.tt_test_matrix(1, 0, 0, 0, 4, N.TT_PREC_BF16, dummy, null) == OK
+    assert L.tt_test_matrix(1, 0, 0, 0, 4, N.TT_PREC_FP16, dummy, null) == OK
+    # FP16 scale helper: null pointers, negative count, unknown dtype; empty is s = 0
+    sv = C.c_int(7)
+    assert L.tt_x_scale_log2(null, N.TT_F32, 4, C.byref(sv), null) == BAD
+    assert L.tt_x_scale_log2(dummy, N.TT_F32, 4, None, null) == BAD
+    assert L.tt_x_scale_log2(dummy, N.TT_F32, -1, C.byref(sv), null) == BAD
+    assert L.tt_x_scale_log2(dummy, 5, 4, C.byref(sv), null) == BAD
+    assert L.tt_x_scale_log2(dummy, N.TT_F32, 0, C.byref(sv), null) == OK and sv.value == 0
     # raw Philox
     assert L.tt_philox4x32_10(null, 1, 2, dummy, 4, null) == BAD
     assert L.tt_philox4x32_10(dummy, 1, 2, dummy, -1, null) == BAD

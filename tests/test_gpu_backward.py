@@ -137,15 +137,18 @@ def test_reconstruct_backward_matches_autograd():
     assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-10
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_vjp_mixed_precision_matches_rounded_oracle(prec):
     """Mixed paths: the adjoint runs in FP32 with the rounded test matrices;
     compared with the oracle gradient of the map whose test matrices are
     rounded to the same type (the FP32 generator flips a few rounding
-    decisions, and X is FP32, so the bar is looser than the FP64 path's)."""
+    decisions, and X is FP32, so the bar is looser than the FP64 path's).
+    FP16 plans take the SIMT adjoint; the power-of-two scale of their split
+    does not enter the gradient."""
     dims, r, target, p = [6, 5, 7, 4], [1, 3, 4, 3, 1], [1, 2, 3, 2, 1], 4
     x = ti.random_tt(dims, r, seed=4, noise=1e-2).astype(np.float32).astype(np.float64)
-    t = TTSketch(dims, ranks=target, p=p, seed=2, x_dtype=torch.float32, prec=prec)
+    s = 15 - int(np.frexp(float(np.max(np.abs(x))))[1]) if prec == "fp16" else 0
+    t = TTSketch(dims, ranks=target, p=p, seed=2, x_dtype=torch.float32, prec=prec, x_scale_log2=s)
     t.pstt2(to_dev(x, torch.float32))
     _, ranks = t.status()
     ref = OG.forward_ref(x, dims, ranks=target, p=p, seed=2, test_fmt=prec)

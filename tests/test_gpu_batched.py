@@ -116,18 +116,23 @@ def test_autotuner_picks_a_candidate_and_keeps_results():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_batched_small_plane_matches_single_plans_and_oracle(prec):
     """Mixed-precision batch whose items all fit the small-plane kernel
     (n_1, n_d <= 32): each item within 10 eps of the FP64 oracle and of its
-    own single-tensor plan (the two differ only in FP32 accumulation order)."""
+    own single-tensor plan (the two differ only in FP32 accumulation order).
+    FP16 items carry their own scale (each item's largest |X|)."""
     xs, probs = make_batch(24, cap=200_000, seed=19, dtype=np.float32)
+    if prec == "fp16":
+        for x, pr in zip(xs, probs):
+            pr["x_scale_log2"] = 15 - int(np.frexp(float(np.max(np.abs(x))))[1])
     t, dev = run_batched(xs, probs, prec=prec, x_dtype=torch.float32)
     st, _ = t.status()
     assert st in (0, 7)
     for b, (x, pr) in enumerate(zip(xs, probs)):
         x64 = x.astype(np.float64)
-        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float32, prec=prec)
+        s = TTSketch(pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], x_dtype=torch.float32, prec=prec,
+                     x_scale_log2=pr.get("x_scale_log2", 0))
         s.pstt2(dev[b])
         torch.cuda.synchronize()
         got, single = full(t.core_list(b)), full(s.core_list(0))

@@ -9,7 +9,13 @@ benchmark times.
   times the oracle's rounded test-matrix rows.  The middle sketches S_2 and R_2
   (test matrices of 65,536 rows) take a few rows each; the outermost S_1 and
   R_3 (16.7 M rows) one row each, in slabs.  Then the whole one-pass pipeline:
-  X~ within 10 eps of X and of the FP64 path.
+  X~ within 10 eps of X and of the FP64 path.  BF16 and FP16 (X 2^16, as
+  |X| <= 1/4).
+* The same tensor streamed as the benchmark streams it: 16 slabs of 16
+  slices (1 GiB each) in shuffled order, Khatri-Rao test matrices, FP16: no
+  rank cap, the FP64 path's ranks or at most one more on a bond (the FP32
+  accumulation of the tensor cores), X~ within 10 eps of X and of the FP64
+  path.
 * Precision form: random TT, d = 6, n = 24, internal ranks 10, +1e-6 noise
   (1.91e8 FP32 entries), eps = 1e-5, p = 10, rmax = 16 (the small-plane
   kernel), BF16 and TF32: sampled rows of every sketch (S_1..S_3, R_3..R_5;
@@ -36,10 +42,14 @@ STREAMING = dict(eps=1e-6, rmax=6, p=10, seed=1)
 PRECISION = dict(eps=1e-5, rmax=16, p=10, seed=1)
 
 
-def _split(x, prec):
-    hi = philox.round_to(x, prec)
-    lo = philox.round_to(x - hi, prec)
-    return hi + lo
+def _split(x, prec, s=0):
+    xs = np.asarray(x, dtype=np.float64) * 2.0 ** s
+    hi = philox.round_to(xs, prec)
+    lo = philox.round_to(xs - hi, prec)
+    return (hi + lo) * 2.0 ** -s
+
+
+S16 = 16  # FP16 scale of the Hilbert-type tensor: |X| <= 1/4, X 2^16 <= 2^14
 
 
 def _rowerr(got, ref):
@@ -63,21 +73,23 @@ def hilbert256():
     torch.cuda.empty_cache()
 
 
-def test_streaming_256_sampled_sketch_rows(hilbert256):
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_streaming_256_sampled_sketch_rows(hilbert256, prec):
     dims, Xd = hilbert256
     n1, n2, n3, n4 = dims
     seed = STREAMING["seed"]
-    t = TTSketch(dims, x_dtype=torch.float32, prec="bf16", **STREAMING)
+    s = S16 if prec == "fp16" else 0
+    t = TTSketch(dims, x_dtype=torch.float32, prec=prec, x_scale_log2=s, **STREAMING)
     assert t.kernel_kind() == 2
     t.begin()
     t.accumulate(Xd, 0, n4)
-    sk = {(ty, k): S for ty, k, S in t.sketches(0)}
+    sk = {(ty, k): S * 2.0 ** -s for ty, k, S in t.sketches(0)}
     l = sk[(0, 1)].shape[1]
-    sub = lambda idx: _split(ti.hilbert_type_block(dims, idx).astype(np.float64), "bf16")
+    sub = lambda idx: _split(ti.hilbert_type_block(dims, idx).astype(np.float64), prec, s)
     rng = np.random.default_rng(11)
     errs = {}
-    Om2 = _tm(seed, 2, np.arange(n3 * n4), l, "bf16")
-    Ps2 = _tm(seed, 66, np.arange(n1 * n2), l, "bf16")
+    Om2 = _tm(seed, 2, np.arange(n3 * n4), l, prec)
+    Ps2 = _tm(seed, 66, np.arange(n1 * n2), l, prec)
     for _ in range(4):
         i1, i2, i3, i4 = [int(rng.integers(v)) for v in dims]
         # S_2(i1 + n1 i2, :) = sum_{i3,i4} X(i1,i2,i3,i4) Omega_2[i3 + n3 i4, :]
@@ -93,16 +105,16 @@ def test_streaming_256_sampled_sketch_rows(hilbert256):
     ref = np.zeros(l)
     for j4 in range(n4):   # S_1(i1, :) = sum X(i1, i2, i3, i4) Omega_1[i2 + n2 i3 + n2 n3 i4, :]
         rows = j4 * n2 * n3 + np.arange(n2 * n3)
-        ref += sub([[i1], None, None, [j4]]) @ _tm(seed, 1, rows, l, "bf16")
+        ref += sub([[i1], None, None, [j4]]) @ _tm(seed, 1, rows, l, prec)
     errs["S1"] = [_rowerr(sk[(0, 1)][i1].cpu().numpy(), ref)]
     ref = np.zeros(l)
     for j3 in range(n3):   # R_3(i4, :) = sum X(i1, i2, i3, i4) Psi_3[i1 + n1 i2 + n1 n2 i3, :]
         rows = j3 * n1 * n2 + np.arange(n1 * n2)
-        ref += sub([None, None, [j3], [i4]]) @ _tm(seed, 67, rows, l, "bf16")
+        ref += sub([None, None, [j3], [i4]]) @ _tm(seed, 67, rows, l, prec)
     errs["R3"] = [_rowerr(sk[(1, 3)][i4].cpu().numpy(), ref)]
     t.finalize()
     e = {k: max(v) for k, v in errs.items()}
-    print("256^4 sampled sketch rows, max rel err:", e)
+    print(f"256^4 sampled sketch rows {prec}, max rel err:", e)
     assert all(v <= 2e-3 for v in e.values()), e
 
 
@@ -120,6 +132,37 @@ def test_streaming_256_pipeline_within_10eps(hilbert256):
     del Xf
     rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
     print(f"256^4 pipeline: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={ranks}")
+    assert rx <= 10 * eps and rf <= 10 * eps
+
+
+def test_streaming_256_fp16_slabs_no_rank_cap(hilbert256):
+    """The benchmark's streaming configuration: FP16 with Khatri-Rao test
+    matrices, sixteen 1 GiB slabs of 16 slices in shuffled order.  The FP16
+    split (2^-22 relative) resolves the rank threshold eps / sqrt(d - 1):
+    status OK (no rank cap), the ranks of the FP64 path or one more on a bond
+    (FP32 accumulation noise of the tensor cores near the threshold), X~
+    within 10 eps of X and of the FP64 path's X~."""
+    dims, Xd = hilbert256
+    eps = STREAMING["eps"]
+    t = TTSketch(dims, x_dtype=torch.float32, prec="fp16", drm="kr", x_scale_log2=S16, **STREAMING)
+    assert t.kernel_kind(16) == 2
+    nd1 = 256 ** 3
+    order = list(range(0, 256, 16))
+    np.random.default_rng(2).shuffle(order)
+    t.begin()
+    for a in order:
+        t.accumulate(Xd[a * nd1:(a + 16) * nd1], a, 16)
+    t.finalize()
+    st, ranks = t.status()
+    f = TTSketch(dims, x_dtype=torch.float32, prec="fp64", drm="kr", **STREAMING).pstt2(Xd)
+    e_x = t.error(Xd).cpu().numpy()
+    Xf = f.reconstruct(torch.float32)
+    e_f = t.error(Xf).cpu().numpy()
+    del Xf
+    rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
+    print(f"256^4 FP16 slabs: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={ranks} fp64 ranks={f.status()[1]}")
+    r64 = f.status()[1]
+    assert st == 0 and all(a <= b <= a + 1 for a, b in zip(r64, ranks)), (r64, ranks)
     assert rx <= 10 * eps and rf <= 10 * eps
 
 

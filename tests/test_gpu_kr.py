@@ -25,10 +25,17 @@ from tests.gpu_util import rel, sketch_dict, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _split(x, prec):
-    hi = philox.round_to(x, prec)
-    lo = philox.round_to(x - hi, prec)
-    return hi + lo
+def _split(x, prec, s=0):
+    """hi + lo of X 2^s in the MMA type, at the scale of X (s: FP16 only)."""
+    xs = np.asarray(x, dtype=np.float64) * 2.0 ** s
+    hi = philox.round_to(xs, prec)
+    lo = philox.round_to(xs - hi, prec)
+    return (hi + lo) * 2.0 ** -s
+
+
+def _scale_of(x, prec):
+    """FP16 scale exponent (the rule of tt_x_scale_log2); 0 otherwise."""
+    return 15 - int(np.frexp(float(np.max(np.abs(x))))[1]) if prec == "fp16" else 0
 
 
 def _close(G, S, what):
@@ -95,35 +102,37 @@ def test_fp64_streaming_slabs_equal_one_shot():
     ([128, 64, 48, 128], dict(eps=1e-6, rmax=6, p=10), 2),             # the same, several tiles a CTA
     ([256, 7, 128], dict(ranks=[1, 4, 4, 1], p=12), 1),                # d = 3: the generic kernel
 ])
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_mixed_sketches_match_oracle(dims, kw, kind, prec):
     if kind == 2 and prec == "tf32":
-        pytest.skip("the tcgen05 kernels are BF16 only")
-    if kind == 1 and prec == "tf32" and len(dims) == 3:
+        pytest.skip("the tcgen05 kernels are BF16 / FP16 only")
+    if kind == 1 and prec != "bf16" and len(dims) == 3:
         pytest.skip("covered in BF16")
     d = len(dims)
     x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, drm="kr", **kw)
+    s = _scale_of(x, prec)
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, drm="kr", x_scale_log2=s, **kw)
     assert t.kernel_kind() == kind
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
-    sk = sketch_dict(t)
+    sk = {k: v * 2.0 ** -s for k, v in sketch_dict(t).items()}
     t.finalize()
     widths = OP.sketch_widths(d, OP.clamp_ranks(dims, kw["ranks"]) if "ranks" in kw else None, kw["p"],
                               "eps" in kw, kw.get("rmax"))
-    o = OP.sketches(_split(x.astype(np.float64), prec), dims, widths, 7, 1, test_fmt=prec, drm="kr")
+    o = OP.sketches(_split(x.astype(np.float64), prec, s), dims, widths, 7, 1, test_fmt=prec, drm="kr")
     for k, S in o["S"].items():
         _close(sk[(0, k)], S, ("S", k))
     for k, R in o["R"].items():
         _close(sk[(1, k)], R, ("R", k))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_mixed_within_10eps_of_oracle(prec):
     dims, eps = [32] * 4, 1e-6
     x = ti.hilbert_type(dims, np.float32)
     x64 = x.astype(np.float64)
-    t = TTSketch(dims, eps=eps, rmax=6, p=10, seed=1, prec=prec, drm="kr").pstt2(to_dev(x))
+    t = TTSketch(dims, eps=eps, rmax=6, p=10, seed=1, prec=prec, drm="kr",
+                 x_scale_log2=_scale_of(x, prec)).pstt2(to_dev(x))
     o = OP.pstt2(x64, dims, eps=eps, rmax=6, p=10, seed=1, drm="kr")
     xt = t.reconstruct().cpu().numpy()
     assert rel(xt, OT.tt_full(o["cores"]), x64) <= 10 * eps

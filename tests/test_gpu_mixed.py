@@ -1,4 +1,4 @@
-"""GPU parity of the mixed-precision (TF32 / BF16 tensor-core) sketch path.
+"""GPU parity of the mixed-precision (TF32 / BF16 / FP16 tensor-core) sketch path.
 
 Bars (derived from the arithmetic):
 * test-matrix entries: the FP32 generator differs from the FP64 definition by
@@ -10,7 +10,9 @@ Bars (derived from the arithmetic):
   MMA type) with its rounded test matrix; the flips above change a sketch
   entry by about 2^-8 |x w| (BF16), which bounds the relative Frobenius
   difference by 1e-4 and the max-norm difference by 2e-3 of max |S| (FP32
-  accumulation inside a tile adds ~1e-7);
+  accumulation inside a tile adds ~1e-7).  FP16 plans split X 2^s (s from
+  the largest |X|, the rule of tt_x_scale_log2) and their sketches hold 2^s
+  times the values until the finalize: the tests scale them back;
 * reconstruction: within 10 eps of the FP64 oracle (relative Frobenius), the
   precision form's stated target.
 """
@@ -27,11 +29,29 @@ from tests.gpu_util import rel, sketch_dict, to_dev
 
 pytestmark = pytest.mark.gpu
 
-PREC = {"tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16}
-ULP = {"tf32": 2.0 ** -10, "bf16": 2.0 ** -7}
+PREC = {"tf32": N.TT_PREC_TF32, "bf16": N.TT_PREC_BF16, "fp16": N.TT_PREC_FP16}
+ULP = {"tf32": 2.0 ** -10, "bf16": 2.0 ** -7, "fp16": 2.0 ** -10}
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def _scale_of(x):
+    """FP16 scale exponent: 15 - e with 2^(e-1) <= max |x| < 2^e."""
+    m = float(np.max(np.abs(x)))
+    return 0 if m == 0.0 else 15 - int(np.frexp(m)[1])
+
+
+def _mk(dims, prec, x, **kw):
+    """TTSketch of precision prec; FP16 plans get the scale of x.  Returns
+    (plan, s)."""
+    s = _scale_of(x) if prec == "fp16" else 0
+    return TTSketch(dims, x_dtype=torch.float32, prec=prec, x_scale_log2=s, **kw), s
+
+
+def _sketches(t, s):
+    """The sketches read between accumulate and finalize, at the scale of X."""
+    return {k: v * 2.0 ** -s for k, v in sketch_dict(t).items()}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
 def test_test_matrix_mixed_matches_rounded_oracle(prec):
     nrows, ncols, sid = 20000, 26, 5
     out = torch.empty(nrows * ncols, dtype=torch.float64, device="cuda")
@@ -51,24 +71,28 @@ def _close_sketch(G, S, what):
     assert fro <= 1e-4 and mx <= 2e-3, (what, fro, mx)
 
 
-def _split(x, prec):
-    hi = philox.round_to(x, prec)
-    lo = philox.round_to(x - hi, prec)
-    return hi + lo
+def _split(x, prec, s=0):
+    """X as the sketch kernels see it: hi + lo of X 2^s in the MMA type, at the
+    scale of X (s only for FP16)."""
+    s = s if prec == "fp16" else 0
+    xs = np.asarray(x, dtype=np.float64) * 2.0 ** s
+    hi = philox.round_to(xs, prec)
+    lo = philox.round_to(xs - hi, prec)
+    return (hi + lo) * 2.0 ** -s
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
 @pytest.mark.parametrize("dims,r", [([40, 7, 6, 70], [1, 4, 5, 4, 1]), ([9, 8, 7, 6, 5, 9], [1, 5, 6, 6, 5, 5, 1]),
                                     ([130, 100], [1, 6, 1])])
 def test_mixed_sketches_match_oracle(prec, dims, r):
     x = ti.random_tt(dims, r, seed=2, noise=1e-6).astype(np.float32)
     target = [1] + [v for v in r[1:-1]] + [1]
-    t = TTSketch(dims, ranks=target, p=6, seed=4, x_dtype=torch.float32, prec=prec)
+    t, s = _mk(dims, prec, x, ranks=target, p=6, seed=4)
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     t.finalize()
-    xs = _split(x.astype(np.float64), prec)
+    xs = _split(x.astype(np.float64), prec, s)
     o = OP.pstt2(xs, dims, ranks=target, p=6, seed=4, passes=1, test_fmt=prec)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
@@ -78,7 +102,7 @@ def test_mixed_sketches_match_oracle(prec, dims, r):
     assert st == 0
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
 @pytest.mark.parametrize("case", ["config2_small", "config3_small"])
 def test_mixed_within_10eps_of_oracle(prec, case):
     if case == "config2_small":
@@ -88,7 +112,7 @@ def test_mixed_within_10eps_of_oracle(prec, case):
         dims, eps, p, rmax = [32] * 4, 1e-6, 10, 6
         x = ti.hilbert_type(dims, np.float32)
     x64 = x.astype(np.float64)
-    t = TTSketch(dims, eps=eps, rmax=rmax, p=p, seed=1, x_dtype=torch.float32, prec=prec).pstt2(to_dev(x))
+    t = _mk(dims, prec, x, eps=eps, rmax=rmax, p=p, seed=1)[0].pstt2(to_dev(x))
     f = TTSketch(dims, eps=eps, rmax=rmax, p=p, seed=1, x_dtype=torch.float32, prec="fp64").pstt2(to_dev(x))
     o = OP.pstt2(x64, dims, eps=eps, rmax=rmax, p=p, seed=1)
     xt = t.reconstruct().cpu().numpy()
@@ -117,7 +141,7 @@ def test_mixed_streaming_equals_one_shot():
     assert rel(one.reconstruct().cpu().numpy(), t.reconstruct().cpu().numpy(), x) <= 1e-6
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
 def test_generic_staged_rows_streaming_match_oracle(prec):
     # n_1 = 70, n_d = 45: the generic tile kernel with staged test-matrix rows
     # (column side: 2 row tiles of i_1 read each row; row side: planes and
@@ -126,14 +150,14 @@ def test_generic_staged_rows_streaming_match_oracle(prec):
     x = ti.random_tt(dims, r, seed=8, noise=1e-6).astype(np.float32)
     X = to_dev(x)
     Nd1 = 70 * 3 * 5
-    t = TTSketch(dims, ranks=r, p=6, seed=9, x_dtype=torch.float32, prec=prec)
+    t, s = _mk(dims, prec, x, ranks=r, p=6, seed=9)
     assert t.kernel_kind(15) == 1
     t.begin()
     for first, cnt in [(30, 15), (0, 13), (13, 17)]:
         t.accumulate(X[first * Nd1:(first + cnt) * Nd1].clone(), first, cnt)
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     t.finalize()
-    o = OP.pstt2(_split(x.astype(np.float64), prec), dims, ranks=r, p=6, seed=9, passes=1, test_fmt=prec)
+    o = OP.pstt2(_split(x.astype(np.float64), prec, s), dims, ranks=r, p=6, seed=9, passes=1, test_fmt=prec)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
     for k, R in o["sketch"]["R"].items():
@@ -146,18 +170,19 @@ def test_generic_staged_rows_streaming_match_oracle(prec):
     ([256, 3, 4, 256], dict(eps=1e-6, rmax=6, p=10)),               # two halves per side, l = 16
     ([256, 7, 128], dict(ranks=[1, 4, 4, 1], p=12)),                # d = 3
 ])
-def test_tcgen05_sketches_match_oracle(dims, kw):
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tcgen05_sketches_match_oracle(dims, kw, prec):
     x = ti.random_tt(dims, [1] + [3] * (len(dims) - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", **kw)
+    t, s = _mk(dims, prec, x, seed=7, **kw)
     assert t.kernel_kind() == 2
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     t.finalize()
     st, ranks = t.status()
     assert st in (0, N.TT_WARN_RANK_CAP)
-    xs = _split(x.astype(np.float64), "bf16")
-    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt="bf16", **kw)
+    xs = _split(x.astype(np.float64), prec, s)
+    o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt=prec, **kw)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
     for k, R in o["sketch"]["R"].items():
@@ -294,21 +319,21 @@ def test_pinned_host_tensor_read_directly_equals_device_tensor():
     ([8, 7, 6, 5, 4], dict(eps=1e-5, rmax=8, p=5)),           # d = 5
     ([15, 15, 15, 15, 15, 15], dict(eps=1e-5, rmax=16, p=10)),  # ~21 blocks per CTA: periodic flushes
 ])
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_small_plane_sketches_match_oracle(dims, kw, prec):
     """The small-plane kernel (n_1, n_d <= 32): every sketch entry against the
     oracle's FP64 products of the split X with the rounded test matrices."""
     d = len(dims)
     x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, **kw)
+    t, s = _mk(dims, prec, x, seed=7, **kw)
     assert t.kernel_kind() == 3
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     t.finalize()
     st, _ = t.status()
     assert st in (0, N.TT_WARN_RANK_CAP)
-    xs = _split(x.astype(np.float64), prec)
+    xs = _split(x.astype(np.float64), prec, s)
     o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt=prec, **kw)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
@@ -316,14 +341,14 @@ def test_small_plane_sketches_match_oracle(dims, kw, prec):
         _close_sketch(sk[(1, k)], R, ("R", k))
 
 
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_small_plane_within_10eps_of_oracle(prec):
     """The precision-form shape at reduced n: X~ from the small-plane kernel
     within 10 eps of the FP64 oracle's X~ and of X."""
     dims, eps = [10] * 6, 1e-5
     x = ti.random_tt(dims, [1, 10, 10, 10, 10, 10, 1], seed=0, noise=1e-6).astype(np.float32)
     x64 = x.astype(np.float64)
-    t = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, x_dtype=torch.float32, prec=prec)
+    t = _mk(dims, prec, x, eps=eps, rmax=16, p=10, seed=1)[0]
     assert t.kernel_kind() == 3
     t.pstt2(to_dev(x))
     o = OP.pstt2(x64, dims, eps=eps, rmax=16, p=10, seed=1)
@@ -337,7 +362,7 @@ def test_small_plane_within_10eps_of_oracle(prec):
     ([9, 8, 7, 6, 5, 9], [1, 3, 5, 7, 5, 3, 1]),           # widths 8..12 (padding 16)
     ([4] * 9, [1, 4, 12, 18, 19, 19, 18, 12, 4, 1]),       # the paper's d = 9 rank profile, clamped: widths 14..29
 ])
-@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["bf16", "tf32", "fp16"])
 def test_small_plane_unequal_widths_match_oracle(dims, ranks, prec):
     """Fixed ranks give each sketch its own width l_k = r_k + p; the
     small-plane kernel pads them all to the widest and writes each sketch's
@@ -345,15 +370,15 @@ def test_small_plane_unequal_widths_match_oracle(dims, ranks, prec):
     d = len(dims)
     x = ti.random_tt(dims, [1] + [3] * (d - 1) + [1], seed=5, noise=1e-5).astype(np.float32)
     kw = dict(ranks=ranks, p=10)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, **kw)
+    t, s = _mk(dims, prec, x, seed=7, **kw)
     assert t.kernel_kind() == 3
     t.begin()
     t.accumulate(to_dev(x), 0, dims[-1])
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     t.finalize()
     widths = {v.shape[1] for v in sk.values()}
     assert len(widths) > 1
-    xs = _split(x.astype(np.float64), prec)
+    xs = _split(x.astype(np.float64), prec, s)
     o = OP.pstt2(xs, dims, seed=7, passes=1, test_fmt=prec, **kw)
     for k, S in o["sketch"]["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
@@ -361,8 +386,9 @@ def test_small_plane_unequal_widths_match_oracle(dims, ranks, prec):
         _close_sketch(sk[(1, k)], R, ("R", k))
 
 
-@pytest.mark.parametrize("dims", [[256, 64, 48, 256], [128, 64, 96, 128]])
-def test_tcgen05_multitile_every_sketch_entry(dims):
+@pytest.mark.parametrize("dims,prec", [([256, 64, 48, 256], "bf16"), ([128, 64, 96, 128], "bf16"),
+                                       ([128, 64, 96, 128], "fp16")])
+def test_tcgen05_multitile_every_sketch_entry(dims, prec):
     """Every entry of every sketch of one multi-tile launch of the plane kernel
     against the oracle's dense FP64 products (the split X, the BF16-rounded
     test matrices).  At these shapes each CTA walks two to three tiles: the
@@ -374,17 +400,18 @@ def test_tcgen05_multitile_every_sketch_entry(dims):
     nn = (C.c_int64 * 4)(*dims)
     N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, n4, C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
     kw = dict(eps=1e-6, rmax=6, p=10)
-    t = TTSketch(dims, seed=7, prec="bf16", **kw)
+    s = 16 if prec == "fp16" else 0  # |X| <= 1/4
+    t = TTSketch(dims, seed=7, prec=prec, x_scale_log2=s, **kw)
     assert t.kernel_kind() == 2
     t.begin()
     t.accumulate(Xd, 0, n4)
-    sk = sketch_dict(t)
+    sk = _sketches(t, s)
     del Xd
     x = ti.hilbert_type(dims, np.float32).astype(np.float64)
-    xs = _split(x, "bf16")
+    xs = _split(x, prec, s)
     del x
     widths = OP.sketch_widths(4, None, kw["p"], True, kw["rmax"])
-    o = OP.sketches(xs, dims, widths, 7, 1, test_fmt="bf16")
+    o = OP.sketches(xs, dims, widths, 7, 1, test_fmt=prec)
     for k, S in o["S"].items():
         _close_sketch(sk[(0, k)], S, ("S", k))
     for k, R in o["R"].items():

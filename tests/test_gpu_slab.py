@@ -3,8 +3,9 @@ or 64 last-mode slices of a 4-way tensor (the 1 GiB slabs of the 256^4
 streaming workload are 16 slices), accumulated slab by slab in any order.
 
 Every sketch entry after a stream of slabs is compared with the oracle's
-dense FP64 products of the split X (hi + lo in BF16) with its BF16-rounded
-test matrices, dense Gaussian and Khatri-Rao: Frobenius 1e-4 and max 2e-3 of
+dense FP64 products of the split X (hi + lo in BF16, or in FP16 of X 2^s) with
+its test matrices rounded the same way, dense Gaussian and Khatri-Rao:
+Frobenius 1e-4 and max 2e-3 of
 max |S| (the bars and their derivation are those of test_gpu_mixed.py: the
 FP32 generator flips a rare rounding decision).  The slab kernel takes the
 R_3 products against G planes' blocks at once and keeps the diagonal; a
@@ -23,9 +24,10 @@ from tests.gpu_util import rel, sketch_dict, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def _split(x):
-    hi = philox.round_to(x, "bf16")
-    return hi + philox.round_to(x - hi, "bf16")
+def _split(x, prec="bf16", s=0):
+    xs = np.asarray(x, dtype=np.float64) * 2.0 ** s
+    hi = philox.round_to(xs, prec)
+    return (hi + philox.round_to(xs - hi, prec)) * 2.0 ** -s
 
 
 def _close(G, S, what):
@@ -48,8 +50,9 @@ def _slabs(n4, c, seed):
     ([256, 64, 64, 32], 16, dict(eps=1e-6, rmax=6, p=10)),     # two halves of i_1, 64 tiles
 ])
 @pytest.mark.parametrize("drm", ["gauss", "kr"])
-def test_slab_sketches_match_oracle(dims, c, kw, drm):
-    _check_slab(dims, c, kw, drm)
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_slab_sketches_match_oracle(dims, c, kw, drm, prec):
+    _check_slab(dims, c, kw, drm, prec)
 
 
 def test_slab_multitile_every_sketch_entry():
@@ -58,25 +61,28 @@ def test_slab_multitile_every_sketch_entry():
     its run and flushes the column accumulators; every entry against the
     oracle."""
     _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10), "gauss")
+    _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10), "kr", "fp16")
 
 
-def _check_slab(dims, c, kw, drm):
+def _check_slab(dims, c, kw, drm, prec="bf16"):
     n1, n2, n3, n4 = dims
     x = ti.random_tt(dims, [1, 3, 3, 3, 1], seed=5, noise=1e-5).astype(np.float32)
     X = to_dev(x)
-    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec="bf16", drm=drm, **kw)
+    # FP16: X 2^s below 2^15 (the rule of tt_x_scale_log2)
+    s = 15 - int(np.frexp(float(np.max(np.abs(x))))[1]) if prec == "fp16" else 0
+    t = TTSketch(dims, seed=7, x_dtype=torch.float32, prec=prec, drm=drm, x_scale_log2=s, **kw)
     assert t.kernel_kind(c) == 2
     nd1 = n1 * n2 * n3
     t.begin()
     for a, cnt in _slabs(n4, c, 1):
         t.accumulate(X[a * nd1:(a + cnt) * nd1].clone(), a, cnt)
-    sk = sketch_dict(t)
+    sk = {k: v * 2.0 ** -s for k, v in sketch_dict(t).items()}
     t.finalize()
     st, _ = t.status()
     assert st in (0, N.TT_WARN_RANK_CAP)
     widths = OP.sketch_widths(4, OP.clamp_ranks(dims, kw["ranks"]) if "ranks" in kw else None, kw["p"],
                               "eps" in kw, kw.get("rmax"))
-    o = OP.sketches(_split(x.astype(np.float64)), dims, widths, 7, 1, test_fmt="bf16", drm=drm)
+    o = OP.sketches(_split(x.astype(np.float64), prec, s), dims, widths, 7, 1, test_fmt=prec, drm=drm)
     for k, S in o["S"].items():
         _close(sk[(0, k)], S, ("S", k))
     for k, R in o["R"].items():
@@ -110,14 +116,19 @@ def test_slab_stream_equals_whole_tensor(drm):
 
 
 @pytest.mark.parametrize("drm", ["gauss", "kr"])
-def test_slab_pipeline_within_10eps(drm):
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_slab_pipeline_within_10eps(drm, prec):
     """The one-pass pipeline fed by 16-slice slabs: X~ within 10 eps of X and
-    of the FP64 path with the same test matrices."""
+    of the FP64 path with the same test matrices.  FP16 resolves the rank
+    threshold eps / sqrt(d - 1): no rank cap, X~ within eps of X, and the FP64
+    path's ranks (dense) or at most one more on a bond (Khatri-Rao, whose r_2
+    tail on this instance sits at 0.83 of the threshold, inside the FP32
+    accumulation noise of the tensor cores)."""
     dims = [256, 32, 32, 128]
     Xd = torch.empty(int(np.prod(dims)), dtype=torch.float32, device="cuda")
     nn = (C.c_int64 * 4)(*dims)
     N.check(N.lib().tt_generate_hilbert_type(4, nn, 0, dims[-1], C.c_void_p(Xd.data_ptr()), N.TT_F32, None), "gen")
-    t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec="bf16", drm=drm)
+    t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=1, prec=prec, drm=drm, x_scale_log2=16)
     nd1 = 256 * 32 * 32
     t.begin()
     for a, cnt in _slabs(128, 16, 5):
@@ -127,8 +138,13 @@ def test_slab_pipeline_within_10eps(drm):
     e_x = t.error(Xd).cpu().numpy()
     e_f = t.error(f.reconstruct(torch.float32)).cpu().numpy()
     rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
-    print(f"slab pipeline {drm}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
+    print(f"slab pipeline {drm} {prec}: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={t.status()[1]}")
     assert rx <= 1e-5 and rf <= 1e-5
+    if prec == "fp16":
+        st, r16 = t.status()
+        r64 = f.status()[1]
+        assert st == 0 and rx <= 1e-6
+        assert r16 == r64 if drm == "gauss" else all(a <= b <= a + 1 for a, b in zip(r64, r16)), (r64, r16)
 
 
 @pytest.mark.parametrize("drm", ["gauss", "kr"])
