@@ -820,6 +820,11 @@ def run_gpu(a):
             tf = P.TTSketch(dims, prec=a.prec, drm=drm_, **kw)
             forms[f"{drm_}_{sl_}_slices_per_accumulate"] = measure_form(tf, sl_, max(3, min(a.steps, 10)), 2)
             del tf
+        # the headline with TT_FLAG_SHORT_CHAINS: FP32 tensor-memory chains of
+        # 32 MMAs instead of 256 in the column sketches (accuracy for time)
+        tf = P.TTSketch(dims, prec=a.prec, drm=a.drm, short_chains=True, **kw)
+        forms[f"{a.drm}_{slab}_slices_short_chains"] = measure_form(tf, slab, max(3, min(a.steps, 10)), 2)
+        del tf
         out["forms"] = forms
 
     # ---- FP64 GPU path, same eps, same slabs (one step after one warm-up)

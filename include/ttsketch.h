@@ -151,6 +151,15 @@ typedef struct {
  * the workspace by tt_pstt2 and tt_pstt2_begin.  Single-problem plans only
  * (TT_ERR_UNSUPPORTED in batched plans). */
 #define TT_FLAG_KR 4
+/* Tensor-core plans (TF32 / BF16 / FP16) on the tcgen05 kernels: flush the
+ * FP32 tensor-memory accumulators of the column sketches every 32
+ * accumulating MMAs instead of every 256.  Each accumulating MMA adds about
+ * 2e-8 relative error (measured on GB300); in the one-pass middle sketch
+ * S_{d*} that error enters the cores directly.  On the 256^4 Hilbert-type
+ * tensor at eps = 1e-6 (FP16, Khatri-Rao, 1 GiB slabs) it brings ||X - X~||
+ * / ||X|| from 2.1e-6 to 8.9e-7 for about 12 % more sketch time.  Other
+ * kernels ignore it. */
+#define TT_FLAG_SHORT_CHAINS 8
 
 /* ---------------------------------------------------------------- plans */
 

@@ -20,6 +20,7 @@ TT_PREC_FP64, TT_PREC_TF32, TT_PREC_BF16, TT_PREC_FP16 = 0, 1, 2, 3
 TT_FLAG_DIFF = 1
 TT_FLAG_ONESIDED = 2
 TT_FLAG_KR = 4
+TT_FLAG_SHORT_CHAINS = 8
 
 STATUS_NAMES = {
     0: "TT_OK", 1: "TT_ERR_INVALID_ARG", 2: "TT_ERR_UNSUPPORTED", 3: "TT_ERR_CUDA",

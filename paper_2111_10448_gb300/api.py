@@ -26,7 +26,8 @@ class TTSketch:
     passes: 1 (one-pass, the hot path) or 2; x_dtype: torch.float32/float64;
     prec: 'fp64' | 'tf32' | 'bf16' | 'fp16'; x_scale_log2: the power-of-two
     scale s of X before an FP16 split (X 2^s must stay below 65520; see
-    x_scale_log2() below); one_sided: the one-sided PSTT-onepass
+    x_scale_log2() below); short_chains: TT_FLAG_SHORT_CHAINS (shorter FP32
+    accumulation chains in the tcgen05 kernels); one_sided: the one-sided PSTT-onepass
     (every unfolding sketched from the right, last core by least squares)
     instead of the two-sided PSTT2-onepass; drm: 'gauss' (dense Gaussian test
     matrices) or 'kr' (Khatri-Rao products of per-mode Gaussian factors).
@@ -37,7 +38,7 @@ class TTSketch:
 
     def __init__(self, dims, *, ranks=None, eps=0.0, rmax=0, p=5, seed=1, passes=1,
                  x_dtype=torch.float32, prec="fp64", device="cuda", batch=None, diff=False,
-                 one_sided=False, drm="gauss", x_scale_log2=0):
+                 one_sided=False, drm="gauss", x_scale_log2=0, short_chains=False):
         L = N.lib()
         self.device = torch.device(device)
         if batch is None:
@@ -52,7 +53,8 @@ class TTSketch:
                                     x_dtype=_DT[x_dtype], prec=self.PRECS[prec],
                                     flags=(N.TT_FLAG_DIFF if diff else 0) |
                                     (N.TT_FLAG_ONESIDED if one_sided else 0) |
-                                    (N.TT_FLAG_KR if drm == "kr" else 0),
+                                    (N.TT_FLAG_KR if drm == "kr" else 0) |
+                                    (N.TT_FLAG_SHORT_CHAINS if short_chains else 0),
                                     x_scale_log2=pr.get("x_scale_log2", x_scale_log2))
         h = C.c_void_p()
         if batch is None:

@@ -147,6 +147,8 @@ struct DevItem {
   int64_t s2stage_doubles;  // into S_2 after every launch (0: the slab kernel cannot serve the item)
   int64_t off_ytab;         // slab kernel, dense test matrices: Psi_3's 128-row blocks for every
   int64_t ytab_doubles;     // (half of i_1, kL, kR), generated once per decomposition (0: per quarter)
+  int short_chains;         // TT_FLAG_SHORT_CHAINS: tcgen05 column-sketch accumulators flushed every
+                            // kMaxChainS MMAs
   int x_scale_log2;         // FP16: s, the sketch kernels split X 2^s (0 for other precisions)
   float xscale;             // 2^s
 };

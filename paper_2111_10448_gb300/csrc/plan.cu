@@ -426,6 +426,7 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
   }
   if (single) it.off_small = ws.take(4LL * TT_MAXL * TT_MAXL);
   it.diff = (q.flags & TT_FLAG_DIFF) ? 1 : 0;
+  it.short_chains = (q.flags & TT_FLAG_SHORT_CHAINS) ? 1 : 0;
   if (it.diff) {
     int64_t ymax = 1;
     for (int k = 1; k < d; ++k) it.off_Lall[k] = ws.take(it.N[k] * it.rpad[k]);

@@ -1129,7 +1129,7 @@ bool plan_tc(const Plan& P, int item, int64_t count, TcArgs* out) {
   g.tilesL = (g.WL + T2 - 1) / T2;
   g.tilesR = (g.WR + T3 - 1) / T3;
   // accumulating MMAs per L slot and tile: T3 planes x H4 quarters x 8 k-steps x (hi, lo)
-  g.runL = std::max<int64_t>(1, kMaxChainL / (T3 * g.H4 * 16));
+  g.runL = std::max<int64_t>(1, (it.short_chains ? kMaxChainS : kMaxChainL) / (T3 * g.H4 * 16));
   g.ell = ell;
   g.nL = nL;
   g.nR = nR;

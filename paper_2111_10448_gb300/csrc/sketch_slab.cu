@@ -35,9 +35,13 @@
 // row product applied by the epilogue as a column scale per super-plane.
 //
 // Accumulators: one L slot per (kL of the tile, i_1 half), kept for runL
-// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block (of a
-// tile, or of a super-plane with Khatri-Rao) are double-buffered with the
-// epilogue; every accumulator sees at most 256 MMAs before a flush.  Flushes:
+// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block of a
+// tile are double-buffered with the epilogue; every accumulator sees at most
+// 256 MMAs before a flush.  Khatri-Rao: the tensor cores' FP32 accumulation
+// adds ~2e-8 relative error per accumulating MMA (measured), so D_Y and R_2
+// get short chains: a buffer per super-plane (16 MMAs a half of i_1),
+// double-buffered, which the epilogue sums in FP32 (D_Y scaled, and R_2 in
+// shared memory, over a kR group's super-planes).  Flushes:
 // FP64 atomics into S_1, R_2 and R_3; FP32 atomics into a staging copy of S_2
 // (about four CTA partials per entry a launch), added into S_2 by
 // s2_fold_kernel after the launch.
@@ -85,8 +89,13 @@ constexpr int kOffBar = kOffY + kYBlkB;
 // the R_3 area; the slab's mode-4 rows of S_1 and S_2 (FP32, c x l each)
 // follow it
 constexpr int kOffF4 = kOffY + 2 * kRBlkB;
-static_assert(2 * kRBlkB + 2 * 64 * 16 * 4 <= kYBlkB, "Khatri-Rao blocks in the R_3 area");
-constexpr int kSmemBytes = kOffBar + 256 + 1024;
+// and the L flush's FP32 sums of S_1 over a run's kL values ([half][column][lane])
+constexpr int kOffS1 = kOffF4 + 2 * 64 * 16 * 4;
+static_assert(kOffS1 - kOffY + 2 * 16 * 128 * 4 <= kYBlkB, "Khatri-Rao blocks in the R_3 area");
+// Khatri-Rao: the lanes' FP32 sums of R_2 over a kR group's super-planes
+// ([column][lane]), after the barrier words
+constexpr int kOffR2 = kOffBar + 256;
+constexpr int kSmemBytes = kOffR2 + 16 * 128 * 4 + 1024;
 constexpr int kTmemY = 0;         // D_Y buffers at columns 0 and 128, then the L slots, then R_2
 
 struct SlabArgs {
@@ -102,7 +111,7 @@ struct SlabArgs {
   int kry;                 // Khatri-Rao test matrices: R_3 mode by mode (fixed mode-1 block)
   int64_t runL;            // tiles of one kL block accumulated in the L slots before a flush
   uint32_t tab_tx;         // bytes of the staged R_2 blocks copied per super-plane
-  float* s2stage;          // FP32 staging of S_2 (same layout), added into S_2 after the launch
+  float* s2stage;          // FP32 staging of S_2 (row-major: l floats a row), added into S_2 after the launch
   int64_t ytab;            // dense: byte offset of the staged R_3 blocks (-1: regenerated per quarter)
   float xscale;            // FP16 operands: 2^s, X is split as X 2^s (1 with BF16)
   int f16;                 // FP16 operands (else BF16), for the table kernels
@@ -113,6 +122,15 @@ struct TileInfo {
   int64_t kL0, kRg0;
   int nA, nB;
 };
+// dst[0 .. ELL) += v with four-wide FP32 reductions (dst 16-byte aligned).
+template <int ELL>
+__device__ __forceinline__ void red_add_row(float* dst, const float v[ELL]) {
+#pragma unroll
+  for (int q = 0; q < ELL / 4; ++q)
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + 4 * q), "f"(v[4 * q]),
+                 "f"(v[4 * q + 1]), "f"(v[4 * q + 2]), "f"(v[4 * q + 3])
+                 : "memory");
+}
 __device__ __forceinline__ TileInfo tile_info(const SlabArgs& g, int64_t t) {
   TileInfo ti;
   const int64_t tl = t / g.tilesR, tr = t % g.tilesR;  // kL-block-major
@@ -155,11 +173,12 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBar);
   // barrier indices
+  // (TML_EMPTY + a: the L slots of the tile's a-th kL value are free, a < 8)
   const int FULL_A = 0, EMPTY_A = 2, FULL_L = 4, EMPTY_L = 6, TAB_FULL = 8, FULL_Y = 10, EMPTY_Y = 11,
-            TML_FULL = 12, TML_EMPTY = 13, TMR_FULL = 14, TMR_EMPTY = 16, DRAIN = 18, TMY_FULL = 19,
-            TMY_EMPTY = 21;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 192);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 200);
+            TML_FULL = 12, TMR_FULL = 14, TMR_EMPTY = 16, DRAIN = 18, TMY_FULL = 19, TMY_EMPTY = 21,
+            TML_EMPTY = 23;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 248);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 252);
   __shared__ SkTc s_col[2], s_row[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -187,7 +206,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       mbar_init(bar(TMY_EMPTY + s2), kEpiWarps);
     }
     mbar_init(bar(TML_FULL), 1);
-    mbar_init(bar(TML_EMPTY), kEpiWarps);
+    for (int a = 0; a < 8; ++a) mbar_init(bar(TML_EMPTY + a), kEpiWarps);
     mbar_init(bar(DRAIN), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -223,6 +242,8 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         f4s[e] = tb[kb->kr_off[sk ? 1 : 2] + (g.first + r) * kb->kr_lp + j];
       }
     }
+    float* s1z = reinterpret_cast<float*>(sm + kOffS1);
+    for (int e = threadIdx.x; e < g.H1 * ell * 128; e += kThreads) s1z[e] = 0.0f;
     fence_async_smem();
   }
   tc_fence_before();
@@ -561,12 +582,16 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         }
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issue
+    // Khatri-Rao: R_2 into a buffer per super-plane (16 MMAs a half of i_1)
+    // that the epilogue sums in FP32: each accumulating MMA adds ~2e-8
+    // relative error in FP32 (measured), which a chain over the tile's kL
+    // values would bring to the rank rule's threshold.
     const uint32_t idL = make_idesc(NL, true, F16), idR = make_idesc(ell, false, F16),
                    idY = make_idesc(KRY ? ell : g.G * ell, false, F16);
     const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     uint32_t qi = 0, pi = 0, lf = 0, ti_n = 0;
     int64_t cur_tl = -1;
-    uint32_t initL = 0;
+    uint32_t initL = 0, pendL = 0;
     bool ok = true;
     for (int64_t t = t_beg; t < ntiles && ok; ++t, ++ti_n) {
       const TileInfo tinf = tile_info(g, t);
@@ -577,22 +602,30 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
           __syncwarp();
           ++lf;
         }
-        ok = warp_wait(bar(TML_EMPTY), (lf & 1) ^ 1, abort_flag, g.status);
-        if (!ok) break;
-        tc_fence_after();
+        // the epilogue frees the previous run's slots kL by kL: each is
+        // awaited just before its first MMA of this run
+        pendL = 0xFFu;
         initL = 0;
         cur_tl = tl;
       }
       const uint32_t rb = ti_n & 1;
-      ok = warp_wait(bar(TMR_EMPTY + rb), ((ti_n >> 1) & 1) ^ 1, abort_flag, g.status);
-      if (!ok) break;
-      tc_fence_after();
+      if (!KRY) {
+        ok = warp_wait(bar(TMR_EMPTY + rb), ((ti_n >> 1) & 1) ^ 1, abort_flag, g.status);
+        if (!ok) break;
+        tc_fence_after();
+      }
       uint32_t initR = 0;
       bool initY = false;
       const uint32_t dY = tmem + (uint32_t)kTmemY + rb * colYB;
       for (int b = 0; b < tinf.nB && ok; ++b)
         for (int a = 0; a < tinf.nA && ok; ++a, ++pi) {
           const int buf = pi & 1;
+          if ((pendL >> a) & 1u) {
+            ok = warp_wait(bar(TML_EMPTY + a), (lf & 1) ^ 1, abort_flag, g.status);
+            if (!ok) break;
+            tc_fence_after();
+            pendL &= ~(1u << a);
+          }
           ok = warp_wait(bar(FULL_L + buf), (pi >> 1) & 1, abort_flag, g.status);
           if (ok && g.tab_tx) ok = warp_wait(bar(TAB_FULL + buf), (pi >> 1) & 1, abort_flag, g.status);
           // Khatri-Rao: one D_Y accumulator per super-plane, double-buffered
@@ -612,14 +645,16 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
             const uint32_t bR = sR + (buf * 2 + h1) * kRBlkB;
             const int slotL = a * g.H1 + h1;
             const uint32_t dL = tmem + (uint32_t)g.colL + (uint32_t)(slotL * NL);
-            const uint32_t dR = tmem + (uint32_t)g.colR + rb * (uint32_t)(g.T3 * ell) + (uint32_t)(b * ell);
+            const uint32_t dR = KRY ? tmem + (uint32_t)g.colR + yb * (uint32_t)ell
+                                    : tmem + (uint32_t)g.colR + rb * (uint32_t)(g.T3 * ell) + (uint32_t)(b * ell);
             const uint64_t aL0 = make_desc(tileA, kS4, kS1), aR0 = make_desc(tileA, kS1, kS4);
             // Khatri-Rao: the fixed mode-1 block of this half of i_1, into the
             // super-plane's D_Y; dense: the G planes' R_3 blocks into the tile's
             const uint64_t bL0 = make_desc(bL, kS1, kS4), bR0 = make_desc(bR, kS1, kS4),
                            bY0 = make_desc(KRY ? sY + (uint32_t)(h1 * kRBlkB) : sY, kS1, kS4);
             const uint32_t dYq = KRY ? tmem + (uint32_t)kTmemY + yb * colYB : dY;
-            const uint32_t accL0 = (initL >> slotL) & 1u, accR0 = (initR >> b) & 1u,
+            const uint32_t accL0 = (initL >> slotL) & 1u,
+                           accR0 = KRY ? (h1 > 0 ? 1u : 0u) : (initR >> b) & 1u,
                            accY0 = KRY ? (h1 > 0 ? 1u : 0u) : (initY ? 1u : 0u);
             if (elect_one()) {
               // the R_3 products first, so that the RNG warps can refill their
@@ -658,7 +693,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
             __syncwarp();
           }
         }
-      if (ok) {
+      if (ok && !KRY) {
         if (elect_one()) mma_commit(bar(TMR_FULL + rb));
         __syncwarp();
       }
@@ -680,41 +715,58 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
     const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     // L slots of kL block [kL0, kL0 + nA): S_1 (rows i_1, pre-summed over the
     // kL values) and S_2 (rows i_1 + n_1 kL)
+    // Khatri-Rao: kL by kL, each kL's slots handed back as soon as they are
+    // read (the MMA warp waits for a slot only before its first MMA of the
+    // next run), S_1 summed in shared memory over every run of the CTA and
+    // added to the sketch once at its end (its rows are the same for every
+    // run); dense: half by half (the R_3 area holds no room for S_1's sums),
+    // the slots handed back at the end.
     auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
       if (!mbar_wait(bar(TML_FULL), lf & 1, abort_flag, g.status)) return false;
       tc_fence_after();
-      for (int h1 = 0; h1 < g.H1; ++h1) {
-        const int64_t i1 = h1 * 128 + lrow;
-        for (int s = 0; s < 2; ++s) {
-          const SkTc& sk = s_col[s];
-          double* dst = g.ws + sk.off;
+      const SkTc& sk1 = s_col[0];
+      double* dst1 = g.ws + sk1.off;
+      if constexpr (KRY) {
+        float* s1p = reinterpret_cast<float*>(sm + kOffS1);
+        for (int a = 0; a < nA; ++a) {
+          for (int h1 = 0; h1 < g.H1; ++h1) {
+            float v[ell];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL), v);
+#pragma unroll
+            for (int j = 0; j < ell; ++j) s1p[(h1 * ell + j) * 128 + lrow] += v[j];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + ell), v);
+            // S_2: four-wide FP32 reductions into the row-major staging copy
+            // (FP64 atomics here cost the launch ~25 us of drain)
+            red_add_row<ell>(g.s2stage + (h1 * 128 + lrow + g.n1 * (kL0 + a)) * ell, v);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(TML_EMPTY + a));
+        }
+      } else {
+        for (int h1 = 0; h1 < g.H1; ++h1) {
+          const int64_t i1 = h1 * 128 + lrow;
           float acc[ell];
 #pragma unroll
           for (int j = 0; j < ell; ++j) acc[j] = 0.0f;
           for (int a = 0; a < nA; ++a) {
             float v[ell];
-            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + s * ell), v);
-            if (s == 0) {
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL), v);
 #pragma unroll
-              for (int j = 0; j < ell; ++j) acc[j] += v[j];
-            } else {
-              const int64_t row = i1 + g.n1 * (kL0 + a);
-              // S_2: FP32 atomics into the staging copy (each entry receives
-              // about four CTA partials a launch; FP64 atomics here cost the
-              // launch ~25 us of drain)
+            for (int j = 0; j < ell; ++j) acc[j] += v[j];
+            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + ell), v);
+            float* st2 = g.s2stage + (i1 + g.n1 * (kL0 + a)) * ell;
 #pragma unroll
-              for (int j = 0; j < ell; ++j) atomicAdd(g.s2stage + row + sk.rows * j, v[j]);
-            }
+            for (int j = 0; j < ell; ++j) atomicAdd(st2 + j, v[j]);
           }
-          if (s == 0) {
 #pragma unroll
-            for (int j = 0; j < ell; ++j) atomicAdd(dst + i1 + sk.rows * j, (double)acc[j]);
-          }
+          for (int j = 0; j < ell; ++j) atomicAdd(dst1 + i1 + sk1.rows * j, (double)acc[j]);
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          for (int a = 0; a < nA; ++a) mbar_arrive(bar(TML_EMPTY + a));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(TML_EMPTY));
       return true;
     };
     uint32_t lf = 0, ti_n = 0;
@@ -730,6 +782,9 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
     float yacc[ell];
 #pragma unroll
     for (int j = 0; j < ell; ++j) yacc[j] = 0.0f;
+    float* racc = reinterpret_cast<float*>(sm + kOffR2);   // Khatri-Rao: [column][lane]
+    if constexpr (KRY)
+      for (int j = 0; j < ell; ++j) racc[j * 128 + lrow] = 0.0f;
     // Khatri-Rao: the plane's mode-3 and mode-2 factor rows, loaded one
     // super-plane ahead of their use
     float4 ef3[ell / 4], ef2[ell / 4];
@@ -784,47 +839,62 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         // lane's row of D_Y (plane gl, slice kk) times the rounded product of
         // the plane's mode-3 and mode-2 rows, summed into the lane's R_3 row
         bool yok = true;
-        for (int b = 0; b < tinf.nB && yok; ++b)
+        for (int b = 0; b < tinf.nB && yok; ++b) {
           for (int a = 0; a < tinf.nA; ++a, ++spn) {
             const uint32_t yb = spn & 1;
-            // the plane's rows of the mode-3 and mode-2 factors (i_3 = kR_g,
-            // i_2 = kL, loaded during the previous super-plane); product in the
-            // row sketch's decreasing mode order, rounded to the operand type
-            // (the column scale); then the next super-plane's rows go out
-            float4 sc[ell / 4];
-#pragma unroll
-            for (int q = 0; q < ell / 4; ++q)
-              sc[q] = make_float4(round_op16<F16>(__fmul_rn(ef3[q].x, ef2[q].x)),
-                                  round_op16<F16>(__fmul_rn(ef3[q].y, ef2[q].y)),
-                                  round_op16<F16>(__fmul_rn(ef3[q].z, ef2[q].z)),
-                                  round_op16<F16>(__fmul_rn(ef3[q].w, ef2[q].w)));
-            {
-              int64_t kLn, kR0n;
-              if (next_super_plane(g, ntiles, t, a, b, tinf, kLn, kR0n)) e_load(kLn, kR0n);
-            }
             if (!mbar_wait(bar(TMY_FULL + yb), (spn >> 1) & 1, abort_flag, g.status)) {
               yok = false;
               break;
             }
             tc_fence_after();
-            float y[ell];
-            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + yb * colYB, y);
+            {
+              float y[ell];
+              tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)kTmemY + yb * colYB, y);
+              // the plane's rows of the mode-3 and mode-2 factors (i_3 = kR_g,
+              // i_2 = kL, loaded during the previous super-plane); product in
+              // the row sketch's decreasing mode order, rounded to the operand
+              // type (the column scale)
+#pragma unroll
+              for (int q = 0; q < ell / 4; ++q) {
+                yacc[4 * q] = fmaf(y[4 * q], round_op16<F16>(__fmul_rn(ef3[q].x, ef2[q].x)), yacc[4 * q]);
+                yacc[4 * q + 1] = fmaf(y[4 * q + 1], round_op16<F16>(__fmul_rn(ef3[q].y, ef2[q].y)), yacc[4 * q + 1]);
+                yacc[4 * q + 2] = fmaf(y[4 * q + 2], round_op16<F16>(__fmul_rn(ef3[q].z, ef2[q].z)), yacc[4 * q + 2]);
+                yacc[4 * q + 3] = fmaf(y[4 * q + 3], round_op16<F16>(__fmul_rn(ef3[q].w, ef2[q].w)), yacc[4 * q + 3]);
+              }
+            }
+            {  // the next super-plane's factor rows go out
+              int64_t kLn, kR0n;
+              if (next_super_plane(g, ntiles, t, a, b, tinf, kLn, kR0n)) e_load(kLn, kR0n);
+            }
+            {
+              // the super-plane's R_2 partial (rows of the lane's slice), summed
+              // over the kL values of this kR group
+              float r[ell];
+              tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colR + yb * (uint32_t)ell, r);
+#pragma unroll
+              for (int j = 0; j < ell; ++j) racc[j * 128 + lrow] += r[j];
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(TMY_EMPTY + yb));
-#pragma unroll
-            for (int q = 0; q < ell / 4; ++q) {
-              yacc[4 * q] = fmaf(y[4 * q], sc[q].x, yacc[4 * q]);
-              yacc[4 * q + 1] = fmaf(y[4 * q + 1], sc[q].y, yacc[4 * q + 1]);
-              yacc[4 * q + 2] = fmaf(y[4 * q + 2], sc[q].z, yacc[4 * q + 2]);
-              yacc[4 * q + 3] = fmaf(y[4 * q + 3], sc[q].w, yacc[4 * q + 3]);
-            }
             if (++ytiles == kYSuper) {
               flush_Y();
               ytiles = 0;
             }
           }
+          if (!yok) break;
+          // R_2 rows kR_g + n_3 (first + kk) of this kR group
+          const SkTc& sk = s_row[0];
+          double* dst = g.ws + sk.off;
+          const int64_t row = ((tinf.kRg0 + b) * g.G + gl) + sk.hstride * (g.first + kk);
+#pragma unroll
+          for (int j = 0; j < ell; ++j) {
+            atomicAdd(dst + row + sk.rows * j, (double)racc[j * 128 + lrow]);
+            racc[j * 128 + lrow] = 0.0f;
+          }
+        }
         if (!yok) break;
+        continue;
       }
       const uint32_t rb = ti_n & 1;
       if (!mbar_wait(bar(TMR_FULL + rb), (ti_n >> 1) & 1, abort_flag, g.status)) break;
@@ -870,6 +940,18 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
     }
     if (ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
     if (ok && !*abort_flag && ytiles > 0) flush_Y();
+    if constexpr (KRY) {
+      // S_1 rows i_1: the lane's sums over every run of the CTA
+      if (ok && !*abort_flag) {
+        const SkTc& sk1 = s_col[0];
+        const float* s1p = reinterpret_cast<const float*>(sm + kOffS1);
+        for (int h1 = 0; h1 < g.H1; ++h1)
+#pragma unroll
+          for (int j = 0; j < ell; ++j)
+            atomicAdd(g.ws + sk1.off + h1 * 128 + lrow + sk1.rows * j, (double)s1p[(h1 * ell + j) * 128 + lrow]);
+      }
+    }
+
   }
   tc_fence_before();
   __syncthreads();
@@ -911,22 +993,22 @@ __global__ void slab_ytab_kernel(const SlabArgs g) {
   }
 }
 
-// S_2 += the launch's FP32 staging, which is cleared for the next launch;
-// four entries a thread (n = rows l is a multiple of 8, both buffers are
-// 256-byte aligned).
-__global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stage, int64_t n) {
-  double2* d = reinterpret_cast<double2*>(s2);
+// S_2 += the launch's FP32 staging (row-major, l floats a row), which is
+// cleared for the next launch; four columns of a row a thread, consecutive
+// threads on consecutive rows (coalesced FP64 columns).
+__global__ void s2_fold_kernel(double* __restrict__ s2, float* __restrict__ stage, int64_t rows, int ell) {
+  const int qpr = ell / 4;
   float4* f = reinterpret_cast<float4*>(stage);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n / 4; e += (int64_t)gridDim.x * blockDim.x) {
-    const float4 v = f[e];
-    double2 a = d[2 * e], b = d[2 * e + 1];
-    a.x += (double)v.x;
-    a.y += (double)v.y;
-    b.x += (double)v.z;
-    b.y += (double)v.w;
-    d[2 * e] = a;
-    d[2 * e + 1] = b;
-    f[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * qpr; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows;
+    const int q = (int)(e / rows);
+    const float4 v = f[r * qpr + q];
+    double* d = s2 + r + rows * (4 * q);
+    d[0] += (double)v.x;
+    d[rows] += (double)v.y;
+    d[2 * rows] += (double)v.z;
+    d[3 * rows] += (double)v.w;
+    f[r * qpr + q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -994,15 +1076,17 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   g.c = (int)count;
   g.lc = count == 16 ? 4 : count == 32 ? 5 : 6;
   g.G = G;
-  // tensor memory: D_Y (two buffers: of G l columns for a tile, or of l
-  // columns for a super-plane with Khatri-Rao test matrices), L slots
-  // (T2 H1 x 2l), R_2 (two buffers of T3 l); every accumulator sees at most
-  // 256 MMAs (a tile's D_Y T2 T3 H1 x 16, an R_2 slot T2 H1 x 16)
+  // tensor memory, dense test matrices: D_Y (two buffers of G l columns, one
+  // a tile), L slots (T2 H1 x 2l: S_1 | S_2), R_2 (two buffers of T3 l, one a
+  // tile); every accumulator sees at most 256 MMAs (a tile's D_Y T2 T3 H1 x
+  // 16, an R_2 slot T2 H1 x 16).  Khatri-Rao: D_Y and R_2 (l columns each)
+  // in two buffers, one a super-plane (H1 x 16 MMAs), and the L slots.
   g.kry = r3.kr_nm ? 1 : 0;
   const int ycols = g.kry ? ell : G * ell;
   auto fits = [&](int t2, int t3) {
+    if (g.kry) return 2 * ycols + t2 * g.H1 * 2 * ell + 2 * ell <= 512 && t2 * g.H1 * 16 <= kMaxChainL;
     return 2 * ycols + t2 * g.H1 * 2 * ell + 2 * t3 * ell <= 512 && t2 * g.H1 * 16 <= kMaxChainL &&
-           (g.kry || t2 * t3 * g.H1 * 16 <= kMaxChainL);
+           t2 * t3 * g.H1 * 16 <= kMaxChainL;
   };
   // Each CTA takes a contiguous run of tiles, so the launch lasts as long as
   // the CTA with the most super-planes: pick the shape that minimises that,
@@ -1029,7 +1113,11 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   g.colR = g.colL + T2 * g.H1 * 2 * ell;
   g.tilesL = (g.WL + T2 - 1) / T2;
   g.tilesR = (g.WRg + T3 - 1) / T3;
-  g.runL = std::max<int64_t>(1, kMaxChainL / (T3 * 16));
+  // L slots: accumulating MMAs per slot and tile T3 x 16 (T3 super-planes x
+  // 8 k-steps x hi, lo); TT_FLAG_SHORT_CHAINS: runs of kMaxChainS MMAs keep
+  // S_2's FP32 chains short (its accumulation error enters the middle core
+  // directly)
+  g.runL = std::max<int64_t>(1, (it.short_chains ? kMaxChainS : kMaxChainL) / (T3 * 16));
   g.col[0] = SkTc{s1.rows, s1.off, s1.wdiv, s1.hstride, -1, s1.stream_id, s1.kr_nm ? it.sk0 : -1};
   g.col[1] = SkTc{s2.rows, s2.off, s2.wdiv, s2.hstride, -1, s2.stream_id, s2.kr_nm ? it.sk0 + 1 : -1};
   g.row[0] = SkTc{r2.rows, r2.off, r2.wdiv, r2.hstride, -1, r2.stream_id, r2.kr_nm ? it.sk0 + 2 : -1};
@@ -1151,7 +1239,7 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   const int64_t n2 = g.col[1].rows * g.ell;
   count_launch();
   tc::slab::s2_fold_kernel<<<(unsigned)std::min<int64_t>((n2 / 4 + 255) / 256, 8LL * device_sm_count()), 256, 0,
-                             st>>>(g.ws + g.col[1].off, g.s2stage, n2);
+                             st>>>(g.ws + g.col[1].off, g.s2stage, g.col[1].rows, g.ell);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ constexpr int kTileB = 16 * kS4;         // one 128 x 128 BF16 tile
 constexpr int kStageB = 2 * kTileB;      // hi + lo
 constexpr long long kWaitCycles = 4000000000LL;  // bounded waits (~2 s)
 constexpr int kMaxChainL = 256;                   // accumulating MMAs per accumulator between flushes
+constexpr int kMaxChainS = 32;                    // the same with TT_FLAG_SHORT_CHAINS
 
 struct SkTc {
   int64_t rows, off, wdiv, hstride;

@@ -15,7 +15,8 @@ benchmark times.
   slices (1 GiB each) in shuffled order, Khatri-Rao test matrices, FP16: no
   rank cap, the FP64 path's ranks or at most one more on a bond (the FP32
   accumulation of the tensor cores), X~ within 10 eps of X and of the FP64
-  path.
+  path; with TT_FLAG_SHORT_CHAINS, the FP64 path's ranks and X~ within eps
+  of X.
 * Precision form: random TT, d = 6, n = 24, internal ranks 10, +1e-6 noise
   (1.91e8 FP32 entries), eps = 1e-5, p = 10, rmax = 16 (the small-plane
   kernel), BF16 and TF32: sampled rows of every sketch (S_1..S_3, R_3..R_5;
@@ -135,7 +136,8 @@ def test_streaming_256_pipeline_within_10eps(hilbert256):
     assert rx <= 10 * eps and rf <= 10 * eps
 
 
-def test_streaming_256_fp16_slabs_no_rank_cap(hilbert256):
+@pytest.mark.parametrize("short", [False, True])
+def test_streaming_256_fp16_slabs_no_rank_cap(hilbert256, short):
     """The benchmark's streaming configuration: FP16 with Khatri-Rao test
     matrices, sixteen 1 GiB slabs of 16 slices in shuffled order.  The FP16
     split (2^-22 relative) resolves the rank threshold eps / sqrt(d - 1):
@@ -144,7 +146,8 @@ def test_streaming_256_fp16_slabs_no_rank_cap(hilbert256):
     within 10 eps of X and of the FP64 path's X~."""
     dims, Xd = hilbert256
     eps = STREAMING["eps"]
-    t = TTSketch(dims, x_dtype=torch.float32, prec="fp16", drm="kr", x_scale_log2=S16, **STREAMING)
+    t = TTSketch(dims, x_dtype=torch.float32, prec="fp16", drm="kr", x_scale_log2=S16, short_chains=short,
+                 **STREAMING)
     assert t.kernel_kind(16) == 2
     nd1 = 256 ** 3
     order = list(range(0, 256, 16))
@@ -160,10 +163,13 @@ def test_streaming_256_fp16_slabs_no_rank_cap(hilbert256):
     e_f = t.error(Xf).cpu().numpy()
     del Xf
     rx, rf = (e_x[0] / e_x[1]) ** 0.5, (e_f[0] / e_x[1]) ** 0.5
-    print(f"256^4 FP16 slabs: |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={ranks} fp64 ranks={f.status()[1]}")
+    print(f"256^4 FP16 slabs (short chains {short}): |X~-X|={rx:.2e} |X~-X~fp64|={rf:.2e} ranks={ranks} "
+          f"fp64 ranks={f.status()[1]}")
     r64 = f.status()[1]
     assert st == 0 and all(a <= b <= a + 1 for a, b in zip(r64, ranks)), (r64, ranks)
     assert rx <= 10 * eps and rf <= 10 * eps
+    if short:
+        assert ranks == r64 and rx <= eps
 
 
 @pytest.fixture(scope="module")

@@ -59,9 +59,12 @@ def test_slab_multitile_every_sketch_entry():
     """320 tiles (40 kL blocks x 8 kR-group blocks, the last one ragged) over
     the GPU's CTAs: each CTA walks two or three tiles, changes kL block inside
     its run and flushes the column accumulators; every entry against the
-    oracle."""
+    oracle.  With TT_FLAG_SHORT_CHAINS the column accumulators are flushed
+    after every two tiles, kL by kL behind the next run."""
     _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10), "gauss")
     _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10), "kr", "fp16")
+    _check_slab([128, 160, 240, 16], 16, dict(eps=1e-6, rmax=6, p=10, short_chains=True), "kr", "fp16")
+    _check_slab([256, 64, 64, 32], 16, dict(eps=1e-6, rmax=6, p=10, short_chains=True), "gauss", "fp16")
 
 
 def _check_slab(dims, c, kw, drm, prec="bf16"):
@@ -80,6 +83,7 @@ def _check_slab(dims, c, kw, drm, prec="bf16"):
     t.finalize()
     st, _ = t.status()
     assert st in (0, N.TT_WARN_RANK_CAP)
+    kw = {k: v for k, v in kw.items() if k != "short_chains"}
     widths = OP.sketch_widths(4, OP.clamp_ranks(dims, kw["ranks"]) if "ranks" in kw else None, kw["p"],
                               "eps" in kw, kw.get("rmax"))
     o = OP.sketches(_split(x.astype(np.float64), prec, s), dims, widths, 7, 1, test_fmt=prec, drm=drm)
