@@ -95,7 +95,8 @@ cudaError_t launch_sketch_batched(const Plan& P, const void* const* X, const Bat
   if (e != cudaSuccess) return e;
   BatchCfg c = cfg;
   c.ta = ta;
-  return f64 ? launch_sketch_f64_batched(b, c, lmax, st) : launch_sketch_mma_batched(b, c, st);
+  return f64 ? launch_sketch_f64_batched(b, c, lmax, st)
+             : launch_sketch_mma_batched(b, c, plan_items_host(&P)[0].prec == TT_PREC_FP16, st);
 }
 
 }  // namespace tts

@@ -233,7 +233,7 @@ cudaError_t launch_backward(const Plan& P, int item, const double* dcores, void*
 cudaError_t launch_sketch_batched(const Plan& P, const void* const* X, const BatchCfg& cfg, void* ws,
                                   cudaStream_t st);
 cudaError_t launch_sketch_f64_batched(const BatchLaunch& b, const BatchCfg& cfg, int lmax, cudaStream_t st);
-cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, cudaStream_t st);
+cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, bool f16, cudaStream_t st);
 int64_t batched_tiles_f64(int64_t W, int64_t n1, int64_t cnt, int ta);
 int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int ta);
 cudaError_t launch_finalize_mid_batched(const Plan& P, void* ws, const int* ranks, cudaStream_t st);

@@ -232,6 +232,8 @@ constexpr int gLDX = gTA + 8;
 constexpr int gLDG = TT_MAXL + 8;
 
 // One tile (gTA rows of i_1 x gTB columns of i_d of plane w) into every sketch.
+// F16: the 16-bit operands are FP16 (X scaled by 2^s first), else BF16.
+template <bool F16>
 __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
   constexpr int LDX = gTA + 1;
   float* Xh = fsm;                  // LDX x gTB  (X[a + LDX b])        (TF32)
@@ -240,8 +242,13 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
   uint16_t* XhB = reinterpret_cast<uint16_t*>(fsm);   // gTB x gLDX (16-bit)
   uint16_t* XlB = XhB + gLDX * gTB;
   uint16_t* GsB = XlB + gLDX * gTB;                   // gTA x gLDG (16-bit)
-  const bool f16 = a.prec == TT_PREC_FP16;
-  const bool bf = a.prec == TT_PREC_BF16 || f16;      // 16-bit operands (m16n8k16)
+  const bool bf = a.prec == TT_PREC_BF16 || F16;      // 16-bit operands (m16n8k16)
+  // rounding to the MMA type: FP16 in the F16 instance, else TF32 or BF16
+  const bool tf = a.prec == TT_PREC_TF32;
+  auto rnd = [tf](float x) -> float {
+    if constexpr (F16) return round_f16(x);
+    else return tf ? round_tf32(x) : round_bf16(x);
+  };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t nA = (a.n1 + gTA - 1) / gTA;
   const int64_t nB = (a.cnt + gTB - 1) / gTB;
@@ -256,12 +263,13 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
     for (int o = tid; o < gTA * gTB; o += gThreads) {
       const int ia = o % gTA, ib = o / gTA;
       float v = 0.0f;
-      if (ia < ta && ib < tb) v = __fmul_rn(__ldg(a.X + (a0 + ia) + a.n1 * w + a.Nd1 * (b0 + ib)), a.xscale);
-      const float hi = round_prec(v, a.prec);
-      const float lo = round_prec(__fsub_rn(v, hi), a.prec);
+      if (ia < ta && ib < tb) v = __ldg(a.X + (a0 + ia) + a.n1 * w + a.Nd1 * (b0 + ib));
+      if constexpr (F16) v = __fmul_rn(v, a.xscale);
+      const float hi = rnd(v);
+      const float lo = rnd(__fsub_rn(v, hi));
       if (bf) {  // exact: hi, lo are values of the 16-bit type
-        XhB[ib * gLDX + ia] = f16 ? tc::op16_bits<true>(hi) : tc::op16_bits<false>(hi);
-        XlB[ib * gLDX + ia] = f16 ? tc::op16_bits<true>(lo) : tc::op16_bits<false>(lo);
+        XhB[ib * gLDX + ia] = tc::op16_bits<F16>(hi);
+        XlB[ib * gLDX + ia] = tc::op16_bits<F16>(lo);
       } else {
         Xh[ia + LDX * ib] = hi;
         Xl[ia + LDX * ib] = lo;
@@ -307,13 +315,13 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
           if (bf) {
             float zz[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+            for (int u = 0; u < 4; ++u) zz[u] = (4 * q + u < l) ? rnd(z[u]) : 0.0f;
             uint32_t* gp = reinterpret_cast<uint32_t*>(GsB + r * gLDG + 4 * q);
-            gp[0] = f16 ? tc::f16x2_bits(zz[0], zz[1]) : tc::bf16x2_bits(zz[0], zz[1]);
-            gp[1] = f16 ? tc::f16x2_bits(zz[2], zz[3]) : tc::bf16x2_bits(zz[2], zz[3]);
+            gp[0] = tc::op16x2_bits<F16>(zz[0], zz[1]);
+            gp[1] = tc::op16x2_bits<F16>(zz[2], zz[3]);
           } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? round_prec(z[u], a.prec) : 0.0f;
+            for (int u = 0; u < 4; ++u) Gs[r * LDG + 4 * q + u] = (4 * q + u < l) ? rnd(z[u]) : 0.0f;
           }
         }
       }
@@ -341,7 +349,7 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
               g_ldsm_x2(XhB + off, bh);
               g_ldsm_x2(XlB + off, bl);
             }
-            if (f16) {
+            if constexpr (F16) {
               mma_f16(acc, af, bh[0], bh[1]);
               mma_f16(acc, af, bl[0], bl[1]);
             } else {
@@ -381,14 +389,16 @@ __device__ void mma_tile(const MixArgs& a, int64_t item, float* fsm) {
 }
 
 
+template <bool F16>
 __global__ void __launch_bounds__(gThreads, 4) sketch_mma_kernel(const MixArgs a) {
   extern __shared__ float fsm[];
   const int64_t total = a.W * ((a.n1 + gTA - 1) / gTA) * ((a.cnt + gTB - 1) / gTB);
-  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) mma_tile(a, item, fsm);
+  for (int64_t item = blockIdx.x; item < total; item += gridDim.x) mma_tile<F16>(a, item, fsm);
 }
 
 // Batched form (same scheduling as the FP64 batched kernel): persistent CTAs
 // take `chunk` consecutive tiles of the cost-ordered tile sequence at a time.
+template <bool F16>
 __global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const BatchLaunch b) {
   extern __shared__ float fsm[];
   __shared__ MixArgs sa;
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(gThreads) sketch_mma_batched_kernel(const Batc
         __syncthreads();
         cur = it_idx;
       }
-      mma_tile(sa, t - prefix[pos], fsm);
+      mma_tile<F16>(sa, t - prefix[pos], fsm);
     }
     __syncthreads();
   }
@@ -1364,16 +1374,18 @@ cudaError_t launch_sketch_mma(const Plan& P, int item, const void* X, int64_t fi
   const size_t smem = sizeof(float) * (2 * (gTA + 1) * gTB + (size_t)gTA * (TT_MAXL + 4));
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sketch_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    for (auto f : {sketch_mma_kernel<false>, sketch_mma_kernel<true>}) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
     attr_set = true;
   }
   const int64_t nA = (a.n1 + gTA - 1) / gTA, nB = (count + gTB - 1) / gTB;
   const int64_t total = a.W * nA * nB;
   const int64_t grid = std::min<int64_t>(total, (int64_t)device_sm_count() * 8);
   count_launch();
-  sketch_mma_kernel<<<(unsigned)grid, gThreads, smem, st>>>(a);
+  if (it.prec == TT_PREC_FP16) sketch_mma_kernel<true><<<(unsigned)grid, gThreads, smem, st>>>(a);
+  else sketch_mma_kernel<false><<<(unsigned)grid, gThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1381,17 +1393,19 @@ int64_t batched_tiles_mma(int64_t W, int64_t n1, int64_t cnt, int) {
   return W * ((n1 + gTA - 1) / gTA) * ((cnt + gTB - 1) / gTB);
 }
 
-cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, cudaStream_t st) {
+cudaError_t launch_sketch_mma_batched(const BatchLaunch& b, const BatchCfg& cfg, bool f16, cudaStream_t st) {
   const size_t smem = sizeof(float) * (2 * (gTA + 1) * gTB + (size_t)gTA * (TT_MAXL + 4));
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sketch_mma_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    for (auto f : {sketch_mma_batched_kernel<false>, sketch_mma_batched_kernel<true>}) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
     attr_set = true;
   }
   count_launch();
-  sketch_mma_batched_kernel<<<cfg.ctas_per_sm * device_sm_count(), gThreads, smem, st>>>(b);
+  if (f16) sketch_mma_batched_kernel<true><<<cfg.ctas_per_sm * device_sm_count(), gThreads, smem, st>>>(b);
+  else sketch_mma_batched_kernel<false><<<cfg.ctas_per_sm * device_sm_count(), gThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -173,13 +173,17 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float v[ELL]) {
   if constexpr (ELL == 16) tmem_ld16(taddr, v);
   else tmem_ld8(taddr, v);
 }
+// Two FP32 values rounded to nearest-even and packed, `lo` in the low half
+// (cvt packs its first source into the upper half).
 __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
-  __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&b);
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 __device__ __forceinline__ uint32_t f16x2_bits(float lo, float hi) {
-  __half2 h = __floats2half2_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 // The 16-bit MMA operand type of a kernel instance: BF16, or FP16 when F16.
 template <bool F16>
@@ -197,11 +201,9 @@ __device__ __forceinline__ uint16_t op16_bits(float v) {
 template <bool F16>
 __device__ __forceinline__ void split_hi_lo(float x0, float x1, uint32_t& hb, uint32_t& lb) {
   if constexpr (F16) {
-    const __half2 h = __floats2half2_rn(x0, x1);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
-    hb = *reinterpret_cast<const uint32_t*>(&h);
-    lb = *reinterpret_cast<const uint32_t*>(&l);
+    hb = f16x2_bits(x0, x1);
+    const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hb));
+    lb = f16x2_bits(__fsub_rn(x0, hf.x), __fsub_rn(x1, hf.y));
   } else {
     hb = bf16x2_bits(x0, x1);
     const float h0 = __uint_as_float(hb << 16), h1 = __uint_as_float(hb & 0xFFFF0000u);
