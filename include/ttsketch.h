@@ -214,7 +214,8 @@ tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, in
  * side <= 32) or the slab kernel (d = 4, n_1 in {128, 256}, l in {8, 16},
  * count_last = 16, 32 or 64 -- a 1 GiB slab of the 256^4 FP32 tensor is 16 --
  * or, with Khatri-Rao test matrices, any multiple of 64, taken 64 slices a
- * launch), both BF16 and two-sided; 3 = small-plane kernel (BF16 or TF32,
+ * launch), both BF16 or FP16 and two-sided; 3 = small-plane kernel (BF16,
+ * FP16 or TF32,
  * n_1 and count_last <= 32, widths l_k <= 32, padded to the widest; mma.sync
  * with test-matrix rows shared by many planes staged once per call).  Host
  * only. */

@@ -133,3 +133,24 @@ def test_fp16_meets_eps_where_bf16_caps(drm):
     else:
         assert all(a <= b <= a + 1 for a, b in zip(r64, r16)), (r64, r16)
     assert e16 <= 1e-6
+
+
+def test_short_chains_on_the_plane_kernel():
+    """TT_FLAG_SHORT_CHAINS on the whole-last-mode plane kernel (its L slots
+    flushed after every tile): the same ranks as the default chains and X~
+    within 10 eps of X and of the default's X~ (they differ by FP32
+    accumulation order only)."""
+    dims = [256, 16, 16, 256]
+    x = ti.hilbert_type(dims, np.float32)
+    X = to_dev(x)
+    out = []
+    for short in (False, True):
+        t = TTSketch(dims, eps=1e-6, rmax=6, p=10, seed=2, prec="fp16", x_scale_log2=16, short_chains=short)
+        assert t.kernel_kind() == 2
+        t.pstt2(X)
+        e = t.error(X).cpu().numpy()
+        out.append((t.status(), (e[0] / e[1]) ** 0.5, t.reconstruct().cpu().numpy()))
+    print([(o[0], f"{o[1]:.2e}") for o in out])
+    assert out[0][0][0] == 0 and out[1][0][0] == 0
+    assert out[0][1] <= 1e-5 and out[1][1] <= 1e-5
+    assert np.linalg.norm(out[0][2] - out[1][2]) <= 1e-5 * np.linalg.norm(x)
