@@ -248,6 +248,26 @@ tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_la
 tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
                             tt_stream_t stream);
 
+/* Checkpoint / resume of a stream (no counterpart in the paper, whose
+ * streaming is restartable by construction: the sketch accumulators and the
+ * set of slabs already added are the entire state of PSTT2-onepass between
+ * slabs, Sec. 4.2).  Single-problem one-pass plans only (TT_ERR_UNSUPPORTED
+ * otherwise).
+ *   tt_pstt2_state_size: bytes of the state (a header with the problem, the
+ *     slab bitmap, every sketch in FP64).
+ *   tt_pstt2_export_state: SYNCHRONOUS (waits for `stream`); copies the state
+ *     of the stream begun on ws (after tt_pstt2_begin and any accumulates,
+ *     before tt_pstt2_finalize) into `host` (host memory, `bytes` >= the
+ *     state size).  TT_ERR_STATE when no stream of this plan is open on ws.
+ *   tt_pstt2_import_state: SYNCHRONOUS; opens a stream on ws from an exported
+ *     state instead of tt_pstt2_begin (any plan object and workspace of the
+ *     same problem: every field of the problem must match, else
+ *     TT_ERR_INVALID_ARG); then accumulate the remaining slabs and finalize.
+ *     The result equals the uninterrupted stream's up to summation order. */
+tt_status tt_pstt2_state_size(tt_plan_t plan, size_t* bytes);
+tt_status tt_pstt2_export_state(tt_plan_t plan, const void* ws, void* host, size_t bytes, tt_stream_t stream);
+tt_status tt_pstt2_import_state(tt_plan_t plan, void* ws, const void* host, size_t bytes, tt_stream_t stream);
+
 /* tt_pstt2 without a caller workspace (the paper has no counterpart; this is
  * a library convenience).  For callers that cannot allocate device memory
  * where they call: the workspace is a fixed 32 MiB array inside this library,
@@ -300,7 +320,13 @@ tt_status tt_plan_batch_config(tt_plan_t plan, int ta, int chunk, int ctas_per_s
  * each) and keeps the fastest in the plan, then runs the decomposition once
  * more with it so that cores and ranks hold a valid result.  Synchronises;
  * refused during stream capture (TT_ERR_STATE).  best_out (host, 3 ints, may
- * be NULL) receives the chosen ta, chunk and ctas_per_sm. */
+ * be NULL) receives the chosen ta, chunk and ctas_per_sm.  With the
+ * environment variable TT_TUNE_CACHE naming a text file, a batch whose key
+ * (device, and every item's precision, shape and sketch widths) is in the
+ * file takes the stored shape without timing, and a tuned batch appends
+ * its line "key ta chunk ctas_per_sm".  (TT_LOG=1 in the environment prints
+ * plan layouts, the kernel of every accumulate and the tuner's choice on
+ * stderr.) */
 tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores, int* ranks,
                            tt_stream_t stream, int* best_out);
 

@@ -105,6 +105,25 @@ class TTSketch:
         N.check(N.lib().tt_pstt2_accumulate(self.plan, _ptr(slab), int(first), int(count), _ptr(self.ws),
                                             _stream(stream)), "tt_pstt2_accumulate")
 
+    def export_state(self, stream=None):
+        """The state of the stream in progress (sketches, slabs added) as a
+        host uint8 array; resume it with import_state on any TTSketch of the
+        same problem."""
+        import numpy as np
+        n = C.c_size_t()
+        N.check(N.lib().tt_pstt2_state_size(self.plan, C.byref(n)), "tt_pstt2_state_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        N.check(N.lib().tt_pstt2_export_state(self.plan, _ptr(self.ws), C.c_void_p(buf.ctypes.data), n.value,
+                                              _stream(stream)), "tt_pstt2_export_state")
+        return buf
+
+    def import_state(self, buf, stream=None):
+        """Open a stream from an exported state (instead of begin)."""
+        import numpy as np
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        N.check(N.lib().tt_pstt2_import_state(self.plan, _ptr(self.ws), C.c_void_p(buf.ctypes.data), buf.size,
+                                              _stream(stream)), "tt_pstt2_import_state")
+
     def finalize(self, stream=None):
         N.check(N.lib().tt_pstt2_finalize(self.plan, _ptr(self.ws), _ptr(self.cores), _ptr(self.ranks),
                                           _stream(stream)), "tt_pstt2_finalize")

@@ -10,9 +10,11 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -41,6 +43,23 @@ struct Plan {
 };
 
 static constexpr int64_t kTableOff = 256;  // bytes
+
+// Host log (TT_LOG set to anything but "0" in the environment): plan layouts
+// and the sketch kernel of every accumulate, one line each on stderr.
+static bool log_on() {
+  static const int on = [] {
+    const char* v = std::getenv("TT_LOG");
+    return (v && *v && std::strcmp(v, "0") != 0) ? 1 : 0;
+  }();
+  return on != 0;
+}
+#define TT_LOGF(...)                               \
+  do {                                             \
+    if (log_on()) {                                \
+      std::fprintf(stderr, "ttsketch: " __VA_ARGS__); \
+      std::fputc('\n', stderr);                    \
+    }                                              \
+  } while (0)
 
 // Workspace registry: for every workspace address a plan has used, which plan's
 // tables it holds and whether it holds that plan's saved forward state (the
@@ -527,6 +546,19 @@ static tt_status make_plan(const tt_problem* probs, int count, tt_plan_t* out) {
   int64_t n1max = 1;
   for (const DevItem& it : P->items) n1max = std::max(n1max, it.n[0]);
   P->bcfg = BatchCfg{n1max <= 32 ? 32 : 64, 4, 4};
+  if (log_on()) {
+    static const char* kPrec[] = {"fp64", "tf32", "bf16", "fp16"};
+    for (size_t i = 0; i < P->items.size() && i < 8; ++i) {
+      const DevItem& it = P->items[i];
+      char dims[160] = {0};
+      int o = 0;
+      for (int k = 0; k < it.d && o < 140; ++k) o += std::snprintf(dims + o, sizeof(dims) - o, k ? "x%lld" : "%lld", (long long)it.n[k]);
+      TT_LOGF("plan %llu item %zu: %s %s, %d sketches, %s, passes %d", (unsigned long long)P->id, i, dims,
+              kPrec[it.prec & 3], it.nsk, it.eps_mode ? "tolerance" : "fixed ranks", it.passes);
+    }
+    TT_LOGF("plan %llu: %zu item(s), workspace %.1f MB, %lld core entries", (unsigned long long)P->id,
+            P->items.size(), P->ws_doubles * 8.0 / 1e6, (long long)P->core_entries);
+  }
   *out = reinterpret_cast<tt_plan_t>(P);
   return TT_OK;
 }
@@ -741,9 +773,137 @@ tt_status tt_pstt2_accumulate(tt_plan_t plan, const void* slab, int64_t first_la
     return TT_ERR_INVALID_ARG;
   for (int64_t i = first_last; i < first_last + count_last; ++i)
     if (P->slab_seen[(size_t)i]) return TT_ERR_STATE;
+  if (log_on()) {
+    static const char* kKind[] = {"FP64 SIMT", "generic mma.sync tile", "tcgen05", "small-plane mma.sync"};
+    const int kind = tt_sketch_kernel_kind(plan, count_last);
+    TT_LOGF("plan %llu accumulate slices [%lld, %lld): %s kernel", (unsigned long long)P->id, (long long)first_last,
+            (long long)(first_last + count_last), kKind[kind & 3]);
+  }
   tt_status s = accumulate(*P, 0, slab, first_last, count_last, ws, (cudaStream_t)stream);
   if (s != TT_OK) return s;
   for (int64_t i = first_last; i < first_last + count_last; ++i) P->slab_seen[(size_t)i] = 1;
+  return TT_OK;
+}
+
+// ------------------------------------------------ streaming state export
+// Layout: StateHead, the slab bitmap (n_d bytes, padded to 8), then every
+// sketch of the item (FP64, rows x width, column-major) in plan order.
+namespace {
+struct StateHead {
+  char magic[8];
+  int32_t d, passes, x_dtype, prec, flags, x_scale_log2, rmax, p, status_word, nsk;
+  int64_t n[TT_MAXD];
+  int32_t ranks[TT_MAXD + 1];
+  int32_t pad_;
+  double eps;
+  uint64_t seed;
+  int64_t sketch_doubles;
+};
+const char kStateMagic[8] = {'T', 'T', 'S', 'K', 'S', 'T', '0', '1'};
+
+void state_head(const Plan& P, StateHead& h) {
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kStateMagic, 8);
+  const tt_problem& q = P.probs[0];
+  const DevItem& it = P.items[0];
+  h.d = q.d;
+  h.passes = q.passes;
+  h.x_dtype = q.x_dtype;
+  h.prec = q.prec;
+  h.flags = q.flags;
+  h.x_scale_log2 = it.x_scale_log2;
+  h.rmax = q.eps > 0.0 ? q.rmax : 0;
+  h.p = q.p;
+  h.nsk = it.nsk;
+  for (int k = 0; k < q.d; ++k) h.n[k] = q.n[k];
+  if (!(q.eps > 0.0))
+    for (int k = 0; k <= q.d; ++k) h.ranks[k] = q.ranks[k];
+  h.eps = q.eps;
+  h.seed = q.seed;
+  for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) h.sketch_doubles += P.sketches[si].rows * P.sketches[si].width;
+}
+size_t state_bytes(const Plan& P) {
+  StateHead h;
+  state_head(P, h);
+  const int64_t nd = P.items[0].n[P.items[0].d - 1];
+  return sizeof(StateHead) + (size_t)((nd + 7) / 8 * 8) + sizeof(double) * (size_t)h.sketch_doubles;
+}
+bool state_usable(const Plan* P) { return P && P->items.size() == 1 && P->items[0].passes == 1; }
+}  // namespace
+
+tt_status tt_pstt2_state_size(tt_plan_t plan, size_t* bytes) {
+  Plan* P = as_plan(plan);
+  if (!P || !bytes) return TT_ERR_INVALID_ARG;
+  if (!state_usable(P)) return TT_ERR_UNSUPPORTED;
+  *bytes = state_bytes(*P);
+  return TT_OK;
+}
+
+tt_status tt_pstt2_export_state(tt_plan_t plan, const void* ws, void* host, size_t bytes, tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_export_state");
+  Plan* P = as_plan(plan);
+  if (!P || !ws || !host) return TT_ERR_INVALID_ARG;
+  if (!state_usable(P)) return TT_ERR_UNSUPPORTED;
+  if (bytes < state_bytes(*P)) return TT_ERR_INVALID_ARG;
+  if (!P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  StateHead h;
+  state_head(*P, h);
+  char* out = static_cast<char*>(host);
+  const int64_t nd = P->items[0].n[P->items[0].d - 1];
+  char* bitmap = out + sizeof(StateHead);
+  double* dst = reinterpret_cast<double*>(bitmap + (nd + 7) / 8 * 8);
+  std::memset(bitmap, 0, (size_t)((nd + 7) / 8 * 8));
+  for (int64_t i = 0; i < nd; ++i) bitmap[i] = P->slab_seen[(size_t)i] ? 1 : 0;
+  int word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, (const char*)ws + kStatusOff, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const DevItem& it = P->items[0];
+  for (int si = it.sk0; si < it.sk0 + it.nsk && e == cudaSuccess; ++si) {
+    const DevSketch& d = P->sketches[si];
+    e = cudaMemcpyAsync(dst, (const double*)ws + d.off, sizeof(double) * d.rows * d.width, cudaMemcpyDeviceToHost, st);
+    dst += d.rows * d.width;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  h.status_word = word;
+  std::memcpy(out, &h, sizeof(h));
+  return TT_OK;
+}
+
+tt_status tt_pstt2_import_state(tt_plan_t plan, void* ws, const void* host, size_t bytes, tt_stream_t stream) {
+  NvtxRange nvtx("tt_pstt2_import_state");
+  Plan* P = as_plan(plan);
+  if (!P || !ws || !host) return TT_ERR_INVALID_ARG;
+  if (!state_usable(P)) return TT_ERR_UNSUPPORTED;
+  if (bytes < state_bytes(*P)) return TT_ERR_INVALID_ARG;
+  StateHead mine, theirs;
+  state_head(*P, mine);
+  std::memcpy(&theirs, host, sizeof(theirs));
+  mine.status_word = theirs.status_word;  // the only field that is not the problem's
+  if (std::memcmp(&mine, &theirs, sizeof(mine)) != 0) return TT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  tt_status s = ensure_uploaded(*P, ws, st);
+  if (s != TT_OK) return s;
+  s = zero_sketches(*P, 0, ws, st);  // also the status word and the Khatri-Rao factors
+  if (s != TT_OK) return s;
+  const char* in = static_cast<const char*>(host);
+  const int64_t nd = P->items[0].n[P->items[0].d - 1];
+  const char* bitmap = in + sizeof(StateHead);
+  const double* src = reinterpret_cast<const double*>(bitmap + (nd + 7) / 8 * 8);
+  cudaError_t e = cudaMemcpyAsync((char*)ws + kStatusOff, &theirs.status_word, sizeof(int), cudaMemcpyHostToDevice, st);
+  const DevItem& it = P->items[0];
+  for (int si = it.sk0; si < it.sk0 + it.nsk && e == cudaSuccess; ++si) {
+    const DevSketch& d = P->sketches[si];
+    e = cudaMemcpyAsync((double*)ws + d.off, src, sizeof(double) * d.rows * d.width, cudaMemcpyHostToDevice, st);
+    src += d.rows * d.width;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host buffer may go away after the call
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int64_t i = 0; i < nd; ++i) P->slab_seen[(size_t)i] = bitmap[i] ? 1 : 0;
+  P->begun = true;
+  P->stream_tables = false;
+  P->stream_ws = ws;
+  plan_mark_forward(P, ws, false);
   return TT_OK;
 }
 
@@ -825,6 +985,50 @@ tt_status tt_pstt2_batched(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   return TT_OK;
 }
 
+// Autotuner cache (TT_TUNE_CACHE = path of a text file): one line "key ta
+// chunk ctas_per_sm" per tuned batch; the key hashes the device (SM count,
+// compute capability) and every item's precision, shape and sketch widths.
+static std::string tune_key(const Plan& P) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xFF);
+      h *= 1099511628211ull;
+    }
+  };
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  mix(device_sm_count());
+  mix(major * 10 + minor);
+  mix((int64_t)P.items.size());
+  for (const DevItem& it : P.items) {
+    mix(it.prec);
+    mix(it.d);
+    for (int k = 0; k < it.d; ++k) mix(it.n[k]);
+    for (int si = it.sk0; si < it.sk0 + it.nsk; ++si) mix(P.sketches[si].width);
+  }
+  char buf[24];
+  std::snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+  return buf;
+}
+
+static bool tune_cache_find(const char* path, const std::string& key, BatchCfg& out) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char k[64];
+  int ta, chunk, cps;
+  bool found = false;
+  while (std::fscanf(f, "%63s %d %d %d", k, &ta, &chunk, &cps) == 4)
+    if (key == k) {
+      out = BatchCfg{ta, chunk, cps};
+      found = true;  // the last entry for a key wins
+    }
+  std::fclose(f);
+  return found;
+}
+
 tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, double* cores, int* ranks,
                            tt_stream_t stream, int* best_out) {
   NvtxRange nvtx("tt_plan_autotune");
@@ -851,6 +1055,25 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
       for (int chunk : {1, 4, 16})
         for (int cps : {2, 4, 8}) cands.push_back(BatchCfg{ta, chunk, cps});
     }
+  }
+  const char* cache = std::getenv("TT_TUNE_CACHE");
+  const std::string key = (cache && *cache) ? tune_key(*P) : std::string();
+  BatchCfg cached{0, 0, 0};
+  if (!key.empty() && tune_cache_find(cache, key, cached)) {
+    for (const BatchCfg& c : cands)
+      if (c.ta == cached.ta && c.chunk == cached.chunk && c.ctas_per_sm == cached.ctas_per_sm) {
+        TT_LOGF("plan %llu autotune: cached shape %d %d %d (%s)", (unsigned long long)P->id, c.ta, c.chunk,
+                c.ctas_per_sm, key.c_str());
+        P->bcfg = c;
+        if (best_out) {
+          best_out[0] = c.ta;
+          best_out[1] = c.chunk;
+          best_out[2] = c.ctas_per_sm;
+        }
+        s = batched_run(*P, X_ptrs, P->bcfg, ws, cores, ranks, st);
+        if (s == TT_OK) plan_mark_forward(P, ws, true);
+        return s;
+      }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return TT_ERR_CUDA;
@@ -881,6 +1104,14 @@ tt_status tt_plan_autotune(tt_plan_t plan, const void* const* X_ptrs, void* ws, 
   cudaEventDestroy(e1);
   if (s != TT_OK) return s;
   P->bcfg = cands[(size_t)best_i];
+  TT_LOGF("plan %llu autotune: best shape %d %d %d, %.3f ms", (unsigned long long)P->id, P->bcfg.ta, P->bcfg.chunk,
+          P->bcfg.ctas_per_sm, best);
+  if (!key.empty()) {
+    if (FILE* f = std::fopen(cache, "a")) {
+      std::fprintf(f, "%s %d %d %d\n", key.c_str(), P->bcfg.ta, P->bcfg.chunk, P->bcfg.ctas_per_sm);
+      std::fclose(f);
+    }
+  }
   if (best_out) {
     best_out[0] = P->bcfg.ta;
     best_out[1] = P->bcfg.chunk;

@@ -395,3 +395,46 @@ def test_khatri_rao_plans():
     arr = (N.tt_problem * 2)(krq, krq)
     h = C.c_void_p()
     assert L.tt_sketch_plan_batched(arr, 2, C.byref(h)) == N.TT_ERR_UNSUPPORTED
+
+
+def test_stream_state_checks_on_the_host():
+    """Checkpoint calls: size of the state (header + slab bitmap + every sketch
+    in FP64), refusal for batched and two-pass plans, argument and state errors
+    before any device work (no stream is open on a fresh plan)."""
+    L = N.lib()
+    st, h = plan([40, 7, 6, 70], ranks=[1, 4, 5, 4, 1], p=6)
+    assert st == N.TT_OK
+    n = C.c_size_t()
+    N.check(L.tt_pstt2_state_size(h, C.byref(n)), "size")
+    sk = sketch_list(h)
+    assert n.value == 272 + 72 + 8 * sum(rows * w for _, _, rows, w, _ in sk)
+    dummy, null = C.c_void_p(256), C.c_void_p(None)
+    buf = (C.c_ubyte * n.value)()
+    assert L.tt_pstt2_state_size(h, None) == N.TT_ERR_INVALID_ARG
+    assert L.tt_pstt2_export_state(h, dummy, buf, n.value - 1, null) == N.TT_ERR_INVALID_ARG
+    assert L.tt_pstt2_export_state(h, null, buf, n.value, null) == N.TT_ERR_INVALID_ARG
+    assert L.tt_pstt2_export_state(h, dummy, buf, n.value, null) == N.TT_ERR_STATE      # nothing begun
+    assert L.tt_pstt2_import_state(h, dummy, buf, n.value - 1, null) == N.TT_ERR_INVALID_ARG
+    assert L.tt_pstt2_import_state(h, dummy, buf, n.value, null) == N.TT_ERR_INVALID_ARG  # no header
+    L.tt_plan_destroy(h)
+    st, h2 = plan([40, 7, 6, 70], ranks=[1, 4, 5, 4, 1], p=6, passes=2)
+    assert L.tt_pstt2_state_size(h2, C.byref(n)) == N.TT_ERR_UNSUPPORTED
+    L.tt_plan_destroy(h2)
+
+
+def test_tt_log_prints_plan_layouts(tmp_path):
+    """TT_LOG=1: one stderr line per plan item and one for the plan (host only)."""
+    import subprocess
+    import sys
+    code = ("import ctypes as C; from paper_2111_10448_gb300 import _native as N; "
+            "q = N.make_problem([64, 8, 8, 64], eps=1e-6, rmax=6, p=10, prec=N.TT_PREC_FP16, x_scale_log2=3); "
+            "h = C.c_void_p(); N.check(N.lib().tt_sketch_plan(C.byref(q), C.byref(h)), 'plan'); "
+            "N.lib().tt_plan_destroy(h)")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TT_LOG="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "ttsketch: plan" in r.stderr and "64x8x8x64 fp16" in r.stderr, r.stderr
+    env["TT_LOG"] = "0"
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "ttsketch:" not in r.stderr

@@ -198,3 +198,34 @@ def test_batched_small_plane_every_block_shape(shape):
         o = OP.pstt2(x64, pr["dims"], eps=EPS, rmax=RMAX, p=P, seed=pr["seed"], passes=1)
         err = np.linalg.norm(full(t.core_list(b)) - OT.tt_full(o["cores"])) / np.linalg.norm(x64)
         assert err <= 10 * EPS, (shape, b, pr["dims"], err)
+
+
+@pytest.mark.gpu
+def test_autotuner_cache(tmp_path, monkeypatch):
+    """TT_TUNE_CACHE: the first call tunes and appends one line; a second plan
+    of the same batch takes the stored shape without timing (a planted line,
+    a valid candidate, wins over the tuned one) and still leaves a valid
+    decomposition."""
+    xs, probs = make_batch(12, cap=100_000, seed=29, dtype=np.float32)
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("TT_TUNE_CACHE", str(cache))
+    dev = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in xs]
+    t = TTSketch(None, batch=probs, x_dtype=torch.float32, prec="bf16")
+    best = t.autotune(dev)
+    lines = cache.read_text().split("\n")
+    lines = [l for l in lines if l]
+    assert len(lines) == 1 and tuple(int(v) for v in lines[0].split()[1:]) == best
+    key = lines[0].split()[0]
+    if best[0] in (1, 2, 4, 8):   # small-plane batch: (kR values per block, blocks per grab, 1)
+        planted = (1, 1, 1) if best != (1, 1, 1) else (1, 4, 1)
+    else:                         # generic tile kernel: (64, tiles per grab, CTAs per SM)
+        planted = (64, 1, 2) if best != (64, 1, 2) else (64, 4, 4)
+    with open(cache, "a") as f:
+        f.write(f"{key} {planted[0]} {planted[1]} {planted[2]}\n")
+    t2 = TTSketch(None, batch=probs, x_dtype=torch.float32, prec="bf16")
+    assert t2.autotune(dev) == planted
+    assert len([l for l in cache.read_text().split("\n") if l]) == 2
+    torch.cuda.synchronize()
+    for b in range(len(xs)):
+        g1, g2 = full(t.core_list(b)), full(t2.core_list(b))
+        assert np.linalg.norm(g1 - g2) <= 1e-5 * np.linalg.norm(xs[b])
