@@ -154,3 +154,23 @@ def test_short_chains_on_the_plane_kernel():
     assert out[0][0][0] == 0 and out[1][0][0] == 0
     assert out[0][1] <= 1e-5 and out[1][1] <= 1e-5
     assert np.linalg.norm(out[0][2] - out[1][2]) <= 1e-5 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("kw", [dict(passes=2), dict(one_sided=True), dict(one_sided=True, passes=2)])
+def test_two_pass_and_one_sided_fp16(kw):
+    """FP16 sketches feeding the two-pass middle core (a second FP64 pass over
+    X itself) and the one-sided PSTT forms: within 10 eps of X and of the FP64
+    path with the same options."""
+    dims, eps = [9] * 6, 1e-5
+    x = ti.random_tt(dims, [1, 9, 10, 10, 10, 9, 1], seed=0, noise=1e-6).astype(np.float32)
+    X = to_dev(x)
+    s = _rule(x)
+    t = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, prec="fp16", x_scale_log2=s, **kw).pstt2(X)
+    f = TTSketch(dims, eps=eps, rmax=16, p=10, seed=1, prec="fp64", x_dtype=torch.float32, **kw).pstt2(X)
+    x64 = x.astype(np.float64)
+    xt = t.reconstruct().cpu().numpy()
+    e_x = np.linalg.norm(xt - x64) / np.linalg.norm(x64)
+    e_f = np.linalg.norm(xt - f.reconstruct().cpu().numpy()) / np.linalg.norm(x64)
+    print(kw, f"|X~-X|={e_x:.2e} |X~-X~fp64|={e_f:.2e} ranks={t.status()[1]}")
+    assert t.status()[0] in (0, N.TT_WARN_RANK_CAP)
+    assert e_x <= 10 * eps and e_f <= 10 * eps
