@@ -825,6 +825,11 @@ def run_gpu(a):
         tf = P.TTSketch(dims, prec=a.prec, drm=a.drm, short_chains=True, **kw)
         forms[f"{a.drm}_{slab}_slices_short_chains"] = measure_form(tf, slab, max(3, min(a.steps, 10)), 2)
         del tf
+        # the headline's other 16-bit split: BF16 (2^-17, below the rank threshold's resolution)
+        other = "bf16" if a.prec == "fp16" else "fp16"
+        tf = P.TTSketch(dims, prec=other, drm=a.drm, **kw)
+        forms[f"{a.drm}_{slab}_slices_{other}"] = measure_form(tf, slab, max(3, min(a.steps, 10)), 2)
+        del tf
         out["forms"] = forms
 
     # ---- FP64 GPU path, same eps, same slabs (one step after one warm-up)
