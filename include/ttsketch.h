@@ -203,7 +203,9 @@ tt_status tt_plan_core_layout(tt_plan_t plan, int item, int64_t* core_off, int* 
  * Omega_k, 1 = row sketch R_k = X_k^T Psi_k.  For tests and inspection; the
  * contents are valid after an accumulate and before the next finalize (the
  * finalize factorises basis sketches in place).  TT_ERR_INVALID_ARG past
- * the last sketch. */
+ * the last sketch.  During a stream, call tt_pstt2_sync first: the slab
+ * kernel stages part of S_{d*}'s partial sums in FP32 and adds them in
+ * batches of a few launches. */
 tt_status tt_plan_sketch_info(tt_plan_t plan, int item, int index, int* type, int* k, int64_t* rows,
                               int* width, int64_t* byte_off);
 
@@ -267,6 +269,12 @@ tt_status tt_pstt2_finalize(tt_plan_t plan, void* ws, double* cores, int* ranks,
  *     TT_ERR_INVALID_ARG); then accumulate the remaining slabs and finalize.
  *     The result equals the uninterrupted stream's up to summation order. */
 tt_status tt_pstt2_state_size(tt_plan_t plan, size_t* bytes);
+/* Complete the sketches of the stream in progress on ws (asynchronous on
+ * `stream`): partial sums still staged by the slab kernel are added into
+ * the FP64 sketches.  Needed only to read sketches between accumulates
+ * (tt_plan_sketch_info); finalize and export do it themselves.  TT_OK
+ * without work when no stream of this plan is open on ws. */
+tt_status tt_pstt2_sync(tt_plan_t plan, void* ws, tt_stream_t stream);
 tt_status tt_pstt2_export_state(tt_plan_t plan, const void* ws, void* host, size_t bytes, tt_stream_t stream);
 tt_status tt_pstt2_import_state(tt_plan_t plan, void* ws, const void* host, size_t bytes, tt_stream_t stream);
 

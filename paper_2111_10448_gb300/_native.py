@@ -73,6 +73,7 @@ _SIGS = {
     "tt_plan_autotune": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "tt_pstt2_begin": (C.c_int, [_P, _P, _P]),
     "tt_pstt2_state_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "tt_pstt2_sync": (C.c_int, [_P, _P, _P]),
     "tt_pstt2_export_state": (C.c_int, [_P, _P, _P, C.c_size_t, _P]),
     "tt_pstt2_import_state": (C.c_int, [_P, _P, _P, C.c_size_t, _P]),
     "tt_pstt2_accumulate": (C.c_int, [_P, _P, C.c_int64, C.c_int64, _P, _P]),

@@ -176,9 +176,10 @@ class TTSketch:
                 "tt_reconstruct_backward")
         return dc
 
-    def sketches(self, item=0):
+    def sketches(self, item=0, stream=None):
         """Every sketch of one item, read from the workspace: list of
         (type, k, tensor rows x width) -- valid between accumulate and finalize."""
+        N.check(N.lib().tt_pstt2_sync(self.plan, _ptr(self.ws), _stream(stream)), "tt_pstt2_sync")
         out = []
         i = 0
         while True:

@@ -1033,6 +1033,10 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
   const DevSketch* sks = plan_sketches_host(&P);
   const int nitems = plan_num_items(&P);
   cudaError_t e;
+  if (nitems == 1) {  // the slab kernel's staged S_2 partials not yet folded
+    e = fold_s2_staging(P, 0, ws, st);
+    if (e != cudaSuccess) return e;
+  }
   static bool attr = false;
   if (!attr) {
     e = cudaFuncSetAttribute(tsqr_level_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsqrSmemMax);

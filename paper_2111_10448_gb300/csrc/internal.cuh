@@ -197,6 +197,8 @@ struct Plan;
 const DevItem* plan_items_host(const Plan* p);
 int plan_num_items(const Plan* p);
 bool& plan_stream_tables(Plan& P);
+int& plan_pending_folds(Plan& P);   // slab launches whose S_2 partials are still in the FP32 staging
+cudaError_t fold_s2_staging(const Plan& P, int item, void* ws, cudaStream_t st);
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_sketch_f64(const Plan& P, int item, const void* X, int64_t first, int64_t count,

@@ -37,6 +37,7 @@ struct Plan {
   std::vector<char> slab_seen;
   bool begun = false;
   bool stream_tables = false;        // staged tables of the slab kernel valid for this decomposition
+  int pending_folds = 0;             // slab launches not yet folded from S_2's FP32 staging
   const void* stream_ws = nullptr;   // workspace of the streaming decomposition begun last
   const void* forward_ws = nullptr;  // workspace of the last completed forward call
   BatchCfg bcfg{64, 4, 4};  // batched sketch launch shape (tt_plan_autotune)
@@ -627,6 +628,7 @@ int device_sm_count() {
 // generated by the first accumulate of a decomposition and reused by the
 // others (begin / tt_pstt2 clear the flag).
 bool& plan_stream_tables(Plan& P) { return P.stream_tables; }
+int& plan_pending_folds(Plan& P) { return P.pending_folds; }
 
 // Start of a decomposition: clear the status word (so that a bit raised by
 // the sketch kernels survives until tt_query_status) and the sketches.
@@ -645,6 +647,7 @@ static tt_status zero_sketches(Plan& P, int item, void* ws, cudaStream_t st) {
   if (it.s2stage_doubles > 0) {
     cudaError_t e = cudaMemsetAsync(base + it.off_s2stage, 0, sizeof(double) * it.s2stage_doubles, st);
     if (e != cudaSuccess) return cuda_status(e);
+    P.pending_folds = 0;
   }
   // Khatri-Rao factors of the call (every later kernel of the call reads them)
   return cuda_status(launch_kr_tables(P, item, ws, st));
@@ -831,6 +834,13 @@ size_t state_bytes(const Plan& P) {
 bool state_usable(const Plan* P) { return P && P->items.size() == 1 && P->items[0].passes == 1; }
 }  // namespace
 
+tt_status tt_pstt2_sync(tt_plan_t plan, void* ws, tt_stream_t stream) {
+  Plan* P = as_plan(plan);
+  if (!P || !ws) return TT_ERR_INVALID_ARG;
+  if (P->items.size() != 1 || !P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_OK;
+  return cuda_status(fold_s2_staging(*P, 0, ws, (cudaStream_t)stream));
+}
+
 tt_status tt_pstt2_state_size(tt_plan_t plan, size_t* bytes) {
   Plan* P = as_plan(plan);
   if (!P || !bytes) return TT_ERR_INVALID_ARG;
@@ -847,6 +857,8 @@ tt_status tt_pstt2_export_state(tt_plan_t plan, const void* ws, void* host, size
   if (bytes < state_bytes(*P)) return TT_ERR_INVALID_ARG;
   if (!P->begun || P->stream_ws != ws || !plan_owns(P, ws)) return TT_ERR_STATE;
   cudaStream_t st = (cudaStream_t)stream;
+  tt_status fs = cuda_status(fold_s2_staging(*P, 0, const_cast<void*>(ws), st));
+  if (fs != TT_OK) return fs;
   StateHead h;
   state_head(*P, h);
   char* out = static_cast<char*>(host);

@@ -993,6 +993,8 @@ __global__ void slab_ytab_kernel(const SlabArgs g) {
   }
 }
 
+constexpr int kFoldEvery = 4;  // slab launches between folds of S_2's FP32 staging
+
 // S_2 += the launch's FP32 staging (row-major, l floats a row), which is
 // cleared for the next launch; four columns of a row a thread, consecutive
 // threads on consecutive rows (coalesced FP64 columns).
@@ -1236,10 +1238,29 @@ static cudaError_t launch_slab_one(const Plan& P, int item, const void* X, int64
   k<<<grid, threads, tc::slab::kSmemBytes, st>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t n2 = g.col[1].rows * g.ell;
+  // S_2's FP32 staging is added into the FP64 sketch every kFoldEvery
+  // launches (each adds about four CTA partials an entry, so the staged sums
+  // hold at most ~16 FP32 terms) and before anything reads S_2
+  if (++plan_pending_folds(const_cast<Plan&>(P)) >= tc::slab::kFoldEvery) return fold_s2_staging(P, item, ws, st);
+  return cudaSuccess;
+}
+
+// S_2 += its FP32 staging, staging cleared (a no-op when nothing is pending).
+cudaError_t fold_s2_staging(const Plan& P, int item, void* ws, cudaStream_t st) {
+  int& pending = plan_pending_folds(const_cast<Plan&>(P));
+  if (pending == 0) return cudaSuccess;
+  const DevItem& it = plan_items_host(&P)[item];
+  if (it.s2stage_doubles <= 0) {
+    pending = 0;
+    return cudaSuccess;
+  }
+  const DevSketch& s2 = plan_sketches_host(&P)[it.sk0 + 1];
+  const int64_t n2 = s2.rows * s2.width;
   count_launch();
   tc::slab::s2_fold_kernel<<<(unsigned)std::min<int64_t>((n2 / 4 + 255) / 256, 8LL * device_sm_count()), 256, 0,
-                             st>>>(g.ws + g.col[1].off, g.s2stage, g.col[1].rows, g.ell);
+                             st>>>((double*)ws + s2.off, reinterpret_cast<float*>((double*)ws + it.off_s2stage),
+                                   s2.rows, s2.width);
+  pending = 0;
   return cudaGetLastError();
 }
 
