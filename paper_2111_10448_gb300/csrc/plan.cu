@@ -254,10 +254,12 @@ static tt_status build_item(Plan& P, const tt_problem& q0, WsAlloc& ws, int64_t&
     // Row blocks of 128 rows, or 4 l when that is more (a multiple of 32,
     // capped at 192 so that a root block and its l x l work matrices fit in
     // shared memory for l <= 64): each tree level shrinks the rows 3-8x, and a
-    // block's QR -- a chain of FP64 steps on one SM -- stays short.  A
-    // 65536-row sketch of width 16 gives 512 leaf blocks (16 KB each, several
-    // resident per SM) and four levels.
-    const int bl = std::min(192, std::max(128, (4 * w + 31) / 32 * 32));
+    // block's QR -- a chain of FP64 steps on one SM -- stays short.  Widths up
+    // to 16 take 256-row blocks: a level costs about its chain whatever the
+    // rows, so fewer levels win (a 65536-row sketch of width 16: 256 leaf
+    // blocks and three levels, 46 us less a 256^4 step than 128-row blocks'
+    // four).
+    const int bl = w <= 16 ? 256 : std::min(192, std::max(128, (4 * w + 31) / 32 * 32));
     if (8 * ((int64_t)(bl + 1) * w + 32 + 2 * TT_MAXL + 3LL * w * w) > kTsqrSmemMax) return TT_ERR_UNSUPPORTED;
     s.bl = bl;
     int64_t m = s.rows;
