@@ -387,16 +387,25 @@ __global__ void __launch_bounds__(kThreads) sketch_unscale_kernel(char* wsb, int
   double* ws = reinterpret_cast<double*>(wsb);
   const double f = ldexp(1.0, -it.x_scale_log2);
   int bad = 0;
+  auto scale = [&](double& x) {
+    const double v = x * f;
+    const bool fin = isfinite(v);
+    bad |= fin ? 0 : 1;
+    x = fin ? v : 0.0;
+  };
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& d = sks[it.sk0 + s];
-    double* p = ws + d.off;
+    double* p = ws + d.off;  // 16-byte aligned (workspace regions are)
     const int64_t n = d.rows * d.width;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-      const double v = p[e] * f;
-      const bool fin = isfinite(v);
-      bad |= fin ? 0 : 1;
-      p[e] = fin ? v : 0.0;
+    double2* p2 = reinterpret_cast<double2*>(p);
+    for (int64_t e = tid; e < n / 2; e += nthr) {
+      double2 v = p2[e];
+      scale(v.x);
+      scale(v.y);
+      p2[e] = v;
     }
+    if ((n & 1) && tid == 0) scale(p[n - 1]);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) flag_status(wsb, ST_NONFINITE);
 }
@@ -1051,7 +1060,7 @@ cudaError_t launch_finalize(const Plan& P, void* ws, double* cores, int* ranks, 
     for (int i = 0; i < nitems; ++i) any16 = any16 || plan_items_host(&P)[i].prec == TT_PREC_FP16;
     if (any16) {
       count_launch();
-      sketch_unscale_kernel<<<dim3((unsigned)(2 * device_sm_count()), (unsigned)nitems), kThreads, 0, st>>>(wsb, 0);
+      sketch_unscale_kernel<<<dim3((unsigned)(4 * device_sm_count()), (unsigned)nitems), kThreads, 0, st>>>(wsb, 0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
