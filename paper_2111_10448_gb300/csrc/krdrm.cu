@@ -19,16 +19,19 @@ namespace {
 
 constexpr int64_t kTableOffB = 256;
 
+// blockIdx.y = the (sketch, factor) pair, in plan order
 __global__ void kr_factor_kernel(char* wsb, int item) {
   const DevTables& T = *reinterpret_cast<const DevTables*>(wsb + kTableOffB);
   const DevItem& it = reinterpret_cast<const DevItem*>(wsb + T.off_items)[item];
   const DevSketch* sks = reinterpret_cast<const DevSketch*>(wsb + T.off_sketches);
   const bool f64 = it.prec == TT_PREC_FP64;
+  int pair = 0;
   for (int s = 0; s < it.nsk; ++s) {
     const DevSketch& sk = sks[it.sk0 + s];
     if (sk.kr_nm == 0) continue;
     const int qpr = sk.kr_lp / 4;
-    for (int t = 0; t < sk.kr_nm; ++t) {
+    for (int t = 0; t < sk.kr_nm; ++t, ++pair) {
+      if (pair != (int)blockIdx.y) continue;
       const uint64_t base = (uint64_t)(0x80000000u + (uint32_t)(sk.kr_mode0 + t)) << 32;
       const int64_t total = sk.kr_n[t] * qpr;
       for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -67,9 +70,11 @@ cudaError_t launch_kr_tables(const Plan& P, int item, void* ws, cudaStream_t st)
     for (int t = 0; t < sk.kr_nm; ++t) most = std::max<int64_t>(most, sk.kr_n[t] * (sk.kr_lp / 4));
   }
   if (!any) return cudaSuccess;
+  int pairs = 0;
+  for (int s = 0; s < it.nsk; ++s) pairs += sks[it.sk0 + s].kr_nm;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((most + 255) / 256, 4LL * device_sm_count()));
   count_launch();
-  kr_factor_kernel<<<grid, 256, 0, st>>>((char*)ws, item);
+  kr_factor_kernel<<<dim3((unsigned)grid, (unsigned)pairs), 256, 0, st>>>((char*)ws, item);
   return cudaGetLastError();
 }
 

@@ -1092,16 +1092,22 @@ bool plan_slab(const Plan& P, int item, int64_t count, slab::SlabArgs* out) {
   };
   // Each CTA takes a contiguous run of tiles, so the launch lasts as long as
   // the CTA with the most super-planes: pick the shape that minimises that,
-  // weighted by the R_2 flush traffic (2048 FP64 atomics per kR group and tile,
-  // i.e. about 1 / T2 of a super-plane's own cost); ties: the larger T2.
+  // weighted by the per-tile cost; ties: the larger T2.  Dense: the R_2 flush
+  // traffic (2048 FP64 atomics per kR group and tile, about 1 / T2 of a
+  // super-plane's own cost).  Khatri-Rao: R_2 is drained per super-plane
+  // whatever the shape, and a tile costs about 0.14 of a super-plane
+  // (measured on 1 GiB slabs of the 256^4 tensor: T2 = 5, 7 and 2 gave 0.754,
+  // 0.746 and 0.689 of HBM); below four kL values a tile the L slots' drain
+  // at every run change stalls the MMAs, so those shapes are left out.
   const int64_t sms = device_sm_count();
   int T2 = 0, T3 = 0;
   double best = 1e300;
   for (int t2 = 1; t2 <= 8; ++t2)
     for (int t3 = 1; t3 <= 8; ++t3) {
       if (t2 > g.WL || t3 > g.WRg || !fits(t2, t3)) continue;
+      if (g.kry && t2 < std::min<int64_t>(4, g.WL)) continue;
       const int64_t tiles = ((g.WL + t2 - 1) / t2) * ((g.WRg + t3 - 1) / t3);
-      const double cost = (double)((tiles + sms - 1) / sms * t2 * t3) * (1.0 + 0.5 / t2);
+      const double cost = (double)((tiles + sms - 1) / sms * t2 * t3) * (1.0 + (g.kry ? 0.14 : 0.5) / t2);
       if (cost < best || (cost == best && t2 > T2)) {
         best = cost;
         T2 = t2;
