@@ -67,6 +67,16 @@ def test_slab_multitile_every_sketch_entry():
     _check_slab([256, 64, 64, 32], 16, dict(eps=1e-6, rmax=6, p=10, short_chains=True), "gauss", "fp16")
 
 
+def test_slab_headline_launch_shape_every_sketch_entry():
+    """The launch shape of the 256^4 stream in 1 GiB slabs, on a 256^3 x 32
+    tensor (two 16-slice slabs): 256 kL values x 32 kR groups, FP16 split,
+    Khatri-Rao test matrices, eps 1e-6, rmax 6, p 10.  The planner's tile of
+    5 kL values leaves a ragged block of one kL value, and each of the 152
+    CTAs walks about 11 tiles (55 super-planes, L chains of 176 MMAs); every
+    entry of the four sketches against the oracle."""
+    _check_slab([256, 256, 256, 32], 16, dict(eps=1e-6, rmax=6, p=10), "kr", "fp16")
+
+
 def _check_slab(dims, c, kw, drm, prec="bf16"):
     n1, n2, n3, n4 = dims
     x = ti.random_tt(dims, [1, 3, 3, 3, 1], seed=5, noise=1e-5).astype(np.float32)
