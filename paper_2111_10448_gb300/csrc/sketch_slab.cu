@@ -35,7 +35,8 @@
 // row product applied by the epilogue as a column scale per super-plane.
 //
 // Accumulators: one L slot per (kL of the tile, i_1 half), kept for runL
-// tiles; the R_2 slots (one per kR group of the tile) and the D_Y block of a
+// tiles (Khatri-Rao: each slot drained by the epilogue right after its last
+// super-plane of the run, overlapping the rest of the tile); the R_2 slots (one per kR group of the tile) and the D_Y block of a
 // tile are double-buffered with the epilogue; every accumulator sees at most
 // 256 MMAs before a flush.  Khatri-Rao: the tensor cores' FP32 accumulation
 // adds ~2e-8 relative error per accumulating MMA (measured), so D_Y and R_2
@@ -598,7 +599,9 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       const int64_t tl = l_group(g, t);
       if (tl != cur_tl) {
         if (cur_tl >= 0) {
-          if (elect_one()) mma_commit(bar(TML_FULL));
+          // Khatri-Rao: the epilogue drains each slot after its last
+          // super-plane of the run (no whole-run commit)
+          if (!KRY && elect_one()) mma_commit(bar(TML_FULL));
           __syncwarp();
           ++lf;
         }
@@ -698,7 +701,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         __syncwarp();
       }
     }
-    if (ok && cur_tl >= 0) {
+    if (!KRY && ok && cur_tl >= 0) {
       if (elect_one()) mma_commit(bar(TML_FULL));
       __syncwarp();
     }
@@ -714,36 +717,37 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
     const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
     const uint32_t colYB = (uint32_t)(KRY ? ell : g.G * ell);
     // L slots of kL block [kL0, kL0 + nA): S_1 (rows i_1, pre-summed over the
-    // kL values) and S_2 (rows i_1 + n_1 kL)
-    // Khatri-Rao: kL by kL, each kL's slots handed back as soon as they are
-    // read (the MMA warp waits for a slot only before its first MMA of the
-    // next run), S_1 summed in shared memory over every run of the CTA and
-    // added to the sketch once at its end (its rows are the same for every
-    // run); dense: half by half (the R_3 area holds no room for S_1's sums),
-    // the slots handed back at the end.
+    // kL values) and S_2 (rows i_1 + n_1 kL).
+    // Khatri-Rao: slot a is drained right after the run's last super-plane
+    // of kL0 + a (its MMAs are complete once that super-plane's D_Y is), so
+    // the drain overlaps the rest of the tile and the MMA warp, which waits
+    // for a slot only before its first MMA of the next run, never stalls on
+    // it; S_1 is summed in shared memory over every run of the CTA and added
+    // to the sketch once at its end (its rows are the same for every run).
+    auto drain_slot = [&](int64_t kL, int a) {
+      float* s1p = reinterpret_cast<float*>(sm + kOffS1);
+      for (int h1 = 0; h1 < g.H1; ++h1) {
+        float v[ell];
+        tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL), v);
+#pragma unroll
+        for (int j = 0; j < ell; ++j) s1p[(h1 * ell + j) * 128 + lrow] += v[j];
+        tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + ell), v);
+        // S_2: four-wide FP32 reductions into the row-major staging copy
+        // (FP64 atomics here cost the launch ~25 us of drain)
+        red_add_row<ell>(g.s2stage + (h1 * 128 + lrow + g.n1 * kL) * ell, v);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(TML_EMPTY + a));
+    };
+    // Dense: half by half (the R_3 area holds no room for S_1's sums), after
+    // the run's last tile, the slots handed back at the end.
     auto flush_L = [&](int64_t kL0, int nA, uint32_t lf) -> bool {
       if (!mbar_wait(bar(TML_FULL), lf & 1, abort_flag, g.status)) return false;
       tc_fence_after();
       const SkTc& sk1 = s_col[0];
       double* dst1 = g.ws + sk1.off;
-      if constexpr (KRY) {
-        float* s1p = reinterpret_cast<float*>(sm + kOffS1);
-        for (int a = 0; a < nA; ++a) {
-          for (int h1 = 0; h1 < g.H1; ++h1) {
-            float v[ell];
-            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL), v);
-#pragma unroll
-            for (int j = 0; j < ell; ++j) s1p[(h1 * ell + j) * 128 + lrow] += v[j];
-            tmem_ld_cols<ell>(tmem + lane_addr + (uint32_t)g.colL + (uint32_t)((a * g.H1 + h1) * NL + ell), v);
-            // S_2: four-wide FP32 reductions into the row-major staging copy
-            // (FP64 atomics here cost the launch ~25 us of drain)
-            red_add_row<ell>(g.s2stage + (h1 * 128 + lrow + g.n1 * (kL0 + a)) * ell, v);
-          }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bar(TML_EMPTY + a));
-        }
-      } else {
+      {
         for (int h1 = 0; h1 < g.H1; ++h1) {
           const int64_t i1 = h1 * 128 + lrow;
           float acc[ell];
@@ -826,7 +830,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
       const int64_t tl = l_group(g, t);
       if (tl != cur_tl) {
         if (cur_tl >= 0) {
-          ok = flush_L(cur_kL0, cur_nA, lf);
+          if (!KRY) ok = flush_L(cur_kL0, cur_nA, lf);
           ++lf;
           if (!ok) break;
         }
@@ -839,6 +843,8 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         // lane's row of D_Y (plane gl, slice kk) times the rounded product of
         // the plane's mode-3 and mode-2 rows, summed into the lane's R_3 row
         bool yok = true;
+        // the run's last tile: each kL slot is drained after its last super-plane
+        const bool run_end = t + 1 >= ntiles || l_group(g, t + 1) != tl;
         for (int b = 0; b < tinf.nB && yok; ++b) {
           for (int a = 0; a < tinf.nA; ++a, ++spn) {
             const uint32_t yb = spn & 1;
@@ -877,6 +883,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(TMY_EMPTY + yb));
+            if (run_end && b == tinf.nB - 1) drain_slot(tinf.kL0 + a, a);
             if (++ytiles == kYSuper) {
               flush_Y();
               ytiles = 0;
@@ -938,7 +945,7 @@ __global__ void __launch_bounds__(Roles<KRY>::threads, 1) sketch_slab_kernel(con
         ytiles = 0;
       }
     }
-    if (ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
+    if (!KRY && ok && cur_tl >= 0 && !*abort_flag) flush_L(cur_kL0, cur_nA, lf);
     if (ok && !*abort_flag && ytiles > 0) flush_Y();
     if constexpr (KRY) {
       // S_1 rows i_1: the lane's sums over every run of the CTA
