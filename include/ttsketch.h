@@ -157,7 +157,7 @@ typedef struct {
  * 2e-8 relative error (measured on GB300); in the one-pass middle sketch
  * S_{d*} that error enters the cores directly.  On the 256^4 Hilbert-type
  * tensor at eps = 1e-6 (FP16, Khatri-Rao, 1 GiB slabs) it brings ||X - X~||
- * / ||X|| from 2.1e-6 to 8.9e-7 for about 7 % more sketch time (dense test
+ * / ||X|| from 2.5e-6 to 8.8e-7 for about 6 % more sketch time (dense test
  * matrices and whole-last-mode launches: 9-14 % more, and the FP64 path's
  * ranks where the default chains take one or two more on the first bond).
  * Other kernels ignore it. */
