@@ -40,3 +40,32 @@ def test_reference_arm_prints_on_rank0_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_traffic_record_is_current_and_goes_null_on_change(tmp_path):
+    """The committed ncu traffic figure is read only while the profiled
+    kernel's source (and its planner) is the one it was captured on: the
+    bench reports it for the current source, and null once that code
+    changes."""
+    import json
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    tag = "sketch_slab_kernel_fp16_kr_256x256x256x16"
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[tag]
+    assert bench.traffic_record(tag) == rec["dram_bytes_per_launch"]
+    # the same check on a copy of the tree whose kernel source differs by one byte
+    fake = tmp_path / "root"
+    (fake / "profiles").mkdir(parents=True)
+    shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), fake / "profiles" / "traffic.json")
+    src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    a = src.index(rec["region"][0].encode()) + len(rec["region"][0])
+    dst = fake / rec["source"]
+    dst.parent.mkdir(parents=True)
+    dst.write_bytes(src[:a] + b" " + src[a:])
+    old = bench.ROOT
+    try:
+        bench.ROOT = str(fake)
+        assert bench.traffic_record(tag) is None
+    finally:
+        bench.ROOT = old
